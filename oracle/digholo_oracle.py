@@ -1,0 +1,317 @@
+"""FP64 CPU oracle for digHolo's off-axis reconstruction path.
+
+TEST INFRASTRUCTURE ONLY.  Nothing in the library imports this module; only ``tests/``,
+``__graft_entry__.smoke()`` and the CPU-baseline / reference legs of ``bench.py`` may use it.  It shares no
+code with the CUDA path: it is written from the paper's description of the method (the user guide's
+"Background" and "digHolo processing pipeline" sections) and computes every step as its plain definition,
+in float64 / complex128, with numpy matrix products as the only library primitive:
+
+1. window cut around the beam centre (pipeline step 1, digHoloConfigSetBeamCentre);
+2. the window's spectrum F(k) = sum_n I_n exp(-2 pi i k x_n / (N px)) evaluated directly on the bins of the
+   selected box (pipeline step 1, the FFT; explicit DFT matrices, no fast transform);
+3. the circular Fourier window of radius w_c around the reference tilt (pipeline step 2,
+   digHoloConfigSetFourierWindowRadius, digHoloConfigSetTilt);
+4. the reduced-size inverse transform with the residual tilt and the defocus removed
+   (pipeline step 2, digHoloConfigSetIFFTResolutionMode, digHoloProcessRemoveTilt, digHoloConfigSetDefocus);
+5. the Hermite-Gaussian basis by its three-term recurrence and the overlap sums
+   (pipeline step 3, digHoloConfigSetBasisGroupCount, digHoloConfigSetBasisWaist);
+6. total captured power per alignment candidate (the quantity the AutoAlign search scores).
+
+Conventions the paper leaves open (the same readings are used by the CUDA library):
+
+* x is the fast axis; window pixel n of polarisation p sits at x_n = (o + n) px - c with
+  o = round_half_away(c / px) - N/2 and c the beam centre in metres;
+* angles map to bins linearly: kappa = theta_rad N px / lambda, r = w_c,rad N px / lambda;
+* the box is M x M bins starting at k0 - M/2 with k0 = round_half_away(kappa); a bin is kept when it lies
+  inside the circle ((k - kappa)/r)^2 summed over both axes <= 1 and inside the real-to-complex half plane
+  0 <= k_x <= N/2; everything else is zero;
+* the field is sampled at x'_i = (i - M/2) N px / M relative to the beam centre and equals
+      E(x'_i, y'_j) = 1/(Nx Ny) sum_q F(k0 + q) exp(+2 pi i q.x'/(N px))
+                       * exp(-2 pi i (kappa - k0).x'/(N px)) * exp(-i pi D |x'|^2 / lambda),
+  i.e. the reference's own tilt and defocus phase multiply the inverse transform, which returns
+  A_R * S for a band-limited signal;
+* M defaults to the paper's size rule M = 16 ceil(2 r / 16) (the FFT [IFFT] table of the Benchmarks
+  section);
+* u_n(x) = (sqrt(2)/w)^(1/2) psi_n(sqrt(2) x / w) with psi_0 = pi^(-1/4) exp(-xi^2/2),
+  psi_{n+1} = sqrt(2/(n+1)) xi psi_n - sqrt(n/(n+1)) psi_{n-1}; modes (m, n) with m + n < G ordered by group
+  then m ascending; c_mn = dx' dy' sum_ij u_m(x'_i) u_n(y'_j) E_ji (the basis is real).
+
+Every function below is pinned by ``tests/test_oracle_pins.py`` against values the paper prints, closed
+forms, library special cases or brute force.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+from typing import List, Sequence, Tuple
+
+import numpy as np
+
+# ---------------------------------------------------------------------------------------------------
+# Geometry rules (Background: "How do you choose the angle of the Reference Field?")
+# ---------------------------------------------------------------------------------------------------
+
+
+def w_max_rad(wavelength: float, pixel: float) -> float:
+    """Largest resolvable angle lambda / (2 px), radians (Background, worked example)."""
+    return wavelength / (2.0 * pixel)
+
+
+def window_radius_fraction() -> float:
+    """Largest non-overlapping window radius as a fraction of w_max: sqrt(2) / (3 + sqrt(2)) (Background)."""
+    return math.sqrt(2.0) / (3.0 + math.sqrt(2.0))
+
+
+def wrap_radius_fraction() -> float:
+    """Window fraction when the window may wrap along one axis: positive root of 8 w^2 + 2 w - 2 = 0
+    (Background; the printed equation is garbled, the printed root (-2 + sqrt(68)) / 16 fixes it)."""
+    a, b, c = 8.0, 2.0, -2.0
+    return (-b + math.sqrt(b * b - 4.0 * a * c)) / (2.0 * a)
+
+
+def rule_tilt(radius: float) -> float:
+    """Per-axis reference tilt 3 w_c / sqrt(2) that puts the window beside the autocorrelation term."""
+    return 3.0 * radius / math.sqrt(2.0)
+
+
+def ifft_size_rule(r_bins: float) -> int:
+    """Reduced inverse-transform size: the window diameter rounded up to a multiple of 16 pixels
+    (the FFT [IFFT] size table of the Benchmarks section: 64[32], 128[48], 256[96], 512[176], 1024[336])."""
+    return int(16 * math.ceil(2.0 * r_bins / 16.0))
+
+
+def round_half_away(v: float) -> int:
+    """Nearest integer, halves rounded away from zero."""
+    return int(math.copysign(math.floor(abs(v) + 0.5), v))
+
+
+@dataclass
+class AxisGeometry:
+    n: int            # FFT window length N along this axis
+    origin: int       # frame index of window pixel 0
+    centre: float     # beam centre, metres
+    kappa: float      # reference tilt, bins
+    k0: int           # box centre bin
+    m: int            # box / field length M
+    dx: float         # field sample pitch N px / M, metres
+
+    @property
+    def klo(self) -> int:
+        return self.k0 - self.m // 2
+
+    def pixel_positions(self, pixel: float) -> np.ndarray:
+        """x_n = (o + n) px - c for the window pixels."""
+        return (self.origin + np.arange(self.n)) * pixel - self.centre
+
+    def field_positions(self) -> np.ndarray:
+        """x'_i = (i - M/2) dx'."""
+        return (np.arange(self.m) - self.m // 2) * self.dx
+
+
+@dataclass
+class PolGeometry:
+    x: AxisGeometry
+    y: AxisGeometry
+    r_x: float        # window radius, bins along x
+    r_y: float        # window radius, bins along y
+    defocus: float    # dioptre
+    waist: float      # metres
+    groups: int
+    pixel: float
+    wavelength: float
+
+
+def pol_geometry(setup, p: int, tilt_deg=None, defocus=None, waist=None) -> PolGeometry:
+    """Per-polarisation geometry from the acquisition settings (Alignment: beam centre, tilt, defocus;
+    Window sizes: FFT window, Fourier window radius, IFFT resolution mode 1)."""
+    px, lam = float(setup.pixel), float(setup.wavelength)
+    n = int(setup.window)
+    tdeg = setup.tilt_deg[p] if tilt_deg is None else tilt_deg
+    dfc = float(setup.defocus[p] if defocus is None else defocus)
+    wst = float(setup.waist[p] if waist is None else waist)
+    r_rad = math.radians(float(setup.radius_deg))
+    axes = []
+    for ax in range(2):
+        c = float(setup.beam_centre[p][ax])
+        origin = round_half_away(c / px) - n // 2
+        kappa = math.radians(float(tdeg[ax])) * n * px / lam
+        axes.append((c, origin, kappa))
+    r_bins = r_rad * n * px / lam
+    m = int(setup.ifft_size) if int(setup.ifft_size) > 0 else ifft_size_rule(r_bins)
+    ag = [AxisGeometry(n=n, origin=o, centre=c, kappa=k, k0=round_half_away(k), m=m, dx=n * px / m)
+          for (c, o, k) in axes]
+    return PolGeometry(x=ag[0], y=ag[1], r_x=r_bins, r_y=r_bins, defocus=dfc, waist=wst,
+                       groups=int(setup.group_count), pixel=px, wavelength=lam)
+
+
+# ---------------------------------------------------------------------------------------------------
+# Pipeline step 1: the window and its spectrum on the selected bins
+# ---------------------------------------------------------------------------------------------------
+
+
+def cut_window(frame: np.ndarray, g: PolGeometry) -> np.ndarray:
+    """The N x N window of polarisation p, as float64 (pipeline step 1; uint16 converts exactly)."""
+    oy, ox, n = g.y.origin, g.x.origin, g.x.n
+    if oy < 0 or ox < 0 or oy + n > frame.shape[0] or ox + n > frame.shape[1]:
+        raise ValueError("window outside the frame")
+    return np.asarray(frame[oy:oy + n, ox:ox + n], dtype=np.float64)
+
+
+def dft_rows(ax: AxisGeometry, pixel: float, bins: np.ndarray) -> np.ndarray:
+    """exp(-2 pi i k x_n / (N px)) for the given integer bins k (rows) and window pixels n (columns)."""
+    xn = ax.pixel_positions(pixel)
+    return np.exp(-2j * np.pi * np.outer(bins, xn) / (ax.n * pixel))
+
+
+def box_bins(ax: AxisGeometry) -> np.ndarray:
+    """The M integer bins k0 - M/2 ... k0 + M/2 - 1 of the selected box (unwrapped)."""
+    return ax.klo + np.arange(ax.m)
+
+
+def window_spectrum(window: np.ndarray, g: PolGeometry, bins_x=None, bins_y=None) -> np.ndarray:
+    """F(k_y, k_x) = sum_{n_y, n_x} I exp(-2 pi i (k_x x_n + k_y y_n) / (N px)) on the box bins, as the
+    separable product A_y I A_x^T of explicit DFT matrices (pipeline step 1, the real-to-complex FFT)."""
+    bx = box_bins(g.x) if bins_x is None else np.asarray(bins_x)
+    by = box_bins(g.y) if bins_y is None else np.asarray(bins_y)
+    ax_m = dft_rows(g.x, g.pixel, bx)
+    ay_m = dft_rows(g.y, g.pixel, by)
+    return ay_m @ window @ ax_m.T
+
+
+# ---------------------------------------------------------------------------------------------------
+# Pipeline step 2: circular Fourier window, reduced inverse transform, tilt and defocus removal
+# ---------------------------------------------------------------------------------------------------
+
+
+def window_mask(g: PolGeometry) -> np.ndarray:
+    """Bins of the box kept by the circular window (radius r around the tilt kappa) and lying in the
+    real-to-complex half plane 0 <= k_x <= N/2 (pipeline step 2; digHoloGetFourierPlaneFull's (w/2+1) width)."""
+    kx = box_bins(g.x).astype(np.float64)
+    ky = box_bins(g.y).astype(np.float64)
+    dx = (kx - g.x.kappa) / g.r_x
+    dy = (ky - g.y.kappa) / g.r_y
+    inside = (dy[:, None] ** 2 + dx[None, :] ** 2) <= 1.0
+    half = (kx >= 0) & (kx <= g.x.n // 2)
+    return inside & half[None, :]
+
+
+def reconstruct_field(f_box: np.ndarray, mask: np.ndarray, g: PolGeometry) -> np.ndarray:
+    """E(x'_i, y'_j) by the explicit inverse sum over the kept bins, times the reference's residual
+    tilt and defocus phase (pipeline step 2 and digHoloProcessRemoveTilt)."""
+    px, lam = g.pixel, g.wavelength
+    out = []
+    for ax in (g.x, g.y):
+        q = np.arange(ax.m) - ax.m // 2                     # k - k0
+        xp = ax.field_positions()
+        inv = np.exp(2j * np.pi * np.outer(xp, q) / (ax.n * px))          # [i][q]
+        tilt = np.exp(-2j * np.pi * (ax.kappa - ax.k0) * xp / (ax.n * px))
+        focus = np.exp(-1j * np.pi * g.defocus * xp ** 2 / lam)
+        out.append((inv, tilt * focus))
+    (bx, cx), (by, cy) = out
+    e = by @ (f_box * mask) @ bx.T / (g.x.n * g.y.n)
+    return e * cy[:, None] * cx[None, :]
+
+
+# ---------------------------------------------------------------------------------------------------
+# Pipeline step 3: Hermite-Gaussian modal decomposition
+# ---------------------------------------------------------------------------------------------------
+
+
+def hg_1d(n_max: int, x: np.ndarray, waist: float) -> np.ndarray:
+    """u_0 .. u_{n_max-1} at positions x by the three-term recurrence (Modal decomposition:
+    Hermite-Gaussian modes of the given waist, stored separably in x and y)."""
+    x = np.asarray(x, dtype=np.float64)
+    xi = math.sqrt(2.0) * x / waist
+    psi = np.zeros((max(n_max, 1),) + x.shape)
+    psi[0] = math.pi ** -0.25 * np.exp(-xi ** 2 / 2.0)
+    if n_max > 1:
+        psi[1] = math.sqrt(2.0) * xi * psi[0]
+    for n in range(1, n_max - 1):
+        psi[n + 1] = math.sqrt(2.0 / (n + 1)) * xi * psi[n] - math.sqrt(n / (n + 1.0)) * psi[n - 1]
+    return math.sqrt(math.sqrt(2.0) / waist) * psi[:n_max]
+
+
+def mode_list(groups: int) -> List[Tuple[int, int]]:
+    """HG(m, n) with m + n < groups, by group g = m + n then m ascending (digHoloConfigSetBasisGroupCount)."""
+    return [(m, g - m) for g in range(groups) for m in range(g + 1)]
+
+
+def overlap(e: np.ndarray, g: PolGeometry) -> np.ndarray:
+    """c_mn = dx' dy' sum_{j,i} u_m(x'_i) u_n(y'_j) E(x'_i, y'_j) for every mode (pipeline step 3)."""
+    if g.groups <= 0:
+        return np.zeros(0, dtype=np.complex128)
+    ux = hg_1d(g.groups, g.x.field_positions(), g.waist)    # [G][Mx]
+    uy = hg_1d(g.groups, g.y.field_positions(), g.waist)    # [G][My]
+    full = uy @ e @ ux.T * (g.x.dx * g.y.dx)                  # [n][m]
+    return np.array([full[n, m] for (m, n) in mode_list(g.groups)])
+
+
+# ---------------------------------------------------------------------------------------------------
+# Whole path
+# ---------------------------------------------------------------------------------------------------
+
+
+def process_window(frame: np.ndarray, g: PolGeometry):
+    """Steps 1-3 for one polarisation of one frame: returns (F_box, mask, field, coefficients)."""
+    win = cut_window(frame, g)
+    f_box = window_spectrum(win, g)
+    mask = window_mask(g)
+    e = reconstruct_field(f_box, mask, g)
+    return f_box, mask, e, overlap(e, g)
+
+
+def process_batch(frames: np.ndarray, setup) -> Tuple[np.ndarray, np.ndarray]:
+    """digHoloProcessBatch: fields [B][P][M][M] and coefficients [B][P][modes] (pol-blocked, as
+    digHoloBasisGetCoefs lays them out)."""
+    geos = [pol_geometry(setup, p) for p in range(setup.pol_count)]
+    m = geos[0].x.m
+    modes = len(mode_list(geos[0].groups))
+    B = frames.shape[0]
+    fields = np.empty((B, setup.pol_count, m, m), dtype=np.complex128)
+    coefs = np.empty((B, setup.pol_count, modes), dtype=np.complex128)
+    for b in range(B):
+        for p, g in enumerate(geos):
+            _, _, e, c = process_window(frames[b], g)
+            fields[b, p] = e
+            coefs[b, p] = c
+    return fields, coefs
+
+
+def score_settings(frames: np.ndarray, setup, tilt_deg: np.ndarray, defocus: np.ndarray,
+                   waist: np.ndarray) -> np.ndarray:
+    """Total captured power P[b][s] = sum_p sum_modes |c_{b,p,s}|^2 for every alignment candidate s,
+    each candidate re-running window selection, inverse transform, correction and overlap with its own
+    tilt, defocus and waist (the inner loop of the AutoAlign search)."""
+    B, S = frames.shape[0], tilt_deg.shape[0]
+    power = np.zeros((B, S))
+    for b in range(B):
+        for s in range(S):
+            tot = 0.0
+            for p in range(setup.pol_count):
+                g = pol_geometry(setup, p, tilt_deg=tilt_deg[s, p], defocus=defocus[s, p], waist=waist[s, p])
+                win = cut_window(frames[b], g)
+                e = reconstruct_field(window_spectrum(win, g), window_mask(g), g)
+                c = overlap(e, g)
+                tot += float(np.sum(np.abs(c) ** 2))
+            power[b, s] = tot
+    return power
+
+
+def output_axes(g: PolGeometry) -> Tuple[np.ndarray, np.ndarray]:
+    """x and y axes of the reconstructed field, metres from the beam centre (digHoloGetFields)."""
+    return g.x.field_positions(), g.y.field_positions()
+
+
+def validate(g: PolGeometry) -> None:
+    """Reject geometries whose circle centre leaves the real-to-complex half plane or whose box is
+    larger than the window (the library returns an invalid-argument code for these)."""
+    if not (0.0 < g.x.kappa <= g.x.n / 2.0):
+        raise ValueError("tilt x outside the half plane")
+    if g.x.m > g.x.n or g.y.m > g.y.n or g.x.m % 16 or g.y.m % 16:
+        raise ValueError("bad field size")
+    if g.r_x <= 0.0:
+        raise ValueError("window radius must be positive")
+
+
+def geometries(setup) -> Sequence[PolGeometry]:
+    return [pol_geometry(setup, p) for p in range(setup.pol_count)]

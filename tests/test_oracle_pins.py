@@ -1,0 +1,281 @@
+"""Pins for the FP64 oracle: each check ties it to something other than itself.
+
+* values the paper prints (worked example of the window-radius rule, the FFT [IFFT] size table);
+* library special cases (numpy.fft.fft2 when the beam centre sits on a pixel, numpy's Hermite polynomials);
+* closed forms (exact recovery of a band-limited signal carried by a tilted, defocused reference; HG
+  orthonormality; single-mode overlaps);
+* invariants (Parseval);
+* planted mistakes, showing that the pins above fail when the oracle is wrong.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+from oracle import digholo_oracle as orc
+from synth import holograms as syn
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "paper_worked_example.json")
+PX, LAM = 20e-6, 1565e-9
+
+
+def _golden():
+    with open(GOLDEN) as f:
+        return json.load(f)
+
+
+# ----------------------------------------------------------------------------- printed values
+
+
+def test_worked_example_window_rule():
+    gd = _golden()
+    tol = gd["printed_precision_rel"]
+    wmax = math.degrees(orc.w_max_rad(gd["wavelength_m"], gd["pixel_m"]))
+    assert wmax == pytest.approx(gd["w_max_deg_printed"], rel=tol)
+    frac = orc.window_radius_fraction()
+    assert frac == pytest.approx(gd["window_fraction_printed"], rel=tol)
+    wc = frac * wmax
+    assert wc <= gd["window_radius_deg_printed_upper_bound"] * (1 + tol)
+    assert wc == pytest.approx(gd["window_radius_deg_printed_upper_bound"], rel=tol)
+    t = orc.rule_tilt(wc)
+    for v in gd["tilt_deg_printed"]:
+        assert t == pytest.approx(v, rel=tol)
+    assert orc.wrap_radius_fraction() == pytest.approx(gd["wrap_fraction_printed"], rel=tol)
+    # the wrap root solves 8 w^2 + 2 w - 2 = 0
+    w = orc.wrap_radius_fraction()
+    assert 8 * w * w + 2 * w - 2 == pytest.approx(0.0, abs=1e-12)
+
+
+def test_ifft_size_table():
+    gd = _golden()
+    for n, m in gd["fft_ifft_sizes_printed"]:
+        r_bins = orc.window_radius_fraction() * n / 2.0   # w_c N px / lambda with w_c = frac * lambda/(2 px)
+        assert orc.ifft_size_rule(r_bins) == m
+
+
+def test_mode_count_and_order():
+    for g, k in [(5, 15), (9, 45), (15, 120), (20, 210), (0, 0), (1, 1)]:
+        assert len(orc.mode_list(g)) == k
+    assert orc.mode_list(3) == [(0, 0), (0, 1), (1, 0), (0, 2), (1, 1), (2, 0)]
+
+
+def test_round_half_away():
+    assert [orc.round_half_away(v) for v in (2.5, -2.5, 2.49, -0.5, 0.5, 3.0)] == [3, -3, 2, -1, 1, 3]
+
+
+# ----------------------------------------------------------------------------- spectrum
+
+
+def _geom(n=16, m=16, centre=(8.0, 8.0), kappa=(5.0, 4.0), r=3.0, defocus=0.0, waist=100e-6, groups=3):
+    ax = []
+    for a in range(2):
+        c = centre[a] * PX
+        o = orc.round_half_away(c / PX) - n // 2
+        ax.append(orc.AxisGeometry(n=n, origin=o, centre=c, kappa=kappa[a], k0=orc.round_half_away(kappa[a]),
+                                   m=m, dx=n * PX / m))
+    return orc.PolGeometry(x=ax[0], y=ax[1], r_x=r, r_y=r, defocus=defocus, waist=waist, groups=groups,
+                           pixel=PX, wavelength=LAM)
+
+
+def test_spectrum_equals_numpy_fft_for_pixel_centred_window():
+    rng = np.random.default_rng(1)
+    n = 16
+    g = _geom(n=n, centre=(10.0, 9.0))
+    frame = rng.standard_normal((24, 24))
+    win = orc.cut_window(frame, g)
+    bins = np.arange(-n // 2, n // 2 + 5)          # more than one period, unwrapped
+    f = orc.window_spectrum(win, g, bins_x=bins, bins_y=bins)
+    d = np.fft.fft2(win)                             # d[ky][kx]
+    sign = (-1.0) ** (bins[:, None] + bins[None, :])
+    ref = sign * d[np.ix_(bins % n, bins % n)]
+    assert np.max(np.abs(f - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+def test_spectrum_parseval_subpixel_centre():
+    rng = np.random.default_rng(2)
+    n = 32
+    g = _geom(n=n, centre=(16.37, 15.81))
+    frame = rng.uniform(0, 4095, size=(40, 40))
+    win = orc.cut_window(frame, g)
+    bins = np.arange(3, 3 + n)                       # any n consecutive bins form a full period
+    f = orc.window_spectrum(win, g, bins_x=bins, bins_y=bins)
+    assert np.sum(np.abs(f) ** 2) / n ** 2 == pytest.approx(np.sum(win ** 2), rel=1e-12)
+
+
+# ----------------------------------------------------------------------------- closed-form recovery
+
+
+def _trig_case(n=64, m=32, centre=(40.37, 39.81), kappa=(12.3, 10.7), r=9.0, dioptre=1.7, a_r=2.5, seed=3):
+    """Linear hologram A_R^2 + 2 Re(A_R S R*) of a signal S chosen so that S R* has integer frequencies:
+    S = P(x, y) exp(-2 pi i (kappa - k0).x/(N px)) exp(-i pi D |x|^2 / lambda), P a trigonometric
+    polynomial whose bins k0 + q lie inside the circle.  The exact reconstruction is A_R S on the grid."""
+    rng = np.random.default_rng(seed)
+    g = _geom(n=n, m=m, centre=centre, kappa=kappa, r=r, defocus=dioptre)
+    k0 = np.array([g.x.k0, g.y.k0])
+    kap = np.array(kappa)
+    qs = []
+    for qx in range(-4, 5):
+        for qy in range(-4, 5):
+            if ((k0[0] + qx - kap[0]) ** 2 + (k0[1] + qy - kap[1]) ** 2) <= (0.9 * r) ** 2 and rng.uniform() < 0.6:
+                qs.append((qx, qy))
+    amps = rng.standard_normal(len(qs)) + 1j * rng.standard_normal(len(qs))
+
+    def signal(X, Y):
+        p = np.zeros(np.broadcast(X, Y).shape, dtype=np.complex128)
+        for (qx, qy), a in zip(qs, amps):
+            p += a * np.exp(2j * np.pi * (qx * X + qy * Y) / (n * PX))
+        res = np.exp(-2j * np.pi * ((kap[0] - k0[0]) * X + (kap[1] - k0[1]) * Y) / (n * PX))
+        foc = np.exp(-1j * np.pi * dioptre * (X ** 2 + Y ** 2) / LAM)
+        return p * res * foc
+
+    H = W = 80
+    X = np.arange(W)[None, :] * PX - g.x.centre
+    Y = np.arange(H)[:, None] * PX - g.y.centre
+    R = np.exp(-2j * np.pi * (kap[0] * X + kap[1] * Y) / (n * PX)) * np.exp(-1j * np.pi * dioptre * (X ** 2 + Y ** 2) / LAM)
+    S = signal(X, Y)
+    frame = a_r ** 2 + 2.0 * np.real(a_r * S * np.conj(R))
+    xp, yp = orc.output_axes(g)
+    expected = a_r * signal(xp[None, :], yp[:, None])
+    return g, frame, expected
+
+
+@pytest.mark.parametrize("case", [
+    dict(),
+    dict(n=32, m=16, centre=(20.5, 19.49), kappa=(6.6, 9.2), r=4.5, dioptre=-3.0),
+    dict(n=64, m=48, centre=(37.0, 41.0), kappa=(14.0, -9.0), r=8.0, dioptre=0.0),
+])
+def test_exact_recovery_band_limited(case):
+    g, frame, expected = _trig_case(**case)
+    _, mask, e, _ = orc.process_window(frame, g)
+    err = np.linalg.norm(e - expected) / np.linalg.norm(expected)
+    assert err < 1e-10, err
+
+
+def test_hermite_recurrence_matches_library_polynomials():
+    x = np.linspace(-2e-3, 2e-3, 401)
+    for w in (150e-6, 400e-6):
+        u = orc.hg_1d(21, x, w)
+        ref = syn.hg_closed_form(21, x, w)
+        assert np.max(np.abs(u - ref)) < 1e-11 * np.max(np.abs(ref))
+    # u_0 has unit norm and the 1/e^2 intensity radius w
+    w = 200e-6
+    u0 = orc.hg_1d(1, np.array([0.0, w]), w)[0]
+    assert u0[1] / u0[0] == pytest.approx(math.exp(-1.0), rel=1e-14)
+    assert u0[0] == pytest.approx((2.0 / (math.pi * w * w)) ** 0.25, rel=1e-14)
+
+
+def test_hg_orthonormal_on_fine_grid():
+    w = 300e-6
+    dx = w / 16
+    x = (np.arange(512) - 256) * dx
+    u = orc.hg_1d(20, x, w)
+    gram = u @ u.T * dx
+    assert np.max(np.abs(gram - np.eye(20))) < 1e-10
+
+
+def test_overlap_single_asymmetric_mode():
+    # fine output grid so the discrete Gram matrix is the identity to rounding
+    n, m = 256, 256
+    g = _geom(n=n, m=m, centre=(128.0, 128.0), kappa=(60.0, 60.0), r=10.0, waist=8 * n * PX / m, groups=6)
+    xp, yp = orc.output_axes(g)
+    ux = orc.hg_1d(6, xp, g.waist)
+    uy = orc.hg_1d(6, yp, g.waist)
+    modes = orc.mode_list(6)
+    for (mm, nn) in [(3, 1), (0, 2), (4, 1)]:
+        e = (1.5 - 0.5j) * uy[nn][:, None] * ux[mm][None, :]
+        c = orc.overlap(e, g)
+        target = np.zeros(len(modes), dtype=complex)
+        target[modes.index((mm, nn))] = 1.5 - 0.5j
+        assert np.max(np.abs(c - target)) < 1e-10
+
+
+def test_end_to_end_hg_recovery_linear_hologram():
+    """A linear hologram of a known HG superposition on an on-bin tilt returns A_R * c_true."""
+    setup = syn.Setup(name="pin", frame_w=160, frame_h=160, pol_count=1, window=128,
+                      beam_centre=[(80.3 * PX, 79.6 * PX)], tilt_deg=[(0.0, 0.0)], defocus=[0.9],
+                      radius_deg=0.32 * math.degrees(LAM / (2 * PX)), ifft_size=64, group_count=5,
+                      waist=[200e-6], signal_groups=5)
+    # tilt so that kappa is an integer number of bins (40, 37)
+    setup.tilt_deg = [(math.degrees(40 * LAM / (128 * PX)), math.degrees(37 * LAM / (128 * PX)))]
+    rng = np.random.default_rng(7)
+    c_true = syn.random_unit_coefs(rng, 15)
+    g = orc.pol_geometry(setup, 0)
+    H = W = 160
+    X = np.arange(W) * PX - g.x.centre
+    Y = np.arange(H) * PX - g.y.centre
+    ux = syn.hg_closed_form(5, X, 200e-6)
+    uy = syn.hg_closed_form(5, Y, 200e-6)
+    S = sum(c * uy[n][:, None] * ux[m][None, :] for c, (m, n) in zip(c_true, orc.mode_list(5)))
+    fx, fy = (math.radians(t) / LAM for t in setup.tilt_deg[0])
+    R = np.exp(-2j * np.pi * (fx * X[None, :] + fy * Y[:, None])) * \
+        np.exp(-1j * np.pi * 0.9 * (X[None, :] ** 2 + Y[:, None] ** 2) / LAM)
+    a_r = float(np.abs(S).max())
+    frame = a_r ** 2 + 2 * np.real(a_r * S * np.conj(R))
+    _, _, _, c = orc.process_window(frame, g)
+    assert np.linalg.norm(c - a_r * c_true) / a_r < 1e-6
+
+
+def test_score_is_total_power_of_per_candidate_runs():
+    setup = syn.setup_plain()
+    setup = syn.with_(setup, group_count=3)
+    data = syn.make_frames(setup, 2, seed=11)
+    cand = syn.candidate_settings(setup, 3, seed=12)
+    p = orc.score_settings(data["frames"], setup, cand["tilt_deg"], cand["defocus"], cand["waist"])
+    for b in range(2):
+        for s in range(3):
+            su = syn.with_(setup, tilt_deg=[tuple(cand["tilt_deg"][s, 0])], defocus=[cand["defocus"][s, 0]],
+                           waist=[cand["waist"][s, 0]])
+            _, coefs = orc.process_batch(data["frames"][b:b + 1], su)
+            assert p[b, s] == pytest.approx(float(np.sum(np.abs(coefs) ** 2)), rel=1e-12)
+
+
+def test_synthetic_frames_recover_close_to_truth():
+    """On the plain 128x128 case the oracle's coefficients approach field_scale * c_true; the |S|^2
+    leakage and noise are physics, so this bound is loose (reported, not a parity bound)."""
+    setup = syn.setup_plain()
+    data = syn.make_frames(setup, 1, seed=5)
+    _, coefs = orc.process_batch(data["frames"], setup)
+    ref = data["field_scale"][0, 0] * data["coefs_true"][0, 0]
+    assert np.linalg.norm(coefs[0, 0] - ref) / np.linalg.norm(ref) < 0.2
+
+
+# ----------------------------------------------------------------------------- planted mistakes
+
+
+def test_planted_defocus_sign_fails_exact_recovery(monkeypatch):
+    g, frame, expected = _trig_case()
+    orig = orc.reconstruct_field
+
+    def mutant(f_box, mask, geo):
+        geo2 = orc.PolGeometry(**{**geo.__dict__, "defocus": -geo.defocus})
+        return orig(f_box, mask, geo2)
+
+    monkeypatch.setattr(orc, "reconstruct_field", mutant)
+    _, _, e, _ = orc.process_window(frame, g)
+    assert np.linalg.norm(e - expected) / np.linalg.norm(expected) > 1e-3
+
+
+def test_planted_transposed_field_fails_mode_pin(monkeypatch):
+    n = m = 256
+    g = _geom(n=n, m=m, centre=(128.0, 128.0), kappa=(60.0, 60.0), r=10.0, waist=8 * n * PX / m, groups=6)
+    xp, yp = orc.output_axes(g)
+    e = orc.hg_1d(6, yp, g.waist)[1][:, None] * orc.hg_1d(6, xp, g.waist)[3][None, :]
+    orig = orc.overlap
+    monkeypatch.setattr(orc, "overlap", lambda f, geo: orig(f.T, geo))
+    c = orc.overlap(e, g)
+    assert abs(c[orc.mode_list(6).index((3, 1))]) < 0.5
+
+
+def test_planted_spectrum_sign_fails_fft_pin(monkeypatch):
+    rng = np.random.default_rng(1)
+    n = 16
+    g = _geom(n=n, centre=(10.0, 9.0))
+    win = orc.cut_window(rng.standard_normal((24, 24)), g)
+    bins = np.arange(-n // 2, n // 2)
+    orig = orc.dft_rows
+    monkeypatch.setattr(orc, "dft_rows", lambda ax, px, b: np.conj(orig(ax, px, b)))
+    f = orc.window_spectrum(win, g, bins_x=bins, bins_y=bins)
+    ref = ((-1.0) ** (bins[:, None] + bins[None, :])) * np.fft.fft2(win)[np.ix_(bins % n, bins % n)]
+    assert np.max(np.abs(f - ref)) > 1e-3 * np.max(np.abs(ref))
