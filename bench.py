@@ -1,0 +1,395 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the reconstruction path (FFT -> window -> IFFT -> HG overlap).
+
+Workload (per GPU and step): 1000 frames of 320x256 uint16 (12-bit, Poisson), two 128x128 polarisation
+windows, 64x64 fields and 45 Hermite-Gaussian coefficients per window.  Synthetic, seeded frames.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  ``value`` is whole-job frames/s with the frames already in HBM; ``e2e`` is the
+same metric through the public API from pinned host frames to host results; ``roofline`` is the dominant
+kernel's algorithmic bytes per launch over its event-timed launch duration against the measured HBM peak;
+``cpu_baseline`` is the FP64 oracle on the host cores.  ``--impl reference`` times the oracle itself, as the
+reference arm.  Multi-GPU runs (torchrun) are weak-scaled: every rank processes its own batch, with no
+collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "frames/s (FFT→window→IFFT→HG overlap) on 1 GB300, % HBM roofline; p99 latency"
+WORKLOAD = "batching: 1000 frames 320x256 u16, 2 pol windows 128x128, 64x64 fields, HG groups 0-8 (45 modes)"
+FRAMES = 1000
+ROTATE = 4                      # distinct input batches cycled between steps (4 x 164 MB > 129 MB L2)
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--precision", choices=["fp32", "split_bf16"], default="fp32")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------------------------ helpers
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def bytes_per_frame(setup, m, modes):
+    """Algorithmic bytes per frame: window pixels read plus fields and coefficients written."""
+    px_bytes = 2 if setup.dtype == "u16" else 4
+    n = setup.window
+    return setup.pol_count * (n * n * px_bytes + m * m * 8 + modes * 8)
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            pk = json.load(f)
+        return float(pk["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs, STREAM-style copy)"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback 6.8 TB/s"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2204_02348_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode())
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel, frames_per_launch):
+    """DRAM bytes per launch from the committed ncu summary, scaled to this launch size, or None when the
+    summary was taken on other kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.md")
+    if not os.path.exists(path):
+        return None
+    src = kernel_source_hash()
+    for line in open(path):
+        m = re.match(r"\|\s*(\w+)\s*\|\s*([0-9a-f]+)\s*\|\s*([0-9.eE+]+)\s*\|\s*(\d+)\s*\|", line)
+        if m and m.group(1) == kernel and m.group(2) == src:
+            return float(m.group(3)) / int(m.group(4)) * frames_per_launch
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms while the timed region runs."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-lms", "50",
+                 "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _oracle_worker(args):
+    frames, setup = args
+    from oracle import digholo_oracle as orc
+    orc.process_batch(frames, setup)
+    return frames.shape[0]
+
+
+class OraclePool:
+    """Spawn-started process pool running the FP64 oracle over frame chunks, one BLAS thread per worker."""
+
+    def __init__(self, workers):
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ[k] = "1"
+        self.workers = workers
+        self.ex = cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn"))
+
+    def warm(self, setup, frames):
+        list(self.ex.map(_oracle_worker, [(frames[:1], setup)] * self.workers))
+
+    def run(self, setup, frames, repeat=1):
+        """Process `repeat` passes over `frames`; returns (frames/s, seconds, frames processed)."""
+        import numpy as np
+        chunks = []
+        for _ in range(repeat):
+            chunks += [c for c in np.array_split(frames, self.workers * 2) if len(c)]
+        t0 = time.perf_counter()
+        n = sum(self.ex.map(_oracle_worker, [(c, setup) for c in chunks]))
+        dt = time.perf_counter() - t0
+        return n / dt, dt, n
+
+    def close(self):
+        self.ex.shutdown()
+
+
+# ------------------------------------------------------------------------------------------ arms
+
+
+def run_reference(args, ws, rank):
+    """Reference arm: the FP64 oracle, as it stands, on the host cores, on the same workload and metric."""
+    from synth import holograms as syn
+    if rank != 0:
+        return
+    setup = syn.setup_batching()
+    sample = 200                                     # frames per step: a bounded sample of the 1000-frame batch
+    data = syn.make_frames(setup, sample)["frames"]
+    workers = os.cpu_count() or 1
+    pool = OraclePool(workers)
+    pool.warm(setup, data)
+    for _ in range(args.warmup):
+        pool.run(setup, data[: max(1, sample // 10)])
+    times = []
+    for _ in range(args.steps):
+        _, dt, n = pool.run(setup, data)
+        times.append(dt)
+    pool.close()
+    total = sum(times)
+    value = args.steps * sample / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "frames_per_step": sample,
+                   "note": "FP64 oracle (explicit DFTs, direct sums) on host cores; each step a 200-frame sample"},
+        "cpu_baseline": {"value": value, "unit": "frames/s", "cores": workers, "kind": "oracle",
+                         "sample": f"{sample} frames of the batching workload per step"},
+        "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args, ws, rank, local):
+    import numpy as np
+    import torch
+
+    import paper_2204_02348_gb300 as dh
+    from synth import holograms as syn
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    setup = syn.setup_batching()
+    prec = dh.DH_PRECISION_SPLIT_BF16 if args.precision == "split_bf16" else dh.DH_PRECISION_FP32
+    data = syn.make_frames(setup, FRAMES, seed=syn.BASE_SEED + 1000 * rank)
+    host = torch.from_numpy(data["frames"]).pin_memory()
+    inputs = [host.to(dev) for _ in range(ROTATE)]
+    h = dh.dh_create()
+    dh.configure(h, setup)
+    dh.dh_set_precision(h, prec)
+    m, modes, _ = dh.dh_get_output_dims(h)
+    P = setup.pol_count
+    fields = torch.empty((FRAMES, P, m, m), dtype=torch.complex64, device=dev)
+    coefs = torch.empty((FRAMES, P, modes), dtype=torch.complex64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(k):
+        dh.dh_process_batch(h, inputs[k % ROTATE], dh.DH_DTYPE_U16, FRAMES, fields, coefs, stream)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    for k in range(max(args.warmup, 3)):
+        step(k)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K steps, event per step, per-kernel events inside the library
+    sampler = ClockSampler(local)
+    dh.dh_set_profiling(h, True)
+    barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    time.sleep(0.1)
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    evs[0].record(stream)
+    for k in range(args.steps):
+        step(k)
+        evs[k + 1].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    prof = dh.dh_get_profile(h)
+    dh.dh_set_profiling(h, False)
+    per_step = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
+    total_ms = evs[0].elapsed_time(evs[-1])
+    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    total_ms = float(t.item())
+    value = ws * FRAMES * args.steps / (total_ms / 1e3)
+
+    # ---- dominant kernel roofline
+    peak, peak_src = measured_peak()
+    bpf = bytes_per_frame(setup, m, modes)
+    dom = max(prof.items(), key=lambda kv: kv[1][1]) if prof else None
+    launches = sum(v[0] for v in prof.values())
+    roofline = None
+    if dom:
+        name, (nl, tms) = dom
+        launches_per_step = nl / args.steps
+        frames_per_launch = FRAMES / launches_per_step
+        avg_s = tms / nl / 1e3
+        achieved = frames_per_launch * bpf / avg_s / 1e9
+        traffic = recorded_traffic(name, frames_per_launch)
+        roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                    "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
+                    "bytes_per_frame": bpf, "frames_per_launch": frames_per_launch,
+                    "kernel_share": tms / sum(v[1] for v in prof.values()),
+                    "step_frac": (value / ws) * bpf / 1e9 / peak}
+
+    # ---- end to end through the public API: pinned host frames in, fields and coefficients out
+    host_f = torch.empty((FRAMES, P, m, m), dtype=torch.complex64).pin_memory()
+    host_c = torch.empty((FRAMES, P, modes), dtype=torch.complex64).pin_memory()
+    dev_in = torch.empty_like(inputs[0])
+    e2e_steps = max(3, min(args.steps, 20))
+
+    def e2e_step():
+        dev_in.copy_(host, non_blocking=True)
+        dh.dh_process_batch(h, dev_in, dh.DH_DTYPE_U16, FRAMES, fields, coefs, stream)
+        host_f.copy_(fields, non_blocking=True)
+        host_c.copy_(coefs, non_blocking=True)
+        stream.synchronize()
+
+    for _ in range(2):
+        e2e_step()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e2e_steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    et = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.all_reduce(et, op=dist.ReduceOp.MAX)
+    e2e = {"value": ws * FRAMES * e2e_steps / (float(et.item()) / 1e3), "unit": "frames/s",
+           "h2d_bytes_per_step": int(host.numel() * 2),
+           "d2h_bytes_per_step": int(host_f.numel() * 8 + host_c.numel() * 8), "steps": e2e_steps}
+
+    # ---- CPU baseline (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        workers = os.cpu_count() or 1
+        pool = OraclePool(workers)
+        pool.warm(setup, data["frames"])
+        rate, dt, n = pool.run(setup, data["frames"], repeat=2)
+        pool.close()
+        cpu = {"value": rate, "unit": "frames/s", "cores": workers, "kind": "oracle",
+               "sample": f"{n} frames (the step's 1000-frame batch, twice) in {dt:.1f} s"}
+
+    dh.dh_destroy(h)
+    if rank == 0:
+        lat = sorted(per_step)
+        line = {
+            "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "frames_per_step_per_gpu": FRAMES, "frame": [320, 256],
+                       "pols": P, "window": setup.window, "field": m, "modes": modes,
+                       "overlap": args.precision, "l2": f"{ROTATE} rotating input batches "
+                       f"({ROTATE * host.numel() * 2 / 1e6:.0f} MB) > 129 MB L2",
+                       "parallelism": f"replicas x{ws}"},
+            "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
+                           "unit": "ms per 1000-frame batch"},
+            "roofline": roofline,
+            "kernels": {k: {"launches": v[0], "total_ms": v[1]} for k, v in prof.items()},
+            "gpu_launches": launches,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    ws, rank, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_ours(args, ws, rank, local)
+
+
+if __name__ == "__main__":
+    main()

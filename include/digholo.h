@@ -1,0 +1,174 @@
+/*
+ * digholo.h - C ABI of the GB300 (sm_103a) batched off-axis hologram reconstruction library.
+ *
+ * The library implements digHolo's processing pipeline (user guide v1.0, "digHolo processing pipeline"):
+ *   1. cut the FFT window around each polarisation's beam centre and Fourier transform it;
+ *   2. select the off-axis term inside a circular Fourier window centred on the reference tilt, shift it
+ *      to the origin, inverse transform it at the window's reduced size, and remove the reference's
+ *      residual tilt and defocus;
+ *   3. project the reconstructed field onto a Hermite-Gaussian basis.
+ * Every step runs as hand-written CUDA kernels on the caller's stream; there is no CPU fallback.
+ *
+ * Conventions (the user guide leaves these open; the same readings are used throughout):
+ *   - frames are row-major [batch][height][width], x fastest; pixel (i, j) is centred at (i px, j px);
+ *   - window origin o = round_half_away(c / px) - N/2 per axis, c the beam centre in metres;
+ *   - angles map to bins linearly: kappa = theta_rad * N * px / lambda, r = w_c,rad * N * px / lambda;
+ *   - the kept bins form an M x M box starting at round_half_away(kappa) - M/2, masked by the circle
+ *     ((k - kappa)/r)^2 summed over both axes <= 1 and by the real-to-complex half plane 0 <= k_x <= N/2;
+ *   - fields are complex64 [batch][pol][M][M] sampled at x'_i = (i - M/2) N px / M from the beam centre,
+ *     E = (1/N^2) sum_q F(k0+q) exp(2 pi i q.x'/(N px)) exp(-2 pi i (kappa-k0).x'/(N px)) exp(-i pi D |x'|^2/lambda);
+ *   - coefficients are complex64 [batch][pol][modes], polarisation-blocked ("HHHHHVVVVV", as
+ *     digHoloBasisGetCoefs lays them out); modes HG(m, n) with m + n < G, ordered by group g = m + n, then m
+ *     ascending; c_mn = dx' dy' sum_ij u_m(x'_i) u_n(y'_j) E_ji with L2-normalised real u_n.
+ *
+ * Ownership: every device pointer passed in (frames, fields, coefficients, powers) is owned by the caller and
+ * must stay valid until the work queued on the given stream has finished.  The library owns only its plan
+ * tables and scratch, which it allocates on the current device when a plan is first used after a change.
+ * Units follow the guide's "units" module: metres, dioptre, degrees.
+ *
+ * Error behaviour: every function returns one of the DH_* codes below (numeric values as the guide's
+ * DIGHOLO_ERROR_* codes, plus DH_ERROR_TIMEOUT and DH_ERROR_CUDA).  dh_last_error() returns a thread-local
+ * description of the most recent failure.  A failed call leaves the handle's settings unchanged.
+ */
+#ifndef DIGHOLO_GB300_H
+#define DIGHOLO_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Error codes ("Error codes" module of the guide; 12 and 13 are added here). */
+#define DH_SUCCESS 0
+#define DH_ERROR_ERROR 1
+#define DH_ERROR_INVALIDHANDLE 2
+#define DH_ERROR_NULLPOINTER 3
+#define DH_ERROR_INVALIDDIMENSION 5
+#define DH_ERROR_INVALIDPOLARISATION 6
+#define DH_ERROR_INVALIDAXIS 7
+#define DH_ERROR_INVALIDARGUMENT 8
+#define DH_ERROR_MEMORYALLOCATION 9
+#define DH_ERROR_TIMEOUT 12
+#define DH_ERROR_CUDA 13
+
+/* Frame pixel types (digHoloSetBatch takes float32, digHoloSetBatchUint16 takes uint16). */
+#define DH_DTYPE_U16 0
+#define DH_DTYPE_F32 1
+
+/* Arithmetic of the modal overlap: plain FP32 on CUDA cores, or BF16 tensor-core MMA with FP32 accumulation
+ * and a hi/lo split of both operands (three products per term). */
+#define DH_PRECISION_FP32 0
+#define DH_PRECISION_SPLIT_BF16 1
+
+/* Largest sizes the kernels accept. */
+#define DH_MAX_POLS 2
+#define DH_MAX_WINDOW 1024
+#define DH_MAX_FIELD 512
+#define DH_MAX_GROUPS 32
+
+typedef int dh_handle;
+
+/* Create a handle with default settings (digHoloCreate).  *out receives the handle index. */
+int dh_create(dh_handle* out);
+
+/* Release a handle and its device tables and scratch (digHoloDestroy).  Synchronises the device. */
+int dh_destroy(dh_handle h);
+
+/* Description of the last error raised on this thread (never NULL). */
+const char* dh_last_error(void);
+
+/* Frame geometry ("Frame buffer" module): width and height in pixels (positive), polarisation count 1 or 2
+ * (the two components sit on opposite halves of the frame width), pixel pitch in metres (> 0).
+ * Returns DH_ERROR_INVALIDDIMENSION, DH_ERROR_INVALIDPOLARISATION or DH_ERROR_INVALIDARGUMENT. */
+int dh_set_frame(dh_handle h, int width, int height, int pol_count, double pixel_size);
+
+/* Operating wavelength in metres, > 0 (digHoloConfigSetWavelengthCentre). */
+int dh_set_wavelength(dh_handle h, double wavelength);
+
+/* FFT window size (digHoloConfigSetfftWindowSize).  Values are floored to a multiple of 16 as the guide's
+ * DIGHOLO_PIXEL_QUANTA rule says; this build accepts square power-of-two windows 16..1024 only
+ * (DH_ERROR_INVALIDDIMENSION otherwise).  *set_nx / *set_ny (nullable) receive the sizes actually set. */
+int dh_set_fft_window(dh_handle h, int nx, int ny, int* set_nx, int* set_ny);
+
+/* Beam centre of one axis (0 = x, 1 = y) and polarisation, metres (digHoloConfigSetBeamCentre). */
+int dh_set_beam_centre(dh_handle h, int axis, int pol, double centre);
+
+/* Radius w_c of the circular Fourier window, degrees, > 0 (digHoloConfigSetFourierWindowRadius). */
+int dh_set_fourier_window_radius(dh_handle h, double radius_deg);
+
+/* Reduced field size M (IFFT resolution mode 1).  0 selects the guide's rule M = 16 ceil(2 r / 16) (the
+ * FFT [IFFT] table of the Benchmarks section); otherwise a positive multiple of 16 up to min(N, 512) whose
+ * odd part has prime factors <= 19.  Square only: mx must equal my. */
+int dh_set_ifft_size(dh_handle h, int mx, int my);
+
+/* Reference tilt of one axis and polarisation, degrees (digHoloConfigSetTilt): the position of the
+ * off-axis term in Fourier space. */
+int dh_set_tilt(dh_handle h, int axis, int pol, double tilt_deg);
+
+/* Reference defocus of one polarisation, dioptre (digHoloConfigSetDefocus). */
+int dh_set_defocus(dh_handle h, int pol, double dioptre);
+
+/* Hermite-Gaussian basis (digHoloConfigSetBasisWaist, digHoloConfigSetBasisGroupCount): waist in metres (> 0)
+ * of polarisation pol, and the group count G (0..DH_MAX_GROUPS, shared by both polarisations; G = 0 means no
+ * modal decomposition and no coefficients). */
+int dh_set_basis(dh_handle h, int pol, double waist, int group_count);
+
+/* Overlap arithmetic: DH_PRECISION_FP32 or DH_PRECISION_SPLIT_BF16. */
+int dh_set_precision(dh_handle h, int precision);
+
+/* Validate the settings and report the output geometry: field size M (square), number of modes, and the
+ * field sample pitch dx' = N px / M in metres.  Any pointer may be NULL.  Returns DH_ERROR_INVALIDARGUMENT
+ * when a polarisation's window leaves the frame, its tilt centre leaves the half plane 0 < kappa_x <= N/2,
+ * or M exceeds N. */
+int dh_get_output_dims(dh_handle h, int* m, int* modes, double* dx);
+
+/* Field axes of one polarisation in metres from its beam centre (digHoloGetFields' x and y): host arrays of
+ * at least M doubles each. */
+int dh_get_axes(dh_handle h, int pol, double* x, double* y);
+
+/* Reconstruct a batch (digHoloProcessBatch).  d_frames: device array [batch][height][width] of uint16 or
+ * float32 (dtype); d_fields (nullable): device complex64 [batch][pol][M][M]; d_coefs (nullable, ignored when
+ * G = 0): device complex64 [batch][pol][modes].  batch < 1 is treated as 1 (digHoloConfigSetBatchCount).
+ * Asynchronous on stream (a cudaStream_t, NULL = legacy default stream); the plan tables are uploaded on
+ * the first call after a settings change, which synchronises the device once. */
+int dh_process_batch(dh_handle h, const void* d_frames, int dtype, int batch, void* d_fields, void* d_coefs,
+                     void* stream);
+
+/* As dh_process_batch, and also writes the Fourier window that is inverse transformed for every (frame, pol)
+ * (digHoloGetFourierPlaneWindow): d_window complex64 [batch][pol][M][M] with
+ * d_window[q][p] = mask(p, q) (-1)^(p+q) F(k0x - M/2 + p, k0y - M/2 + q) / N^2, F the window spectrum in the
+ * conventions above (the (-1)^(p+q) factor centres the inverse transform on the beam centre).  This entry
+ * always takes the generic multi-kernel path. */
+int dh_process_batch_window(dh_handle h, const void* d_frames, int dtype, int batch, void* d_window,
+                            void* d_fields, void* d_coefs, void* stream);
+
+/* One alignment candidate for dh_score_settings: per polarisation tilt (x, y) in degrees, defocus in
+ * dioptre and basis waist in metres. */
+typedef struct dh_setting {
+    double tilt_deg[DH_MAX_POLS][2];
+    double defocus[DH_MAX_POLS];
+    double waist[DH_MAX_POLS];
+} dh_setting;
+
+/* Total captured power of every frame under every candidate (the quantity the guide's AutoAlign search
+ * maximises): d_power device float32 [batch][count], P[b][s] = sum_pol sum_modes |c_{b,pol,s}|^2, with each
+ * candidate's own tilt, defocus and waist and the handle's other settings.  settings: host array of count
+ * candidates (count >= 1).  Fields are not written. */
+int dh_score_settings(dh_handle h, const void* d_frames, int dtype, int batch, const dh_setting* settings,
+                      int count, float* d_power, void* stream);
+
+/* Per-kernel device timing (the analogue of digHoloBenchmark's per-stage rates).  While enabled, every kernel
+ * the handle launches is bracketed by a CUDA event pair recorded on the launch stream.  dh_set_profiling
+ * clears the totals.  dh_get_profile waits for the recorded events and reports, per kernel, its name
+ * (names: max_kernels slots of 64 chars, nullable), number of launches and total milliseconds since the last
+ * reset; *count receives the number of distinct kernels (may exceed max_kernels). */
+int dh_set_profiling(dh_handle h, int enable);
+int dh_get_profile(dh_handle h, int max_kernels, char* names, long long* launches, double* total_ms, int* count);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DIGHOLO_GB300_H */

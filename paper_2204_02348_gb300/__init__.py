@@ -1,0 +1,276 @@
+"""GB300-native batched off-axis hologram reconstruction (digHolo's processing pipeline).
+
+Thin ctypes binding over the C ABI in ``include/digholo.h``: the functions keep the ABI's names and only
+marshal arguments (torch tensors become device pointers, streams become ``cudaStream_t`` handles).  Every
+step of the reconstruction runs in the library's CUDA kernels; importing this package without the built
+native library raises ImportError (there is no CPU fallback).  Build with ``python
+paper_2204_02348_gb300/_build.py`` or ``__graft_entry__.build()``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_native", "libdigholo_gb300.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"native library missing at {LIB_PATH}; build it with `python paper_2204_02348_gb300/_build.py`")
+
+_lib = ctypes.CDLL(LIB_PATH)
+
+# constants (include/digholo.h)
+DH_SUCCESS = 0
+DH_ERROR_ERROR = 1
+DH_ERROR_INVALIDHANDLE = 2
+DH_ERROR_NULLPOINTER = 3
+DH_ERROR_INVALIDDIMENSION = 5
+DH_ERROR_INVALIDPOLARISATION = 6
+DH_ERROR_INVALIDAXIS = 7
+DH_ERROR_INVALIDARGUMENT = 8
+DH_ERROR_MEMORYALLOCATION = 9
+DH_ERROR_TIMEOUT = 12
+DH_ERROR_CUDA = 13
+DH_DTYPE_U16 = 0
+DH_DTYPE_F32 = 1
+DH_PRECISION_FP32 = 0
+DH_PRECISION_SPLIT_BF16 = 1
+DH_MAX_POLS = 2
+
+
+class DigHoloError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"digholo error {code}: {msg}")
+        self.code = code
+
+
+class dh_setting(ctypes.Structure):
+    _fields_ = [("tilt_deg", (ctypes.c_double * 2) * DH_MAX_POLS),
+                ("defocus", ctypes.c_double * DH_MAX_POLS),
+                ("waist", ctypes.c_double * DH_MAX_POLS)]
+
+
+_i, _d, _p = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
+_PROTOS = {
+    "dh_create": [ctypes.POINTER(_i)],
+    "dh_destroy": [_i],
+    "dh_set_frame": [_i, _i, _i, _i, _d],
+    "dh_set_wavelength": [_i, _d],
+    "dh_set_fft_window": [_i, _i, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)],
+    "dh_set_beam_centre": [_i, _i, _i, _d],
+    "dh_set_fourier_window_radius": [_i, _d],
+    "dh_set_ifft_size": [_i, _i, _i],
+    "dh_set_tilt": [_i, _i, _i, _d],
+    "dh_set_defocus": [_i, _i, _d],
+    "dh_set_basis": [_i, _i, _d, _i],
+    "dh_set_precision": [_i, _i],
+    "dh_get_output_dims": [_i, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_d)],
+    "dh_get_axes": [_i, _i, ctypes.POINTER(_d), ctypes.POINTER(_d)],
+    "dh_process_batch": [_i, _p, _i, _i, _p, _p, _p],
+    "dh_process_batch_window": [_i, _p, _i, _i, _p, _p, _p, _p],
+    "dh_score_settings": [_i, _p, _i, _i, ctypes.POINTER(dh_setting), _i, _p, _p],
+    "dh_set_profiling": [_i, _i],
+    "dh_get_profile": [_i, _i, ctypes.c_char_p, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_d),
+                       ctypes.POINTER(_i)],
+}
+_lib.dh_last_error.restype = ctypes.c_char_p
+_lib.dh_last_error.argtypes = []
+for _name, _args in _PROTOS.items():
+    _fn = getattr(_lib, _name)
+    _fn.argtypes = _args
+    _fn.restype = _i
+
+# every C-ABI name exported by the library, as declared in include/digholo.h
+ABI_NAMES = tuple(_PROTOS) + ("dh_last_error",)
+
+
+def dh_last_error() -> str:
+    return _lib.dh_last_error().decode()
+
+
+def _check(rc: int) -> None:
+    if rc != DH_SUCCESS:
+        raise DigHoloError(rc, dh_last_error())
+
+
+def _ptr(t) -> int:
+    """Device (or host) address of a tensor / integer / None."""
+    if t is None:
+        return None
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(s) -> int:
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+# ------------------------------------------------------------------------------------------ ABI calls
+
+
+def dh_create() -> int:
+    h = _i()
+    _check(_lib.dh_create(ctypes.byref(h)))
+    return h.value
+
+
+def dh_destroy(h: int) -> None:
+    _check(_lib.dh_destroy(h))
+
+
+def dh_set_frame(h: int, width: int, height: int, pol_count: int, pixel_size: float) -> None:
+    _check(_lib.dh_set_frame(h, width, height, pol_count, pixel_size))
+
+
+def dh_set_wavelength(h: int, wavelength: float) -> None:
+    _check(_lib.dh_set_wavelength(h, wavelength))
+
+
+def dh_set_fft_window(h: int, nx: int, ny: int):
+    a, b = _i(), _i()
+    _check(_lib.dh_set_fft_window(h, nx, ny, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def dh_set_beam_centre(h: int, axis: int, pol: int, centre: float) -> None:
+    _check(_lib.dh_set_beam_centre(h, axis, pol, centre))
+
+
+def dh_set_fourier_window_radius(h: int, radius_deg: float) -> None:
+    _check(_lib.dh_set_fourier_window_radius(h, radius_deg))
+
+
+def dh_set_ifft_size(h: int, mx: int, my: int) -> None:
+    _check(_lib.dh_set_ifft_size(h, mx, my))
+
+
+def dh_set_tilt(h: int, axis: int, pol: int, tilt_deg: float) -> None:
+    _check(_lib.dh_set_tilt(h, axis, pol, tilt_deg))
+
+
+def dh_set_defocus(h: int, pol: int, dioptre: float) -> None:
+    _check(_lib.dh_set_defocus(h, pol, dioptre))
+
+
+def dh_set_basis(h: int, pol: int, waist: float, group_count: int) -> None:
+    _check(_lib.dh_set_basis(h, pol, waist, group_count))
+
+
+def dh_set_precision(h: int, precision: int) -> None:
+    _check(_lib.dh_set_precision(h, precision))
+
+
+def dh_get_output_dims(h: int):
+    m, modes, dx = _i(), _i(), _d()
+    _check(_lib.dh_get_output_dims(h, ctypes.byref(m), ctypes.byref(modes), ctypes.byref(dx)))
+    return m.value, modes.value, dx.value
+
+
+def dh_get_axes(h: int, pol: int):
+    m, _, _ = dh_get_output_dims(h)
+    x, y = (_d * m)(), (_d * m)()
+    _check(_lib.dh_get_axes(h, pol, x, y))
+    return list(x), list(y)
+
+
+def dh_process_batch(h: int, frames, dtype: int, batch: int, fields=None, coefs=None, stream=None) -> None:
+    _check(_lib.dh_process_batch(h, _ptr(frames), dtype, batch, _ptr(fields), _ptr(coefs), _stream(stream)))
+
+
+def dh_process_batch_window(h: int, frames, dtype: int, batch: int, window, fields=None, coefs=None,
+                            stream=None) -> None:
+    _check(_lib.dh_process_batch_window(h, _ptr(frames), dtype, batch, _ptr(window), _ptr(fields), _ptr(coefs),
+                                        _stream(stream)))
+
+
+def dh_score_settings(h: int, frames, dtype: int, batch: int, settings, power, stream=None) -> None:
+    arr = (dh_setting * len(settings))(*settings)
+    _check(_lib.dh_score_settings(h, _ptr(frames), dtype, batch, arr, len(settings), _ptr(power), _stream(stream)))
+
+
+def dh_set_profiling(h: int, enable: bool) -> None:
+    _check(_lib.dh_set_profiling(h, 1 if enable else 0))
+
+
+def dh_get_profile(h: int, max_kernels: int = 16):
+    """{kernel name: (launches, total milliseconds)} since the last dh_set_profiling."""
+    names = ctypes.create_string_buffer(64 * max_kernels)
+    launches = (ctypes.c_longlong * max_kernels)()
+    total = (_d * max_kernels)()
+    count = _i()
+    _check(_lib.dh_get_profile(h, max_kernels, names, launches, total, ctypes.byref(count)))
+    out = {}
+    for i in range(min(count.value, max_kernels)):
+        nm = names.raw[64 * i:64 * (i + 1)].split(b"\0", 1)[0].decode()
+        out[nm] = (int(launches[i]), float(total[i]))
+    return out
+
+
+# ------------------------------------------------------------------------------------------ convenience
+
+
+def make_setting(tilt_deg, defocus, waist) -> dh_setting:
+    """dh_setting from per-polarisation sequences: tilt_deg[p] = (x, y), defocus[p], waist[p]."""
+    s = dh_setting()
+    for p in range(len(defocus)):
+        s.tilt_deg[p][0] = float(tilt_deg[p][0])
+        s.tilt_deg[p][1] = float(tilt_deg[p][1])
+        s.defocus[p] = float(defocus[p])
+        s.waist[p] = float(waist[p])
+    return s
+
+
+def configure(h: int, setup) -> None:
+    """Apply an acquisition description (attributes frame_w, frame_h, pol_count, pixel, wavelength, window,
+    beam_centre, tilt_deg, defocus, radius_deg, ifft_size, group_count, waist and optionally precision) to a
+    handle through the setters."""
+    dh_set_frame(h, setup.frame_w, setup.frame_h, setup.pol_count, setup.pixel)
+    dh_set_wavelength(h, setup.wavelength)
+    dh_set_fft_window(h, setup.window, setup.window)
+    dh_set_fourier_window_radius(h, setup.radius_deg)
+    dh_set_ifft_size(h, setup.ifft_size, setup.ifft_size)
+    for p in range(setup.pol_count):
+        for ax in range(2):
+            dh_set_beam_centre(h, ax, p, setup.beam_centre[p][ax])
+            dh_set_tilt(h, ax, p, setup.tilt_deg[p][ax])
+        dh_set_defocus(h, p, setup.defocus[p])
+        dh_set_basis(h, p, setup.waist[p], setup.group_count)
+    dh_set_precision(h, getattr(setup, "precision", DH_PRECISION_FP32))
+
+
+class Reconstructor:
+    """A handle plus output allocation: ``rec(frames)`` returns (fields, coefs) as torch tensors."""
+
+    def __init__(self, setup, precision: int = DH_PRECISION_FP32):
+        self.h = dh_create()
+        configure(self.h, setup)
+        dh_set_precision(self.h, precision)
+        self.m, self.modes, self.dx = dh_get_output_dims(self.h)
+        self.pols = setup.pol_count
+
+    def __call__(self, frames, fields: bool = True, coefs: bool = True, stream=None):
+        import torch
+        b = frames.shape[0]
+        dt = DH_DTYPE_U16 if frames.dtype == torch.uint16 else DH_DTYPE_F32
+        f = torch.empty((b, self.pols, self.m, self.m), dtype=torch.complex64, device=frames.device) if fields else None
+        c = torch.empty((b, self.pols, self.modes), dtype=torch.complex64, device=frames.device) \
+            if (coefs and self.modes) else None
+        dh_process_batch(self.h, frames, dt, b, f, c, stream)
+        return f, c
+
+    def close(self) -> None:
+        if self.h is not None:
+            dh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,517 @@
+// extern "C" entry points declared in include/digholo.h.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/digholo.h"
+#include "kernels.cuh"
+#include "plan.hpp"
+#include "runtime.hpp"
+
+namespace dh {
+
+static thread_local std::string g_err = "no error";
+
+int fail(int code, const std::string& why) {
+    g_err = why;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+    std::string s = std::string(where) + ": " + cudaGetErrorString(e);
+    return fail(DH_ERROR_CUDA, s);
+}
+
+// ------------------------------------------------------------------------------------------- handles
+
+static std::mutex g_handles_mu;
+static std::vector<std::unique_ptr<Handle>> g_handles;
+
+Handle* get_handle(dh_handle h) {
+    std::lock_guard<std::mutex> lk(g_handles_mu);
+    if (h < 0 || h >= (int)g_handles.size() || !g_handles[h]) return nullptr;
+    return g_handles[h].get();
+}
+
+static void release_device(Handle* H) {
+    if (H->d_blob || H->d_scratch) {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        if (H->device >= 0 && H->device != cur) cudaSetDevice(H->device);
+        if (H->d_blob) cudaFree(H->d_blob);
+        if (H->d_scratch) cudaFree(H->d_scratch);
+        if (H->device >= 0 && H->device != cur && cur >= 0) cudaSetDevice(cur);
+    }
+    H->d_blob = nullptr;
+    H->d_scratch = nullptr;
+    H->scratch_bytes = 0;
+    H->device = -1;
+}
+
+// ------------------------------------------------------------------------------------------- plan upload
+
+struct Blob {
+    std::vector<unsigned char> bytes;
+    size_t put(const void* p, size_t n) {
+        size_t off = (bytes.size() + 255) & ~(size_t)255;
+        bytes.resize(off + std::max(n, (size_t)1));
+        if (n) std::memcpy(bytes.data() + off, p, n);
+        return off;
+    }
+};
+
+static std::vector<int> pos_table(int len, const std::vector<int>& rad) {
+    // position of frequency k after DIF passes with these radices (first pass first)
+    std::vector<int> pos(len);
+    for (int k = 0; k < len; ++k) {
+        int p = 0, s = len, rem = k;
+        for (int r : rad) {
+            s /= r;
+            p += (rem % r) * s;
+            rem /= r;
+        }
+        pos[k] = p;
+    }
+    return pos;
+}
+
+int upload_plan(const Settings& s, const Geometry& g, const Tables& t, void** out_blob, dhk::Plan* out) {
+    if ((int)t.radix_n.size() > dhk::kMaxRadices || (int)t.radix_m.size() > dhk::kMaxRadices)
+        return fail(DH_ERROR_INVALIDDIMENSION, "too many radix passes");
+    Blob b;
+    const size_t o_twn = b.put(t.tw_fwd_n.data(), t.tw_fwd_n.size() * 4);
+    const size_t o_twm = b.put(t.tw_inv_m.data(), t.tw_inv_m.size() * 4);
+    std::vector<int> pn = pos_table(g.n, t.radix_n), pm = pos_table(g.m, t.radix_m);
+    const size_t o_pn = b.put(pn.data(), pn.size() * 4);
+    const size_t o_pm = b.put(pm.data(), pm.size() * 4);
+    const size_t o_mm = b.put(t.mode_m.data(), t.mode_m.size() * 4);
+    const size_t o_mn = b.put(t.mode_n.data(), t.mode_n.size() * 4);
+    size_t o_pol[DH_MAX_POLS][8] = {};
+    for (int p = 0; p < g.pols; ++p) {
+        const PolTables& pt = t.pol[p];
+        o_pol[p][0] = b.put(pt.mask_lo.data(), pt.mask_lo.size() * 4);
+        o_pol[p][1] = b.put(pt.mask_hi.data(), pt.mask_hi.size() * 4);
+        o_pol[p][2] = b.put(pt.phase_x.data(), pt.phase_x.size() * 4);
+        o_pol[p][3] = b.put(pt.phase_y.data(), pt.phase_y.size() * 4);
+        o_pol[p][4] = b.put(pt.corr_x.data(), pt.corr_x.size() * 4);
+        o_pol[p][5] = b.put(pt.corr_y.data(), pt.corr_y.size() * 4);
+        o_pol[p][6] = b.put(pt.hg_x.data(), pt.hg_x.size() * 4);
+        o_pol[p][7] = b.put(pt.hg_y.data(), pt.hg_y.size() * 4);
+    }
+    void* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, b.bytes.size());
+    if (e != cudaSuccess) return fail(DH_ERROR_MEMORYALLOCATION, std::string("plan tables: ") + cudaGetErrorString(e));
+    e = cudaMemcpy(d, b.bytes.data(), b.bytes.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(d);
+        return cuda_fail(e, "plan upload");
+    }
+    unsigned char* base = (unsigned char*)d;
+    dhk::Plan& P = *out;
+    std::memset(&P, 0, sizeof P);
+    P.n = g.n;
+    P.m = g.m;
+    P.groups = g.groups;
+    P.modes = g.modes;
+    P.pols = g.pols;
+    P.width = s.width;
+    P.height = s.height;
+    P.precision = s.precision;
+    P.nrad_n = (int)t.radix_n.size();
+    P.nrad_m = (int)t.radix_m.size();
+    for (int i = 0; i < P.nrad_n; ++i) P.rad_n[i] = t.radix_n[i];
+    for (int i = 0; i < P.nrad_m; ++i) P.rad_m[i] = t.radix_m[i];
+    P.tw_fwd_n = (const float2*)(base + o_twn);
+    P.tw_inv_m = (const float2*)(base + o_twm);
+    P.pos_n = (const int*)(base + o_pn);
+    P.pos_m = (const int*)(base + o_pm);
+    P.mode_m = (const int*)(base + o_mm);
+    P.mode_n = (const int*)(base + o_mn);
+    for (int p = 0; p < g.pols; ++p) {
+        dhk::PolDev& pd = P.pol[p];
+        pd.ox = g.pol[p].ax[0].origin;
+        pd.oy = g.pol[p].ax[1].origin;
+        pd.klx = g.pol[p].ax[0].klo;
+        pd.kly = g.pol[p].ax[1].klo;
+        pd.mask_lo = (const int*)(base + o_pol[p][0]);
+        pd.mask_hi = (const int*)(base + o_pol[p][1]);
+        pd.phase_x = (const float2*)(base + o_pol[p][2]);
+        pd.phase_y = (const float2*)(base + o_pol[p][3]);
+        pd.corr_x = (const float2*)(base + o_pol[p][4]);
+        pd.corr_y = (const float2*)(base + o_pol[p][5]);
+        pd.hg_x = (const float*)(base + o_pol[p][6]);
+        pd.hg_y = (const float*)(base + o_pol[p][7]);
+    }
+    *out_blob = d;
+    return DH_SUCCESS;
+}
+
+int init_device_once(int dev) {
+    static std::mutex mu;
+    static bool inited[64] = {false};
+    std::lock_guard<std::mutex> lk(mu);
+    if (dev >= 0 && dev < 64 && inited[dev]) return DH_SUCCESS;
+    cudaError_t e = dhk::split_init();
+    if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
+    e = fused_init();
+    if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
+    if (dev >= 0 && dev < 64) inited[dev] = true;
+    return DH_SUCCESS;
+}
+
+int ensure_plan(Handle* H) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (!H->dirty && H->device == dev && H->d_blob) return DH_SUCCESS;
+    Geometry g;
+    std::string why;
+    int rc = build_geometry(H->s, &g, &why);
+    if (rc) return fail(rc, why);
+    Tables t;
+    build_tables(H->s, g, &t);
+    rc = init_device_once(dev);
+    if (rc) return rc;
+    if (H->device != dev) release_device(H);
+    void* blob = nullptr;
+    dhk::Plan P;
+    rc = upload_plan(H->s, g, t, &blob, &P);
+    if (rc) return rc;
+    if (H->d_blob) cudaFree(H->d_blob);
+    H->d_blob = blob;
+    H->plan = P;
+    H->device = dev;
+    H->geo = g;
+    H->tab = t;
+    H->dirty = false;
+    return DH_SUCCESS;
+}
+
+int ensure_scratch(Handle* H, size_t bytes) {
+    if (H->scratch_bytes >= bytes) return DH_SUCCESS;
+    if (H->d_scratch) cudaFree(H->d_scratch);
+    H->d_scratch = nullptr;
+    H->scratch_bytes = 0;
+    cudaError_t e = cudaMalloc(&H->d_scratch, bytes);
+    if (e != cudaSuccess) {
+        H->d_scratch = nullptr;
+        return fail(DH_ERROR_MEMORYALLOCATION, std::string("scratch: ") + cudaGetErrorString(e));
+    }
+    H->scratch_bytes = bytes;
+    return DH_SUCCESS;
+}
+
+size_t split_window_bytes(const dhk::Plan& P) { return ((size_t)P.m * P.n + (size_t)P.m * P.m) * sizeof(float2); }
+
+// ------------------------------------------------------------------------------------------- profiler
+
+cudaEvent_t Profiler::take() {
+    if (!pool.empty()) {
+        cudaEvent_t e = pool.back();
+        pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void Profiler::start(cudaStream_t s) {
+    open = take();
+    cudaEventRecord(open, s);
+}
+
+void Profiler::stop(cudaStream_t s, const char* kernel) {
+    cudaEvent_t b = take();
+    cudaEventRecord(b, s);
+    pending.push_back(Rec{kernel, open, b});
+    open = nullptr;
+}
+
+int Profiler::resolve() {
+    for (Rec& r : pending) {
+        cudaError_t e = cudaEventSynchronize(r.b);
+        if (e != cudaSuccess) return cuda_fail(e, "profile events");
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, r.a, r.b);
+        size_t i = 0;
+        while (i < names.size() && names[i] != r.name) ++i;
+        if (i == names.size()) {
+            names.push_back(r.name);
+            launches.push_back(0);
+            total_ms.push_back(0.0);
+        }
+        launches[i] += 1;
+        total_ms[i] += ms;
+        pool.push_back(r.a);
+        pool.push_back(r.b);
+    }
+    pending.clear();
+    return DH_SUCCESS;
+}
+
+void Profiler::reset() {
+    resolve();
+    names.clear();
+    launches.clear();
+    total_ms.clear();
+}
+
+Profiler::~Profiler() {
+    for (Rec& r : pending) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (cudaEvent_t e : pool) cudaEventDestroy(e);
+}
+
+int process(Handle* H, const void* frames, int dtype, int batch, void* window, void* fields, void* coefs,
+            cudaStream_t st) {
+    if (!frames) return fail(DH_ERROR_NULLPOINTER, "frames pointer is null");
+    if (dtype != DH_DTYPE_U16 && dtype != DH_DTYPE_F32) return fail(DH_ERROR_INVALIDARGUMENT, "dtype must be DH_DTYPE_U16 or DH_DTYPE_F32");
+    if (batch < 1) batch = 1;
+    int rc = ensure_plan(H);
+    if (rc) return rc;
+    const dhk::Plan& P = H->plan;
+    if (P.modes == 0) coefs = nullptr;
+    if (use_fused(P) && !window) return launch_fused_path(H, frames, dtype, batch, fields, coefs, st);
+    const size_t per_frame = split_window_bytes(P) * P.pols;
+    int chunk = (int)std::max<size_t>(1, kScratchTarget / per_frame);
+    chunk = std::min(chunk, batch);
+    rc = ensure_scratch(H, per_frame * chunk);
+    if (rc) return rc;
+    return run_split(P, H->d_scratch, H->scratch_bytes, frames, dtype, batch, window, fields, coefs, st, H->timer());
+}
+
+int run_split(const dhk::Plan& P, void* scratch, size_t scratch_bytes, const void* frames, int dtype, int batch,
+              void* window, void* fields, void* coefs, cudaStream_t st, dhk::StageTimer* timer) {
+    const size_t per_frame = split_window_bytes(P) * P.pols;
+    const int chunk = (int)std::min<size_t>((size_t)batch, scratch_bytes / per_frame);
+    if (chunk < 1) return fail(DH_ERROR_MEMORYALLOCATION, "scratch smaller than one frame");
+    float2* r1 = (float2*)scratch;
+    float2* g = r1 + (size_t)chunk * P.pols * P.m * P.n;
+    for (int f0 = 0; f0 < batch; f0 += chunk) {
+        dhk::Batch B;
+        B.src = frames;
+        B.dtype = dtype;
+        B.frame0 = f0;
+        B.count = std::min(chunk, batch - f0);
+        B.r1 = r1;
+        B.g = g;
+        B.window = (float2*)window;
+        B.fields = (float2*)fields;
+        B.coefs = (float2*)coefs;
+        cudaError_t e = dhk::launch_split(P, B, st, timer);
+        if (e != cudaSuccess) return cuda_fail(e, "launch");
+    }
+    return DH_SUCCESS;
+}
+
+}  // namespace dh
+
+using namespace dh;
+
+#define GET_HANDLE(h)                                                     \
+    Handle* H = get_handle(h);                                            \
+    if (!H) return fail(DH_ERROR_INVALIDHANDLE, "invalid handle");      \
+    std::lock_guard<std::mutex> lk(H->mu)
+
+extern "C" {
+
+const char* dh_last_error(void) { return g_err.c_str(); }
+
+int dh_create(dh_handle* out) {
+    if (!out) return fail(DH_ERROR_NULLPOINTER, "out is null");
+    std::lock_guard<std::mutex> lk(g_handles_mu);
+    g_handles.emplace_back(new Handle());
+    *out = (dh_handle)(g_handles.size() - 1);
+    return DH_SUCCESS;
+}
+
+int dh_destroy(dh_handle h) {
+    std::unique_ptr<Handle> owned;
+    {
+        std::lock_guard<std::mutex> lk(g_handles_mu);
+        if (h < 0 || h >= (int)g_handles.size() || !g_handles[h]) return fail(DH_ERROR_INVALIDHANDLE, "invalid handle");
+        owned = std::move(g_handles[h]);
+    }
+    std::lock_guard<std::mutex> lk(owned->mu);
+    if (owned->d_blob || owned->d_scratch) cudaDeviceSynchronize();
+    release_device(owned.get());
+    return DH_SUCCESS;
+}
+
+int dh_set_frame(dh_handle h, int width, int height, int pol_count, double pixel_size) {
+    GET_HANDLE(h);
+    if (width <= 0 || height <= 0) return fail(DH_ERROR_INVALIDDIMENSION, "frame width and height must be positive");
+    if (pol_count < 1 || pol_count > DH_MAX_POLS) return fail(DH_ERROR_INVALIDPOLARISATION, "polarisation count must be 1 or 2");
+    if (!(pixel_size > 0.0) || !std::isfinite(pixel_size)) return fail(DH_ERROR_INVALIDARGUMENT, "pixel size must be positive");
+    H->s.width = width;
+    H->s.height = height;
+    H->s.pols = pol_count;
+    H->s.pixel = pixel_size;
+    H->dirty = true;
+    return DH_SUCCESS;
+}
+
+int dh_set_wavelength(dh_handle h, double wavelength) {
+    GET_HANDLE(h);
+    if (!(wavelength > 0.0) || !std::isfinite(wavelength)) return fail(DH_ERROR_INVALIDARGUMENT, "wavelength must be positive");
+    H->s.wavelength = wavelength;
+    H->dirty = true;
+    return DH_SUCCESS;
+}
+
+int dh_set_fft_window(dh_handle h, int nx, int ny, int* set_nx, int* set_ny) {
+    GET_HANDLE(h);
+    const int fx = (nx / 16) * 16, fy = (ny / 16) * 16;
+    if (fx <= 0 || fy <= 0) return fail(DH_ERROR_INVALIDDIMENSION, "window size must be at least 16");
+    if (fx != fy) return fail(DH_ERROR_INVALIDDIMENSION, "only square FFT windows are supported");
+    if (fx > DH_MAX_WINDOW || (fx & (fx - 1))) return fail(DH_ERROR_INVALIDDIMENSION, "window size must be a power of two up to 1024");
+    H->s.n = fx;
+    H->dirty = true;
+    if (set_nx) *set_nx = fx;
+    if (set_ny) *set_ny = fy;
+    return DH_SUCCESS;
+}
+
+int dh_set_beam_centre(dh_handle h, int axis, int pol, double centre) {
+    GET_HANDLE(h);
+    if (axis < 0 || axis > 1) return fail(DH_ERROR_INVALIDAXIS, "axis must be 0 (x) or 1 (y)");
+    if (pol < 0 || pol >= DH_MAX_POLS) return fail(DH_ERROR_INVALIDPOLARISATION, "polarisation must be 0 or 1");
+    if (!std::isfinite(centre)) return fail(DH_ERROR_INVALIDARGUMENT, "beam centre must be finite");
+    H->s.centre[pol][axis] = centre;
+    H->dirty = true;
+    return DH_SUCCESS;
+}
+
+int dh_set_fourier_window_radius(dh_handle h, double radius_deg) {
+    GET_HANDLE(h);
+    if (!(radius_deg > 0.0) || !std::isfinite(radius_deg)) return fail(DH_ERROR_INVALIDARGUMENT, "window radius must be positive");
+    H->s.radius_deg = radius_deg;
+    H->dirty = true;
+    return DH_SUCCESS;
+}
+
+int dh_set_ifft_size(dh_handle h, int mx, int my) {
+    GET_HANDLE(h);
+    if (mx != my) return fail(DH_ERROR_INVALIDDIMENSION, "only square fields are supported");
+    if (mx < 0 || (mx > 0 && (mx % 16 || mx > DH_MAX_FIELD || radix_plan(mx).empty())))
+        return fail(DH_ERROR_INVALIDDIMENSION, "field size must be 0 or a multiple of 16 up to 512 with a 19-smooth odd part");
+    H->s.m_req = mx;
+    H->dirty = true;
+    return DH_SUCCESS;
+}
+
+int dh_set_tilt(dh_handle h, int axis, int pol, double tilt_deg) {
+    GET_HANDLE(h);
+    if (axis < 0 || axis > 1) return fail(DH_ERROR_INVALIDAXIS, "axis must be 0 (x) or 1 (y)");
+    if (pol < 0 || pol >= DH_MAX_POLS) return fail(DH_ERROR_INVALIDPOLARISATION, "polarisation must be 0 or 1");
+    if (!std::isfinite(tilt_deg)) return fail(DH_ERROR_INVALIDARGUMENT, "tilt must be finite");
+    H->s.tilt_deg[pol][axis] = tilt_deg;
+    H->dirty = true;
+    return DH_SUCCESS;
+}
+
+int dh_set_defocus(dh_handle h, int pol, double dioptre) {
+    GET_HANDLE(h);
+    if (pol < 0 || pol >= DH_MAX_POLS) return fail(DH_ERROR_INVALIDPOLARISATION, "polarisation must be 0 or 1");
+    if (!std::isfinite(dioptre)) return fail(DH_ERROR_INVALIDARGUMENT, "defocus must be finite");
+    H->s.defocus[pol] = dioptre;
+    H->dirty = true;
+    return DH_SUCCESS;
+}
+
+int dh_set_basis(dh_handle h, int pol, double waist, int group_count) {
+    GET_HANDLE(h);
+    if (pol < 0 || pol >= DH_MAX_POLS) return fail(DH_ERROR_INVALIDPOLARISATION, "polarisation must be 0 or 1");
+    if (group_count < 0 || group_count > DH_MAX_GROUPS) return fail(DH_ERROR_INVALIDDIMENSION, "group count must be in 0..32");
+    if (!(waist > 0.0) || !std::isfinite(waist)) return fail(DH_ERROR_INVALIDDIMENSION, "waist must be positive");
+    H->s.waist[pol] = waist;
+    H->s.groups = group_count;
+    H->dirty = true;
+    return DH_SUCCESS;
+}
+
+int dh_set_precision(dh_handle h, int precision) {
+    GET_HANDLE(h);
+    if (precision != DH_PRECISION_FP32 && precision != DH_PRECISION_SPLIT_BF16)
+        return fail(DH_ERROR_INVALIDARGUMENT, "precision must be DH_PRECISION_FP32 or DH_PRECISION_SPLIT_BF16");
+    H->s.precision = precision;
+    H->dirty = true;
+    return DH_SUCCESS;
+}
+
+int dh_get_output_dims(dh_handle h, int* m, int* modes, double* dx) {
+    GET_HANDLE(h);
+    Geometry g;
+    std::string why;
+    int rc = build_geometry(H->s, &g, &why);
+    if (rc) return fail(rc, why);
+    if (m) *m = g.m;
+    if (modes) *modes = g.modes;
+    if (dx) *dx = g.dx;
+    return DH_SUCCESS;
+}
+
+int dh_get_axes(dh_handle h, int pol, double* x, double* y) {
+    GET_HANDLE(h);
+    if (!x || !y) return fail(DH_ERROR_NULLPOINTER, "axis arrays are null");
+    if (pol < 0 || pol >= H->s.pols) return fail(DH_ERROR_INVALIDPOLARISATION, "no such polarisation");
+    Geometry g;
+    std::string why;
+    int rc = build_geometry(H->s, &g, &why);
+    if (rc) return fail(rc, why);
+    for (int i = 0; i < g.m; ++i) {
+        x[i] = (double)(i - g.m / 2) * g.dx;
+        y[i] = (double)(i - g.m / 2) * g.dx;
+    }
+    return DH_SUCCESS;
+}
+
+int dh_process_batch(dh_handle h, const void* d_frames, int dtype, int batch, void* d_fields, void* d_coefs,
+                     void* stream) {
+    GET_HANDLE(h);
+    return process(H, d_frames, dtype, batch, nullptr, d_fields, d_coefs, (cudaStream_t)stream);
+}
+
+int dh_process_batch_window(dh_handle h, const void* d_frames, int dtype, int batch, void* d_window,
+                            void* d_fields, void* d_coefs, void* stream) {
+    GET_HANDLE(h);
+    if (!d_window) return fail(DH_ERROR_NULLPOINTER, "window pointer is null");
+    return process(H, d_frames, dtype, batch, d_window, d_fields, d_coefs, (cudaStream_t)stream);
+}
+
+int dh_set_profiling(dh_handle h, int enable) {
+    GET_HANDLE(h);
+    H->prof.reset();
+    H->prof.on = enable != 0;
+    return DH_SUCCESS;
+}
+
+int dh_get_profile(dh_handle h, int max_kernels, char* names, long long* launches, double* total_ms, int* count) {
+    GET_HANDLE(h);
+    if (!count) return fail(DH_ERROR_NULLPOINTER, "count is null");
+    int rc = H->prof.resolve();
+    if (rc) return rc;
+    const int n = (int)H->prof.names.size();
+    *count = n;
+    for (int i = 0; i < n && i < max_kernels; ++i) {
+        if (names) {
+            std::strncpy(names + 64 * i, H->prof.names[i].c_str(), 63);
+            names[64 * i + 63] = 0;
+        }
+        if (launches) launches[i] = H->prof.launches[i];
+        if (total_ms) total_ms[i] = H->prof.total_ms[i];
+    }
+    return DH_SUCCESS;
+}
+
+}  // extern "C"

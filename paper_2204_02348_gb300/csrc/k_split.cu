@@ -1,0 +1,232 @@
+// Generic reconstruction path: three kernels joined by L2-sized scratch, for any window N (16..1024,
+// power of two) and field size M (multiple of 16 with a 19-smooth odd part).
+//
+//   k_ypass : pipeline step 1, first half.  Pairs of real window columns (x, x + N/2) are packed into one
+//             complex column, transformed along y (N-point DIF), and the M box rows (k_y in
+//             [k0y - M/2, k0y + M/2) mod N) of both real columns are separated from the packed spectrum.
+//             Writes r1[q][x] (M x N complex per window).
+//   k_xpass : pipeline step 1, second half, and step 2 along x.  Each box row is transformed along x
+//             (N-point DIF); the M box columns are selected, masked by the circular window and multiplied by
+//             the beam-centre phase and 1/N, then inverse transformed along x (M-point DIT).  Writes g[q][i].
+//   k_yinv  : step 2 along y, tilt/defocus removal and step 3.  Column chunks of g are inverse transformed
+//             along y, multiplied by the separable correction, written as the field, and contracted with the
+//             Hermite-Gaussian tables (first over y, then over x) into per-mode accumulators held in
+//             registers, in a fixed order (deterministic, no atomics).
+#include <algorithm>
+
+#include "fft.cuh"
+#include "kernels.cuh"
+
+namespace dhk {
+
+constexpr int kThreads = 256;
+constexpr int kChunkI = 32;      // columns per k_yinv chunk
+constexpr int kMaxSmem = 227 * 1024;
+
+template <typename T>
+__device__ __forceinline__ float to_f(T v) { return (float)v; }
+
+template <typename T>
+__global__ void __launch_bounds__(kThreads, 2) k_ypass(const __grid_constant__ Plan P, const __grid_constant__ Batch B,
+                                                    int logc) {
+    extern __shared__ float2 smem[];
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int C = 1 << logc;
+    const int N = P.n, M = P.m, half = N / 2;
+    const int pol = blockIdx.y;
+    const PolDev& pd = P.pol[pol];
+    const int x0 = blockIdx.x * C;
+    for (int fb = blockIdx.z; fb < B.count; fb += gridDim.z) {
+        const int f = B.frame0 + fb;
+        const T* fr = (const T*)B.src + (size_t)f * P.width * P.height;
+        for (int idx = tid; idx < N * C; idx += nthr) {
+            const int y = idx >> logc, c = idx & (C - 1);
+            const T* row = fr + (size_t)(pd.oy + y) * P.width + pd.ox + x0 + c;
+            smem[idx] = make_float2(to_f(row[0]), to_f(row[half]));
+        }
+        __syncthreads();
+        fft_run<false>(smem, N, P.rad_n, P.nrad_n, logc, C, P.tw_fwd_n, tid, nthr);
+        float2* r1 = B.r1 + (size_t)(fb * P.pols + pol) * M * N;
+        for (int idx = tid; idx < M * C; idx += nthr) {
+            const int q = idx >> logc, c = idx & (C - 1);
+            int k = (pd.kly + q) % N;
+            if (k < 0) k += N;
+            const int km = (N - k) & (N - 1);
+            const float2 za = smem[P.pos_n[k] * C + c];
+            const float2 zb = smem[P.pos_n[km] * C + c];
+            // column x: (Z(k) + conj Z(-k)) / 2 ; column x + N/2: (Z(k) - conj Z(-k)) / (2i)
+            r1[(size_t)q * N + x0 + c] = make_float2(0.5f * (za.x + zb.x), 0.5f * (za.y - zb.y));
+            r1[(size_t)q * N + x0 + c + half] = make_float2(0.5f * (za.y + zb.y), 0.5f * (zb.x - za.x));
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 2) k_xpass(const __grid_constant__ Plan P, const __grid_constant__ Batch B,
+                                                    int logr, int logn) {
+    extern __shared__ float2 smem[];
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int R = 1 << logr, es = R + 1;
+    const int N = P.n, M = P.m;
+    float2* bufN = smem;
+    float2* bufM = smem + (size_t)N * es;
+    const int pol = blockIdx.y;
+    const PolDev& pd = P.pol[pol];
+    const int q0 = blockIdx.x * R;
+    for (int fb = blockIdx.z; fb < B.count; fb += gridDim.z) {
+        const int f = B.frame0 + fb;
+        const float2* r1 = B.r1 + (size_t)(fb * P.pols + pol) * M * N;
+        for (int idx = tid; idx < R * N; idx += nthr) {
+            const int row = idx >> logn, x = idx & (N - 1);
+            const int q = q0 + row;
+            bufN[x * es + row] = (q < M) ? r1[(size_t)q * N + x] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        fft_run<false>(bufN, N, P.rad_n, P.nrad_n, logr, es, P.tw_fwd_n, tid, nthr);
+        for (int idx = tid; idx < R * M; idx += nthr) {
+            const int row = idx & (R - 1), pp = idx >> logr;
+            const int q = q0 + row;
+            float2 v = make_float2(0.f, 0.f);
+            if (q < M) {
+                if (pp >= pd.mask_lo[q] && pp <= pd.mask_hi[q]) {
+                    int kx = (pd.klx + pp) % N;
+                    if (kx < 0) kx += N;
+                    v = cmul(cmul(bufN[P.pos_n[kx] * es + row], pd.phase_x[pp]), pd.phase_y[q]);
+                }
+                if (B.window) B.window[((size_t)(f * P.pols + pol) * M + q) * M + pp] = v;
+            }
+            bufM[P.pos_m[pp] * es + row] = v;
+        }
+        __syncthreads();
+        fft_run<true>(bufM, M, P.rad_m, P.nrad_m, logr, es, P.tw_inv_m, tid, nthr);
+        float2* g = B.g + (size_t)(fb * P.pols + pol) * M * M;
+        for (int idx = tid; idx < R * M; idx += nthr) {
+            const int row = idx / M, i = idx - row * M;
+            const int q = q0 + row;
+            if (q < M) g[(size_t)q * M + i] = bufM[i * es + row];
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 2) k_yinv(const __grid_constant__ Plan P, const __grid_constant__ Batch B) {
+    extern __shared__ float2 smem[];
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int M = P.m, G = P.groups, modes = P.modes;
+    float2* buf = smem;                          // [M][kChunkI]
+    float2* tp = smem + (size_t)M * kChunkI;     // [G][kChunkI]
+    const int pol = blockIdx.x;
+    const PolDev& pd = P.pol[pol];
+    for (int fb = blockIdx.y; fb < B.count; fb += gridDim.y) {
+        const int f = B.frame0 + fb;
+        const float2* g = B.g + (size_t)(fb * P.pols + pol) * M * M;
+        float2 acc[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
+        for (int i0 = 0; i0 < M; i0 += kChunkI) {
+            for (int idx = tid; idx < M * kChunkI; idx += nthr) {
+                const int q = idx >> 5, i = idx & (kChunkI - 1);
+                buf[P.pos_m[q] * kChunkI + i] = (i0 + i < M) ? g[(size_t)q * M + i0 + i] : make_float2(0.f, 0.f);
+            }
+            __syncthreads();
+            fft_run<true>(buf, M, P.rad_m, P.nrad_m, 5, kChunkI, P.tw_inv_m, tid, nthr);
+            for (int idx = tid; idx < M * kChunkI; idx += nthr) {
+                const int j = idx >> 5, i = idx & (kChunkI - 1);
+                if (i0 + i < M) {
+                    const float2 e = cmul(cmul(buf[idx], pd.corr_y[j]), pd.corr_x[i0 + i]);
+                    buf[idx] = e;
+                    if (B.fields) B.fields[((size_t)(f * P.pols + pol) * M + j) * M + i0 + i] = e;
+                } else {
+                    buf[idx] = make_float2(0.f, 0.f);
+                }
+            }
+            __syncthreads();
+            if (G > 0) {
+                // T[n][i] = sum_j u_n(y'_j) E[j][i]
+                for (int idx = tid; idx < G * kChunkI; idx += nthr) {
+                    const int n = idx >> 5, i = idx & (kChunkI - 1);
+                    const float* u = pd.hg_y + (size_t)n * M;
+                    float2 s = make_float2(0.f, 0.f);
+                    for (int j = 0; j < M; ++j) {
+                        const float w = __ldg(&u[j]);
+                        const float2 e = buf[j * kChunkI + i];
+                        s.x = fmaf(w, e.x, s.x);
+                        s.y = fmaf(w, e.y, s.y);
+                    }
+                    tp[n * kChunkI + i] = s;
+                }
+                __syncthreads();
+                // c_mn += sum_i u_m(x'_i) T[n][i]
+#pragma unroll
+                for (int kk = 0; kk < 3; ++kk) {
+                    const int k = tid + kk * nthr;
+                    if (k < modes) {
+                        const float* u = pd.hg_x + (size_t)P.mode_m[k] * M + i0;
+                        const float2* t = tp + P.mode_n[k] * kChunkI;
+                        const int lim = min(kChunkI, M - i0);
+                        for (int i = 0; i < lim; ++i) {
+                            const float w = __ldg(&u[i]);
+                            acc[kk].x = fmaf(w, t[i].x, acc[kk].x);
+                            acc[kk].y = fmaf(w, t[i].y, acc[kk].y);
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        if (B.coefs) {
+#pragma unroll
+            for (int kk = 0; kk < 3; ++kk) {
+                const int k = tid + kk * nthr;
+                if (k < modes) B.coefs[(size_t)(f * P.pols + pol) * modes + k] = acc[kk];
+            }
+        }
+    }
+}
+
+static int ilog2(int v) {
+    int l = 0;
+    while ((1 << (l + 1)) <= v) ++l;
+    return l;
+}
+
+cudaError_t split_init() {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_ypass<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem))) return e;
+    if ((e = cudaFuncSetAttribute(k_ypass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem))) return e;
+    if ((e = cudaFuncSetAttribute(k_xpass, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem))) return e;
+    if ((e = cudaFuncSetAttribute(k_yinv, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem))) return e;
+    return cudaSuccess;
+}
+
+cudaError_t launch_split(const Plan& P, const Batch& B, cudaStream_t st, StageTimer* tm) {
+    const int N = P.n, M = P.m;
+    const int zf = std::min(B.count, 65535);
+    // k_ypass: C packed column pairs per block, N x C complex in shared memory
+    int logc = (N >= 1024) ? 4 : 5;
+    logc = std::min(logc, ilog2(N / 2));
+    const int C = 1 << logc;
+    dim3 g1((N / 2) / C, P.pols, zf);
+    const size_t sm1 = (size_t)N * C * sizeof(float2);
+    if (tm) tm->start(st);
+    if (B.dtype == DH_DTYPE_U16)
+        k_ypass<uint16_t><<<g1, kThreads, sm1, st>>>(P, B, logc);
+    else
+        k_ypass<float><<<g1, kThreads, sm1, st>>>(P, B, logc);
+    if (tm) tm->stop(st, "k_ypass");
+    // k_xpass: R box rows per block
+    const int logr = (N >= 512) ? 4 : 5;
+    const int R = 1 << logr;
+    dim3 g2((M + R - 1) / R, P.pols, zf);
+    const size_t sm2 = (size_t)(N + M) * (R + 1) * sizeof(float2);
+    if (tm) tm->start(st);
+    k_xpass<<<g2, kThreads, sm2, st>>>(P, B, logr, ilog2(N));
+    if (tm) tm->stop(st, "k_xpass");
+    // k_yinv: one block per window
+    dim3 g3(P.pols, zf);
+    const size_t sm3 = (size_t)(M + std::max(P.groups, 1)) * kChunkI * sizeof(float2);
+    if (tm) tm->start(st);
+    k_yinv<<<g3, kThreads, sm3, st>>>(P, B);
+    if (tm) tm->stop(st, "k_yinv");
+    return cudaGetLastError();
+}
+
+}  // namespace dhk

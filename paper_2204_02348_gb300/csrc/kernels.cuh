@@ -1,0 +1,67 @@
+// Parameter blocks shared by the host launch code and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/digholo.h"
+
+namespace dhk {
+
+constexpr int kMaxRadices = 6;
+
+// Device tables of one polarisation (all pointers into the plan's device blob).
+struct PolDev {
+    int ox, oy;              // window origin in the frame
+    int klx, kly;            // first box bin along x and y (unwrapped)
+    const int* mask_lo;      // [M] first kept column of box row q
+    const int* mask_hi;      // [M] last kept column of box row q
+    const float2* phase_x;   // [M] (-1)^klo exp(-2 pi i (klo+p) eps / N) / N
+    const float2* phase_y;   // [M]
+    const float2* corr_x;    // [M] (-1)^i residual-tilt and defocus phase
+    const float2* corr_y;    // [M]
+    const float* hg_x;       // [G][M] u_g(x'_i) sqrt(dx')
+    const float* hg_y;       // [G][M]
+};
+
+struct Plan {
+    int n, m, groups, modes, pols;
+    int width, height;
+    int precision;           // DH_PRECISION_*
+    int nrad_n, nrad_m;
+    int rad_n[kMaxRadices];
+    int rad_m[kMaxRadices];
+    const float2* tw_fwd_n;  // [N]
+    const float2* tw_inv_m;  // [M]
+    const int* pos_n;        // [N] position of frequency k after the forward DIF passes
+    const int* pos_m;        // [M] position of index k for the inverse DIT input
+    const int* mode_m;       // [modes]
+    const int* mode_n;       // [modes]
+    PolDev pol[DH_MAX_POLS];
+};
+
+// One launch of the generic path over frames [frame0, frame0 + frames).
+struct Batch {
+    const void* src;         // frames [B][H][W] uint16 or float32
+    int dtype;
+    int frame0, count;       // frames [frame0, frame0 + count) of this launch
+    float2* r1;              // scratch [frames][pol][M][N]: y-transformed box rows
+    float2* g;               // scratch [frames][pol][M][M]: x-inverse-transformed rows
+    float2* window;          // nullable [B][pol][M][M] masked window (natural order)
+    float2* fields;          // nullable [B][pol][M][M]
+    float2* coefs;           // nullable [B][pol][modes]
+};
+
+// Optional per-kernel device timing: start() before and stop() after every launch, on the launch stream.
+struct StageTimer {
+    virtual void start(cudaStream_t s) = 0;
+    virtual void stop(cudaStream_t s, const char* kernel) = 0;
+    virtual ~StageTimer() {}
+};
+
+// Launchers of the generic three-kernel path (k_split.cu).  Return cudaGetLastError().
+cudaError_t launch_split(const Plan& plan, const Batch& batch, cudaStream_t stream, StageTimer* timer);
+// Shared-memory opt-in, once per process and device.
+cudaError_t split_init();
+
+}  // namespace dhk

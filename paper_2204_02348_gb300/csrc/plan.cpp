@@ -1,0 +1,186 @@
+// Host-side geometry and tables.  Compiled with -ffp-contract=off so every FP64 expression rounds exactly
+// as written; the window-mask decision (a floating-point comparison that decides which bins are kept) is
+// taken here, in FP64, once per plan.
+#include "plan.hpp"
+
+#include <cmath>
+#include <cstdio>
+
+namespace dh {
+
+static const double kPi = 3.14159265358979323846;
+static const double kDegToRad = kPi / 180.0;
+
+int round_half_away(double v) { return (int)std::copysign(std::floor(std::fabs(v) + 0.5), v); }
+
+int ifft_size_rule(double r_bins) { return 16 * (int)std::ceil(2.0 * r_bins / 16.0); }
+
+std::vector<int> radix_plan(int len) {
+    std::vector<int> out;
+    if (len < 2) return out;
+    int odd = len, two = 0;
+    while (odd % 2 == 0) { odd /= 2; ++two; }
+    // power-of-two part 2^two: few passes of radix 16 / 8, at most one smaller pass
+    static const int pow2_plan[11][3] = {
+        {0, 0, 0}, {2, 0, 0}, {4, 0, 0}, {8, 0, 0}, {16, 0, 0}, {8, 4, 0},
+        {8, 8, 0}, {16, 8, 0}, {16, 16, 0}, {8, 8, 8}, {16, 8, 8}};
+    if (two > 10) return out;
+    for (int i = 0; i < 3 && pow2_plan[two][i]; ++i) out.push_back(pow2_plan[two][i]);
+    static const int primes[] = {3, 5, 7, 11, 13, 17, 19};
+    for (int p : primes)
+        while (odd % p == 0) { out.push_back(p); odd /= p; }
+    if (odd != 1) out.clear();
+    return out;
+}
+
+static int axis_geometry(const Settings& s, int p, int ax, const double tilt_deg, AxisGeom* a) {
+    const double c = s.centre[p][ax];
+    const int rc = round_half_away(c / s.pixel);
+    a->origin = rc - s.n / 2;
+    a->eps = (double)rc - c / s.pixel;
+    a->kappa = tilt_deg * kDegToRad * (double)s.n * s.pixel / s.wavelength;
+    a->k0 = round_half_away(a->kappa);
+    return DH_SUCCESS;
+}
+
+static int fill(const Settings& s, const double tilt[DH_MAX_POLS][2], const double* defocus,
+                const double* waist, Geometry* g, std::string* why) {
+    if (s.width <= 0 || s.height <= 0) { *why = "frame size not set"; return DH_ERROR_INVALIDDIMENSION; }
+    if (s.pols < 1 || s.pols > DH_MAX_POLS) { *why = "polarisation count must be 1 or 2"; return DH_ERROR_INVALIDPOLARISATION; }
+    if (!(s.pixel > 0.0) || !(s.wavelength > 0.0)) { *why = "pixel size and wavelength must be positive"; return DH_ERROR_INVALIDARGUMENT; }
+    if (!(s.radius_deg > 0.0)) { *why = "Fourier window radius must be positive"; return DH_ERROR_INVALIDARGUMENT; }
+    g->n = s.n;
+    g->pols = s.pols;
+    g->groups = s.groups;
+    g->modes = s.groups * (s.groups + 1) / 2;
+    const double r = s.radius_deg * kDegToRad * (double)s.n * s.pixel / s.wavelength;
+    g->m = s.m_req > 0 ? s.m_req : ifft_size_rule(r);
+    if (g->m < 16 || g->m % 16 || g->m > s.n || g->m > DH_MAX_FIELD || radix_plan(g->m).empty()) {
+        char b[160];
+        std::snprintf(b, sizeof b, "field size M=%d invalid for window N=%d (multiple of 16, <= N, <= %d, odd part 19-smooth)",
+                      g->m, s.n, DH_MAX_FIELD);
+        *why = b;
+        return DH_ERROR_INVALIDARGUMENT;
+    }
+    g->dx = (double)s.n * s.pixel / (double)g->m;
+    for (int p = 0; p < s.pols; ++p) {
+        PolGeom& pg = g->pol[p];
+        for (int ax = 0; ax < 2; ++ax) axis_geometry(s, p, ax, tilt[p][ax], &pg.ax[ax]);
+        pg.r = r;
+        pg.defocus = defocus[p];
+        pg.waist = waist[p];
+        for (int ax = 0; ax < 2; ++ax) pg.ax[ax].klo = pg.ax[ax].k0 - g->m / 2;
+        const int lim[2] = {s.width, s.height};
+        for (int ax = 0; ax < 2; ++ax) {
+            if (pg.ax[ax].origin < 0 || pg.ax[ax].origin + s.n > lim[ax]) {
+                char b[160];
+                std::snprintf(b, sizeof b, "window of polarisation %d leaves the frame along axis %d (origin %d, N %d, frame %d)",
+                              p, ax, pg.ax[ax].origin, s.n, lim[ax]);
+                *why = b;
+                return DH_ERROR_INVALIDARGUMENT;
+            }
+        }
+        if (!(pg.ax[0].kappa > 0.0 && pg.ax[0].kappa <= s.n / 2.0)) {
+            *why = "tilt x must place the window centre inside the half plane 0 < kappa_x <= N/2";
+            return DH_ERROR_INVALIDARGUMENT;
+        }
+        if (s.groups > 0 && !(pg.waist > 0.0)) { *why = "basis waist must be positive"; return DH_ERROR_INVALIDARGUMENT; }
+    }
+    return DH_SUCCESS;
+}
+
+int build_geometry(const Settings& s, Geometry* g, std::string* why) {
+    return fill(s, s.tilt_deg, s.defocus, s.waist, g, why);
+}
+
+int build_geometry_candidate(const Settings& s, const dh_setting& c, Geometry* g, std::string* why) {
+    return fill(s, c.tilt_deg, c.defocus, c.waist, g, why);
+}
+
+void hg_table(int groups, const double* x, int len, double waist, double* out) {
+    const double s2 = std::sqrt(2.0);
+    const double norm = std::sqrt(s2 / waist);
+    for (int i = 0; i < len; ++i) {
+        const double xi = s2 * x[i] / waist;
+        double prev = 0.0, cur = std::pow(kPi, -0.25) * std::exp(-0.5 * xi * xi);
+        for (int k = 0; k < groups; ++k) {
+            out[(size_t)k * len + i] = norm * cur;
+            // psi_{k+1} = sqrt(2/(k+1)) xi psi_k - sqrt(k/(k+1)) psi_{k-1}
+            const double next = std::sqrt(2.0 / (k + 1)) * xi * cur - std::sqrt((double)k / (k + 1)) * prev;
+            prev = cur;
+            cur = next;
+        }
+    }
+}
+
+static void push_c(std::vector<float>& v, double re, double im) {
+    v.push_back((float)re);
+    v.push_back((float)im);
+}
+
+void build_tables(const Settings& s, const Geometry& g, Tables* t) {
+    const int n = g.n, m = g.m;
+    t->tw_fwd_n.clear();
+    t->tw_inv_m.clear();
+    for (int k = 0; k < n; ++k) push_c(t->tw_fwd_n, std::cos(-2.0 * kPi * k / n), std::sin(-2.0 * kPi * k / n));
+    for (int k = 0; k < m; ++k) push_c(t->tw_inv_m, std::cos(2.0 * kPi * k / m), std::sin(2.0 * kPi * k / m));
+    t->radix_n = radix_plan(n);
+    t->radix_m = radix_plan(m);
+    t->mode_m.clear();
+    t->mode_n.clear();
+    for (int gg = 0; gg < g.groups; ++gg)
+        for (int mm = 0; mm <= gg; ++mm) { t->mode_m.push_back(mm); t->mode_n.push_back(gg - mm); }
+    std::vector<double> xp(m);
+    for (int i = 0; i < m; ++i) xp[i] = (double)(i - m / 2) * g.dx;
+    for (int p = 0; p < g.pols; ++p) {
+        const PolGeom& pg = g.pol[p];
+        PolTables& pt = t->pol[p];
+        std::vector<float>* ph[2] = {&pt.phase_x, &pt.phase_y};
+        std::vector<float>* co[2] = {&pt.corr_x, &pt.corr_y};
+        for (int ax = 0; ax < 2; ++ax) {
+            const AxisGeom& a = pg.ax[ax];
+            ph[ax]->clear();
+            co[ax]->clear();
+            const double sgn = (a.klo % 2 == 0) ? 1.0 : -1.0;
+            for (int q = 0; q < m; ++q) {
+                const double ang = -2.0 * kPi * (double)(a.klo + q) * a.eps / n;
+                push_c(*ph[ax], sgn * std::cos(ang) / n, sgn * std::sin(ang) / n);
+            }
+            for (int i = 0; i < m; ++i) {
+                const double ang = -2.0 * kPi * (a.kappa - a.k0) * (double)(i - m / 2) / m
+                                   - kPi * pg.defocus * xp[i] * xp[i] / s.wavelength;
+                const double sg = (i % 2 == 0) ? 1.0 : -1.0;
+                push_c(*co[ax], sg * std::cos(ang), sg * std::sin(ang));
+            }
+        }
+        // mask rows: the same FP64 expression as the definition, ((ky-kappa_y)/r)^2 + ((kx-kappa_x)/r)^2 <= 1
+        pt.mask_lo.assign(m, 1);
+        pt.mask_hi.assign(m, 0);
+        for (int q = 0; q < m; ++q) {
+            const double ky = (double)(pg.ax[1].klo + q);
+            const double ddy = (ky - pg.ax[1].kappa) / pg.r;
+            int lo = -1, hi = -2;
+            for (int pp = 0; pp < m; ++pp) {
+                const int kxi = pg.ax[0].klo + pp;
+                const double ddx = ((double)kxi - pg.ax[0].kappa) / pg.r;
+                const bool keep = (ddy * ddy + ddx * ddx <= 1.0) && kxi >= 0 && kxi <= n / 2;
+                if (keep) {
+                    if (lo < 0) lo = pp;
+                    hi = pp;
+                }
+            }
+            if (lo >= 0) { pt.mask_lo[q] = lo; pt.mask_hi[q] = hi; }
+        }
+        const double sq = std::sqrt(g.dx);
+        std::vector<double> u((size_t)std::max(g.groups, 1) * m);
+        pt.hg_x.clear();
+        pt.hg_y.clear();
+        if (g.groups > 0) {
+            hg_table(g.groups, xp.data(), m, pg.waist, u.data());
+            for (size_t k = 0; k < (size_t)g.groups * m; ++k) pt.hg_x.push_back((float)(u[k] * sq));
+            pt.hg_y = pt.hg_x;   // the y grid equals the x grid (square box, same pitch)
+        }
+    }
+}
+
+}  // namespace dh

@@ -1,0 +1,85 @@
+// Host-side plan of one handle: settings, validation, FP64 geometry and the device tables derived from them.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/digholo.h"
+
+namespace dh {
+
+// Settings exactly as the caller gave them (guide modules "Frame buffer", "Window sizes", "Wavelength",
+// "Alignment", "Modal decomposition").
+struct Settings {
+    int width = 0, height = 0, pols = 1;
+    double pixel = 20e-6;
+    double wavelength = 1565e-9;
+    int n = 128;                         // FFT window (square)
+    double centre[DH_MAX_POLS][2] = {{0, 0}, {0, 0}};
+    double radius_deg = 0.0;
+    int m_req = 0;                       // 0: the guide's size rule
+    double tilt_deg[DH_MAX_POLS][2] = {{0, 0}, {0, 0}};
+    double defocus[DH_MAX_POLS] = {0, 0};
+    double waist[DH_MAX_POLS] = {100e-6, 100e-6};
+    int groups = 0;
+    int precision = DH_PRECISION_FP32;
+};
+
+// Geometry of one axis of one polarisation (all FP64, computed as the conventions in digholo.h state).
+struct AxisGeom {
+    int origin;      // frame index of window pixel 0
+    double eps;      // round_half_away(c/px) - c/px, the sub-pixel offset of the window grid
+    double kappa;    // tilt in bins
+    int k0;          // box centre bin
+    int klo;         // first box bin, k0 - M/2
+};
+
+struct PolGeom {
+    AxisGeom ax[2];
+    double r;        // window radius in bins
+    double defocus, waist;
+};
+
+struct Geometry {
+    int n, m, groups, modes, pols;
+    double dx;       // field pitch N px / M
+    PolGeom pol[DH_MAX_POLS];
+};
+
+// Per-polarisation host tables in the layouts the kernels read (FP64 arithmetic, stored FP32).
+struct PolTables {
+    std::vector<float> phase_x, phase_y;   // complex [M]: (-1)^klo exp(-2 pi i (klo+p) eps / N) / N
+    std::vector<float> corr_x, corr_y;     // complex [M]: (-1)^i exp(-2 pi i (kappa-k0)(i-M/2)/M) exp(-i pi D x'^2/lambda)
+    std::vector<int> mask_lo, mask_hi;     // [M] per box row q: kept columns p in [lo, hi] (empty if lo > hi)
+    std::vector<float> hg_x, hg_y;         // [G][M]: u_g(x'_i) sqrt(dx')
+};
+
+struct Tables {
+    std::vector<float> tw_fwd_n;   // complex [N]: exp(-2 pi i k / N)
+    std::vector<float> tw_inv_m;   // complex [M]: exp(+2 pi i k / M)
+    std::vector<int> radix_n;      // radices of N (first pass first)
+    std::vector<int> radix_m;      // radices of M
+    std::vector<int> mode_m, mode_n;
+    PolTables pol[DH_MAX_POLS];
+};
+
+// Round half away from zero, as the window origin and the box centre use.
+int round_half_away(double v);
+// The guide's reduced field size rule: 16 ceil(2 r / 16).
+int ifft_size_rule(double r_bins);
+// Factor a length into the radices the kernels implement; empty if impossible.
+std::vector<int> radix_plan(int len);
+
+// Validate settings and derive the geometry.  Returns DH_SUCCESS or an error code with a message.
+int build_geometry(const Settings& s, Geometry* g, std::string* why);
+// Geometry for one alignment candidate (tilt, defocus, waist replaced).
+int build_geometry_candidate(const Settings& s, const dh_setting& c, Geometry* g, std::string* why);
+// Fill the host tables of a geometry.
+void build_tables(const Settings& s, const Geometry& g, Tables* t);
+// HG 1D functions u_0..u_{G-1} at positions x (recurrence, FP64), row-major [G][len].
+void hg_table(int groups, const double* x, int len, double waist, double* out);
+
+}  // namespace dh

@@ -1,0 +1,74 @@
+// Handle state and the host-side helpers shared by the entry points.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstddef>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "kernels.cuh"
+#include "plan.hpp"
+
+namespace dh {
+
+// Scratch budget per launch chunk of the generic path: small enough that the intermediate spectra of one
+// chunk stay resident in the 129 MB L2 between the kernels that produce and consume them.
+constexpr size_t kScratchTarget = 48ull << 20;
+
+// Records a CUDA event pair around every kernel launch of a handle while enabled; totals per kernel name.
+struct Profiler : dhk::StageTimer {
+    bool on = false;
+    struct Rec {
+        std::string name;
+        cudaEvent_t a, b;
+    };
+    std::vector<cudaEvent_t> pool;
+    std::vector<Rec> pending;
+    cudaEvent_t open = nullptr;
+    std::vector<std::string> names;
+    std::vector<long long> launches;
+    std::vector<double> total_ms;
+    cudaEvent_t take();
+    void start(cudaStream_t s) override;
+    void stop(cudaStream_t s, const char* kernel) override;
+    int resolve();   // wait for pending events, fold them into the totals
+    void reset();
+    ~Profiler() override;
+};
+
+struct Handle {
+    std::mutex mu;
+    Settings s;
+    bool dirty = true;
+    int device = -1;
+    Geometry geo{};
+    Tables tab;
+    void* d_blob = nullptr;       // plan tables (device)
+    dhk::Plan plan{};
+    void* d_scratch = nullptr;    // generic-path scratch (device)
+    size_t scratch_bytes = 0;
+    Profiler prof;
+    dhk::StageTimer* timer() { return prof.on ? &prof : nullptr; }
+};
+
+int fail(int code, const std::string& why);
+int cuda_fail(cudaError_t e, const char* where);
+Handle* get_handle(dh_handle h);
+int ensure_plan(Handle* H);
+int ensure_scratch(Handle* H, size_t bytes);
+size_t split_window_bytes(const dhk::Plan& P);
+// Upload the tables of a geometry to a fresh device blob and fill the kernel plan that points into it.
+int upload_plan(const Settings& s, const Geometry& g, const Tables& t, void** out_blob, dhk::Plan* out);
+// Queue the generic three-kernel path for frames [0, batch) with the given plan and scratch.
+int run_split(const dhk::Plan& P, void* scratch, size_t scratch_bytes, const void* frames, int dtype, int batch,
+              void* window, void* fields, void* coefs, cudaStream_t st, dhk::StageTimer* timer);
+
+// Fused single-kernel path for small windows (k_fused.cu).
+bool use_fused(const dhk::Plan& P);
+cudaError_t fused_init();
+int launch_fused_path(Handle* H, const void* frames, int dtype, int batch, void* fields, void* coefs,
+                      cudaStream_t st);
+
+}  // namespace dh

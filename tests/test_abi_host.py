@@ -1,0 +1,154 @@
+"""Host-only tests of the C ABI: the library loads, exports every declared symbol, validates settings with
+the guide's error codes and derives the same geometry as the oracle.  No GPU work is queued here."""
+import math
+import os
+import re
+
+import pytest
+
+import paper_2204_02348_gb300 as dh
+from oracle import digholo_oracle as orc
+from synth import holograms as syn
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "digholo.h")
+
+
+def _declared():
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"^\s*(?:int|const char\*)\s+(dh_\w+)\s*\(", txt, re.M)))
+
+
+def test_every_declared_symbol_is_exported():
+    names = _declared()
+    assert len(names) >= 17
+    for n in names:
+        assert hasattr(dh._lib, n), n
+    assert set(names) <= set(dh.ABI_NAMES)
+
+
+def test_error_codes_match_guide_values():
+    txt = open(HEADER).read()
+    codes = dict(re.findall(r"#define (DH_(?:SUCCESS|ERROR_\w+))\s+(\d+)", txt))
+    assert codes == {"DH_SUCCESS": "0", "DH_ERROR_ERROR": "1", "DH_ERROR_INVALIDHANDLE": "2",
+                     "DH_ERROR_NULLPOINTER": "3", "DH_ERROR_INVALIDDIMENSION": "5",
+                     "DH_ERROR_INVALIDPOLARISATION": "6", "DH_ERROR_INVALIDAXIS": "7",
+                     "DH_ERROR_INVALIDARGUMENT": "8", "DH_ERROR_MEMORYALLOCATION": "9",
+                     "DH_ERROR_TIMEOUT": "12", "DH_ERROR_CUDA": "13"}
+
+
+def _code(fn, *a):
+    with pytest.raises(dh.DigHoloError) as ei:
+        fn(*a)
+    return ei.value.code
+
+
+def test_invalid_handle_and_arguments():
+    assert _code(dh.dh_set_frame, 12345, 64, 64, 1, 20e-6) == dh.DH_ERROR_INVALIDHANDLE
+    h = dh.dh_create()
+    try:
+        assert _code(dh.dh_set_frame, h, 0, 64, 1, 20e-6) == dh.DH_ERROR_INVALIDDIMENSION
+        assert _code(dh.dh_set_frame, h, 64, 64, 3, 20e-6) == dh.DH_ERROR_INVALIDPOLARISATION
+        assert _code(dh.dh_set_frame, h, 64, 64, 1, -1.0) == dh.DH_ERROR_INVALIDARGUMENT
+        assert _code(dh.dh_set_beam_centre, h, 2, 0, 0.0) == dh.DH_ERROR_INVALIDAXIS
+        assert _code(dh.dh_set_tilt, h, 0, 2, 1.0) == dh.DH_ERROR_INVALIDPOLARISATION
+        assert _code(dh.dh_set_wavelength, h, 0.0) == dh.DH_ERROR_INVALIDARGUMENT
+        assert _code(dh.dh_set_fourier_window_radius, h, -1.0) == dh.DH_ERROR_INVALIDARGUMENT
+        assert _code(dh.dh_set_ifft_size, h, 40, 40) == dh.DH_ERROR_INVALIDDIMENSION
+        assert _code(dh.dh_set_ifft_size, h, 16 * 23, 16 * 23) == dh.DH_ERROR_INVALIDDIMENSION  # prime 23
+        assert _code(dh.dh_set_basis, h, 0, 100e-6, 40) == dh.DH_ERROR_INVALIDDIMENSION
+        assert _code(dh.dh_set_precision, h, 7) == dh.DH_ERROR_INVALIDARGUMENT
+        assert _code(dh.dh_set_fft_window, h, 64, 128) == dh.DH_ERROR_INVALIDDIMENSION
+        assert _code(dh.dh_set_fft_window, h, 15, 15) == dh.DH_ERROR_INVALIDDIMENSION
+        assert "square" in dh.dh_last_error() or "16" in dh.dh_last_error()
+        # frame geometry never set
+        assert _code(dh.dh_get_output_dims, h) == dh.DH_ERROR_INVALIDDIMENSION
+    finally:
+        dh.dh_destroy(h)
+    assert _code(dh.dh_destroy, h) == dh.DH_ERROR_INVALIDHANDLE
+
+
+def test_fft_window_floors_to_pixel_quanta():
+    h = dh.dh_create()
+    try:
+        assert dh.dh_set_fft_window(h, 130, 140) == (128, 128)   # floor to multiples of 16, then equal
+        assert _code(dh.dh_set_fft_window, h, 100, 100) == dh.DH_ERROR_INVALIDDIMENSION  # 96: not a power of two
+    finally:
+        dh.dh_destroy(h)
+
+
+@pytest.mark.parametrize("name", ["plain", "batching", "precision", "large_batch"])
+def test_output_dims_and_axes_match_oracle(name):
+    s = syn.WORKLOADS[name]()
+    h = dh.dh_create()
+    try:
+        dh.configure(h, s)
+        m, modes, dx = dh.dh_get_output_dims(h)
+        geos = orc.geometries(s)
+        assert m == geos[0].x.m
+        assert modes == len(orc.mode_list(s.group_count))
+        assert dx == pytest.approx(geos[0].x.dx, rel=1e-15)
+        for p in range(s.pol_count):
+            x, y = dh.dh_get_axes(h, p)
+            ox, oy = orc.output_axes(geos[p])
+            assert max(abs(a - b) for a, b in zip(x, ox)) == 0.0
+            assert max(abs(a - b) for a, b in zip(y, oy)) == 0.0
+    finally:
+        dh.dh_destroy(h)
+    expected_m = {"plain": 32, "batching": 64, "precision": 96, "large_batch": 176}[name]
+    assert m == expected_m
+
+
+def test_window_outside_frame_and_half_plane_rejected():
+    s = syn.setup_plain()
+    h = dh.dh_create()
+    try:
+        dh.configure(h, s)
+        dh.dh_set_beam_centre(h, 0, 0, 10 * s.pixel)     # window would start at x = -54
+        assert _code(dh.dh_get_output_dims, h) == dh.DH_ERROR_INVALIDARGUMENT
+        dh.dh_set_beam_centre(h, 0, 0, s.beam_centre[0][0])
+        dh.dh_set_tilt(h, 0, 0, -1.0)                     # off-axis term in the missing half plane
+        assert _code(dh.dh_get_output_dims, h) == dh.DH_ERROR_INVALIDARGUMENT
+        dh.dh_set_tilt(h, 0, 0, 1.0)
+        dh.dh_set_ifft_size(h, 0, 0)                      # the guide's rule: 48 for a 128 window at 0.32 w_max
+        assert dh.dh_get_output_dims(h)[0] == 48
+        dh.dh_set_basis(h, 0, 150e-6, 0)                  # no modal decomposition
+        assert dh.dh_get_output_dims(h)[1] == 0
+    finally:
+        dh.dh_destroy(h)
+
+
+def test_serving_geometries_are_accepted():
+    import numpy as np
+    rng = np.random.default_rng(4)
+    for kind in syn.SERVING_KINDS:
+        for _ in range(5):
+            s = syn.serving_geometry(kind, rng)
+            h = dh.dh_create()
+            try:
+                dh.configure(h, s)
+                m, modes, _ = dh.dh_get_output_dims(h)
+                assert m == orc.geometries(s)[0].x.m and m % 16 == 0
+                assert modes == s.group_count * (s.group_count + 1) // 2
+            finally:
+                dh.dh_destroy(h)
+
+
+def test_paper_size_rule_table_through_abi():
+    # FFT [IFFT] sizes of the Benchmarks table, with the window radius at the non-overlap limit
+    for n, m in [(64, 32), (128, 48), (256, 96), (512, 176), (1024, 336)]:
+        h = dh.dh_create()
+        try:
+            px, lam = 20e-6, 1565e-9
+            dh.dh_set_frame(h, n, n, 1, px)
+            dh.dh_set_wavelength(h, lam)
+            dh.dh_set_fft_window(h, n, n)
+            dh.dh_set_beam_centre(h, 0, 0, n / 2 * px)
+            dh.dh_set_beam_centre(h, 1, 0, n / 2 * px)
+            wmax = math.degrees(lam / (2 * px))
+            rad = orc.window_radius_fraction() * wmax
+            dh.dh_set_fourier_window_radius(h, rad)
+            dh.dh_set_tilt(h, 0, 0, orc.rule_tilt(rad))
+            dh.dh_set_tilt(h, 1, 0, orc.rule_tilt(rad))
+            assert dh.dh_get_output_dims(h)[0] == m
+        finally:
+            dh.dh_destroy(h)

@@ -1,0 +1,191 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the same seeded frames.
+
+Bars (per frame and polarisation): field relative L2 <= 1e-5 and coefficient relative L2 <= 1e-5 on the
+FP32 path; the masked Fourier window <= 2e-6.  Outputs are NaN-poisoned before each call.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from gpu_util import (COEF_TOL, FIELD_TOL, WINDOW_TOL, oracle_window, rel_l2, run_library)
+from oracle import digholo_oracle as orc
+from synth import holograms as syn
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _check(setup, frames, out, field_tol=FIELD_TOL, coef_tol=COEF_TOL):
+    f_ref, c_ref = orc.process_batch(frames, setup)
+    if out["fields"] is not None:
+        ef = rel_l2(out["fields"], f_ref)
+        assert np.all(np.isfinite(out["fields"]))
+        assert ef.max() <= field_tol, ef
+    if out["coefs"] is not None:
+        ec = rel_l2(out["coefs"], c_ref)
+        assert np.all(np.isfinite(out["coefs"]))
+        assert ec.max() <= coef_tol, ec
+    return f_ref, c_ref
+
+
+def test_plain_128_f32():
+    s = syn.setup_plain()
+    d = syn.make_frames(s, 1)
+    out = run_library(s, d["frames"], window=True)
+    _check(s, d["frames"], out)
+    w_ref = oracle_window(d["frames"][0], orc.pol_geometry(s, 0))
+    assert rel_l2(out["window"][:, :1], w_ref[None, None])[0, 0] <= WINDOW_TOL
+
+
+def test_plain_with_paper_size_rule():
+    s = syn.with_(syn.setup_plain(), ifft_size=0)     # 48 x 48 field, radix 16 x 3
+    d = syn.make_frames(s, 2, seed=9)
+    out = run_library(s, d["frames"])
+    assert out["m"] == 48
+    _check(s, d["frames"], out)
+
+
+def test_batching_320x256_u16_two_pols():
+    s = syn.setup_batching()
+    d = syn.make_frames(s, 5)
+    out = run_library(s, d["frames"], window=True)
+    _check(s, d["frames"], out)
+    for p in range(2):
+        w_ref = oracle_window(d["frames"][3], orc.pol_geometry(s, p))
+        assert rel_l2(out["window"][3:4, p:p + 1], w_ref[None, None])[0, 0] <= WINDOW_TOL
+
+
+def test_precision_640x512_fp32_overlap():
+    s = syn.setup_precision()
+    d = syn.make_frames(s, 2)
+    out = run_library(s, d["frames"])
+    _check(s, d["frames"], out)
+
+
+def test_large_window_512_m176_g20():
+    s = syn.setup_large_batch()
+    d = syn.make_frames(s, 1)
+    out = run_library(s, d["frames"])
+    _check(s, d["frames"], out)
+
+
+@pytest.mark.parametrize("kind", list(syn.SERVING_KINDS))
+def test_serving_geometries(kind):
+    rng = np.random.default_rng(list(syn.SERVING_KINDS).index(kind) + 100)
+    s = syn.serving_geometry(kind, rng)
+    d = syn.make_frames(s, 1, seed=21)
+    out = run_library(s, d["frames"])
+    _check(s, d["frames"], out)
+
+
+def test_largest_window_and_field_1024_m336():
+    s = syn.serving_geometry("1024x1024_1pol", np.random.default_rng(0))
+    wm = syn.w_max_deg()
+    s = syn.with_(s, radius_deg=0.32 * wm, tilt_deg=[(3 * 0.32 * wm / math.sqrt(2),) * 2], group_count=16)
+    d = syn.make_frames(s, 1, seed=22)
+    out = run_library(s, d["frames"])
+    assert out["m"] == 336
+    _check(s, d["frames"], out)
+
+
+def test_box_wraps_in_y_and_crosses_nyquist():
+    base = syn.setup_plain()
+    for ty in (-1.0, 1.9, 2.2):
+        s = syn.with_(base, tilt_deg=[(1.0, ty)], ifft_size=48)
+        d = syn.make_frames(s, 1, seed=int(ty * 10) + 50)
+        out = run_library(s, d["frames"])
+        _check(s, d["frames"], out)
+
+
+def test_subpixel_beam_centre_and_defocus():
+    base = syn.setup_batching()
+    s = syn.with_(base, beam_centre=[(80.37 * 20e-6, 127.62 * 20e-6), (239.51 * 20e-6, 128.49 * 20e-6)],
+                  defocus=[0.8, -1.3])
+    d = syn.make_frames(s, 2, seed=31)
+    out = run_library(s, d["frames"])
+    _check(s, d["frames"], out)
+
+
+def test_tiny_radius_mostly_empty_rows():
+    s = syn.with_(syn.setup_plain(), radius_deg=0.05, ifft_size=32)
+    d = syn.make_frames(s, 1, seed=41)
+    out = run_library(s, d["frames"])
+    _check(s, d["frames"], out)
+
+
+def test_small_window_64():
+    s = syn.with_(syn.setup_plain(), frame_w=64, frame_h=64, window=64, beam_centre=[(32 * 20e-6, 32 * 20e-6)],
+                  ifft_size=32, group_count=3, waist=[80e-6], signal_groups=3)
+    d = syn.make_frames(s, 3, seed=42)
+    out = run_library(s, d["frames"])
+    _check(s, d["frames"], out)
+
+
+def test_no_basis_and_partial_outputs():
+    s = syn.with_(syn.setup_batching(), group_count=0)
+    d = syn.make_frames(s, 2, seed=43)
+    out = run_library(s, d["frames"])
+    assert out["coefs"] is None and out["modes"] == 0
+    _check(s, d["frames"], out)
+    s2 = syn.setup_batching()
+    o1 = run_library(s2, d["frames"], fields=False)
+    o2 = run_library(s2, d["frames"], coefs=False)
+    assert o1["fields"] is None and o2["coefs"] is None
+    _check(s2, d["frames"], o1)
+    _check(s2, d["frames"], o2)
+
+
+def test_batch_below_one_processes_one_frame():
+    s = syn.setup_plain()
+    d = syn.make_frames(s, 1, seed=44)
+    out = run_library(s, d["frames"], batch=0)
+    _check(s, d["frames"], out)
+
+
+def test_deterministic_bitwise():
+    s = syn.setup_batching()
+    d = syn.make_frames(s, 3, seed=45)
+    a = run_library(s, d["frames"])
+    b = run_library(s, d["frames"])
+    assert np.array_equal(a["fields"].view(np.uint32), b["fields"].view(np.uint32))
+    assert np.array_equal(a["coefs"].view(np.uint32), b["coefs"].view(np.uint32))
+
+
+def test_full_size_batching_sampled():
+    """The bench's workload (1000 frames of 320x256, one call); sampled frames checked against the oracle."""
+    s = syn.setup_batching()
+    d = syn.make_frames(s, 1000)
+    out = run_library(s, d["frames"])
+    idx = [0, 1, 499, 998, 999]
+    f_ref, c_ref = orc.process_batch(d["frames"][idx], s)
+    assert rel_l2(out["fields"][idx], f_ref).max() <= FIELD_TOL
+    assert rel_l2(out["coefs"][idx], c_ref).max() <= COEF_TOL
+    assert np.all(np.isfinite(out["fields"])) and np.all(np.isfinite(out["coefs"]))
+
+
+def test_score_settings_matches_oracle():
+    import torch
+    import paper_2204_02348_gb300 as dh
+    s = syn.with_(syn.setup_batching(), group_count=5)
+    d = syn.make_frames(s, 3, seed=46)
+    cand = syn.candidate_settings(s, 4, seed=47)
+    ref = orc.score_settings(d["frames"], s, cand["tilt_deg"], cand["defocus"], cand["waist"])
+    h = dh.dh_create()
+    try:
+        dh.configure(h, s)
+        fr = torch.from_numpy(d["frames"]).cuda()
+        pw = torch.full((3, 4), float("nan"), dtype=torch.float32, device="cuda")
+        sets = [dh.make_setting(cand["tilt_deg"][k], cand["defocus"][k], cand["waist"][k]) for k in range(4)]
+        dh.dh_score_settings(h, fr, dh.DH_DTYPE_U16, 3, sets, pw)
+        torch.cuda.synchronize()
+        got = pw.cpu().numpy()
+    finally:
+        dh.dh_destroy(h)
+    assert np.all(np.abs(got - ref) / ref <= 2 * COEF_TOL), (got, ref)
