@@ -20,7 +20,7 @@ struct PolDev {
     const float2* phase_y;   // [M]
     const float2* corr_x;    // [M] (-1)^i residual-tilt and defocus phase
     const float2* corr_y;    // [M]
-    const float* hg_x;       // [G][M] u_g(x'_i) sqrt(dx')
+    const float* hg_x;       // [G][M] u_g(x'_i) dx'
     const float* hg_y;       // [G][M]
 };
 

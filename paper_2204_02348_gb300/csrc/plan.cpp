@@ -171,13 +171,13 @@ void build_tables(const Settings& s, const Geometry& g, Tables* t) {
             }
             if (lo >= 0) { pt.mask_lo[q] = lo; pt.mask_hi[q] = hi; }
         }
-        const double sq = std::sqrt(g.dx);
+        const double w = g.dx;   // quadrature weight of one axis: c = dx' dy' sum u_m u_n E
         std::vector<double> u((size_t)std::max(g.groups, 1) * m);
         pt.hg_x.clear();
         pt.hg_y.clear();
         if (g.groups > 0) {
             hg_table(g.groups, xp.data(), m, pg.waist, u.data());
-            for (size_t k = 0; k < (size_t)g.groups * m; ++k) pt.hg_x.push_back((float)(u[k] * sq));
+            for (size_t k = 0; k < (size_t)g.groups * m; ++k) pt.hg_x.push_back((float)(u[k] * w));
             pt.hg_y = pt.hg_x;   // the y grid equals the x grid (square box, same pitch)
         }
     }

@@ -54,7 +54,7 @@ struct PolTables {
     std::vector<float> phase_x, phase_y;   // complex [M]: (-1)^klo exp(-2 pi i (klo+p) eps / N) / N
     std::vector<float> corr_x, corr_y;     // complex [M]: (-1)^i exp(-2 pi i (kappa-k0)(i-M/2)/M) exp(-i pi D x'^2/lambda)
     std::vector<int> mask_lo, mask_hi;     // [M] per box row q: kept columns p in [lo, hi] (empty if lo > hi)
-    std::vector<float> hg_x, hg_y;         // [G][M]: u_g(x'_i) sqrt(dx')
+    std::vector<float> hg_x, hg_y;         // [G][M]: u_g(x'_i) dx'
 };
 
 struct Tables {
