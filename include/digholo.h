@@ -144,6 +144,27 @@ int dh_process_batch(dh_handle h, const void* d_frames, int dtype, int batch, vo
 int dh_process_batch_window(dh_handle h, const void* d_frames, int dtype, int batch, void* d_window,
                             void* d_fields, void* d_coefs, void* stream);
 
+/* Allocation-free variant of dh_process_batch.  The paper has no counterpart (digHolo allocates its own
+ * buffers).  It exists for callers that cannot let a library allocate device memory while they process: code
+ * whose device memory belongs to another allocator (a framework's caching pool, a serving process that has
+ * already divided a fixed HBM budget) and acquisition loops that must not stall, since cudaMalloc / cudaFree
+ * synchronise the device and can fail in the middle of a run.  It runs the same kernels as dh_process_batch
+ * (FP32 overlap) with the same arguments, outputs and error codes, but takes its plan tables and scratch from
+ * one 16 MiB array of static device memory (1 MiB of tables, 15 MiB of scratch) that every GPU loading the
+ * library holds until the process exits; it calls no cudaMalloc, cudaFree or other allocating routine.
+ *   - The first call on each device looks up the array's device address (cudaGetSymbolAddress) with that
+ *     device current and sets the kernels' shared-memory attribute; make that first call before any stream
+ *     capture.
+ *   - Each call uploads its plan tables with a copy ordered on `stream` (which first waits for the work
+ *     already queued on that stream), then processes the batch in chunks that fit the scratch.
+ *   - Geometries whose tables exceed 1 MiB, or whose single frame needs more than 15 MiB of scratch, are
+ *     rejected with DH_ERROR_INVALIDDIMENSION (the supported limits, N <= 1024 and M <= 512, fit).
+ *   - All calls share the array, which keeps the last call's contents; nothing in it needs to start at zero
+ *     (every element is written before it is read within a call).  Calls that overlap on the GPU (different
+ *     streams, or threads without ordering) race on the array: serialise them on one stream. */
+int dh_process_batch_noalloc(dh_handle h, const void* d_frames, int dtype, int batch, void* d_fields, void* d_coefs,
+                             void* stream);
+
 /* One alignment candidate for dh_score_settings: per polarisation tilt (x, y) in degrees, defocus in
  * dioptre and basis waist in metres. */
 typedef struct dh_setting {

@@ -68,6 +68,7 @@ _PROTOS = {
     "dh_get_axes": [_i, _i, ctypes.POINTER(_d), ctypes.POINTER(_d)],
     "dh_process_batch": [_i, _p, _i, _i, _p, _p, _p],
     "dh_process_batch_window": [_i, _p, _i, _i, _p, _p, _p, _p],
+    "dh_process_batch_noalloc": [_i, _p, _i, _i, _p, _p, _p],
     "dh_score_settings": [_i, _p, _i, _i, ctypes.POINTER(dh_setting), _i, _p, _p],
     "dh_set_profiling": [_i, _i],
     "dh_get_profile": [_i, _i, ctypes.c_char_p, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_d),
@@ -187,6 +188,12 @@ def dh_process_batch_window(h: int, frames, dtype: int, batch: int, window, fiel
                             stream=None) -> None:
     _check(_lib.dh_process_batch_window(h, _ptr(frames), dtype, batch, _ptr(window), _ptr(fields), _ptr(coefs),
                                         _stream(stream)))
+
+
+def dh_process_batch_noalloc(h: int, frames, dtype: int, batch: int, fields=None, coefs=None, stream=None) -> None:
+    """dh_process_batch without device allocation: tables and scratch come from the library's static
+    16 MiB device array (see include/digholo.h for the limits and the sharing rules)."""
+    _check(_lib.dh_process_batch_noalloc(h, _ptr(frames), dtype, batch, _ptr(fields), _ptr(coefs), _stream(stream)))
 
 
 def dh_score_settings(h: int, frames, dtype: int, batch: int, settings, power, stream=None) -> None:
