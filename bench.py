@@ -46,6 +46,7 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp32", "split_bf16"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--frames", type=int, default=FRAMES, help="frames per step and GPU (default: the workload's 1000)")
     return ap.parse_args()
 
 
@@ -245,7 +246,8 @@ def run_ours(args, ws, rank, local):
         dist.init_process_group("nccl", device_id=dev)
     setup = syn.setup_batching()
     prec = dh.DH_PRECISION_SPLIT_BF16 if args.precision == "split_bf16" else dh.DH_PRECISION_FP32
-    data = syn.make_frames(setup, FRAMES, seed=syn.BASE_SEED + 1000 * rank)
+    frames_n = args.frames
+    data = syn.make_frames(setup, frames_n, seed=syn.BASE_SEED + 1000 * rank)
     host = torch.from_numpy(data["frames"]).pin_memory()
     inputs = [host.to(dev) for _ in range(ROTATE)]
     h = dh.dh_create()
@@ -253,12 +255,12 @@ def run_ours(args, ws, rank, local):
     dh.dh_set_precision(h, prec)
     m, modes, _ = dh.dh_get_output_dims(h)
     P = setup.pol_count
-    fields = torch.empty((FRAMES, P, m, m), dtype=torch.complex64, device=dev)
-    coefs = torch.empty((FRAMES, P, modes), dtype=torch.complex64, device=dev)
+    fields = torch.empty((frames_n, P, m, m), dtype=torch.complex64, device=dev)
+    coefs = torch.empty((frames_n, P, modes), dtype=torch.complex64, device=dev)
     stream = torch.cuda.current_stream(dev)
 
     def step(k):
-        dh.dh_process_batch(h, inputs[k % ROTATE], dh.DH_DTYPE_U16, FRAMES, fields, coefs, stream)
+        dh.dh_process_batch(h, inputs[k % ROTATE], dh.DH_DTYPE_U16, frames_n, fields, coefs, stream)
 
     def barrier():
         if ws > 1:
@@ -293,7 +295,7 @@ def run_ours(args, ws, rank, local):
         import torch.distributed as dist
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     total_ms = float(t.item())
-    value = ws * FRAMES * args.steps / (total_ms / 1e3)
+    value = ws * frames_n * args.steps / (total_ms / 1e3)
 
     # ---- dominant kernel roofline
     peak, peak_src = measured_peak()
@@ -304,7 +306,7 @@ def run_ours(args, ws, rank, local):
     if dom:
         name, (nl, tms) = dom
         launches_per_step = nl / args.steps
-        frames_per_launch = FRAMES / launches_per_step
+        frames_per_launch = frames_n / launches_per_step
         avg_s = tms / nl / 1e3
         achieved = frames_per_launch * bpf / avg_s / 1e9
         traffic = recorded_traffic(name, frames_per_launch)
@@ -315,14 +317,14 @@ def run_ours(args, ws, rank, local):
                     "step_frac": (value / ws) * bpf / 1e9 / peak}
 
     # ---- end to end through the public API: pinned host frames in, fields and coefficients out
-    host_f = torch.empty((FRAMES, P, m, m), dtype=torch.complex64).pin_memory()
-    host_c = torch.empty((FRAMES, P, modes), dtype=torch.complex64).pin_memory()
+    host_f = torch.empty((frames_n, P, m, m), dtype=torch.complex64).pin_memory()
+    host_c = torch.empty((frames_n, P, modes), dtype=torch.complex64).pin_memory()
     dev_in = torch.empty_like(inputs[0])
     e2e_steps = max(3, min(args.steps, 20))
 
     def e2e_step():
         dev_in.copy_(host, non_blocking=True)
-        dh.dh_process_batch(h, dev_in, dh.DH_DTYPE_U16, FRAMES, fields, coefs, stream)
+        dh.dh_process_batch(h, dev_in, dh.DH_DTYPE_U16, frames_n, fields, coefs, stream)
         host_f.copy_(fields, non_blocking=True)
         host_c.copy_(coefs, non_blocking=True)
         stream.synchronize()
@@ -340,7 +342,7 @@ def run_ours(args, ws, rank, local):
     if ws > 1:
         import torch.distributed as dist
         dist.all_reduce(et, op=dist.ReduceOp.MAX)
-    e2e = {"value": ws * FRAMES * e2e_steps / (float(et.item()) / 1e3), "unit": "frames/s",
+    e2e = {"value": ws * frames_n * e2e_steps / (float(et.item()) / 1e3), "unit": "frames/s",
            "h2d_bytes_per_step": int(host.numel() * 2),
            "d2h_bytes_per_step": int(host_f.numel() * 8 + host_c.numel() * 8), "steps": e2e_steps}
 
@@ -350,10 +352,10 @@ def run_ours(args, ws, rank, local):
         workers = os.cpu_count() or 1
         pool = OraclePool(workers)
         pool.warm(setup, data["frames"])
-        rate, dt, n = pool.run(setup, data["frames"], repeat=2)
+        rate, dt, n = pool.run(setup, data["frames"], repeat=max(1, 3000 // frames_n))
         pool.close()
         cpu = {"value": rate, "unit": "frames/s", "cores": workers, "kind": "oracle",
-               "sample": f"{n} frames (the step's 1000-frame batch, twice) in {dt:.1f} s"}
+               "sample": f"{n} frames (repeated passes over the step's batch) in {dt:.1f} s on {workers} processes"}
 
     dh.dh_destroy(h)
     if rank == 0:
@@ -362,13 +364,14 @@ def run_ours(args, ws, rank, local):
             "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
             "warmup": max(args.warmup, 3), "ms_per_step": total_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "frames_per_step_per_gpu": FRAMES, "frame": [320, 256],
+            "config": {"workload": WORKLOAD if frames_n == FRAMES else WORKLOAD.replace("1000", str(frames_n)),
+                       "frames_per_step_per_gpu": frames_n, "frame": [320, 256],
                        "pols": P, "window": setup.window, "field": m, "modes": modes,
                        "overlap": args.precision, "l2": f"{ROTATE} rotating input batches "
                        f"({ROTATE * host.numel() * 2 / 1e6:.0f} MB) > 129 MB L2",
                        "parallelism": f"replicas x{ws}"},
             "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
-                           "unit": "ms per 1000-frame batch"},
+                           "unit": f"ms per {frames_n}-frame batch"},
             "roofline": roofline,
             "kernels": {k: {"launches": v[0], "total_ms": v[1]} for k, v in prof.items()},
             "gpu_launches": launches,
