@@ -352,7 +352,7 @@ def run_ours(args, ws, rank, local):
         workers = os.cpu_count() or 1
         pool = OraclePool(workers)
         pool.warm(setup, data["frames"])
-        rate, dt, n = pool.run(setup, data["frames"], repeat=max(1, 3000 // frames_n))
+        rate, dt, n = pool.run(setup, data["frames"], repeat=max(1, 6000 // frames_n))
         pool.close()
         cpu = {"value": rate, "unit": "frames/s", "cores": workers, "kind": "oracle",
                "sample": f"{n} frames (repeated passes over the step's batch) in {dt:.1f} s on {workers} processes"}

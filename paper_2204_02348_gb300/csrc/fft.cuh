@@ -119,7 +119,7 @@ __device__ __forceinline__ void dft_direct(float2* a, const float2* __restrict__
     for (int k = 0; k < R; ++k) {
         float2 acc = a[0];
 #pragma unroll
-        for (int r = 1; r < R; ++r) acc = cadd(acc, cmul(a[r], __ldg(&tw[((r * k) % R) * step])));
+        for (int r = 1; r < R; ++r) acc = cadd(acc, cmul(a[r], tw[((r * k) % R) * step]));
         y[k] = acc;
     }
 #pragma unroll
@@ -159,12 +159,12 @@ __device__ __forceinline__ void fft_pass(float2* buf, int L, int span, int lognb
         for (int r = 0; r < R; ++r) v[r] = buf[(base + r * s) * es + b];
         if (INV) {
 #pragma unroll
-            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], __ldg(&tw[j * r * tw_step]));
+            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[j * r * tw_step]);
         }
         dft<R, INV>(v, tw, L / R);
         if (!INV) {
 #pragma unroll
-            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], __ldg(&tw[j * r * tw_step]));
+            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[j * r * tw_step]);
         }
 #pragma unroll
         for (int r = 0; r < R; ++r) buf[(base + r * s) * es + b] = v[r];
@@ -210,6 +210,43 @@ __device__ __forceinline__ void fft_run(float2* buf, int L, const int* radices, 
             fft_pass_any<true>(R, buf, L, span, lognb, es, tw, tid, nthr);
             __syncthreads();
         }
+    }
+}
+
+}  // namespace dhk
+
+namespace dhk {
+
+// ---------------------------------------------------------------------------------------------- static passes
+// Compile-time variant of one radix-R pass: NB transforms of length L, element e of transform b at
+// buf[e * ES + b * BS]; DIT selects decimation in time (twiddle before the butterfly), otherwise decimation in
+// frequency (twiddle after).  SPAN is the block length (DIF: before the pass; DIT: after).  tw holds W_L^k
+// with the transform's sign.  Tasks are spread over NTHR threads with the transform index fastest.
+template <int R, bool INV, bool DIT, int L, int SPAN, int NB, int ES, int BS, int NTHR>
+__device__ __forceinline__ void spass(float2* buf, const float2* tw, int tid) {
+    constexpr int S = SPAN / R;
+    constexpr int TW = L / SPAN;
+    constexpr int TASKS = NB * (L / R);
+    for (int t = tid; t < TASKS; t += NTHR) {
+        const int b = t % NB;
+        const int bf = t / NB;
+        const int blk = bf / S;
+        const int j = bf - blk * S;
+        const int base = blk * SPAN + j;
+        float2 v[R];
+#pragma unroll
+        for (int r = 0; r < R; ++r) v[r] = buf[(base + r * S) * ES + b * BS];
+        if (DIT) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[j * r * TW]);
+        }
+        dft<R, INV>(v, tw, L / R);
+        if (!DIT) {
+#pragma unroll
+            for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[j * r * TW]);
+        }
+#pragma unroll
+        for (int r = 0; r < R; ++r) buf[(base + r * S) * ES + b * BS] = v[r];
     }
 }
 

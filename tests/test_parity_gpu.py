@@ -38,10 +38,11 @@ def _check(setup, frames, out, field_tol=FIELD_TOL, coef_tol=COEF_TOL):
 def test_plain_128_f32():
     s = syn.setup_plain()
     d = syn.make_frames(s, 1)
-    out = run_library(s, d["frames"], window=True)
+    out = run_library(s, d["frames"], window=True)        # generic multi-kernel path
     _check(s, d["frames"], out)
     w_ref = oracle_window(d["frames"][0], orc.pol_geometry(s, 0))
     assert rel_l2(out["window"][:, :1], w_ref[None, None])[0, 0] <= WINDOW_TOL
+    _check(s, d["frames"], run_library(s, d["frames"]))   # fused single-kernel path
 
 
 def test_plain_with_paper_size_rule():
@@ -55,7 +56,8 @@ def test_plain_with_paper_size_rule():
 def test_batching_320x256_u16_two_pols():
     s = syn.setup_batching()
     d = syn.make_frames(s, 5)
-    out = run_library(s, d["frames"], window=True)
+    _check(s, d["frames"], run_library(s, d["frames"]))   # fused single-kernel path
+    out = run_library(s, d["frames"], window=True)        # generic multi-kernel path
     _check(s, d["frames"], out)
     for p in range(2):
         w_ref = oracle_window(d["frames"][3], orc.pol_geometry(s, p))
@@ -111,6 +113,26 @@ def test_subpixel_beam_centre_and_defocus():
     d = syn.make_frames(s, 2, seed=31)
     out = run_library(s, d["frames"])
     _check(s, d["frames"], out)
+
+
+def test_odd_window_origin_unaligned_pixel_pairs():
+    """Odd window origins (and an odd frame width) force the scalar pixel loads of the fused path."""
+    base = syn.setup_batching()
+    s = syn.with_(base, beam_centre=[(81.2 * 20e-6, 128.0 * 20e-6), (240.0 * 20e-6, 129.3 * 20e-6)])
+    d = syn.make_frames(s, 2, seed=32)
+    _check(s, d["frames"], run_library(s, d["frames"]))
+    s2 = syn.with_(syn.setup_plain(), frame_w=131, beam_centre=[(64.6 * 20e-6, 64.0 * 20e-6)])
+    d2 = syn.make_frames(s2, 2, seed=33)
+    _check(s2, d2["frames"], run_library(s2, d2["frames"]))
+
+
+def test_fused_and_generic_paths_agree():
+    s = syn.setup_batching()
+    d = syn.make_frames(s, 7, seed=34)
+    a = run_library(s, d["frames"])
+    b = run_library(s, d["frames"], window=True)
+    assert rel_l2(a["fields"], b["fields"]).max() <= FIELD_TOL
+    assert rel_l2(a["coefs"], b["coefs"]).max() <= COEF_TOL
 
 
 def test_tiny_radius_mostly_empty_rows():
