@@ -93,7 +93,7 @@ int upload_plan(const Settings& s, const Geometry& g, const Tables& t, void** ou
     const size_t o_pm = b.put(pm.data(), pm.size() * 4);
     const size_t o_mm = b.put(t.mode_m.data(), t.mode_m.size() * 4);
     const size_t o_mn = b.put(t.mode_n.data(), t.mode_n.size() * 4);
-    size_t o_pol[DH_MAX_POLS][8] = {};
+    size_t o_pol[DH_MAX_POLS][9] = {};
     for (int p = 0; p < g.pols; ++p) {
         const PolTables& pt = t.pol[p];
         o_pol[p][0] = b.put(pt.mask_lo.data(), pt.mask_lo.size() * 4);
@@ -104,6 +104,7 @@ int upload_plan(const Settings& s, const Geometry& g, const Tables& t, void** ou
         o_pol[p][5] = b.put(pt.corr_y.data(), pt.corr_y.size() * 4);
         o_pol[p][6] = b.put(pt.hg_x.data(), pt.hg_x.size() * 4);
         o_pol[p][7] = b.put(pt.hg_y.data(), pt.hg_y.size() * 4);
+        o_pol[p][8] = b.put(pt.hgy_tc.data(), pt.hgy_tc.size() * 2);
     }
     void* d = nullptr;
     cudaError_t e = cudaMalloc(&d, b.bytes.size());
@@ -124,6 +125,7 @@ int upload_plan(const Settings& s, const Geometry& g, const Tables& t, void** ou
     P.width = s.width;
     P.height = s.height;
     P.precision = s.precision;
+    P.tc_np = tc_rows(g.groups);
     P.nrad_n = (int)t.radix_n.size();
     P.nrad_m = (int)t.radix_m.size();
     for (int i = 0; i < P.nrad_n; ++i) P.rad_n[i] = t.radix_n[i];
@@ -148,6 +150,7 @@ int upload_plan(const Settings& s, const Geometry& g, const Tables& t, void** ou
         pd.corr_y = (const float2*)(base + o_pol[p][5]);
         pd.hg_x = (const float*)(base + o_pol[p][6]);
         pd.hg_y = (const float*)(base + o_pol[p][7]);
+        pd.hgy_tc = (const uint16_t*)(base + o_pol[p][8]);
     }
     *out_blob = d;
     return DH_SUCCESS;
@@ -159,6 +162,8 @@ int init_device_once(int dev) {
     std::lock_guard<std::mutex> lk(mu);
     if (dev >= 0 && dev < 64 && inited[dev]) return DH_SUCCESS;
     cudaError_t e = dhk::split_init();
+    if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
+    e = dhk::tc_init();
     if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
     e = fused_init();
     if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");

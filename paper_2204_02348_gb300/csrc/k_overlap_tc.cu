@@ -1,0 +1,250 @@
+// Split-BF16 tensor-core variant of the generic path's last kernel (pipeline step 2 along y, tilt and defocus
+// removal, and the HG modal decomposition of step 3).
+//
+// One block per (frame, polarisation) window, 64 field columns per chunk.  After the y inverse transform and
+// the correction, the chunk's field E[j][i] (FP32) is split into bfloat16 hi + lo parts and written as the A
+// operand of a 128 x NP x M contraction (rows: real and imaginary parts of the 64 columns; K: the field row
+// j), whose B operand holds u_n(y'_j) dy' as bfloat16 hi + lo (host-built, FP64 -> bf16).  One elected thread
+// issues the three products hi*hi + hi*lo + lo*hi per 16-wide K step with tcgen05.mma (kind::f16, FP32
+// accumulation in tensor memory) and commits them to an mbarrier; the four warps of the first warpgroup read
+// the 128 x NP accumulator back with tcgen05.ld and finish the second (x) contraction on CUDA cores with a
+// fixed shuffle tree.  The lo*lo product is below FP32 rounding of the result and is dropped.
+//
+// Operands use the no-swizzle K-major canonical layout: 8-row x 16-byte core matrices stored contiguously,
+// core (rb, kb) at (rb * K/8 + kb) * 128 bytes, so the descriptor's leading-dimension offset (between cores
+// along K) is 128 bytes and its stride-dimension offset (between 8-row groups) is 16 K bytes.
+// Every wait on the mbarrier is bounded; on expiry the window's coefficients are written as NaN and the
+// block releases its tensor memory before it returns.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "fft.cuh"
+#include "kernels.cuh"
+
+namespace dhk {
+
+namespace {
+
+constexpr int kTcThreads = 256;
+constexpr int kTcCols = 64;          // field columns per chunk (A rows = 2 * 64 = 128)
+constexpr int kTcMaxM = 192;         // shared-memory bound of this kernel
+constexpr int kTmemCols = 32;
+constexpr long kWaitLimit = 1L << 24;
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+    uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+    d |= (uint64_t)1 << 46;   // descriptor version
+    return d;                 // base offset 0, no swizzle
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ bool wait_parity(uint32_t mbar, uint32_t parity) {
+    uint32_t done = 0;
+    for (long it = 0; it < kWaitLimit && !done; ++it) {
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
+    }
+    return done != 0;
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* out) {
+    uint32_t v[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
+          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) out[i] = __uint_as_float(v[i]);
+}
+
+struct TcLayout {
+    size_t buf, a, b, part, bytes;
+};
+
+__host__ __device__ inline TcLayout tc_layout(int M, int NP, int modes) {
+    TcLayout L;
+    L.buf = 0;                                             // float2 [M][64]
+    L.a = L.buf + (size_t)M * kTcCols * 8;                  // bf16 [2][128][M]
+    L.b = L.a + (size_t)2 * 128 * M * 2;                    // bf16 [2][NP][M]
+    L.part = L.b + (size_t)2 * NP * M * 2;                  // float [4][modes]
+    L.bytes = L.part + (size_t)4 * (modes > 0 ? modes : 1) * 4 + 64;
+    L.bytes = (L.bytes + 1023) & ~(size_t)1023;
+    return L;
+}
+
+}  // namespace
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_yinv_tc(const __grid_constant__ Plan P, const __grid_constant__ Batch B) {
+    extern __shared__ __align__(1024) unsigned char sm[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int M = P.m, G = P.groups, modes = P.modes, NP = P.tc_np;
+    const TcLayout L = tc_layout(M, NP, modes);
+    float2* buf = reinterpret_cast<float2*>(sm + L.buf);
+    __nv_bfloat16* A = reinterpret_cast<__nv_bfloat16*>(sm + L.a);
+    __nv_bfloat16* Bm = reinterpret_cast<__nv_bfloat16*>(sm + L.b);
+    float* part = reinterpret_cast<float*>(sm + L.part);
+    const int pol = blockIdx.x;
+    const PolDev& pd = P.pol[pol];
+
+    // B operand (static per polarisation): 16-byte copies
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(pd.hgy_tc);
+        uint4* dst = reinterpret_cast<uint4*>(Bm);
+        const int n16 = (2 * NP * M * 2) / 16;
+        for (int i = tid; i < n16; i += kTcThreads) dst[i] = __ldg(&src[i]);
+    }
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(&tmem_slot)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&mbar)));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+    const uint32_t tmem = tmem_slot;
+    const uint32_t mbar_a = smem_addr(&mbar);
+    const uint32_t a_hi = smem_addr(A), a_lo = a_hi + 128 * M * 2;
+    const uint32_t b_hi = smem_addr(Bm), b_lo = b_hi + NP * M * 2;
+    const uint32_t lbo = 128, sbo = 16 * M;
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NP >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    uint32_t phase = 0;
+    bool ok = true;
+
+    for (int fb = blockIdx.y; fb < B.count; fb += gridDim.y) {
+        const int f = B.frame0 + fb;
+        const float2* g = B.g + (size_t)(fb * P.pols + pol) * M * M;
+        float2 acc = make_float2(0.f, 0.f);   // mode tid (modes <= 256)
+        for (int i0 = 0; i0 < M; i0 += kTcCols) {
+            for (int idx = tid; idx < M * kTcCols; idx += kTcThreads) {
+                const int q = idx >> 6, i = idx & (kTcCols - 1);
+                buf[P.pos_m[q] * kTcCols + i] = (i0 + i < M) ? g[(size_t)q * M + i0 + i] : make_float2(0.f, 0.f);
+            }
+            __syncthreads();
+            fft_run<true>(buf, M, P.rad_m, P.nrad_m, 6, kTcCols, P.tw_inv_m, tid, kTcThreads);
+            for (int idx = tid; idx < M * kTcCols; idx += kTcThreads) {
+                const int j = idx >> 6, i = idx & (kTcCols - 1);
+                if (i0 + i < M) {
+                    const float2 e = cmul(cmul(buf[idx], pd.corr_y[j]), pd.corr_x[i0 + i]);
+                    buf[idx] = e;
+                    if (B.fields) B.fields[((size_t)(f * P.pols + pol) * M + j) * M + i0 + i] = e;
+                } else {
+                    buf[idx] = make_float2(0.f, 0.f);
+                }
+            }
+            __syncthreads();
+            // A operand: rows r = i (real part) and 64 + i (imaginary part), K = j; 8 consecutive j per task
+            for (int t = tid; t < kTcCols * (M / 8); t += kTcThreads) {
+                const int i = t & (kTcCols - 1), jb = t >> 6;
+                __align__(16) __nv_bfloat16 hr[8], hi_[8], lr[8], li[8];
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    const float2 e = buf[(8 * jb + c) * kTcCols + i];
+                    const __nv_bfloat16 xr = __float2bfloat16_rn(e.x), xi = __float2bfloat16_rn(e.y);
+                    hr[c] = xr;
+                    hi_[c] = xi;
+                    lr[c] = __float2bfloat16_rn(e.x - __bfloat162float(xr));
+                    li[c] = __float2bfloat16_rn(e.y - __bfloat162float(xi));
+                }
+                const int rr = i, ri = 64 + i;
+                const size_t o_r = ((size_t)(rr >> 3) * (M >> 3) + jb) * 64 + (rr & 7) * 8;
+                const size_t o_i = ((size_t)(ri >> 3) * (M >> 3) + jb) * 64 + (ri & 7) * 8;
+                *reinterpret_cast<uint4*>(A + o_r) = *reinterpret_cast<const uint4*>(hr);
+                *reinterpret_cast<uint4*>(A + o_i) = *reinterpret_cast<const uint4*>(hi_);
+                *reinterpret_cast<uint4*>(A + 128 * M + o_r) = *reinterpret_cast<const uint4*>(lr);
+                *reinterpret_cast<uint4*>(A + 128 * M + o_i) = *reinterpret_cast<const uint4*>(li);
+            }
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            __syncthreads();
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            if (tid == 0 && ok) {
+                for (int ks = 0; ks < M / 16; ++ks) {
+                    const uint32_t ko = ks * 256;
+                    mma_bf16(tmem, smem_desc(a_hi + ko, lbo, sbo), smem_desc(b_hi + ko, lbo, sbo), idesc, ks > 0);
+                    mma_bf16(tmem, smem_desc(a_hi + ko, lbo, sbo), smem_desc(b_lo + ko, lbo, sbo), idesc, 1);
+                    mma_bf16(tmem, smem_desc(a_lo + ko, lbo, sbo), smem_desc(b_hi + ko, lbo, sbo), idesc, 1);
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar_a)
+                             : "memory");
+            }
+            const bool done = ok && wait_parity(mbar_a, phase);
+            phase ^= 1u;
+            ok = ok && done;
+            asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+            if (warp < 4) {
+                float T[32];
+                if (ok) {
+                    const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16);
+                    tmem_ld16(ta, T);
+                    if (NP > 16) tmem_ld16(ta + 16, T + 16);
+                }
+                // row r = 32 warp + lane: column i = r mod 64, part c = r / 64 (0 real, 1 imaginary)
+                const int i = (32 * warp + lane) & 63;
+                const bool in = (i0 + i) < M;
+#pragma unroll
+                for (int n = 0; n < 32; ++n) {
+                    if (n < G && (n < 16 || NP > 16)) {
+                        for (int m = 0; m + n < G; ++m) {
+                            const int k = (m + n) * (m + n + 1) / 2 + m;
+                            float v = (in && ok) ? __ldg(&pd.hg_x[(size_t)m * M + i0 + i]) * T[n] : 0.f;
+#pragma unroll
+                            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+                            if (lane == 0) part[warp * modes + k] = v;
+                        }
+                    }
+                }
+            }
+            asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+            __syncthreads();
+            if (tid < modes) {
+                acc.x += part[0 * modes + tid] + part[1 * modes + tid];
+                acc.y += part[2 * modes + tid] + part[3 * modes + tid];
+            }
+            __syncthreads();
+        }
+        if (B.coefs && tid < modes)
+            B.coefs[(size_t)(f * P.pols + pol) * modes + tid] = ok ? acc : make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols));
+}
+
+bool tc_supported(const Plan& P) {
+    return P.precision == DH_PRECISION_SPLIT_BF16 && P.groups > 0 && P.modes <= kTcThreads && P.m <= kTcMaxM &&
+           P.m % 16 == 0 && P.tc_np <= kTmemCols;
+}
+
+cudaError_t tc_init() {
+    return cudaFuncSetAttribute(k_yinv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024 - 1024);
+}
+
+cudaError_t launch_yinv_tc(const Plan& P, const Batch& B, cudaStream_t st) {
+    const TcLayout L = tc_layout(P.m, P.tc_np, P.modes);
+    dim3 grid(P.pols, B.count < 65535 ? B.count : 65535);
+    k_yinv_tc<<<grid, kTcThreads, L.bytes, st>>>(P, B);
+    return cudaGetLastError();
+}
+
+}  // namespace dhk

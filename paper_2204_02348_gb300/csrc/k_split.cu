@@ -223,6 +223,13 @@ cudaError_t launch_split(const Plan& P, const Batch& B, cudaStream_t st, StageTi
     // k_yinv: one block per window
     dim3 g3(P.pols, zf);
     const size_t sm3 = (size_t)(M + std::max(P.groups, 1)) * kChunkI * sizeof(float2);
+    if (tc_supported(P)) {
+        if (tm) tm->start(st);
+        cudaError_t e = launch_yinv_tc(P, B, st);
+        if (tm) tm->stop(st, "k_yinv_tc");
+        if (e != cudaSuccess) return e;
+        return cudaGetLastError();
+    }
     if (tm) tm->start(st);
     k_yinv<<<g3, kThreads, sm3, st>>>(P, B);
     if (tm) tm->stop(st, "k_yinv");

@@ -22,12 +22,14 @@ struct PolDev {
     const float2* corr_y;    // [M]
     const float* hg_x;       // [G][M] u_g(x'_i) dx'
     const float* hg_y;       // [G][M]
+    const uint16_t* hgy_tc;  // [2][NP][M] bf16 hi / lo of hg_y, tensor-core core-matrix layout
 };
 
 struct Plan {
     int n, m, groups, modes, pols;
     int width, height;
     int precision;           // DH_PRECISION_*
+    int tc_np;               // rows of the tensor-core B operand (16 or 32)
     int nrad_n, nrad_m;
     int rad_n[kMaxRadices];
     int rad_m[kMaxRadices];
@@ -63,5 +65,10 @@ struct StageTimer {
 cudaError_t launch_split(const Plan& plan, const Batch& batch, cudaStream_t stream, StageTimer* timer);
 // Shared-memory opt-in, once per process and device.
 cudaError_t split_init();
+
+// Split-BF16 tensor-core variant of the last generic kernel (k_overlap_tc.cu).
+bool tc_supported(const Plan& plan);
+cudaError_t tc_init();
+cudaError_t launch_yinv_tc(const Plan& plan, const Batch& batch, cudaStream_t stream);
 
 }  // namespace dhk

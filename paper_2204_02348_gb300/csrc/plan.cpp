@@ -5,6 +5,7 @@
 
 #include <cmath>
 #include <cstdio>
+#include <cstring>
 
 namespace dh {
 
@@ -113,6 +114,24 @@ void hg_table(int groups, const double* x, int len, double waist, double* out) {
     }
 }
 
+int tc_rows(int groups) { return groups <= 16 ? 16 : 32; }
+
+uint16_t bf16_bits(float v) {
+    uint32_t u;
+    std::memcpy(&u, &v, 4);
+    if ((u & 0x7f800000u) == 0x7f800000u) return (uint16_t)(u >> 16);   // inf / nan unchanged
+    const uint32_t lsb = (u >> 16) & 1u;
+    u += 0x7fffu + lsb;
+    return (uint16_t)(u >> 16);
+}
+
+static float bf16_value(uint16_t b) {
+    const uint32_t u = (uint32_t)b << 16;
+    float f;
+    std::memcpy(&f, &u, 4);
+    return f;
+}
+
 static void push_c(std::vector<float>& v, double re, double im) {
     v.push_back((float)re);
     v.push_back((float)im);
@@ -179,6 +198,18 @@ void build_tables(const Settings& s, const Geometry& g, Tables* t) {
             hg_table(g.groups, xp.data(), m, pg.waist, u.data());
             for (size_t k = 0; k < (size_t)g.groups * m; ++k) pt.hg_x.push_back((float)(u[k] * w));
             pt.hg_y = pt.hg_x;   // the y grid equals the x grid (square box, same pitch)
+            const int np = tc_rows(g.groups);
+            pt.hgy_tc.assign((size_t)2 * np * m, 0);
+            for (int n = 0; n < g.groups; ++n) {
+                for (int j = 0; j < m; ++j) {
+                    const double v = u[(size_t)n * m + j] * w;
+                    const uint16_t hi = bf16_bits((float)v);
+                    const uint16_t lo = bf16_bits((float)(v - (double)bf16_value(hi)));
+                    const size_t off = ((size_t)(n / 8) * (m / 8) + j / 8) * 64 + (n % 8) * 8 + (j % 8);
+                    pt.hgy_tc[off] = hi;
+                    pt.hgy_tc[(size_t)np * m + off] = lo;
+                }
+            }
         }
     }
 }

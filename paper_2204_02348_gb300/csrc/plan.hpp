@@ -6,6 +6,7 @@
 #include <mutex>
 #include <string>
 #include <vector>
+#include <cstdint>
 
 #include "../../include/digholo.h"
 
@@ -55,7 +56,15 @@ struct PolTables {
     std::vector<float> corr_x, corr_y;     // complex [M]: (-1)^i exp(-2 pi i (kappa-k0)(i-M/2)/M) exp(-i pi D x'^2/lambda)
     std::vector<int> mask_lo, mask_hi;     // [M] per box row q: kept columns p in [lo, hi] (empty if lo > hi)
     std::vector<float> hg_x, hg_y;         // [G][M]: u_g(x'_i) dx'
+    // split-BF16 tensor-core operand: u_n(y'_j) dy' as bf16 hi then lo, each [NP][M] in the K-major core-matrix
+    // layout (8 rows x 8 values per 128-byte core; core (nb, kb) at (nb * M/8 + kb) * 128 bytes); rows n >= G zero
+    std::vector<uint16_t> hgy_tc;
 };
+
+// Rows of the tensor-core B operand (the group count rounded up to 16).
+int tc_rows(int groups);
+// Round-to-nearest-even bfloat16 bits of a float.
+uint16_t bf16_bits(float v);
 
 struct Tables {
     std::vector<float> tw_fwd_n;   // complex [N]: exp(-2 pi i k / N)

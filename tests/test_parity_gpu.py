@@ -8,7 +8,7 @@ import math
 import numpy as np
 import pytest
 
-from gpu_util import (COEF_TOL, FIELD_TOL, WINDOW_TOL, oracle_window, rel_l2, run_library)
+from gpu_util import (COEF_TOL, FIELD_TOL, SPLIT_COEF_TOL, WINDOW_TOL, oracle_window, rel_l2, run_library)
 from oracle import digholo_oracle as orc
 from synth import holograms as syn
 
@@ -211,3 +211,29 @@ def test_score_settings_matches_oracle():
     finally:
         dh.dh_destroy(h)
     assert np.all(np.abs(got - ref) / ref <= 2 * COEF_TOL), (got, ref)
+
+
+# --------------------------------------------------------------------------------- split-BF16 tensor-core overlap
+
+SPLIT = 1   # DH_PRECISION_SPLIT_BF16
+
+
+@pytest.mark.parametrize("name,frames", [("precision", 2), ("large_batch", 1), ("plain", 2)])
+def test_split_bf16_overlap(name, frames):
+    s = syn.WORKLOADS[name]()
+    d = syn.make_frames(s, frames, seed=60)
+    out = run_library(s, d["frames"], precision=SPLIT)
+    _check(s, d["frames"], out, coef_tol=SPLIT_COEF_TOL)
+    plain = run_library(s, d["frames"])
+    # the split overlap agrees with the FP32 overlap within the split bar, and its fields are the FP32 fields
+    assert rel_l2(out["coefs"], plain["coefs"]).max() <= SPLIT_COEF_TOL
+    assert rel_l2(out["fields"], plain["fields"]).max() <= FIELD_TOL
+
+
+def test_split_bf16_serving_geometry_and_determinism():
+    s = syn.serving_geometry("512x512_2pol", np.random.default_rng(61))
+    d = syn.make_frames(s, 3, seed=62)
+    a = run_library(s, d["frames"], precision=SPLIT)
+    b = run_library(s, d["frames"], precision=SPLIT)
+    _check(s, d["frames"], a, coef_tol=SPLIT_COEF_TOL)
+    assert np.array_equal(a["coefs"].view(np.uint32), b["coefs"].view(np.uint32))
