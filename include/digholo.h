@@ -180,6 +180,52 @@ typedef struct dh_setting {
 int dh_score_settings(dh_handle h, const void* d_frames, int dtype, int batch, const dh_setting* settings,
                       int count, float* d_power, void* stream);
 
+/* ------------------------------------------------------------------------------------------------------------
+ * Serving loop (continuous batching).  The guide's library processes one batch per call on the caller's thread;
+ * this server accepts requests at any time from any thread, admits each as soon as a stream slot is free and
+ * its device memory fits a fixed HBM budget, and overlaps admitted requests on the device.  Plans (bases,
+ * twiddles, masks) stay resident on the device per geometry handle.
+ *
+ * A request names a configured handle (its geometry and settings, which must not change while the request is
+ * pending), host frames [batch][height][width] and optional host outputs (fields [batch][pol][M][M] and
+ * coefficients [batch][pol][modes], complex64).  Pinned host memory gives asynchronous copies.  A request
+ * larger than the budget is processed in consecutive frame chunks inside its reservation; a request whose
+ * single frame does not fit is rejected at submission with DH_ERROR_MEMORYALLOCATION.  Results do not depend
+ * on which other requests share the device (the kernels are deterministic and requests never share memory).
+ * ------------------------------------------------------------------------------------------------------------ */
+typedef struct dh_server_s* dh_server;
+
+typedef struct dh_request {
+    dh_handle geometry;        /* configured handle */
+    const void* h_frames;      /* host frames */
+    int dtype;                 /* DH_DTYPE_U16 or DH_DTYPE_F32 */
+    int batch;                 /* frames, >= 1 */
+    void* h_fields;            /* nullable host output */
+    void* h_coefs;             /* nullable host output */
+} dh_request;
+
+typedef struct dh_stats {
+    long long submitted, completed, failed, frames;
+    double p50_ms, p99_ms, max_ms;   /* submit-to-completion latency of completed requests */
+    double frames_per_s;             /* frames completed / (last completion - first submission) */
+    size_t budget_bytes, peak_bytes; /* HBM budget and the largest reservation total seen */
+    int max_inflight, peak_inflight;
+} dh_stats;
+
+/* Create a server on the current device with an HBM budget in bytes (reserved with one allocation; 0 is
+ * allowed and then admits nothing) and at most max_inflight concurrently processed requests (1..64, one
+ * stream each). */
+int dh_server_create(size_t hbm_budget, int max_inflight, dh_server* out);
+/* Queue a request; *ticket identifies it.  Validation errors are returned here. */
+int dh_server_submit(dh_server s, const dh_request* r, uint64_t* ticket);
+/* Wait for a request to finish (timeout_ms < 0: no limit).  Returns the request's own status, or
+ * DH_ERROR_TIMEOUT when the wait ran out (the request keeps running). */
+int dh_server_wait(dh_server s, uint64_t ticket, int timeout_ms);
+/* Counters and latency percentiles of the server so far. */
+int dh_server_stats(dh_server s, dh_stats* out);
+/* Finish in-flight requests, fail queued ones, release the budget and the streams. */
+int dh_server_destroy(dh_server s);
+
 /* Per-kernel device timing (the analogue of digHoloBenchmark's per-stage rates).  While enabled, every kernel
  * the handle launches is bracketed by a CUDA event pair recorded on the launch stream.  dh_set_profiling
  * clears the totals.  dh_get_profile waits for the recorded events and reports, per kernel, its name

@@ -50,6 +50,18 @@ class dh_setting(ctypes.Structure):
                 ("waist", ctypes.c_double * DH_MAX_POLS)]
 
 
+class dh_request(ctypes.Structure):
+    _fields_ = [("geometry", ctypes.c_int), ("h_frames", ctypes.c_void_p), ("dtype", ctypes.c_int),
+                ("batch", ctypes.c_int), ("h_fields", ctypes.c_void_p), ("h_coefs", ctypes.c_void_p)]
+
+
+class dh_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong), ("failed", ctypes.c_longlong),
+                ("frames", ctypes.c_longlong), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
+                ("max_ms", ctypes.c_double), ("frames_per_s", ctypes.c_double), ("budget_bytes", ctypes.c_size_t),
+                ("peak_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int), ("peak_inflight", ctypes.c_int)]
+
+
 _i, _d, _p = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
 _PROTOS = {
     "dh_create": [ctypes.POINTER(_i)],
@@ -71,6 +83,11 @@ _PROTOS = {
     "dh_process_batch_noalloc": [_i, _p, _i, _i, _p, _p, _p],
     "dh_score_settings": [_i, _p, _i, _i, ctypes.POINTER(dh_setting), _i, _p, _p],
     "dh_set_profiling": [_i, _i],
+    "dh_server_create": [ctypes.c_size_t, _i, ctypes.POINTER(_p)],
+    "dh_server_submit": [_p, ctypes.POINTER(dh_request), ctypes.POINTER(ctypes.c_uint64)],
+    "dh_server_wait": [_p, ctypes.c_uint64, _i],
+    "dh_server_stats": [_p, ctypes.POINTER(dh_stats)],
+    "dh_server_destroy": [_p],
     "dh_get_profile": [_i, _i, ctypes.c_char_p, ctypes.POINTER(ctypes.c_longlong), ctypes.POINTER(_d),
                        ctypes.POINTER(_i)],
 }
@@ -217,6 +234,34 @@ def dh_get_profile(h: int, max_kernels: int = 16):
         nm = names.raw[64 * i:64 * (i + 1)].split(b"\0", 1)[0].decode()
         out[nm] = (int(launches[i]), float(total[i]))
     return out
+
+
+def dh_server_create(hbm_budget: int, max_inflight: int = 8) -> int:
+    out = _p()
+    _check(_lib.dh_server_create(hbm_budget, max_inflight, ctypes.byref(out)))
+    return out.value
+
+
+def dh_server_submit(server: int, geometry: int, frames, dtype: int, batch: int, fields=None, coefs=None) -> int:
+    """Queue a request on host buffers (tensors or addresses); returns its ticket."""
+    req = dh_request(geometry, _ptr(frames), dtype, batch, _ptr(fields), _ptr(coefs))
+    t = ctypes.c_uint64()
+    _check(_lib.dh_server_submit(server, ctypes.byref(req), ctypes.byref(t)))
+    return t.value
+
+
+def dh_server_wait(server: int, ticket: int, timeout_ms: int = -1) -> None:
+    _check(_lib.dh_server_wait(server, ticket, timeout_ms))
+
+
+def dh_server_stats(server: int) -> dict:
+    st = dh_stats()
+    _check(_lib.dh_server_stats(server, ctypes.byref(st)))
+    return {k: getattr(st, k) for k, _ in dh_stats._fields_}
+
+
+def dh_server_destroy(server: int) -> None:
+    _check(_lib.dh_server_destroy(server))
 
 
 # ------------------------------------------------------------------------------------------ convenience

@@ -286,13 +286,21 @@ int process(Handle* H, const void* frames, int dtype, int batch, void* window, v
     if (rc) return rc;
     const dhk::Plan& P = H->plan;
     if (P.modes == 0) coefs = nullptr;
-    if (use_fused(P) && !window) return launch_fused_path(H, frames, dtype, batch, fields, coefs, st);
+    if (use_fused(P) && !window) return launch_fused_path(H, frames, dtype, batch, fields, coefs, st, H->timer());
     const size_t per_frame = split_window_bytes(P) * P.pols;
     int chunk = (int)std::max<size_t>(1, kScratchTarget / per_frame);
     chunk = std::min(chunk, batch);
     rc = ensure_scratch(H, per_frame * chunk);
     if (rc) return rc;
     return run_split(P, H->d_scratch, H->scratch_bytes, frames, dtype, batch, window, fields, coefs, st, H->timer());
+}
+
+int process_with(Handle* H, const void* frames, int dtype, int batch, void* fields, void* coefs, void* scratch,
+                 size_t scratch_bytes, cudaStream_t st) {
+    const dhk::Plan& P = H->plan;
+    if (P.modes == 0) coefs = nullptr;
+    if (use_fused(P)) return launch_fused_path(H, frames, dtype, batch, fields, coefs, st, nullptr);
+    return run_split(P, scratch, scratch_bytes, frames, dtype, batch, nullptr, fields, coefs, st, nullptr);
 }
 
 int run_split(const dhk::Plan& P, void* scratch, size_t scratch_bytes, const void* frames, int dtype, int batch,

@@ -279,7 +279,7 @@ cudaError_t fused_init() {
 }
 
 int launch_fused_path(Handle* H, const void* frames, int dtype, int batch, void* fields, void* coefs,
-                      cudaStream_t st) {
+                      cudaStream_t st, dhk::StageTimer* tm) {
     const dhk::Plan& P = H->plan;
     int dev = H->device;
     if (dev < 0 || dev >= 64) return fail(DH_ERROR_ERROR, "device index out of range");
@@ -301,7 +301,6 @@ int launch_fused_path(Handle* H, const void* frames, int dtype, int batch, void*
     A.coefs = (float2*)coefs;
     const long long windows = (long long)batch * P.pols;
     const int grid = (int)std::min<long long>(windows, 2LL * g_sm_count[dev]);
-    dhk::StageTimer* tm = H->timer();
     if (tm) tm->start(st);
     switch (P.m) {
         case 32: dhk::launch<32, 8, 4>(P, A, dtype, grid, st); break;

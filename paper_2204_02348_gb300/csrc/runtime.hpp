@@ -69,6 +69,11 @@ int run_split(const dhk::Plan& P, void* scratch, size_t scratch_bytes, const voi
 bool use_fused(const dhk::Plan& P);
 cudaError_t fused_init();
 int launch_fused_path(Handle* H, const void* frames, int dtype, int batch, void* fields, void* coefs,
-                      cudaStream_t st);
+                      cudaStream_t st, dhk::StageTimer* timer);
+
+// Queue one batch with the handle's uploaded plan and caller-provided scratch (used by the serving loop,
+// where concurrent requests of one handle must not share the handle's scratch).  No profiling.
+int process_with(Handle* H, const void* frames, int dtype, int batch, void* fields, void* coefs, void* scratch,
+                 size_t scratch_bytes, cudaStream_t st);
 
 }  // namespace dh

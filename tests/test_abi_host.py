@@ -152,3 +152,15 @@ def test_paper_size_rule_table_through_abi():
             assert dh.dh_get_output_dims(h)[0] == m
         finally:
             dh.dh_destroy(h)
+
+
+def test_server_entry_points_fail_cleanly_without_device_work():
+    with pytest.raises(dh.DigHoloError) as ei:
+        dh.dh_server_submit(0, 0, 0, dh.DH_DTYPE_U16, 1)
+    assert ei.value.code == dh.DH_ERROR_INVALIDHANDLE
+    with pytest.raises(dh.DigHoloError) as ei:
+        dh.dh_server_create(1 << 20, 0)
+    assert ei.value.code == dh.DH_ERROR_INVALIDARGUMENT
+    with pytest.raises(dh.DigHoloError) as ei:
+        dh.dh_server_stats(0)
+    assert ei.value.code == dh.DH_ERROR_INVALIDHANDLE

@@ -1,0 +1,145 @@
+"""Serving loop: requests of mixed geometries arrive while others run; each result must equal the same
+request processed alone (the kernels are deterministic and requests never share device memory)."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+from synth import holograms as syn
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _alone(dh, torch, h, setup, frames):
+    m, modes, _ = dh.dh_get_output_dims(h)
+    fr = torch.from_numpy(frames).cuda()
+    f = torch.empty((frames.shape[0], setup.pol_count, m, m), dtype=torch.complex64, device="cuda")
+    c = torch.empty((frames.shape[0], setup.pol_count, modes), dtype=torch.complex64, device="cuda")
+    dh.dh_process_batch(h, fr, dh.DH_DTYPE_U16, frames.shape[0], f, c)
+    torch.cuda.synchronize()
+    return f.cpu().numpy(), c.cpu().numpy()
+
+
+def _geometries():
+    rng = np.random.default_rng(90)
+    out = []
+    for kind in syn.SERVING_KINDS:
+        s = syn.serving_geometry(kind, rng)
+        out.append(s)
+    return out
+
+
+def test_mixed_requests_equal_alone_and_overlap():
+    import torch
+    import paper_2204_02348_gb300 as dh
+    geos = _geometries()
+    handles = []
+    for s in geos:
+        h = dh.dh_create()
+        dh.configure(h, s)
+        handles.append(h)
+    rng = np.random.default_rng(91)
+    reqs = []
+    for k in range(18):
+        gi = int(rng.integers(0, len(geos)))
+        n = int(rng.integers(1, 5))
+        fr = syn.make_frames(geos[gi], n, seed=1000 + k)["frames"]
+        m, modes, _ = dh.dh_get_output_dims(handles[gi])
+        host_in = torch.from_numpy(fr).pin_memory()
+        f = torch.full((n, geos[gi].pol_count, m, m), complex(float("nan"), 0), dtype=torch.complex64).pin_memory()
+        c = torch.full((n, geos[gi].pol_count, modes), complex(float("nan"), 0), dtype=torch.complex64).pin_memory()
+        reqs.append((gi, fr, host_in, f, c))
+    alone = [_alone(dh, torch, handles[gi], geos[gi], fr) for gi, fr, _, _, _ in reqs]
+    srv = dh.dh_server_create(2 << 30, 4)
+    try:
+        tickets = [None] * len(reqs)
+
+        def producer():
+            arr = np.random.default_rng(92)
+            for i, (gi, fr, hin, f, c) in enumerate(reqs):
+                tickets[i] = dh.dh_server_submit(srv, handles[gi], hin, dh.DH_DTYPE_U16, fr.shape[0], f, c)
+                if i % 3 == 2:
+                    time.sleep(float(arr.exponential(0.002)))
+
+        th = threading.Thread(target=producer)
+        th.start()
+        th.join()
+        for t in tickets:
+            dh.dh_server_wait(srv, t, -1)
+        st = dh.dh_server_stats(srv)
+    finally:
+        dh.dh_server_destroy(srv)
+        for h in handles:
+            dh.dh_destroy(h)
+    assert st["completed"] == len(reqs) and st["failed"] == 0
+    assert st["p99_ms"] >= st["p50_ms"] > 0
+    assert st["peak_inflight"] >= 2, st
+    for (gi, fr, hin, f, c), (fa, ca) in zip(reqs, alone):
+        assert np.array_equal(f.numpy().view(np.uint32), fa.view(np.uint32))
+        assert np.array_equal(c.numpy().view(np.uint32), ca.view(np.uint32))
+
+
+def test_small_budget_chunks_a_large_request():
+    import torch
+    import paper_2204_02348_gb300 as dh
+    s = syn.serving_geometry("1024x1024_1pol", np.random.default_rng(93))
+    fr = syn.make_frames(s, 10, seed=94)["frames"]
+    h = dh.dh_create()
+    dh.configure(h, s)
+    try:
+        fa, ca = _alone(dh, torch, h, s, fr)
+        srv = dh.dh_server_create(48 << 20, 2)
+        try:
+            hin = torch.from_numpy(fr).pin_memory()
+            f = torch.empty(fa.shape, dtype=torch.complex64).pin_memory()
+            c = torch.empty(ca.shape, dtype=torch.complex64).pin_memory()
+            t = dh.dh_server_submit(srv, h, hin, dh.DH_DTYPE_U16, 10, f, c)
+            dh.dh_server_wait(srv, t, -1)
+            st = dh.dh_server_stats(srv)
+        finally:
+            dh.dh_server_destroy(srv)
+        assert st["peak_bytes"] <= st["budget_bytes"] == 48 << 20
+        assert np.array_equal(f.numpy().view(np.uint32), fa.view(np.uint32))
+        assert np.array_equal(c.numpy().view(np.uint32), ca.view(np.uint32))
+    finally:
+        dh.dh_destroy(h)
+
+
+def test_budget_errors_and_timeouts():
+    import torch
+    import paper_2204_02348_gb300 as dh
+    s = syn.serving_geometry("1024x1024_1pol", np.random.default_rng(95))
+    h = dh.dh_create()
+    dh.configure(h, s)
+    fr = torch.from_numpy(syn.make_frames(s, 1, seed=96)["frames"]).pin_memory()
+    try:
+        srv0 = dh.dh_server_create(0, 1)
+        try:
+            with pytest.raises(dh.DigHoloError) as ei:
+                dh.dh_server_submit(srv0, h, fr, dh.DH_DTYPE_U16, 1)
+            assert ei.value.code == dh.DH_ERROR_MEMORYALLOCATION
+            with pytest.raises(dh.DigHoloError) as ei:
+                dh.dh_server_wait(srv0, 12345, 0)
+            assert ei.value.code == dh.DH_ERROR_INVALIDARGUMENT
+        finally:
+            dh.dh_server_destroy(srv0)
+        big = torch.from_numpy(np.repeat(fr.numpy(), 48, axis=0)).pin_memory()
+        srv = dh.dh_server_create(1 << 30, 1)
+        try:
+            t = dh.dh_server_submit(srv, h, big, dh.DH_DTYPE_U16, 48)
+            with pytest.raises(dh.DigHoloError) as ei:
+                dh.dh_server_wait(srv, t, 0)
+            assert ei.value.code == dh.DH_ERROR_TIMEOUT
+            dh.dh_server_wait(srv, t, -1)
+        finally:
+            dh.dh_server_destroy(srv)
+    finally:
+        dh.dh_destroy(h)
