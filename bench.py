@@ -47,6 +47,8 @@ def parse_args():
     ap.add_argument("--precision", choices=["fp32", "split_bf16"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--frames", type=int, default=FRAMES, help="frames per step and GPU (default: the workload's 1000)")
+    ap.add_argument("--workload", choices=["batching", "serving"], default="batching")
+    ap.add_argument("--requests", type=int, default=120, help="requests per serving run")
     return ap.parse_args()
 
 
@@ -58,6 +60,27 @@ def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return ws, rank, local
+
+
+def max_over_ranks(value_ms, ws, device=None):
+    """Largest per-rank value (the job's wall time); a plain float when there is one rank."""
+    if ws <= 1:
+        return float(value_ms)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value_ms)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(ws, frames_per_rank, steps, max_ms):
+    """Frames per second of the whole job: every rank processed frames_per_rank frames per step."""
+    return ws * frames_per_rank * steps / (max_ms / 1e3)
+
+
+def rank_seed(base, rank):
+    """Each rank draws its own frames (weak scaling over disjoint synthetic shards)."""
+    return base + 1000 * rank
 
 
 def bytes_per_frame(setup, m, modes):
@@ -247,7 +270,7 @@ def run_ours(args, ws, rank, local):
     setup = syn.setup_batching()
     prec = dh.DH_PRECISION_SPLIT_BF16 if args.precision == "split_bf16" else dh.DH_PRECISION_FP32
     frames_n = args.frames
-    data = syn.make_frames(setup, frames_n, seed=syn.BASE_SEED + 1000 * rank)
+    data = syn.make_frames(setup, frames_n, seed=rank_seed(syn.BASE_SEED, rank))
     host = torch.from_numpy(data["frames"]).pin_memory()
     inputs = [host.to(dev) for _ in range(ROTATE)]
     h = dh.dh_create()
@@ -289,13 +312,8 @@ def run_ours(args, ws, rank, local):
     prof = dh.dh_get_profile(h)
     dh.dh_set_profiling(h, False)
     per_step = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
-    total_ms = evs[0].elapsed_time(evs[-1])
-    t = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-    if ws > 1:
-        import torch.distributed as dist
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
-    value = ws * frames_n * args.steps / (total_ms / 1e3)
+    total_ms = max_over_ranks(evs[0].elapsed_time(evs[-1]), ws, dev)
+    value = whole_job_rate(ws, frames_n, args.steps, total_ms)
 
     # ---- dominant kernel roofline
     peak, peak_src = measured_peak()
@@ -338,11 +356,8 @@ def run_ours(args, ws, rank, local):
         e2e_step()
     e1.record(stream)
     torch.cuda.synchronize()
-    et = torch.tensor([e0.elapsed_time(e1)], dtype=torch.float64, device=dev)
-    if ws > 1:
-        import torch.distributed as dist
-        dist.all_reduce(et, op=dist.ReduceOp.MAX)
-    e2e = {"value": ws * frames_n * e2e_steps / (float(et.item()) / 1e3), "unit": "frames/s",
+    e_ms = max_over_ranks(e0.elapsed_time(e1), ws, dev)
+    e2e = {"value": whole_job_rate(ws, frames_n, e2e_steps, e_ms), "unit": "frames/s",
            "h2d_bytes_per_step": int(host.numel() * 2),
            "d2h_bytes_per_step": int(host_f.numel() * 8 + host_c.numel() * 8), "steps": e2e_steps}
 
@@ -385,11 +400,105 @@ def run_ours(args, ws, rank, local):
         dist.destroy_process_group()
 
 
+SERVING_METRIC = "serving frames/s with p50/p99 request latency (mixed geometries, continuous batching) on 1 GB300"
+
+
+def run_serving(args, ws, rank, local):
+    """Mixed-geometry request stream through the serving loop: requests of U{1..256} frames over three
+    geometries (256x256/1 pol, 512x512 with two 256x256 windows, 1024x1024/1 pol), window radius
+    U(0.15, 0.32) w_max, G in {6..16}, coefficients returned to host.  A saturation run (all requests at
+    once) measures the service rate; Poisson arrivals at 0.5 and 0.9 of it measure latency.  Runs with the
+    FP32 and the split-BF16 overlap."""
+    import numpy as np
+    import torch
+
+    import paper_2204_02348_gb300 as dh
+    from synth import holograms as syn
+
+    torch.cuda.set_device(local)
+    rng = np.random.default_rng(syn.BASE_SEED + 3)
+    kinds = list(syn.SERVING_KINDS)
+    pools, geos = {}, {}
+    for ki, kind in enumerate(kinds):
+        gl = [syn.serving_geometry(kind, rng) for _ in range(8)]          # device-resident plans per kind
+        geos[kind] = gl
+        base = syn.make_frames(gl[0], 4, seed=syn.BASE_SEED + 50 + ki)["frames"]
+        pools[kind] = torch.from_numpy(np.ascontiguousarray(np.resize(base, (256,) + base.shape[1:]))).pin_memory()
+    plan_req = []
+    for _ in range(args.requests):
+        kind = kinds[int(rng.integers(0, 3))]
+        plan_req.append((kind, int(rng.integers(0, 8)), int(rng.integers(1, 257))))
+    total_frames = sum(n for _, _, n in plan_req)
+    out = {}
+    for prec_name, prec in (("fp32", dh.DH_PRECISION_FP32), ("split_bf16", dh.DH_PRECISION_SPLIT_BF16)):
+        handles = {}
+        outs = []
+        for kind in kinds:
+            for gi, g in enumerate(geos[kind]):
+                h = dh.dh_create()
+                dh.configure(h, g)
+                dh.dh_set_precision(h, prec)
+                handles[(kind, gi)] = h
+        for kind, gi, n in plan_req:
+            m, modes, _ = dh.dh_get_output_dims(handles[(kind, gi)])
+            outs.append(torch.empty((n, geos[kind][gi].pol_count, modes), dtype=torch.complex64).pin_memory())
+
+        def run(load, arr_rng):
+            srv = dh.dh_server_create(8 << 30, 8)
+            try:
+                # upload every plan and warm the kernels outside the clock
+                for (kind, gi), h in handles.items():
+                    m, modes, _ = dh.dh_get_output_dims(h)
+                    tmp = torch.empty((1, geos[kind][gi].pol_count, modes), dtype=torch.complex64).pin_memory()
+                    dh.dh_server_wait(srv, dh.dh_server_submit(srv, h, pools[kind], dh.DH_DTYPE_U16, 1, None, tmp), -1)
+                srv2 = srv
+                tickets = []
+                mean_gap = None if load is None else (total_frames / len(plan_req)) / (load * out[prec_name]["saturated"])
+                t0 = time.perf_counter()
+                next_t = t0
+                for (kind, gi, n), o in zip(plan_req, outs):
+                    if mean_gap is not None:
+                        next_t += float(arr_rng.exponential(mean_gap))
+                        while time.perf_counter() < next_t:
+                            pass
+                    tickets.append(dh.dh_server_submit(srv2, handles[(kind, gi)], pools[kind], dh.DH_DTYPE_U16, n, None, o))
+                for t in tickets:
+                    dh.dh_server_wait(srv2, t, -1)
+                wall = time.perf_counter() - t0
+                st = dh.dh_server_stats(srv2)
+            finally:
+                dh.dh_server_destroy(srv)
+            return {"frames_per_s": total_frames / wall, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
+                    "max_ms": st["max_ms"], "peak_inflight": st["peak_inflight"], "peak_bytes": st["peak_bytes"]}
+
+        sat = run(None, None)
+        out[prec_name] = {"saturated": sat["frames_per_s"], "saturation_run": sat}
+        for load in (0.5, 0.9):
+            out[prec_name][f"load_{load}"] = run(load, np.random.default_rng(7))
+        for h in handles.values():
+            dh.dh_destroy(h)
+    if rank == 0:
+        line = {
+            "metric": SERVING_METRIC, "value": out["split_bf16"]["saturated"], "unit": "frames/s", "n_gpus": ws,
+            "steps": 1, "warmup": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32 FFT, split-bf16 overlap", "data": "synthetic",
+            "config": {"workload": "serving: %d requests of U{1..256} frames over 256x256/1pol, 512x512/2pol, "
+                                   "1024x1024/1pol; radius U(0.15,0.32) w_max; G 6..16; 8 GiB budget; 8 streams" %
+                                   args.requests, "frames": total_frames,
+                       "frame_content": "per-kind pools of seeded synthetic frames, tiled; per-request geometry from "
+                                        "8 resident plans per kind", "outputs": "coefficients to pinned host memory"},
+            "serving": out,
+        }
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse_args()
     ws, rank, local = dist_env()
     if args.impl == "reference":
         run_reference(args, ws, rank)
+    elif args.workload == "serving":
+        run_serving(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
 
