@@ -44,7 +44,12 @@ struct FusedLayout {
     static constexpr int ZT = kFN * kFCY;
     static constexpr int WB = M * PITCH;
     static constexpr int UN = ZT > WB ? ZT : WB;
-    static constexpr size_t bytes = (size_t)(R1 + UN + kFN + M) * sizeof(float2) + (size_t)M * sizeof(int);
+    // float2 region: r1, union, twiddles N and M, phase x / y, correction x / y
+    static constexpr int F2 = R1 + UN + kFN + M + 4 * M;
+    // float region: hg_x, hg_y [kFGMax][M]; int region: posM, mask lo / hi, mode m / n
+    static constexpr int FL = 2 * kFGMax * M;
+    static constexpr int IN = 3 * M + 2 * (kFGMax * (kFGMax + 1) / 2);
+    static constexpr size_t bytes = (size_t)F2 * sizeof(float2) + (size_t)FL * sizeof(float) + (size_t)IN * sizeof(int);
 };
 
 __device__ __forceinline__ float2 load_pair(const uint16_t* p, bool vec) {
@@ -59,6 +64,27 @@ __device__ __forceinline__ float2 load_pair(const float* p, bool vec) {
     if (vec) return __ldg(reinterpret_cast<const float2*>(p));
     return make_float2(__ldg(p), __ldg(p + 1));
 }
+
+// Raw pixel pair held between its load and its use: two uint16 in one word, or two floats.
+template <typename T>
+struct RawPair;
+template <>
+struct RawPair<uint16_t> {
+    using type = uint32_t;
+    static __device__ __forceinline__ uint32_t load(const uint16_t* p, bool vec) {
+        if (vec) return __ldg(reinterpret_cast<const unsigned int*>(p));
+        return (uint32_t)__ldg(p) | ((uint32_t)__ldg(p + 1) << 16);
+    }
+    static __device__ __forceinline__ float2 value(uint32_t u) {
+        return make_float2((float)(u & 0xffffu), (float)(u >> 16));
+    }
+};
+template <>
+struct RawPair<float> {
+    using type = float2;
+    static __device__ __forceinline__ float2 load(const float* p, bool vec) { return load_pair(p, vec); }
+    static __device__ __forceinline__ float2 value(float2 v) { return v; }
+};
 
 // Write the separated spectra of columns x and x+1 at frequency k (if k is a box row).
 __device__ __forceinline__ void emit_pair(float2* r1, int pitch, int M, int kly, int x, int k, float2 zk, float2 zm) {
@@ -80,31 +106,69 @@ __global__ void __launch_bounds__(kFThreads, 2) k_fused128(const __grid_constant
     float2* un = r1 + L::R1;
     float2* twN = un + L::UN;
     float2* twM = twN + N;
-    int* posM = reinterpret_cast<int*>(twM + M);
+    float2* phx = twM + M;
+    float2* phy = phx + M;
+    float2* cx = phy + M;
+    float2* cy = cx + M;
+    float* hgx = reinterpret_cast<float*>(cy + M);
+    float* hgy = hgx + kFGMax * M;
+    int* posM = reinterpret_cast<int*>(hgy + kFGMax * M);
+    int* mlo = posM + M;
+    int* mhi = mlo + M;
+    int* mdm = mhi + M;
+    int* mdn = mdm + kFGMax * (kFGMax + 1) / 2;
     const int tid = threadIdx.x;
+    // every block serves one polarisation: its tables are staged once
+    const int pol = blockIdx.x % P.pols;
+    const PolDev& pd = P.pol[pol];
+    const int G = P.groups, modes = P.modes;
     for (int i = tid; i < N; i += NT) twN[i] = P.tw_fwd_n[i];
     for (int i = tid; i < M; i += NT) {
         twM[i] = P.tw_inv_m[i];
         posM[i] = P.pos_m[i];
+        phx[i] = pd.phase_x[i];
+        phy[i] = pd.phase_y[i];
+        cx[i] = pd.corr_x[i];
+        cy[i] = pd.corr_y[i];
+        mlo[i] = pd.mask_lo[i];
+        mhi[i] = pd.mask_hi[i];
+    }
+    for (int i = tid; i < G * M; i += NT) {
+        hgx[i] = pd.hg_x[i];
+        hgy[i] = pd.hg_y[i];
+    }
+    for (int i = tid; i < modes; i += NT) {
+        mdm[i] = P.mode_m[i];
+        mdn[i] = P.mode_n[i];
     }
     __syncthreads();
-    const int G = P.groups, modes = P.modes;
-    const int total = A.count * P.pols;
     const bool vec = A.vec_ok != 0;
-    for (int w = blockIdx.x; w < total; w += gridDim.x) {
-        const int b = w / P.pols, pol = w - b * P.pols;
+    const int fstride = gridDim.x / P.pols;
+    for (int b = blockIdx.x / P.pols; b < A.count; b += fstride) {
         const int f = A.frame0 + b;
-        const PolDev& pd = P.pol[pol];
         const T* fr = static_cast<const T*>(A.src) + (size_t)f * P.width * P.height + (size_t)pd.oy * P.width + pd.ox;
 
         // ---------------------------------------------------------------- y pass, two chunks of 32 column pairs
+        // (the second chunk's pixel pairs are loaded before the first chunk is transformed)
+        using RP = RawPair<T>;
+        typename RP::type pre[16];
+        {
+            const int c = tid & 31, j = tid >> 5;
+#pragma unroll
+            for (int r = 0; r < 16; ++r) pre[r] = RP::load(fr + (size_t)(j + 8 * r) * P.width + 2 * c, vec);
+        }
+#pragma unroll
         for (int cc = 0; cc < 2; ++cc) {
             {
                 const int c = tid & 31, j = tid >> 5;
-                const int x = 2 * (c + kFCY * cc);
                 float2 v[16];
 #pragma unroll
-                for (int r = 0; r < 16; ++r) v[r] = load_pair(fr + (size_t)(j + 8 * r) * P.width + x, vec);
+                for (int r = 0; r < 16; ++r) v[r] = RP::value(pre[r]);
+                if (cc == 0) {
+#pragma unroll
+                    for (int r = 0; r < 16; ++r)
+                        pre[r] = RP::load(fr + (size_t)(j + 8 * r) * P.width + 2 * (c + kFCY), vec);
+                }
                 dft16<false>(v);
 #pragma unroll
                 for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], twN[j * r]);
@@ -150,15 +214,14 @@ __global__ void __launch_bounds__(kFThreads, 2) k_fused128(const __grid_constant
 #pragma unroll
             for (int r = 0; r < 8; ++r) v[r] = r1[(8 * d + r) * PITCH + q];
             dft8<false>(v);
-            const int lo = __ldg(&pd.mask_lo[q]), hi = __ldg(&pd.mask_hi[q]);
-            const float2 phy = __ldg(&pd.phase_y[q]);
+            const int lo = mlo[q], hi = mhi[q];
+            const float2 py = phy[q];
 #pragma unroll
             for (int r = 0; r < 8; ++r) {
-                int p = (d + 16 * r - pd.klx) % N;
-                if (p < 0) p += N;
+                const int p = (d + 16 * r - pd.klx) & (N - 1);
                 if (p < M) {
                     float2 val = make_float2(0.f, 0.f);
-                    if (p >= lo && p <= hi) val = cmul(cmul(v[r], __ldg(&pd.phase_x[p])), phy);
+                    if (p >= lo && p <= hi) val = cmul(cmul(v[r], phx[p]), py);
                     un[posM[p] * PITCH + q] = val;
                 }
             }
@@ -180,7 +243,7 @@ __global__ void __launch_bounds__(kFThreads, 2) k_fused128(const __grid_constant
         for (int t = tid; t < M * M; t += NT) {
             const int i = t % M, j = t / M;
             const int a = i * PITCH + posM[j];
-            const float2 e = cmul(cmul(un[a], __ldg(&pd.corr_x[i])), __ldg(&pd.corr_y[j]));
+            const float2 e = cmul(cmul(un[a], cx[i]), cy[j]);
             un[a] = e;
             if (fld) fld[t] = e;
         }
@@ -191,20 +254,25 @@ __global__ void __launch_bounds__(kFThreads, 2) k_fused128(const __grid_constant
             constexpr int JQ = NT / M;                 // thread groups splitting the y sum
             constexpr int JL = (M + JQ - 1) / JQ;
             float2* part = r1;                         // [JQ][G][M]
+            float2* tsum = r1 + JQ * kFGMax * M;       // [G][M]
             if (tid < JQ * M) {
                 const int i = tid % M, jq = tid / M;
                 const int j0 = jq * JL, j1 = min(M, j0 + JL);
                 float2 acc[kFGMax];
 #pragma unroll
                 for (int n = 0; n < kFGMax; ++n) acc[n] = make_float2(0.f, 0.f);
-                for (int j = j0; j < j1; ++j) {
-                    const float2 e = un[i * PITCH + posM[j]];
 #pragma unroll
-                    for (int n = 0; n < kFGMax; ++n) {
-                        if (n < G) {
-                            const float u = __ldg(&pd.hg_y[n * M + j]);
-                            acc[n].x = fmaf(u, e.x, acc[n].x);
-                            acc[n].y = fmaf(u, e.y, acc[n].y);
+                for (int jj = 0; jj < JL; ++jj) {
+                    const int j = j0 + jj;
+                    if (j < j1) {
+                        const float2 e = un[i * PITCH + posM[j]];
+#pragma unroll
+                        for (int n = 0; n < kFGMax; ++n) {
+                            if (n < G) {
+                                const float u = hgy[n * M + j];
+                                acc[n].x = fmaf(u, e.x, acc[n].x);
+                                acc[n].y = fmaf(u, e.y, acc[n].y);
+                            }
                         }
                     }
                 }
@@ -213,29 +281,57 @@ __global__ void __launch_bounds__(kFThreads, 2) k_fused128(const __grid_constant
                     if (n < G) part[(jq * G + n) * M + i] = acc[n];
             }
             __syncthreads();
+            // T[n][i]: the y partial sums added in a fixed order
+            for (int t = tid; t < G * M; t += NT) {
+                float2 v = part[t];
+#pragma unroll
+                for (int jq = 1; jq < JQ; ++jq) {
+                    const float2 w = part[jq * G * M + t];
+                    v.x += w.x;
+                    v.y += w.y;
+                }
+                tsum[t] = v;
+            }
+            __syncthreads();
+            // c_mn = sum_i u_m(x'_i) T[n][i]: one warp per mode, fixed shuffle tree
             const int warp = tid >> 5, lane = tid & 31;
             float2* cf = A.coefs + (size_t)(f * P.pols + pol) * modes;
-            for (int k = warp; k < modes; k += NT / 32) {
-                const int m = __ldg(&P.mode_m[k]), n = __ldg(&P.mode_n[k]);
-                float2 s = make_float2(0.f, 0.f);
-                for (int i = lane; i < M; i += 32) {
-                    float2 tsum = part[n * M + i];
+            // modes k = warp + 8 (k0 + kk), groups of KW: independent products first, then interleaved
+            // shuffle trees
+            constexpr int KW = 4;
+            for (int k0 = 0; warp + k0 * (NT / 32) < modes; k0 += KW) {
+            float2 s[KW];
 #pragma unroll
-                    for (int jq = 1; jq < JQ; ++jq) {
-                        const float2 v = part[(jq * G + n) * M + i];
-                        tsum.x += v.x;
-                        tsum.y += v.y;
+            for (int kk = 0; kk < KW; ++kk) {
+                s[kk] = make_float2(0.f, 0.f);
+                const int k = warp + (k0 + kk) * (NT / 32);
+                if (k < modes) {
+                    const float* um = hgx + mdm[k] * M;
+                    const float2* tn = tsum + mdn[k] * M;
+#pragma unroll
+                    for (int i = lane; i < M; i += 32) {
+                        const float u = um[i];
+                        const float2 t = tn[i];
+                        s[kk].x = fmaf(u, t.x, s[kk].x);
+                        s[kk].y = fmaf(u, t.y, s[kk].y);
                     }
-                    const float u = __ldg(&pd.hg_x[m * M + i]);
-                    s.x = fmaf(u, tsum.x, s.x);
-                    s.y = fmaf(u, tsum.y, s.y);
                 }
+            }
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-                    s.x += __shfl_xor_sync(0xffffffffu, s.x, o);
-                    s.y += __shfl_xor_sync(0xffffffffu, s.y, o);
+            for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+                for (int kk = 0; kk < KW; ++kk) {
+                    s[kk].x += __shfl_xor_sync(0xffffffffu, s[kk].x, o);
+                    s[kk].y += __shfl_xor_sync(0xffffffffu, s[kk].y, o);
                 }
-                if (lane == 0) cf[k] = s;
+            }
+            if (lane == 0) {
+#pragma unroll
+                for (int kk = 0; kk < KW; ++kk) {
+                    const int k = warp + (k0 + kk) * (NT / 32);
+                    if (k < modes) cf[k] = s[kk];
+                }
+            }
             }
         }
         __syncthreads();
@@ -299,8 +395,9 @@ int launch_fused_path(Handle* H, const void* frames, int dtype, int batch, void*
     A.vec_ok = ok ? 1 : 0;
     A.fields = (float2*)fields;
     A.coefs = (float2*)coefs;
-    const long long windows = (long long)batch * P.pols;
-    const int grid = (int)std::min<long long>(windows, 2LL * g_sm_count[dev]);
+    // blocks serve one polarisation each: the grid is a multiple of the polarisation count
+    const long long per_pol = std::min<long long>(batch, (2LL * g_sm_count[dev]) / P.pols);
+    const int grid = (int)std::max<long long>(1, per_pol) * P.pols;
     if (tm) tm->start(st);
     switch (P.m) {
         case 32: dhk::launch<32, 8, 4>(P, A, dtype, grid, st); break;
