@@ -41,7 +41,7 @@ FALLBACK_HBM_GBS = 6800.0
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp32", "split_bf16"], default="fp32")
@@ -297,16 +297,20 @@ def run_ours(args, ws, rank, local):
     # ---- timed region: K steps, event per step, per-kernel events inside the library
     sampler = ClockSampler(local)
     dh.dh_set_profiling(h, True)
+    sampler.start()
+    time.sleep(0.5)                 # let the sampler start before the clock runs
+    import gc
+    gc.collect()
+    gc.disable()
     barrier()
     torch.cuda.synchronize()
-    sampler.start()
-    time.sleep(0.1)
     evs = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     evs[0].record(stream)
     for k in range(args.steps):
         step(k)
         evs[k + 1].record(stream)
     torch.cuda.synchronize()
+    gc.enable()
     barrier()
     clocks = sampler.stop()
     prof = dh.dh_get_profile(h)

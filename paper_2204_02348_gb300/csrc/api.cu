@@ -93,6 +93,8 @@ int upload_plan(const Settings& s, const Geometry& g, const Tables& t, void** ou
     const size_t o_pm = b.put(pm.data(), pm.size() * 4);
     const size_t o_mm = b.put(t.mode_m.data(), t.mode_m.size() * 4);
     const size_t o_mn = b.put(t.mode_n.data(), t.mode_n.size() * 4);
+    const int zero_status[4] = {0, 0, 0, 0};
+    const size_t o_st = b.put(zero_status, sizeof zero_status);
     size_t o_pol[DH_MAX_POLS][9] = {};
     for (int p = 0; p < g.pols; ++p) {
         const PolTables& pt = t.pol[p];
@@ -136,6 +138,7 @@ int upload_plan(const Settings& s, const Geometry& g, const Tables& t, void** ou
     P.pos_m = (const int*)(base + o_pm);
     P.mode_m = (const int*)(base + o_mm);
     P.mode_n = (const int*)(base + o_mn);
+    P.status = (int*)(base + o_st);
     for (int p = 0; p < g.pols; ++p) {
         dhk::PolDev& pd = P.pol[p];
         pd.ox = g.pol[p].ax[0].origin;
@@ -286,7 +289,8 @@ int process(Handle* H, const void* frames, int dtype, int batch, void* window, v
     if (rc) return rc;
     const dhk::Plan& P = H->plan;
     if (P.modes == 0) coefs = nullptr;
-    if (use_fused(P) && !window) return launch_fused_path(H, frames, dtype, batch, fields, coefs, st, H->timer());
+    if (use_fused(P) && !window && fused_frames_ok(P, frames, dtype))
+        return launch_fused_path(H, frames, dtype, batch, fields, coefs, st, H->timer());
     const size_t per_frame = split_window_bytes(P) * P.pols;
     int chunk = (int)std::max<size_t>(1, kScratchTarget / per_frame);
     chunk = std::min(chunk, batch);
@@ -299,7 +303,8 @@ int process_with(Handle* H, const void* frames, int dtype, int batch, void* fiel
                  size_t scratch_bytes, cudaStream_t st) {
     const dhk::Plan& P = H->plan;
     if (P.modes == 0) coefs = nullptr;
-    if (use_fused(P)) return launch_fused_path(H, frames, dtype, batch, fields, coefs, st, nullptr);
+    if (use_fused(P) && fused_frames_ok(P, frames, dtype))
+        return launch_fused_path(H, frames, dtype, batch, fields, coefs, st, nullptr);
     return run_split(P, scratch, scratch_bytes, frames, dtype, batch, nullptr, fields, coefs, st, nullptr);
 }
 

@@ -14,10 +14,13 @@
 //            fixed shuffle tree (deterministic, no atomics).
 // Shared memory: r1[N][M+1] box rows (x-major, padded pitch) and one union region used in turn as the y-pass
 // tile, the M x (M+1) window / field, and the overlap partials; twiddles and the digit-reversal table.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <algorithm>
+#include <string>
 
 #include "fft.cuh"
 #include "runtime.hpp"
@@ -25,71 +28,85 @@
 namespace dhk {
 
 constexpr int kFN = 128;          // window size of this path
-constexpr int kFThreads = 256;
-constexpr int kFCY = 32;          // column pairs per y-pass chunk
+constexpr int kFThreads = 512;
 constexpr int kFGMax = 16;        // largest group count of this path
+constexpr int kFRows = 128;       // staged window rows
+constexpr long kFWaitLimit = 1L << 24;
 
 struct FusedArgs {
     const void* src;              // frames [B][H][W]
     int frame0, count;
-    int vec_ok;                   // 1 when pixel pairs can be loaded as one aligned vector
+    int xo[DH_MAX_POLS];          // window origin minus the 16-byte-aligned staging origin, per polarisation
+    int x0[DH_MAX_POLS];          // staging origin (16-byte aligned element index), per polarisation
     float2* fields;               // nullable [B][pol][M][M]
     float2* coefs;                // nullable [B][pol][modes]
 };
 
-template <int M>
+template <typename T>
+struct Staging {
+    static constexpr int ALIGN = 16 / (int)sizeof(T);     // elements per 16 bytes
+    static constexpr int W = kFN + ALIGN;                  // staged row width (window plus alignment slack)
+    static constexpr int BYTES = kFRows * W * (int)sizeof(T);
+};
+
+template <int M, typename T>
 struct FusedLayout {
     static constexpr int PITCH = M + 1;
     static constexpr int R1 = kFN * PITCH;
-    static constexpr int ZT = kFN * kFCY;
+    static constexpr int YT = kFN * (kFN / 2);                 // y tile: 128 rows x 64 column pairs
     static constexpr int WB = M * PITCH;
-    static constexpr int UN = ZT > WB ? ZT : WB;
-    // float2 region: r1, union, twiddles N and M, phase x / y, correction x / y
+    static constexpr int UN = YT > WB + kFGMax * M ? YT : WB + kFGMax * M;
     static constexpr int F2 = R1 + UN + kFN + M + 4 * M;
-    // float region: hg_x, hg_y [kFGMax][M]; int region: posM, mask lo / hi, mode m / n
     static constexpr int FL = 2 * kFGMax * M;
     static constexpr int IN = 3 * M + 2 * (kFGMax * (kFGMax + 1) / 2);
-    static constexpr size_t bytes = (size_t)F2 * sizeof(float2) + (size_t)FL * sizeof(float) + (size_t)IN * sizeof(int);
+    static constexpr size_t STG = (size_t)Staging<T>::BYTES;   // first, 1024-byte aligned
+    static constexpr size_t bytes = STG + (size_t)F2 * sizeof(float2) + (size_t)FL * sizeof(float) + (size_t)IN * sizeof(int);
+    static constexpr int JQ0 = (kFThreads / M) < (R1 / (kFGMax * M)) ? (kFThreads / M) : (R1 / (kFGMax * M));
 };
 
-__device__ __forceinline__ float2 load_pair(const uint16_t* p, bool vec) {
-    if (vec) {
-        const uint32_t u = __ldg(reinterpret_cast<const unsigned int*>(p));
-        return make_float2((float)(u & 0xffffu), (float)(u >> 16));
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
+    uint32_t done = 0;
+    for (long it = 0; it < kFWaitLimit && !done; ++it) {
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(mbar), "r"(parity)
+            : "memory");
     }
-    return make_float2((float)__ldg(p), (float)__ldg(p + 1));
+    return done != 0;
 }
 
-__device__ __forceinline__ float2 load_pair(const float* p, bool vec) {
-    if (vec) return __ldg(reinterpret_cast<const float2*>(p));
-    return make_float2(__ldg(p), __ldg(p + 1));
+// One thread: expect the window's bytes on the mbarrier and start the tensor copy of frame f.
+__device__ __forceinline__ void stage_window(const CUtensorMap* tmap, uint32_t dst, uint32_t mbar, int x0, int y0, int f,
+                                             int bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar), "r"(bytes) : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x0), "r"(y0), "r"(f), "r"(mbar)
+        : "memory");
 }
 
-// Raw pixel pair held between its load and its use: two uint16 in one word, or two floats.
 template <typename T>
-struct RawPair;
+__device__ __forceinline__ float2 staged_pair(const T* row, int x, bool even);
 template <>
-struct RawPair<uint16_t> {
-    using type = uint32_t;
-    static __device__ __forceinline__ uint32_t load(const uint16_t* p, bool vec) {
-        if (vec) return __ldg(reinterpret_cast<const unsigned int*>(p));
-        return (uint32_t)__ldg(p) | ((uint32_t)__ldg(p + 1) << 16);
-    }
-    static __device__ __forceinline__ float2 value(uint32_t u) {
+__device__ __forceinline__ float2 staged_pair<uint16_t>(const uint16_t* row, int x, bool even) {
+    if (even) {
+        const uint32_t u = *reinterpret_cast<const uint32_t*>(row + x);
         return make_float2((float)(u & 0xffffu), (float)(u >> 16));
     }
-};
+    return make_float2((float)row[x], (float)row[x + 1]);
+}
 template <>
-struct RawPair<float> {
-    using type = float2;
-    static __device__ __forceinline__ float2 load(const float* p, bool vec) { return load_pair(p, vec); }
-    static __device__ __forceinline__ float2 value(float2 v) { return v; }
-};
+__device__ __forceinline__ float2 staged_pair<float>(const float* row, int x, bool even) {
+    if (even) return *reinterpret_cast<const float2*>(row + x);
+    return make_float2(row[x], row[x + 1]);
+}
 
 // Write the separated spectra of columns x and x+1 at frequency k (if k is a box row).
 __device__ __forceinline__ void emit_pair(float2* r1, int pitch, int M, int kly, int x, int k, float2 zk, float2 zm) {
-    int q = (k - kly) % kFN;
-    if (q < 0) q += kFN;
+    const int q = (k - kly) & (kFN - 1);
     if (q < M) {
         r1[x * pitch + q] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
         r1[(x + 1) * pitch + q] = make_float2(0.5f * (zk.y + zm.y), 0.5f * (zm.x - zk.x));
@@ -97,12 +114,16 @@ __device__ __forceinline__ void emit_pair(float2* r1, int pitch, int M, int kly,
 }
 
 template <int M, int MR0, int MR1, typename T>
-__global__ void __launch_bounds__(kFThreads, 2) k_fused128(const __grid_constant__ Plan P,
-                                                           const __grid_constant__ FusedArgs A) {
-    using L = FusedLayout<M>;
+__global__ void __launch_bounds__(kFThreads, 1) k_fused128(const __grid_constant__ Plan P, const __grid_constant__ FusedArgs A,
+                                                           const __grid_constant__ CUtensorMap tmap) {
+    using L = FusedLayout<M, T>;
+    using S = Staging<T>;
     constexpr int N = kFN, PITCH = L::PITCH, NT = kFThreads;
-    extern __shared__ float2 smem[];
-    float2* r1 = smem;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ int abort_flag;
+    T* stg = reinterpret_cast<T*>(smem_raw);
+    float2* r1 = reinterpret_cast<float2*>(smem_raw + L::STG);
     float2* un = r1 + L::R1;
     float2* twN = un + L::UN;
     float2* twM = twN + N;
@@ -141,69 +162,73 @@ __global__ void __launch_bounds__(kFThreads, 2) k_fused128(const __grid_constant
         mdm[i] = P.mode_m[i];
         mdn[i] = P.mode_n[i];
     }
-    __syncthreads();
-    const bool vec = A.vec_ok != 0;
+    const uint32_t mb = smem_u32(&mbar), dst = smem_u32(stg);
     const int fstride = gridDim.x / P.pols;
-    for (int b = blockIdx.x / P.pols; b < A.count; b += fstride) {
+    int b = blockIdx.x / P.pols;
+    if (tid == 0) {
+        abort_flag = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        if (b < A.count) stage_window(&tmap, dst, mb, A.x0[pol], pd.oy, A.frame0 + b, S::BYTES);
+    }
+    __syncthreads();
+    const int xo = A.xo[pol];
+    const bool even = (xo & 1) == 0;
+    uint32_t parity = 0;
+    for (; b < A.count; b += fstride) {
         const int f = A.frame0 + b;
-        const T* fr = static_cast<const T*>(A.src) + (size_t)f * P.width * P.height + (size_t)pd.oy * P.width + pd.ox;
-
-        // ---------------------------------------------------------------- y pass, two chunks of 32 column pairs
-        // (the second chunk's pixel pairs are loaded before the first chunk is transformed)
-        using RP = RawPair<T>;
-        typename RP::type pre[16];
-        {
-            const int c = tid & 31, j = tid >> 5;
-#pragma unroll
-            for (int r = 0; r < 16; ++r) pre[r] = RP::load(fr + (size_t)(j + 8 * r) * P.width + 2 * c, vec);
+        const bool ok = mbar_wait(mb, parity);
+        parity ^= 1u;
+        if (!ok) abort_flag = 1;
+        __syncthreads();
+        if (abort_flag) {
+            if (tid == 0 && P.status) atomicOr(P.status, 1);
+            break;
         }
+
+        // ---------------------------------------------------------------- y pass on 64 column pairs
+        {
+            const int c = tid & 63, j = tid >> 6;
+            float2 v[16];
 #pragma unroll
-        for (int cc = 0; cc < 2; ++cc) {
-            {
-                const int c = tid & 31, j = tid >> 5;
-                float2 v[16];
+            for (int r = 0; r < 16; ++r) v[r] = staged_pair<T>(stg + (j + 8 * r) * S::W, xo + 2 * c, even);
+            dft16<false>(v);
 #pragma unroll
-                for (int r = 0; r < 16; ++r) v[r] = RP::value(pre[r]);
-                if (cc == 0) {
+            for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], twN[j * r]);
 #pragma unroll
-                    for (int r = 0; r < 16; ++r)
-                        pre[r] = RP::load(fr + (size_t)(j + 8 * r) * P.width + 2 * (c + kFCY), vec);
-                }
-                dft16<false>(v);
+            for (int r = 0; r < 16; ++r) un[(j + 8 * r) * 64 + c] = v[r];
+        }
+        // the staged window has been read: order those reads before the next tensor copy into the buffer
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        __syncthreads();
+        if (tid == 0 && b + fstride < A.count) stage_window(&tmap, dst, mb, A.x0[pol], pd.oy, f + fstride, S::BYTES);
+        {
+            const int c = tid & 63, u = tid >> 6;
+            const int d1 = u, d2 = (u == 0) ? 8 : 16 - u;
+            float2 z1[8], z2[8];
 #pragma unroll
-                for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], twN[j * r]);
-#pragma unroll
-                for (int r = 0; r < 16; ++r) un[(j + 8 * r) * kFCY + c] = v[r];
+            for (int r = 0; r < 8; ++r) {
+                z1[r] = un[(8 * d1 + r) * 64 + c];
+                z2[r] = un[(8 * d2 + r) * 64 + c];
             }
-            __syncthreads();
-            {
-                const int c = tid & 31, u = tid >> 5;
-                const int d1 = u, d2 = (u == 0) ? 8 : 16 - u;
-                float2 z1[8], z2[8];
+            dft8<false>(z1);
+            dft8<false>(z2);
+            const int x = 2 * c;
+            if (u != 0) {
 #pragma unroll
                 for (int r = 0; r < 8; ++r) {
-                    z1[r] = un[(8 * d1 + r) * kFCY + c];
-                    z2[r] = un[(8 * d2 + r) * kFCY + c];
+                    emit_pair(r1, PITCH, M, pd.kly, x, d1 + 16 * r, z1[r], z2[7 - r]);
+                    emit_pair(r1, PITCH, M, pd.kly, x, d2 + 16 * r, z2[r], z1[7 - r]);
                 }
-                dft8<false>(z1);
-                dft8<false>(z2);
-                const int x = 2 * (c + kFCY * cc);
-                if (u != 0) {
+            } else {
 #pragma unroll
-                    for (int r = 0; r < 8; ++r) {
-                        emit_pair(r1, PITCH, M, pd.kly, x, d1 + 16 * r, z1[r], z2[7 - r]);
-                        emit_pair(r1, PITCH, M, pd.kly, x, d2 + 16 * r, z2[r], z1[7 - r]);
-                    }
-                } else {
-#pragma unroll
-                    for (int r = 0; r < 8; ++r) {
-                        emit_pair(r1, PITCH, M, pd.kly, x, 16 * r, z1[r], z1[(8 - r) & 7]);
-                        emit_pair(r1, PITCH, M, pd.kly, x, 8 + 16 * r, z2[r], z2[7 - r]);
-                    }
+                for (int r = 0; r < 8; ++r) {
+                    emit_pair(r1, PITCH, M, pd.kly, x, 16 * r, z1[r], z1[(8 - r) & 7]);
+                    emit_pair(r1, PITCH, M, pd.kly, x, 8 + 16 * r, z2[r], z2[7 - r]);
                 }
             }
-            __syncthreads();
         }
+        __syncthreads();
 
         // ---------------------------------------------------------------- x pass on the M box rows
         spass<16, false, false, N, N, M, PITCH, 1, NT>(r1, twN, tid);
@@ -251,10 +276,10 @@ __global__ void __launch_bounds__(kFThreads, 2) k_fused128(const __grid_constant
 
         // ---------------------------------------------------------------- HG overlap
         if (A.coefs && G > 0) {
-            constexpr int JQ = NT / M;                 // thread groups splitting the y sum
+            constexpr int JQ = L::JQ0;                 // thread groups splitting the y sum
             constexpr int JL = (M + JQ - 1) / JQ;
             float2* part = r1;                         // [JQ][G][M]
-            float2* tsum = r1 + JQ * kFGMax * M;       // [G][M]
+            float2* tsum = un + L::WB;                 // [G][M]
             if (tid < JQ * M) {
                 const int i = tid % M, jq = tid / M;
                 const int j0 = jq * JL, j1 = min(M, j0 + JL);
@@ -293,67 +318,68 @@ __global__ void __launch_bounds__(kFThreads, 2) k_fused128(const __grid_constant
                 tsum[t] = v;
             }
             __syncthreads();
-            // c_mn = sum_i u_m(x'_i) T[n][i]: one warp per mode, fixed shuffle tree
+            // c_mn = sum_i u_m(x'_i) T[n][i]: modes spread over the warps in groups of KW; independent
+            // products first, then interleaved shuffle trees (fixed order)
             const int warp = tid >> 5, lane = tid & 31;
+            constexpr int NW = NT / 32, KW = 4;
             float2* cf = A.coefs + (size_t)(f * P.pols + pol) * modes;
-            // modes k = warp + 8 (k0 + kk), groups of KW: independent products first, then interleaved
-            // shuffle trees
-            constexpr int KW = 4;
-            for (int k0 = 0; warp + k0 * (NT / 32) < modes; k0 += KW) {
-            float2 s[KW];
+            for (int k0 = 0; warp + k0 * NW < modes; k0 += KW) {
+                float2 sacc[KW];
 #pragma unroll
-            for (int kk = 0; kk < KW; ++kk) {
-                s[kk] = make_float2(0.f, 0.f);
-                const int k = warp + (k0 + kk) * (NT / 32);
-                if (k < modes) {
-                    const float* um = hgx + mdm[k] * M;
-                    const float2* tn = tsum + mdn[k] * M;
+                for (int kk = 0; kk < KW; ++kk) {
+                    sacc[kk] = make_float2(0.f, 0.f);
+                    const int k = warp + (k0 + kk) * NW;
+                    if (k < modes) {
+                        const float* um = hgx + mdm[k] * M;
+                        const float2* tn = tsum + mdn[k] * M;
 #pragma unroll
-                    for (int i = lane; i < M; i += 32) {
-                        const float u = um[i];
-                        const float2 t = tn[i];
-                        s[kk].x = fmaf(u, t.x, s[kk].x);
-                        s[kk].y = fmaf(u, t.y, s[kk].y);
+                        for (int i = lane; i < M; i += 32) {
+                            const float u = um[i];
+                            const float2 t = tn[i];
+                            sacc[kk].x = fmaf(u, t.x, sacc[kk].x);
+                            sacc[kk].y = fmaf(u, t.y, sacc[kk].y);
+                        }
                     }
                 }
-            }
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) {
+                for (int o = 16; o > 0; o >>= 1) {
 #pragma unroll
-                for (int kk = 0; kk < KW; ++kk) {
-                    s[kk].x += __shfl_xor_sync(0xffffffffu, s[kk].x, o);
-                    s[kk].y += __shfl_xor_sync(0xffffffffu, s[kk].y, o);
+                    for (int kk = 0; kk < KW; ++kk) {
+                        sacc[kk].x += __shfl_xor_sync(0xffffffffu, sacc[kk].x, o);
+                        sacc[kk].y += __shfl_xor_sync(0xffffffffu, sacc[kk].y, o);
+                    }
                 }
-            }
-            if (lane == 0) {
+                if (lane == 0) {
 #pragma unroll
-                for (int kk = 0; kk < KW; ++kk) {
-                    const int k = warp + (k0 + kk) * (NT / 32);
-                    if (k < modes) cf[k] = s[kk];
+                    for (int kk = 0; kk < KW; ++kk) {
+                        const int k = warp + (k0 + kk) * NW;
+                        if (k < modes) cf[k] = sacc[kk];
+                    }
                 }
-            }
             }
         }
         __syncthreads();
     }
+    // a tensor copy still in flight (only after an expired wait) must land before the block exits
+    if (abort_flag && tid == 0) mbar_wait(mb, parity);
 }
 
 template <int M, int MR0, int MR1>
 static cudaError_t set_attr() {
     cudaError_t e;
-    const int bytes = (int)FusedLayout<M>::bytes;
-    if ((e = cudaFuncSetAttribute(k_fused128<M, MR0, MR1, uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes)))
+    if ((e = cudaFuncSetAttribute(k_fused128<M, MR0, MR1, uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)FusedLayout<M, uint16_t>::bytes)))
         return e;
-    return cudaFuncSetAttribute(k_fused128<M, MR0, MR1, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    return cudaFuncSetAttribute(k_fused128<M, MR0, MR1, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)FusedLayout<M, float>::bytes);
 }
 
 template <int M, int MR0, int MR1>
-static void launch(const Plan& P, const FusedArgs& A, int dtype, int grid, cudaStream_t st) {
-    const size_t bytes = FusedLayout<M>::bytes;
+static void launch(const Plan& P, const FusedArgs& A, const CUtensorMap& tm, int dtype, int grid, cudaStream_t st) {
     if (dtype == DH_DTYPE_U16)
-        k_fused128<M, MR0, MR1, uint16_t><<<grid, kFThreads, bytes, st>>>(P, A);
+        k_fused128<M, MR0, MR1, uint16_t><<<grid, kFThreads, FusedLayout<M, uint16_t>::bytes, st>>>(P, A, tm);
     else
-        k_fused128<M, MR0, MR1, float><<<grid, kFThreads, bytes, st>>>(P, A);
+        k_fused128<M, MR0, MR1, float><<<grid, kFThreads, FusedLayout<M, float>::bytes, st>>>(P, A, tm);
 }
 
 }  // namespace dhk
@@ -361,14 +387,28 @@ static void launch(const Plan& P, const FusedArgs& A, int dtype, int grid, cudaS
 namespace dh {
 
 static int g_sm_count[64] = {0};
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
 bool use_fused(const dhk::Plan& P) {
     if (P.n != dhk::kFN || P.groups > dhk::kFGMax || P.precision != DH_PRECISION_FP32) return false;
     return P.m == 32 || P.m == 48 || P.m == 64;
 }
 
+bool fused_frames_ok(const dhk::Plan& P, const void* frames, int dtype) {
+    const int esz = dtype == DH_DTYPE_U16 ? 2 : 4;
+    // tensor-copy rules: 16-byte aligned base and row pitch
+    return ((uintptr_t)frames % 16 == 0) && ((size_t)P.width * esz) % 16 == 0;
+}
+
 cudaError_t fused_init() {
     cudaError_t e;
+    if (!g_encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return e != cudaSuccess ? e : cudaErrorNotSupported;
+        g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
     if ((e = dhk::set_attr<32, 8, 4>())) return e;
     if ((e = dhk::set_attr<48, 16, 3>())) return e;
     return dhk::set_attr<64, 8, 8>();
@@ -385,24 +425,39 @@ int launch_fused_path(Handle* H, const void* frames, int dtype, int batch, void*
         if (e != cudaSuccess) return cuda_fail(e, "device attribute");
         g_sm_count[dev] = n;
     }
+    if (!g_encode) return fail(DH_ERROR_ERROR, "tensor-map encoder unavailable");
+    const int esz = dtype == DH_DTYPE_U16 ? 2 : 4;
+    const int align = 16 / esz;
+    // frames as a 3-D tensor [batch][height][width]; one box = the window rows plus alignment slack
+    CUtensorMap tmap;
+    const cuuint64_t gdim[3] = {(cuuint64_t)P.width, (cuuint64_t)P.height, (cuuint64_t)batch};
+    const cuuint64_t gstride[2] = {(cuuint64_t)P.width * esz, (cuuint64_t)P.width * P.height * esz};
+    const cuuint32_t box[3] = {(cuuint32_t)(dhk::kFN + align), (cuuint32_t)dhk::kFRows, 1};
+    const cuuint32_t estride[3] = {1, 1, 1};
+    CUresult cr = g_encode(&tmap, dtype == DH_DTYPE_U16 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
+                           const_cast<void*>(frames), gdim, gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) return fail(DH_ERROR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)cr) + ")");
     dhk::FusedArgs A;
     A.src = frames;
     A.frame0 = 0;
     A.count = batch;
-    const int esz = dtype == DH_DTYPE_U16 ? 2 : 4;
-    bool ok = (P.width % 2 == 0) && (((uintptr_t)frames) % (2 * esz) == 0);
-    for (int p = 0; p < P.pols; ++p) ok = ok && (P.pol[p].ox % 2 == 0);
-    A.vec_ok = ok ? 1 : 0;
+    for (int p = 0; p < DH_MAX_POLS; ++p) {
+        const int ox = p < P.pols ? P.pol[p].ox : 0;
+        A.x0[p] = (ox / align) * align;          // window origins are >= 0
+        A.xo[p] = ox - A.x0[p];
+    }
     A.fields = (float2*)fields;
     A.coefs = (float2*)coefs;
-    // blocks serve one polarisation each: the grid is a multiple of the polarisation count
-    const long long per_pol = std::min<long long>(batch, (2LL * g_sm_count[dev]) / P.pols);
-    const int grid = (int)std::max<long long>(1, per_pol) * P.pols;
+    // one block per SM; each block serves one polarisation, so the grid is a multiple of the polarisation count
+    const long long per_pol = std::min<long long>(batch, std::max(1, g_sm_count[dev] / P.pols));
+    const int grid = (int)per_pol * P.pols;
     if (tm) tm->start(st);
     switch (P.m) {
-        case 32: dhk::launch<32, 8, 4>(P, A, dtype, grid, st); break;
-        case 48: dhk::launch<48, 16, 3>(P, A, dtype, grid, st); break;
-        default: dhk::launch<64, 8, 8>(P, A, dtype, grid, st); break;
+        case 32: dhk::launch<32, 8, 4>(P, A, tmap, dtype, grid, st); break;
+        case 48: dhk::launch<48, 16, 3>(P, A, tmap, dtype, grid, st); break;
+        default: dhk::launch<64, 8, 8>(P, A, tmap, dtype, grid, st); break;
     }
     if (tm) tm->stop(st, "k_fused128");
     cudaError_t e = cudaGetLastError();

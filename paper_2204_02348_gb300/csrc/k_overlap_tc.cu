@@ -190,6 +190,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_yinv_tc(const __grid_constant
             }
             const bool done = ok && wait_parity(mbar_a, phase);
             phase ^= 1u;
+            if (ok && !done && tid == 0 && P.status) atomicOr(P.status, 2);
             ok = ok && done;
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
             if (warp < 4) {

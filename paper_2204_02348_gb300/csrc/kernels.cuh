@@ -39,6 +39,7 @@ struct Plan {
     const int* pos_m;        // [M] position of index k for the inverse DIT input
     const int* mode_m;       // [modes]
     const int* mode_n;       // [modes]
+    int* status;             // nullable device status word: bit 0 set when a bounded wait expired
     PolDev pol[DH_MAX_POLS];
 };
 

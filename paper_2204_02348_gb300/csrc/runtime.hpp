@@ -67,6 +67,8 @@ int run_split(const dhk::Plan& P, void* scratch, size_t scratch_bytes, const voi
 
 // Fused single-kernel path for small windows (k_fused.cu).
 bool use_fused(const dhk::Plan& P);
+// The fused kernel stages windows with tensor copies: the frames need a 16-byte aligned base and row pitch.
+bool fused_frames_ok(const dhk::Plan& P, const void* frames, int dtype);
 cudaError_t fused_init();
 int launch_fused_path(Handle* H, const void* frames, int dtype, int batch, void* fields, void* coefs,
                       cudaStream_t st, dhk::StageTimer* timer);

@@ -334,7 +334,10 @@ int dh_server_submit(dh_server s, const dh_request* r, uint64_t* ticket) {
     const size_t frame = (size_t)P.width * P.height * esz;
     const size_t field = r->h_fields ? (size_t)P.pols * P.m * P.m * 8 : 0;
     const size_t coef = (r->h_coefs && P.modes) ? (size_t)P.pols * P.modes * 8 : 0;
-    const size_t scratch = use_fused(P) ? 0 : split_window_bytes(P) * P.pols;
+    // the fused path needs no scratch; frames staged in the arena are 256-byte aligned, so only the row pitch
+    // decides whether tensor copies apply
+    const bool fused = use_fused(P) && ((size_t)P.width * esz) % 16 == 0;
+    const size_t scratch = fused ? 0 : split_window_bytes(P) * P.pols;
     const size_t per_frame = frame + field + coef + scratch;
     const size_t cap = std::max(s->budget / 2, per_frame);
     if (align_up(frame) + align_up(field) + align_up(coef) + align_up(scratch) > s->budget) {
