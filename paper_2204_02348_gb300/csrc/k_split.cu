@@ -220,9 +220,14 @@ cudaError_t launch_split(const Plan& P, const Batch& B, cudaStream_t st, StageTi
     if (tm) tm->start(st);
     k_xpass<<<g2, kThreads, sm2, st>>>(P, B, logr, ilog2(N));
     if (tm) tm->stop(st, "k_xpass");
-    // k_yinv: one block per window
+    return launch_last(P, B, st, tm);
+}
+
+cudaError_t launch_last(const Plan& P, const Batch& B, cudaStream_t st, StageTimer* tm) {
+    // k_yinv (or its tensor-core variant): one block per window
+    const int zf = std::min(B.count, 65535);
     dim3 g3(P.pols, zf);
-    const size_t sm3 = (size_t)(M + std::max(P.groups, 1)) * kChunkI * sizeof(float2);
+    const size_t sm3 = (size_t)(P.m + std::max(P.groups, 1)) * kChunkI * sizeof(float2);
     if (tc_supported(P)) {
         if (tm) tm->start(st);
         cudaError_t e = launch_yinv_tc(P, B, st);
@@ -233,6 +238,23 @@ cudaError_t launch_split(const Plan& P, const Batch& B, cudaStream_t st, StageTi
     if (tm) tm->start(st);
     k_yinv<<<g3, kThreads, sm3, st>>>(P, B);
     if (tm) tm->stop(st, "k_yinv");
+    return cudaGetLastError();
+}
+
+cudaError_t launch_ypass(const Plan& P, const Batch& B, cudaStream_t st, StageTimer* tm) {
+    const int N = P.n;
+    const int zf = std::min(B.count, 65535);
+    int logc = (N >= 1024) ? 4 : 5;
+    logc = std::min(logc, ilog2(N / 2));
+    const int C = 1 << logc;
+    dim3 g1((N / 2) / C, P.pols, zf);
+    const size_t sm1 = (size_t)N * C * sizeof(float2);
+    if (tm) tm->start(st);
+    if (B.dtype == DH_DTYPE_U16)
+        k_ypass<uint16_t><<<g1, kThreads, sm1, st>>>(P, B, logc);
+    else
+        k_ypass<float><<<g1, kThreads, sm1, st>>>(P, B, logc);
+    if (tm) tm->stop(st, "k_ypass");
     return cudaGetLastError();
 }
 

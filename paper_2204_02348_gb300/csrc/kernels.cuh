@@ -64,8 +64,12 @@ struct StageTimer {
 
 // Launchers of the generic three-kernel path (k_split.cu).  Return cudaGetLastError().
 cudaError_t launch_split(const Plan& plan, const Batch& batch, cudaStream_t stream, StageTimer* timer);
+// The first and the last kernel of the generic path on their own (candidate scoring reuses them).
+cudaError_t launch_ypass(const Plan& plan, const Batch& batch, cudaStream_t stream, StageTimer* timer);
+cudaError_t launch_last(const Plan& plan, const Batch& batch, cudaStream_t stream, StageTimer* timer);
 // Shared-memory opt-in, once per process and device.
 cudaError_t split_init();
+cudaError_t score_init();
 
 // Split-BF16 tensor-core variant of the last generic kernel (k_overlap_tc.cu).
 bool tc_supported(const Plan& plan);

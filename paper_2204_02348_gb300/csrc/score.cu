@@ -1,20 +1,34 @@
 // Alignment-candidate scoring: total captured power of every frame under every candidate setting (the
 // quantity the guide's AutoAlign search maximises while it perturbs tilt, defocus and waist).
+//
+// The forward transform does not depend on the candidate except through which bins its box selects, so it
+// runs once per frame on a superset box that covers every candidate's box:
+//   k_ypass  (generic path, with the superset rows)  -> r1s[q][x]   (Ms x N per window)
+//   k_xfwd   x transform of the superset rows, keep the superset columns -> xs[q][c] (Ms x Msx, raw DFT bins)
+// and then, per candidate, only the candidate-specific work runs:
+//   k_xinv_sel  gather the candidate's M x M box from xs, apply its circular mask and beam-centre phase,
+//               x inverse transform                                     -> g[q][i]
+//   k_yinv / k_yinv_tc  y inverse transform, correction, HG overlap with the candidate's tables -> coefficients
+//   k_power     P[b][s] = sum over pols and modes of |c|^2, fixed-order warp reduction.
+// Candidates whose boxes do not fit one superset of at most N rows and columns fall back to the full path.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <string>
 #include <vector>
 
+#include "fft.cuh"
 #include "runtime.hpp"
 
 namespace dhk {
 
+constexpr int kSThreads = 256;
+
 // power[b * count + s] = sum over pols and modes of |c|^2, summed in a fixed order by one warp per frame.
-__global__ void k_power(const float2* __restrict__ coefs, int per_frame, int frames, float* __restrict__ power,
+__global__ void k_power(const float2* __restrict__ coefs, int per_frame, int frame0, int frames, float* __restrict__ power,
                         int count, int s) {
-    const int b = blockIdx.x;
-    if (b >= frames) return;
+    const int b = frame0 + blockIdx.x;
+    if (blockIdx.x >= frames) return;
     const float2* c = coefs + (size_t)b * per_frame;
     float acc = 0.f;
     for (int k = threadIdx.x; k < per_frame; k += 32) acc = fmaf(c[k].x, c[k].x, fmaf(c[k].y, c[k].y, acc));
@@ -23,9 +37,92 @@ __global__ void k_power(const float2* __restrict__ coefs, int per_frame, int fra
     if (threadIdx.x == 0) power[(size_t)b * count + s] = acc;
 }
 
+struct Superset {
+    int ms, msx;                  // superset rows and columns
+    int klx[DH_MAX_POLS];         // first superset column bin (unwrapped)
+};
+
+// x transform of R superset rows per block; keeps the superset columns in natural order.
+__global__ void __launch_bounds__(kSThreads, 2) k_xfwd(const __grid_constant__ Plan P, const __grid_constant__ Superset S,
+                                                       const float2* __restrict__ r1s, float2* __restrict__ xs, int count,
+                                                       int logr, int logn) {
+    extern __shared__ float2 smem[];
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int R = 1 << logr, es = R + 1, N = P.n;
+    const int pol = blockIdx.y, q0 = blockIdx.x * R;
+    for (int fb = blockIdx.z; fb < count; fb += gridDim.z) {
+        const float2* src = r1s + (size_t)(fb * P.pols + pol) * S.ms * N;
+        for (int idx = tid; idx < R * N; idx += nthr) {
+            const int row = idx >> logn, x = idx & (N - 1);
+            const int q = q0 + row;
+            smem[x * es + row] = (q < S.ms) ? src[(size_t)q * N + x] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        fft_run<false>(smem, N, P.rad_n, P.nrad_n, logr, es, P.tw_fwd_n, tid, nthr);
+        float2* dst = xs + (size_t)(fb * P.pols + pol) * S.ms * S.msx;
+        for (int idx = tid; idx < R * S.msx; idx += nthr) {
+            const int row = idx / S.msx, c = idx - row * S.msx;
+            const int q = q0 + row;
+            if (q < S.ms) {
+                const int kx = (S.klx[pol] + c) & (N - 1);
+                dst[(size_t)q * S.msx + c] = smem[P.pos_n[kx] * es + row];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// One candidate: gather its box from the superset, mask and phase it, x inverse transform.
+__global__ void __launch_bounds__(kSThreads, 2) k_xinv_sel(const __grid_constant__ Plan P, const __grid_constant__ Superset S,
+                                                           const float2* __restrict__ xs, float2* __restrict__ g,
+                                                           int count, int qoff0, int qoff1, int poff0, int poff1, int logr) {
+    extern __shared__ float2 smem[];
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    const int R = 1 << logr, es = R + 1, M = P.m;
+    const int pol = blockIdx.y, q0 = blockIdx.x * R;
+    const int qoff = pol ? qoff1 : qoff0, poff = pol ? poff1 : poff0;
+    const PolDev& pd = P.pol[pol];
+    for (int fb = blockIdx.z; fb < count; fb += gridDim.z) {
+        const float2* src = xs + (size_t)(fb * P.pols + pol) * S.ms * S.msx;
+        for (int idx = tid; idx < R * M; idx += nthr) {
+            const int row = idx / M, p = idx - row * M;
+            const int q = q0 + row;
+            float2 v = make_float2(0.f, 0.f);
+            if (q < M && p >= pd.mask_lo[q] && p <= pd.mask_hi[q])
+                v = cmul(cmul(src[(size_t)(qoff + q) * S.msx + poff + p], pd.phase_x[p]), pd.phase_y[q]);
+            smem[P.pos_m[p] * es + row] = v;
+        }
+        __syncthreads();
+        fft_run<true>(smem, M, P.rad_m, P.nrad_m, logr, es, P.tw_inv_m, tid, nthr);
+        float2* dst = g + (size_t)(fb * P.pols + pol) * M * M;
+        for (int idx = tid; idx < R * M; idx += nthr) {
+            const int row = idx / M, i = idx - row * M;
+            const int q = q0 + row;
+            if (q < M) dst[(size_t)q * M + i] = smem[i * es + row];
+        }
+        __syncthreads();
+    }
+}
+
+cudaError_t score_init() {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_xfwd, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024))) return e;
+    return cudaFuncSetAttribute(k_xinv_sel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+}
+
 }  // namespace dhk
 
 using namespace dh;
+
+namespace {
+
+int ilog2i(int v) {
+    int l = 0;
+    while ((1 << (l + 1)) <= v) ++l;
+    return l;
+}
+
+}  // namespace
 
 extern "C" int dh_score_settings(dh_handle h, const void* d_frames, int dtype, int batch, const dh_setting* settings,
                                  int count, float* d_power, void* stream) {
@@ -39,10 +136,17 @@ extern "C" int dh_score_settings(dh_handle h, const void* d_frames, int dtype, i
     int rc = ensure_plan(H);
     if (rc) return rc;
     if (H->plan.modes == 0) return fail(DH_ERROR_INVALIDARGUMENT, "scoring needs a basis (group count > 0)");
+    static bool score_ready[64] = {false};
+    if (H->device >= 0 && H->device < 64 && !score_ready[H->device]) {
+        cudaError_t e = dhk::score_init();
+        if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
+        score_ready[H->device] = true;
+    }
     cudaStream_t st = (cudaStream_t)stream;
     // candidate plans: geometry and tables of every candidate, validated before any work is queued
     std::vector<void*> blobs;
     std::vector<dhk::Plan> plans;
+    std::vector<Geometry> geos;
     auto cleanup = [&]() {
         if (!blobs.empty()) cudaStreamSynchronize(st);
         for (void* b : blobs) cudaFree(b);
@@ -66,35 +170,121 @@ extern "C" int dh_score_settings(dh_handle h, const void* d_frames, int dtype, i
         }
         blobs.push_back(blob);
         plans.push_back(P);
+        geos.push_back(g);
     }
     const dhk::Plan& P0 = H->plan;
-    const int per_frame = P0.pols * P0.modes;
-    const size_t per_frame_scratch = split_window_bytes(P0) * P0.pols;
+    const int N = P0.n, M = P0.m, pols = P0.pols;
+    const int per_frame = pols * P0.modes;
+    // superset box over all candidates, per polarisation
+    dhk::Superset S{};
+    int kly_min[DH_MAX_POLS] = {0, 0};
+    int ms = M, msx = M;
+    for (int p = 0; p < pols; ++p) {
+        int ylo = geos[0].pol[p].ax[1].klo, yhi = ylo, xlo = geos[0].pol[p].ax[0].klo, xhi = xlo;
+        for (const Geometry& g : geos) {
+            ylo = std::min(ylo, g.pol[p].ax[1].klo);
+            yhi = std::max(yhi, g.pol[p].ax[1].klo);
+            xlo = std::min(xlo, g.pol[p].ax[0].klo);
+            xhi = std::max(xhi, g.pol[p].ax[0].klo);
+        }
+        kly_min[p] = ylo;
+        S.klx[p] = xlo;
+        ms = std::max(ms, M + (yhi - ylo));
+        msx = std::max(msx, M + (xhi - xlo));
+    }
+    S.ms = ms;
+    S.msx = msx;
+    const bool superset = ms <= N && msx <= N;
+    const size_t coef_bytes = ((size_t)batch * per_frame * sizeof(float2) + 255) & ~(size_t)255;
+    size_t per_frame_scratch;
+    if (superset)
+        per_frame_scratch = ((size_t)ms * N + (size_t)ms * msx + (size_t)M * M) * sizeof(float2) * pols;
+    else
+        per_frame_scratch = split_window_bytes(P0) * pols;
     int chunk = (int)std::max<size_t>(1, kScratchTarget / per_frame_scratch);
     chunk = std::min(chunk, batch);
-    const size_t coef_bytes = ((size_t)batch * per_frame * sizeof(float2) + 255) & ~(size_t)255;
     rc = ensure_scratch(H, per_frame_scratch * chunk + coef_bytes);
     if (rc) {
         cleanup();
         return rc;
     }
     float2* coefs = (float2*)((char*)H->d_scratch + per_frame_scratch * chunk);
-    for (int s = 0; s < count; ++s) {
-        rc = run_split(plans[s], H->d_scratch, per_frame_scratch * chunk, d_frames, dtype, batch, nullptr, nullptr,
-                       coefs, st, H->timer());
-        if (rc) {
-            cleanup();
-            return rc;
-        }
-        if (H->timer()) H->prof.start(st);
-        dhk::k_power<<<batch, 32, 0, st>>>(coefs, per_frame, batch, d_power, count, s);
-        if (H->timer()) H->prof.stop(st, "k_power");
+    dhk::StageTimer* tm = H->timer();
+    auto power = [&](int s, int f0, int n) -> int {
+        if (tm) tm->start(st);
+        dhk::k_power<<<n, 32, 0, st>>>(coefs, per_frame, f0, n, d_power, count, s);
+        if (tm) tm->stop(st, "k_power");
         cudaError_t e = cudaGetLastError();
+        return e == cudaSuccess ? DH_SUCCESS : cuda_fail(e, "power");
+    };
+    if (!superset) {
+        for (int s = 0; s < count && rc == DH_SUCCESS; ++s) {
+            rc = run_split(plans[s], H->d_scratch, per_frame_scratch * chunk, d_frames, dtype, batch, nullptr, nullptr,
+                           coefs, st, tm);
+            if (rc == DH_SUCCESS) rc = power(s, 0, batch);
+        }
+        cleanup();
+        return rc;
+    }
+    float2* r1s = (float2*)H->d_scratch;
+    float2* xs = r1s + (size_t)chunk * pols * ms * N;
+    float2* gbuf = xs + (size_t)chunk * pols * ms * msx;
+    dhk::Plan Psup = P0;                 // the y pass extracts the superset rows
+    Psup.m = ms;
+    for (int p = 0; p < pols; ++p) Psup.pol[p].kly = kly_min[p];
+    const int logr = (N >= 512) ? 4 : 5;
+    const int R = 1 << logr;
+    for (int f0 = 0; f0 < batch && rc == DH_SUCCESS; f0 += chunk) {
+        const int n = std::min(chunk, batch - f0);
+        const int zf = std::min(n, 65535);
+        dhk::Batch B{};
+        B.src = d_frames;
+        B.dtype = dtype;
+        B.frame0 = f0;
+        B.count = n;
+        B.r1 = r1s;
+        cudaError_t e = dhk::launch_ypass(Psup, B, st, tm);
+        if (e == cudaSuccess) {
+            dim3 gx((ms + R - 1) / R, pols, zf);
+            if (tm) tm->start(st);
+            dhk::k_xfwd<<<gx, dhk::kSThreads, (size_t)N * (R + 1) * sizeof(float2), st>>>(P0, S, r1s, xs, n, logr, ilog2i(N));
+            if (tm) tm->stop(st, "k_xfwd");
+            e = cudaGetLastError();
+        }
         if (e != cudaSuccess) {
-            cleanup();
-            return cuda_fail(e, "power");
+            rc = cuda_fail(e, "superset transform");
+            break;
+        }
+        for (int s = 0; s < count && rc == DH_SUCCESS; ++s) {
+            const dhk::Plan& Pc = plans[s];
+            int qo[2] = {0, 0}, po[2] = {0, 0};
+            for (int p = 0; p < pols; ++p) {
+                qo[p] = Pc.pol[p].kly - kly_min[p];
+                po[p] = Pc.pol[p].klx - S.klx[p];
+            }
+            dim3 gi((M + R - 1) / R, pols, zf);
+            if (tm) tm->start(st);
+            dhk::k_xinv_sel<<<gi, dhk::kSThreads, (size_t)M * (R + 1) * sizeof(float2), st>>>(Pc, S, xs, gbuf, n, qo[0], qo[1],
+                                                                                              po[0], po[1], logr);
+            if (tm) tm->stop(st, "k_xinv_sel");
+            e = cudaGetLastError();
+            if (e == cudaSuccess) {
+                dhk::Batch Bc{};
+                Bc.src = d_frames;
+                Bc.dtype = dtype;
+                Bc.frame0 = f0;
+                Bc.count = n;
+                Bc.g = gbuf;
+                Bc.coefs = coefs;
+                e = dhk::launch_last(Pc, Bc, st, tm);
+            }
+            if (e != cudaSuccess) {
+                rc = cuda_fail(e, "candidate");
+                break;
+            }
+            rc = power(s, f0, n);
         }
     }
     cleanup();
-    return DH_SUCCESS;
+    return rc;
 }

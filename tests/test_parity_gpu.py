@@ -237,3 +237,42 @@ def test_split_bf16_serving_geometry_and_determinism():
     b = run_library(s, d["frames"], precision=SPLIT)
     _check(s, d["frames"], a, coef_tol=SPLIT_COEF_TOL)
     assert np.array_equal(a["coefs"].view(np.uint32), b["coefs"].view(np.uint32))
+
+
+def _score(setup, frames, cand, precision=0):
+    import torch
+    import paper_2204_02348_gb300 as dh
+    B, S = frames.shape[0], cand["tilt_deg"].shape[0]
+    h = dh.dh_create()
+    try:
+        dh.configure(h, setup)
+        dh.dh_set_precision(h, precision)
+        fr = torch.from_numpy(frames).cuda()
+        pw = torch.full((B, S), float("nan"), dtype=torch.float32, device="cuda")
+        sets = [dh.make_setting(cand["tilt_deg"][k], cand["defocus"][k], cand["waist"][k]) for k in range(S)]
+        dt = dh.DH_DTYPE_U16 if frames.dtype == np.uint16 else dh.DH_DTYPE_F32
+        dh.dh_score_settings(h, fr, dt, B, sets, pw)
+        torch.cuda.synchronize()
+        return pw.cpu().numpy()
+    finally:
+        dh.dh_destroy(h)
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 2 * COEF_TOL), (1, 2 * SPLIT_COEF_TOL)])
+def test_score_large_geometry_superset(precision, tol):
+    s = syn.setup_large_batch()
+    d = syn.make_frames(s, 2, seed=70)
+    cand = syn.candidate_settings(s, 6, seed=71)
+    ref = orc.score_settings(d["frames"], s, cand["tilt_deg"], cand["defocus"], cand["waist"])
+    got = _score(s, d["frames"], cand, precision)
+    assert np.all(np.abs(got - ref) / ref <= tol), (got, ref)
+
+
+def test_score_candidates_outside_one_superset_fall_back():
+    s = syn.with_(syn.setup_plain(), ifft_size=64, group_count=4)
+    d = syn.make_frames(s, 2, seed=72)
+    tilt = np.array([[[1.0, 1.0]], [[1.0, -1.5]], [[1.2, 0.8]]])
+    cand = {"tilt_deg": tilt, "defocus": np.array([[0.0], [0.5], [-0.3]]), "waist": np.array([[150e-6], [140e-6], [160e-6]])}
+    ref = orc.score_settings(d["frames"], s, cand["tilt_deg"], cand["defocus"], cand["waist"])
+    got = _score(s, d["frames"], cand)
+    assert np.all(np.abs(got - ref) / ref <= 2 * COEF_TOL), (got, ref)
