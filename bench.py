@@ -47,7 +47,7 @@ def parse_args():
     ap.add_argument("--precision", choices=["fp32", "split_bf16"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--frames", type=int, default=FRAMES, help="frames per step and GPU (default: the workload's 1000)")
-    ap.add_argument("--workload", choices=["batching", "serving"], default="batching")
+    ap.add_argument("--workload", choices=["batching", "serving", "plain", "precision", "large_batch"], default="batching")
     ap.add_argument("--requests", type=int, default=120, help="requests per serving run")
     return ap.parse_args()
 
@@ -496,6 +496,143 @@ def run_serving(args, ws, rank, local):
         print(json.dumps(line), flush=True)
 
 
+def _tiled_frames(setup, count, distinct, seed):
+    """count frames of the seeded stream: `distinct` generated frames repeated (frame content does not change
+    the work; the generator is the expensive part for large frames)."""
+    import numpy as np
+    from synth import holograms as syn
+    base = syn.make_frames(setup, distinct, seed=seed)
+    idx = np.arange(count) % distinct
+    return base, np.ascontiguousarray(base["frames"][idx])
+
+
+def _event_time(fn, steps, warmup):
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        fn()
+    b.record()
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def run_workload(args, ws, rank, local):
+    """Secondary workloads, one JSON line each:
+    plain       1 frame 128x128 float32, 15 modes, 32x32 field: latency of single-frame calls (p50/p99), device
+                input and end to end from host;
+    precision   1024 frames 640x512 u16, two 256x256 windows, 120 modes: FP32 and split-BF16 overlaps, frames/s
+                and coefficient error against the FP64 oracle on sampled frames;
+    large_batch 2000 frames 1280x1024 u16, two 512x512 windows, 210 modes, 64 alignment candidates scored with
+                the split-BF16 overlap: frames/s (every frame under all 64 candidates)."""
+    import numpy as np
+    import torch
+
+    import paper_2204_02348_gb300 as dh
+    from synth import holograms as syn
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    out = {"metric": None, "n_gpus": ws, "data": "synthetic", "vs_baseline": None, "scaling": "weak",
+           "higher_is_better": True}
+    if args.workload == "plain":
+        s = syn.setup_plain()
+        d = syn.make_frames(s, 1)
+        h = dh.dh_create()
+        dh.configure(h, s)
+        m, modes, _ = dh.dh_get_output_dims(h)
+        fr = torch.from_numpy(d["frames"]).to(dev)
+        f = torch.empty((1, 1, m, m), dtype=torch.complex64, device=dev)
+        c = torch.empty((1, 1, modes), dtype=torch.complex64, device=dev)
+        host = torch.from_numpy(d["frames"]).pin_memory()
+        hc = torch.empty((1, 1, modes), dtype=torch.complex64).pin_memory()
+        hf = torch.empty((1, 1, m, m), dtype=torch.complex64).pin_memory()
+        stream = torch.cuda.current_stream(dev)
+        lat, lat_e2e = [], []
+        for it in range(args.steps + args.warmup):
+            t0 = time.perf_counter()
+            dh.dh_process_batch(h, fr, dh.DH_DTYPE_F32, 1, f, c, stream)
+            stream.synchronize()
+            t1 = time.perf_counter()
+            fr.copy_(host, non_blocking=True)
+            dh.dh_process_batch(h, fr, dh.DH_DTYPE_F32, 1, f, c, stream)
+            hf.copy_(f, non_blocking=True)
+            hc.copy_(c, non_blocking=True)
+            stream.synchronize()
+            t2 = time.perf_counter()
+            if it >= args.warmup:
+                lat.append(1e3 * (t1 - t0))
+                lat_e2e.append(1e3 * (t2 - t1))
+        dh.dh_destroy(h)
+        lat.sort()
+        lat_e2e.sort()
+        pct = lambda l, p: l[min(len(l) - 1, int(p * len(l)))]
+        out.update({"metric": "single-frame latency (plain 128x128 f32 case), ms", "value": pct(lat, 0.5), "unit": "ms",
+                    "higher_is_better": False, "steps": args.steps, "warmup": args.warmup, "dtype": "f32",
+                    "config": {"workload": "plain: 1 frame 128x128 f32, 15 modes, 32x32 field, one call per frame"},
+                    "latency_ms": {"p50": pct(lat, 0.5), "p99": pct(lat, 0.99)},
+                    "e2e_latency_ms": {"p50": pct(lat_e2e, 0.5), "p99": pct(lat_e2e, 0.99),
+                                       "note": "host frame in, host field and coefficients out"}})
+    elif args.workload == "precision":
+        from oracle import digholo_oracle as orc
+        s = syn.setup_precision()
+        B = 1024
+        base, frames = _tiled_frames(s, B, 16, syn.BASE_SEED + 2)
+        fr = torch.from_numpy(frames).to(dev)
+        f_ref, c_ref = orc.process_batch(base["frames"][:2], s)
+        res = {}
+        for name, prec in (("fp32", dh.DH_PRECISION_FP32), ("split_bf16", dh.DH_PRECISION_SPLIT_BF16)):
+            h = dh.dh_create()
+            dh.configure(h, s)
+            dh.dh_set_precision(h, prec)
+            m, modes, _ = dh.dh_get_output_dims(h)
+            f = torch.empty((B, 2, m, m), dtype=torch.complex64, device=dev)
+            c = torch.empty((B, 2, modes), dtype=torch.complex64, device=dev)
+            ms = _event_time(lambda: dh.dh_process_batch(h, fr, dh.DH_DTYPE_U16, B, f, c), max(3, args.steps // 20), 3)
+            cc = c[:2].cpu().numpy()
+            ff = f[:2].cpu().numpy()
+            err_c = max(np.linalg.norm(cc[b, p] - c_ref[b, p]) / np.linalg.norm(c_ref[b, p]) for b in range(2) for p in range(2))
+            err_f = max(np.linalg.norm(ff[b, p] - f_ref[b, p]) / np.linalg.norm(f_ref[b, p]) for b in range(2) for p in range(2))
+            res[name] = {"frames_per_s": B / (ms / 1e3), "ms_per_batch": ms, "coef_rel_l2_max": err_c,
+                         "field_rel_l2_max": err_f}
+            dh.dh_destroy(h)
+        bpf = 2 * (256 * 256 * 2 + 96 * 96 * 8 + 120 * 8)
+        peak, _ = measured_peak()
+        out.update({"metric": "frames/s, precision case (split-BF16 vs FP32 overlap)", "value": res["split_bf16"]["frames_per_s"],
+                    "unit": "frames/s", "steps": max(3, args.steps // 20), "warmup": 3, "dtype": "f32 FFT, split-bf16 overlap",
+                    "config": {"workload": "precision: 1024 frames 640x512 u16, 2 windows 256x256, 96x96 fields, 120 modes",
+                               "frame_content": "16 seeded frames tiled"},
+                    "precision": res,
+                    "hbm_frac": {k: v["frames_per_s"] * bpf / 1e9 / peak for k, v in res.items()}})
+    elif args.workload == "large_batch":
+        s = syn.setup_large_batch()
+        B, S = 2000, 64
+        _, frames = _tiled_frames(s, B, 8, syn.BASE_SEED + 4)
+        fr = torch.from_numpy(frames).to(dev)
+        cand = syn.candidate_settings(s, S)
+        h = dh.dh_create()
+        dh.configure(h, s)
+        dh.dh_set_precision(h, dh.DH_PRECISION_SPLIT_BF16)
+        sets = [dh.make_setting(cand["tilt_deg"][k], cand["defocus"][k], cand["waist"][k]) for k in range(S)]
+        pw = torch.empty((B, S), dtype=torch.float32, device=dev)
+        dh.dh_set_profiling(h, True)
+        ms = _event_time(lambda: dh.dh_score_settings(h, fr, dh.DH_DTYPE_U16, B, sets, pw), 2, 1)
+        prof = dh.dh_get_profile(h)
+        dh.dh_destroy(h)
+        out.update({"metric": "frames/s scored under 64 alignment candidates (large case, split-BF16)", "value": B / (ms / 1e3),
+                    "unit": "frames/s", "steps": 2, "warmup": 1, "dtype": "f32 FFT, split-bf16 overlap",
+                    "config": {"workload": "large_batch: 2000 frames 1280x1024 u16, 2 windows 512x512, 176x176 fields, 210 "
+                                           "modes, 64 candidates (tilt +-0.02 deg, defocus U(0,0.05) waves, waist x U(0.9,1.1))",
+                               "frame_content": "8 seeded frames tiled"},
+                    "ms_per_batch": ms, "candidate_windows_per_s": B * 2 * S / (ms / 1e3),
+                    "kernels": {k: {"launches": v[0], "total_ms": v[1]} for k, v in prof.items()}})
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse_args()
     ws, rank, local = dist_env()
@@ -503,6 +640,8 @@ def main():
         run_reference(args, ws, rank)
     elif args.workload == "serving":
         run_serving(args, ws, rank, local)
+    elif args.workload in ("plain", "precision", "large_batch"):
+        run_workload(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
 

@@ -216,6 +216,20 @@ int ensure_scratch(Handle* H, size_t bytes) {
     return DH_SUCCESS;
 }
 
+int chunk_frames(size_t per_frame_bytes, int pols, int batch, int device) {
+    static int sms[64] = {0};
+    int n = 148;
+    if (device >= 0 && device < 64) {
+        if (!sms[device]) cudaDeviceGetAttribute(&sms[device], cudaDevAttrMultiProcessorCount, device);
+        if (sms[device] > 0) n = sms[device];
+    }
+    const size_t per = std::max<size_t>(per_frame_bytes, 1);
+    size_t frames = ((size_t)8 * n + pols - 1) / pols;
+    frames = std::max(frames, kScratchTarget / per);
+    frames = std::min(frames, std::max<size_t>(1, kScratchCap / per));
+    return (int)std::max<size_t>(1, std::min<size_t>(frames, (size_t)batch));
+}
+
 size_t split_window_bytes(const dhk::Plan& P) { return ((size_t)P.m * P.n + (size_t)P.m * P.m) * sizeof(float2); }
 
 // ------------------------------------------------------------------------------------------- profiler
@@ -292,8 +306,7 @@ int process(Handle* H, const void* frames, int dtype, int batch, void* window, v
     if (use_fused(P) && !window && fused_frames_ok(P, frames, dtype))
         return launch_fused_path(H, frames, dtype, batch, fields, coefs, st, H->timer());
     const size_t per_frame = split_window_bytes(P) * P.pols;
-    int chunk = (int)std::max<size_t>(1, kScratchTarget / per_frame);
-    chunk = std::min(chunk, batch);
+    const int chunk = chunk_frames(per_frame, P.pols, batch, H->device);
     rc = ensure_scratch(H, per_frame * chunk);
     if (rc) return rc;
     return run_split(P, H->d_scratch, H->scratch_bytes, frames, dtype, batch, window, fields, coefs, st, H->timer());

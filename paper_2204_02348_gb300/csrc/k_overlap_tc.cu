@@ -7,14 +7,14 @@
 // j), whose B operand holds u_n(y'_j) dy' as bfloat16 hi + lo (host-built, FP64 -> bf16).  One elected thread
 // issues the three products hi*hi + hi*lo + lo*hi per 16-wide K step with tcgen05.mma (kind::f16, FP32
 // accumulation in tensor memory) and commits them to an mbarrier; the four warps of the first warpgroup read
-// the 128 x NP accumulator back with tcgen05.ld and finish the second (x) contraction on CUDA cores with a
-// fixed shuffle tree.  The lo*lo product is below FP32 rounding of the result and is dropped.
+// the 128 x NP accumulator back with tcgen05.ld into shared memory, and one thread per mode finishes the
+// second (x) contraction on CUDA cores in a fixed order.  The lo*lo product is below FP32 rounding of the result and is dropped.
 //
 // Operands use the no-swizzle K-major canonical layout: 8-row x 16-byte core matrices stored contiguously,
 // core (rb, kb) at (rb * K/8 + kb) * 128 bytes, so the descriptor's leading-dimension offset (between cores
 // along K) is 128 bytes and its stride-dimension offset (between 8-row groups) is 16 K bytes.
-// Every wait on the mbarrier is bounded; on expiry the window's coefficients are written as NaN and the
-// block releases its tensor memory before it returns.
+// Every wait on the mbarrier is bounded; on expiry the window's coefficients are written as NaN, the plan's
+// status word records it, and the block releases its tensor memory before it returns.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -73,34 +73,39 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* out) {
     for (int i = 0; i < 16; ++i) out[i] = __uint_as_float(v[i]);
 }
 
+constexpr int kTsPitch = 129;        // accumulator rows per mode row in shared memory (padded)
+
 struct TcLayout {
-    size_t buf, a, b, part, bytes;
+    size_t buf, a, b, bytes;
 };
 
-__host__ __device__ inline TcLayout tc_layout(int M, int NP, int modes) {
+// buf holds the field chunk, then (after the A operand is built from it) the accumulator T[n][r]
+__host__ __device__ inline TcLayout tc_layout(int M, int NP) {
     TcLayout L;
-    L.buf = 0;                                             // float2 [M][64]
-    L.a = L.buf + (size_t)M * kTcCols * 8;                  // bf16 [2][128][M]
+    L.buf = 0;                                             // float2 [M][64]  /  float [NP][129]
+    size_t bufb = (size_t)M * kTcCols * 8;
+    const size_t tsb = (size_t)NP * kTsPitch * 4;
+    if (tsb > bufb) bufb = tsb;
+    L.a = L.buf + ((bufb + 1023) & ~(size_t)1023);         // bf16 [2][128][M]
     L.b = L.a + (size_t)2 * 128 * M * 2;                    // bf16 [2][NP][M]
-    L.part = L.b + (size_t)2 * NP * M * 2;                  // float [4][modes]
-    L.bytes = L.part + (size_t)4 * (modes > 0 ? modes : 1) * 4 + 64;
+    L.bytes = L.b + (size_t)2 * NP * M * 2;
     L.bytes = (L.bytes + 1023) & ~(size_t)1023;
     return L;
 }
 
 }  // namespace
 
-__global__ void __launch_bounds__(kTcThreads, 1) k_yinv_tc(const __grid_constant__ Plan P, const __grid_constant__ Batch B) {
+__global__ void __launch_bounds__(kTcThreads, 2) k_yinv_tc(const __grid_constant__ Plan P, const __grid_constant__ Batch B) {
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_slot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int M = P.m, G = P.groups, modes = P.modes, NP = P.tc_np;
-    const TcLayout L = tc_layout(M, NP, modes);
+    const TcLayout L = tc_layout(M, NP);
     float2* buf = reinterpret_cast<float2*>(sm + L.buf);
+    float* Ts = reinterpret_cast<float*>(sm + L.buf);
     __nv_bfloat16* A = reinterpret_cast<__nv_bfloat16*>(sm + L.a);
     __nv_bfloat16* Bm = reinterpret_cast<__nv_bfloat16*>(sm + L.b);
-    float* part = reinterpret_cast<float*>(sm + L.part);
     const int pol = blockIdx.x;
     const PolDev& pd = P.pol[pol];
 
@@ -194,33 +199,32 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_yinv_tc(const __grid_constant
             ok = ok && done;
             asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
             if (warp < 4) {
-                float T[32];
-                if (ok) {
-                    const uint32_t ta = tmem + ((uint32_t)(32 * warp) << 16);
-                    tmem_ld16(ta, T);
-                    if (NP > 16) tmem_ld16(ta + 16, T + 16);
-                }
-                // row r = 32 warp + lane: column i = r mod 64, part c = r / 64 (0 real, 1 imaginary)
-                const int i = (32 * warp + lane) & 63;
-                const bool in = (i0 + i) < M;
+                // accumulator row r = 32 warp + lane (column i = r mod 64; real part for r < 64, imaginary
+                // part above) to shared memory, T[n][r] with a padded pitch
+                float T[16];
+                const int r = 32 * warp + lane;
+                for (int c0 = 0; c0 < NP; c0 += 16) {
+                    if (ok) tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16) + c0, T);
 #pragma unroll
-                for (int n = 0; n < 32; ++n) {
-                    if (n < G && (n < 16 || NP > 16)) {
-                        for (int m = 0; m + n < G; ++m) {
-                            const int k = (m + n) * (m + n + 1) / 2 + m;
-                            float v = (in && ok) ? __ldg(&pd.hg_x[(size_t)m * M + i0 + i]) * T[n] : 0.f;
-#pragma unroll
-                            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                            if (lane == 0) part[warp * modes + k] = v;
-                        }
-                    }
+                    for (int n = 0; n < 16; ++n) Ts[(c0 + n) * kTsPitch + r] = ok ? T[n] : 0.f;
                 }
             }
             asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
             __syncthreads();
+            // c_mn += sum_i u_m(x'_i) T[n][i] over this chunk's columns, one mode per thread, fixed order
             if (tid < modes) {
-                acc.x += part[0 * modes + tid] + part[1 * modes + tid];
-                acc.y += part[2 * modes + tid] + part[3 * modes + tid];
+                const int m = P.mode_m[tid], n = P.mode_n[tid];
+                const float* u = pd.hg_x + (size_t)m * M + i0;
+                const float* tr = Ts + n * kTsPitch;
+                const int lim = min(kTcCols, M - i0);
+                float sr = 0.f, si = 0.f;
+                for (int i = 0; i < lim; ++i) {
+                    const float w = __ldg(&u[i]);
+                    sr = fmaf(w, tr[i], sr);
+                    si = fmaf(w, tr[64 + i], si);
+                }
+                acc.x += sr;
+                acc.y += si;
             }
             __syncthreads();
         }
@@ -242,7 +246,7 @@ cudaError_t tc_init() {
 }
 
 cudaError_t launch_yinv_tc(const Plan& P, const Batch& B, cudaStream_t st) {
-    const TcLayout L = tc_layout(P.m, P.tc_np, P.modes);
+    const TcLayout L = tc_layout(P.m, P.tc_np);
     dim3 grid(P.pols, B.count < 65535 ? B.count : 65535);
     k_yinv_tc<<<grid, kTcThreads, L.bytes, st>>>(P, B);
     return cudaGetLastError();

@@ -13,9 +13,12 @@
 
 namespace dh {
 
-// Scratch budget per launch chunk of the generic path: small enough that the intermediate spectra of one
-// chunk stay resident in the 129 MB L2 between the kernels that produce and consume them.
+// Frames per launch chunk of the generic path: enough windows for several waves of its one-block-per-window
+// kernels (at least 8 per SM), at least what fits 48 MB (the chunk then stays in the 129 MB L2 between its
+// kernels), and at most 1 GiB of scratch.
 constexpr size_t kScratchTarget = 48ull << 20;
+constexpr size_t kScratchCap = 1ull << 30;
+int chunk_frames(size_t per_frame_bytes, int pols, int batch, int device);
 
 // Records a CUDA event pair around every kernel launch of a handle while enabled; totals per kernel name.
 struct Profiler : dhk::StageTimer {

@@ -24,17 +24,20 @@ namespace dhk {
 
 constexpr int kSThreads = 256;
 
-// power[b * count + s] = sum over pols and modes of |c|^2, summed in a fixed order by one warp per frame.
-__global__ void k_power(const float2* __restrict__ coefs, int per_frame, int frame0, int frames, float* __restrict__ power,
-                        int count, int s) {
-    const int b = frame0 + blockIdx.x;
-    if (blockIdx.x >= frames) return;
-    const float2* c = coefs + (size_t)b * per_frame;
+// power[(frame0 + b) * count + s0 + s] = sum over pols and modes of |c|^2 for the candidates s0 .. s0 + ns - 1 of a
+// chunk (coefficients of candidate s at frame slot b: coefs[(s * cstride + b) * per_frame ...], frame index
+// relative to the chunk), one warp per (frame, candidate), summed in a fixed order.
+__global__ void k_power(const float2* __restrict__ coefs, int per_frame, int frame0, int frames, int ns, int s0,
+                        int cstride, float* __restrict__ power, int count) {
+    const int w = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+    if (w >= frames * ns) return;
+    const int s = w / frames, b = w - s * frames;
+    const float2* c = coefs + ((size_t)s * cstride + b) * per_frame;
     float acc = 0.f;
-    for (int k = threadIdx.x; k < per_frame; k += 32) acc = fmaf(c[k].x, c[k].x, fmaf(c[k].y, c[k].y, acc));
+    for (int k = lane; k < per_frame; k += 32) acc = fmaf(c[k].x, c[k].x, fmaf(c[k].y, c[k].y, acc));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (threadIdx.x == 0) power[(size_t)b * count + s] = acc;
+    if (lane == 0) power[(size_t)(frame0 + b) * count + s0 + s] = acc;
 }
 
 struct Superset {
@@ -195,37 +198,51 @@ extern "C" int dh_score_settings(dh_handle h, const void* d_frames, int dtype, i
     S.ms = ms;
     S.msx = msx;
     const bool superset = ms <= N && msx <= N;
-    const size_t coef_bytes = ((size_t)batch * per_frame * sizeof(float2) + 255) & ~(size_t)255;
-    size_t per_frame_scratch;
-    if (superset)
-        per_frame_scratch = ((size_t)ms * N + (size_t)ms * msx + (size_t)M * M) * sizeof(float2) * pols;
-    else
-        per_frame_scratch = split_window_bytes(P0) * pols;
-    int chunk = (int)std::max<size_t>(1, kScratchTarget / per_frame_scratch);
-    chunk = std::min(chunk, batch);
-    rc = ensure_scratch(H, per_frame_scratch * chunk + coef_bytes);
-    if (rc) {
-        cleanup();
-        return rc;
-    }
-    float2* coefs = (float2*)((char*)H->d_scratch + per_frame_scratch * chunk);
     dhk::StageTimer* tm = H->timer();
-    auto power = [&](int s, int f0, int n) -> int {
-        if (tm) tm->start(st);
-        dhk::k_power<<<n, 32, 0, st>>>(coefs, per_frame, f0, n, d_power, count, s);
-        if (tm) tm->stop(st, "k_power");
-        cudaError_t e = cudaGetLastError();
-        return e == cudaSuccess ? DH_SUCCESS : cuda_fail(e, "power");
-    };
     if (!superset) {
+        // one candidate at a time through the full generic path, coefficients for the whole batch
+        const size_t per_frame_scratch = split_window_bytes(P0) * pols;
+        const int chunk = chunk_frames(per_frame_scratch, pols, batch, H->device);
+        const size_t spectra_bytes = (per_frame_scratch * chunk + 255) & ~(size_t)255;
+        rc = ensure_scratch(H, spectra_bytes + (size_t)batch * per_frame * sizeof(float2));
+        if (rc) {
+            cleanup();
+            return rc;
+        }
+        float2* coefs = (float2*)((char*)H->d_scratch + spectra_bytes);   // [batch][pols * modes]
         for (int s = 0; s < count && rc == DH_SUCCESS; ++s) {
             rc = run_split(plans[s], H->d_scratch, per_frame_scratch * chunk, d_frames, dtype, batch, nullptr, nullptr,
                            coefs, st, tm);
-            if (rc == DH_SUCCESS) rc = power(s, 0, batch);
+            if (rc) break;
+            if (tm) tm->start(st);
+            dhk::k_power<<<(batch + 7) / 8, 256, 0, st>>>(coefs, per_frame, 0, batch, 1, s, batch, d_power, count);
+            if (tm) tm->stop(st, "k_power");
+            cudaError_t e = cudaGetLastError();
+            if (e != cudaSuccess) rc = cuda_fail(e, "power");
         }
         cleanup();
         return rc;
     }
+    // per frame: the superset spectra plus every candidate's coefficients
+    const size_t per_frame_scratch = ((size_t)ms * N + (size_t)ms * msx + (size_t)M * M) * sizeof(float2) * pols;
+    const size_t per_frame_coefs = (size_t)count * per_frame * sizeof(float2);
+    const int chunk = chunk_frames(per_frame_scratch + per_frame_coefs, pols, batch, H->device);
+    const size_t spectra_bytes = (per_frame_scratch * chunk + 255) & ~(size_t)255;
+    rc = ensure_scratch(H, spectra_bytes + per_frame_coefs * chunk);
+    if (rc) {
+        cleanup();
+        return rc;
+    }
+    float2* coefs = (float2*)((char*)H->d_scratch + spectra_bytes);   // [count][chunk][pols * modes]
+    auto power = [&](int f0, int n) -> int {
+        const int warps = n * count, per_block = 8;
+        if (tm) tm->start(st);
+        dhk::k_power<<<(warps + per_block - 1) / per_block, 32 * per_block, 0, st>>>(coefs, per_frame, f0, n, count, 0,
+                                                                                  chunk, d_power, count);
+        if (tm) tm->stop(st, "k_power");
+        cudaError_t e = cudaGetLastError();
+        return e == cudaSuccess ? DH_SUCCESS : cuda_fail(e, "power");
+    };
     float2* r1s = (float2*)H->d_scratch;
     float2* xs = r1s + (size_t)chunk * pols * ms * N;
     float2* gbuf = xs + (size_t)chunk * pols * ms * msx;
@@ -275,15 +292,16 @@ extern "C" int dh_score_settings(dh_handle h, const void* d_frames, int dtype, i
                 Bc.frame0 = f0;
                 Bc.count = n;
                 Bc.g = gbuf;
-                Bc.coefs = coefs;
+                // the last kernel writes frame f at (f * pols + pol) * modes: shift so frame f0 lands at slot 0
+                Bc.coefs = coefs + (size_t)s * chunk * per_frame - (size_t)f0 * per_frame;
                 e = dhk::launch_last(Pc, Bc, st, tm);
             }
             if (e != cudaSuccess) {
                 rc = cuda_fail(e, "candidate");
                 break;
             }
-            rc = power(s, f0, n);
         }
+        if (rc == DH_SUCCESS) rc = power(f0, n);
     }
     cleanup();
     return rc;
