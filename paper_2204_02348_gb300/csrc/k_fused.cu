@@ -9,9 +9,9 @@
 //            selection, the circular mask and the beam-centre phase;
 //   inverse  M-point inverse transform along x (DIT, digit-reversed in / natural out) and along y (DIF,
 //            natural in / digit-reversed out), in place;
-//   epilogue residual tilt and defocus removal, field write (coalesced along x), and the separable HG
-//            contraction: partial sums over y per thread group, then one warp per mode sums over x with a
-//            fixed shuffle tree (deterministic, no atomics).
+//   epilogue residual tilt and defocus removal in registers inside the last y pass, field write (coalesced
+//            along x), and the separable HG contraction: partial sums over y per thread group, then the modes
+//            spread over the warps with fixed shuffle trees (deterministic, no atomics).
 // Shared memory: r1[N][M+1] box rows (x-major, padded pitch) and one union region used in turn as the y-pass
 // tile, the M x (M+1) window / field, and the overlap partials; twiddles and the digit-reversal table.
 #include <cuda.h>
@@ -55,13 +55,15 @@ struct FusedLayout {
     static constexpr int R1 = kFN * PITCH;
     static constexpr int YT = kFN * (kFN / 2);                 // y tile: 128 rows x 64 column pairs
     static constexpr int WB = M * PITCH;
-    static constexpr int UN = YT > WB + kFGMax * M ? YT : WB + kFGMax * M;
+    static constexpr int UN = YT > WB ? YT : WB;
+    static_assert(R1 >= M * M + kFGMax * M, "r1 holds the corrected field and T");
     static constexpr int F2 = R1 + UN + kFN + M + 4 * M;
     static constexpr int FL = 2 * kFGMax * M;
     static constexpr int IN = 3 * M + 2 * (kFGMax * (kFGMax + 1) / 2);
     static constexpr size_t STG = (size_t)Staging<T>::BYTES;   // first, 1024-byte aligned
     static constexpr size_t bytes = STG + (size_t)F2 * sizeof(float2) + (size_t)FL * sizeof(float) + (size_t)IN * sizeof(int);
-    static constexpr int JQ0 = (kFThreads / M) < (R1 / (kFGMax * M)) ? (kFThreads / M) : (R1 / (kFGMax * M));
+    // overlap partial sums live in the union region once the field has moved to r1
+    static constexpr int JQ0 = (kFThreads / M) < (UN / (kFGMax * M)) ? (kFThreads / M) : (UN / (kFGMax * M));
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -260,17 +262,29 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused128(const __grid_constant
         __syncthreads();
         spass<MR0, true, false, M, M, M, 1, PITCH, NT>(un, twM, tid);
         __syncthreads();
-        spass<MR1, true, false, M, MR1, M, 1, PITCH, NT>(un, twM, tid);
-        __syncthreads();
 
-        // ---------------------------------------------------------------- correction and field
-        float2* fld = A.fields ? A.fields + (size_t)(f * P.pols + pol) * M * M : nullptr;
-        for (int t = tid; t < M * M; t += NT) {
-            const int i = t % M, j = t / M;
-            const int a = i * PITCH + posM[j];
-            const float2 e = cmul(cmul(un[a], cx[i]), cy[j]);
-            un[a] = e;
-            if (fld) fld[t] = e;
+        // ---------------------------------------------------------------- last y pass, correction and field
+        // The last DIF pass (span MR1, no twiddles) leaves output j = blk + MR0 r at position blk MR1 + r of
+        // column i; it is corrected in registers and written in natural order to r1 (for the overlap) and to
+        // the field (coalesced along i).
+        float2* enat = r1;                         // [M][M], j-major
+        {
+            float2* fld = A.fields ? A.fields + (size_t)(f * P.pols + pol) * M * M : nullptr;
+            for (int t = tid; t < M * (M / MR1); t += NT) {
+                const int i = t % M, blk = t / M;
+                float2 v[MR1];
+#pragma unroll
+                for (int r = 0; r < MR1; ++r) v[r] = un[i * PITCH + blk * MR1 + r];
+                dft<MR1, true>(v, twM, M / MR1);
+                const float2 ci = cx[i];
+#pragma unroll
+                for (int r = 0; r < MR1; ++r) {
+                    const int j = blk + MR0 * r;
+                    const float2 e = cmul(cmul(v[r], ci), cy[j]);
+                    enat[j * M + i] = e;
+                    if (fld) fld[j * M + i] = e;
+                }
+            }
         }
         __syncthreads();
 
@@ -278,8 +292,8 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused128(const __grid_constant
         if (A.coefs && G > 0) {
             constexpr int JQ = L::JQ0;                 // thread groups splitting the y sum
             constexpr int JL = (M + JQ - 1) / JQ;
-            float2* part = r1;                         // [JQ][G][M]
-            float2* tsum = un + L::WB;                 // [G][M]
+            float2* part = un;                         // [JQ][G][M]
+            float2* tsum = r1 + M * M;                 // [G][M]
             if (tid < JQ * M) {
                 const int i = tid % M, jq = tid / M;
                 const int j0 = jq * JL, j1 = min(M, j0 + JL);
@@ -290,7 +304,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused128(const __grid_constant
                 for (int jj = 0; jj < JL; ++jj) {
                     const int j = j0 + jj;
                     if (j < j1) {
-                        const float2 e = un[i * PITCH + posM[j]];
+                        const float2 e = enat[j * M + i];
 #pragma unroll
                         for (int n = 0; n < kFGMax; ++n) {
                             if (n < G) {
