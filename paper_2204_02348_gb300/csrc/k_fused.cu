@@ -2,9 +2,9 @@
 // one (frame, polarisation) window entirely in shared memory, persistent over windows, two blocks per SM.
 //
 // Per window (the guide's pipeline steps 1-3 and digHoloProcessRemoveTilt):
-//   y pass   pairs of adjacent real columns (x, x+1) packed as one complex column; radix-16 DIF pass straight
-//            from global memory (coalesced 32-bit / 64-bit pixel-pair loads), radix-8 pass fused with the
-//            separation of the two real spectra (Z(k), conj Z(-k)) and the selection of the M box rows;
+//   y pass   real columns x and x + 64 packed as one complex column; radix-16 DIF pass from the window staged
+//            in shared memory by a tensor copy, radix-8 pass fused with the separation of the two real spectra
+//            (Z(k), conj Z(-k)) and the selection of the M box rows;
 //   x pass   radix-16 then radix-8 DIF along x on the M box rows, the second pass fused with the box-column
 //            selection, the circular mask and the beam-centre phase;
 //   inverse  M-point inverse transform along x (DIT, digit-reversed in / natural out) and along y (DIF,
@@ -56,14 +56,12 @@ struct FusedLayout {
     static constexpr int YT = kFN * (kFN / 2);                 // y tile: 128 rows x 64 column pairs
     static constexpr int WB = M * PITCH;
     static constexpr int UN = YT > WB ? YT : WB;
-    static_assert(R1 >= M * M + kFGMax * M, "r1 holds the corrected field and T");
+    static_assert(UN >= kFGMax * M, "the union region holds T");
     static constexpr int F2 = R1 + UN + kFN + M + 4 * M;
     static constexpr int FL = 2 * kFGMax * M;
     static constexpr int IN = 3 * M + 2 * (kFGMax * (kFGMax + 1) / 2);
     static constexpr size_t STG = (size_t)Staging<T>::BYTES;   // first, 1024-byte aligned
     static constexpr size_t bytes = STG + (size_t)F2 * sizeof(float2) + (size_t)FL * sizeof(float) + (size_t)IN * sizeof(int);
-    // overlap partial sums live in the union region once the field has moved to r1
-    static constexpr int JQ0 = (kFThreads / M) < (UN / (kFGMax * M)) ? (kFThreads / M) : (UN / (kFGMax * M));
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -90,28 +88,18 @@ __device__ __forceinline__ void stage_window(const CUtensorMap* tmap, uint32_t d
         : "memory");
 }
 
+// Columns x and x + N/2 of a staged row, packed as one complex value.
 template <typename T>
-__device__ __forceinline__ float2 staged_pair(const T* row, int x, bool even);
-template <>
-__device__ __forceinline__ float2 staged_pair<uint16_t>(const uint16_t* row, int x, bool even) {
-    if (even) {
-        const uint32_t u = *reinterpret_cast<const uint32_t*>(row + x);
-        return make_float2((float)(u & 0xffffu), (float)(u >> 16));
-    }
-    return make_float2((float)row[x], (float)row[x + 1]);
-}
-template <>
-__device__ __forceinline__ float2 staged_pair<float>(const float* row, int x, bool even) {
-    if (even) return *reinterpret_cast<const float2*>(row + x);
-    return make_float2(row[x], row[x + 1]);
+__device__ __forceinline__ float2 staged_pair(const T* row, int x) {
+    return make_float2((float)row[x], (float)row[x + kFN / 2]);
 }
 
-// Write the separated spectra of columns x and x+1 at frequency k (if k is a box row).
+// Write the separated spectra of columns x and x + N/2 at frequency k (if k is a box row).
 __device__ __forceinline__ void emit_pair(float2* r1, int pitch, int M, int kly, int x, int k, float2 zk, float2 zm) {
     const int q = (k - kly) & (kFN - 1);
     if (q < M) {
         r1[x * pitch + q] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
-        r1[(x + 1) * pitch + q] = make_float2(0.5f * (zk.y + zm.y), 0.5f * (zm.x - zk.x));
+        r1[(x + kFN / 2) * pitch + q] = make_float2(0.5f * (zk.y + zm.y), 0.5f * (zm.x - zk.x));
     }
 }
 
@@ -121,6 +109,8 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused128(const __grid_constant
     using L = FusedLayout<M, T>;
     using S = Staging<T>;
     constexpr int N = kFN, PITCH = L::PITCH, NT = kFThreads;
+    static_assert(M == MR0 * MR1, "field size = product of the two radices");
+    static_assert(L::R1 >= (M / MR1) * kFGMax * M, "r1 holds the overlap partial sums");
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ int abort_flag;
@@ -148,7 +138,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused128(const __grid_constant
     for (int i = tid; i < N; i += NT) twN[i] = P.tw_fwd_n[i];
     for (int i = tid; i < M; i += NT) {
         twM[i] = P.tw_inv_m[i];
-        posM[i] = P.pos_m[i];
+        posM[i] = (i % MR0) * MR1 + i / MR0;   // position of index i after DIF passes of radix MR0 then MR1
         phx[i] = pd.phase_x[i];
         phy[i] = pd.phase_y[i];
         cx[i] = pd.corr_x[i];
@@ -175,7 +165,6 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused128(const __grid_constant
     }
     __syncthreads();
     const int xo = A.xo[pol];
-    const bool even = (xo & 1) == 0;
     uint32_t parity = 0;
     for (; b < A.count; b += fstride) {
         const int f = A.frame0 + b;
@@ -193,7 +182,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused128(const __grid_constant
             const int c = tid & 63, j = tid >> 6;
             float2 v[16];
 #pragma unroll
-            for (int r = 0; r < 16; ++r) v[r] = staged_pair<T>(stg + (j + 8 * r) * S::W, xo + 2 * c, even);
+            for (int r = 0; r < 16; ++r) v[r] = staged_pair<T>(stg + (j + 8 * r) * S::W, xo + c);
             dft16<false>(v);
 #pragma unroll
             for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], twN[j * r]);
@@ -215,7 +204,7 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused128(const __grid_constant
             }
             dft8<false>(z1);
             dft8<false>(z2);
-            const int x = 2 * c;
+            const int x = c;
             if (u != 0) {
 #pragma unroll
                 for (int r = 0; r < 8; ++r) {
@@ -263,14 +252,17 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused128(const __grid_constant
         spass<MR0, true, false, M, M, M, 1, PITCH, NT>(un, twM, tid);
         __syncthreads();
 
-        // ---------------------------------------------------------------- last y pass, correction and field
+        // ---------------------------------------------------------------- last y pass, correction, field, y overlap
         // The last DIF pass (span MR1, no twiddles) leaves output j = blk + MR0 r at position blk MR1 + r of
-        // column i; it is corrected in registers and written in natural order to r1 (for the overlap) and to
-        // the field (coalesced along i).
-        float2* enat = r1;                         // [M][M], j-major
+        // column i; it is corrected in registers, written to the field (coalesced along i) and contracted with
+        // u_n(y'_j) into the partial sums part[blk][n][i] over the thread's MR1 rows.
+        constexpr int NBLK = M / MR1;
+        float2* part = r1;                         // [NBLK][G][M]
+        float2* tsum = un;                         // [G][M]
+        const bool ov = A.coefs && G > 0;
         {
             float2* fld = A.fields ? A.fields + (size_t)(f * P.pols + pol) * M * M : nullptr;
-            for (int t = tid; t < M * (M / MR1); t += NT) {
+            for (int t = tid; t < M * NBLK; t += NT) {
                 const int i = t % M, blk = t / M;
                 float2 v[MR1];
 #pragma unroll
@@ -280,52 +272,36 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused128(const __grid_constant
 #pragma unroll
                 for (int r = 0; r < MR1; ++r) {
                     const int j = blk + MR0 * r;
-                    const float2 e = cmul(cmul(v[r], ci), cy[j]);
-                    enat[j * M + i] = e;
-                    if (fld) fld[j * M + i] = e;
+                    v[r] = cmul(cmul(v[r], ci), cy[j]);
+                    if (fld) fld[j * M + i] = v[r];
+                }
+                if (ov) {
+#pragma unroll
+                    for (int n = 0; n < kFGMax; ++n) {
+                        if (n < G) {
+                            float2 a = make_float2(0.f, 0.f);
+#pragma unroll
+                            for (int r = 0; r < MR1; ++r) {
+                                const float u = hgy[n * M + blk + MR0 * r];
+                                a.x = fmaf(u, v[r].x, a.x);
+                                a.y = fmaf(u, v[r].y, a.y);
+                            }
+                            part[(blk * G + n) * M + i] = a;
+                        }
+                    }
                 }
             }
         }
         __syncthreads();
 
-        // ---------------------------------------------------------------- HG overlap
-        if (A.coefs && G > 0) {
-            constexpr int JQ = L::JQ0;                 // thread groups splitting the y sum
-            constexpr int JL = (M + JQ - 1) / JQ;
-            float2* part = un;                         // [JQ][G][M]
-            float2* tsum = r1 + M * M;                 // [G][M]
-            if (tid < JQ * M) {
-                const int i = tid % M, jq = tid / M;
-                const int j0 = jq * JL, j1 = min(M, j0 + JL);
-                float2 acc[kFGMax];
-#pragma unroll
-                for (int n = 0; n < kFGMax; ++n) acc[n] = make_float2(0.f, 0.f);
-#pragma unroll
-                for (int jj = 0; jj < JL; ++jj) {
-                    const int j = j0 + jj;
-                    if (j < j1) {
-                        const float2 e = enat[j * M + i];
-#pragma unroll
-                        for (int n = 0; n < kFGMax; ++n) {
-                            if (n < G) {
-                                const float u = hgy[n * M + j];
-                                acc[n].x = fmaf(u, e.x, acc[n].x);
-                                acc[n].y = fmaf(u, e.y, acc[n].y);
-                            }
-                        }
-                    }
-                }
-#pragma unroll
-                for (int n = 0; n < kFGMax; ++n)
-                    if (n < G) part[(jq * G + n) * M + i] = acc[n];
-            }
-            __syncthreads();
-            // T[n][i]: the y partial sums added in a fixed order
+        // ---------------------------------------------------------------- HG overlap, x contraction
+        if (ov) {
+            // T[n][i]: the partial sums of the NBLK row groups added in a fixed order
             for (int t = tid; t < G * M; t += NT) {
                 float2 v = part[t];
 #pragma unroll
-                for (int jq = 1; jq < JQ; ++jq) {
-                    const float2 w = part[jq * G * M + t];
+                for (int q = 1; q < NBLK; ++q) {
+                    const float2 w = part[q * G * M + t];
                     v.x += w.x;
                     v.y += w.y;
                 }
@@ -424,7 +400,7 @@ cudaError_t fused_init() {
         g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     }
     if ((e = dhk::set_attr<32, 8, 4>())) return e;
-    if ((e = dhk::set_attr<48, 16, 3>())) return e;
+    if ((e = dhk::set_attr<48, 3, 16>())) return e;
     return dhk::set_attr<64, 8, 8>();
 }
 
@@ -470,7 +446,7 @@ int launch_fused_path(Handle* H, const void* frames, int dtype, int batch, void*
     if (tm) tm->start(st);
     switch (P.m) {
         case 32: dhk::launch<32, 8, 4>(P, A, tmap, dtype, grid, st); break;
-        case 48: dhk::launch<48, 16, 3>(P, A, tmap, dtype, grid, st); break;
+        case 48: dhk::launch<48, 3, 16>(P, A, tmap, dtype, grid, st); break;
         default: dhk::launch<64, 8, 8>(P, A, tmap, dtype, grid, st); break;
     }
     if (tm) tm->stop(st, "k_fused128");
