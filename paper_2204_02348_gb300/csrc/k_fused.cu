@@ -146,9 +146,11 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused128(const __grid_constant
         mlo[i] = pd.mask_lo[i];
         mhi[i] = pd.mask_hi[i];
     }
-    for (int i = tid; i < G * M; i += NT) {
-        hgx[i] = pd.hg_x[i];
-        hgy[i] = pd.hg_y[i];
+    for (int i = tid; i < G * M; i += NT) hgx[i] = pd.hg_x[i];
+    // u_n(y'_j) stored [j][n] (n fastest, kFGMax wide) so the y contraction reads four groups per load
+    for (int i = tid; i < kFGMax * M; i += NT) {
+        const int j = i / kFGMax, n = i - j * kFGMax;
+        hgy[i] = n < G ? pd.hg_y[n * M + j] : 0.f;
     }
     for (int i = tid; i < modes; i += NT) {
         mdm[i] = P.mode_m[i];
@@ -277,16 +279,25 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused128(const __grid_constant
                 }
                 if (ov) {
 #pragma unroll
-                    for (int n = 0; n < kFGMax; ++n) {
-                        if (n < G) {
-                            float2 a = make_float2(0.f, 0.f);
+                    for (int n4 = 0; n4 < kFGMax; n4 += 4) {
+                        if (n4 < G) {
+                            float2 a[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f),
+                                           make_float2(0.f, 0.f)};
 #pragma unroll
                             for (int r = 0; r < MR1; ++r) {
-                                const float u = hgy[n * M + blk + MR0 * r];
-                                a.x = fmaf(u, v[r].x, a.x);
-                                a.y = fmaf(u, v[r].y, a.y);
+                                const float4 u = *reinterpret_cast<const float4*>(hgy + (blk + MR0 * r) * kFGMax + n4);
+                                a[0].x = fmaf(u.x, v[r].x, a[0].x);
+                                a[0].y = fmaf(u.x, v[r].y, a[0].y);
+                                a[1].x = fmaf(u.y, v[r].x, a[1].x);
+                                a[1].y = fmaf(u.y, v[r].y, a[1].y);
+                                a[2].x = fmaf(u.z, v[r].x, a[2].x);
+                                a[2].y = fmaf(u.z, v[r].y, a[2].y);
+                                a[3].x = fmaf(u.w, v[r].x, a[3].x);
+                                a[3].y = fmaf(u.w, v[r].y, a[3].y);
                             }
-                            part[(blk * G + n) * M + i] = a;
+#pragma unroll
+                            for (int c = 0; c < 4; ++c)
+                                if (n4 + c < G) part[(blk * G + n4 + c) * M + i] = a[c];
                         }
                     }
                 }
