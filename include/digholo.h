@@ -115,6 +115,12 @@ int dh_set_defocus(dh_handle h, int pol, double dioptre);
  * modal decomposition and no coefficients). */
 int dh_set_basis(dh_handle h, int pol, double waist, int group_count);
 
+/* Fill-factor correction (digHoloConfigSetFillFactorCorrectionEnabled): when enabled (nonzero) the frames are
+ * taken to come from pixels with a 100 % fill factor, and the kept Fourier bins are divided by the pixel
+ * response sinc(k/N) = sin(pi k/N) / (pi k/N) of both axes (k the unwrapped bin) before the inverse transform.
+ * Off by default. */
+int dh_set_fill_factor_correction(dh_handle h, int enabled);
+
 /* Overlap arithmetic: DH_PRECISION_FP32 or DH_PRECISION_SPLIT_BF16. */
 int dh_set_precision(dh_handle h, int precision);
 
@@ -225,6 +231,15 @@ int dh_server_wait(dh_server s, uint64_t ticket, int timeout_ms);
 int dh_server_stats(dh_server s, dh_stats* out);
 /* Finish in-flight requests, fail queued ones, release the budget and the streams. */
 int dh_server_destroy(dh_server s);
+
+/* Failure detection.  Every wait inside a kernel (tensor-copy and tensor-core mbarriers) is bounded; when a
+ * bound runs out the kernel writes NaN outputs for the affected windows, sets a bit in the handle's device
+ * status word (bit 0: a staged-window copy did not arrive; bit 1: a tensor-core product did not complete) and
+ * returns, leaving the context usable.  dh_get_device_status synchronises with the device, returns the word in
+ * *status and clears it.  dh_check_bounded_wait runs the same bounded wait on an mbarrier that nothing ever
+ * completes, with `limit` tries, and reports in *expired whether the limit ran out (1) as it must. */
+int dh_get_device_status(dh_handle h, int* status);
+int dh_check_bounded_wait(long long limit, int* expired);
 
 /* Per-kernel device timing (the analogue of digHoloBenchmark's per-stage rates).  While enabled, every kernel
  * the handle launches is bracketed by a CUDA event pair recorded on the launch stream.  dh_set_profiling

@@ -119,6 +119,7 @@ class PolGeometry:
     groups: int
     pixel: float
     wavelength: float
+    fill_factor: bool = False   # divide the window by the 100 %-fill-factor pixel response
 
 
 def pol_geometry(setup, p: int, tilt_deg=None, defocus=None, waist=None) -> PolGeometry:
@@ -141,7 +142,8 @@ def pol_geometry(setup, p: int, tilt_deg=None, defocus=None, waist=None) -> PolG
     ag = [AxisGeometry(n=n, origin=o, centre=c, kappa=k, k0=round_half_away(k), m=m, dx=n * px / m)
           for (c, o, k) in axes]
     return PolGeometry(x=ag[0], y=ag[1], r_x=r_bins, r_y=r_bins, defocus=dfc, waist=wst,
-                       groups=int(setup.group_count), pixel=px, wavelength=lam)
+                       groups=int(setup.group_count), pixel=px, wavelength=lam,
+                       fill_factor=bool(getattr(setup, "fill_factor", False)))
 
 
 # ---------------------------------------------------------------------------------------------------
@@ -195,10 +197,20 @@ def window_mask(g: PolGeometry) -> np.ndarray:
     return inside & half[None, :]
 
 
+def pixel_response(ax: AxisGeometry, bins: np.ndarray) -> np.ndarray:
+    """Spectral response sinc(k / N) = sin(pi k / N) / (pi k / N) of a pixel that integrates over its full
+    width (digHoloConfigSetFillFactorCorrectionEnabled: a 100 % fill factor)."""
+    return np.sinc(np.asarray(bins, dtype=np.float64) / ax.n)
+
+
 def reconstruct_field(f_box: np.ndarray, mask: np.ndarray, g: PolGeometry) -> np.ndarray:
     """E(x'_i, y'_j) by the explicit inverse sum over the kept bins, times the reference's residual
-    tilt and defocus phase (pipeline step 2 and digHoloProcessRemoveTilt)."""
+    tilt and defocus phase (pipeline step 2 and digHoloProcessRemoveTilt).  With fill-factor correction the
+    kept bins are first divided by the pixel response of both axes (done during the inverse transform in the
+    guide)."""
     px, lam = g.pixel, g.wavelength
+    if g.fill_factor:
+        f_box = f_box / np.outer(pixel_response(g.y, box_bins(g.y)), pixel_response(g.x, box_bins(g.x)))
     out = []
     for ax in (g.x, g.y):
         q = np.arange(ax.m) - ax.m // 2                     # k - k0

@@ -76,6 +76,7 @@ _PROTOS = {
     "dh_set_defocus": [_i, _i, _d],
     "dh_set_basis": [_i, _i, _d, _i],
     "dh_set_precision": [_i, _i],
+    "dh_set_fill_factor_correction": [_i, _i],
     "dh_get_output_dims": [_i, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_d)],
     "dh_get_axes": [_i, _i, ctypes.POINTER(_d), ctypes.POINTER(_d)],
     "dh_process_batch": [_i, _p, _i, _i, _p, _p, _p],
@@ -83,6 +84,8 @@ _PROTOS = {
     "dh_process_batch_noalloc": [_i, _p, _i, _i, _p, _p, _p],
     "dh_score_settings": [_i, _p, _i, _i, ctypes.POINTER(dh_setting), _i, _p, _p],
     "dh_set_profiling": [_i, _i],
+    "dh_get_device_status": [_i, ctypes.POINTER(_i)],
+    "dh_check_bounded_wait": [ctypes.c_longlong, ctypes.POINTER(_i)],
     "dh_server_create": [ctypes.c_size_t, _i, ctypes.POINTER(_p)],
     "dh_server_submit": [_p, ctypes.POINTER(dh_request), ctypes.POINTER(ctypes.c_uint64)],
     "dh_server_wait": [_p, ctypes.c_uint64, _i],
@@ -180,6 +183,10 @@ def dh_set_basis(h: int, pol: int, waist: float, group_count: int) -> None:
     _check(_lib.dh_set_basis(h, pol, waist, group_count))
 
 
+def dh_set_fill_factor_correction(h: int, enabled: bool) -> None:
+    _check(_lib.dh_set_fill_factor_correction(h, 1 if enabled else 0))
+
+
 def dh_set_precision(h: int, precision: int) -> None:
     _check(_lib.dh_set_precision(h, precision))
 
@@ -216,6 +223,20 @@ def dh_process_batch_noalloc(h: int, frames, dtype: int, batch: int, fields=None
 def dh_score_settings(h: int, frames, dtype: int, batch: int, settings, power, stream=None) -> None:
     arr = (dh_setting * len(settings))(*settings)
     _check(_lib.dh_score_settings(h, _ptr(frames), dtype, batch, arr, len(settings), _ptr(power), _stream(stream)))
+
+
+def dh_get_device_status(h: int) -> int:
+    """Bits of the handle's device status word since the last call (0: no bounded wait ran out)."""
+    st = _i()
+    _check(_lib.dh_get_device_status(h, ctypes.byref(st)))
+    return st.value
+
+
+def dh_check_bounded_wait(limit: int) -> bool:
+    """Run the kernels' bounded mbarrier wait on a barrier nothing completes; True when it expired."""
+    ex = _i()
+    _check(_lib.dh_check_bounded_wait(limit, ctypes.byref(ex)))
+    return bool(ex.value)
 
 
 def dh_set_profiling(h: int, enable: bool) -> None:
@@ -294,6 +315,7 @@ def configure(h: int, setup) -> None:
         dh_set_defocus(h, p, setup.defocus[p])
         dh_set_basis(h, p, setup.waist[p], setup.group_count)
     dh_set_precision(h, getattr(setup, "precision", DH_PRECISION_FP32))
+    dh_set_fill_factor_correction(h, bool(getattr(setup, "fill_factor", False)))
 
 
 class Reconstructor:

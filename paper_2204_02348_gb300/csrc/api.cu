@@ -471,6 +471,13 @@ int dh_set_basis(dh_handle h, int pol, double waist, int group_count) {
     return DH_SUCCESS;
 }
 
+int dh_set_fill_factor_correction(dh_handle h, int enabled) {
+    GET_HANDLE(h);
+    H->s.fill_factor = enabled != 0;
+    H->dirty = true;
+    return DH_SUCCESS;
+}
+
 int dh_set_precision(dh_handle h, int precision) {
     GET_HANDLE(h);
     if (precision != DH_PRECISION_FP32 && precision != DH_PRECISION_SPLIT_BF16)

@@ -24,6 +24,7 @@
 
 #include "fft.cuh"
 #include "runtime.hpp"
+#include "sync.cuh"
 
 namespace dhk {
 
@@ -64,19 +65,7 @@ struct FusedLayout {
     static constexpr size_t bytes = STG + (size_t)F2 * sizeof(float2) + (size_t)FL * sizeof(float) + (size_t)IN * sizeof(int);
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) {
-    uint32_t done = 0;
-    for (long it = 0; it < kFWaitLimit && !done; ++it) {
-        asm volatile(
-            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(mbar), "r"(parity)
-            : "memory");
-    }
-    return done != 0;
-}
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity) { return bounded_mbar_wait(mbar, parity, kFWaitLimit); }
 
 // One thread: expect the window's bytes on the mbarrier and start the tensor copy of frame f.
 __device__ __forceinline__ void stage_window(const CUtensorMap* tmap, uint32_t dst, uint32_t mbar, int x0, int y0, int f,

@@ -21,6 +21,7 @@
 
 #include "fft.cuh"
 #include "kernels.cuh"
+#include "sync.cuh"
 
 namespace dhk {
 
@@ -32,7 +33,7 @@ constexpr int kTcMaxM = 192;         // shared-memory bound of this kernel
 constexpr int kTmemCols = 32;
 constexpr long kWaitLimit = 1L << 24;
 
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return smem_u32(p); }
 
 __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
     uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
@@ -49,17 +50,7 @@ __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, 
         "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
 }
 
-__device__ __forceinline__ bool wait_parity(uint32_t mbar, uint32_t parity) {
-    uint32_t done = 0;
-    for (long it = 0; it < kWaitLimit && !done; ++it) {
-        asm volatile(
-            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(done)
-            : "r"(mbar), "r"(parity)
-            : "memory");
-    }
-    return done != 0;
-}
+__device__ __forceinline__ bool wait_parity(uint32_t mbar, uint32_t parity) { return bounded_mbar_wait(mbar, parity, kWaitLimit); }
 
 __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* out) {
     uint32_t v[16];

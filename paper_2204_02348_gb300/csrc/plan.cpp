@@ -163,7 +163,13 @@ void build_tables(const Settings& s, const Geometry& g, Tables* t) {
             const double sgn = (a.klo % 2 == 0) ? 1.0 : -1.0;
             for (int q = 0; q < m; ++q) {
                 const double ang = -2.0 * kPi * (double)(a.klo + q) * a.eps / n;
-                push_c(*ph[ax], sgn * std::cos(ang) / n, sgn * std::sin(ang) / n);
+                double w = sgn / n;
+                if (s.fill_factor) {
+                    // 100 % fill factor: divide by the pixel response sinc(k / N) of this axis
+                    const double u = kPi * (double)(a.klo + q) / n;
+                    w /= (u == 0.0) ? 1.0 : std::sin(u) / u;
+                }
+                push_c(*ph[ax], w * std::cos(ang), w * std::sin(ang));
             }
             for (int i = 0; i < m; ++i) {
                 const double ang = -2.0 * kPi * (a.kappa - a.k0) * (double)(i - m / 2) / m

@@ -27,6 +27,7 @@ struct Settings {
     double waist[DH_MAX_POLS] = {100e-6, 100e-6};
     int groups = 0;
     int precision = DH_PRECISION_FP32;
+    int fill_factor = 0;                 // divide the window by the pixel response sinc(k/N) per axis
 };
 
 // Geometry of one axis of one polarisation (all FP64, computed as the conventions in digholo.h state).

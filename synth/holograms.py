@@ -65,6 +65,7 @@ class Setup:
     peak_counts: float = 4000.0
     pixel: float = PIXEL
     wavelength: float = WAVELENGTH
+    fill_factor: bool = False                    # reconstruct with the pixel-response (fill-factor) correction
     extra: dict = field(default_factory=dict)
 
     @property

@@ -279,3 +279,36 @@ def test_planted_spectrum_sign_fails_fft_pin(monkeypatch):
     f = orc.window_spectrum(win, g, bins_x=bins, bins_y=bins)
     ref = ((-1.0) ** (bins[:, None] + bins[None, :])) * np.fft.fft2(win)[np.ix_(bins % n, bins % n)]
     assert np.max(np.abs(f - ref)) > 1e-3 * np.max(np.abs(ref))
+
+
+def _box_integrated_case(n=64, m=32, centre=(40.37, 39.81), kappa=(12.3, 10.7), r=9.0, dioptre=0.0, a_r=2.0, seed=8):
+    """Linear hologram of a trigonometric-polynomial cross term recorded by pixels that integrate over their
+    whole width: every component exp(2 pi i k.x / (N px)) is multiplied by sinc(k_x/N) sinc(k_y/N)."""
+    rng = np.random.default_rng(seed)
+    g = _geom(n=n, m=m, centre=centre, kappa=kappa, r=r, defocus=dioptre)
+    k0 = np.array([g.x.k0, g.y.k0])
+    kap = np.array(kappa)
+    qs = [(qx, qy) for qx in range(-3, 4) for qy in range(-3, 4)
+          if ((k0[0] + qx - kap[0]) ** 2 + (k0[1] + qy - kap[1]) ** 2) <= (0.9 * r) ** 2]
+    amps = rng.standard_normal(len(qs)) + 1j * rng.standard_normal(len(qs))
+    X = np.arange(80)[None, :] * PX - g.x.centre
+    Y = np.arange(80)[:, None] * PX - g.y.centre
+    cross = np.zeros((80, 80), dtype=complex)
+    for (qx, qy), a in zip(qs, amps):
+        kx, ky = k0[0] + qx, k0[1] + qy
+        cross += a * np.sinc(kx / n) * np.sinc(ky / n) * np.exp(2j * np.pi * (kx * X + ky * Y) / (n * PX))
+    frame = a_r ** 2 + 2.0 * np.real(a_r * cross)
+    xp, yp = orc.output_axes(g)
+    res = np.exp(-2j * np.pi * ((kap[0] - k0[0]) * xp[None, :] + (kap[1] - k0[1]) * yp[:, None]) / (n * PX))
+    p = sum(a * np.exp(2j * np.pi * (qx * xp[None, :] + qy * yp[:, None]) / (n * PX)) for (qx, qy), a in zip(qs, amps))
+    return g, frame, a_r * p * res
+
+
+def test_fill_factor_correction_recovers_box_integrated_signal():
+    g, frame, expected = _box_integrated_case()
+    g.fill_factor = True
+    _, _, e, _ = orc.process_window(frame, g)
+    assert np.linalg.norm(e - expected) / np.linalg.norm(expected) < 1e-10
+    g.fill_factor = False
+    _, _, e2, _ = orc.process_window(frame, g)
+    assert np.linalg.norm(e2 - expected) / np.linalg.norm(expected) > 1e-3

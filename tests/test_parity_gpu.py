@@ -276,3 +276,13 @@ def test_score_candidates_outside_one_superset_fall_back():
     ref = orc.score_settings(d["frames"], s, cand["tilt_deg"], cand["defocus"], cand["waist"])
     got = _score(s, d["frames"], cand)
     assert np.all(np.abs(got - ref) / ref <= 2 * COEF_TOL), (got, ref)
+
+
+def test_fill_factor_correction_parity():
+    s = syn.with_(syn.setup_batching(), fill_factor=True)
+    d = syn.make_frames(s, 3, seed=80)
+    _check(s, d["frames"], run_library(s, d["frames"]))                # fused path
+    _check(s, d["frames"], run_library(s, d["frames"], window=True))   # generic path
+    s2 = syn.with_(syn.setup_precision(), fill_factor=True)
+    d2 = syn.make_frames(s2, 1, seed=81)
+    _check(s2, d2["frames"], run_library(s2, d2["frames"]))
