@@ -14,7 +14,9 @@ in float64 / complex128, with numpy matrix products as the only library primitiv
 4. the reduced-size inverse transform with the residual tilt and the defocus removed
    (pipeline step 2, digHoloConfigSetIFFTResolutionMode, digHoloProcessRemoveTilt, digHoloConfigSetDefocus);
 5. the Hermite-Gaussian basis by its three-term recurrence and the overlap sums
-   (pipeline step 3, digHoloConfigSetBasisGroupCount, digHoloConfigSetBasisWaist);
+   (pipeline step 3, digHoloConfigSetBasisGroupCount, digHoloConfigSetBasisWaist); Laguerre-Gaussian
+   overlaps by direct sums with LG modes from Laguerre polynomials, and custom bases as a matrix applied to
+   the HG overlaps (digHoloConfigSetBasisType*);
 6. total captured power per alignment candidate (the quantity the AutoAlign search scores).
 
 Conventions the paper leaves open (the same readings are used by the CUDA library):
@@ -258,6 +260,49 @@ def overlap(e: np.ndarray, g: PolGeometry) -> np.ndarray:
     return np.array([full[n, m] for (m, n) in mode_list(g.groups)])
 
 
+def lg_mode_list(groups: int) -> List[Tuple[int, int]]:
+    """Laguerre-Gaussian (p, l) with mode group N = 2p + |l| < groups, ordered by group, then l ascending
+    (-N, -N+2, ..., N); the same count per group as the HG basis (digHoloConfigSetBasisTypeLG)."""
+    out = []
+    for n_grp in range(groups):
+        for l in range(-n_grp, n_grp + 1, 2):
+            out.append(((n_grp - abs(l)) // 2, l))
+    return out
+
+
+def lg_2d(p: int, l: int, x: np.ndarray, y: np.ndarray, waist: float) -> np.ndarray:
+    """LG_p^l(x, y) = sqrt(2 p! / (pi (p+|l|)!)) / w (sqrt(2) r / w)^|l| L_p^|l|(2 r^2 / w^2) exp(-r^2/w^2)
+    exp(i l phi), L the generalised Laguerre polynomial (scipy.special.eval_genlaguerre), L2-normalised;
+    returned as [len(y)][len(x)]."""
+    from scipy.special import eval_genlaguerre
+    X, Y = np.meshgrid(np.asarray(x, dtype=np.float64), np.asarray(y, dtype=np.float64))
+    r2 = X * X + Y * Y
+    c = math.sqrt(2.0 * math.factorial(p) / (math.pi * math.factorial(p + abs(l)))) / waist
+    radial = (2.0 * r2 / waist ** 2) ** (abs(l) / 2.0) * eval_genlaguerre(p, abs(l), 2.0 * r2 / waist ** 2)
+    return c * radial * np.exp(-r2 / waist ** 2) * np.exp(1j * l * np.arctan2(Y, X))
+
+
+def overlap_lg(e: np.ndarray, g: PolGeometry) -> np.ndarray:
+    """c_pl = dx' dy' sum_ij conj(LG_p^l(x'_i, y'_j)) E(x'_i, y'_j) by direct sums over the field grid."""
+    xp, yp = output_axes(g)
+    return np.array([np.sum(np.conj(lg_2d(p, l, xp, yp, g.waist)) * e) * g.x.dx * g.y.dx
+                     for (p, l) in lg_mode_list(g.groups)])
+
+
+def basis_coefficients(e: np.ndarray, g: PolGeometry, basis: str = "hg", transform=None) -> np.ndarray:
+    """Coefficients in the chosen basis: HG overlaps, LG overlaps, or a custom matrix applied to the HG
+    overlaps (digHoloConfigSetBasisTypeCustom: transform is [modes_out][modes_in], columns beyond the HG mode
+    count are unused)."""
+    if basis == "hg":
+        return overlap(e, g)
+    if basis == "lg":
+        return overlap_lg(e, g)
+    c = overlap(e, g)
+    t = np.asarray(transform, dtype=np.complex128)
+    k = min(t.shape[1], c.shape[0])
+    return t[:, :k] @ c[:k]
+
+
 # ---------------------------------------------------------------------------------------------------
 # Whole path
 # ---------------------------------------------------------------------------------------------------
@@ -274,10 +319,13 @@ def process_window(frame: np.ndarray, g: PolGeometry):
 
 def process_batch(frames: np.ndarray, setup) -> Tuple[np.ndarray, np.ndarray]:
     """digHoloProcessBatch: fields [B][P][M][M] and coefficients [B][P][modes] (pol-blocked, as
-    digHoloBasisGetCoefs lays them out)."""
+    digHoloBasisGetCoefs lays them out), in the setup's basis (attribute basis: "hg" default, "lg", or
+    "custom" with attribute basis_transform)."""
     geos = [pol_geometry(setup, p) for p in range(setup.pol_count)]
     m = geos[0].x.m
-    modes = len(mode_list(geos[0].groups))
+    basis = getattr(setup, "basis", "hg")
+    transform = getattr(setup, "basis_transform", None)
+    modes = np.asarray(transform).shape[0] if basis == "custom" else len(mode_list(geos[0].groups))
     B = frames.shape[0]
     fields = np.empty((B, setup.pol_count, m, m), dtype=np.complex128)
     coefs = np.empty((B, setup.pol_count, modes), dtype=np.complex128)
@@ -285,7 +333,7 @@ def process_batch(frames: np.ndarray, setup) -> Tuple[np.ndarray, np.ndarray]:
         for p, g in enumerate(geos):
             _, _, e, c = process_window(frames[b], g)
             fields[b, p] = e
-            coefs[b, p] = c
+            coefs[b, p] = c if basis == "hg" else basis_coefficients(e, g, basis, transform)
     return fields, coefs
 
 

@@ -66,6 +66,8 @@ class Setup:
     pixel: float = PIXEL
     wavelength: float = WAVELENGTH
     fill_factor: bool = False                    # reconstruct with the pixel-response (fill-factor) correction
+    basis: str = "hg"                            # coefficient basis: "hg", "lg" or "custom"
+    basis_transform: object = None               # custom basis: complex matrix [modes_out][modes_in]
     extra: dict = field(default_factory=dict)
 
     @property

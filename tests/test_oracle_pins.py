@@ -312,3 +312,47 @@ def test_fill_factor_correction_recovers_box_integrated_signal():
     g.fill_factor = False
     _, _, e2, _ = orc.process_window(frame, g)
     assert np.linalg.norm(e2 - expected) / np.linalg.norm(expected) > 1e-3
+
+
+# ----------------------------------------------------------------------------- LG and custom bases
+
+
+def test_lg_modes_orthonormal_and_textbook_low_orders():
+    w = 1.0
+    x = (np.arange(320) - 160) * (w / 16)
+    modes = orc.lg_mode_list(5)
+    assert len(modes) == 15 and modes[:6] == [(0, 0), (0, -1), (0, 1), (0, -2), (1, 0), (0, 2)]
+    L = np.array([orc.lg_2d(p, l, x, x, w).ravel() for (p, l) in modes])
+    gram = np.conj(L) @ L.T * (w / 16) ** 2
+    assert np.max(np.abs(gram - np.eye(len(modes)))) < 1e-10
+    u = orc.hg_1d(3, x, w)
+    hg = lambda m, n: u[n][:, None] * u[m][None, :]
+    assert np.max(np.abs(orc.lg_2d(0, 0, x, x, w) - hg(0, 0))) < 1e-12
+    # LG_0^{+-1} = (HG_10 +- i HG_01) / sqrt(2): exp(+- i phi) r exp(-r^2/w^2) is proportional to x +- i y
+    for l in (1, -1):
+        ref = (hg(1, 0) + 1j * l * hg(0, 1)) / math.sqrt(2.0)
+        assert np.max(np.abs(orc.lg_2d(0, l, x, x, w) - ref)) < 1e-12
+
+
+def test_lg_overlap_recovers_single_mode_on_fine_grid():
+    n = m = 256
+    g = _geom(n=n, m=m, centre=(128.0, 128.0), kappa=(60.0, 60.0), r=10.0, waist=8 * n * PX / m, groups=5)
+    xp, yp = orc.output_axes(g)
+    modes = orc.lg_mode_list(5)
+    for (p, l) in [(1, 2), (0, -3), (2, 0)]:
+        e = (0.5 + 2j) * orc.lg_2d(p, l, xp, yp, g.waist)
+        c = orc.overlap_lg(e, g)
+        target = np.zeros(len(modes), dtype=complex)
+        target[modes.index((p, l))] = 0.5 + 2j
+        assert np.max(np.abs(c - target)) < 1e-10
+
+
+def test_custom_basis_is_the_matrix_applied_to_hg_overlaps():
+    rng = np.random.default_rng(12)
+    g = _geom(n=64, m=32, centre=(32.0, 32.0), kappa=(14.0, 12.0), r=8.0, waist=200e-6, groups=4)
+    e = rng.standard_normal((32, 32)) + 1j * rng.standard_normal((32, 32))
+    t = rng.standard_normal((5, 12)) + 1j * rng.standard_normal((5, 12))   # more inputs than the 10 HG modes
+    c = orc.basis_coefficients(e, g, "custom", t)
+    assert c.shape == (5,)
+    assert np.allclose(c, t[:, :10] @ orc.overlap(e, g), rtol=1e-13, atol=0)
+    assert np.allclose(orc.basis_coefficients(e, g, "custom", np.eye(10)), orc.overlap(e, g), rtol=1e-14, atol=0)
