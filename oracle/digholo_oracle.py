@@ -17,7 +17,9 @@ in float64 / complex128, with numpy matrix products as the only library primitiv
    (pipeline step 3, digHoloConfigSetBasisGroupCount, digHoloConfigSetBasisWaist); Laguerre-Gaussian
    overlaps by direct sums with LG modes from Laguerre polynomials, and custom bases as a matrix applied to
    the HG overlaps (digHoloConfigSetBasisType*);
-6. total captured power per alignment candidate (the quantity the AutoAlign search scores).
+6. total captured power per alignment candidate (the quantity the AutoAlign search scores);
+7. batch averaging (digHoloSetBatchAvg, "Averaging modes"): the windows of the frames of one averaging
+   group, rotated into phase with the group's first frame, averaged, then inverse transformed once.
 
 Conventions the paper leaves open (the same readings are used by the CUDA library):
 
@@ -334,6 +336,68 @@ def process_batch(frames: np.ndarray, setup) -> Tuple[np.ndarray, np.ndarray]:
             _, _, e, c = process_window(frames[b], g)
             fields[b, p] = e
             coefs[b, p] = c if basis == "hg" else basis_coefficients(e, g, basis, transform)
+    return fields, coefs
+
+
+# ---------------------------------------------------------------------------------------------------
+# Batch averaging (digHoloSetBatchAvg, digHoloConfigSetBatchAvgCount, "Averaging modes")
+# ---------------------------------------------------------------------------------------------------
+
+
+def avg_member_index(group: int, member: int, batch: int, avg_count: int, avg_mode: int) -> int:
+    """Frame index of member j of averaging group g: sequential blocks [A A A B B B] (mode 0, and mode 2,
+    which equals mode 0 with a single wavelength) at g avg_count + j, interlaced [A B A B] (mode 1) at
+    j batch + g."""
+    if avg_mode == 1:
+        return member * batch + group
+    return group * avg_count + member
+
+
+def align_phases(windows) -> np.ndarray:
+    """Unit phasors a_j that bring the windows of one group in phase with its first member: with
+    <W_0, W_j> = sum over polarisations and bins of conj(W_0) W_j, a_j = conj(<W_0, W_j>) / |<W_0, W_j>|
+    (1 when the inner product vanishes), so that arg <W_0, a_j W_j> = 0.  windows: [A][P][...]."""
+    out = np.ones(len(windows), dtype=np.complex128)
+    for j in range(len(windows)):
+        d = sum(np.vdot(windows[0][p], windows[j][p]) for p in range(len(windows[0])))
+        if d != 0:
+            out[j] = np.conj(d) / abs(d)
+    return out
+
+
+def process_batch_avg(frames: np.ndarray, setup, avg_count: int, avg_mode: int = 0):
+    """Averaged reconstruction of batch = len(frames) / avg_count fields: per group, every member's kept
+    window (after the fill-factor correction when enabled, i.e. the spectrum that is inverse transformed)
+    is phase-aligned with the first member's by align_phases, the aligned windows are averaged, and the
+    average is inverse transformed and decomposed once.  Returns fields [batch][P][M][M] and coefficients
+    [batch][P][modes] in the setup's basis."""
+    geos = [pol_geometry(setup, p) for p in range(setup.pol_count)]
+    A = max(int(avg_count), 1)
+    B = frames.shape[0] // A
+    m = geos[0].x.m
+    basis = getattr(setup, "basis", "hg")
+    transform = getattr(setup, "basis_transform", None)
+    modes = np.asarray(transform).shape[0] if basis == "custom" else len(mode_list(geos[0].groups))
+    fields = np.empty((B, setup.pol_count, m, m), dtype=np.complex128)
+    coefs = np.empty((B, setup.pol_count, modes), dtype=np.complex128)
+    masks = [window_mask(g) for g in geos]
+    corr = []
+    for g in geos:
+        if g.fill_factor:
+            corr.append(1.0 / np.outer(pixel_response(g.y, box_bins(g.y)), pixel_response(g.x, box_bins(g.x))))
+        else:
+            corr.append(np.ones((m, m)))
+    for b in range(B):
+        boxes = []
+        for j in range(A):
+            fr = frames[avg_member_index(b, j, B, A, avg_mode)]
+            boxes.append([window_spectrum(cut_window(fr, g), g) * masks[p] for p, g in enumerate(geos)])
+        a = align_phases([[boxes[j][p] * corr[p] for p in range(len(geos))] for j in range(A)])
+        for p, g in enumerate(geos):
+            avg = sum(a[j] * boxes[j][p] for j in range(A)) / A
+            e = reconstruct_field(avg, masks[p], g)
+            fields[b, p] = e
+            coefs[b, p] = overlap(e, g) if basis == "hg" else basis_coefficients(e, g, basis, transform)
     return fields, coefs
 
 

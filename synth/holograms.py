@@ -252,27 +252,12 @@ def _haar_cache(seed: int, p: int, k: int) -> np.ndarray:
     return _HAAR[key]
 
 
-def make_frames(setup: Setup, count: int, seed: int = BASE_SEED, first: int = 0):
-    """Generate frames ``first .. first+count-1`` of the seeded stream for ``setup``.
-
-    Returns a dict with
-      frames      : [count][H][W] uint16 (12-bit, Poisson) or float32 (Gaussian noise, peak 1),
-      coefs_true  : [count][P][signal_modes] complex128 signal coefficients,
-      field_scale : [count][P] float64, the factor A_R * (intensity scale) that multiplies S in the
-                    linear cross term, so an ideal reconstruction returns field_scale * S.
-    """
+def _pol_tables(setup: Setup):
+    """Per-polarisation reference wave R and HG tables on the frame grid (independent of the frame)."""
     H, W, P = setup.frame_h, setup.frame_w, setup.pol_count
     strip = W // P
     px, lam = setup.pixel, setup.wavelength
-    out_dtype = np.uint16 if setup.dtype == "u16" else np.float32
-    frames = np.empty((count, H, W), dtype=out_dtype)
-    coefs = np.empty((count, P, setup.signal_modes), dtype=np.complex128)
-    fscale = np.empty((count, P), dtype=np.float64)
-    modes = mode_indices(setup.signal_groups)
-    mi = np.array([m for m, _ in modes])
-    ni = np.array([n for _, n in modes])
     ys = np.arange(H) * px
-    # per-polarisation reference and basis tables (independent of the frame)
     pol_tabs = []
     for p in range(P):
         cx, cy = setup.beam_centre[p]
@@ -286,31 +271,88 @@ def make_frames(setup: Setup, count: int, seed: int = BASE_SEED, first: int = 0)
         ux = hg_closed_form(setup.signal_groups, X, setup.waist[p])   # [G][strip]
         uy = hg_closed_form(setup.signal_groups, Y, setup.waist[p])   # [G][H]
         pol_tabs.append((ry[:, None] * rx[None, :], ux, uy))
+    return pol_tabs
+
+
+def _render(setup: Setup, pol_tabs, coefs_p, rng: np.random.Generator, ref_phase: float = 0.0):
+    """One camera frame |S + A_R R exp(i ref_phase)|^2 with the setup's noise; returns (frame, field_scale[P])."""
+    H, W, P = setup.frame_h, setup.frame_w, setup.pol_count
+    strip = W // P
+    modes = mode_indices(setup.signal_groups)
+    mi = np.array([m for m, _ in modes])
+    ni = np.array([n for _, n in modes])
+    inten = np.empty((H, W), dtype=np.float64)
+    amps = []
+    rot = complex(math.cos(ref_phase), math.sin(ref_phase))
+    for p in range(P):
+        R, ux, uy = pol_tabs[p]
+        C = np.zeros((setup.signal_groups, setup.signal_groups), dtype=np.complex128)
+        C[ni, mi] = coefs_p[p]                          # C[n][m]
+        S = uy.T @ C @ ux                               # [H][strip]
+        a_r = float(np.abs(S).max())
+        amps.append(a_r)
+        inten[:, p * strip:(p + 1) * strip] = np.abs(S + a_r * rot * R) ** 2
+    peak = inten.max()
+    if setup.dtype == "u16":
+        scale = setup.peak_counts / peak
+        counts = rng.poisson(inten * scale)
+        frame = np.clip(counts, 0, 4095).astype(np.uint16)
+    else:
+        scale = 1.0 / peak
+        frame = (inten * scale + rng.normal(0.0, 1e-3, size=inten.shape)).astype(np.float32)
+    return frame, np.array(amps) * scale
+
+
+def make_frames(setup: Setup, count: int, seed: int = BASE_SEED, first: int = 0):
+    """Generate frames ``first .. first+count-1`` of the seeded stream for ``setup``.
+
+    Returns a dict with
+      frames      : [count][H][W] uint16 (12-bit, Poisson) or float32 (Gaussian noise, peak 1),
+      coefs_true  : [count][P][signal_modes] complex128 signal coefficients,
+      field_scale : [count][P] float64, the factor A_R * (intensity scale) that multiplies S in the
+                    linear cross term, so an ideal reconstruction returns field_scale * S.
+    """
+    H, W, P = setup.frame_h, setup.frame_w, setup.pol_count
+    out_dtype = np.uint16 if setup.dtype == "u16" else np.float32
+    frames = np.empty((count, H, W), dtype=out_dtype)
+    coefs = np.empty((count, P, setup.signal_modes), dtype=np.complex128)
+    fscale = np.empty((count, P), dtype=np.float64)
+    pol_tabs = _pol_tables(setup)
     for i in range(count):
         b = first + i
         rng = np.random.default_rng([seed, b])
-        inten = np.empty((H, W), dtype=np.float64)
-        amps = []
         for p in range(P):
-            R, ux, uy = pol_tabs[p]
-            c = _signal_coefs(setup, b, p, rng, seed)
-            coefs[i, p] = c
-            C = np.zeros((setup.signal_groups, setup.signal_groups), dtype=np.complex128)
-            C[ni, mi] = c                                   # C[n][m]
-            S = uy.T @ C @ ux                               # [H][strip]
-            a_r = float(np.abs(S).max())
-            amps.append(a_r)
-            inten[:, p * strip:(p + 1) * strip] = np.abs(S + a_r * R) ** 2
-        peak = inten.max()
-        if setup.dtype == "u16":
-            scale = setup.peak_counts / peak
-            counts = rng.poisson(inten * scale)
-            frames[i] = np.clip(counts, 0, 4095).astype(np.uint16)
-        else:
-            scale = 1.0 / peak
-            frames[i] = (inten * scale + rng.normal(0.0, 1e-3, size=inten.shape)).astype(np.float32)
-        fscale[i] = np.array(amps) * scale
+            coefs[i, p] = _signal_coefs(setup, b, p, rng, seed)
+        frames[i], fscale[i] = _render(setup, pol_tabs, coefs[i], rng)
     return {"frames": frames, "coefs_true": coefs, "field_scale": fscale}
+
+
+def make_avg_frames(setup: Setup, batch: int, avg_count: int, avg_mode: int, seed: int = BASE_SEED,
+                    drift: float = math.pi):
+    """Frames for averaged processing: ``batch`` distinct fields, each measured ``avg_count`` times with
+    independent noise and a reference phase drawn uniformly from [-drift, drift] per measurement (the drift
+    that phase-aligned averaging removes).  Arranged as the averaging modes lay them out: sequential blocks
+    (mode 0, and mode 2 with a single wavelength) [A A A B B B], or interlaced (mode 1) [A B A B A B].
+
+    Returns a dict with frames [batch * avg_count][H][W], coefs_true [batch][P][signal_modes],
+    ref_phase [batch][avg_count] and field_scale [batch][avg_count][P].
+    """
+    H, W, P = setup.frame_h, setup.frame_w, setup.pol_count
+    out_dtype = np.uint16 if setup.dtype == "u16" else np.float32
+    frames = np.empty((batch * avg_count, H, W), dtype=out_dtype)
+    coefs = np.empty((batch, P, setup.signal_modes), dtype=np.complex128)
+    phase = np.empty((batch, avg_count), dtype=np.float64)
+    fscale = np.empty((batch, avg_count, P), dtype=np.float64)
+    pol_tabs = _pol_tables(setup)
+    for g in range(batch):
+        rng = np.random.default_rng([seed, g, 3])
+        for p in range(P):
+            coefs[g, p] = _signal_coefs(setup, g, p, rng, seed)
+        for j in range(avg_count):
+            phase[g, j] = float(rng.uniform(-drift, drift))
+            at = g * avg_count + j if avg_mode != 1 else j * batch + g
+            frames[at], fscale[g, j] = _render(setup, pol_tabs, coefs[g], rng, phase[g, j])
+    return {"frames": frames, "coefs_true": coefs, "ref_phase": phase, "field_scale": fscale}
 
 
 def candidate_settings(setup: Setup, count: int = 64, seed: int = BASE_SEED + 5):

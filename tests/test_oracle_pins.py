@@ -356,3 +356,73 @@ def test_custom_basis_is_the_matrix_applied_to_hg_overlaps():
     assert c.shape == (5,)
     assert np.allclose(c, t[:, :10] @ orc.overlap(e, g), rtol=1e-13, atol=0)
     assert np.allclose(orc.basis_coefficients(e, g, "custom", np.eye(10)), orc.overlap(e, g), rtol=1e-14, atol=0)
+
+
+# ----------------------------------------------------------------------------- batch averaging
+
+
+def test_avg_member_layouts():
+    # sequential [A A A B B B]: group 1 of 2, 3 per group -> frames 3, 4, 5; interlaced [A B A B A B] -> 1, 3, 5
+    assert [orc.avg_member_index(1, j, 2, 3, 0) for j in range(3)] == [3, 4, 5]
+    assert [orc.avg_member_index(1, j, 2, 3, 2) for j in range(3)] == [3, 4, 5]
+    assert [orc.avg_member_index(1, j, 2, 3, 1) for j in range(3)] == [1, 3, 5]
+
+
+def test_align_phases_hand_example_and_pure_rotation():
+    # W_0 = [1, 0], W_1 = [i, 1]: <W_0, W_1> = i, so W_1 is rotated by -i -> [1, -i]; average [1, -i/2]
+    w = [[np.array([1.0 + 0j, 0.0])], [np.array([1j, 1.0 + 0j])]]
+    a = orc.align_phases(w)
+    assert np.allclose(a, [1.0, -1j], atol=1e-15)
+    assert np.allclose((a[0] * w[0][0] + a[1] * w[1][0]) / 2, [1.0, -0.5j], atol=1e-15)
+    # copies of one window rotated by arbitrary phases average back to the first copy exactly
+    rng = np.random.default_rng(31)
+    base = [rng.standard_normal((4, 4)) + 1j * rng.standard_normal((4, 4)) for _ in range(2)]
+    th = np.array([0.0, 2.5, -1.2, 3.1])
+    group = [[np.exp(1j * t) * base[p] for p in range(2)] for t in th]
+    a = orc.align_phases(group)
+    assert np.allclose(a, np.exp(-1j * th), atol=1e-14)
+    # a zero window (no light) keeps phasor 1
+    assert orc.align_phases([[np.ones(3)], [np.zeros(3)]])[1] == 1.0
+
+
+def test_avg_count_one_is_plain_processing_and_modes_agree():
+    s = syn.setup_batching()
+    d = syn.make_frames(s, 3, seed=40)
+    f1, c1 = orc.process_batch(d["frames"], s)
+    fa, ca = orc.process_batch_avg(d["frames"], s, 1, 0)
+    assert np.allclose(fa, f1, rtol=0, atol=1e-12 * np.abs(f1).max())
+    assert np.allclose(ca, c1, rtol=0, atol=1e-12 * np.abs(c1).max())
+    # the same frames laid out interlaced give the same averages as the sequential layout
+    dd = syn.make_avg_frames(s, 2, 3, 0, seed=41)
+    seq = dd["frames"]
+    inter = np.stack([seq[g * 3 + j] for j in range(3) for g in range(2)])
+    fs, _ = orc.process_batch_avg(seq, s, 3, 0)
+    fi, _ = orc.process_batch_avg(inter, s, 3, 1)
+    assert np.array_equal(fs, fi)
+
+
+def test_avg_of_identical_frames_and_drift_removal():
+    s = syn.setup_batching()
+    d = syn.make_frames(s, 1, seed=42)
+    f1, _ = orc.process_batch(d["frames"], s)
+    fa, _ = orc.process_batch_avg(np.repeat(d["frames"], 4, axis=0), s, 4, 0)
+    assert np.allclose(fa, f1, rtol=0, atol=1e-12 * np.abs(f1).max())
+    # one field measured 6 times with reference drift: the aligned average stays close to the true field
+    # (times the first member's phase), closer than a single noisy measurement, while the plain mean of the
+    # drifting fields loses most of its amplitude
+    dd = syn.make_avg_frames(s, 1, 6, 0, seed=43)
+    fa, _ = orc.process_batch_avg(dd["frames"], s, 6, 0)
+    singles, _ = orc.process_batch(dd["frames"], s)
+    g0 = orc.pol_geometry(s, 0)
+    xp, yp = orc.output_axes(g0)
+    true = np.zeros((len(yp), len(xp)), dtype=complex)
+    u_x = syn.hg_closed_form(s.signal_groups, xp, s.waist[0])
+    u_y = syn.hg_closed_form(s.signal_groups, yp, s.waist[0])
+    for k, (m, n) in enumerate(syn.mode_indices(s.signal_groups)):
+        true += dd["coefs_true"][0, 0, k] * np.outer(u_y[n], u_x[m])
+    def err(e):   # relative error after the best global phase
+        z = np.vdot(true, e)
+        return np.linalg.norm(e * np.conj(z) / abs(z) / np.linalg.norm(e) - true / np.linalg.norm(true))
+    assert err(fa[0, 0]) < min(err(singles[j, 0]) for j in range(6))
+    plain_mean = singles[:, 0].mean(axis=0)
+    assert np.linalg.norm(plain_mean) < 0.8 * np.linalg.norm(fa[0, 0])
