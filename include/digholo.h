@@ -19,7 +19,8 @@
  *     E = (1/N^2) sum_q F(k0+q) exp(2 pi i q.x'/(N px)) exp(-2 pi i (kappa-k0).x'/(N px)) exp(-i pi D |x'|^2/lambda);
  *   - coefficients are complex64 [batch][pol][modes], polarisation-blocked ("HHHHHVVVVV", as
  *     digHoloBasisGetCoefs lays them out); modes HG(m, n) with m + n < G, ordered by group g = m + n, then m
- *     ascending; c_mn = dx' dy' sum_ij u_m(x'_i) u_n(y'_j) E_ji with L2-normalised real u_n.
+ *     ascending; c_mn = dx' dy' sum_ij u_m(x'_i) u_n(y'_j) E_ji with L2-normalised real u_n (other bases:
+ *     dh_set_basis_type).
  *
  * Ownership: every device pointer passed in (frames, fields, coefficients, powers) is owned by the caller and
  * must stay valid until the work queued on the given stream has finished.  The library owns only its plan
@@ -62,11 +63,23 @@ extern "C" {
 #define DH_PRECISION_FP32 0
 #define DH_PRECISION_SPLIT_BF16 1
 
+/* Coefficient bases (digHoloConfigSetBasisType): the field is always projected onto the HG modes; LG and
+ * custom coefficients are a matrix applied to the HG coefficients. */
+#define DH_BASIS_HG 0
+#define DH_BASIS_LG 1
+#define DH_BASIS_CUSTOM 2
+
 /* Largest sizes the kernels accept. */
 #define DH_MAX_POLS 2
 #define DH_MAX_WINDOW 1024
 #define DH_MAX_FIELD 512
 #define DH_MAX_GROUPS 32
+#define DH_MAX_AVG_COUNT 4096
+
+/* Averaging modes ("Averaging modes" module): where the avg_count frames of averaging group g sit. */
+#define DH_AVGMODE_SEQUENTIAL 0        /* frames g avg_count + j: [A A A B B B] */
+#define DH_AVGMODE_INTERLACED 1        /* frames j batch + g: [A B A B A B] */
+#define DH_AVGMODE_SEQUENTIALSWEEP 2   /* blocks of wavelength sweeps; one wavelength here, so as SEQUENTIAL */
 
 typedef int dh_handle;
 
@@ -121,13 +134,32 @@ int dh_set_basis(dh_handle h, int pol, double waist, int group_count);
  * Off by default. */
 int dh_set_fill_factor_correction(dh_handle h, int enabled);
 
+/* Coefficient basis (digHoloConfigSetBasisType; "Modal decomposition" module): DH_BASIS_HG, DH_BASIS_LG or
+ * DH_BASIS_CUSTOM.  The field is always decomposed in the separable HG basis; the other bases are a matrix T
+ * applied to each polarisation's HG coefficients on the GPU, c_out[k] = sum_l T[k][l] c_HG[l], FP32.
+ *   - LG: modes LG_p^l with group N = 2p + |l| < G, ordered by group, then l ascending (-N, -N+2, ..., N);
+ *     LG_p^l(r, phi) = sqrt(2 p! / (pi (p+|l|)!)) / w (sqrt(2) r / w)^|l| L_p^|l|(2 r^2/w^2) exp(-r^2/w^2)
+ *     exp(i l phi) with L the generalised Laguerre polynomial, and c_pl = <LG_p^l | E>.  The matrix is built in
+ *     FP64 from the closed-form HG-LG relation; G modes per group, so the count equals the HG count.
+ *   - custom: the matrix set by dh_set_basis_transform.  Selecting DH_BASIS_CUSTOM before any matrix was set
+ *     computes HG coefficients, as the guide states.
+ * Returns DH_ERROR_INVALIDARGUMENT for other values.  dh_get_output_dims reports the coefficient count of the
+ * selected basis; dh_score_settings always scores the HG coefficients. */
+int dh_set_basis_type(dh_handle h, int basis);
+
+/* Custom basis (digHoloConfigSetBasisTypeCustom): copies the host complex64 matrix transform
+ * [modes_out][modes_in] (row-major, interleaved re/im) and selects DH_BASIS_CUSTOM.  Columns beyond the HG mode
+ * count of the current G are unused; HG modes beyond modes_in contribute nothing.  1 <= modes_in, modes_out
+ * and modes_in * modes_out <= 2^24, else DH_ERROR_INVALIDDIMENSION; NULL transform gives DH_ERROR_NULLPOINTER. */
+int dh_set_basis_transform(dh_handle h, int modes_in, int modes_out, const void* transform);
+
 /* Overlap arithmetic: DH_PRECISION_FP32 or DH_PRECISION_SPLIT_BF16. */
 int dh_set_precision(dh_handle h, int precision);
 
-/* Validate the settings and report the output geometry: field size M (square), number of modes, and the
- * field sample pitch dx' = N px / M in metres.  Any pointer may be NULL.  Returns DH_ERROR_INVALIDARGUMENT
- * when a polarisation's window leaves the frame, its tilt centre leaves the half plane 0 < kappa_x <= N/2,
- * or M exceeds N. */
+/* Validate the settings and report the output geometry: field size M (square), number of coefficients per
+ * polarisation in the selected basis, and the field sample pitch dx' = N px / M in metres.  Any pointer may be
+ * NULL.  Returns DH_ERROR_INVALIDARGUMENT when a polarisation's window leaves the frame, its tilt centre leaves
+ * the half plane 0 < kappa_x <= N/2, or M exceeds N. */
 int dh_get_output_dims(dh_handle h, int* m, int* modes, double* dx);
 
 /* Field axes of one polarisation in metres from its beam centre (digHoloGetFields' x and y): host arrays of
@@ -150,6 +182,19 @@ int dh_process_batch(dh_handle h, const void* d_frames, int dtype, int batch, vo
 int dh_process_batch_window(dh_handle h, const void* d_frames, int dtype, int batch, void* d_window,
                             void* d_fields, void* d_coefs, void* stream);
 
+/* Averaged reconstruction (digHoloSetBatchAvg / digHoloSetBatchAvgUint16 followed by digHoloProcessBatch).
+ * d_frames holds batch * avg_count frames laid out as avg_mode says; the frames of each averaging group are
+ * Fourier transformed and windowed, the kept window of member j is multiplied by the unit phasor
+ * a_j = conj(d_j) / |d_j| with d_j = sum over polarisations and kept bins of conj(W_0) W_j (a_0 = 1; a_j = 1
+ * when d_j = 0), so that it is in phase with the group's first member, and the aligned windows are averaged,
+ * (1/avg_count) sum_j a_j W_j (after the fill-factor correction when it is enabled).  One inverse transform,
+ * correction and decomposition per group follow: d_fields [batch][pol][M][M], d_coefs [batch][pol][modes] as
+ * for dh_process_batch.  batch < 1 and avg_count < 1 are treated as 1 (avg_count = 1 is dh_process_batch);
+ * avg_count > DH_MAX_AVG_COUNT gives DH_ERROR_INVALIDDIMENSION and an unknown avg_mode
+ * DH_ERROR_INVALIDARGUMENT.  Always takes the generic multi-kernel path; asynchronous on stream. */
+int dh_process_batch_avg(dh_handle h, const void* d_frames, int dtype, int batch, int avg_count, int avg_mode,
+                         void* d_fields, void* d_coefs, void* stream);
+
 /* Allocation-free variant of dh_process_batch.  The paper has no counterpart (digHolo allocates its own
  * buffers).  It exists for callers that cannot let a library allocate device memory while they process: code
  * whose device memory belongs to another allocator (a framework's caching pool, a serving process that has
@@ -164,7 +209,8 @@ int dh_process_batch_window(dh_handle h, const void* d_frames, int dtype, int ba
  *   - Each call uploads its plan tables with a copy ordered on `stream` (which first waits for the work
  *     already queued on that stream), then processes the batch in chunks that fit the scratch.
  *   - Geometries whose tables exceed 1 MiB, or whose single frame needs more than 15 MiB of scratch, are
- *     rejected with DH_ERROR_INVALIDDIMENSION (the supported limits, N <= 1024 and M <= 512, fit).
+ *     rejected with DH_ERROR_INVALIDDIMENSION (the supported limits, N <= 1024 and M <= 512, fit; an
+ *     output-basis matrix counts against the tables: the LG matrix fits up to G = 16 at every supported size).
  *   - All calls share the array, which keeps the last call's contents; nothing in it needs to start at zero
  *     (every element is written before it is read within a call).  Calls that overlap on the GPU (different
  *     streams, or threads without ordering) race on the array: serialise them on one stream. */

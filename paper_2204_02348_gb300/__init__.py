@@ -35,6 +35,13 @@ DH_DTYPE_U16 = 0
 DH_DTYPE_F32 = 1
 DH_PRECISION_FP32 = 0
 DH_PRECISION_SPLIT_BF16 = 1
+DH_BASIS_HG = 0
+DH_BASIS_LG = 1
+DH_BASIS_CUSTOM = 2
+DH_AVGMODE_SEQUENTIAL = 0
+DH_AVGMODE_INTERLACED = 1
+DH_AVGMODE_SEQUENTIALSWEEP = 2
+DH_MAX_AVG_COUNT = 4096
 DH_MAX_POLS = 2
 
 
@@ -77,11 +84,14 @@ _PROTOS = {
     "dh_set_basis": [_i, _i, _d, _i],
     "dh_set_precision": [_i, _i],
     "dh_set_fill_factor_correction": [_i, _i],
+    "dh_set_basis_type": [_i, _i],
+    "dh_set_basis_transform": [_i, _i, _i, _p],
     "dh_get_output_dims": [_i, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_d)],
     "dh_get_axes": [_i, _i, ctypes.POINTER(_d), ctypes.POINTER(_d)],
     "dh_process_batch": [_i, _p, _i, _i, _p, _p, _p],
     "dh_process_batch_window": [_i, _p, _i, _i, _p, _p, _p, _p],
     "dh_process_batch_noalloc": [_i, _p, _i, _i, _p, _p, _p],
+    "dh_process_batch_avg": [_i, _p, _i, _i, _i, _i, _p, _p, _p],
     "dh_score_settings": [_i, _p, _i, _i, ctypes.POINTER(dh_setting), _i, _p, _p],
     "dh_set_profiling": [_i, _i],
     "dh_get_device_status": [_i, ctypes.POINTER(_i)],
@@ -187,6 +197,19 @@ def dh_set_fill_factor_correction(h: int, enabled: bool) -> None:
     _check(_lib.dh_set_fill_factor_correction(h, 1 if enabled else 0))
 
 
+def dh_set_basis_type(h: int, basis: int) -> None:
+    _check(_lib.dh_set_basis_type(h, basis))
+
+
+def dh_set_basis_transform(h: int, transform) -> None:
+    """transform: complex matrix [modes_out][modes_in] (anything numpy converts); copied by the library."""
+    import numpy as np
+    t = np.ascontiguousarray(np.asarray(transform, dtype=np.complex64))
+    if t.ndim != 2:
+        raise ValueError("transform must be a 2-D matrix [modes_out][modes_in]")
+    _check(_lib.dh_set_basis_transform(h, t.shape[1], t.shape[0], t.ctypes.data_as(_p)))
+
+
 def dh_set_precision(h: int, precision: int) -> None:
     _check(_lib.dh_set_precision(h, precision))
 
@@ -212,6 +235,12 @@ def dh_process_batch_window(h: int, frames, dtype: int, batch: int, window, fiel
                             stream=None) -> None:
     _check(_lib.dh_process_batch_window(h, _ptr(frames), dtype, batch, _ptr(window), _ptr(fields), _ptr(coefs),
                                         _stream(stream)))
+
+
+def dh_process_batch_avg(h: int, frames, dtype: int, batch: int, avg_count: int, avg_mode: int, fields=None,
+                         coefs=None, stream=None) -> None:
+    _check(_lib.dh_process_batch_avg(h, _ptr(frames), dtype, batch, avg_count, avg_mode, _ptr(fields), _ptr(coefs),
+                                     _stream(stream)))
 
 
 def dh_process_batch_noalloc(h: int, frames, dtype: int, batch: int, fields=None, coefs=None, stream=None) -> None:
@@ -301,8 +330,8 @@ def make_setting(tilt_deg, defocus, waist) -> dh_setting:
 
 def configure(h: int, setup) -> None:
     """Apply an acquisition description (attributes frame_w, frame_h, pol_count, pixel, wavelength, window,
-    beam_centre, tilt_deg, defocus, radius_deg, ifft_size, group_count, waist and optionally precision) to a
-    handle through the setters."""
+    beam_centre, tilt_deg, defocus, radius_deg, ifft_size, group_count, waist and optionally precision,
+    fill_factor, basis and basis_transform) to a handle through the setters."""
     dh_set_frame(h, setup.frame_w, setup.frame_h, setup.pol_count, setup.pixel)
     dh_set_wavelength(h, setup.wavelength)
     dh_set_fft_window(h, setup.window, setup.window)
@@ -316,6 +345,11 @@ def configure(h: int, setup) -> None:
         dh_set_basis(h, p, setup.waist[p], setup.group_count)
     dh_set_precision(h, getattr(setup, "precision", DH_PRECISION_FP32))
     dh_set_fill_factor_correction(h, bool(getattr(setup, "fill_factor", False)))
+    basis = getattr(setup, "basis", "hg")
+    if basis == "custom":
+        dh_set_basis_transform(h, setup.basis_transform)
+    else:
+        dh_set_basis_type(h, DH_BASIS_LG if basis == "lg" else DH_BASIS_HG)
 
 
 class Reconstructor:

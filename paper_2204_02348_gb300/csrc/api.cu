@@ -41,17 +41,20 @@ Handle* get_handle(dh_handle h) {
 }
 
 static void release_device(Handle* H) {
-    if (H->d_blob || H->d_scratch) {
+    if (H->d_blob || H->d_scratch || H->d_hg) {
         int cur = -1;
         cudaGetDevice(&cur);
         if (H->device >= 0 && H->device != cur) cudaSetDevice(H->device);
         if (H->d_blob) cudaFree(H->d_blob);
         if (H->d_scratch) cudaFree(H->d_scratch);
+        if (H->d_hg) cudaFree(H->d_hg);
         if (H->device >= 0 && H->device != cur && cur >= 0) cudaSetDevice(cur);
     }
     H->d_blob = nullptr;
     H->d_scratch = nullptr;
     H->scratch_bytes = 0;
+    H->d_hg = nullptr;
+    H->hg_bytes = 0;
     H->device = -1;
 }
 
@@ -95,6 +98,7 @@ int upload_plan(const Settings& s, const Geometry& g, const Tables& t, void** ou
     const size_t o_mn = b.put(t.mode_n.data(), t.mode_n.size() * 4);
     const int zero_status[4] = {0, 0, 0, 0};
     const size_t o_st = b.put(zero_status, sizeof zero_status);
+    const size_t o_bt = b.put(t.basis_tt.data(), t.basis_tt.size() * 4);
     size_t o_pol[DH_MAX_POLS][9] = {};
     for (int p = 0; p < g.pols; ++p) {
         const PolTables& pt = t.pol[p];
@@ -139,6 +143,8 @@ int upload_plan(const Settings& s, const Geometry& g, const Tables& t, void** ou
     P.mode_m = (const int*)(base + o_mm);
     P.mode_n = (const int*)(base + o_mn);
     P.status = (int*)(base + o_st);
+    P.modes_out = g.modes_out;
+    P.basis_tt = t.basis_tt.empty() ? nullptr : (const float2*)(base + o_bt);
     for (int p = 0; p < g.pols; ++p) {
         dhk::PolDev& pd = P.pol[p];
         pd.ox = g.pol[p].ax[0].origin;
@@ -169,6 +175,8 @@ int init_device_once(int dev) {
     e = dhk::tc_init();
     if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
     e = fused_init();
+    if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
+    e = dhk::basis_init();
     if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
     if (dev >= 0 && dev < 64) inited[dev] = true;
     return DH_SUCCESS;
@@ -294,6 +302,40 @@ Profiler::~Profiler() {
     for (cudaEvent_t e : pool) cudaEventDestroy(e);
 }
 
+size_t basis_scratch_bytes(const dhk::Plan& P) {
+    return P.basis_tt ? (size_t)P.pols * P.modes * sizeof(float2) : 0;
+}
+
+// The output-basis transform after the HG overlap: the path writes HG coefficients to `hg`, k_basis writes
+// the caller's coefficients.
+static int finish_basis(const dhk::Plan& P, void* hg, void* coefs, int batch, cudaStream_t st,
+                        dhk::StageTimer* timer) {
+    cudaError_t e = dhk::launch_basis(P, (const float2*)hg, (float2*)coefs, batch * P.pols, st, timer);
+    return e == cudaSuccess ? DH_SUCCESS : cuda_fail(e, "basis transform launch");
+}
+
+// Point *coefs at the handle's HG-coefficient scratch when an output-basis transform follows; returns the
+// caller's buffer in *out.
+static int basis_target(Handle* H, int batch, void** coefs, void** out) {
+    const dhk::Plan& P = H->plan;
+    *out = *coefs;
+    if (!*coefs || !P.basis_tt) return DH_SUCCESS;
+    const size_t need = basis_scratch_bytes(P) * batch;
+    if (H->hg_bytes < need) {
+        if (H->d_hg) cudaFree(H->d_hg);
+        H->d_hg = nullptr;
+        H->hg_bytes = 0;
+        cudaError_t e = cudaMalloc(&H->d_hg, need);
+        if (e != cudaSuccess) {
+            H->d_hg = nullptr;
+            return fail(DH_ERROR_MEMORYALLOCATION, std::string("basis scratch: ") + cudaGetErrorString(e));
+        }
+        H->hg_bytes = need;
+    }
+    *coefs = H->d_hg;
+    return DH_SUCCESS;
+}
+
 int process(Handle* H, const void* frames, int dtype, int batch, void* window, void* fields, void* coefs,
             cudaStream_t st) {
     if (!frames) return fail(DH_ERROR_NULLPOINTER, "frames pointer is null");
@@ -303,22 +345,124 @@ int process(Handle* H, const void* frames, int dtype, int batch, void* window, v
     if (rc) return rc;
     const dhk::Plan& P = H->plan;
     if (P.modes == 0) coefs = nullptr;
-    if (use_fused(P) && !window && fused_frames_ok(P, frames, dtype))
-        return launch_fused_path(H, frames, dtype, batch, fields, coefs, st, H->timer());
-    const size_t per_frame = split_window_bytes(P) * P.pols;
-    const int chunk = chunk_frames(per_frame, P.pols, batch, H->device);
-    rc = ensure_scratch(H, per_frame * chunk);
+    void* out = nullptr;
+    rc = basis_target(H, batch, &coefs, &out);
     if (rc) return rc;
-    return run_split(P, H->d_scratch, H->scratch_bytes, frames, dtype, batch, window, fields, coefs, st, H->timer());
+    if (use_fused(P) && !window && fused_frames_ok(P, frames, dtype)) {
+        rc = launch_fused_path(H, frames, dtype, batch, fields, coefs, st, H->timer());
+    } else {
+        const size_t per_frame = split_window_bytes(P) * P.pols;
+        const int chunk = chunk_frames(per_frame, P.pols, batch, H->device);
+        rc = ensure_scratch(H, per_frame * chunk);
+        if (rc) return rc;
+        rc = run_split(P, H->d_scratch, H->scratch_bytes, frames, dtype, batch, window, fields, coefs, st, H->timer());
+    }
+    if (rc || out == coefs) return rc;
+    return finish_basis(P, coefs, out, batch, st, H->timer());
+}
+
+// Batch averaging on the generic path: per chunk of averaging groups, the forward kernels fill the
+// x-inverse-transformed windows of every member, k_avg_dot / k_avg_sum form the phase-aligned means, and the
+// last kernel transforms and decomposes one window per group.
+int process_avg(Handle* H, const void* frames, int dtype, int batch, int avg, int mode, void* fields, void* coefs,
+                cudaStream_t st) {
+    if (!frames) return fail(DH_ERROR_NULLPOINTER, "frames pointer is null");
+    if (dtype != DH_DTYPE_U16 && dtype != DH_DTYPE_F32) return fail(DH_ERROR_INVALIDARGUMENT, "dtype must be DH_DTYPE_U16 or DH_DTYPE_F32");
+    if (mode != DH_AVGMODE_SEQUENTIAL && mode != DH_AVGMODE_INTERLACED && mode != DH_AVGMODE_SEQUENTIALSWEEP)
+        return fail(DH_ERROR_INVALIDARGUMENT, "avg_mode must be DH_AVGMODE_SEQUENTIAL, _INTERLACED or _SEQUENTIALSWEEP");
+    if (avg > DH_MAX_AVG_COUNT) return fail(DH_ERROR_INVALIDDIMENSION, "avg_count exceeds DH_MAX_AVG_COUNT");
+    if (batch < 1) batch = 1;
+    if (avg <= 1) return process(H, frames, dtype, batch, nullptr, fields, coefs, st);
+    int rc = ensure_plan(H);
+    if (rc) return rc;
+    const dhk::Plan& P = H->plan;
+    if (P.modes == 0) coefs = nullptr;
+    void* out = nullptr;
+    rc = basis_target(H, batch, &coefs, &out);
+    if (rc) return rc;
+    const long long elems = (long long)P.pols * P.m * P.m;
+    const int slices = dhk::avg_slices(elems);
+    const size_t split = split_window_bytes(P) * P.pols;
+    const size_t per_group = (size_t)avg * split + (size_t)elems * sizeof(float2) + (size_t)avg * slices * sizeof(float2);
+    // groups per chunk: enough member windows for several waves of the forward kernels, about the L2-sized
+    // scratch target, at most the scratch cap and the grid limit
+    int dev_sms = 148;
+    cudaDeviceGetAttribute(&dev_sms, cudaDevAttrMultiProcessorCount, H->device);
+    size_t groups = std::max<size_t>(((size_t)8 * dev_sms + (size_t)avg * P.pols - 1) / ((size_t)avg * P.pols),
+                                     kScratchTarget / per_group);
+    groups = std::min(groups, std::max<size_t>(1, kScratchCap / per_group));
+    groups = std::min<size_t>(std::min<size_t>(groups, (size_t)batch), 65535);
+    const int chunk = (int)std::max<size_t>(1, groups);
+    rc = ensure_scratch(H, per_group * chunk);
+    if (rc) return rc;
+    float2* r1 = (float2*)H->d_scratch;
+    float2* gbuf = r1 + (size_t)chunk * avg * P.pols * P.m * P.n;
+    float2* mean = gbuf + (size_t)chunk * avg * elems;
+    float2* part = mean + (size_t)chunk * elems;
+    dhk::StageTimer* tm = H->timer();
+    for (int g0 = 0; g0 < batch; g0 += chunk) {
+        const int n = std::min(chunk, batch - g0);
+        dhk::Batch B{};
+        B.src = frames;
+        B.dtype = dtype;
+        B.r1 = r1;
+        long long mstride, gstride;
+        cudaError_t e = cudaSuccess;
+        if (mode == DH_AVGMODE_INTERLACED) {
+            // member j of groups [g0, g0 + n) is the contiguous frame range [j batch + g0, j batch + g0 + n)
+            for (int j = 0; j < avg && e == cudaSuccess; ++j) {
+                B.frame0 = j * batch + g0;
+                B.count = n;
+                B.g = gbuf + (size_t)j * n * elems;
+                e = dhk::launch_forward(P, B, st, tm);
+            }
+            mstride = (long long)n * elems;
+            gstride = elems;
+        } else {
+            B.frame0 = g0 * avg;
+            B.count = n * avg;
+            B.g = gbuf;
+            e = dhk::launch_forward(P, B, st, tm);
+            mstride = elems;
+            gstride = (long long)avg * elems;
+        }
+        if (e == cudaSuccess) e = dhk::launch_avg(gbuf, part, mean, n, avg, elems, mstride, gstride, st, tm);
+        if (e == cudaSuccess) {
+            dhk::Batch L{};
+            L.src = frames;
+            L.dtype = dtype;
+            L.frame0 = g0;
+            L.count = n;
+            L.g = mean;
+            L.fields = (float2*)fields;
+            L.coefs = (float2*)coefs;
+            e = dhk::launch_last(P, L, st, tm);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "averaging launch");
+    }
+    if (out == coefs) return DH_SUCCESS;
+    return finish_basis(P, coefs, out, batch, st, tm);
 }
 
 int process_with(Handle* H, const void* frames, int dtype, int batch, void* fields, void* coefs, void* scratch,
                  size_t scratch_bytes, cudaStream_t st) {
     const dhk::Plan& P = H->plan;
     if (P.modes == 0) coefs = nullptr;
+    void* out = coefs;
+    if (coefs && P.basis_tt) {
+        // the HG coefficients take the end of the scratch
+        const size_t need = basis_scratch_bytes(P) * batch;
+        if (scratch_bytes < need) return fail(DH_ERROR_MEMORYALLOCATION, "scratch smaller than the basis transform needs");
+        scratch_bytes -= need;
+        coefs = (unsigned char*)scratch + scratch_bytes;
+    }
+    int rc;
     if (use_fused(P) && fused_frames_ok(P, frames, dtype))
-        return launch_fused_path(H, frames, dtype, batch, fields, coefs, st, nullptr);
-    return run_split(P, scratch, scratch_bytes, frames, dtype, batch, nullptr, fields, coefs, st, nullptr);
+        rc = launch_fused_path(H, frames, dtype, batch, fields, coefs, st, nullptr);
+    else
+        rc = run_split(P, scratch, scratch_bytes, frames, dtype, batch, nullptr, fields, coefs, st, nullptr);
+    if (rc || out == coefs) return rc;
+    return finish_basis(P, coefs, out, batch, st, nullptr);
 }
 
 int run_split(const dhk::Plan& P, void* scratch, size_t scratch_bytes, const void* frames, int dtype, int batch,
@@ -374,7 +518,7 @@ int dh_destroy(dh_handle h) {
         owned = std::move(g_handles[h]);
     }
     std::lock_guard<std::mutex> lk(owned->mu);
-    if (owned->d_blob || owned->d_scratch) cudaDeviceSynchronize();
+    if (owned->d_blob || owned->d_scratch || owned->d_hg) cudaDeviceSynchronize();
     release_device(owned.get());
     return DH_SUCCESS;
 }
@@ -487,6 +631,29 @@ int dh_set_precision(dh_handle h, int precision) {
     return DH_SUCCESS;
 }
 
+int dh_set_basis_type(dh_handle h, int basis) {
+    GET_HANDLE(h);
+    if (basis != DH_BASIS_HG && basis != DH_BASIS_LG && basis != DH_BASIS_CUSTOM)
+        return fail(DH_ERROR_INVALIDARGUMENT, "basis must be DH_BASIS_HG, DH_BASIS_LG or DH_BASIS_CUSTOM");
+    H->s.basis = basis;
+    H->dirty = true;
+    return DH_SUCCESS;
+}
+
+int dh_set_basis_transform(dh_handle h, int modes_in, int modes_out, const void* transform) {
+    GET_HANDLE(h);
+    if (!transform) return fail(DH_ERROR_NULLPOINTER, "transform is null");
+    if (modes_in < 1 || modes_out < 1 || (long long)modes_in * modes_out > (1ll << 24))
+        return fail(DH_ERROR_INVALIDDIMENSION, "transform dimensions must be >= 1 with modes_in * modes_out <= 2^24");
+    const float* t = (const float*)transform;
+    H->s.custom.assign(t, t + (size_t)2 * modes_in * modes_out);
+    H->s.custom_in = modes_in;
+    H->s.custom_out = modes_out;
+    H->s.basis = DH_BASIS_CUSTOM;
+    H->dirty = true;
+    return DH_SUCCESS;
+}
+
 int dh_get_output_dims(dh_handle h, int* m, int* modes, double* dx) {
     GET_HANDLE(h);
     Geometry g;
@@ -494,7 +661,7 @@ int dh_get_output_dims(dh_handle h, int* m, int* modes, double* dx) {
     int rc = build_geometry(H->s, &g, &why);
     if (rc) return fail(rc, why);
     if (m) *m = g.m;
-    if (modes) *modes = g.modes;
+    if (modes) *modes = g.modes_out;
     if (dx) *dx = g.dx;
     return DH_SUCCESS;
 }
@@ -525,6 +692,12 @@ int dh_process_batch_window(dh_handle h, const void* d_frames, int dtype, int ba
     GET_HANDLE(h);
     if (!d_window) return fail(DH_ERROR_NULLPOINTER, "window pointer is null");
     return process(H, d_frames, dtype, batch, d_window, d_fields, d_coefs, (cudaStream_t)stream);
+}
+
+int dh_process_batch_avg(dh_handle h, const void* d_frames, int dtype, int batch, int avg_count, int avg_mode,
+                         void* d_fields, void* d_coefs, void* stream) {
+    GET_HANDLE(h);
+    return process_avg(H, d_frames, dtype, batch, avg_count, avg_mode, d_fields, d_coefs, (cudaStream_t)stream);
 }
 
 int dh_set_profiling(dh_handle h, int enable) {

@@ -198,6 +198,12 @@ cudaError_t split_init() {
 }
 
 cudaError_t launch_split(const Plan& P, const Batch& B, cudaStream_t st, StageTimer* tm) {
+    cudaError_t e = launch_forward(P, B, st, tm);
+    if (e != cudaSuccess) return e;
+    return launch_last(P, B, st, tm);
+}
+
+cudaError_t launch_forward(const Plan& P, const Batch& B, cudaStream_t st, StageTimer* tm) {
     const int N = P.n, M = P.m;
     const int zf = std::min(B.count, 65535);
     // k_ypass: C packed column pairs per block, N x C complex in shared memory
@@ -220,7 +226,7 @@ cudaError_t launch_split(const Plan& P, const Batch& B, cudaStream_t st, StageTi
     if (tm) tm->start(st);
     k_xpass<<<g2, kThreads, sm2, st>>>(P, B, logr, ilog2(N));
     if (tm) tm->stop(st, "k_xpass");
-    return launch_last(P, B, st, tm);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_last(const Plan& P, const Batch& B, cudaStream_t st, StageTimer* tm) {

@@ -39,6 +39,8 @@ struct Plan {
     const int* pos_m;        // [M] position of index k for the inverse DIT input
     const int* mode_m;       // [modes]
     const int* mode_n;       // [modes]
+    int modes_out;           // coefficients per polarisation in the output basis
+    const float2* basis_tt;  // nullable [modes][modes_out]: transposed HG -> output-basis matrix (null: HG)
     int* status;             // nullable device status word: bit 0 set when a bounded wait expired
     PolDev pol[DH_MAX_POLS];
 };
@@ -64,12 +66,27 @@ struct StageTimer {
 
 // Launchers of the generic three-kernel path (k_split.cu).  Return cudaGetLastError().
 cudaError_t launch_split(const Plan& plan, const Batch& batch, cudaStream_t stream, StageTimer* timer);
-// The first and the last kernel of the generic path on their own (candidate scoring reuses them).
+// k_ypass + k_xpass (window spectrum to x-inverse-transformed rows in batch.g) and the last kernel on their
+// own (candidate scoring and batch averaging reuse them).
+cudaError_t launch_forward(const Plan& plan, const Batch& batch, cudaStream_t stream, StageTimer* timer);
 cudaError_t launch_ypass(const Plan& plan, const Batch& batch, cudaStream_t stream, StageTimer* timer);
 cudaError_t launch_last(const Plan& plan, const Batch& batch, cudaStream_t stream, StageTimer* timer);
 // Shared-memory opt-in, once per process and device.
 cudaError_t split_init();
 cudaError_t score_init();
+
+// Output-basis transform (basis.cu): out[v][k] = sum_l T[k][l] hg[v][l] over `vectors` coefficient vectors
+// (frames x polarisations) of plan.modes HG coefficients each; out holds plan.modes_out per vector.
+cudaError_t launch_basis(const Plan& plan, const float2* hg, float2* out, int vectors, cudaStream_t stream,
+                         StageTimer* timer);
+cudaError_t basis_init();
+
+// Batch averaging (k_avg.cu): phase-aligned mean of the x-inverse-transformed windows of each averaging
+// group.  g holds groups x members windows of E = pols * M * M elements, member j of group gi at element
+// offset gi * gstride + j * mstride; out receives [groups][E]; part is scratch of groups * members * slices.
+int avg_slices(long long elems);
+cudaError_t launch_avg(const float2* g, float2* part, float2* out, int groups, int members, long long elems,
+                       long long mstride, long long gstride, cudaStream_t stream, StageTimer* timer);
 
 // Split-BF16 tensor-core variant of the last generic kernel (k_overlap_tc.cu).
 bool tc_supported(const Plan& plan);

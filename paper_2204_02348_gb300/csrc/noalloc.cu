@@ -15,6 +15,7 @@
 // stream.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 #include <string>
@@ -47,6 +48,7 @@ int noalloc_area(int dev, unsigned char** out) {
         cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_area);
         if (e != cudaSuccess || !p) return cuda_fail(e != cudaSuccess ? e : cudaErrorInvalidSymbol, "cudaGetSymbolAddress");
         e = dhk::split_init();
+        if (e == cudaSuccess) e = dhk::basis_init();
         if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
         g_noalloc_addr[dev] = (unsigned char*)p;
     }
@@ -91,6 +93,7 @@ int pack_plan(const Settings& s, const Geometry& g, const Tables& t, unsigned ch
     const size_t o_pm = pk->put(pm.data(), pm.size() * 4);
     const size_t o_mm = pk->put(t.mode_m.data(), t.mode_m.size() * 4);
     const size_t o_mn = pk->put(t.mode_n.data(), t.mode_n.size() * 4);
+    const size_t o_bt = pk->put(t.basis_tt.data(), t.basis_tt.size() * 4);
     dhk::Plan& P = *out;
     std::memset(&P, 0, sizeof P);
     P.n = g.n;
@@ -111,6 +114,8 @@ int pack_plan(const Settings& s, const Geometry& g, const Tables& t, unsigned ch
     P.pos_m = (const int*)(dev_tables + o_pm);
     P.mode_m = (const int*)(dev_tables + o_mm);
     P.mode_n = (const int*)(dev_tables + o_mn);
+    P.modes_out = g.modes_out;
+    P.basis_tt = t.basis_tt.empty() ? nullptr : (const float2*)(dev_tables + o_bt);
     for (int p = 0; p < g.pols; ++p) {
         const PolTables& pt = t.pol[p];
         dhk::PolDev& pd = P.pol[p];
@@ -162,7 +167,9 @@ extern "C" int dh_process_batch_noalloc(dh_handle h, const void* d_frames, int d
     dhk::Plan P;
     rc = pack_plan(H->s, g, t, area, &pk, &P);
     if (rc) return rc;
-    const size_t per_frame = split_window_bytes(P) * P.pols;
+    if (P.modes == 0) d_coefs = nullptr;
+    const size_t hg_frame = d_coefs ? basis_scratch_bytes(P) : 0;
+    const size_t per_frame = split_window_bytes(P) * P.pols + hg_frame;
     if (per_frame > kNoallocScratchBytes) {
         return fail(DH_ERROR_INVALIDDIMENSION, "one frame of this geometry needs " + std::to_string(per_frame) +
                                                    " bytes of scratch; the static scratch holds " +
@@ -171,7 +178,24 @@ extern "C" int dh_process_batch_noalloc(dh_handle h, const void* d_frames, int d
     cudaStream_t st = (cudaStream_t)stream;
     e = cudaMemcpyAsync(area, pk.bytes.data(), pk.bytes.size(), cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_fail(e, "plan table upload");
-    if (P.modes == 0) d_coefs = nullptr;
-    return run_split(P, area + kNoallocTableBytes, kNoallocScratchBytes, d_frames, dtype, batch, nullptr, d_fields,
-                     d_coefs, st, nullptr);
+    unsigned char* scratch = area + kNoallocTableBytes;
+    if (!hg_frame)
+        return run_split(P, scratch, kNoallocScratchBytes, d_frames, dtype, batch, nullptr, d_fields, d_coefs, st,
+                         nullptr);
+    // output-basis transform: chunks whose HG coefficients sit at the end of the static scratch
+    const int chunk = (int)std::min<size_t>((size_t)batch, kNoallocScratchBytes / per_frame);
+    const size_t frame_bytes = (size_t)P.width * P.height * (dtype == DH_DTYPE_U16 ? 2 : 4);
+    const size_t field_bytes = (size_t)P.pols * P.m * P.m * sizeof(float2);
+    const size_t coef_bytes = (size_t)P.pols * P.modes_out * sizeof(float2);
+    float2* hg = (float2*)(scratch + kNoallocScratchBytes - (size_t)chunk * hg_frame);
+    for (int f0 = 0; f0 < batch; f0 += chunk) {
+        const int n = std::min(chunk, batch - f0);
+        rc = run_split(P, scratch, kNoallocScratchBytes - (size_t)chunk * hg_frame,
+                       (const unsigned char*)d_frames + f0 * frame_bytes, dtype, n, nullptr,
+                       d_fields ? (unsigned char*)d_fields + f0 * field_bytes : nullptr, hg, st, nullptr);
+        if (rc) return rc;
+        e = dhk::launch_basis(P, hg, (float2*)((unsigned char*)d_coefs + f0 * coef_bytes), n * P.pols, st, nullptr);
+        if (e != cudaSuccess) return cuda_fail(e, "basis transform launch");
+    }
+    return DH_SUCCESS;
 }

@@ -3,6 +3,7 @@
 // taken here, in FP64, once per plan.
 #include "plan.hpp"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -54,6 +55,8 @@ static int fill(const Settings& s, const double tilt[DH_MAX_POLS][2], const doub
     g->pols = s.pols;
     g->groups = s.groups;
     g->modes = s.groups * (s.groups + 1) / 2;
+    g->basis = s.basis == DH_BASIS_CUSTOM && s.custom.empty() ? DH_BASIS_HG : s.basis;
+    g->modes_out = g->modes == 0 ? 0 : g->basis == DH_BASIS_CUSTOM ? s.custom_out : g->modes;
     const double r = s.radius_deg * kDegToRad * (double)s.n * s.pixel / s.wavelength;
     g->m = s.m_req > 0 ? s.m_req : ifft_size_rule(r);
     if (g->m < 16 || g->m % 16 || g->m > s.n || g->m > DH_MAX_FIELD || radix_plan(g->m).empty()) {
@@ -137,6 +140,49 @@ static void push_c(std::vector<float>& v, double re, double im) {
     v.push_back((float)im);
 }
 
+// LG_p^l as a sum over the HG modes of its group N = 2p + |l| (Hermite-Laguerre-Gauss relation, as in
+// Beijersbergen et al., Opt. Commun. 96, 123 (1993)): with n = p + max(l, 0), m = p + max(-l, 0),
+//   <HG(N-k, k) | LG_p^l> = (-1)^p (-i)^k b(n, m, k),
+//   b(n, m, k) = sqrt((N-k)! k! / (2^N n! m!)) sum_j C(n, j) (-1)^j C(m, k-j),
+// HG(a, b) = u_a(x) u_b(y) and LG_p^l carrying exp(+i l phi).  The LG coefficient of a field is
+// <LG | E> = sum_k conj(<HG_k | LG>) <HG_k | E>, so T holds the conjugates: (-1)^p i^k b(n, m, k).  The binomial
+// sums are integers below 2^(N+5) and are summed exactly in 64-bit integers.
+void lg_transform(int groups, std::vector<double>* t) {
+    const int modes = groups * (groups + 1) / 2;
+    t->assign((size_t)2 * modes * modes, 0.0);
+    auto binom = [](int a, int b) -> long long {
+        if (b < 0 || b > a) return 0;
+        long long r = 1;
+        for (int i = 1; i <= b; ++i) r = r * (a - b + i) / i;
+        return r;
+    };
+    auto lfact = [](int a) { return std::lgamma((double)a + 1.0); };
+    int base = 0;
+    for (int grp = 0; grp < groups; ++grp) {
+        int row = base;
+        for (int l = -grp; l <= grp; l += 2, ++row) {
+            const int p = (grp - std::abs(l)) / 2;
+            const int n = p + std::max(l, 0), m = p + std::max(-l, 0);
+            for (int k = 0; k <= grp; ++k) {
+                long long sum = 0;
+                for (int j = 0; j <= std::min(n, k); ++j) {
+                    const long long term = binom(n, j) * binom(m, k - j);
+                    sum += (j % 2) ? -term : term;
+                }
+                const double mag = std::exp(0.5 * (lfact(grp - k) + lfact(k) - grp * std::log(2.0) - lfact(n) - lfact(m)));
+                const double b = mag * (double)sum * ((p % 2) ? -1.0 : 1.0);
+                // i^k b; HG(x order grp - k, y order k) sits at column base + (grp - k)
+                const double re = (k % 4 == 0) ? b : (k % 4 == 2) ? -b : 0.0;
+                const double im = (k % 4 == 1) ? b : (k % 4 == 3) ? -b : 0.0;
+                const size_t at = (size_t)row * modes + base + (grp - k);
+                (*t)[2 * at] = re;
+                (*t)[2 * at + 1] = im;
+            }
+        }
+        base += grp + 1;
+    }
+}
+
 void build_tables(const Settings& s, const Geometry& g, Tables* t) {
     const int n = g.n, m = g.m;
     t->tw_fwd_n.clear();
@@ -149,6 +195,28 @@ void build_tables(const Settings& s, const Geometry& g, Tables* t) {
     t->mode_n.clear();
     for (int gg = 0; gg < g.groups; ++gg)
         for (int mm = 0; mm <= gg; ++mm) { t->mode_m.push_back(mm); t->mode_n.push_back(gg - mm); }
+    t->basis_tt.clear();
+    if (g.modes > 0 && g.basis != DH_BASIS_HG) {
+        const int mi = g.modes, mo = g.modes_out;
+        t->basis_tt.assign((size_t)2 * mi * mo, 0.f);
+        if (g.basis == DH_BASIS_LG) {
+            std::vector<double> lg;
+            lg_transform(g.groups, &lg);
+            for (int k = 0; k < mo; ++k)
+                for (int l = 0; l < mi; ++l) {
+                    t->basis_tt[2 * ((size_t)l * mo + k)] = (float)lg[2 * ((size_t)k * mi + l)];
+                    t->basis_tt[2 * ((size_t)l * mo + k) + 1] = (float)lg[2 * ((size_t)k * mi + l) + 1];
+                }
+        } else {
+            // columns beyond the HG mode count are unused; HG modes beyond the matrix's columns contribute 0
+            const int used = std::min(mi, s.custom_in);
+            for (int k = 0; k < mo; ++k)
+                for (int l = 0; l < used; ++l) {
+                    t->basis_tt[2 * ((size_t)l * mo + k)] = s.custom[2 * ((size_t)k * s.custom_in + l)];
+                    t->basis_tt[2 * ((size_t)l * mo + k) + 1] = s.custom[2 * ((size_t)k * s.custom_in + l) + 1];
+                }
+        }
+    }
     std::vector<double> xp(m);
     for (int i = 0; i < m; ++i) xp[i] = (double)(i - m / 2) * g.dx;
     for (int p = 0; p < g.pols; ++p) {

@@ -28,6 +28,9 @@ struct Settings {
     int groups = 0;
     int precision = DH_PRECISION_FP32;
     int fill_factor = 0;                 // divide the window by the pixel response sinc(k/N) per axis
+    int basis = DH_BASIS_HG;             // coefficient basis (custom falls back to HG until a matrix is set)
+    int custom_in = 0, custom_out = 0;   // custom transform dimensions (modes in x modes out)
+    std::vector<float> custom;           // custom transform, complex [custom_out][custom_in], interleaved re/im
 };
 
 // Geometry of one axis of one polarisation (all FP64, computed as the conventions in digholo.h state).
@@ -47,6 +50,8 @@ struct PolGeom {
 
 struct Geometry {
     int n, m, groups, modes, pols;
+    int basis;       // effective basis: DH_BASIS_HG, DH_BASIS_LG or DH_BASIS_CUSTOM
+    int modes_out;   // coefficients per polarisation in that basis (0 when G = 0)
     double dx;       // field pitch N px / M
     PolGeom pol[DH_MAX_POLS];
 };
@@ -73,6 +78,8 @@ struct Tables {
     std::vector<int> radix_n;      // radices of N (first pass first)
     std::vector<int> radix_m;      // radices of M
     std::vector<int> mode_m, mode_n;
+    // basis transform, transposed: complex [modes][modes_out] holding T[k][l] at [l][k]; empty for HG
+    std::vector<float> basis_tt;
     PolTables pol[DH_MAX_POLS];
 };
 
@@ -89,6 +96,9 @@ int build_geometry(const Settings& s, Geometry* g, std::string* why);
 int build_geometry_candidate(const Settings& s, const dh_setting& c, Geometry* g, std::string* why);
 // Fill the host tables of a geometry.
 void build_tables(const Settings& s, const Geometry& g, Tables* t);
+// HG -> LG coefficient matrix (FP64, complex interleaved [modes][modes], LG rows by group then l ascending,
+// HG columns by group then m ascending): c_LG = T c_HG.
+void lg_transform(int groups, std::vector<double>* t);
 // HG 1D functions u_0..u_{G-1} at positions x (recurrence, FP64), row-major [G][len].
 void hg_table(int groups, const double* x, int len, double waist, double* out);
 

@@ -52,6 +52,8 @@ struct Handle {
     dhk::Plan plan{};
     void* d_scratch = nullptr;    // generic-path scratch (device)
     size_t scratch_bytes = 0;
+    void* d_hg = nullptr;         // HG coefficients ahead of an output-basis transform (device)
+    size_t hg_bytes = 0;
     Profiler prof;
     dhk::StageTimer* timer() { return prof.on ? &prof : nullptr; }
 };
@@ -76,8 +78,12 @@ cudaError_t fused_init();
 int launch_fused_path(Handle* H, const void* frames, int dtype, int batch, void* fields, void* coefs,
                       cudaStream_t st, dhk::StageTimer* timer);
 
+// HG coefficient bytes per frame that an output-basis transform needs as scratch (0 for the HG basis).
+size_t basis_scratch_bytes(const dhk::Plan& P);
+
 // Queue one batch with the handle's uploaded plan and caller-provided scratch (used by the serving loop,
-// where concurrent requests of one handle must not share the handle's scratch).  No profiling.
+// where concurrent requests of one handle must not share the handle's scratch).  With an output-basis
+// transform the last batch * basis_scratch_bytes of the scratch hold the HG coefficients.  No profiling.
 int process_with(Handle* H, const void* frames, int dtype, int batch, void* fields, void* coefs, void* scratch,
                  size_t scratch_bytes, cudaStream_t st);
 

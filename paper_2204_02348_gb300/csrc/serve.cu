@@ -172,7 +172,7 @@ void launch(dh_server_s* S, Req* r, Slot& sl) {
     const size_t esz = r->r.dtype == DH_DTYPE_U16 ? 2 : 4;
     const size_t frame_bytes = (size_t)P.width * P.height * esz;
     const size_t field_bytes = (size_t)P.pols * P.m * P.m * 8;
-    const size_t coef_bytes = (size_t)P.pols * P.modes * 8;
+    const size_t coef_bytes = (size_t)P.pols * P.modes_out * 8;
     for (int f0 = 0; f0 < r->r.batch && rc == DH_SUCCESS; f0 += r->chunk) {
         const int n = std::min(r->chunk, r->r.batch - f0);
         cudaError_t e = cudaMemcpyAsync(d_frames, (const unsigned char*)r->r.h_frames + f0 * frame_bytes, n * frame_bytes,
@@ -333,11 +333,11 @@ int dh_server_submit(dh_server s, const dh_request* r, uint64_t* ticket) {
     const size_t esz = r->dtype == DH_DTYPE_U16 ? 2 : 4;
     const size_t frame = (size_t)P.width * P.height * esz;
     const size_t field = r->h_fields ? (size_t)P.pols * P.m * P.m * 8 : 0;
-    const size_t coef = (r->h_coefs && P.modes) ? (size_t)P.pols * P.modes * 8 : 0;
+    const size_t coef = (r->h_coefs && P.modes) ? (size_t)P.pols * P.modes_out * 8 : 0;
     // the fused path needs no scratch; frames staged in the arena are 256-byte aligned, so only the row pitch
     // decides whether tensor copies apply
     const bool fused = use_fused(P) && ((size_t)P.width * esz) % 16 == 0;
-    const size_t scratch = fused ? 0 : split_window_bytes(P) * P.pols;
+    const size_t scratch = (fused ? 0 : split_window_bytes(P) * P.pols) + (coef ? basis_scratch_bytes(P) : 0);
     const size_t per_frame = frame + field + coef + scratch;
     const size_t cap = std::max(s->budget / 2, per_frame);
     if (align_up(frame) + align_up(field) + align_up(coef) + align_up(scratch) > s->budget) {

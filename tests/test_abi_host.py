@@ -164,3 +164,51 @@ def test_server_entry_points_fail_cleanly_without_device_work():
     with pytest.raises(dh.DigHoloError) as ei:
         dh.dh_server_stats(0)
     assert ei.value.code == dh.DH_ERROR_INVALIDHANDLE
+
+
+def test_basis_selection_and_output_mode_counts():
+    s = syn.setup_plain()                       # G = 4: 10 HG modes
+    h = dh.dh_create()
+    try:
+        dh.configure(h, s)
+        modes_hg = s.group_count * (s.group_count + 1) // 2
+        assert dh.dh_get_output_dims(h)[1] == modes_hg
+        assert _code(dh.dh_set_basis_type, h, 3) == dh.DH_ERROR_INVALIDARGUMENT
+        assert _code(dh.dh_set_basis_type, h, -1) == dh.DH_ERROR_INVALIDARGUMENT
+        dh.dh_set_basis_type(h, dh.DH_BASIS_CUSTOM)          # no matrix yet: HG coefficients
+        assert dh.dh_get_output_dims(h)[1] == modes_hg
+        dh.dh_set_basis_type(h, dh.DH_BASIS_LG)
+        assert dh.dh_get_output_dims(h)[1] == modes_hg
+        dh.dh_set_basis_transform(h, [[1.0] * 12] * 5)        # 5 outputs from 12 inputs
+        assert dh.dh_get_output_dims(h)[1] == 5
+        dh.dh_set_basis_type(h, dh.DH_BASIS_HG)
+        assert dh.dh_get_output_dims(h)[1] == modes_hg
+        dh.dh_set_basis_type(h, dh.DH_BASIS_CUSTOM)          # the stored matrix applies again
+        assert dh.dh_get_output_dims(h)[1] == 5
+        assert dh._lib.dh_set_basis_transform(h, 2, 2, None) == dh.DH_ERROR_NULLPOINTER
+        buf = (dh.ctypes.c_float * 8)()
+        assert dh._lib.dh_set_basis_transform(h, 0, 2, buf) == dh.DH_ERROR_INVALIDDIMENSION
+        assert dh._lib.dh_set_basis_transform(h, 2, -1, buf) == dh.DH_ERROR_INVALIDDIMENSION
+        assert dh._lib.dh_set_basis_transform(h, 1 << 13, 1 << 12, buf) == dh.DH_ERROR_INVALIDDIMENSION
+        assert dh.dh_get_output_dims(h)[1] == 5                # failed calls keep the settings
+        dh.dh_set_basis(h, 0, s.waist[0], 0)                   # G = 0: no coefficients in any basis
+        assert dh.dh_get_output_dims(h)[1] == 0
+    finally:
+        dh.dh_destroy(h)
+
+
+def test_process_batch_avg_argument_errors_before_device_work():
+    s = syn.setup_plain()
+    h = dh.dh_create()
+    try:
+        dh.configure(h, s)
+        fake = 16   # never dereferenced: the arguments are rejected first
+        assert dh._lib.dh_process_batch_avg(h, None, 0, 1, 2, 0, None, None, None) == dh.DH_ERROR_NULLPOINTER
+        assert dh._lib.dh_process_batch_avg(h, fake, 7, 1, 2, 0, None, None, None) == dh.DH_ERROR_INVALIDARGUMENT
+        assert dh._lib.dh_process_batch_avg(h, fake, 0, 1, 2, 3, None, None, None) == dh.DH_ERROR_INVALIDARGUMENT
+        assert dh._lib.dh_process_batch_avg(h, fake, 0, 1, 2, -1, None, None, None) == dh.DH_ERROR_INVALIDARGUMENT
+        assert dh._lib.dh_process_batch_avg(h, fake, 0, 1, dh.DH_MAX_AVG_COUNT + 1, 0, None, None, None) \
+            == dh.DH_ERROR_INVALIDDIMENSION
+        assert dh._lib.dh_process_batch_avg(12345, fake, 0, 1, 2, 0, None, None, None) == dh.DH_ERROR_INVALIDHANDLE
+    finally:
+        dh.dh_destroy(h)

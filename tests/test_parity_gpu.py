@@ -286,3 +286,44 @@ def test_fill_factor_correction_parity():
     s2 = syn.with_(syn.setup_precision(), fill_factor=True)
     d2 = syn.make_frames(s2, 1, seed=81)
     _check(s2, d2["frames"], run_library(s2, d2["frames"]))
+
+
+# ----------------------------------------------------------------------------- LG and custom bases
+
+
+@pytest.mark.parametrize("name,frames", [("batching", 3), ("precision", 1), ("large_batch", 1)])
+def test_lg_basis_against_direct_lg_overlaps(name, frames):
+    # the oracle overlaps the field with LG modes evaluated from Laguerre polynomials; the library applies
+    # its closed-form HG -> LG matrix to the HG coefficients
+    s = syn.with_(syn.WORKLOADS[name](), basis="lg")
+    d = syn.make_frames(s, frames, seed=120)
+    out = run_library(s, d["frames"])
+    assert out["modes"] == len(orc.lg_mode_list(s.group_count))
+    _check(s, d["frames"], out)
+    _check(s, d["frames"], run_library(s, d["frames"], window=True))          # generic path
+    _check(s, d["frames"], run_library(s, d["frames"], precision=1), coef_tol=SPLIT_COEF_TOL)
+
+
+def test_lg_total_power_equals_hg_total_power():
+    s = syn.setup_batching()
+    d = syn.make_frames(s, 4, seed=121)
+    hg = run_library(s, d["frames"])["coefs"]
+    lg = run_library(syn.with_(s, basis="lg"), d["frames"])["coefs"]
+    p_hg = np.sum(np.abs(hg.astype(np.complex128)) ** 2, axis=-1)
+    p_lg = np.sum(np.abs(lg.astype(np.complex128)) ** 2, axis=-1)
+    assert np.max(np.abs(p_lg - p_hg) / p_hg) <= 1e-5
+
+
+@pytest.mark.parametrize("modes_in_extra", [7, -4])
+def test_custom_basis_more_and_fewer_inputs_than_hg_modes(modes_in_extra):
+    rng = np.random.default_rng(122)
+    s = syn.setup_batching()
+    modes_hg = s.group_count * (s.group_count + 1) // 2
+    t = (rng.standard_normal((23, modes_hg + modes_in_extra))
+         + 1j * rng.standard_normal((23, modes_hg + modes_in_extra))) / math.sqrt(modes_hg)
+    sc = syn.with_(s, basis="custom", basis_transform=t)
+    d = syn.make_frames(sc, 3, seed=123)
+    out = run_library(sc, d["frames"])
+    assert out["modes"] == 23
+    _check(sc, d["frames"], out)
+    _check(sc, d["frames"], run_library(sc, d["frames"], window=True))

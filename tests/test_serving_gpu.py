@@ -143,3 +143,31 @@ def test_budget_errors_and_timeouts():
             dh.dh_server_destroy(srv)
     finally:
         dh.dh_destroy(h)
+
+
+@pytest.mark.parametrize("kind", ["batching", "512x512_2pol", "1024x1024_1pol"])
+def test_lg_basis_request_equals_alone(kind):
+    # the HG coefficients of the transform sit in the request's own scratch: the fused path (no other
+    # scratch) on the 320x256 batching geometry, the generic path on the others; the 1024 window chunks
+    import torch
+    import paper_2204_02348_gb300 as dh
+    base = syn.setup_batching() if kind == "batching" else syn.serving_geometry(kind, np.random.default_rng(125))
+    s = syn.with_(base, basis="lg")
+    fr = syn.make_frames(s, 6, seed=126)["frames"]
+    h = dh.dh_create()
+    dh.configure(h, s)
+    try:
+        fa, ca = _alone(dh, torch, h, s, fr)
+        srv = dh.dh_server_create(48 << 20, 2)
+        try:
+            hin = torch.from_numpy(fr).pin_memory()
+            f = torch.empty(fa.shape, dtype=torch.complex64).pin_memory()
+            c = torch.empty(ca.shape, dtype=torch.complex64).pin_memory()
+            t = dh.dh_server_submit(srv, h, hin, dh.DH_DTYPE_U16, fr.shape[0], f, c)
+            dh.dh_server_wait(srv, t, -1)
+        finally:
+            dh.dh_server_destroy(srv)
+        assert np.array_equal(f.numpy().view(np.uint32), fa.view(np.uint32))
+        assert np.array_equal(c.numpy().view(np.uint32), ca.view(np.uint32))
+    finally:
+        dh.dh_destroy(h)

@@ -73,3 +73,15 @@ def test_noalloc_matches_allocating_entry_on_two_calls_in_a_row():
     # once the array is resident, a call leaves the device's free memory unchanged
     before, after = got3[2]
     assert before == after
+
+
+def test_noalloc_lg_basis_matches_oracle():
+    from oracle import digholo_oracle as orc
+    s = syn.with_(syn.setup_batching(), basis="lg")
+    fr = syn.make_frames(s, 150, seed=124)["frames"]       # several chunks of the static scratch
+    got = _run(s, fr, noalloc=True)
+    ref = _run(s, fr, noalloc=False)
+    assert np.all(np.isfinite(got[1]))
+    assert rel_l2(got[1], ref[1]).max() <= COEF_TOL
+    _, c_ref = orc.process_batch(fr[:3], s)
+    assert rel_l2(got[1][:3], c_ref).max() <= COEF_TOL
