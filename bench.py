@@ -338,29 +338,25 @@ def run_ours(args, ws, rank, local):
                     "kernel_share": tms / sum(v[1] for v in prof.values()),
                     "step_frac": (value / ws) * bpf / 1e9 / peak}
 
-    # ---- end to end through the public API: pinned host frames in, fields and coefficients out
+    # ---- end to end through the public host-buffer call: pinned host frames in, fields and coefficients out
+    # (dh_process_batch_host overlaps the copies of one chunk with the kernels of the next; it returns when
+    # the outputs are in host memory, so the wall clock around the calls is the end-to-end time)
     host_f = torch.empty((frames_n, P, m, m), dtype=torch.complex64).pin_memory()
     host_c = torch.empty((frames_n, P, modes), dtype=torch.complex64).pin_memory()
-    dev_in = torch.empty_like(inputs[0])
     e2e_steps = max(3, min(args.steps, 20))
 
     def e2e_step():
-        dev_in.copy_(host, non_blocking=True)
-        dh.dh_process_batch(h, dev_in, dh.DH_DTYPE_U16, frames_n, fields, coefs, stream)
-        host_f.copy_(fields, non_blocking=True)
-        host_c.copy_(coefs, non_blocking=True)
-        stream.synchronize()
+        dh.dh_process_batch_host(h, host, dh.DH_DTYPE_U16, frames_n, host_f, host_c, stream)
 
     for _ in range(2):
         e2e_step()
     barrier()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
     for _ in range(e2e_steps):
         e2e_step()
-    e1.record(stream)
     torch.cuda.synchronize()
-    e_ms = max_over_ranks(e0.elapsed_time(e1), ws, dev)
+    e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0), ws, dev)
     e2e = {"value": whole_job_rate(ws, frames_n, e2e_steps, e_ms), "unit": "frames/s",
            "h2d_bytes_per_step": int(host.numel() * 2),
            "d2h_bytes_per_step": int(host_f.numel() * 8 + host_c.numel() * 8), "steps": e2e_steps}

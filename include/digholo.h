@@ -174,6 +174,18 @@ int dh_get_axes(dh_handle h, int pol, double* x, double* y);
 int dh_process_batch(dh_handle h, const void* d_frames, int dtype, int batch, void* d_fields, void* d_coefs,
                      void* stream);
 
+/* Host-buffer variant of dh_process_batch, as the guide's own processing call works on frames in host memory
+ * (digHoloSetBatch / digHoloSetBatchUint16, then digHoloProcessBatch).  h_frames: host [batch][height][width]
+ * uint16 or float32; h_fields (nullable): host complex64 [batch][pol][M][M]; h_coefs (nullable, ignored when
+ * G = 0): host complex64 [batch][pol][modes].  The batch is cut into chunks that cycle over three internal
+ * streams with their own device staging buffers (at most 256 MiB each, owned by the handle and kept for the
+ * next call), so that host-to-device copies, reconstruction and device-to-host copies of consecutive chunks
+ * overlap; the kernels and results are those of dh_process_batch.  The work starts after the work already
+ * queued on stream; the call returns when the outputs are in host memory (stream then also waits for it).
+ * Page-locked host buffers are needed for the copies to overlap; pageable ones work but copy synchronously. */
+int dh_process_batch_host(dh_handle h, const void* h_frames, int dtype, int batch, void* h_fields, void* h_coefs,
+                          void* stream);
+
 /* As dh_process_batch, and also writes the Fourier window that is inverse transformed for every (frame, pol)
  * (digHoloGetFourierPlaneWindow): d_window complex64 [batch][pol][M][M] with
  * d_window[q][p] = mask(p, q) (-1)^(p+q) F(k0x - M/2 + p, k0y - M/2 + q) / N^2, F the window spectrum in the

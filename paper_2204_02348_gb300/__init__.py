@@ -92,6 +92,7 @@ _PROTOS = {
     "dh_process_batch_window": [_i, _p, _i, _i, _p, _p, _p, _p],
     "dh_process_batch_noalloc": [_i, _p, _i, _i, _p, _p, _p],
     "dh_process_batch_avg": [_i, _p, _i, _i, _i, _i, _p, _p, _p],
+    "dh_process_batch_host": [_i, _p, _i, _i, _p, _p, _p],
     "dh_score_settings": [_i, _p, _i, _i, ctypes.POINTER(dh_setting), _i, _p, _p],
     "dh_set_profiling": [_i, _i],
     "dh_get_device_status": [_i, ctypes.POINTER(_i)],
@@ -130,7 +131,11 @@ def _ptr(t) -> int:
         return None
     if isinstance(t, int):
         return t
-    return t.data_ptr()
+    if hasattr(t, "data_ptr"):
+        return t.data_ptr()
+    if not t.flags["C_CONTIGUOUS"]:
+        raise ValueError("numpy arrays passed to the library must be C-contiguous")
+    return t.ctypes.data
 
 
 def _stream(s) -> int:
@@ -235,6 +240,11 @@ def dh_process_batch_window(h: int, frames, dtype: int, batch: int, window, fiel
                             stream=None) -> None:
     _check(_lib.dh_process_batch_window(h, _ptr(frames), dtype, batch, _ptr(window), _ptr(fields), _ptr(coefs),
                                         _stream(stream)))
+
+
+def dh_process_batch_host(h: int, frames, dtype: int, batch: int, fields=None, coefs=None, stream=None) -> None:
+    """frames, fields, coefs: host tensors or numpy arrays (page-locked for overlapped copies)."""
+    _check(_lib.dh_process_batch_host(h, _ptr(frames), dtype, batch, _ptr(fields), _ptr(coefs), _stream(stream)))
 
 
 def dh_process_batch_avg(h: int, frames, dtype: int, batch: int, avg_count: int, avg_mode: int, fields=None,

@@ -41,6 +41,7 @@ Handle* get_handle(dh_handle h) {
 }
 
 static void release_device(Handle* H) {
+    release_pipe(H);
     if (H->d_blob || H->d_scratch || H->d_hg) {
         int cur = -1;
         cudaGetDevice(&cur);

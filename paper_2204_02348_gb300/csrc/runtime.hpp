@@ -41,6 +41,8 @@ struct Profiler : dhk::StageTimer {
     ~Profiler() override;
 };
 
+struct HostPipe;   // streams and staging buffers of dh_process_batch_host (host.cu)
+
 struct Handle {
     std::mutex mu;
     Settings s;
@@ -54,9 +56,13 @@ struct Handle {
     size_t scratch_bytes = 0;
     void* d_hg = nullptr;         // HG coefficients ahead of an output-basis transform (device)
     size_t hg_bytes = 0;
+    HostPipe* pipe = nullptr;     // host-buffer pipeline, created on first use
     Profiler prof;
     dhk::StageTimer* timer() { return prof.on ? &prof : nullptr; }
 };
+
+// Free the host-buffer pipeline of a handle (streams, events, device buffers).
+void release_pipe(Handle* H);
 
 int fail(int code, const std::string& why);
 int cuda_fail(cudaError_t e, const char* where);

@@ -212,3 +212,14 @@ def test_process_batch_avg_argument_errors_before_device_work():
         assert dh._lib.dh_process_batch_avg(12345, fake, 0, 1, 2, 0, None, None, None) == dh.DH_ERROR_INVALIDHANDLE
     finally:
         dh.dh_destroy(h)
+
+
+def test_process_batch_host_argument_errors_before_device_work():
+    h = dh.dh_create()
+    try:
+        dh.configure(h, syn.setup_plain())
+        assert dh._lib.dh_process_batch_host(h, None, 0, 1, None, None, None) == dh.DH_ERROR_NULLPOINTER
+        assert dh._lib.dh_process_batch_host(h, 16, 9, 1, None, None, None) == dh.DH_ERROR_INVALIDARGUMENT
+        assert dh._lib.dh_process_batch_host(12345, 16, 0, 1, None, None, None) == dh.DH_ERROR_INVALIDHANDLE
+    finally:
+        dh.dh_destroy(h)

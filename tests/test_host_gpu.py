@@ -1,0 +1,87 @@
+"""dh_process_batch_host: host buffers in and out through the chunked three-stream pipeline, against
+dh_process_batch on device buffers (bit-identical: the same kernels on the same frames) and the oracle."""
+import math
+
+import numpy as np
+import pytest
+
+from gpu_util import COEF_TOL, FIELD_TOL, rel_l2
+from oracle import digholo_oracle as orc
+from synth import holograms as syn
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _device(dh, torch, h, setup, frames):
+    m, modes, _ = dh.dh_get_output_dims(h)
+    fr = torch.from_numpy(frames).cuda()
+    dt = dh.DH_DTYPE_U16 if frames.dtype == np.uint16 else dh.DH_DTYPE_F32
+    f = torch.empty((frames.shape[0], setup.pol_count, m, m), dtype=torch.complex64, device="cuda")
+    c = torch.empty((frames.shape[0], setup.pol_count, modes), dtype=torch.complex64, device="cuda") if modes else None
+    dh.dh_process_batch(h, fr, dt, frames.shape[0], f, c)
+    torch.cuda.synchronize()
+    return f.cpu().numpy(), (None if c is None else c.cpu().numpy())
+
+
+def _host(dh, torch, h, setup, frames, pinned=True, fields=True):
+    m, modes, _ = dh.dh_get_output_dims(h)
+    dt = dh.DH_DTYPE_U16 if frames.dtype == np.uint16 else dh.DH_DTYPE_F32
+    nan = complex(math.nan, math.nan)
+    if pinned:
+        hin = torch.from_numpy(frames).pin_memory()
+        f = torch.full((frames.shape[0], setup.pol_count, m, m), nan, dtype=torch.complex64).pin_memory()
+        c = torch.full((frames.shape[0], setup.pol_count, modes), nan, dtype=torch.complex64).pin_memory()
+    else:
+        hin = np.ascontiguousarray(frames)
+        f = np.full((frames.shape[0], setup.pol_count, m, m), nan, dtype=np.complex64)
+        c = np.full((frames.shape[0], setup.pol_count, modes), nan, dtype=np.complex64)
+    dh.dh_process_batch_host(h, hin, dt, frames.shape[0], f if fields else None, c)
+    f = np.asarray(f) if not pinned else f.numpy()
+    c = np.asarray(c) if not pinned else c.numpy()
+    return f, c
+
+
+@pytest.mark.parametrize("name,count", [("batching", 300), ("plain", 5), ("precision", 70)])
+def test_host_pipeline_equals_device_entry(name, count):
+    import torch
+    import paper_2204_02348_gb300 as dh
+    s = syn.WORKLOADS[name]()
+    fr = syn.make_frames(s, count, seed=140)["frames"]
+    h = dh.dh_create()
+    try:
+        dh.configure(h, s)
+        fd, cd = _device(dh, torch, h, s, fr)
+        fh, ch = _host(dh, torch, h, s, fr)
+        assert np.array_equal(fh.view(np.uint32), fd.view(np.uint32))
+        assert np.array_equal(ch.view(np.uint32), cd.view(np.uint32))
+        # a second call reuses the pipeline buffers; pageable numpy buffers copy synchronously, same results
+        fh2, ch2 = _host(dh, torch, h, s, fr[: max(1, count // 2)], pinned=False)
+        assert np.array_equal(fh2.view(np.uint32), fd[: max(1, count // 2)].view(np.uint32))
+        assert np.array_equal(ch2.view(np.uint32), cd[: max(1, count // 2)].view(np.uint32))
+    finally:
+        dh.dh_destroy(h)
+    f_ref, c_ref = orc.process_batch(fr[:2], s)
+    assert rel_l2(fh[:2], f_ref).max() <= FIELD_TOL
+    assert rel_l2(ch[:2], c_ref).max() <= COEF_TOL
+
+
+def test_host_pipeline_generic_geometry_lg_basis_coefficients_only():
+    import torch
+    import paper_2204_02348_gb300 as dh
+    s = syn.with_(syn.serving_geometry("1024x1024_1pol", np.random.default_rng(141)), basis="lg")
+    fr = syn.make_frames(s, 40, seed=142)["frames"]
+    h = dh.dh_create()
+    try:
+        dh.configure(h, s)
+        fd, cd = _device(dh, torch, h, s, fr)
+        _, ch = _host(dh, torch, h, s, fr, fields=False)
+        assert np.array_equal(ch.view(np.uint32), cd.view(np.uint32))
+    finally:
+        dh.dh_destroy(h)
