@@ -19,7 +19,9 @@ in float64 / complex128, with numpy matrix products as the only library primitiv
    the HG overlaps (digHoloConfigSetBasisType*);
 6. total captured power per alignment candidate (the quantity the AutoAlign search scores);
 7. batch averaging (digHoloSetBatchAvg, "Averaging modes"): the windows of the frames of one averaging
-   group, rotated into phase with the group's first frame, averaged, then inverse transformed once.
+   group, rotated into phase with the group's first frame, averaged, then inverse transformed once;
+8. reference-wave calibration (digHoloConfigSetRefCalibrationIntensity): the frame divided pixel by pixel by
+   the reference's relative amplitude sqrt(cal / max cal) before the transform.
 
 Conventions the paper leaves open (the same readings are used by the CUDA library):
 
@@ -153,6 +155,29 @@ def pol_geometry(setup, p: int, tilt_deg=None, defocus=None, waist=None) -> PolG
 # ---------------------------------------------------------------------------------------------------
 # Pipeline step 1: the window and its spectrum on the selected bins
 # ---------------------------------------------------------------------------------------------------
+
+
+def reference_calibration_factor(cal) -> np.ndarray:
+    """Per-pixel factor that removes a non-uniform reference amplitude: the measured reference intensity
+    (uint16 [H][W], or [L][H][W] per wavelength, of which the single wavelength used here is the first) is
+    normalised by its maximum over all pixels and frames, and the frame is multiplied by
+    sqrt(max / cal) = 1 / (relative reference amplitude), 0 where cal = 0 (no reference light)."""
+    c = np.asarray(cal, dtype=np.float64)
+    top = float(c.max())
+    first = c[0] if c.ndim == 3 else c
+    out = np.zeros_like(first)
+    lit = first > 0
+    out[lit] = np.sqrt(top / first[lit])
+    return out
+
+
+def calibrated(frame: np.ndarray, setup) -> np.ndarray:
+    """The frame as the transform sees it: with a reference calibration, divided by the reference's
+    relative amplitude; otherwise unchanged."""
+    cal = getattr(setup, "ref_cal", None)
+    if cal is None:
+        return frame
+    return np.asarray(frame, dtype=np.float64) * reference_calibration_factor(cal)
 
 
 def cut_window(frame: np.ndarray, g: PolGeometry) -> np.ndarray:
@@ -332,8 +357,9 @@ def process_batch(frames: np.ndarray, setup) -> Tuple[np.ndarray, np.ndarray]:
     fields = np.empty((B, setup.pol_count, m, m), dtype=np.complex128)
     coefs = np.empty((B, setup.pol_count, modes), dtype=np.complex128)
     for b in range(B):
+        frame = calibrated(frames[b], setup)
         for p, g in enumerate(geos):
-            _, _, e, c = process_window(frames[b], g)
+            _, _, e, c = process_window(frame, g)
             fields[b, p] = e
             coefs[b, p] = c if basis == "hg" else basis_coefficients(e, g, basis, transform)
     return fields, coefs
@@ -390,7 +416,7 @@ def process_batch_avg(frames: np.ndarray, setup, avg_count: int, avg_mode: int =
     for b in range(B):
         boxes = []
         for j in range(A):
-            fr = frames[avg_member_index(b, j, B, A, avg_mode)]
+            fr = calibrated(frames[avg_member_index(b, j, B, A, avg_mode)], setup)
             boxes.append([window_spectrum(cut_window(fr, g), g) * masks[p] for p, g in enumerate(geos)])
         a = align_phases([[boxes[j][p] * corr[p] for p in range(len(geos))] for j in range(A)])
         for p, g in enumerate(geos):
@@ -409,11 +435,12 @@ def score_settings(frames: np.ndarray, setup, tilt_deg: np.ndarray, defocus: np.
     B, S = frames.shape[0], tilt_deg.shape[0]
     power = np.zeros((B, S))
     for b in range(B):
+        frame = calibrated(frames[b], setup)
         for s in range(S):
             tot = 0.0
             for p in range(setup.pol_count):
                 g = pol_geometry(setup, p, tilt_deg=tilt_deg[s, p], defocus=defocus[s, p], waist=waist[s, p])
-                win = cut_window(frames[b], g)
+                win = cut_window(frame, g)
                 e = reconstruct_field(window_spectrum(win, g), window_mask(g), g)
                 c = overlap(e, g)
                 tot += float(np.sum(np.abs(c) ** 2))

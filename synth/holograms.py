@@ -68,6 +68,8 @@ class Setup:
     fill_factor: bool = False                    # reconstruct with the pixel-response (fill-factor) correction
     basis: str = "hg"                            # coefficient basis: "hg", "lg" or "custom"
     basis_transform: object = None               # custom basis: complex matrix [modes_out][modes_in]
+    ref_amplitude: object = None                 # simulator: relative reference amplitude on the camera [H][W]
+    ref_cal: object = None                       # reconstruction: measured reference intensity, uint16 [H][W]
     extra: dict = field(default_factory=dict)
 
     @property
@@ -284,8 +286,11 @@ def _render(setup: Setup, pol_tabs, coefs_p, rng: np.random.Generator, ref_phase
     inten = np.empty((H, W), dtype=np.float64)
     amps = []
     rot = complex(math.cos(ref_phase), math.sin(ref_phase))
+    amp = None if setup.ref_amplitude is None else np.asarray(setup.ref_amplitude, dtype=np.float64)
     for p in range(P):
         R, ux, uy = pol_tabs[p]
+        if amp is not None:
+            R = R * amp[:, p * strip:(p + 1) * strip]
         C = np.zeros((setup.signal_groups, setup.signal_groups), dtype=np.complex128)
         C[ni, mi] = coefs_p[p]                          # C[n][m]
         S = uy.T @ C @ ux                               # [H][strip]
@@ -301,6 +306,20 @@ def _render(setup: Setup, pol_tabs, coefs_p, rng: np.random.Generator, ref_phase
         scale = 1.0 / peak
         frame = (inten * scale + rng.normal(0.0, 1e-3, size=inten.shape)).astype(np.float32)
     return frame, np.array(amps) * scale
+
+
+def reference_profile(setup: Setup, sigma_fraction: float = 0.45, floor: int = 600, peak: int = 4000):
+    """A non-uniform reference beam for calibration tests: a measured reference intensity cal (uint16 [H][W],
+    a Gaussian of width sigma_fraction x frame size centred on the frame, from `floor` to `peak` counts) and
+    the relative amplitude sqrt(cal / max cal) that the simulator gives the reference (so the measured
+    calibration describes the simulated beam exactly)."""
+    H, W = setup.frame_h, setup.frame_w
+    y = (np.arange(H) - (H - 1) / 2.0) / (sigma_fraction * H)
+    x = (np.arange(W) - (W - 1) / 2.0) / (sigma_fraction * W)
+    g = np.exp(-0.5 * (y[:, None] ** 2 + x[None, :] ** 2))
+    cal = np.rint(floor + (peak - floor) * g).astype(np.uint16)
+    amp = np.sqrt(cal.astype(np.float64) / float(cal.max()))
+    return cal, amp
 
 
 def make_frames(setup: Setup, count: int, seed: int = BASE_SEED, first: int = 0):

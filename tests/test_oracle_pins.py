@@ -426,3 +426,56 @@ def test_avg_of_identical_frames_and_drift_removal():
     assert err(fa[0, 0]) < min(err(singles[j, 0]) for j in range(6))
     plain_mean = singles[:, 0].mean(axis=0)
     assert np.linalg.norm(plain_mean) < 0.8 * np.linalg.norm(fa[0, 0])
+
+
+# ----------------------------------------------------------------------------- reference calibration
+
+
+def test_reference_calibration_factor_values():
+    cal = np.array([[4000, 1000], [0, 250]], dtype=np.uint16)
+    f = orc.reference_calibration_factor(cal)
+    assert np.array_equal(f, np.array([[1.0, 2.0], [0.0, 4.0]]))           # sqrt(4000 / cal), 0 for dark pixels
+    # with several wavelength frames the maximum is taken over all of them; the first frame is used
+    cal3 = np.stack([cal, np.full((2, 2), 16000, dtype=np.uint16)])
+    assert np.array_equal(orc.reference_calibration_factor(cal3), np.array([[2.0, 4.0], [0.0, 8.0]]))
+
+
+def test_reference_calibration_removes_a_nonuniform_reference_exactly_on_the_cross_term():
+    # linear hologram 2 Re(S a R*) with a non-uniform reference amplitude a = sqrt(cal / max cal): after the
+    # calibration it is exactly the uniform-reference hologram 2 Re(S R*), so the reconstructions agree to
+    # rounding, pixel for pixel (a transposed or wrongly scaled factor fails)
+    s = syn.setup_batching()
+    cal, amp = syn.reference_profile(s, sigma_fraction=0.3)
+    assert amp.shape == (s.frame_h, s.frame_w) and amp.min() < 0.5
+    rng = np.random.default_rng(50)
+    H, W = s.frame_h, s.frame_w
+    cross = rng.standard_normal((H, W))            # any pattern: the identity is pixelwise
+    f_uniform, c_uniform = orc.process_batch(cross[None], s)
+    sc = syn.with_(s, ref_cal=cal)
+    f_cal, c_cal = orc.process_batch((cross * amp)[None], sc)
+    assert np.allclose(f_cal, f_uniform, rtol=0, atol=1e-12 * np.abs(f_uniform).max())
+    assert np.allclose(c_cal, c_uniform, rtol=0, atol=1e-12 * np.abs(c_uniform).max())
+
+
+def test_reference_calibration_improves_recovery_on_simulated_frames():
+    # a reference beam narrower than the frame, so its amplitude falls steeply across both polarisation
+    # windows (beams at W/4 and 3W/4): uncalibrated, the field carries that envelope
+    s0 = syn.setup_batching()
+    cal, amp = syn.reference_profile(s0, sigma_fraction=0.15, floor=200)
+    s = syn.with_(s0, ref_amplitude=amp)
+    d = syn.make_frames(s, 1, seed=51)
+    g = orc.pol_geometry(s, 0)
+    xp, yp = orc.output_axes(g)
+    true = np.zeros((len(yp), len(xp)), dtype=complex)
+    u_x = syn.hg_closed_form(s.signal_groups, xp, s.waist[0])
+    u_y = syn.hg_closed_form(s.signal_groups, yp, s.waist[0])
+    for k, (m, n) in enumerate(syn.mode_indices(s.signal_groups)):
+        true += d["coefs_true"][0, 0, k] * np.outer(u_y[n], u_x[m])
+
+    def err(e):
+        z = np.vdot(true, e)
+        return np.linalg.norm(e * np.conj(z) / abs(z) / np.linalg.norm(e) - true / np.linalg.norm(true))
+
+    f_plain, _ = orc.process_batch(d["frames"], s)
+    f_cal, _ = orc.process_batch(d["frames"], syn.with_(s, ref_cal=cal))
+    assert err(f_cal[0, 0]) < 0.5 * err(f_plain[0, 0])
