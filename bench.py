@@ -8,7 +8,9 @@ windows, 64x64 fields and 45 Hermite-Gaussian coefficients per window.  Syntheti
 
 Prints one JSON line (rank 0).  ``value`` is whole-job frames/s with the frames already in HBM; ``e2e`` is the
 same metric through the public API from pinned host frames to host results; ``roofline`` is the dominant
-kernel's algorithmic bytes per launch over its event-timed launch duration against the measured HBM peak;
+kernel's algorithmic work per launch over its event-timed launch duration, against the binding ceiling: the
+FP32 peak (derived from SM count, lanes and clock) when algorithmic flops limit the frame rate before the
+measured HBM bandwidth does, else the HBM peak; both are reported under ``roofline.alu`` / ``roofline.hbm``;
 ``cpu_baseline`` is the FP64 oracle on the host cores.  ``--impl reference`` times the oracle itself, as the
 reference arm.  Multi-GPU runs (torchrun) are weak-scaled: every rank processes its own batch, with no
 collective on the data path.
@@ -90,6 +92,32 @@ def bytes_per_frame(setup, m, modes):
     return setup.pol_count * (n * n * px_bytes + m * m * 8 + modes * 8)
 
 
+def flops_per_frame(setup, m, modes):
+    """Algorithmic FP32 flops per frame by the nominal counts: 2.5 N log2 N per real and 5 N log2 N per
+    complex transform of length N, the forward transform pruned to the M box columns (N real rows, M complex
+    columns), the M x M inverse, and the separable overlap 4 M^2 G + 4 M modes."""
+    n = setup.window
+    g = setup.group_count
+    lg_n, lg_m = math.log2(n), math.log2(m)
+    per_window = (n * 2.5 * n * lg_n + m * 5.0 * n * lg_n + 2 * m * 5.0 * m * lg_m
+                  + (4.0 * m * m * g + 4.0 * m * modes if g else 0.0))
+    return setup.pol_count * per_window
+
+
+def fp32_peak_tflops(dev):
+    """FP32 peak derived from unit counts and the maximum SM clock: SMs x 128 FP32 lanes x 2 flops (FMA) x
+    clock (MEASURED_PEAKS.json sm_max_mhz, else 2070 MHz)."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz, src = 2070.0, "nominal 2070 MHz"
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz, src = float(json.load(f)["sm_max_mhz"]), "MEASURED_PEAKS.json sm_max_mhz"
+    except Exception:
+        pass
+    return sms * 128 * 2 * mhz * 1e6 / 1e12, f"derived: {sms} SMs x 128 FP32 lanes x 2 flops x {mhz:.0f} MHz ({src})"
+
+
 def measured_peak():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -100,14 +128,23 @@ def measured_peak():
         return FALLBACK_HBM_GBS, "fallback 6.8 TB/s"
 
 
-def kernel_source_hash():
+# source file of each timed kernel; its hash also covers the device headers every kernel includes
+KERNEL_SOURCES = {"k_fused128": "k_fused.cu", "k_yinv_tc": "k_overlap_tc.cu", "k_ypass": "k_split.cu",
+                  "k_xpass": "k_split.cu", "k_yinv": "k_split.cu"}
+DEVICE_HEADERS = ("fft.cuh", "kernels.cuh", "sync.cuh")
+
+
+def kernel_source_hash(kernel):
+    """sha256 (first 16 hex digits) over the kernel's source file and the shared device headers, or None
+    for a kernel without a recorded source."""
+    if kernel not in KERNEL_SOURCES:
+        return None
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2204_02348_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(name.encode())
-                h.update(f.read())
+    for name in (KERNEL_SOURCES[kernel],) + DEVICE_HEADERS:
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
     return h.hexdigest()[:16]
 
 
@@ -117,7 +154,7 @@ def recorded_traffic(kernel, frames_per_launch):
     path = os.path.join(ROOT, "profiles", "traffic.md")
     if not os.path.exists(path):
         return None
-    src = kernel_source_hash()
+    src = kernel_source_hash(kernel)
     for line in open(path):
         m = re.match(r"\|\s*(\w+)\s*\|\s*([0-9a-f]+)\s*\|\s*([0-9.eE+]+)\s*\|\s*(\d+)\s*\|", line)
         if m and m.group(1) == kernel and m.group(2) == src:
@@ -332,11 +369,21 @@ def run_ours(args, ws, rank, local):
         avg_s = tms / nl / 1e3
         achieved = frames_per_launch * bpf / avg_s / 1e9
         traffic = recorded_traffic(name, frames_per_launch)
-        roofline = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                    "frac": achieved / peak, "traffic": traffic, "peak_source": peak_src,
-                    "bytes_per_frame": bpf, "frames_per_launch": frames_per_launch,
+        # the binding ceiling is the lower of the HBM and the FP32 ones (frames/s at peak bytes or flops)
+        fpf = flops_per_frame(setup, m, modes)
+        fpk, fpk_src = fp32_peak_tflops(dev)
+        alu_tflops = frames_per_launch * fpf / avg_s / 1e12
+        hbm = {"achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+               "peak_source": peak_src, "bytes_per_frame": bpf, "ceiling_frames_per_s": peak * 1e9 / bpf}
+        alu = {"achieved": alu_tflops, "peak": fpk, "unit": "TFLOP/s", "frac": alu_tflops / fpk,
+               "peak_source": fpk_src, "flops_per_frame": fpf, "ceiling_frames_per_s": fpk * 1e12 / fpf}
+        bound, lim = ("alu", alu) if alu["ceiling_frames_per_s"] < hbm["ceiling_frames_per_s"] else ("hbm", hbm)
+        roofline = {"bound": bound, "kernel": name, "achieved": lim["achieved"], "peak": lim["peak"],
+                    "unit": lim["unit"], "frac": lim["frac"], "traffic": traffic, "peak_source": lim["peak_source"],
+                    "frames_per_launch": frames_per_launch,
                     "kernel_share": tms / sum(v[1] for v in prof.values()),
-                    "step_frac": (value / ws) * bpf / 1e9 / peak}
+                    "step_frac": (value / ws) / lim["ceiling_frames_per_s"],
+                    "hbm": hbm, "alu": alu}
 
     # ---- end to end through the public host-buffer call: pinned host frames in, fields and coefficients out
     # (dh_process_batch_host overlaps the copies of one chunk with the kernels of the next; it returns when

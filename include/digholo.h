@@ -153,6 +153,22 @@ int dh_set_basis_type(dh_handle h, int basis);
  * and modes_in * modes_out <= 2^24, else DH_ERROR_INVALIDDIMENSION; NULL transform gives DH_ERROR_NULLPOINTER. */
 int dh_set_basis_transform(dh_handle h, int modes_in, int modes_out, const void* transform);
 
+/* Reference-wave calibration (digHoloConfigSetRefCalibrationIntensity): cal is a host uint16 array of
+ * wavelength_count frames [height][width], the measured intensity of the reference wave alone (any exposure).
+ * It is normalised by its maximum over all its pixels and frames, and every frame is multiplied pixel by pixel
+ * by sqrt(max / cal) = 1 / (relative reference amplitude) before the transform (0 where cal = 0), which removes
+ * a non-uniform reference amplitude from the off-axis term.  One wavelength is processed here, so the first
+ * calibration frame is used.  The array is copied; the calibration is enabled.  width x height must equal the
+ * frame size when a batch is processed (DH_ERROR_INVALIDDIMENSION otherwise).  As in the guide, an invalid
+ * call (cal NULL: DH_ERROR_NULLPOINTER; a count or size < 1, or an all-zero array: DH_ERROR_INVALIDARGUMENT)
+ * disables the calibration: the one exception to "a failed call leaves the settings unchanged".  With the
+ * calibration enabled, batches take the generic multi-kernel path. */
+int dh_set_ref_calibration(dh_handle h, const uint16_t* cal, int wavelength_count, int width, int height);
+
+/* Enable (nonzero) or disable the reference calibration last set (digHoloConfigSetRefCalibrationEnabled);
+ * enabling without one gives DH_ERROR_INVALIDARGUMENT. */
+int dh_set_ref_calibration_enabled(dh_handle h, int enabled);
+
 /* Overlap arithmetic: DH_PRECISION_FP32 or DH_PRECISION_SPLIT_BF16. */
 int dh_set_precision(dh_handle h, int precision);
 

@@ -85,6 +85,8 @@ _PROTOS = {
     "dh_set_precision": [_i, _i],
     "dh_set_fill_factor_correction": [_i, _i],
     "dh_set_basis_type": [_i, _i],
+    "dh_set_ref_calibration": [_i, _p, _i, _i, _i],
+    "dh_set_ref_calibration_enabled": [_i, _i],
     "dh_set_basis_transform": [_i, _i, _i, _p],
     "dh_get_output_dims": [_i, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_d)],
     "dh_get_axes": [_i, _i, ctypes.POINTER(_d), ctypes.POINTER(_d)],
@@ -200,6 +202,19 @@ def dh_set_basis(h: int, pol: int, waist: float, group_count: int) -> None:
 
 def dh_set_fill_factor_correction(h: int, enabled: bool) -> None:
     _check(_lib.dh_set_fill_factor_correction(h, 1 if enabled else 0))
+
+
+def dh_set_ref_calibration(h: int, cal) -> None:
+    """cal: uint16 array [height][width] or [wavelengths][height][width] (copied by the library)."""
+    import numpy as np
+    c = np.ascontiguousarray(np.asarray(cal, dtype=np.uint16))
+    if c.ndim == 2:
+        c = c[None]
+    _check(_lib.dh_set_ref_calibration(h, c.ctypes.data_as(_p), c.shape[0], c.shape[2], c.shape[1]))
+
+
+def dh_set_ref_calibration_enabled(h: int, enabled: bool) -> None:
+    _check(_lib.dh_set_ref_calibration_enabled(h, 1 if enabled else 0))
 
 
 def dh_set_basis_type(h: int, basis: int) -> None:
@@ -341,7 +356,7 @@ def make_setting(tilt_deg, defocus, waist) -> dh_setting:
 def configure(h: int, setup) -> None:
     """Apply an acquisition description (attributes frame_w, frame_h, pol_count, pixel, wavelength, window,
     beam_centre, tilt_deg, defocus, radius_deg, ifft_size, group_count, waist and optionally precision,
-    fill_factor, basis and basis_transform) to a handle through the setters."""
+    fill_factor, basis, basis_transform and ref_cal) to a handle through the setters."""
     dh_set_frame(h, setup.frame_w, setup.frame_h, setup.pol_count, setup.pixel)
     dh_set_wavelength(h, setup.wavelength)
     dh_set_fft_window(h, setup.window, setup.window)
@@ -355,6 +370,9 @@ def configure(h: int, setup) -> None:
         dh_set_basis(h, p, setup.waist[p], setup.group_count)
     dh_set_precision(h, getattr(setup, "precision", DH_PRECISION_FP32))
     dh_set_fill_factor_correction(h, bool(getattr(setup, "fill_factor", False)))
+    cal = getattr(setup, "ref_cal", None)
+    if cal is not None:
+        dh_set_ref_calibration(h, cal)
     basis = getattr(setup, "basis", "hg")
     if basis == "custom":
         dh_set_basis_transform(h, setup.basis_transform)

@@ -100,7 +100,7 @@ int upload_plan(const Settings& s, const Geometry& g, const Tables& t, void** ou
     const int zero_status[4] = {0, 0, 0, 0};
     const size_t o_st = b.put(zero_status, sizeof zero_status);
     const size_t o_bt = b.put(t.basis_tt.data(), t.basis_tt.size() * 4);
-    size_t o_pol[DH_MAX_POLS][9] = {};
+    size_t o_pol[DH_MAX_POLS][10] = {};
     for (int p = 0; p < g.pols; ++p) {
         const PolTables& pt = t.pol[p];
         o_pol[p][0] = b.put(pt.mask_lo.data(), pt.mask_lo.size() * 4);
@@ -112,6 +112,7 @@ int upload_plan(const Settings& s, const Geometry& g, const Tables& t, void** ou
         o_pol[p][6] = b.put(pt.hg_x.data(), pt.hg_x.size() * 4);
         o_pol[p][7] = b.put(pt.hg_y.data(), pt.hg_y.size() * 4);
         o_pol[p][8] = b.put(pt.hgy_tc.data(), pt.hgy_tc.size() * 2);
+        o_pol[p][9] = b.put(pt.cal.data(), pt.cal.size() * 4);
     }
     void* d = nullptr;
     cudaError_t e = cudaMalloc(&d, b.bytes.size());
@@ -161,6 +162,7 @@ int upload_plan(const Settings& s, const Geometry& g, const Tables& t, void** ou
         pd.hg_x = (const float*)(base + o_pol[p][6]);
         pd.hg_y = (const float*)(base + o_pol[p][7]);
         pd.hgy_tc = (const uint16_t*)(base + o_pol[p][8]);
+        pd.cal = t.pol[p].cal.empty() ? nullptr : (const float*)(base + o_pol[p][9]);
     }
     *out_blob = d;
     return DH_SUCCESS;
@@ -628,6 +630,36 @@ int dh_set_precision(dh_handle h, int precision) {
     if (precision != DH_PRECISION_FP32 && precision != DH_PRECISION_SPLIT_BF16)
         return fail(DH_ERROR_INVALIDARGUMENT, "precision must be DH_PRECISION_FP32 or DH_PRECISION_SPLIT_BF16");
     H->s.precision = precision;
+    H->dirty = true;
+    return DH_SUCCESS;
+}
+
+int dh_set_ref_calibration(dh_handle h, const uint16_t* cal, int wavelength_count, int width, int height) {
+    GET_HANDLE(h);
+    H->dirty = true;
+    if (!cal || wavelength_count < 1 || width < 1 || height < 1) {
+        H->s.cal_on = 0;   // as the guide specifies: an invalid calibration disables the calibration
+        return fail(cal ? DH_ERROR_INVALIDARGUMENT : DH_ERROR_NULLPOINTER, "invalid reference calibration; calibration disabled");
+    }
+    const size_t px = (size_t)width * height;
+    uint16_t top = 0;
+    for (size_t i = 0; i < px * wavelength_count; ++i) top = std::max(top, cal[i]);
+    if (top == 0) {
+        H->s.cal_on = 0;
+        return fail(DH_ERROR_INVALIDARGUMENT, "reference calibration is all zero; calibration disabled");
+    }
+    H->s.cal.assign(cal, cal + px);
+    H->s.cal_w = width;
+    H->s.cal_h = height;
+    H->s.cal_max = (double)top;
+    H->s.cal_on = 1;
+    return DH_SUCCESS;
+}
+
+int dh_set_ref_calibration_enabled(dh_handle h, int enabled) {
+    GET_HANDLE(h);
+    if (enabled && H->s.cal.empty()) return fail(DH_ERROR_INVALIDARGUMENT, "no reference calibration has been set");
+    H->s.cal_on = enabled != 0;
     H->dirty = true;
     return DH_SUCCESS;
 }

@@ -381,6 +381,7 @@ static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
 bool use_fused(const dhk::Plan& P) {
     if (P.n != dhk::kFN || P.groups > dhk::kFGMax || P.precision != DH_PRECISION_FP32) return false;
+    if (P.pol[0].cal) return false;   // the reference calibration runs on the generic path
     return P.m == 32 || P.m == 48 || P.m == 64;
 }
 

@@ -42,7 +42,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_ypass(const __grid_constant__ P
         for (int idx = tid; idx < N * C; idx += nthr) {
             const int y = idx >> logc, c = idx & (C - 1);
             const T* row = fr + (size_t)(pd.oy + y) * P.width + pd.ox + x0 + c;
-            smem[idx] = make_float2(to_f(row[0]), to_f(row[half]));
+            float2 v = make_float2(to_f(row[0]), to_f(row[half]));
+            if (pd.cal) {
+                const float* k = pd.cal + (size_t)y * N + x0 + c;
+                v.x *= __ldg(k);
+                v.y *= __ldg(k + half);
+            }
+            smem[idx] = v;
         }
         __syncthreads();
         fft_run<false>(smem, N, P.rad_n, P.nrad_n, logc, C, P.tw_fwd_n, tid, nthr);

@@ -23,6 +23,7 @@ struct PolDev {
     const float* hg_x;       // [G][M] u_g(x'_i) dx'
     const float* hg_y;       // [G][M]
     const uint16_t* hgy_tc;  // [2][NP][M] bf16 hi / lo of hg_y, tensor-core core-matrix layout
+    const float* cal;        // nullable [N][N] reference-calibration factor over the window
 };
 
 struct Plan {

@@ -131,6 +131,8 @@ int pack_plan(const Settings& s, const Geometry& g, const Tables& t, unsigned ch
         pd.corr_y = (const float2*)(dev_tables + pk->put(pt.corr_y.data(), pt.corr_y.size() * 4));
         pd.hg_x = (const float*)(dev_tables + pk->put(pt.hg_x.data(), pt.hg_x.size() * 4));
         pd.hg_y = (const float*)(dev_tables + pk->put(pt.hg_y.data(), pt.hg_y.size() * 4));
+        const size_t o_cal = pk->put(pt.cal.data(), pt.cal.size() * 4);
+        pd.cal = pt.cal.empty() ? nullptr : (const float*)(dev_tables + o_cal);
     }
     if (pk->bytes.size() > kNoallocTableBytes)
         return fail(DH_ERROR_INVALIDDIMENSION, "plan tables of this geometry exceed the 1 MiB static table area");

@@ -66,6 +66,13 @@ static int fill(const Settings& s, const double tilt[DH_MAX_POLS][2], const doub
         *why = b;
         return DH_ERROR_INVALIDARGUMENT;
     }
+    if (s.cal_on && (s.cal_w != s.width || s.cal_h != s.height)) {
+        char b[160];
+        std::snprintf(b, sizeof b, "reference calibration is %d x %d, frames are %d x %d", s.cal_w, s.cal_h, s.width,
+                      s.height);
+        *why = b;
+        return DH_ERROR_INVALIDDIMENSION;
+    }
     g->dx = (double)s.n * s.pixel / (double)g->m;
     for (int p = 0; p < s.pols; ++p) {
         PolGeom& pg = g->pol[p];
@@ -222,6 +229,16 @@ void build_tables(const Settings& s, const Geometry& g, Tables* t) {
     for (int p = 0; p < g.pols; ++p) {
         const PolGeom& pg = g.pol[p];
         PolTables& pt = t->pol[p];
+        pt.cal.clear();
+        if (s.cal_on) {
+            // divide the frame by the reference's relative amplitude sqrt(cal / max cal)
+            pt.cal.resize((size_t)n * n);
+            for (int y = 0; y < n; ++y)
+                for (int x = 0; x < n; ++x) {
+                    const double c = s.cal[(size_t)(pg.ax[1].origin + y) * s.cal_w + pg.ax[0].origin + x];
+                    pt.cal[(size_t)y * n + x] = c > 0.0 ? (float)std::sqrt(s.cal_max / c) : 0.f;
+                }
+        }
         std::vector<float>* ph[2] = {&pt.phase_x, &pt.phase_y};
         std::vector<float>* co[2] = {&pt.corr_x, &pt.corr_y};
         for (int ax = 0; ax < 2; ++ax) {

@@ -31,6 +31,10 @@ struct Settings {
     int basis = DH_BASIS_HG;             // coefficient basis (custom falls back to HG until a matrix is set)
     int custom_in = 0, custom_out = 0;   // custom transform dimensions (modes in x modes out)
     std::vector<float> custom;           // custom transform, complex [custom_out][custom_in], interleaved re/im
+    int cal_on = 0;                      // reference calibration enabled
+    int cal_w = 0, cal_h = 0;            // calibration frame size
+    double cal_max = 0.0;                // maximum over every calibration frame
+    std::vector<uint16_t> cal;           // first calibration frame [cal_h][cal_w] (the single wavelength)
 };
 
 // Geometry of one axis of one polarisation (all FP64, computed as the conventions in digholo.h state).
@@ -65,6 +69,8 @@ struct PolTables {
     // split-BF16 tensor-core operand: u_n(y'_j) dy' as bf16 hi then lo, each [NP][M] in the K-major core-matrix
     // layout (8 rows x 8 values per 128-byte core; core (nb, kb) at (nb * M/8 + kb) * 128 bytes); rows n >= G zero
     std::vector<uint16_t> hgy_tc;
+    // reference calibration over the window, [N][N] (y, x): sqrt(max cal / cal), 0 where cal = 0; empty if off
+    std::vector<float> cal;
 };
 
 // Rows of the tensor-core B operand (the group count rounded up to 16).

@@ -223,3 +223,30 @@ def test_process_batch_host_argument_errors_before_device_work():
         assert dh._lib.dh_process_batch_host(12345, 16, 0, 1, None, None, None) == dh.DH_ERROR_INVALIDHANDLE
     finally:
         dh.dh_destroy(h)
+
+
+def test_reference_calibration_setters():
+    import numpy as np
+    s = syn.setup_batching()
+    h = dh.dh_create()
+    try:
+        dh.configure(h, s)
+        assert _code(dh.dh_set_ref_calibration_enabled, h, True) == dh.DH_ERROR_INVALIDARGUMENT   # none set yet
+        cal, _ = syn.reference_profile(s)
+        dh.dh_set_ref_calibration(h, cal)
+        assert dh.dh_get_output_dims(h)[0] == 64
+        dh.dh_set_ref_calibration_enabled(h, False)
+        dh.dh_set_ref_calibration_enabled(h, True)
+        # a calibration of another size is rejected when the geometry is validated
+        dh.dh_set_ref_calibration(h, np.ones((8, 16), dtype=np.uint16))
+        assert _code(dh.dh_get_output_dims, h) == dh.DH_ERROR_INVALIDDIMENSION
+        # invalid calls disable the calibration (and so the size mismatch disappears)
+        assert _code(dh.dh_set_ref_calibration, h, np.zeros((s.frame_h, s.frame_w), dtype=np.uint16)) \
+            == dh.DH_ERROR_INVALIDARGUMENT
+        assert dh.dh_get_output_dims(h)[0] == 64
+        assert dh._lib.dh_set_ref_calibration(h, None, 1, s.frame_w, s.frame_h) == dh.DH_ERROR_NULLPOINTER
+        buf = (dh.ctypes.c_uint16 * 4)(1, 2, 3, 4)
+        assert dh._lib.dh_set_ref_calibration(h, buf, 0, 2, 2) == dh.DH_ERROR_INVALIDARGUMENT
+        assert dh._lib.dh_set_ref_calibration(h, buf, 1, 0, 2) == dh.DH_ERROR_INVALIDARGUMENT
+    finally:
+        dh.dh_destroy(h)

@@ -114,3 +114,13 @@ def test_avg_many_groups_span_several_chunks():
         sub = np.stack([d["frames"][j * G + g] for j in range(A)])
         f_ref, c_ref = orc.process_batch_avg(sub, s, A, 0)
         _check(f[g:g + 1], c[g:g + 1], f_ref, c_ref)
+
+
+def test_avg_with_reference_calibration():
+    s0 = syn.setup_batching()
+    cal, amp = syn.reference_profile(s0, sigma_fraction=0.15, floor=200)
+    s = syn.with_(s0, ref_amplitude=amp, ref_cal=cal)
+    d = syn.make_avg_frames(s, 2, 3, 0, seed=137)
+    f, c = _run_avg(s, d["frames"], 2, 3, 0)
+    f_ref, c_ref = orc.process_batch_avg(d["frames"], s, 3, 0)
+    _check(f, c, f_ref, c_ref)

@@ -327,3 +327,31 @@ def test_custom_basis_more_and_fewer_inputs_than_hg_modes(modes_in_extra):
     assert out["modes"] == 23
     _check(sc, d["frames"], out)
     _check(sc, d["frames"], run_library(sc, d["frames"], window=True))
+
+
+# ----------------------------------------------------------------------------- reference calibration
+
+
+def _calibrated(setup, sigma=0.15):
+    cal, amp = syn.reference_profile(setup, sigma_fraction=sigma, floor=200)
+    return syn.with_(setup, ref_amplitude=amp, ref_cal=cal)
+
+
+def test_reference_calibration_parity():
+    s = _calibrated(syn.setup_batching())
+    d = syn.make_frames(s, 3, seed=150)
+    _check(s, d["frames"], run_library(s, d["frames"]))
+    _check(s, d["frames"], run_library(s, d["frames"], window=True))
+    s2 = _calibrated(syn.setup_precision(), sigma=0.2)
+    d2 = syn.make_frames(s2, 1, seed=151)
+    _check(s2, d2["frames"], run_library(s2, d2["frames"]))
+    _check(s2, d2["frames"], run_library(s2, d2["frames"], precision=1), coef_tol=SPLIT_COEF_TOL)
+
+
+def test_reference_calibration_scoring():
+    s = _calibrated(syn.setup_batching())
+    d = syn.make_frames(s, 2, seed=152)
+    cand = syn.candidate_settings(s, 5, seed=153)
+    ref = orc.score_settings(d["frames"], s, cand["tilt_deg"], cand["defocus"], cand["waist"])
+    got = _score(s, d["frames"], cand)
+    assert np.all(np.abs(got - ref) / ref <= 2 * COEF_TOL), (got, ref)

@@ -85,3 +85,15 @@ def test_noalloc_lg_basis_matches_oracle():
     assert rel_l2(got[1], ref[1]).max() <= COEF_TOL
     _, c_ref = orc.process_batch(fr[:3], s)
     assert rel_l2(got[1][:3], c_ref).max() <= COEF_TOL
+
+
+def test_noalloc_reference_calibration_matches_oracle():
+    from oracle import digholo_oracle as orc
+    s0 = syn.setup_batching()
+    cal, amp = syn.reference_profile(s0, sigma_fraction=0.15, floor=200)
+    s = syn.with_(s0, ref_amplitude=amp, ref_cal=cal)
+    fr = syn.make_frames(s, 2, seed=138)["frames"]
+    got = _run(s, fr, noalloc=True)
+    f_ref, c_ref = orc.process_batch(fr, s)
+    assert rel_l2(got[0], f_ref).max() <= FIELD_TOL
+    assert rel_l2(got[1], c_ref).max() <= COEF_TOL
