@@ -21,7 +21,9 @@ in float64 / complex128, with numpy matrix products as the only library primitiv
 7. batch averaging (digHoloSetBatchAvg, "Averaging modes"): the windows of the frames of one averaging
    group, rotated into phase with the group's first frame, averaged, then inverse transformed once;
 8. reference-wave calibration (digHoloConfigSetRefCalibrationIntensity): the frame divided pixel by pixel by
-   the reference's relative amplitude sqrt(cal / max cal) before the transform.
+   the reference's relative amplitude sqrt(cal / max cal) before the transform;
+9. the transfer-matrix metrics of the AutoAlign section (DIGHOLO_METRIC_IL ... SNRMG, digHoloAutoAlignCalcMetrics)
+   and the fine-alignment search that maximises the captured power (digHoloAutoAlign's tweak stage).
 
 Conventions the paper leaves open (the same readings are used by the CUDA library):
 
@@ -446,6 +448,129 @@ def score_settings(frames: np.ndarray, setup, tilt_deg: np.ndarray, defocus: np.
                 tot += float(np.sum(np.abs(c) ** 2))
             power[b, s] = tot
     return power
+
+
+# ---------------------------------------------------------------------------------------------------
+# Transfer-matrix metrics and the fine-alignment search (AutoAlign section)
+# ---------------------------------------------------------------------------------------------------
+
+METRICS = ("IL", "MDL", "DIAG", "SNRAVG", "DIAGBEST", "DIAGWORST", "SNRBEST", "SNRWORST", "SNRMG")
+
+
+def _db(v: float) -> float:
+    """10 log10(v) with the IEEE limits: -inf for 0, +inf for +inf."""
+    with np.errstate(divide="ignore"):
+        return float(10.0 * np.log10(v))
+
+
+def _ratio(num: float, den: float) -> float:
+    return math.inf if den == 0.0 else num / den
+
+
+def transfer_metrics(coefs: np.ndarray, groups=None, mul_conj_trans: bool = False) -> dict:
+    """The AutoAlign metrics of a batch of coefficient vectors (the transfer matrix A: row b = batch element b,
+    column k = coefficient k of all polarisations, [B][P][modes] flattened to [B][P modes]), all in dB:
+
+    IL        mean of the eigenvalues of the Gram matrix of A (its squared singular values; the smaller of
+              A A^H and A^H A)                                             (insertion loss)
+    MDL       largest over smallest of those eigenvalues                   (mode dependent loss; eigenvalues
+              below 1e-12 of the largest count as zero, giving +inf)
+    DIAG      total power on the diagonal, sum_i |X_ii|^2
+    SNRAVG    diagonal power over off-diagonal power
+    DIAGBEST / DIAGWORST   largest / smallest diagonal element power
+    SNRBEST / SNRWORST     largest / smallest row ratio |X_ii|^2 / sum_{j != i} |X_ij|^2
+    SNRMG     as SNRAVG, with every coupling inside one mode group of one polarisation counted as signal;
+              NaN-free only for group-ordered bases: groups = G, modes per polarisation G (G + 1) / 2, row i and
+              column i describing the same mode (pol-blocked)
+
+    X is A, or A A^H with mul_conj_trans (digHoloConfigSetAutoAlignBasisMulConjTrans).  The diagonal has
+    min(rows, columns) elements; rows without one count in the totals only.  SNRMG is None (not calculated)
+    without a group structure."""
+    c = np.asarray(coefs, dtype=np.complex128)
+    B = c.shape[0]
+    P = c.shape[1]
+    modes = c.shape[2]
+    A = c.reshape(B, P * modes)
+    gram = A @ A.conj().T if B <= P * modes else A.conj().T @ A
+    # eigenvalues of a Gram matrix are >= 0; rounding can leave the zero ones of a rank-deficient matrix at a
+    # relative size near the FP64 epsilon, which counts as zero (MDL infinite)
+    lam = np.linalg.eigvalsh(gram)
+    lam = np.where(lam <= 1e-12 * max(float(lam.max()), 0.0), 0.0, lam)
+    out = {"IL": _db(float(lam.sum()) / lam.size), "MDL": _db(_ratio(float(lam.max()), float(lam.min())))}
+    X = A @ A.conj().T if mul_conj_trans else A
+    pw = np.abs(X) ** 2
+    r, k = pw.shape
+    nd = min(r, k)
+    d = np.array([pw[i, i] for i in range(nd)])
+    t = pw.sum(axis=1)
+    out["DIAG"] = _db(float(d.sum()))
+    out["SNRAVG"] = _db(_ratio(float(d.sum()), float(t.sum() - d.sum())))
+    out["DIAGBEST"] = _db(float(d.max()))
+    out["DIAGWORST"] = _db(float(d.min()))
+    snr = [_ratio(float(d[i]), float(t[i] - d[i])) for i in range(nd)]
+    out["SNRBEST"] = _db(max(snr))
+    out["SNRWORST"] = _db(min(snr))
+    if groups is not None and modes == groups * (groups + 1) // 2:
+        grp = np.array([g for g in range(groups) for _ in range(g + 1)])
+        def key(i):
+            return (i // modes, grp[i % modes])
+        sig = sum(pw[i, j] for i in range(r) for j in range(k) if key(i) == key(j))
+        out["SNRMG"] = _db(_ratio(float(sig), float(t.sum() - sig)))
+    else:
+        out["SNRMG"] = None
+    return out
+
+
+def search_candidates(tilt: np.ndarray, defocus: np.ndarray, waist: np.ndarray, steps: np.ndarray):
+    """The compass stencil of the fine-alignment search around the current settings: the centre, then for each
+    polarisation p and parameter (tilt x, tilt y, defocus, waist) the settings with that parameter moved by
+    -step and +step (waist steps are relative: w (1 -/+ step)).  Returns (tilt [S][P][2], defocus [S][P],
+    waist [S][P]) with S = 1 + 8 P."""
+    P = tilt.shape[0]
+    T, D, W = [tilt.copy()], [defocus.copy()], [waist.copy()]
+    for p in range(P):
+        for par in range(4):
+            for sgn in (-1.0, 1.0):
+                t, dd, w = tilt.copy(), defocus.copy(), waist.copy()
+                if par < 2:
+                    t[p, par] += sgn * steps[0]
+                elif par == 2:
+                    dd[p] += sgn * steps[1]
+                else:
+                    w[p] *= 1.0 + sgn * steps[2]
+                T.append(t)
+                D.append(dd)
+                W.append(w)
+    return np.array(T), np.array(D), np.array(W)
+
+
+def auto_align_tweak(frames: np.ndarray, setup, steps=(0.02, 0.1, 0.05), min_steps=(2e-4, 1e-3, 5e-4),
+                     max_iter: int = 40):
+    """Fine-alignment search (the tweak stage of digHoloAutoAlign, goal: captured power, i.e. insertion loss):
+    a compass search that scores the stencil of search_candidates with score_settings, moves to the stencil
+    point of largest total power sum_b P[b][s] when it beats the centre, and otherwise halves every step;
+    it stops when all steps are below min_steps or after max_iter scorings.  Ties go to the lowest stencil index.
+    steps / min_steps: (tilt degrees, defocus dioptre, relative waist).  Returns (tilt [P][2], defocus [P],
+    waist [P], total power, scorings)."""
+    P = setup.pol_count
+    tilt = np.array(setup.tilt_deg, dtype=np.float64).reshape(P, 2)
+    defocus = np.array(setup.defocus, dtype=np.float64).reshape(P)
+    waist = np.array(setup.waist, dtype=np.float64).reshape(P)
+    st = np.array(steps, dtype=np.float64)
+    lo = np.array(min_steps, dtype=np.float64)
+    best = None
+    it = 0
+    while it < max_iter and np.any(st >= lo):
+        T, D, W = search_candidates(tilt, defocus, waist, st)
+        power = score_settings(frames, setup, T, D, W).sum(axis=0)
+        it += 1
+        k = int(np.argmax(power))
+        best = float(power[0])
+        if power[k] > power[0]:
+            tilt, defocus, waist, best = T[k], D[k], W[k], float(power[k])
+        else:
+            st = st / 2.0
+    return tilt, defocus, waist, best, it
 
 
 def output_axes(g: PolGeometry) -> Tuple[np.ndarray, np.ndarray]:

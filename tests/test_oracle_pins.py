@@ -479,3 +479,97 @@ def test_reference_calibration_improves_recovery_on_simulated_frames():
     f_plain, _ = orc.process_batch(d["frames"], s)
     f_cal, _ = orc.process_batch(d["frames"], syn.with_(s, ref_cal=cal))
     assert err(f_cal[0, 0]) < 0.5 * err(f_plain[0, 0])
+
+
+# ----------------------------------------------------------------------------- transfer-matrix metrics
+
+
+def _m(A, groups=None, mct=False):
+    A = np.asarray(A, dtype=np.complex128)
+    return orc.transfer_metrics(A[:, None, :], groups=groups, mul_conj_trans=mct)
+
+
+def test_metrics_identity_and_unitary():
+    m = _m(np.eye(6), groups=3)
+    assert m["IL"] == 0.0 and m["MDL"] == 0.0 and m["DIAGBEST"] == 0.0 and m["DIAGWORST"] == 0.0
+    assert m["DIAG"] == pytest.approx(10 * math.log10(6), abs=1e-12)
+    assert m["SNRAVG"] == math.inf and m["SNRBEST"] == math.inf and m["SNRWORST"] == math.inf
+    assert m["SNRMG"] == math.inf
+    u = syn.haar_unitary(np.random.default_rng(60), 10)
+    mu = _m(u, groups=4)
+    assert abs(mu["IL"]) < 1e-12 and abs(mu["MDL"]) < 1e-12
+    mc = _m(u, groups=4, mct=True)                     # U U^H = I
+    assert mc["SNRAVG"] > 250 and mc["DIAG"] == pytest.approx(10.0, abs=1e-12)
+
+
+def test_metrics_closed_forms_3x3():
+    # singular values^2 {1, 1/2, 1/4}: IL = 10 log10(1.75 / 3), MDL = 10 log10 4
+    d = _m(np.diag([1.0, math.sqrt(0.5), 0.5]))
+    assert d["IL"] == pytest.approx(10 * math.log10(1.75 / 3), abs=1e-12)
+    assert d["MDL"] == pytest.approx(10 * math.log10(4.0), abs=1e-12)
+    # powers [[1, .25, 0], [0, 4, .04], [.01, 0, 1]]; groups: mode 0 alone, modes 1-2 together (G = 2)
+    A = np.array([[1, 0.5, 0], [0, 2, 0.2j], [-0.1, 0, 1j]])
+    m = _m(A, groups=2)
+    assert m["DIAG"] == pytest.approx(10 * math.log10(6.0), abs=1e-12)
+    assert m["SNRAVG"] == pytest.approx(10 * math.log10(6.0 / 0.3), abs=1e-10)
+    assert m["DIAGBEST"] == pytest.approx(10 * math.log10(4.0), abs=1e-12)
+    assert m["DIAGWORST"] == pytest.approx(0.0, abs=1e-12)
+    assert m["SNRBEST"] == pytest.approx(20.0, abs=1e-10)
+    assert m["SNRWORST"] == pytest.approx(10 * math.log10(4.0), abs=1e-10)
+    assert m["SNRMG"] == pytest.approx(10 * math.log10(6.04 / 0.26), abs=1e-10)
+    sv = np.linalg.svd(A, compute_uv=False) ** 2    # an independent routine for the eigenvalues
+    assert m["IL"] == pytest.approx(10 * math.log10(sv.mean()), abs=1e-12)
+    assert m["MDL"] == pytest.approx(10 * math.log10(sv.max() / sv.min()), abs=1e-10)
+    assert _m(A)["SNRMG"] is None                     # no group structure given
+
+
+def test_metrics_rectangular_and_two_polarisations():
+    rng = np.random.default_rng(61)
+    c = rng.standard_normal((4, 2, 3)) + 1j * rng.standard_normal((4, 2, 3))     # 4 rows, 6 columns
+    m = orc.transfer_metrics(c, groups=2)
+    A = c.reshape(4, 6)
+    sv = np.linalg.svd(A, compute_uv=False) ** 2
+    assert m["IL"] == pytest.approx(10 * math.log10(sv.mean()), abs=1e-10)
+    pw = np.abs(A) ** 2
+    d = np.diag(pw)
+    assert m["DIAG"] == pytest.approx(10 * math.log10(d.sum()), abs=1e-12)
+    # SNRMG signal: same polarisation block (column // 3 == row // 3) and same group
+    grp = [0, 1, 1]
+    sig = sum(pw[i, j] for i in range(4) for j in range(6) if i // 3 == j // 3 and grp[i % 3] == grp[j % 3])
+    assert m["SNRMG"] == pytest.approx(10 * math.log10(sig / (pw.sum() - sig)), abs=1e-10)
+    c8 = rng.standard_normal((8, 2, 3)) + 1j * rng.standard_normal((8, 2, 3))     # 8 rows > 6 columns
+    mt = orc.transfer_metrics(c8, groups=2)
+    sv8 = np.linalg.svd(c8.reshape(8, 6), compute_uv=False) ** 2
+    assert mt["IL"] == pytest.approx(10 * math.log10(sv8.mean()), abs=1e-10)
+    assert mt["MDL"] == pytest.approx(10 * math.log10(sv8.max() / sv8.min()), abs=1e-9)
+    # a rank-deficient matrix has an infinite MDL
+    assert orc.transfer_metrics(np.concatenate([c, c], axis=0), groups=2)["MDL"] == math.inf
+
+
+# ----------------------------------------------------------------------------- fine-alignment search
+
+
+def test_search_stencil():
+    t = np.array([[1.0, 2.0], [3.0, 4.0]])
+    T, D, W = orc.search_candidates(t, np.array([0.1, 0.2]), np.array([1e-4, 2e-4]), np.array([0.5, 0.25, 0.1]))
+    assert T.shape == (17, 2, 2) and D.shape == (17, 2) and W.shape == (17, 2)
+    assert np.array_equal(T[0], t)
+    assert T[1][0, 0] == 0.5 and T[2][0, 0] == 1.5 and T[3][0, 1] == 1.5 and T[4][0, 1] == 2.5
+    assert D[5][0] == pytest.approx(-0.15) and D[6][0] == pytest.approx(0.35)
+    assert W[7][0] == pytest.approx(0.9e-4) and W[8][0] == pytest.approx(1.1e-4)
+    assert T[9][1, 0] == 2.5 and W[16][1] == pytest.approx(2.2e-4)
+
+
+def test_search_recovers_the_true_alignment():
+    s = syn.setup_plain()
+    d = syn.make_frames(s, 1, seed=62)
+    off = syn.with_(s, tilt_deg=[(s.tilt_deg[0][0] + 0.03, s.tilt_deg[0][1] - 0.02)],
+                    waist=[s.waist[0] * 1.06])
+    t, dfc, w, power, its = orc.auto_align_tweak(d["frames"], off, max_iter=60)
+    assert abs(t[0, 0] - s.tilt_deg[0][0]) < 4e-3 and abs(t[0, 1] - s.tilt_deg[0][1]) < 4e-3
+    assert abs(w[0] / s.waist[0] - 1.0) < 0.01
+    p_true = orc.score_settings(d["frames"], s, np.array([s.tilt_deg]), np.array([s.defocus]),
+                                np.array([s.waist])).sum()
+    p_start = orc.score_settings(d["frames"], off, np.array([off.tilt_deg]), np.array([off.defocus]),
+                                 np.array([off.waist])).sum()
+    assert power >= p_true * (1 - 1e-3) and power > p_start
