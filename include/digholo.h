@@ -69,6 +69,19 @@ extern "C" {
 #define DH_BASIS_LG 1
 #define DH_BASIS_CUSTOM 2
 
+/* Transfer-matrix metrics (DIGHOLO_METRIC_*, same indices). */
+#define DH_METRIC_IL 0
+#define DH_METRIC_MDL 1
+#define DH_METRIC_DIAG 2
+#define DH_METRIC_SNRAVG 3
+#define DH_METRIC_DIAGBEST 4
+#define DH_METRIC_DIAGWORST 5
+#define DH_METRIC_SNRBEST 6
+#define DH_METRIC_SNRWORST 7
+#define DH_METRIC_SNRMG 8
+#define DH_METRIC_COUNT 9
+#define DH_MAX_METRIC_SIZE 1024
+
 /* Largest sizes the kernels accept. */
 #define DH_MAX_POLS 2
 #define DH_MAX_WINDOW 1024
@@ -259,6 +272,43 @@ typedef struct dh_setting {
  * candidates (count >= 1).  Fields are not written. */
 int dh_score_settings(dh_handle h, const void* d_frames, int dtype, int batch, const dh_setting* settings,
                       int count, float* d_power, void* stream);
+
+/* Transfer-matrix metrics of a coefficient batch (digHoloAutoAlignCalcMetrics; AutoAlign metric defines).
+ * d_coefs: device complex64 [batch][pol][modes] as this handle writes them (modes as dh_get_output_dims
+ * reports); row b of the transfer matrix A is batch element b, its columns are the pol x modes coefficients.
+ * metrics: host double[DH_METRIC_COUNT], all in dB (10 log10):
+ *   IL = mean eigenvalue of the Gram matrix (the smaller of A A^H, A^H A: the squared singular values),
+ *   MDL = largest / smallest of them (eigenvalues below 1e-12 of the largest count as 0: MDL = +inf),
+ *   DIAG = sum_i |X_ii|^2, SNRAVG = diagonal / off-diagonal power, DIAGBEST / DIAGWORST = largest / smallest
+ *   |X_ii|^2, SNRBEST / SNRWORST = largest / smallest row ratio |X_ii|^2 / sum_{j != i} |X_ij|^2, SNRMG = as
+ *   SNRAVG with every coupling inside one mode group of one polarisation counted as signal (row i and column
+ *   i taken as the same mode); X = A, or A A^H when mul_conj_trans is nonzero
+ *   (digHoloConfigSetAutoAlignBasisMulConjTrans); the diagonal has min(rows, columns) elements.  Zero power
+ *   gives -inf, a zero denominator +inf; SNRMG is -FLT_MAX ("not calculated", as the guide) for a custom basis.
+ * eigenvalues (nullable): host double[min(batch, pol x modes)], the Gram eigenvalues (unsorted).
+ * The Gram products and the eigenvalues (parallel cyclic Jacobi, at most 40 sweeps) run in FP64 on the GPU;
+ * min(batch, pol x modes) and, with mul_conj_trans, batch must be <= DH_MAX_METRIC_SIZE
+ * (DH_ERROR_INVALIDDIMENSION).  FP64 is slow on this GPU: about 10 ms at 100 rows, seconds at 1024.
+ * Synchronous: allocates scratch, queues on stream and waits. */
+int dh_calc_metrics(dh_handle h, const void* d_coefs, int batch, int mul_conj_trans, double* metrics,
+                    double* eigenvalues, void* stream);
+
+/* Current alignment settings of every polarisation (digHoloConfigGetTilt / GetDefocus / GetBasisWaist) into
+ * *out (host). */
+int dh_get_alignment(dh_handle h, dh_setting* out);
+
+/* Fine-alignment search (digHoloAutoAlign's tweak stage; goal: captured power / insertion loss).  Starting from
+ * the handle's tilt, defocus and waist, each iteration scores with dh_score_settings the centre and, for every
+ * polarisation and parameter (tilt x, tilt y, defocus, waist), the settings with that parameter moved by -step
+ * and +step (candidates in that order; waist steps relative, w (1 -/+ step)); it moves to the candidate with the
+ * largest power summed over the batch (FP64 sum on the GPU) when that beats the centre (ties: first candidate),
+ * and otherwise halves every step.  It stops when every step is below its minimum or after max_iter scorings,
+ * and writes the final settings to the handle.  steps / min_steps: host double[3] (tilt degrees, defocus
+ * dioptre, relative waist); NULL gives {0.02, 0.1, 0.05} / {2e-4, 1e-3, 5e-4}.  power (nullable): the final
+ * total power; iterations (nullable): scorings run.  Synchronous. */
+int dh_auto_align(dh_handle h, const void* d_frames, int dtype, int batch, const double* steps,
+                  const double* min_steps, int max_iter, double* power, int* iterations, void* stream);
+
 
 /* ------------------------------------------------------------------------------------------------------------
  * Serving loop (continuous batching).  The guide's library processes one batch per call on the caller's thread;

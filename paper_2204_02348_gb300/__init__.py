@@ -95,6 +95,10 @@ _PROTOS = {
     "dh_process_batch_noalloc": [_i, _p, _i, _i, _p, _p, _p],
     "dh_process_batch_avg": [_i, _p, _i, _i, _i, _i, _p, _p, _p],
     "dh_process_batch_host": [_i, _p, _i, _i, _p, _p, _p],
+    "dh_get_alignment": [_i, ctypes.POINTER(dh_setting)],
+    "dh_calc_metrics": [_i, _p, _i, _i, ctypes.POINTER(_d), ctypes.POINTER(_d), _p],
+    "dh_auto_align": [_i, _p, _i, _i, ctypes.POINTER(_d), ctypes.POINTER(_d), _i, ctypes.POINTER(_d),
+                      ctypes.POINTER(_i), _p],
     "dh_score_settings": [_i, _p, _i, _i, ctypes.POINTER(dh_setting), _i, _p, _p],
     "dh_set_profiling": [_i, _i],
     "dh_get_device_status": [_i, ctypes.POINTER(_i)],
@@ -266,6 +270,40 @@ def dh_process_batch_avg(h: int, frames, dtype: int, batch: int, avg_count: int,
                          coefs=None, stream=None) -> None:
     _check(_lib.dh_process_batch_avg(h, _ptr(frames), dtype, batch, avg_count, avg_mode, _ptr(fields), _ptr(coefs),
                                      _stream(stream)))
+
+
+METRIC_NAMES = ("IL", "MDL", "DIAG", "SNRAVG", "DIAGBEST", "DIAGWORST", "SNRBEST", "SNRWORST", "SNRMG")
+NOT_CALCULATED = -3.4028234663852886e38      # -FLT_MAX
+
+
+def dh_calc_metrics(h: int, coefs, batch: int, mul_conj_trans: bool = False, stream=None):
+    """Transfer-matrix metrics (dB) of a device coefficient tensor [batch][pol][modes]: (dict name -> value,
+    None when not calculated; the Gram eigenvalues as a list)."""
+    rows = min(batch, int(coefs.shape[1]) * int(coefs.shape[2]))
+    out = (ctypes.c_double * 9)()
+    eig = (ctypes.c_double * max(rows, 1))()
+    _check(_lib.dh_calc_metrics(h, _ptr(coefs), batch, 1 if mul_conj_trans else 0, out, eig, _stream(stream)))
+    vals = {n: (None if out[i] == NOT_CALCULATED else out[i]) for i, n in enumerate(METRIC_NAMES)}
+    return vals, list(eig)[:rows]
+
+
+def dh_get_alignment(h: int):
+    """Current (tilt_deg [P][2], defocus [P], waist [P]) of every polarisation slot (DH_MAX_POLS)."""
+    out = dh_setting()
+    _check(_lib.dh_get_alignment(h, ctypes.byref(out)))
+    return ([[out.tilt_deg[p][0], out.tilt_deg[p][1]] for p in range(DH_MAX_POLS)],
+            [out.defocus[p] for p in range(DH_MAX_POLS)], [out.waist[p] for p in range(DH_MAX_POLS)])
+
+
+def dh_auto_align(h: int, frames, dtype: int, batch: int, steps=None, min_steps=None, max_iter: int = 40,
+                  stream=None):
+    """Fine-alignment search; returns (total power, scorings).  The final settings are written to the handle."""
+    st = None if steps is None else (ctypes.c_double * 3)(*steps)
+    lo = None if min_steps is None else (ctypes.c_double * 3)(*min_steps)
+    power, its = _d(), _i()
+    _check(_lib.dh_auto_align(h, _ptr(frames), dtype, batch, st, lo, max_iter, ctypes.byref(power), ctypes.byref(its),
+                              _stream(stream)))
+    return power.value, its.value
 
 
 def dh_process_batch_noalloc(h: int, frames, dtype: int, batch: int, fields=None, coefs=None, stream=None) -> None:

@@ -250,3 +250,20 @@ def test_reference_calibration_setters():
         assert dh._lib.dh_set_ref_calibration(h, buf, 1, 0, 2) == dh.DH_ERROR_INVALIDARGUMENT
     finally:
         dh.dh_destroy(h)
+
+
+def test_alignment_getter_and_search_argument_errors():
+    s = syn.setup_batching()
+    h = dh.dh_create()
+    try:
+        dh.configure(h, s)
+        tilt, dfc, waist = dh.dh_get_alignment(h)
+        assert tilt[1] == list(s.tilt_deg[1]) and dfc[:2] == list(s.defocus) and waist[:2] == list(s.waist)
+        bad = (dh.ctypes.c_double * 3)(0.0, 0.1, 0.05)
+        assert dh._lib.dh_auto_align(h, 16, 0, 1, bad, None, 10, None, None, None) == dh.DH_ERROR_INVALIDARGUMENT
+        assert dh._lib.dh_auto_align(h, None, 0, 1, None, None, 10, None, None, None) == dh.DH_ERROR_NULLPOINTER
+        assert dh._lib.dh_calc_metrics(h, None, 4, 0, None, None, None) == dh.DH_ERROR_NULLPOINTER
+        dh.dh_set_basis(h, 0, s.waist[0], 0)
+        assert dh._lib.dh_auto_align(h, 16, 0, 1, None, None, 10, None, None, None) == dh.DH_ERROR_INVALIDARGUMENT
+    finally:
+        dh.dh_destroy(h)
