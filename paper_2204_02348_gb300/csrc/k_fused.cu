@@ -1,5 +1,6 @@
 // Fused single-kernel path for 128 x 128 windows (field sizes 32, 48 and 64): one thread block reconstructs
-// one (frame, polarisation) window entirely in shared memory, persistent over windows, two blocks per SM.
+// one (frame, polarisation) window entirely in shared memory, persistent over windows.  uint16 frames run two
+// 256-thread blocks per SM, float32 frames (twice the staging buffer) one 512-thread block.
 //
 // Per window (the guide's pipeline steps 1-3 and digHoloProcessRemoveTilt):
 //   y pass   real columns x and x + 64 packed as one complex column; radix-16 DIF pass from the window staged
@@ -10,10 +11,13 @@
 //   inverse  M-point inverse transform along x (DIT, digit-reversed in / natural out) and along y (DIF,
 //            natural in / digit-reversed out), in place;
 //   epilogue residual tilt and defocus removal in registers inside the last y pass, field write (coalesced
-//            along x), and the separable HG contraction: partial sums over y per thread group, then the modes
-//            spread over the warps with fixed shuffle trees (deterministic, no atomics).
-// Shared memory: r1[N][M+1] box rows (x-major, padded pitch) and one union region used in turn as the y-pass
-// tile, the M x (M+1) window / field, and the overlap partials; twiddles and the digit-reversal table.
+//            along x), and the separable HG contraction: partial sums over y per group of row blocks, then the
+//            modes spread over the warps with fixed shuffle trees (deterministic, no atomics).
+// Shared memory: the staging buffer of the next window (filled by the tensor copy while the current one is
+// processed), one complex work buffer used in place by every step (y tile, box rows, window, field partial
+// sums), twiddles, phases, the HG tables and the digit-reversal table: ~112 KB for uint16 frames, so two blocks
+// share an SM.  Where a step writes over data other threads still read, the reads complete first (held in
+// registers across a barrier).
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -29,7 +33,6 @@
 namespace dhk {
 
 constexpr int kFN = 128;          // window size of this path
-constexpr int kFThreads = 512;
 constexpr int kFGMax = 16;        // largest group count of this path
 constexpr int kFRows = 128;       // staged window rows
 constexpr long kFWaitLimit = 1L << 24;
@@ -50,18 +53,26 @@ struct Staging {
     static constexpr int BYTES = kFRows * W * (int)sizeof(T);
 };
 
+// Threads per block and blocks per SM: uint16 frames fit two 256-thread blocks per SM (two windows in flight,
+// so one block's barriers overlap the other's work); float32 frames need twice the staging buffer and run one
+// 512-thread block per SM.
+template <typename T>
+struct FusedShape {
+    static constexpr int NT = sizeof(T) == 2 ? 256 : 512;
+    static constexpr int MINB = sizeof(T) == 2 ? 2 : 1;
+};
+
 template <int M, typename T>
 struct FusedLayout {
     static constexpr int PITCH = M + 1;
-    static constexpr int R1 = kFN * PITCH;
+    static constexpr int R1 = kFN * PITCH;                     // box rows r1[x][q], x-major
     static constexpr int YT = kFN * (kFN / 2);                 // y tile: 128 rows x 64 column pairs
-    static constexpr int WB = M * PITCH;
-    static constexpr int UN = YT > WB ? YT : WB;
-    static_assert(UN >= kFGMax * M, "the union region holds T");
-    static constexpr int F2 = R1 + UN + kFN + M + 4 * M;
-    static constexpr int FL = 2 * kFGMax * M;
+    static constexpr int BUF = R1 > YT ? R1 : YT;              // the one complex work buffer, used in place
+    static constexpr int WB = M * PITCH;                       // window / field [.][pitch]
+    static constexpr int F2 = BUF + kFN + M + 4 * M;
+    static constexpr int FL = 2 * kFGMax * M;                  // HG table as [n][i] and as [j][n]
     static constexpr int IN = 3 * M + 2 * (kFGMax * (kFGMax + 1) / 2);
-    static constexpr size_t STG = (size_t)Staging<T>::BYTES;   // first, 1024-byte aligned
+    static constexpr size_t STG = (size_t)Staging<T>::BYTES;   // first, 128-byte aligned
     static constexpr size_t bytes = STG + (size_t)F2 * sizeof(float2) + (size_t)FL * sizeof(float) + (size_t)IN * sizeof(int);
 };
 
@@ -93,27 +104,32 @@ __device__ __forceinline__ void emit_pair(float2* r1, int pitch, int M, int kly,
 }
 
 template <int M, int MR0, int MR1, typename T>
-__global__ void __launch_bounds__(kFThreads, 1) k_fused128(const __grid_constant__ Plan P, const __grid_constant__ FusedArgs A,
-                                                           const __grid_constant__ CUtensorMap tmap) {
+__global__ void __launch_bounds__(FusedShape<T>::NT, FusedShape<T>::MINB)
+    k_fused128(const __grid_constant__ Plan P, const __grid_constant__ FusedArgs A, const __grid_constant__ CUtensorMap tmap) {
     using L = FusedLayout<M, T>;
     using S = Staging<T>;
-    constexpr int N = kFN, PITCH = L::PITCH, NT = kFThreads;
+    constexpr int N = kFN, PITCH = L::PITCH, NT = FusedShape<T>::NT;
+    constexpr int NBLK = M / MR1;                  // row blocks of the last inverse pass
+    constexpr int QB = NBLK < 4 ? NBLK : 4;        // partial-sum groups of the y contraction
+    constexpr int BPQ = NBLK / QB;                 // row blocks per group
     static_assert(M == MR0 * MR1, "field size = product of the two radices");
-    static_assert(L::R1 >= (M / MR1) * kFGMax * M, "r1 holds the overlap partial sums");
-    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    static_assert(NBLK % QB == 0, "row blocks split evenly into the partial-sum groups");
+    static_assert(L::WB + QB * kFGMax * M <= L::BUF, "the partial sums fit behind the window");
+    static_assert(M % 8 == 0, "box rows below M come in whole radix-8 tasks");
+    // 128-byte alignment: tensor-copy destination; no larger, so that two blocks fit an SM
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ int abort_flag;
     T* stg = reinterpret_cast<T*>(smem_raw);
-    float2* r1 = reinterpret_cast<float2*>(smem_raw + L::STG);
-    float2* un = r1 + L::R1;
-    float2* twN = un + L::UN;
+    float2* buf = reinterpret_cast<float2*>(smem_raw + L::STG);
+    float2* twN = buf + L::BUF;
     float2* twM = twN + N;
     float2* phx = twM + M;
     float2* phy = phx + M;
     float2* cx = phy + M;
     float2* cy = cx + M;
-    float* hgx = reinterpret_cast<float*>(cy + M);
-    float* hgy = hgx + kFGMax * M;
+    float* hgx = reinterpret_cast<float*>(cy + M);   // u_m(x'_i) dx' at [m][i]
+    float* hgy = hgx + kFGMax * M;                   // u_n(y'_j) dy' at [j][n] (n fastest, kFGMax wide)
     int* posM = reinterpret_cast<int*>(hgy + kFGMax * M);
     int* mlo = posM + M;
     int* mhi = mlo + M;
@@ -169,8 +185,8 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused128(const __grid_constant
         }
 
         // ---------------------------------------------------------------- y pass on 64 column pairs
-        {
-            const int c = tid & 63, j = tid >> 6;
+        for (int t = tid; t < 512; t += NT) {
+            const int c = t & 63, j = t >> 6;
             float2 v[16];
 #pragma unroll
             for (int r = 0; r < 16; ++r) v[r] = staged_pair<T>(stg + (j + 8 * r) * S::W, xo + c);
@@ -178,93 +194,145 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused128(const __grid_constant
 #pragma unroll
             for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], twN[j * r]);
 #pragma unroll
-            for (int r = 0; r < 16; ++r) un[(j + 8 * r) * 64 + c] = v[r];
+            for (int r = 0; r < 16; ++r) buf[(j + 8 * r) * 64 + c] = v[r];
         }
         // the staged window has been read: order those reads before the next tensor copy into the buffer
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         __syncthreads();
         if (tid == 0 && b + fstride < A.count) stage_window(&tmap, dst, mb, A.x0[pol], pd.oy, f + fstride, S::BYTES);
         {
-            const int c = tid & 63, u = tid >> 6;
-            const int d1 = u, d2 = (u == 0) ? 8 : 16 - u;
-            float2 z1[8], z2[8];
+            // radix-8 pass and separation of the two real spectra, in place: every task's inputs are read
+            // before the box rows r1[x][q] overwrite the tile
+            constexpr int TPT = 512 / NT;
+            float2 z1[TPT][8], z2[TPT][8];
 #pragma unroll
-            for (int r = 0; r < 8; ++r) {
-                z1[r] = un[(8 * d1 + r) * 64 + c];
-                z2[r] = un[(8 * d2 + r) * 64 + c];
-            }
-            dft8<false>(z1);
-            dft8<false>(z2);
-            const int x = c;
-            if (u != 0) {
+            for (int k = 0; k < TPT; ++k) {
+                const int t = tid + k * NT, c = t & 63, u = t >> 6;
+                const int d1 = u, d2 = (u == 0) ? 8 : 16 - u;
 #pragma unroll
                 for (int r = 0; r < 8; ++r) {
-                    emit_pair(r1, PITCH, M, pd.kly, x, d1 + 16 * r, z1[r], z2[7 - r]);
-                    emit_pair(r1, PITCH, M, pd.kly, x, d2 + 16 * r, z2[r], z1[7 - r]);
+                    z1[k][r] = buf[(8 * d1 + r) * 64 + c];
+                    z2[k][r] = buf[(8 * d2 + r) * 64 + c];
                 }
-            } else {
+                dft8<false>(z1[k]);
+                dft8<false>(z2[k]);
+            }
+            __syncthreads();
 #pragma unroll
-                for (int r = 0; r < 8; ++r) {
-                    emit_pair(r1, PITCH, M, pd.kly, x, 16 * r, z1[r], z1[(8 - r) & 7]);
-                    emit_pair(r1, PITCH, M, pd.kly, x, 8 + 16 * r, z2[r], z2[7 - r]);
+            for (int k = 0; k < TPT; ++k) {
+                const int t = tid + k * NT, x = t & 63, u = t >> 6;
+                const int d1 = u, d2 = (u == 0) ? 8 : 16 - u;
+                if (u != 0) {
+#pragma unroll
+                    for (int r = 0; r < 8; ++r) {
+                        emit_pair(buf, PITCH, M, pd.kly, x, d1 + 16 * r, z1[k][r], z2[k][7 - r]);
+                        emit_pair(buf, PITCH, M, pd.kly, x, d2 + 16 * r, z2[k][r], z1[k][7 - r]);
+                    }
+                } else {
+#pragma unroll
+                    for (int r = 0; r < 8; ++r) {
+                        emit_pair(buf, PITCH, M, pd.kly, x, 16 * r, z1[k][r], z1[k][(8 - r) & 7]);
+                        emit_pair(buf, PITCH, M, pd.kly, x, 8 + 16 * r, z2[k][r], z2[k][7 - r]);
+                    }
                 }
             }
         }
         __syncthreads();
 
         // ---------------------------------------------------------------- x pass on the M box rows
-        spass<16, false, false, N, N, M, PITCH, 1, NT>(r1, twN, tid);
+        spass<16, false, false, N, N, M, PITCH, 1, NT>(buf, twN, tid);
         __syncthreads();
-        for (int t = tid; t < M * 16; t += NT) {
-            const int q = t % M, d = t / M;
-            float2 v[8];
+        {
+            // radix-8 pass fused with the box-column selection, mask and beam-centre phase, writing the window
+            // w[posM[p]][q] over box rows x < M: the tasks that read those rows (d < M/8) keep their outputs in
+            // registers across a barrier; the others read rows >= M, which nothing overwrites
+            constexpr int LOW = (M / 8) * M;
+            constexpr int LT = (LOW + NT - 1) / NT;
+            float2 keep[LT][8];
 #pragma unroll
-            for (int r = 0; r < 8; ++r) v[r] = r1[(8 * d + r) * PITCH + q];
-            dft8<false>(v);
-            const int lo = mlo[q], hi = mhi[q];
-            const float2 py = phy[q];
+            for (int k = 0; k < LT; ++k) {
+                const int t = tid + k * NT;
+                if (t < LOW) {
+                    const int q = t % M, d = t / M;
 #pragma unroll
-            for (int r = 0; r < 8; ++r) {
-                const int p = (d + 16 * r - pd.klx) & (N - 1);
-                if (p < M) {
-                    float2 val = make_float2(0.f, 0.f);
-                    if (p >= lo && p <= hi) val = cmul(cmul(v[r], phx[p]), py);
-                    un[posM[p] * PITCH + q] = val;
+                    for (int r = 0; r < 8; ++r) keep[k][r] = buf[(8 * d + r) * PITCH + q];
+                    dft8<false>(keep[k]);
+                    const int lo = mlo[q], hi = mhi[q];
+                    const float2 py = phy[q];
+#pragma unroll
+                    for (int r = 0; r < 8; ++r) {
+                        const int p = (d + 16 * r - pd.klx) & (N - 1);
+                        keep[k][r] = (p < M && p >= lo && p <= hi) ? cmul(cmul(keep[k][r], phx[p]), py) : make_float2(0.f, 0.f);
+                    }
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int k = 0; k < LT; ++k) {
+                const int t = tid + k * NT;
+                if (t < LOW) {
+                    const int q = t % M, d = t / M;
+#pragma unroll
+                    for (int r = 0; r < 8; ++r) {
+                        const int p = (d + 16 * r - pd.klx) & (N - 1);
+                        if (p < M) buf[posM[p] * PITCH + q] = keep[k][r];
+                    }
+                }
+            }
+            for (int t = LOW + tid; t < M * 16; t += NT) {
+                const int q = t % M, d = t / M;
+                float2 v[8];
+#pragma unroll
+                for (int r = 0; r < 8; ++r) v[r] = buf[(8 * d + r) * PITCH + q];
+                dft8<false>(v);
+                const int lo = mlo[q], hi = mhi[q];
+                const float2 py = phy[q];
+#pragma unroll
+                for (int r = 0; r < 8; ++r) {
+                    const int p = (d + 16 * r - pd.klx) & (N - 1);
+                    if (p < M) {
+                        float2 val = make_float2(0.f, 0.f);
+                        if (p >= lo && p <= hi) val = cmul(cmul(v[r], phx[p]), py);
+                        buf[posM[p] * PITCH + q] = val;
+                    }
                 }
             }
         }
         __syncthreads();
 
         // ---------------------------------------------------------------- inverse transforms
-        spass<MR1, true, true, M, MR1, M, PITCH, 1, NT>(un, twM, tid);
+        spass<MR1, true, true, M, MR1, M, PITCH, 1, NT>(buf, twM, tid);
         __syncthreads();
-        spass<MR0, true, true, M, M, M, PITCH, 1, NT>(un, twM, tid);
+        spass<MR0, true, true, M, M, M, PITCH, 1, NT>(buf, twM, tid);
         __syncthreads();
-        spass<MR0, true, false, M, M, M, 1, PITCH, NT>(un, twM, tid);
+        spass<MR0, true, false, M, M, M, 1, PITCH, NT>(buf, twM, tid);
         __syncthreads();
 
         // ---------------------------------------------------------------- last y pass, correction, field, y overlap
         // The last DIF pass (span MR1, no twiddles) leaves output j = blk + MR0 r at position blk MR1 + r of
         // column i; it is corrected in registers, written to the field (coalesced along i) and contracted with
-        // u_n(y'_j) into the partial sums part[blk][n][i] over the thread's MR1 rows.
-        constexpr int NBLK = M / MR1;
-        float2* part = r1;                         // [NBLK][G][M]
-        float2* tsum = un;                         // [G][M]
+        // u_n(y'_j) into the partial sums part[qb][n][i] over the BPQ row blocks of group qb.
+        float2* part = buf + L::WB;                // [QB][G][M], behind the window
+        float2* tsum = buf;                        // [G][M], over the consumed window
         const bool ov = A.coefs && G > 0;
         {
             float2* fld = A.fields ? A.fields + (size_t)(f * P.pols + pol) * M * M : nullptr;
-            for (int t = tid; t < M * NBLK; t += NT) {
-                const int i = t % M, blk = t / M;
-                float2 v[MR1];
-#pragma unroll
-                for (int r = 0; r < MR1; ++r) v[r] = un[i * PITCH + blk * MR1 + r];
-                dft<MR1, true>(v, twM, M / MR1);
+            for (int t = tid; t < M * QB; t += NT) {
+                const int i = t % M, qb = t / M;
                 const float2 ci = cx[i];
+                float2 v[BPQ][MR1];
 #pragma unroll
-                for (int r = 0; r < MR1; ++r) {
-                    const int j = blk + MR0 * r;
-                    v[r] = cmul(cmul(v[r], ci), cy[j]);
-                    if (fld) fld[j * M + i] = v[r];
+                for (int bb = 0; bb < BPQ; ++bb) {
+                    const int blk = qb * BPQ + bb;
+#pragma unroll
+                    for (int r = 0; r < MR1; ++r) v[bb][r] = buf[i * PITCH + blk * MR1 + r];
+                    dft<MR1, true>(v[bb], twM, M / MR1);
+#pragma unroll
+                    for (int r = 0; r < MR1; ++r) {
+                        const int j = blk + MR0 * r;
+                        v[bb][r] = cmul(cmul(v[bb][r], ci), cy[j]);
+                        if (fld) fld[j * M + i] = v[bb][r];
+                    }
                 }
                 if (ov) {
 #pragma unroll
@@ -273,20 +341,25 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused128(const __grid_constant
                             float2 a[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f),
                                            make_float2(0.f, 0.f)};
 #pragma unroll
-                            for (int r = 0; r < MR1; ++r) {
-                                const float4 u = *reinterpret_cast<const float4*>(hgy + (blk + MR0 * r) * kFGMax + n4);
-                                a[0].x = fmaf(u.x, v[r].x, a[0].x);
-                                a[0].y = fmaf(u.x, v[r].y, a[0].y);
-                                a[1].x = fmaf(u.y, v[r].x, a[1].x);
-                                a[1].y = fmaf(u.y, v[r].y, a[1].y);
-                                a[2].x = fmaf(u.z, v[r].x, a[2].x);
-                                a[2].y = fmaf(u.z, v[r].y, a[2].y);
-                                a[3].x = fmaf(u.w, v[r].x, a[3].x);
-                                a[3].y = fmaf(u.w, v[r].y, a[3].y);
+                            for (int bb = 0; bb < BPQ; ++bb) {
+#pragma unroll
+                                for (int r = 0; r < MR1; ++r) {
+                                    const int j = qb * BPQ + bb + MR0 * r;
+                                    const float4 u = *reinterpret_cast<const float4*>(hgy + j * kFGMax + n4);
+                                    const float2 e = v[bb][r];
+                                    a[0].x = fmaf(u.x, e.x, a[0].x);
+                                    a[0].y = fmaf(u.x, e.y, a[0].y);
+                                    a[1].x = fmaf(u.y, e.x, a[1].x);
+                                    a[1].y = fmaf(u.y, e.y, a[1].y);
+                                    a[2].x = fmaf(u.z, e.x, a[2].x);
+                                    a[2].y = fmaf(u.z, e.y, a[2].y);
+                                    a[3].x = fmaf(u.w, e.x, a[3].x);
+                                    a[3].y = fmaf(u.w, e.y, a[3].y);
+                                }
                             }
 #pragma unroll
                             for (int c = 0; c < 4; ++c)
-                                if (n4 + c < G) part[(blk * G + n4 + c) * M + i] = a[c];
+                                if (n4 + c < G) part[(qb * G + n4 + c) * M + i] = a[c];
                         }
                     }
                 }
@@ -296,11 +369,11 @@ __global__ void __launch_bounds__(kFThreads, 1) k_fused128(const __grid_constant
 
         // ---------------------------------------------------------------- HG overlap, x contraction
         if (ov) {
-            // T[n][i]: the partial sums of the NBLK row groups added in a fixed order
+            // T[n][i]: the partial sums of the QB row groups added in a fixed order
             for (int t = tid; t < G * M; t += NT) {
                 float2 v = part[t];
 #pragma unroll
-                for (int q = 1; q < NBLK; ++q) {
+                for (int q = 1; q < QB; ++q) {
                     const float2 w = part[q * G * M + t];
                     v.x += w.x;
                     v.y += w.y;
@@ -364,12 +437,26 @@ static cudaError_t set_attr() {
                                 (int)FusedLayout<M, float>::bytes);
 }
 
+// Resident blocks per SM of one instantiation (the persistent grid is SMs x this).
+template <int M, int MR0, int MR1>
+static int blocks_per_sm(int dtype) {
+    int n = 0;
+    cudaError_t e;
+    if (dtype == DH_DTYPE_U16)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused128<M, MR0, MR1, uint16_t>, FusedShape<uint16_t>::NT,
+                                                          FusedLayout<M, uint16_t>::bytes);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused128<M, MR0, MR1, float>, FusedShape<float>::NT,
+                                                          FusedLayout<M, float>::bytes);
+    return (e == cudaSuccess && n > 0) ? n : 1;
+}
+
 template <int M, int MR0, int MR1>
 static void launch(const Plan& P, const FusedArgs& A, const CUtensorMap& tm, int dtype, int grid, cudaStream_t st) {
     if (dtype == DH_DTYPE_U16)
-        k_fused128<M, MR0, MR1, uint16_t><<<grid, kFThreads, FusedLayout<M, uint16_t>::bytes, st>>>(P, A, tm);
+        k_fused128<M, MR0, MR1, uint16_t><<<grid, FusedShape<uint16_t>::NT, FusedLayout<M, uint16_t>::bytes, st>>>(P, A, tm);
     else
-        k_fused128<M, MR0, MR1, float><<<grid, kFThreads, FusedLayout<M, float>::bytes, st>>>(P, A, tm);
+        k_fused128<M, MR0, MR1, float><<<grid, FusedShape<float>::NT, FusedLayout<M, float>::bytes, st>>>(P, A, tm);
 }
 
 }  // namespace dhk
@@ -377,6 +464,7 @@ static void launch(const Plan& P, const FusedArgs& A, const CUtensorMap& tm, int
 namespace dh {
 
 static int g_sm_count[64] = {0};
+static int g_bps[64][6] = {};   // resident blocks per SM per (field size, pixel type)
 static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
 bool use_fused(const dhk::Plan& P) {
@@ -441,8 +529,16 @@ int launch_fused_path(Handle* H, const void* frames, int dtype, int batch, void*
     }
     A.fields = (float2*)fields;
     A.coefs = (float2*)coefs;
-    // one block per SM; each block serves one polarisation, so the grid is a multiple of the polarisation count
-    const long long per_pol = std::min<long long>(batch, std::max(1, g_sm_count[dev] / P.pols));
+    // a persistent grid of every resident block; each block serves one polarisation, so the grid is a multiple
+    // of the polarisation count
+    const int slot = (P.m == 32 ? 0 : P.m == 48 ? 1 : 2) * 2 + (dtype == DH_DTYPE_U16 ? 0 : 1);
+    if (!g_bps[dev][slot]) {
+        g_bps[dev][slot] = P.m == 32   ? dhk::blocks_per_sm<32, 8, 4>(dtype)
+                           : P.m == 48 ? dhk::blocks_per_sm<48, 3, 16>(dtype)
+                                       : dhk::blocks_per_sm<64, 8, 8>(dtype);
+    }
+    const int resident = g_sm_count[dev] * g_bps[dev][slot];
+    const long long per_pol = std::min<long long>(batch, std::max(1, resident / P.pols));
     const int grid = (int)per_pol * P.pols;
     if (tm) tm->start(st);
     switch (P.m) {
