@@ -92,6 +92,15 @@ def bytes_per_frame(setup, m, modes):
     return setup.pol_count * (n * n * px_bytes + m * m * 8 + modes * 8)
 
 
+def window_rows(setup):
+    """Frame rows the host-buffer call copies to the device: from the first to the last row of any
+    polarisation window (window origin round_half_away(c / px) - N/2)."""
+    def rha(v):
+        return int(math.floor(abs(v) + 0.5)) * (1 if v >= 0 else -1)
+    oy = [rha(setup.beam_centre[p][1] / setup.pixel) - setup.window // 2 for p in range(setup.pol_count)]
+    return max(oy) + setup.window - min(oy)
+
+
 def flops_per_frame(setup, m, modes):
     """Algorithmic FP32 flops per frame by the nominal counts: 2.5 N log2 N per real and 5 N log2 N per
     complex transform of length N, the forward transform pruned to the M box columns (N real rows, M complex
@@ -405,7 +414,7 @@ def run_ours(args, ws, rank, local):
     torch.cuda.synchronize()
     e_ms = max_over_ranks(1e3 * (time.perf_counter() - t0), ws, dev)
     e2e = {"value": whole_job_rate(ws, frames_n, e2e_steps, e_ms), "unit": "frames/s",
-           "h2d_bytes_per_step": int(host.numel() * 2),
+           "h2d_bytes_per_step": int(frames_n * window_rows(setup) * setup.frame_w * 2),
            "d2h_bytes_per_step": int(host_f.numel() * 8 + host_c.numel() * 8), "steps": e2e_steps}
 
     # ---- CPU baseline (rank 0, N = 1 only)

@@ -209,7 +209,8 @@ int dh_process_batch(dh_handle h, const void* d_frames, int dtype, int batch, vo
  * G = 0): host complex64 [batch][pol][modes].  The batch is cut into chunks that cycle over three internal
  * streams with their own device staging buffers (at most 256 MiB each, owned by the handle and kept for the
  * next call), so that host-to-device copies, reconstruction and device-to-host copies of consecutive chunks
- * overlap; the kernels and results are those of dh_process_batch.  The work starts after the work already
+ * overlap; only the frame rows that hold the polarisation windows are copied to the device.  The kernels and
+ * results are those of dh_process_batch.  The work starts after the work already
  * queued on stream; the call returns when the outputs are in host memory (stream then also waits for it).
  * Page-locked host buffers are needed for the copies to overlap; pageable ones work but copy synchronously. */
 int dh_process_batch_host(dh_handle h, const void* h_frames, int dtype, int batch, void* h_fields, void* h_coefs,

@@ -352,7 +352,7 @@ int process(Handle* H, const void* frames, int dtype, int batch, void* window, v
     rc = basis_target(H, batch, &coefs, &out);
     if (rc) return rc;
     if (use_fused(P) && !window && fused_frames_ok(P, frames, dtype)) {
-        rc = launch_fused_path(H, frames, dtype, batch, fields, coefs, st, H->timer());
+        rc = launch_fused_path(H, P, frames, dtype, batch, fields, coefs, st, H->timer());
     } else {
         const size_t per_frame = split_window_bytes(P) * P.pols;
         const int chunk = chunk_frames(per_frame, P.pols, batch, H->device);
@@ -449,7 +449,11 @@ int process_avg(Handle* H, const void* frames, int dtype, int batch, int avg, in
 
 int process_with(Handle* H, const void* frames, int dtype, int batch, void* fields, void* coefs, void* scratch,
                  size_t scratch_bytes, cudaStream_t st) {
-    const dhk::Plan& P = H->plan;
+    return process_plan(H, H->plan, frames, dtype, batch, fields, coefs, scratch, scratch_bytes, st);
+}
+
+int process_plan(Handle* H, const dhk::Plan& P, const void* frames, int dtype, int batch, void* fields, void* coefs,
+                 void* scratch, size_t scratch_bytes, cudaStream_t st) {
     if (P.modes == 0) coefs = nullptr;
     void* out = coefs;
     if (coefs && P.basis_tt) {
@@ -461,11 +465,21 @@ int process_with(Handle* H, const void* frames, int dtype, int batch, void* fiel
     }
     int rc;
     if (use_fused(P) && fused_frames_ok(P, frames, dtype))
-        rc = launch_fused_path(H, frames, dtype, batch, fields, coefs, st, nullptr);
+        rc = launch_fused_path(H, P, frames, dtype, batch, fields, coefs, st, nullptr);
     else
         rc = run_split(P, scratch, scratch_bytes, frames, dtype, batch, nullptr, fields, coefs, st, nullptr);
     if (rc || out == coefs) return rc;
     return finish_basis(P, coefs, out, batch, st, nullptr);
+}
+
+void window_rows(const dhk::Plan& P, int* row0, int* rows) {
+    int lo = P.height, hi = 0;
+    for (int p = 0; p < P.pols; ++p) {
+        lo = std::min(lo, P.pol[p].oy);
+        hi = std::max(hi, P.pol[p].oy + P.n);
+    }
+    *row0 = lo;
+    *rows = hi - lo;
 }
 
 int run_split(const dhk::Plan& P, void* scratch, size_t scratch_bytes, const void* frames, int dtype, int batch,

@@ -3,7 +3,9 @@
 // host memory.  dh_process_batch_host does the same on the GPU with the copies hidden behind the kernels:
 // the batch is cut into chunks that cycle over kSlots streams, each with its own device staging buffers, so
 // the host-to-device copy of one chunk, the reconstruction of the previous one and the device-to-host copy of
-// the one before that run at the same time (the two copy directions use separate copy engines).
+// the one before that run at the same time (the two copy directions use separate copy engines).  Only the frame
+// rows that hold the polarisation windows are copied (one strided copy per chunk), and the kernels run with a
+// copy of the plan whose frame height and window rows are those of the cropped frames.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -96,7 +98,13 @@ static int process_host(Handle* H, const void* h_frames, int dtype, int batch, v
     const dhk::Plan& P = H->plan;
     if (P.modes == 0) h_coefs = nullptr;
     const size_t esz = dtype == DH_DTYPE_U16 ? 2 : 4;
-    const size_t frame = (size_t)P.width * P.height * esz;
+    int row0 = 0, rows = 0;
+    window_rows(P, &row0, &rows);
+    dhk::Plan Pc = P;                      // the plan of the cropped frames
+    Pc.height = rows;
+    for (int p = 0; p < P.pols; ++p) Pc.pol[p].oy -= row0;
+    const size_t full = (size_t)P.width * P.height * esz;
+    const size_t frame = (size_t)P.width * rows * esz;
     const size_t field = h_fields ? (size_t)P.pols * P.m * P.m * sizeof(float2) : 0;
     const size_t coef = h_coefs ? (size_t)P.pols * P.modes_out * sizeof(float2) : 0;
     // staged frames start 256-byte aligned, so the row pitch alone decides whether the fused path applies
@@ -134,13 +142,14 @@ static int process_host(Handle* H, const void* h_frames, int dtype, int batch, v
         unsigned char* d_fields = field ? base + b_frames : nullptr;
         unsigned char* d_coefs = coef ? base + b_frames + b_fields : nullptr;
         unsigned char* d_scratch = scratch ? base + b_frames + b_fields + b_coefs : nullptr;
-        e = cudaMemcpyAsync(d_frames, (const unsigned char*)h_frames + (size_t)f0 * frame, (size_t)n * frame,
-                            cudaMemcpyHostToDevice, st);
+        // rows [row0, row0 + rows) of each of the chunk's frames, packed
+        e = cudaMemcpy2DAsync(d_frames, frame, (const unsigned char*)h_frames + (size_t)f0 * full + (size_t)row0 * P.width * esz,
+                              full, frame, n, cudaMemcpyHostToDevice, st);
         if (e != cudaSuccess) {
             rc = cuda_fail(e, "frames upload");
             break;
         }
-        rc = process_with(H, d_frames, dtype, n, d_fields, d_coefs, d_scratch, b_scratch, st);
+        rc = process_plan(H, Pc, d_frames, dtype, n, d_fields, d_coefs, d_scratch, b_scratch, st);
         if (rc) break;
         if (d_fields) {
             e = cudaMemcpyAsync((unsigned char*)h_fields + (size_t)f0 * field, d_fields, (size_t)n * field,

@@ -493,9 +493,8 @@ cudaError_t fused_init() {
     return dhk::set_attr<64, 8, 8>();
 }
 
-int launch_fused_path(Handle* H, const void* frames, int dtype, int batch, void* fields, void* coefs,
-                      cudaStream_t st, dhk::StageTimer* tm) {
-    const dhk::Plan& P = H->plan;
+int launch_fused_path(Handle* H, const dhk::Plan& P, const void* frames, int dtype, int batch, void* fields,
+                      void* coefs, cudaStream_t st, dhk::StageTimer* tm) {
     int dev = H->device;
     if (dev < 0 || dev >= 64) return fail(DH_ERROR_ERROR, "device index out of range");
     if (!g_sm_count[dev]) {

@@ -81,8 +81,8 @@ bool use_fused(const dhk::Plan& P);
 // The fused kernel stages windows with tensor copies: the frames need a 16-byte aligned base and row pitch.
 bool fused_frames_ok(const dhk::Plan& P, const void* frames, int dtype);
 cudaError_t fused_init();
-int launch_fused_path(Handle* H, const void* frames, int dtype, int batch, void* fields, void* coefs,
-                      cudaStream_t st, dhk::StageTimer* timer);
+int launch_fused_path(Handle* H, const dhk::Plan& P, const void* frames, int dtype, int batch, void* fields,
+                      void* coefs, cudaStream_t st, dhk::StageTimer* timer);
 
 // HG coefficient bytes per frame that an output-basis transform needs as scratch (0 for the HG basis).
 size_t basis_scratch_bytes(const dhk::Plan& P);
@@ -92,5 +92,10 @@ size_t basis_scratch_bytes(const dhk::Plan& P);
 // transform the last batch * basis_scratch_bytes of the scratch hold the HG coefficients.  No profiling.
 int process_with(Handle* H, const void* frames, int dtype, int batch, void* fields, void* coefs, void* scratch,
                  size_t scratch_bytes, cudaStream_t st);
+// As process_with, with a copy of the handle's plan (the host pipeline's row-cropped frames).
+int process_plan(Handle* H, const dhk::Plan& P, const void* frames, int dtype, int batch, void* fields, void* coefs,
+                 void* scratch, size_t scratch_bytes, cudaStream_t st);
+// Rows [row0, row0 + rows) of a frame that hold every polarisation's window.
+void window_rows(const dhk::Plan& P, int* row0, int* rows);
 
 }  // namespace dh

@@ -2,8 +2,8 @@
 //
 // One scheduler thread per server owns the device work.  Submitted requests wait in a FIFO queue; the head is
 // admitted as soon as a stream slot is free and the budget arena (one device allocation, first-fit with
-// coalescing) can hold its reservation: input frames, the requested outputs and the generic path's scratch
-// for one chunk of frames.  An admitted request is queued on its slot's stream as host-to-device copy,
+// coalescing) can hold its reservation: input frames (the rows holding the windows), the requested outputs and
+// the generic path's scratch for one chunk of frames.  An admitted request is queued on its slot's stream as host-to-device copy,
 // reconstruction (the same kernels as dh_process_batch, with the handle's device-resident plan and the
 // request's own scratch), and device-to-host copies of its outputs, chunk after chunk, followed by an event.
 // The scheduler polls the events, releases the reservation and the slot of every finished request, records
@@ -170,18 +170,26 @@ void launch(dh_server_s* S, Req* r, Slot& sl) {
     unsigned char* d_coefs = r->b_coefs ? base + r->b_frames + r->b_fields : nullptr;
     unsigned char* d_scratch = r->b_scratch ? base + r->b_frames + r->b_fields + r->b_coefs : nullptr;
     const size_t esz = r->r.dtype == DH_DTYPE_U16 ? 2 : 4;
-    const size_t frame_bytes = (size_t)P.width * P.height * esz;
+    // only the rows holding the windows are uploaded; the kernels run on a plan of the cropped frames
+    int row0 = 0, rows = 0;
+    window_rows(P, &row0, &rows);
+    dhk::Plan Pc = P;
+    Pc.height = rows;
+    for (int p = 0; p < P.pols; ++p) Pc.pol[p].oy -= row0;
+    const size_t full_bytes = (size_t)P.width * P.height * esz;
+    const size_t frame_bytes = (size_t)P.width * rows * esz;
     const size_t field_bytes = (size_t)P.pols * P.m * P.m * 8;
     const size_t coef_bytes = (size_t)P.pols * P.modes_out * 8;
     for (int f0 = 0; f0 < r->r.batch && rc == DH_SUCCESS; f0 += r->chunk) {
         const int n = std::min(r->chunk, r->r.batch - f0);
-        cudaError_t e = cudaMemcpyAsync(d_frames, (const unsigned char*)r->r.h_frames + f0 * frame_bytes, n * frame_bytes,
-                                        cudaMemcpyHostToDevice, sl.st);
+        cudaError_t e = cudaMemcpy2DAsync(d_frames, frame_bytes,
+                                          (const unsigned char*)r->r.h_frames + f0 * full_bytes + (size_t)row0 * P.width * esz,
+                                          full_bytes, frame_bytes, n, cudaMemcpyHostToDevice, sl.st);
         if (e != cudaSuccess) {
             rc = cuda_fail(e, "request frames upload");
             break;
         }
-        rc = process_with(H, d_frames, r->r.dtype, n, d_fields, d_coefs, d_scratch, r->b_scratch, sl.st);
+        rc = process_plan(H, Pc, d_frames, r->r.dtype, n, d_fields, d_coefs, d_scratch, r->b_scratch, sl.st);
         if (rc) break;
         if (d_fields) {
             e = cudaMemcpyAsync((unsigned char*)r->r.h_fields + f0 * field_bytes, d_fields, n * field_bytes,
@@ -331,7 +339,9 @@ int dh_server_submit(dh_server s, const dh_request* r, uint64_t* ticket) {
     q->r = *r;
     q->H = H;
     const size_t esz = r->dtype == DH_DTYPE_U16 ? 2 : 4;
-    const size_t frame = (size_t)P.width * P.height * esz;
+    int row0 = 0, rows = 0;
+    window_rows(P, &row0, &rows);
+    const size_t frame = (size_t)P.width * rows * esz;   // the uploaded rows of one frame
     const size_t field = r->h_fields ? (size_t)P.pols * P.m * P.m * 8 : 0;
     const size_t coef = (r->h_coefs && P.modes) ? (size_t)P.pols * P.modes_out * 8 : 0;
     // the fused path needs no scratch; frames staged in the arena are 256-byte aligned, so only the row pitch
