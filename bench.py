@@ -50,7 +50,7 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--frames", type=int, default=FRAMES, help="frames per step and GPU (default: the workload's 1000)")
     ap.add_argument("--workload", choices=["batching", "serving", "plain", "precision", "large_batch"], default="batching")
-    ap.add_argument("--requests", type=int, default=120, help="requests per serving run")
+    ap.add_argument("--requests", type=int, default=2000, help="requests per serving run")
     return ap.parse_args()
 
 
@@ -499,8 +499,8 @@ def run_serving(args, ws, rank, local):
             m, modes, _ = dh.dh_get_output_dims(handles[(kind, gi)])
             outs.append(torch.empty((n, geos[kind][gi].pol_count, modes), dtype=torch.complex64).pin_memory())
 
-        def run(load, arr_rng):
-            srv = dh.dh_server_create(8 << 30, 8)
+        def run(load, arr_rng, budget=8 << 30):
+            srv = dh.dh_server_create(budget, 8)
             try:
                 # upload every plan and warm the kernels outside the clock
                 for (kind, gi), h in handles.items():
@@ -531,6 +531,8 @@ def run_serving(args, ws, rank, local):
         out[prec_name] = {"saturated": sat["frames_per_s"], "saturation_run": sat}
         for load in (0.5, 0.9):
             out[prec_name][f"load_{load}"] = run(load, np.random.default_rng(7))
+        # stress: the same saturated stream through a 256 MiB budget (requests chunked to fit)
+        out[prec_name]["saturated_256MiB"] = run(None, None, budget=256 << 20)
         for h in handles.values():
             dh.dh_destroy(h)
     if rank == 0:
@@ -539,7 +541,8 @@ def run_serving(args, ws, rank, local):
             "steps": 1, "warmup": 1, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32 FFT, split-bf16 overlap", "data": "synthetic",
             "config": {"workload": "serving: %d requests of U{1..256} frames over 256x256/1pol, 512x512/2pol, "
-                                   "1024x1024/1pol; radius U(0.15,0.32) w_max; G 6..16; 8 GiB budget; 8 streams" %
+                                   "1024x1024/1pol; radius U(0.15,0.32) w_max; G 6..16; 8 GiB budget (and a 256 MiB "
+                                   "stress run); 8 streams" %
                                    args.requests, "frames": total_frames,
                        "frame_content": "per-kind pools of seeded synthetic frames, tiled; per-request geometry from "
                                         "8 resident plans per kind", "outputs": "coefficients to pinned host memory"},
