@@ -1,6 +1,6 @@
 // Fused single-kernel path for 128 x 128 windows (field sizes 32, 48 and 64): one thread block reconstructs
 // one (frame, polarisation) window entirely in shared memory, persistent over windows.  uint16 frames run two
-// 256-thread blocks per SM, float32 frames (twice the staging buffer) one 512-thread block.
+// blocks per SM, float32 frames (twice the staging buffer) one 512-thread block.
 //
 // Per window (the guide's pipeline steps 1-3 and digHoloProcessRemoveTilt):
 //   y pass   real columns x and x + 64 packed as one complex column; radix-16 DIF pass from the window staged
@@ -53,12 +53,12 @@ struct Staging {
     static constexpr int BYTES = kFRows * W * (int)sizeof(T);
 };
 
-// Threads per block and blocks per SM: uint16 frames fit two 256-thread blocks per SM (two windows in flight,
-// so one block's barriers overlap the other's work); float32 frames need twice the staging buffer and run one
-// 512-thread block per SM.
-template <typename T>
+// Threads per block and blocks per SM: uint16 frames fit two blocks per SM (two windows in flight, so one
+// block's barriers overlap the other's work), of 512 threads at 64 registers for M = 64 (no spills) and of
+// 256 threads otherwise; float32 frames need twice the staging buffer and run one 512-thread block per SM.
+template <int M, typename T>
 struct FusedShape {
-    static constexpr int NT = sizeof(T) == 2 ? 256 : 512;
+    static constexpr int NT = (sizeof(T) == 2 && M != 64) ? 256 : 512;
     static constexpr int MINB = sizeof(T) == 2 ? 2 : 1;
 };
 
@@ -104,11 +104,11 @@ __device__ __forceinline__ void emit_pair(float2* r1, int pitch, int M, int kly,
 }
 
 template <int M, int MR0, int MR1, typename T>
-__global__ void __launch_bounds__(FusedShape<T>::NT, FusedShape<T>::MINB)
+__global__ void __launch_bounds__(FusedShape<M, T>::NT, FusedShape<M, T>::MINB)
     k_fused128(const __grid_constant__ Plan P, const __grid_constant__ FusedArgs A, const __grid_constant__ CUtensorMap tmap) {
     using L = FusedLayout<M, T>;
     using S = Staging<T>;
-    constexpr int N = kFN, PITCH = L::PITCH, NT = FusedShape<T>::NT;
+    constexpr int N = kFN, PITCH = L::PITCH, NT = FusedShape<M, T>::NT;
     constexpr int NBLK = M / MR1;                  // row blocks of the last inverse pass
     constexpr int QB = NBLK < 4 ? NBLK : 4;        // partial-sum groups of the y contraction
     constexpr int BPQ = NBLK / QB;                 // row blocks per group
@@ -443,10 +443,10 @@ static int blocks_per_sm(int dtype) {
     int n = 0;
     cudaError_t e;
     if (dtype == DH_DTYPE_U16)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused128<M, MR0, MR1, uint16_t>, FusedShape<uint16_t>::NT,
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused128<M, MR0, MR1, uint16_t>, FusedShape<M, uint16_t>::NT,
                                                           FusedLayout<M, uint16_t>::bytes);
     else
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused128<M, MR0, MR1, float>, FusedShape<float>::NT,
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused128<M, MR0, MR1, float>, FusedShape<M, float>::NT,
                                                           FusedLayout<M, float>::bytes);
     return (e == cudaSuccess && n > 0) ? n : 1;
 }
@@ -454,9 +454,9 @@ static int blocks_per_sm(int dtype) {
 template <int M, int MR0, int MR1>
 static void launch(const Plan& P, const FusedArgs& A, const CUtensorMap& tm, int dtype, int grid, cudaStream_t st) {
     if (dtype == DH_DTYPE_U16)
-        k_fused128<M, MR0, MR1, uint16_t><<<grid, FusedShape<uint16_t>::NT, FusedLayout<M, uint16_t>::bytes, st>>>(P, A, tm);
+        k_fused128<M, MR0, MR1, uint16_t><<<grid, FusedShape<M, uint16_t>::NT, FusedLayout<M, uint16_t>::bytes, st>>>(P, A, tm);
     else
-        k_fused128<M, MR0, MR1, float><<<grid, FusedShape<float>::NT, FusedLayout<M, float>::bytes, st>>>(P, A, tm);
+        k_fused128<M, MR0, MR1, float><<<grid, FusedShape<M, float>::NT, FusedLayout<M, float>::bytes, st>>>(P, A, tm);
 }
 
 }  // namespace dhk
