@@ -82,10 +82,21 @@ __global__ void __launch_bounds__(kThreads, 2) k_xpass(const __grid_constant__ P
     for (int fb = blockIdx.z; fb < B.count; fb += gridDim.z) {
         const int f = B.frame0 + fb;
         const float2* r1 = B.r1 + (size_t)(fb * P.pols + pol) * M * N;
-        for (int idx = tid; idx < R * N; idx += nthr) {
-            const int row = idx >> logn, x = idx & (N - 1);
-            const int q = q0 + row;
-            bufN[x * es + row] = (q < M) ? r1[(size_t)q * N + x] : make_float2(0.f, 0.f);
+        // eight independent loads in flight per thread before their shared-memory stores
+        for (int i0 = tid; i0 < R * N; i0 += 8 * nthr) {
+            float2 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int idx = i0 + u * nthr;
+                const int row = idx >> logn, x = idx & (N - 1);
+                const int q = q0 + row;
+                v[u] = (idx < R * N && q < M) ? r1[(size_t)q * N + x] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int idx = i0 + u * nthr;
+                if (idx < R * N) bufN[(idx & (N - 1)) * es + (idx >> logn)] = v[u];
+            }
         }
         __syncthreads();
         fft_run<false>(bufN, N, P.rad_n, P.nrad_n, logr, es, P.tw_fwd_n, tid, nthr);
@@ -128,9 +139,20 @@ __global__ void __launch_bounds__(kThreads, 2) k_yinv(const __grid_constant__ Pl
         const float2* g = B.g + (size_t)(fb * P.pols + pol) * M * M;
         float2 acc[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
         for (int i0 = 0; i0 < M; i0 += kChunkI) {
-            for (int idx = tid; idx < M * kChunkI; idx += nthr) {
-                const int q = idx >> 5, i = idx & (kChunkI - 1);
-                buf[P.pos_m[q] * kChunkI + i] = (i0 + i < M) ? g[(size_t)q * M + i0 + i] : make_float2(0.f, 0.f);
+            // eight independent loads in flight per thread before their shared-memory stores
+            for (int j0 = tid; j0 < M * kChunkI; j0 += 8 * nthr) {
+                float2 v[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int idx = j0 + u * nthr;
+                    const int q = idx >> 5, i = idx & (kChunkI - 1);
+                    v[u] = (idx < M * kChunkI && i0 + i < M) ? g[(size_t)q * M + i0 + i] : make_float2(0.f, 0.f);
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int idx = j0 + u * nthr;
+                    if (idx < M * kChunkI) buf[P.pos_m[idx >> 5] * kChunkI + (idx & (kChunkI - 1))] = v[u];
+                }
             }
             __syncthreads();
             fft_run<true>(buf, M, P.rad_m, P.nrad_m, 5, kChunkI, P.tw_inv_m, tid, nthr);

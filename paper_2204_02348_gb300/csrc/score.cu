@@ -55,10 +55,20 @@ __global__ void __launch_bounds__(kSThreads, 2) k_xfwd(const __grid_constant__ P
     const int pol = blockIdx.y, q0 = blockIdx.x * R;
     for (int fb = blockIdx.z; fb < count; fb += gridDim.z) {
         const float2* src = r1s + (size_t)(fb * P.pols + pol) * S.ms * N;
-        for (int idx = tid; idx < R * N; idx += nthr) {
-            const int row = idx >> logn, x = idx & (N - 1);
-            const int q = q0 + row;
-            smem[x * es + row] = (q < S.ms) ? src[(size_t)q * N + x] : make_float2(0.f, 0.f);
+        // eight independent loads in flight per thread before their shared-memory stores
+        for (int i0 = tid; i0 < R * N; i0 += 8 * nthr) {
+            float2 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int idx = i0 + u * nthr;
+                const int q = q0 + (idx >> logn);
+                v[u] = (idx < R * N && q < S.ms) ? src[(size_t)q * N + (idx & (N - 1))] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int idx = i0 + u * nthr;
+                if (idx < R * N) smem[(idx & (N - 1)) * es + (idx >> logn)] = v[u];
+            }
         }
         __syncthreads();
         fft_run<false>(smem, N, P.rad_n, P.nrad_n, logr, es, P.tw_fwd_n, tid, nthr);
@@ -87,13 +97,29 @@ __global__ void __launch_bounds__(kSThreads, 2) k_xinv_sel(const __grid_constant
     const PolDev& pd = P.pol[pol];
     for (int fb = blockIdx.z; fb < count; fb += gridDim.z) {
         const float2* src = xs + (size_t)(fb * P.pols + pol) * S.ms * S.msx;
-        for (int idx = tid; idx < R * M; idx += nthr) {
-            const int row = idx / M, p = idx - row * M;
-            const int q = q0 + row;
-            float2 v = make_float2(0.f, 0.f);
-            if (q < M && p >= pd.mask_lo[q] && p <= pd.mask_hi[q])
-                v = cmul(cmul(src[(size_t)(qoff + q) * S.msx + poff + p], pd.phase_x[p]), pd.phase_y[q]);
-            smem[P.pos_m[p] * es + row] = v;
+        // eight independent loads in flight per thread before their shared-memory stores
+        for (int i0 = tid; i0 < R * M; i0 += 8 * nthr) {
+            float2 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int idx = i0 + u * nthr;
+                const int row = idx / M, p = idx - row * M;
+                const int q = q0 + row;
+                v[u] = make_float2(0.f, 0.f);
+                if (idx < R * M && q < M && p >= pd.mask_lo[q] && p <= pd.mask_hi[q])
+                    v[u] = src[(size_t)(qoff + q) * S.msx + poff + p];
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int idx = i0 + u * nthr;
+                if (idx < R * M) {
+                    const int row = idx / M, p = idx - row * M;
+                    const int q = q0 + row;
+                    float2 w = make_float2(0.f, 0.f);
+                    if (q < M && p >= pd.mask_lo[q] && p <= pd.mask_hi[q]) w = cmul(cmul(v[u], pd.phase_x[p]), pd.phase_y[q]);
+                    smem[P.pos_m[p] * es + row] = w;
+                }
+            }
         }
         __syncthreads();
         fft_run<true>(smem, M, P.rad_m, P.nrad_m, logr, es, P.tw_inv_m, tid, nthr);

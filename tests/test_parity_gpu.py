@@ -355,3 +355,19 @@ def test_reference_calibration_scoring():
     ref = orc.score_settings(d["frames"], s, cand["tilt_deg"], cand["defocus"], cand["waist"])
     got = _score(s, d["frames"], cand)
     assert np.all(np.abs(got - ref) / ref <= 2 * COEF_TOL), (got, ref)
+
+
+# ----------------------------------------------------------------------------- every fused-kernel instantiation
+
+
+@pytest.mark.parametrize("m,dtype", [(32, "u16"), (48, "u16"), (64, "u16"), (32, "f32"), (48, "f32"), (64, "f32")])
+def test_fused_instantiations_against_oracle(m, dtype):
+    # the fused kernel is compiled per field size and pixel type (uint16: two blocks per SM of 256 or 512
+    # threads; float32: one 512-thread block); G = 16 is its largest group count
+    s = syn.with_(syn.setup_batching(), ifft_size=m, dtype=dtype, group_count=16, signal_groups=9)
+    d = syn.make_frames(s, 5, seed=170 + m)
+    assert d["frames"].dtype == (np.uint16 if dtype == "u16" else np.float32)
+    out = run_library(s, d["frames"])
+    _check(s, d["frames"], out)
+    # the same frames through the generic path (window output forces it) agree as well
+    _check(s, d["frames"], run_library(s, d["frames"], window=True))
