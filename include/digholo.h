@@ -114,7 +114,7 @@ int dh_set_frame(dh_handle h, int width, int height, int pol_count, double pixel
 int dh_set_wavelength(dh_handle h, double wavelength);
 
 /* FFT window size (digHoloConfigSetfftWindowSize).  Values are floored to a multiple of 16 as the guide's
- * DIGHOLO_PIXEL_QUANTA rule says; this build accepts square power-of-two windows 16..1024 only
+ * DIGHOLO_PIXEL_QUANTA rule says; the library accepts square power-of-two windows 16..1024 only
  * (DH_ERROR_INVALIDDIMENSION otherwise).  *set_nx / *set_ny (nullable) receive the sizes actually set. */
 int dh_set_fft_window(dh_handle h, int nx, int ny, int* set_nx, int* set_ny);
 
