@@ -579,8 +579,9 @@ def run_workload(args, ws, rank, local):
     """Secondary workloads, one JSON line each:
     plain       1 frame 128x128 float32, 15 modes, 32x32 field: latency of single-frame calls (p50/p99), device
                 input and end to end from host;
-    precision   1024 frames 640x512 u16, two 256x256 windows, 120 modes: FP32 and split-BF16 overlaps, frames/s
-                and coefficient error against the FP64 oracle on sampled frames;
+    precision   1024 frames 640x512 u16, two 256x256 windows, 120 modes: FP32 and split-BF16 overlaps, frames/s,
+                and the split-BF16 coefficients' deviation from the FP32 ones (accuracy against the FP64 oracle is
+                what the parity tests establish);
     large_batch 2000 frames 1280x1024 u16, two 512x512 windows, 210 modes, 64 alignment candidates scored with
                 the split-BF16 overlap: frames/s (every frame under all 64 candidates)."""
     import numpy as np
@@ -632,13 +633,11 @@ def run_workload(args, ws, rank, local):
                     "e2e_latency_ms": {"p50": pct(lat_e2e, 0.5), "p99": pct(lat_e2e, 0.99),
                                        "note": "host frame in, host field and coefficients out"}})
     elif args.workload == "precision":
-        from oracle import digholo_oracle as orc
         s = syn.setup_precision()
         B = 1024
         base, frames = _tiled_frames(s, B, 16, syn.BASE_SEED + 2)
         fr = torch.from_numpy(frames).to(dev)
-        f_ref, c_ref = orc.process_batch(base["frames"][:2], s)
-        res = {}
+        res, c_fp32 = {}, None
         for name, prec in (("fp32", dh.DH_PRECISION_FP32), ("split_bf16", dh.DH_PRECISION_SPLIT_BF16)):
             h = dh.dh_create()
             dh.configure(h, s)
@@ -647,12 +646,13 @@ def run_workload(args, ws, rank, local):
             f = torch.empty((B, 2, m, m), dtype=torch.complex64, device=dev)
             c = torch.empty((B, 2, modes), dtype=torch.complex64, device=dev)
             ms = _event_time(lambda: dh.dh_process_batch(h, fr, dh.DH_DTYPE_U16, B, f, c), max(3, args.steps // 20), 3)
-            cc = c[:2].cpu().numpy()
-            ff = f[:2].cpu().numpy()
-            err_c = max(np.linalg.norm(cc[b, p] - c_ref[b, p]) / np.linalg.norm(c_ref[b, p]) for b in range(2) for p in range(2))
-            err_f = max(np.linalg.norm(ff[b, p] - f_ref[b, p]) / np.linalg.norm(f_ref[b, p]) for b in range(2) for p in range(2))
-            res[name] = {"frames_per_s": B / (ms / 1e3), "ms_per_batch": ms, "coef_rel_l2_max": err_c,
-                         "field_rel_l2_max": err_f}
+            cc = c.cpu().numpy().astype(np.complex128)
+            res[name] = {"frames_per_s": B / (ms / 1e3), "ms_per_batch": ms}
+            if c_fp32 is None:
+                c_fp32 = cc
+            else:
+                dev_rel = np.linalg.norm(cc - c_fp32, axis=-1) / np.linalg.norm(c_fp32, axis=-1)
+                res[name]["coef_rel_l2_vs_fp32_max"] = float(dev_rel.max())
             dh.dh_destroy(h)
         bpf = 2 * (256 * 256 * 2 + 96 * 96 * 8 + 120 * 8)
         peak, _ = measured_peak()
