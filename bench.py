@@ -49,7 +49,8 @@ def parse_args():
     ap.add_argument("--precision", choices=["fp32", "split_bf16"], default="fp32")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--frames", type=int, default=FRAMES, help="frames per step and GPU (default: the workload's 1000)")
-    ap.add_argument("--workload", choices=["batching", "serving", "plain", "precision", "large_batch"], default="batching")
+    ap.add_argument("--workload", choices=["batching", "serving", "plain", "precision", "large_batch", "extensions"],
+                    default="batching")
     ap.add_argument("--requests", type=int, default=2000, help="requests per serving run")
     return ap.parse_args()
 
@@ -688,6 +689,99 @@ def run_workload(args, ws, rank, local):
         print(json.dumps(out), flush=True)
 
 
+def run_extensions(args, ws, rank, local):
+    """The optional stages on the batching geometry (320x256 u16 frames, two 128x128 windows, M = 64, 45 modes),
+    one JSON line: batch averaging (4000 input frames in sequential groups of 4 -> 1000 outputs), LG
+    coefficients, fill-factor correction, reference-wave calibration (1000 frames each), transfer-matrix metrics
+    of a 90 x 90 coefficient batch, and the fine-alignment search on 16 frames from a perturbed start.  Device
+    buffers; CUDA events on the launching stream; per-kernel times from the library's profiler."""
+    import numpy as np
+    import torch
+
+    import paper_2204_02348_gb300 as dh
+    from synth import holograms as syn
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    steps = max(5, args.steps // 20)
+    base = syn.setup_batching()
+    res = {}
+
+    def timed(setup, frames, call, n_out, extra=None):
+        h = dh.dh_create()
+        dh.configure(h, setup)
+        m, modes, _ = dh.dh_get_output_dims(h)
+        fr = torch.from_numpy(frames).to(dev)
+        f = torch.empty((n_out, setup.pol_count, m, m), dtype=torch.complex64, device=dev)
+        c = torch.empty((n_out, setup.pol_count, modes), dtype=torch.complex64, device=dev)
+        for _ in range(3):
+            call(h, fr, f, c)
+        torch.cuda.synchronize()
+        dh.dh_set_profiling(h, True)
+        ms = _event_time(lambda: call(h, fr, f, c), steps, 0)
+        prof = dh.dh_get_profile(h)
+        dh.dh_destroy(h)
+        out = {"ms_per_call": ms, "kernels": {k: {"launches": v[0], "ms_per_call": v[1] / steps} for k, v in prof.items()}}
+        out.update(extra or {})
+        return out
+
+    # batch averaging: 1000 groups of 4 sequential frames
+    A, G = 4, 1000
+    d = syn.make_avg_frames(base, 16, A, 0, seed=syn.BASE_SEED + 20)
+    frames = np.ascontiguousarray(np.resize(d["frames"], (A * G,) + d["frames"].shape[1:]))
+    r = timed(base, frames, lambda h, fr, f, c: dh.dh_process_batch_avg(h, fr, dh.DH_DTYPE_U16, G, A, 0, f, c), G)
+    r["input_frames_per_s"] = A * G / (r["ms_per_call"] / 1e3)
+    r["output_fields_per_s"] = G / (r["ms_per_call"] / 1e3)
+    res["averaging_4_sequential"] = r
+    # LG basis, fill factor, reference calibration: 1000 frames each
+    _, frames = _tiled_frames(base, 1000, 16, syn.BASE_SEED + 21)
+    plain_call = lambda h, fr, f, c: dh.dh_process_batch(h, fr, dh.DH_DTYPE_U16, 1000, f, c)
+    for name, setup in (("lg_basis", syn.with_(base, basis="lg")), ("fill_factor", syn.with_(base, fill_factor=True))):
+        r = timed(setup, frames, plain_call, 1000)
+        r["frames_per_s"] = 1000 / (r["ms_per_call"] / 1e3)
+        res[name] = r
+    cal, amp = syn.reference_profile(base, sigma_fraction=0.15, floor=200)
+    sc = syn.with_(base, ref_amplitude=amp, ref_cal=cal)
+    _, frames_c = _tiled_frames(sc, 1000, 16, syn.BASE_SEED + 22)
+    r = timed(sc, frames_c, plain_call, 1000)
+    r["frames_per_s"] = 1000 / (r["ms_per_call"] / 1e3)
+    res["ref_calibration"] = r
+    # transfer-matrix metrics of a 90 x 90 batch (45 frames x 2 pols would be rectangular: use 90 rows)
+    rng = np.random.default_rng(syn.BASE_SEED + 23)
+    coefs = torch.from_numpy((rng.standard_normal((90, 2, 45)) + 1j * rng.standard_normal((90, 2, 45))).astype(np.complex64)).to(dev)
+    h = dh.dh_create()
+    dh.configure(h, base)
+    dh.dh_calc_metrics(h, coefs, 90)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        vals, _ = dh.dh_calc_metrics(h, coefs, 90)
+    res["metrics_90x90"] = {"ms_per_call": 1e3 * (time.perf_counter() - t0) / steps, "IL_dB": vals["IL"], "MDL_dB": vals["MDL"]}
+    dh.dh_destroy(h)
+    # fine-alignment search on 16 frames from a perturbed start
+    s16 = syn.setup_batching()
+    d16 = syn.make_frames(s16, 16, seed=syn.BASE_SEED + 24)
+    off = syn.with_(s16, tilt_deg=[(t[0] + 0.03, t[1] - 0.02) for t in s16.tilt_deg], waist=[w * 1.05 for w in s16.waist])
+    h = dh.dh_create()
+    dh.configure(h, off)
+    fr = torch.from_numpy(d16["frames"]).to(dev)
+    t0 = time.perf_counter()
+    power, its = dh.dh_auto_align(h, fr, dh.DH_DTYPE_U16, 16)
+    wall = time.perf_counter() - t0
+    tilt, _, waist = dh.dh_get_alignment(h)
+    dh.dh_destroy(h)
+    res["auto_align_16_frames"] = {"ms_per_search": 1e3 * wall, "scorings": its, "candidates_per_scoring": 17,
+                                   "tilt_error_deg": max(abs(tilt[p][a] - s16.tilt_deg[p][a]) for p in range(2) for a in range(2)),
+                                   "waist_rel_error": max(abs(waist[p] / s16.waist[p] - 1) for p in range(2))}
+    if rank == 0:
+        print(json.dumps({"metric": "optional stages on the batching geometry (frames/s per stage)",
+                          "value": res["averaging_4_sequential"]["input_frames_per_s"], "unit": "input frames/s",
+                          "n_gpus": ws, "steps": steps, "warmup": 3, "higher_is_better": True, "scaling": "weak",
+                          "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                          "config": {"workload": "extensions: batching geometry 320x256 u16, 2 windows 128x128, M 64, 45 modes",
+                                     "frame_content": "16 seeded frames tiled"},
+                          "extensions": res}), flush=True)
+
+
 def main():
     args = parse_args()
     ws, rank, local = dist_env()
@@ -697,6 +791,8 @@ def main():
         run_serving(args, ws, rank, local)
     elif args.workload in ("plain", "precision", "large_batch"):
         run_workload(args, ws, rank, local)
+    elif args.workload == "extensions":
+        run_extensions(args, ws, rank, local)
     else:
         run_ours(args, ws, rank, local)
 

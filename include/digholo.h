@@ -174,8 +174,7 @@ int dh_set_basis_transform(dh_handle h, int modes_in, int modes_out, const void*
  * calibration frame is used.  The array is copied; the calibration is enabled.  width x height must equal the
  * frame size when a batch is processed (DH_ERROR_INVALIDDIMENSION otherwise).  As in the guide, an invalid
  * call (cal NULL: DH_ERROR_NULLPOINTER; a count or size < 1, or an all-zero array: DH_ERROR_INVALIDARGUMENT)
- * disables the calibration: the one exception to "a failed call leaves the settings unchanged".  With the
- * calibration enabled, batches take the generic multi-kernel path. */
+ * disables the calibration: the one exception to "a failed call leaves the settings unchanged". */
 int dh_set_ref_calibration(dh_handle h, const uint16_t* cal, int wavelength_count, int width, int height);
 
 /* Enable (nonzero) or disable the reference calibration last set (digHoloConfigSetRefCalibrationEnabled);

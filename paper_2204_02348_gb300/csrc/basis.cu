@@ -2,18 +2,18 @@
 // digHoloConfigSetBasisTypeLG / digHoloConfigSetBasisTypeCustom: the field is decomposed in the separable HG
 // basis and the coefficients are then multiplied by a transform matrix).
 //
-// One block takes kVB coefficient vectors (frame, polarisation), stages them in shared memory, and every
-// thread owns output modes k (strided by the block size): for each input mode l it reads T[k][l] from the
-// transposed matrix (consecutive k in consecutive threads, so a warp reads one contiguous row segment) and
-// accumulates it against the kVB staged inputs, which the warp reads as a broadcast.  The matrix is read once
-// per block from L2; the sums run in ascending l, so results do not depend on the launch shape.
+// One block takes kVB coefficient vectors (frame, polarisation) and stages them in shared memory; its threads
+// take (vector, output mode) pairs, output mode fastest, and sum T[k][l] c[v][l] over the input modes l in
+// ascending order, reading the transposed matrix T^T[l][k] (consecutive k in consecutive threads: one
+// contiguous row segment per warp) and the staged inputs (a broadcast per vector).  The sums run in a fixed
+// order, so results do not depend on the launch shape.
 #include "kernels.cuh"
 
 namespace dhk {
 
 namespace {
 
-constexpr int kVB = 16;          // coefficient vectors per block
+constexpr int kVB = 8;           // coefficient vectors per block
 constexpr int kThreads = 256;
 constexpr int kMaxModesIn = DH_MAX_GROUPS * (DH_MAX_GROUPS + 1) / 2;
 
@@ -34,18 +34,12 @@ __global__ void __launch_bounds__(kThreads) k_basis(const float2* __restrict__ h
         s_in[i] = v < nv ? hg[(size_t)v0 * modes_in + i] : make_float2(0.f, 0.f);
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < modes_out; k += kThreads) {
-        float2 acc[kVB];
-#pragma unroll
-        for (int v = 0; v < kVB; ++v) acc[v] = make_float2(0.f, 0.f);
-        for (int l = 0; l < modes_in; ++l) {
-            const float2 t = __ldg(tt + (size_t)l * modes_out + k);
-#pragma unroll
-            for (int v = 0; v < kVB; ++v) acc[v] = cmac(acc[v], t, s_in[v * modes_in + l]);
-        }
-#pragma unroll
-        for (int v = 0; v < kVB; ++v)
-            if (v < nv) out[(size_t)(v0 + v) * modes_out + k] = acc[v];
+    for (int t = threadIdx.x; t < nv * modes_out; t += kThreads) {
+        const int v = t / modes_out, k = t - v * modes_out;
+        const float2* in = s_in + v * modes_in;
+        float2 acc = make_float2(0.f, 0.f);
+        for (int l = 0; l < modes_in; ++l) acc = cmac(acc, __ldg(tt + (size_t)l * modes_out + k), in[l]);
+        out[(size_t)(v0 + v) * modes_out + k] = acc;
     }
 }
 

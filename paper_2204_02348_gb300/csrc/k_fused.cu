@@ -3,9 +3,10 @@
 // blocks per SM, float32 frames (twice the staging buffer) one 512-thread block.
 //
 // Per window (the guide's pipeline steps 1-3 and digHoloProcessRemoveTilt):
-//   y pass   real columns x and x + 64 packed as one complex column; radix-16 DIF pass from the window staged
-//            in shared memory by a tensor copy, radix-8 pass fused with the separation of the two real spectra
-//            (Z(k), conj Z(-k)) and the selection of the M box rows;
+//   y pass   real columns x and x + 64 packed as one complex column (times the reference-calibration factors
+//            when enabled); radix-16 DIF pass from the window staged in shared memory by a tensor copy,
+//            radix-8 pass fused with the separation of the two real spectra (Z(k), conj Z(-k)) and the
+//            selection of the M box rows;
 //   x pass   radix-16 then radix-8 DIF along x on the M box rows, the second pass fused with the box-column
 //            selection, the circular mask and the beam-centre phase;
 //   inverse  M-point inverse transform along x (DIT, digit-reversed in / natural out) and along y (DIF,
@@ -190,6 +191,15 @@ __global__ void __launch_bounds__(FusedShape<M, T>::NT, FusedShape<M, T>::MINB)
             float2 v[16];
 #pragma unroll
             for (int r = 0; r < 16; ++r) v[r] = staged_pair<T>(stg + (j + 8 * r) * S::W, xo + c);
+            if (pd.cal) {
+                // reference calibration: window pixel (x, y) times sqrt(max cal / cal), from the L2-resident table
+#pragma unroll
+                for (int r = 0; r < 16; ++r) {
+                    const float* k = pd.cal + (j + 8 * r) * N + c;
+                    v[r].x *= __ldg(k);
+                    v[r].y *= __ldg(k + N / 2);
+                }
+            }
             dft16<false>(v);
 #pragma unroll
             for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], twN[j * r]);
@@ -469,7 +479,6 @@ static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
 bool use_fused(const dhk::Plan& P) {
     if (P.n != dhk::kFN || P.groups > dhk::kFGMax || P.precision != DH_PRECISION_FP32) return false;
-    if (P.pol[0].cal) return false;   // the reference calibration runs on the generic path
     return P.m == 32 || P.m == 48 || P.m == 64;
 }
 
