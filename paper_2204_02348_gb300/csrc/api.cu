@@ -385,8 +385,12 @@ int process_avg(Handle* H, const void* frames, int dtype, int batch, int avg, in
     if (rc) return rc;
     const long long elems = (long long)P.pols * P.m * P.m;
     const int slices = dhk::avg_slices(elems);
-    const size_t split = split_window_bytes(P) * P.pols;
-    const size_t per_group = (size_t)avg * split + (size_t)elems * sizeof(float2) + (size_t)avg * slices * sizeof(float2);
+    // 128 x 128 windows: the fused kernel's forward-only mode writes each member's window and its inverse-only
+    // mode reconstructs the group means (no r1 scratch); otherwise the generic forward kernels
+    const bool fused = use_fused(P) && fused_frames_ok(P, frames, dtype);
+    // per member frame: its window (fused) or the generic path's r1 and window
+    const size_t member = fused ? (size_t)elems * sizeof(float2) : split_window_bytes(P) * P.pols;
+    const size_t per_group = (size_t)avg * member + (size_t)elems * sizeof(float2) + (size_t)avg * slices * sizeof(float2);
     // groups per chunk: enough member windows for several waves of the forward kernels, about the L2-sized
     // scratch target, at most the scratch cap and the grid limit
     int dev_sms = 148;
@@ -398,10 +402,13 @@ int process_avg(Handle* H, const void* frames, int dtype, int batch, int avg, in
     const int chunk = (int)std::max<size_t>(1, groups);
     rc = ensure_scratch(H, per_group * chunk);
     if (rc) return rc;
+    // scratch: [r1 of every member (generic path only)] [member windows] [group means] [inner-product partials]
     float2* r1 = (float2*)H->d_scratch;
-    float2* gbuf = r1 + (size_t)chunk * avg * P.pols * P.m * P.n;
+    float2* gbuf = fused ? r1 : r1 + (size_t)chunk * avg * P.pols * P.m * P.n;
     float2* mean = gbuf + (size_t)chunk * avg * elems;
     float2* part = mean + (size_t)chunk * elems;
+    if ((size_t)((part + (size_t)chunk * avg * slices) - r1) * sizeof(float2) > H->scratch_bytes)
+        return fail(DH_ERROR_ERROR, "averaging scratch layout exceeds the reservation");
     dhk::StageTimer* tm = H->timer();
     for (int g0 = 0; g0 < batch; g0 += chunk) {
         const int n = std::min(chunk, batch - g0);
@@ -411,25 +418,43 @@ int process_avg(Handle* H, const void* frames, int dtype, int batch, int avg, in
         B.r1 = r1;
         long long mstride, gstride;
         cudaError_t e = cudaSuccess;
+        const int total = batch * avg;
         if (mode == DH_AVGMODE_INTERLACED) {
             // member j of groups [g0, g0 + n) is the contiguous frame range [j batch + g0, j batch + g0 + n)
             for (int j = 0; j < avg && e == cudaSuccess; ++j) {
-                B.frame0 = j * batch + g0;
-                B.count = n;
-                B.g = gbuf + (size_t)j * n * elems;
-                e = dhk::launch_forward(P, B, st, tm);
+                if (fused) {
+                    rc = launch_fused(H, P, frames, dtype, total, j * batch + g0, n, dhk::kModeForward, nullptr,
+                                      gbuf + (size_t)j * n * elems, nullptr, nullptr, st, tm);
+                    if (rc) return rc;
+                } else {
+                    B.frame0 = j * batch + g0;
+                    B.count = n;
+                    B.g = gbuf + (size_t)j * n * elems;
+                    e = dhk::launch_forward(P, B, st, tm);
+                }
             }
             mstride = (long long)n * elems;
             gstride = elems;
         } else {
-            B.frame0 = g0 * avg;
-            B.count = n * avg;
-            B.g = gbuf;
-            e = dhk::launch_forward(P, B, st, tm);
+            if (fused) {
+                rc = launch_fused(H, P, frames, dtype, total, g0 * avg, n * avg, dhk::kModeForward, nullptr, gbuf,
+                                  nullptr, nullptr, st, tm);
+                if (rc) return rc;
+            } else {
+                B.frame0 = g0 * avg;
+                B.count = n * avg;
+                B.g = gbuf;
+                e = dhk::launch_forward(P, B, st, tm);
+            }
             mstride = elems;
             gstride = (long long)avg * elems;
         }
         if (e == cudaSuccess) e = dhk::launch_avg(gbuf, part, mean, n, avg, elems, mstride, gstride, st, tm);
+        if (e == cudaSuccess && fused) {
+            rc = launch_fused(H, P, nullptr, dtype, 0, g0, n, dhk::kModeInverse, mean, nullptr, fields, coefs, st, tm);
+            if (rc) return rc;
+            continue;
+        }
         if (e == cudaSuccess) {
             dhk::Batch L{};
             L.src = frames;

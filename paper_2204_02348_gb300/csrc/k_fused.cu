@@ -25,6 +25,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <cstring>
 #include <string>
 
 #include "fft.cuh"
@@ -45,7 +46,10 @@ struct FusedArgs {
     int x0[DH_MAX_POLS];          // staging origin (16-byte aligned element index), per polarisation
     float2* fields;               // nullable [B][pol][M][M]
     float2* coefs;                // nullable [B][pol][modes]
+    float2* win_out;              // forward-only mode: windows [count][pol][M][M] (rows in digit-reversed order)
+    const float2* win_in;         // inverse-only mode: windows in the same layout
 };
+
 
 template <typename T>
 struct Staging {
@@ -104,7 +108,7 @@ __device__ __forceinline__ void emit_pair(float2* r1, int pitch, int M, int kly,
     }
 }
 
-template <int M, int MR0, int MR1, typename T>
+template <int M, int MR0, int MR1, typename T, int MODE>
 __global__ void __launch_bounds__(FusedShape<M, T>::NT, FusedShape<M, T>::MINB)
     k_fused128(const __grid_constant__ Plan P, const __grid_constant__ FusedArgs A, const __grid_constant__ CUtensorMap tmap) {
     using L = FusedLayout<M, T>;
@@ -167,15 +171,23 @@ __global__ void __launch_bounds__(FusedShape<M, T>::NT, FusedShape<M, T>::MINB)
     int b = blockIdx.x / P.pols;
     if (tid == 0) {
         abort_flag = 0;
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb));
-        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-        if (b < A.count) stage_window(&tmap, dst, mb, A.x0[pol], pd.oy, A.frame0 + b, S::BYTES);
+        if (MODE != kModeInverse) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb));
+            asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+            if (b < A.count) stage_window(&tmap, dst, mb, A.x0[pol], pd.oy, A.frame0 + b, S::BYTES);
+        }
     }
     __syncthreads();
     const int xo = A.xo[pol];
     uint32_t parity = 0;
     for (; b < A.count; b += fstride) {
         const int f = A.frame0 + b;
+        if constexpr (MODE == kModeInverse) {
+            // the window comes from memory, rows already in the inverse transform's input order
+            const float2* w = A.win_in + (size_t)(b * P.pols + pol) * M * M;
+            for (int t = tid; t < M * M; t += NT) buf[(t / M) * PITCH + t % M] = w[t];
+            __syncthreads();
+        } else {
         const bool ok = mbar_wait(mb, parity);
         parity ^= 1u;
         if (!ok) abort_flag = 1;
@@ -309,6 +321,13 @@ __global__ void __launch_bounds__(FusedShape<M, T>::NT, FusedShape<M, T>::MINB)
             }
         }
         __syncthreads();
+        }   // forward part
+        if constexpr (MODE == kModeForward) {
+            float2* w = A.win_out + (size_t)(b * P.pols + pol) * M * M;
+            for (int t = tid; t < M * M; t += NT) w[t] = buf[(t / M) * PITCH + t % M];
+            __syncthreads();
+            continue;
+        }
 
         // ---------------------------------------------------------------- inverse transforms
         spass<MR1, true, true, M, MR1, M, PITCH, 1, NT>(buf, twM, tid);
@@ -434,39 +453,62 @@ __global__ void __launch_bounds__(FusedShape<M, T>::NT, FusedShape<M, T>::MINB)
         __syncthreads();
     }
     // a tensor copy still in flight (only after an expired wait) must land before the block exits
-    if (abort_flag && tid == 0) mbar_wait(mb, parity);
+    if (MODE != kModeInverse && abort_flag && tid == 0) mbar_wait(mb, parity);
+}
+
+template <int M, int MR0, int MR1, int MODE>
+static cudaError_t set_attr_mode() {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_fused128<M, MR0, MR1, uint16_t, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)FusedLayout<M, uint16_t>::bytes)))
+        return e;
+    return cudaFuncSetAttribute(k_fused128<M, MR0, MR1, float, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)FusedLayout<M, float>::bytes);
 }
 
 template <int M, int MR0, int MR1>
 static cudaError_t set_attr() {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_fused128<M, MR0, MR1, uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)FusedLayout<M, uint16_t>::bytes)))
-        return e;
-    return cudaFuncSetAttribute(k_fused128<M, MR0, MR1, float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)FusedLayout<M, float>::bytes);
+    if ((e = set_attr_mode<M, MR0, MR1, kModeFull>())) return e;
+    if ((e = set_attr_mode<M, MR0, MR1, kModeForward>())) return e;
+    return cudaFuncSetAttribute(k_fused128<M, MR0, MR1, uint16_t, kModeInverse>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FusedLayout<M, uint16_t>::bytes);
 }
 
-// Resident blocks per SM of one instantiation (the persistent grid is SMs x this).
+// Resident blocks per SM of one instantiation (the persistent grid is SMs x this).  The inverse-only mode
+// does not read frames and always runs the uint16 shape.
 template <int M, int MR0, int MR1>
-static int blocks_per_sm(int dtype) {
+static int blocks_per_sm(int dtype, int mode) {
     int n = 0;
     cudaError_t e;
-    if (dtype == DH_DTYPE_U16)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused128<M, MR0, MR1, uint16_t>, FusedShape<M, uint16_t>::NT,
-                                                          FusedLayout<M, uint16_t>::bytes);
+    if (mode == kModeInverse)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused128<M, MR0, MR1, uint16_t, kModeInverse>,
+                                                          FusedShape<M, uint16_t>::NT, FusedLayout<M, uint16_t>::bytes);
+    else if (dtype == DH_DTYPE_U16)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused128<M, MR0, MR1, uint16_t, kModeFull>,
+                                                          FusedShape<M, uint16_t>::NT, FusedLayout<M, uint16_t>::bytes);
     else
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused128<M, MR0, MR1, float>, FusedShape<M, float>::NT,
-                                                          FusedLayout<M, float>::bytes);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_fused128<M, MR0, MR1, float, kModeFull>,
+                                                          FusedShape<M, float>::NT, FusedLayout<M, float>::bytes);
     return (e == cudaSuccess && n > 0) ? n : 1;
 }
 
+template <int M, int MR0, int MR1, typename T, int MODE>
+static void launch_one(const Plan& P, const FusedArgs& A, const CUtensorMap& tm, int grid, cudaStream_t st) {
+    k_fused128<M, MR0, MR1, T, MODE><<<grid, FusedShape<M, T>::NT, FusedLayout<M, T>::bytes, st>>>(P, A, tm);
+}
+
 template <int M, int MR0, int MR1>
-static void launch(const Plan& P, const FusedArgs& A, const CUtensorMap& tm, int dtype, int grid, cudaStream_t st) {
-    if (dtype == DH_DTYPE_U16)
-        k_fused128<M, MR0, MR1, uint16_t><<<grid, FusedShape<M, uint16_t>::NT, FusedLayout<M, uint16_t>::bytes, st>>>(P, A, tm);
+static void launch(const Plan& P, const FusedArgs& A, const CUtensorMap& tm, int dtype, int mode, int grid,
+                   cudaStream_t st) {
+    if (mode == kModeInverse)
+        launch_one<M, MR0, MR1, uint16_t, kModeInverse>(P, A, tm, grid, st);
+    else if (dtype == DH_DTYPE_U16)
+        mode == kModeForward ? launch_one<M, MR0, MR1, uint16_t, kModeForward>(P, A, tm, grid, st)
+                             : launch_one<M, MR0, MR1, uint16_t, kModeFull>(P, A, tm, grid, st);
     else
-        k_fused128<M, MR0, MR1, float><<<grid, FusedShape<M, float>::NT, FusedLayout<M, float>::bytes, st>>>(P, A, tm);
+        mode == kModeForward ? launch_one<M, MR0, MR1, float, kModeForward>(P, A, tm, grid, st)
+                             : launch_one<M, MR0, MR1, float, kModeFull>(P, A, tm, grid, st);
 }
 
 }  // namespace dhk
@@ -474,7 +516,7 @@ static void launch(const Plan& P, const FusedArgs& A, const CUtensorMap& tm, int
 namespace dh {
 
 static int g_sm_count[64] = {0};
-static int g_bps[64][6] = {};   // resident blocks per SM per (field size, pixel type)
+static int g_bps[64][9] = {};   // resident blocks per SM per (field size, pixel type or inverse mode)
 static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
 bool use_fused(const dhk::Plan& P) {
@@ -502,34 +544,39 @@ cudaError_t fused_init() {
     return dhk::set_attr<64, 8, 8>();
 }
 
-int launch_fused_path(Handle* H, const dhk::Plan& P, const void* frames, int dtype, int batch, void* fields,
-                      void* coefs, cudaStream_t st, dhk::StageTimer* tm) {
+int launch_fused(Handle* H, const dhk::Plan& P, const void* frames, int dtype, int total, int frame0, int count,
+                 int mode, const float2* win_in, float2* win_out, void* fields, void* coefs, cudaStream_t st,
+                 dhk::StageTimer* tm) {
     int dev = H->device;
     if (dev < 0 || dev >= 64) return fail(DH_ERROR_ERROR, "device index out of range");
+    if (count < 1) return DH_SUCCESS;
     if (!g_sm_count[dev]) {
         int n = 0;
         cudaError_t e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return cuda_fail(e, "device attribute");
         g_sm_count[dev] = n;
     }
-    if (!g_encode) return fail(DH_ERROR_ERROR, "tensor-map encoder unavailable");
     const int esz = dtype == DH_DTYPE_U16 ? 2 : 4;
     const int align = 16 / esz;
-    // frames as a 3-D tensor [batch][height][width]; one box = the window rows plus alignment slack
     CUtensorMap tmap;
-    const cuuint64_t gdim[3] = {(cuuint64_t)P.width, (cuuint64_t)P.height, (cuuint64_t)batch};
-    const cuuint64_t gstride[2] = {(cuuint64_t)P.width * esz, (cuuint64_t)P.width * P.height * esz};
-    const cuuint32_t box[3] = {(cuuint32_t)(dhk::kFN + align), (cuuint32_t)dhk::kFRows, 1};
-    const cuuint32_t estride[3] = {1, 1, 1};
-    CUresult cr = g_encode(&tmap, dtype == DH_DTYPE_U16 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
-                           const_cast<void*>(frames), gdim, gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (cr != CUDA_SUCCESS) return fail(DH_ERROR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)cr) + ")");
+    std::memset(&tmap, 0, sizeof tmap);   // unused by the inverse-only mode, which reads no frames
+    if (mode != dhk::kModeInverse) {
+        if (!g_encode) return fail(DH_ERROR_ERROR, "tensor-map encoder unavailable");
+        // frames as a 3-D tensor [total][height][width]; one box = the window rows plus alignment slack
+        const cuuint64_t gdim[3] = {(cuuint64_t)P.width, (cuuint64_t)P.height, (cuuint64_t)total};
+        const cuuint64_t gstride[2] = {(cuuint64_t)P.width * esz, (cuuint64_t)P.width * P.height * esz};
+        const cuuint32_t box[3] = {(cuuint32_t)(dhk::kFN + align), (cuuint32_t)dhk::kFRows, 1};
+        const cuuint32_t estride[3] = {1, 1, 1};
+        CUresult cr = g_encode(&tmap, dtype == DH_DTYPE_U16 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32,
+                               3, const_cast<void*>(frames), gdim, gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (cr != CUDA_SUCCESS) return fail(DH_ERROR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)cr) + ")");
+    }
     dhk::FusedArgs A;
     A.src = frames;
-    A.frame0 = 0;
-    A.count = batch;
+    A.frame0 = frame0;
+    A.count = count;
     for (int p = 0; p < DH_MAX_POLS; ++p) {
         const int ox = p < P.pols ? P.pol[p].ox : 0;
         A.x0[p] = (ox / align) * align;          // window origins are >= 0
@@ -537,27 +584,34 @@ int launch_fused_path(Handle* H, const dhk::Plan& P, const void* frames, int dty
     }
     A.fields = (float2*)fields;
     A.coefs = (float2*)coefs;
+    A.win_out = win_out;
+    A.win_in = win_in;
     // a persistent grid of every resident block; each block serves one polarisation, so the grid is a multiple
     // of the polarisation count
-    const int slot = (P.m == 32 ? 0 : P.m == 48 ? 1 : 2) * 2 + (dtype == DH_DTYPE_U16 ? 0 : 1);
+    const int slot = (P.m == 32 ? 0 : P.m == 48 ? 1 : 2) * 3 + (mode == dhk::kModeInverse ? 2 : dtype == DH_DTYPE_U16 ? 0 : 1);
     if (!g_bps[dev][slot]) {
-        g_bps[dev][slot] = P.m == 32   ? dhk::blocks_per_sm<32, 8, 4>(dtype)
-                           : P.m == 48 ? dhk::blocks_per_sm<48, 3, 16>(dtype)
-                                       : dhk::blocks_per_sm<64, 8, 8>(dtype);
+        g_bps[dev][slot] = P.m == 32   ? dhk::blocks_per_sm<32, 8, 4>(dtype, mode)
+                           : P.m == 48 ? dhk::blocks_per_sm<48, 3, 16>(dtype, mode)
+                                       : dhk::blocks_per_sm<64, 8, 8>(dtype, mode);
     }
     const int resident = g_sm_count[dev] * g_bps[dev][slot];
-    const long long per_pol = std::min<long long>(batch, std::max(1, resident / P.pols));
+    const long long per_pol = std::min<long long>(count, std::max(1, resident / P.pols));
     const int grid = (int)per_pol * P.pols;
     if (tm) tm->start(st);
     switch (P.m) {
-        case 32: dhk::launch<32, 8, 4>(P, A, tmap, dtype, grid, st); break;
-        case 48: dhk::launch<48, 3, 16>(P, A, tmap, dtype, grid, st); break;
-        default: dhk::launch<64, 8, 8>(P, A, tmap, dtype, grid, st); break;
+        case 32: dhk::launch<32, 8, 4>(P, A, tmap, dtype, mode, grid, st); break;
+        case 48: dhk::launch<48, 3, 16>(P, A, tmap, dtype, mode, grid, st); break;
+        default: dhk::launch<64, 8, 8>(P, A, tmap, dtype, mode, grid, st); break;
     }
-    if (tm) tm->stop(st, "k_fused128");
+    if (tm) tm->stop(st, mode == dhk::kModeForward ? "k_fused128_fwd" : mode == dhk::kModeInverse ? "k_fused128_inv" : "k_fused128");
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "fused launch");
     return DH_SUCCESS;
+}
+
+int launch_fused_path(Handle* H, const dhk::Plan& P, const void* frames, int dtype, int batch, void* fields,
+                      void* coefs, cudaStream_t st, dhk::StageTimer* tm) {
+    return launch_fused(H, P, frames, dtype, batch, 0, batch, dhk::kModeFull, nullptr, nullptr, fields, coefs, st, tm);
 }
 
 }  // namespace dh

@@ -10,6 +10,11 @@ namespace dhk {
 
 constexpr int kMaxRadices = 6;
 
+// What one launch of the fused 128 x 128 kernel runs: the whole path, only the forward part (the masked window
+// written to memory), or only the inverse part (the window read from memory).  Batch averaging combines the
+// two split modes around the averaging kernels.
+constexpr int kModeFull = 0, kModeForward = 1, kModeInverse = 2;
+
 // Device tables of one polarisation (all pointers into the plan's device blob).
 struct PolDev {
     int ox, oy;              // window origin in the frame

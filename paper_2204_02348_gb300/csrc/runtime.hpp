@@ -83,6 +83,12 @@ bool fused_frames_ok(const dhk::Plan& P, const void* frames, int dtype);
 cudaError_t fused_init();
 int launch_fused_path(Handle* H, const dhk::Plan& P, const void* frames, int dtype, int batch, void* fields,
                       void* coefs, cudaStream_t st, dhk::StageTimer* timer);
+// The fused kernel in one of its modes (0 whole path, 1 forward only: windows to win_out [count][pol][M][M],
+// 2 inverse only: windows from win_in) over frames [frame0, frame0 + count) of an array of `total` frames;
+// outputs and windows are indexed from frame0 (outputs) or 0 (windows).
+int launch_fused(Handle* H, const dhk::Plan& P, const void* frames, int dtype, int total, int frame0, int count,
+                 int mode, const float2* win_in, float2* win_out, void* fields, void* coefs, cudaStream_t st,
+                 dhk::StageTimer* timer);
 
 // HG coefficient bytes per frame that an output-basis transform needs as scratch (0 for the HG basis).
 size_t basis_scratch_bytes(const dhk::Plan& P);
