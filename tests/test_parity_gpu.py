@@ -371,3 +371,42 @@ def test_fused_instantiations_against_oracle(m, dtype):
     _check(s, d["frames"], out)
     # the same frames through the generic path (window output forces it) agree as well
     _check(s, d["frames"], run_library(s, d["frames"], window=True))
+
+
+# ----------------------------------------------------------------------------- full-size configurations, sampled
+
+
+def _tiled(setup, count, distinct, seed):
+    """count frames cycling over `distinct` seeded frames (the work per frame is the same; generating every
+    frame of the large configurations would dominate the test)."""
+    d = syn.make_frames(setup, distinct, seed=seed)
+    idx = np.arange(count) % distinct
+    return d["frames"], np.ascontiguousarray(d["frames"][idx])
+
+
+@pytest.mark.parametrize("precision,coef_tol", [(0, COEF_TOL), (1, SPLIT_COEF_TOL)])
+def test_full_size_precision_sampled(precision, coef_tol):
+    """The precision configuration at full size (1024 frames of 640x512, two 256x256 windows, 120 modes) in
+    one call, as the bench runs it; sampled frames against the oracle."""
+    s = syn.setup_precision()
+    distinct, frames = _tiled(s, 1024, 16, seed=180)
+    out = run_library(s, frames, precision=precision)
+    assert np.all(np.isfinite(out["fields"])) and np.all(np.isfinite(out["coefs"]))
+    idx = [0, 17, 511, 1023]
+    f_ref, c_ref = orc.process_batch(distinct[[i % 16 for i in idx]], s)
+    assert rel_l2(out["fields"][idx], f_ref).max() <= FIELD_TOL
+    assert rel_l2(out["coefs"][idx], c_ref).max() <= coef_tol
+
+
+def test_full_size_large_scoring_sampled():
+    """The large scoring configuration at full size (2000 frames of 1280x1024, two 512x512 windows, 210 modes,
+    64 candidates, split-BF16) in one call; sampled (frame, candidate) powers against the oracle."""
+    s = syn.setup_large_batch()
+    distinct, frames = _tiled(s, 2000, 8, seed=181)
+    cand = syn.candidate_settings(s, 64)
+    got = _score(s, frames, cand, precision=1)
+    assert got.shape == (2000, 64) and np.all(np.isfinite(got))
+    for b, k in [(0, 0), (1001, 37), (1999, 63)]:
+        ref = orc.score_settings(distinct[b % 8][None], s, cand["tilt_deg"][k:k + 1], cand["defocus"][k:k + 1],
+                                 cand["waist"][k:k + 1])[0, 0]
+        assert abs(got[b, k] - ref) / ref <= 2 * SPLIT_COEF_TOL, (b, k, got[b, k], ref)
