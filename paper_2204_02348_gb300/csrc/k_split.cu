@@ -68,6 +68,83 @@ __global__ void __launch_bounds__(kThreads, 2) k_ypass(const __grid_constant__ P
     }
 }
 
+// k_ypass for the power-of-two windows, with the host plan's radix sequence fixed at compile time (128: 16 x 8,
+// 256: 16 x 16, 512: 8 x 8 x 8, 1024: 16 x 8 x 8): no runtime radix dispatch, twiddles staged in shared
+// memory, 2^LOGC column pairs per block.  Same inputs, outputs and arithmetic order as k_ypass.
+template <typename T, int N, int R0, int R1, int R2, int LOGC>
+__global__ void __launch_bounds__(kThreads, 2) k_ypass_s(const __grid_constant__ Plan P, const __grid_constant__ Batch B) {
+    extern __shared__ float2 smem[];   // [N][C] tile, then the twiddles W_N^k
+    constexpr int C = 1 << LOGC, half = N / 2;
+    static_assert(R0 * R1 * R2 == N, "the radices multiply to N");
+    float2* tw = smem + N * C;
+    const int tid = threadIdx.x;
+    const int M = P.m;
+    const int pol = blockIdx.y;
+    const PolDev& pd = P.pol[pol];
+    const int x0 = blockIdx.x * C;
+    for (int i = tid; i < N; i += kThreads) tw[i] = P.tw_fwd_n[i];
+    for (int fb = blockIdx.z; fb < B.count; fb += gridDim.z) {
+        const int f = B.frame0 + fb;
+        const T* fr = (const T*)B.src + (size_t)f * P.width * P.height;
+        for (int idx = tid; idx < N * C; idx += kThreads) {
+            const int y = idx >> LOGC, c = idx & (C - 1);
+            const T* row = fr + (size_t)(pd.oy + y) * P.width + pd.ox + x0 + c;
+            float2 v = make_float2(to_f(row[0]), to_f(row[half]));
+            if (pd.cal) {
+                const float* k = pd.cal + (size_t)y * N + x0 + c;
+                v.x *= __ldg(k);
+                v.y *= __ldg(k + half);
+            }
+            smem[idx] = v;
+        }
+        __syncthreads();
+        spass<R0, false, false, N, N, C, C, 1, kThreads>(smem, tw, tid);
+        __syncthreads();
+        spass<R1, false, false, N, N / R0, C, C, 1, kThreads>(smem, tw, tid);
+        __syncthreads();
+        if constexpr (R2 > 1) {
+            spass<R2, false, false, N, N / (R0 * R1), C, C, 1, kThreads>(smem, tw, tid);
+            __syncthreads();
+        }
+        float2* r1 = B.r1 + (size_t)(fb * P.pols + pol) * M * N;
+        for (int idx = tid; idx < M * C; idx += kThreads) {
+            const int q = idx >> LOGC, c = idx & (C - 1);
+            int k = (pd.kly + q) % N;
+            if (k < 0) k += N;
+            const int km = (N - k) & (N - 1);
+            const float2 za = smem[P.pos_n[k] * C + c];
+            const float2 zb = smem[P.pos_n[km] * C + c];
+            r1[(size_t)q * N + x0 + c] = make_float2(0.5f * (za.x + zb.x), 0.5f * (za.y - zb.y));
+            r1[(size_t)q * N + x0 + c + half] = make_float2(0.5f * (za.y + zb.y), 0.5f * (zb.x - za.x));
+        }
+        __syncthreads();
+    }
+}
+
+template <typename T, int N, int R0, int R1, int R2, int LOGC>
+static void launch_ys(const Plan& P, const Batch& B, int zf, cudaStream_t st) {
+    constexpr int C = 1 << LOGC;
+    dim3 g((N / 2) / C, P.pols, zf);
+    const size_t sm = ((size_t)N * C + N) * sizeof(float2);
+    k_ypass_s<T, N, R0, R1, R2, LOGC><<<g, kThreads, sm, st>>>(P, B);
+}
+
+template <typename T>
+static bool launch_ypass_static(const Plan& P, const Batch& B, int zf, cudaStream_t st) {
+    // only for the host's radix plans of these sizes
+    auto is = [&](int a, int b, int c) {
+        const int n = c > 1 ? 3 : 2;
+        return P.nrad_n == n && P.rad_n[0] == a && P.rad_n[1] == b && (n == 2 || P.rad_n[2] == c);
+    };
+    switch (P.n) {
+        case 128: if (!is(16, 8, 1)) return false; launch_ys<T, 128, 16, 8, 1, 5>(P, B, zf, st); return true;
+        case 256: if (!is(16, 16, 1)) return false; launch_ys<T, 256, 16, 16, 1, 5>(P, B, zf, st); return true;
+        case 512: if (!is(8, 8, 8)) return false; launch_ys<T, 512, 8, 8, 8, 4>(P, B, zf, st); return true;
+        case 1024: if (!is(16, 8, 8)) return false; launch_ys<T, 1024, 16, 8, 8, 3>(P, B, zf, st); return true;
+        default: return false;
+    }
+}
+
 __global__ void __launch_bounds__(kThreads, 2) k_xpass(const __grid_constant__ Plan P, const __grid_constant__ Batch B,
                                                     int logr, int logn) {
     extern __shared__ float2 smem[];
@@ -221,6 +298,14 @@ cudaError_t split_init() {
     if ((e = cudaFuncSetAttribute(k_ypass<uint16_t>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem))) return e;
     if ((e = cudaFuncSetAttribute(k_ypass<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem))) return e;
     if ((e = cudaFuncSetAttribute(k_xpass, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem))) return e;
+#define DH_YS_ATTR(T, N, A, B2, C2, L)                                                                            \
+    if ((e = cudaFuncSetAttribute(k_ypass_s<T, N, A, B2, C2, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem))) \
+        return e;
+    DH_YS_ATTR(uint16_t, 128, 16, 8, 1, 5) DH_YS_ATTR(float, 128, 16, 8, 1, 5)
+    DH_YS_ATTR(uint16_t, 256, 16, 16, 1, 5) DH_YS_ATTR(float, 256, 16, 16, 1, 5)
+    DH_YS_ATTR(uint16_t, 512, 8, 8, 8, 4) DH_YS_ATTR(float, 512, 8, 8, 8, 4)
+    DH_YS_ATTR(uint16_t, 1024, 16, 8, 8, 3) DH_YS_ATTR(float, 1024, 16, 8, 8, 3)
+#undef DH_YS_ATTR
     if ((e = cudaFuncSetAttribute(k_yinv, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem))) return e;
     return cudaSuccess;
 }
@@ -241,10 +326,14 @@ cudaError_t launch_forward(const Plan& P, const Batch& B, cudaStream_t st, Stage
     dim3 g1((N / 2) / C, P.pols, zf);
     const size_t sm1 = (size_t)N * C * sizeof(float2);
     if (tm) tm->start(st);
-    if (B.dtype == DH_DTYPE_U16)
-        k_ypass<uint16_t><<<g1, kThreads, sm1, st>>>(P, B, logc);
-    else
-        k_ypass<float><<<g1, kThreads, sm1, st>>>(P, B, logc);
+    const bool done = B.dtype == DH_DTYPE_U16 ? launch_ypass_static<uint16_t>(P, B, zf, st)
+                                              : launch_ypass_static<float>(P, B, zf, st);
+    if (!done) {
+        if (B.dtype == DH_DTYPE_U16)
+            k_ypass<uint16_t><<<g1, kThreads, sm1, st>>>(P, B, logc);
+        else
+            k_ypass<float><<<g1, kThreads, sm1, st>>>(P, B, logc);
+    }
     if (tm) tm->stop(st, "k_ypass");
     // k_xpass: R box rows per block
     const int logr = (N >= 512) ? 4 : 5;
@@ -284,10 +373,14 @@ cudaError_t launch_ypass(const Plan& P, const Batch& B, cudaStream_t st, StageTi
     dim3 g1((N / 2) / C, P.pols, zf);
     const size_t sm1 = (size_t)N * C * sizeof(float2);
     if (tm) tm->start(st);
-    if (B.dtype == DH_DTYPE_U16)
-        k_ypass<uint16_t><<<g1, kThreads, sm1, st>>>(P, B, logc);
-    else
-        k_ypass<float><<<g1, kThreads, sm1, st>>>(P, B, logc);
+    const bool done = B.dtype == DH_DTYPE_U16 ? launch_ypass_static<uint16_t>(P, B, zf, st)
+                                              : launch_ypass_static<float>(P, B, zf, st);
+    if (!done) {
+        if (B.dtype == DH_DTYPE_U16)
+            k_ypass<uint16_t><<<g1, kThreads, sm1, st>>>(P, B, logc);
+        else
+            k_ypass<float><<<g1, kThreads, sm1, st>>>(P, B, logc);
+    }
     if (tm) tm->stop(st, "k_ypass");
     return cudaGetLastError();
 }
