@@ -203,6 +203,98 @@ __global__ void __launch_bounds__(kThreads, 2) k_xpass(const __grid_constant__ P
     }
 }
 
+// k_xpass with the x transform's radix sequence fixed at compile time (the same plans as k_ypass_s) and its
+// twiddles in shared memory; the M-point inverse keeps the runtime plan.  Same results as k_xpass.
+template <int N, int R0, int R1, int R2, int LOGR>
+__global__ void __launch_bounds__(kThreads, 2) k_xpass_s(const __grid_constant__ Plan P, const __grid_constant__ Batch B) {
+    extern __shared__ float2 smem[];
+    const int tid = threadIdx.x, nthr = blockDim.x;
+    constexpr int R = 1 << LOGR, es = R + 1, logr = LOGR, logn = (N == 128 ? 7 : N == 256 ? 8 : N == 512 ? 9 : 10);
+    static_assert(R0 * R1 * R2 == N && (1 << logn) == N, "the radices multiply to N");
+    const int M = P.m;
+    float2* bufN = smem;
+    float2* bufM = smem + (size_t)N * es;
+    float2* twN = bufM + (size_t)M * es;
+    for (int i = tid; i < N; i += kThreads) twN[i] = P.tw_fwd_n[i];
+    const int pol = blockIdx.y;
+    const PolDev& pd = P.pol[pol];
+    const int q0 = blockIdx.x * R;
+    for (int fb = blockIdx.z; fb < B.count; fb += gridDim.z) {
+        const int f = B.frame0 + fb;
+        const float2* r1 = B.r1 + (size_t)(fb * P.pols + pol) * M * N;
+        // eight independent loads in flight per thread before their shared-memory stores
+        for (int i0 = tid; i0 < R * N; i0 += 8 * nthr) {
+            float2 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int idx = i0 + u * nthr;
+                const int row = idx >> logn, x = idx & (N - 1);
+                const int q = q0 + row;
+                v[u] = (idx < R * N && q < M) ? r1[(size_t)q * N + x] : make_float2(0.f, 0.f);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int idx = i0 + u * nthr;
+                if (idx < R * N) bufN[(idx & (N - 1)) * es + (idx >> logn)] = v[u];
+            }
+        }
+        __syncthreads();
+        spass<R0, false, false, N, N, R, es, 1, kThreads>(bufN, twN, tid);
+        __syncthreads();
+        spass<R1, false, false, N, N / R0, R, es, 1, kThreads>(bufN, twN, tid);
+        __syncthreads();
+        if constexpr (R2 > 1) {
+            spass<R2, false, false, N, N / (R0 * R1), R, es, 1, kThreads>(bufN, twN, tid);
+            __syncthreads();
+        }
+        for (int idx = tid; idx < R * M; idx += nthr) {
+            const int row = idx & (R - 1), pp = idx >> logr;
+            const int q = q0 + row;
+            float2 v = make_float2(0.f, 0.f);
+            if (q < M) {
+                if (pp >= pd.mask_lo[q] && pp <= pd.mask_hi[q]) {
+                    int kx = (pd.klx + pp) % N;
+                    if (kx < 0) kx += N;
+                    v = cmul(cmul(bufN[P.pos_n[kx] * es + row], pd.phase_x[pp]), pd.phase_y[q]);
+                }
+                if (B.window) B.window[((size_t)(f * P.pols + pol) * M + q) * M + pp] = v;
+            }
+            bufM[P.pos_m[pp] * es + row] = v;
+        }
+        __syncthreads();
+        fft_run<true>(bufM, M, P.rad_m, P.nrad_m, logr, es, P.tw_inv_m, tid, nthr);
+        float2* g = B.g + (size_t)(fb * P.pols + pol) * M * M;
+        for (int idx = tid; idx < R * M; idx += nthr) {
+            const int row = idx / M, i = idx - row * M;
+            const int q = q0 + row;
+            if (q < M) g[(size_t)q * M + i] = bufM[i * es + row];
+        }
+        __syncthreads();
+    }
+}
+
+template <int N, int R0, int R1, int R2, int LOGR>
+static void launch_xs(const Plan& P, const Batch& B, int zf, cudaStream_t st) {
+    constexpr int R = 1 << LOGR;
+    dim3 g((P.m + R - 1) / R, P.pols, zf);
+    const size_t sm = ((size_t)(N + P.m) * (R + 1) + N) * sizeof(float2);
+    k_xpass_s<N, R0, R1, R2, LOGR><<<g, kThreads, sm, st>>>(P, B);
+}
+
+static bool launch_xpass_static(const Plan& P, const Batch& B, int zf, cudaStream_t st) {
+    auto is = [&](int a, int b, int c) {
+        const int n = c > 1 ? 3 : 2;
+        return P.nrad_n == n && P.rad_n[0] == a && P.rad_n[1] == b && (n == 2 || P.rad_n[2] == c);
+    };
+    switch (P.n) {
+        case 128: if (!is(16, 8, 1)) return false; launch_xs<128, 16, 8, 1, 5>(P, B, zf, st); return true;
+        case 256: if (!is(16, 16, 1)) return false; launch_xs<256, 16, 16, 1, 5>(P, B, zf, st); return true;
+        case 512: if (!is(8, 8, 8)) return false; launch_xs<512, 8, 8, 8, 4>(P, B, zf, st); return true;
+        case 1024: if (!is(16, 8, 8)) return false; launch_xs<1024, 16, 8, 8, 4>(P, B, zf, st); return true;
+        default: return false;
+    }
+}
+
 __global__ void __launch_bounds__(kThreads, 2) k_yinv(const __grid_constant__ Plan P, const __grid_constant__ Batch B) {
     extern __shared__ float2 smem[];
     const int tid = threadIdx.x, nthr = blockDim.x;
@@ -306,6 +398,10 @@ cudaError_t split_init() {
     DH_YS_ATTR(uint16_t, 512, 8, 8, 8, 4) DH_YS_ATTR(float, 512, 8, 8, 8, 4)
     DH_YS_ATTR(uint16_t, 1024, 16, 8, 8, 3) DH_YS_ATTR(float, 1024, 16, 8, 8, 3)
 #undef DH_YS_ATTR
+    if ((e = cudaFuncSetAttribute(k_xpass_s<128, 16, 8, 1, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem))) return e;
+    if ((e = cudaFuncSetAttribute(k_xpass_s<256, 16, 16, 1, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem))) return e;
+    if ((e = cudaFuncSetAttribute(k_xpass_s<512, 8, 8, 8, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem))) return e;
+    if ((e = cudaFuncSetAttribute(k_xpass_s<1024, 16, 8, 8, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem))) return e;
     if ((e = cudaFuncSetAttribute(k_yinv, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem))) return e;
     return cudaSuccess;
 }
@@ -341,7 +437,7 @@ cudaError_t launch_forward(const Plan& P, const Batch& B, cudaStream_t st, Stage
     dim3 g2((M + R - 1) / R, P.pols, zf);
     const size_t sm2 = (size_t)(N + M) * (R + 1) * sizeof(float2);
     if (tm) tm->start(st);
-    k_xpass<<<g2, kThreads, sm2, st>>>(P, B, logr, ilog2(N));
+    if (!launch_xpass_static(P, B, zf, st)) k_xpass<<<g2, kThreads, sm2, st>>>(P, B, logr, ilog2(N));
     if (tm) tm->stop(st, "k_xpass");
     return cudaGetLastError();
 }
