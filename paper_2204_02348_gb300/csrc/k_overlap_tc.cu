@@ -86,6 +86,9 @@ __host__ __device__ inline TcLayout tc_layout(int M, int NP) {
 
 }  // namespace
 
+// R0 R1 R2: the host plan's radices of M fixed at compile time (inverse passes run last radix first), or
+// R0 = 0 for the runtime plan.
+template <int R0, int R1, int R2>
 __global__ void __launch_bounds__(kTcThreads, 2) k_yinv_tc(const __grid_constant__ Plan P, const __grid_constant__ Batch B) {
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ __align__(8) uint64_t mbar;
@@ -138,7 +141,19 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_yinv_tc(const __grid_constant
                 buf[P.pos_m[q] * kTcCols + i] = (i0 + i < M) ? g[(size_t)q * M + i0 + i] : make_float2(0.f, 0.f);
             }
             __syncthreads();
-            fft_run<true>(buf, M, P.rad_m, P.nrad_m, 6, kTcCols, P.tw_inv_m, tid, kTcThreads);
+            if constexpr (R0 == 0) {
+                fft_run<true>(buf, M, P.rad_m, P.nrad_m, 6, kTcCols, P.tw_inv_m, tid, kTcThreads);
+            } else {
+                constexpr int MM = R0 * R1 * R2;
+                if constexpr (R2 > 1) {
+                    spass<R2, true, true, MM, R2, kTcCols, kTcCols, 1, kTcThreads>(buf, P.tw_inv_m, tid);
+                    __syncthreads();
+                }
+                spass<R1, true, true, MM, R1 * R2, kTcCols, kTcCols, 1, kTcThreads>(buf, P.tw_inv_m, tid);
+                __syncthreads();
+                spass<R0, true, true, MM, MM, kTcCols, kTcCols, 1, kTcThreads>(buf, P.tw_inv_m, tid);
+                __syncthreads();
+            }
             for (int idx = tid; idx < M * kTcCols; idx += kTcThreads) {
                 const int j = idx >> 6, i = idx & (kTcCols - 1);
                 if (i0 + i < M) {
@@ -233,13 +248,29 @@ bool tc_supported(const Plan& P) {
 }
 
 cudaError_t tc_init() {
-    return cudaFuncSetAttribute(k_yinv_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024 - 1024);
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(k_yinv_tc<0, 0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024 - 1024)))
+        return e;
+    if ((e = cudaFuncSetAttribute(k_yinv_tc<8, 4, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024 - 1024)))
+        return e;
+    return cudaFuncSetAttribute(k_yinv_tc<16, 11, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024 - 1024);
 }
 
 cudaError_t launch_yinv_tc(const Plan& P, const Batch& B, cudaStream_t st) {
     const TcLayout L = tc_layout(P.m, P.tc_np);
     dim3 grid(P.pols, B.count < 65535 ? B.count : 65535);
-    k_yinv_tc<<<grid, kTcThreads, L.bytes, st>>>(P, B);
+    // the field sizes of the precision (96 = 8 4 3) and large (176 = 16 11) configurations run with their
+    // radix plan fixed at compile time
+    auto plan_is = [&](int a, int b, int c) {
+        const int n = c > 1 ? 3 : 2;
+        return P.nrad_m == n && P.rad_m[0] == a && P.rad_m[1] == b && (n == 2 || P.rad_m[2] == c);
+    };
+    if (P.m == 96 && plan_is(8, 4, 3))
+        k_yinv_tc<8, 4, 3><<<grid, kTcThreads, L.bytes, st>>>(P, B);
+    else if (P.m == 176 && plan_is(16, 11, 1))
+        k_yinv_tc<16, 11, 1><<<grid, kTcThreads, L.bytes, st>>>(P, B);
+    else
+        k_yinv_tc<0, 0, 0><<<grid, kTcThreads, L.bytes, st>>>(P, B);
     return cudaGetLastError();
 }
 
