@@ -250,4 +250,21 @@ __device__ __forceinline__ void spass(float2* buf, const float2* tw, int tid) {
     }
 }
 
+
+// Inverse (DIT) transform with the radix plan fixed at compile time: R0 R1 R2 in the host plan's DIF order
+// (R2 = 1 for a two-radix plan), passes run last radix first, as fft_run<true> does at run time.  NB
+// transforms, element e of transform b at buf[e * ES + b].  Ends with a barrier.
+template <int R0, int R1, int R2, int NB, int ES, int NTHR>
+__device__ __forceinline__ void ifft_static(float2* buf, const float2* tw, int tid) {
+    constexpr int MM = R0 * R1 * R2;
+    if constexpr (R2 > 1) {
+        spass<R2, true, true, MM, R2, NB, ES, 1, NTHR>(buf, tw, tid);
+        __syncthreads();
+    }
+    spass<R1, true, true, MM, R1 * R2, NB, ES, 1, NTHR>(buf, tw, tid);
+    __syncthreads();
+    spass<R0, true, true, MM, MM, NB, ES, 1, NTHR>(buf, tw, tid);
+    __syncthreads();
+}
+
 }  // namespace dhk

@@ -144,15 +144,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_yinv_tc(const __grid_constant
             if constexpr (R0 == 0) {
                 fft_run<true>(buf, M, P.rad_m, P.nrad_m, 6, kTcCols, P.tw_inv_m, tid, kTcThreads);
             } else {
-                constexpr int MM = R0 * R1 * R2;
-                if constexpr (R2 > 1) {
-                    spass<R2, true, true, MM, R2, kTcCols, kTcCols, 1, kTcThreads>(buf, P.tw_inv_m, tid);
-                    __syncthreads();
-                }
-                spass<R1, true, true, MM, R1 * R2, kTcCols, kTcCols, 1, kTcThreads>(buf, P.tw_inv_m, tid);
-                __syncthreads();
-                spass<R0, true, true, MM, MM, kTcCols, kTcCols, 1, kTcThreads>(buf, P.tw_inv_m, tid);
-                __syncthreads();
+                ifft_static<R0, R1, R2, kTcCols, kTcCols, kTcThreads>(buf, P.tw_inv_m, tid);
             }
             for (int idx = tid; idx < M * kTcCols; idx += kTcThreads) {
                 const int j = idx >> 6, i = idx & (kTcCols - 1);

@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_xpass(const __grid_constant__ P
 
 // k_xpass with the x transform's radix sequence fixed at compile time (the same plans as k_ypass_s) and its
 // twiddles in shared memory; the M-point inverse keeps the runtime plan.  Same results as k_xpass.
-template <int N, int R0, int R1, int R2, int LOGR>
+template <int N, int R0, int R1, int R2, int LOGR, int MR0, int MR1, int MR2>
 __global__ void __launch_bounds__(kThreads, 2) k_xpass_s(const __grid_constant__ Plan P, const __grid_constant__ Batch B) {
     extern __shared__ float2 smem[];
     const int tid = threadIdx.x, nthr = blockDim.x;
@@ -262,7 +262,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_xpass_s(const __grid_constant__
             bufM[P.pos_m[pp] * es + row] = v;
         }
         __syncthreads();
-        fft_run<true>(bufM, M, P.rad_m, P.nrad_m, logr, es, P.tw_inv_m, tid, nthr);
+        if constexpr (MR0 == 0)
+            fft_run<true>(bufM, M, P.rad_m, P.nrad_m, logr, es, P.tw_inv_m, tid, nthr);
+        else
+            ifft_static<MR0, MR1, MR2, R, es, kThreads>(bufM, P.tw_inv_m, tid);
         float2* g = B.g + (size_t)(fb * P.pols + pol) * M * M;
         for (int idx = tid; idx < R * M; idx += nthr) {
             const int row = idx / M, i = idx - row * M;
@@ -273,12 +276,31 @@ __global__ void __launch_bounds__(kThreads, 2) k_xpass_s(const __grid_constant__
     }
 }
 
+// Whether the host plan of M is the radix sequence (a, b, c) (c = 1: two radices).
+static bool m_plan_is(const Plan& P, int a, int b, int c) {
+    const int n = c > 1 ? 3 : 2;
+    return P.nrad_m == n && P.rad_m[0] == a && P.rad_m[1] == b && (n == 2 || P.rad_m[2] == c);
+}
+
 template <int N, int R0, int R1, int R2, int LOGR>
 static void launch_xs(const Plan& P, const Batch& B, int zf, cudaStream_t st) {
     constexpr int R = 1 << LOGR;
     dim3 g((P.m + R - 1) / R, P.pols, zf);
     const size_t sm = ((size_t)(N + P.m) * (R + 1) + N) * sizeof(float2);
-    k_xpass_s<N, R0, R1, R2, LOGR><<<g, kThreads, sm, st>>>(P, B);
+    // the precision (256: M = 96) and large (512: M = 176) configurations also fix the inverse plan
+    if constexpr (N == 256) {
+        if (P.m == 96 && m_plan_is(P, 8, 4, 3)) {
+            k_xpass_s<N, R0, R1, R2, LOGR, 8, 4, 3><<<g, kThreads, sm, st>>>(P, B);
+            return;
+        }
+    }
+    if constexpr (N == 512) {
+        if (P.m == 176 && m_plan_is(P, 16, 11, 1)) {
+            k_xpass_s<N, R0, R1, R2, LOGR, 16, 11, 1><<<g, kThreads, sm, st>>>(P, B);
+            return;
+        }
+    }
+    k_xpass_s<N, R0, R1, R2, LOGR, 0, 0, 0><<<g, kThreads, sm, st>>>(P, B);
 }
 
 static bool launch_xpass_static(const Plan& P, const Batch& B, int zf, cudaStream_t st) {
@@ -295,6 +317,8 @@ static bool launch_xpass_static(const Plan& P, const Batch& B, int zf, cudaStrea
     }
 }
 
+// MR0 MR1 MR2: the radix plan of M fixed at compile time, or MR0 = 0 for the runtime plan.
+template <int MR0, int MR1, int MR2>
 __global__ void __launch_bounds__(kThreads, 2) k_yinv(const __grid_constant__ Plan P, const __grid_constant__ Batch B) {
     extern __shared__ float2 smem[];
     const int tid = threadIdx.x, nthr = blockDim.x;
@@ -324,7 +348,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_yinv(const __grid_constant__ Pl
                 }
             }
             __syncthreads();
-            fft_run<true>(buf, M, P.rad_m, P.nrad_m, 5, kChunkI, P.tw_inv_m, tid, nthr);
+            if constexpr (MR0 == 0)
+                fft_run<true>(buf, M, P.rad_m, P.nrad_m, 5, kChunkI, P.tw_inv_m, tid, nthr);
+            else
+                ifft_static<MR0, MR1, MR2, kChunkI, kChunkI, kThreads>(buf, P.tw_inv_m, tid);
             for (int idx = tid; idx < M * kChunkI; idx += nthr) {
                 const int j = idx >> 5, i = idx & (kChunkI - 1);
                 if (i0 + i < M) {
@@ -398,11 +425,16 @@ cudaError_t split_init() {
     DH_YS_ATTR(uint16_t, 512, 8, 8, 8, 4) DH_YS_ATTR(float, 512, 8, 8, 8, 4)
     DH_YS_ATTR(uint16_t, 1024, 16, 8, 8, 3) DH_YS_ATTR(float, 1024, 16, 8, 8, 3)
 #undef DH_YS_ATTR
-    if ((e = cudaFuncSetAttribute(k_xpass_s<128, 16, 8, 1, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem))) return e;
-    if ((e = cudaFuncSetAttribute(k_xpass_s<256, 16, 16, 1, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem))) return e;
-    if ((e = cudaFuncSetAttribute(k_xpass_s<512, 8, 8, 8, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem))) return e;
-    if ((e = cudaFuncSetAttribute(k_xpass_s<1024, 16, 8, 8, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem))) return e;
-    if ((e = cudaFuncSetAttribute(k_yinv, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem))) return e;
+#define DH_XS_ATTR(...)                                                                                         \
+    if ((e = cudaFuncSetAttribute(k_xpass_s<__VA_ARGS__>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem))) \
+        return e;
+    DH_XS_ATTR(128, 16, 8, 1, 5, 0, 0, 0) DH_XS_ATTR(256, 16, 16, 1, 5, 0, 0, 0)
+    DH_XS_ATTR(512, 8, 8, 8, 4, 0, 0, 0) DH_XS_ATTR(1024, 16, 8, 8, 4, 0, 0, 0)
+    DH_XS_ATTR(256, 16, 16, 1, 5, 8, 4, 3) DH_XS_ATTR(512, 8, 8, 8, 4, 16, 11, 1)
+#undef DH_XS_ATTR
+    if ((e = cudaFuncSetAttribute(k_yinv<8, 4, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem))) return e;
+    if ((e = cudaFuncSetAttribute(k_yinv<16, 11, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem))) return e;
+    if ((e = cudaFuncSetAttribute(k_yinv<0, 0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem))) return e;
     return cudaSuccess;
 }
 
@@ -455,7 +487,12 @@ cudaError_t launch_last(const Plan& P, const Batch& B, cudaStream_t st, StageTim
         return cudaGetLastError();
     }
     if (tm) tm->start(st);
-    k_yinv<<<g3, kThreads, sm3, st>>>(P, B);
+    if (P.m == 96 && m_plan_is(P, 8, 4, 3))
+        k_yinv<8, 4, 3><<<g3, kThreads, sm3, st>>>(P, B);
+    else if (P.m == 176 && m_plan_is(P, 16, 11, 1))
+        k_yinv<16, 11, 1><<<g3, kThreads, sm3, st>>>(P, B);
+    else
+        k_yinv<0, 0, 0><<<g3, kThreads, sm3, st>>>(P, B);
     if (tm) tm->stop(st, "k_yinv");
     return cudaGetLastError();
 }
