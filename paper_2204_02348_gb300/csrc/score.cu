@@ -86,6 +86,9 @@ __global__ void __launch_bounds__(kSThreads, 2) k_xfwd(const __grid_constant__ P
 }
 
 // One candidate: gather its box from the superset, mask and phase it, x inverse transform.
+// MR0 MR1 MR2: the radix plan of M fixed at compile time (then 16 rows per block, logr = 4), or MR0 = 0 for
+// the runtime plan.
+template <int MR0, int MR1, int MR2>
 __global__ void __launch_bounds__(kSThreads, 2) k_xinv_sel(const __grid_constant__ Plan P, const __grid_constant__ Superset S,
                                                            const float2* __restrict__ xs, float2* __restrict__ g,
                                                            int count, int qoff0, int qoff1, int poff0, int poff1, int logr) {
@@ -122,7 +125,10 @@ __global__ void __launch_bounds__(kSThreads, 2) k_xinv_sel(const __grid_constant
             }
         }
         __syncthreads();
-        fft_run<true>(smem, M, P.rad_m, P.nrad_m, logr, es, P.tw_inv_m, tid, nthr);
+        if constexpr (MR0 == 0)
+            fft_run<true>(smem, M, P.rad_m, P.nrad_m, logr, es, P.tw_inv_m, tid, nthr);
+        else
+            ifft_static<MR0, MR1, MR2, 16, 17, kSThreads>(smem, P.tw_inv_m, tid);
         float2* dst = g + (size_t)(fb * P.pols + pol) * M * M;
         for (int idx = tid; idx < R * M; idx += nthr) {
             const int row = idx / M, i = idx - row * M;
@@ -136,7 +142,8 @@ __global__ void __launch_bounds__(kSThreads, 2) k_xinv_sel(const __grid_constant
 cudaError_t score_init() {
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_xfwd, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024))) return e;
-    return cudaFuncSetAttribute(k_xinv_sel, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if ((e = cudaFuncSetAttribute(k_xinv_sel<0, 0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024))) return e;
+    return cudaFuncSetAttribute(k_xinv_sel<16, 11, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
 }
 
 }  // namespace dhk
@@ -307,7 +314,12 @@ extern "C" int dh_score_settings(dh_handle h, const void* d_frames, int dtype, i
             }
             dim3 gi((M + R - 1) / R, pols, zf);
             if (tm) tm->start(st);
-            dhk::k_xinv_sel<<<gi, dhk::kSThreads, (size_t)M * (R + 1) * sizeof(float2), st>>>(Pc, S, xs, gbuf, n, qo[0], qo[1],
+            // the large configuration's field size (176 = 16 11) runs with its inverse plan fixed at compile time
+            if (M == 176 && R == 16 && Pc.nrad_m == 2 && Pc.rad_m[0] == 16 && Pc.rad_m[1] == 11)
+                dhk::k_xinv_sel<16, 11, 1><<<gi, dhk::kSThreads, (size_t)M * (R + 1) * sizeof(float2), st>>>(Pc, S, xs, gbuf, n, qo[0], qo[1],
+                                                                                              po[0], po[1], logr);
+            else
+                dhk::k_xinv_sel<0, 0, 0><<<gi, dhk::kSThreads, (size_t)M * (R + 1) * sizeof(float2), st>>>(Pc, S, xs, gbuf, n, qo[0], qo[1],
                                                                                               po[0], po[1], logr);
             if (tm) tm->stop(st, "k_xinv_sel");
             e = cudaGetLastError();
