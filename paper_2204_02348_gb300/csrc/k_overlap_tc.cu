@@ -136,9 +136,29 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_yinv_tc(const __grid_constant
         const float2* g = B.g + (size_t)(fb * P.pols + pol) * M * M;
         float2 acc = make_float2(0.f, 0.f);   // mode tid (modes <= 256)
         for (int i0 = 0; i0 < M; i0 += kTcCols) {
-            for (int idx = tid; idx < M * kTcCols; idx += kTcThreads) {
-                const int q = idx >> 6, i = idx & (kTcCols - 1);
-                buf[P.pos_m[q] * kTcCols + i] = (i0 + i < M) ? g[(size_t)q * M + i0 + i] : make_float2(0.f, 0.f);
+            if constexpr (R0 == 0 || R0 * R1 * R2 > 128) {
+                for (int idx = tid; idx < M * kTcCols; idx += kTcThreads) {
+                    const int q = idx >> 6, i = idx & (kTcCols - 1);
+                    buf[P.pos_m[q] * kTcCols + i] = (i0 + i < M) ? g[(size_t)q * M + i0 + i] : make_float2(0.f, 0.f);
+                }
+            } else {
+                // a small fixed plan leaves the registers for eight loads in flight per thread (at M = 176 the
+                // extra registers cost more than the loads gain)
+                constexpr int MM = R0 * R1 * R2;
+                for (int j0 = tid; j0 < MM * kTcCols; j0 += 8 * kTcThreads) {
+                    float2 v[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int idx = j0 + u * kTcThreads;
+                        const int q = idx >> 6, i = idx & (kTcCols - 1);
+                        v[u] = (idx < MM * kTcCols && i0 + i < MM) ? g[(size_t)q * MM + i0 + i] : make_float2(0.f, 0.f);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int idx = j0 + u * kTcThreads;
+                        if (idx < MM * kTcCols) buf[P.pos_m[idx >> 6] * kTcCols + (idx & (kTcCols - 1))] = v[u];
+                    }
+                }
             }
             __syncthreads();
             if constexpr (R0 == 0) {
