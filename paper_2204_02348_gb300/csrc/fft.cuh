@@ -236,12 +236,14 @@ __device__ __forceinline__ void spass(float2* buf, const float2* tw, int tid) {
         float2 v[R];
 #pragma unroll
         for (int r = 0; r < R; ++r) v[r] = buf[(base + r * S) * ES + b * BS];
-        if (DIT) {
+        // with S = 1 every j is 0 and the twiddles are exactly 1
+        constexpr bool TWID = S > 1;
+        if (DIT && TWID) {
 #pragma unroll
             for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[j * r * TW]);
         }
         dft<R, INV>(v, tw, L / R);
-        if (!DIT) {
+        if (!DIT && TWID) {
 #pragma unroll
             for (int r = 1; r < R; ++r) v[r] = cmul(v[r], tw[j * r * TW]);
         }

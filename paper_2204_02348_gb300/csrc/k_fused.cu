@@ -99,12 +99,14 @@ __device__ __forceinline__ float2 staged_pair(const T* row, int x) {
     return make_float2((float)row[x], (float)row[x + kFN / 2]);
 }
 
-// Write the separated spectra of columns x and x + N/2 at frequency k (if k is a box row).
+// Write the separated spectra of columns x and x + N/2 at frequency k (if k is a box row), times 2: the
+// factor 1/2 of the separation is carried by the y beam-centre phase (a power of two, so the rounding of every
+// step in between is unchanged).
 __device__ __forceinline__ void emit_pair(float2* r1, int pitch, int M, int kly, int x, int k, float2 zk, float2 zm) {
     const int q = (k - kly) & (kFN - 1);
     if (q < M) {
-        r1[x * pitch + q] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
-        r1[(x + kFN / 2) * pitch + q] = make_float2(0.5f * (zk.y + zm.y), 0.5f * (zm.x - zk.x));
+        r1[x * pitch + q] = make_float2(zk.x + zm.x, zk.y - zm.y);
+        r1[(x + kFN / 2) * pitch + q] = make_float2(zk.y + zm.y, zm.x - zk.x);
     }
 }
 
@@ -120,6 +122,8 @@ __global__ void __launch_bounds__(FusedShape<M, T>::NT, FusedShape<M, T>::MINB)
     static_assert(M == MR0 * MR1, "field size = product of the two radices");
     static_assert(NBLK % QB == 0, "row blocks split evenly into the partial-sum groups");
     static_assert(L::WB + QB * kFGMax * M <= L::BUF, "the partial sums fit behind the window");
+    // y contraction over mirrored rows: group 0 holds blocks 0 and MR0/2, group qb > 0 blocks qb and MR0 - qb
+    constexpr bool PAIRS = MR0 == 8 && QB == 4 && BPQ == 2 && MR1 % 2 == 0;
     static_assert(M % 8 == 0, "box rows below M come in whole radix-8 tasks");
     // 128-byte alignment: tensor-copy destination; no larger, so that two blocks fit an SM
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -150,7 +154,7 @@ __global__ void __launch_bounds__(FusedShape<M, T>::NT, FusedShape<M, T>::MINB)
         twM[i] = P.tw_inv_m[i];
         posM[i] = (i % MR0) * MR1 + i / MR0;   // position of index i after DIF passes of radix MR0 then MR1
         phx[i] = pd.phase_x[i];
-        phy[i] = pd.phase_y[i];
+        phy[i] = cscale(pd.phase_y[i], 0.5f);   // with the 1/2 of the real-spectra separation
         cx[i] = pd.corr_x[i];
         cy[i] = pd.corr_y[i];
         mlo[i] = pd.mask_lo[i];
@@ -284,7 +288,8 @@ __global__ void __launch_bounds__(FusedShape<M, T>::NT, FusedShape<M, T>::MINB)
 #pragma unroll
                     for (int r = 0; r < 8; ++r) {
                         const int p = (d + 16 * r - pd.klx) & (N - 1);
-                        keep[k][r] = (p < M && p >= lo && p <= hi) ? cmul(cmul(keep[k][r], phx[p]), py) : make_float2(0.f, 0.f);
+                        if (p < M)   // the same for the whole warp (d is)
+                            keep[k][r] = (p >= lo && p <= hi) ? cmul(cmul(keep[k][r], phx[p]), py) : make_float2(0.f, 0.f);
                     }
                 }
             }
@@ -340,9 +345,9 @@ __global__ void __launch_bounds__(FusedShape<M, T>::NT, FusedShape<M, T>::MINB)
         // ---------------------------------------------------------------- last y pass, correction, field, y overlap
         // The last DIF pass (span MR1, no twiddles) leaves output j = blk + MR0 r at position blk MR1 + r of
         // column i; it is corrected in registers, written to the field (coalesced along i) and contracted with
-        // u_n(y'_j) into the partial sums part[qb][n][i] over the BPQ row blocks of group qb.
+        // u_n(y'_j) into the partial sums part[qb][n][i] over the BPQ row blocks of group qb (with PAIRS, the
+        // blocks of a group hold each other's mirror rows M - j).
         float2* part = buf + L::WB;                // [QB][G][M], behind the window
-        float2* tsum = buf;                        // [G][M], over the consumed window
         const bool ov = A.coefs && G > 0;
         {
             float2* fld = A.fields ? A.fields + (size_t)(f * P.pols + pol) * M * M : nullptr;
@@ -352,7 +357,7 @@ __global__ void __launch_bounds__(FusedShape<M, T>::NT, FusedShape<M, T>::MINB)
                 float2 v[BPQ][MR1];
 #pragma unroll
                 for (int bb = 0; bb < BPQ; ++bb) {
-                    const int blk = qb * BPQ + bb;
+                    const int blk = PAIRS ? (qb == 0 ? bb * (MR0 / 2) : (bb == 0 ? qb : MR0 - qb)) : qb * BPQ + bb;
 #pragma unroll
                     for (int r = 0; r < MR1; ++r) v[bb][r] = buf[i * PITCH + blk * MR1 + r];
                     dft<MR1, true>(v[bb], twM, M / MR1);
@@ -364,31 +369,94 @@ __global__ void __launch_bounds__(FusedShape<M, T>::NT, FusedShape<M, T>::MINB)
                     }
                 }
                 if (ov) {
+                    if constexpr (PAIRS) {
+                        // rows j and M - j carry u_n(y'_{M-j}) = (-1)^n u_n(y'_j): the even modes contract the
+                        // sums E_j + E_{M-j}, the odd ones the differences, each with u_n(y'_j) (half the products)
+                        float2 sp[MR1 + 1], sm[MR1 + 1];
+                        int jr[MR1 + 1];
+                        if (qb == 0) {
+                            // block 0 (rows MR0 r) pairs r with MR1 - r; row 0 has no mirror and row M/2 is its own
+                            // (odd modes vanish there); block MR0/2 pairs r with MR1 - 1 - r
+                            int u = 0;
 #pragma unroll
-                    for (int n4 = 0; n4 < kFGMax; n4 += 4) {
-                        if (n4 < G) {
-                            float2 a[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f),
-                                           make_float2(0.f, 0.f)};
-#pragma unroll
-                            for (int bb = 0; bb < BPQ; ++bb) {
-#pragma unroll
-                                for (int r = 0; r < MR1; ++r) {
-                                    const int j = qb * BPQ + bb + MR0 * r;
-                                    const float4 u = *reinterpret_cast<const float4*>(hgy + j * kFGMax + n4);
-                                    const float2 e = v[bb][r];
-                                    a[0].x = fmaf(u.x, e.x, a[0].x);
-                                    a[0].y = fmaf(u.x, e.y, a[0].y);
-                                    a[1].x = fmaf(u.y, e.x, a[1].x);
-                                    a[1].y = fmaf(u.y, e.y, a[1].y);
-                                    a[2].x = fmaf(u.z, e.x, a[2].x);
-                                    a[2].y = fmaf(u.z, e.y, a[2].y);
-                                    a[3].x = fmaf(u.w, e.x, a[3].x);
-                                    a[3].y = fmaf(u.w, e.y, a[3].y);
-                                }
+                            for (int r = 1; r < MR1 / 2; ++r, ++u) {
+                                sp[u] = cadd(v[0][r], v[0][MR1 - r]);
+                                sm[u] = csub(v[0][r], v[0][MR1 - r]);
+                                jr[u] = MR0 * r;
                             }
+                            sp[u] = sm[u] = v[0][0];
+                            jr[u++] = 0;
+                            sp[u] = sm[u] = v[0][MR1 / 2];
+                            jr[u++] = M / 2;
 #pragma unroll
-                            for (int c = 0; c < 4; ++c)
-                                if (n4 + c < G) part[(qb * G + n4 + c) * M + i] = a[c];
+                            for (int r = 0; r < MR1 / 2; ++r, ++u) {
+                                sp[u] = cadd(v[1][r], v[1][MR1 - 1 - r]);
+                                sm[u] = csub(v[1][r], v[1][MR1 - 1 - r]);
+                                jr[u] = MR0 / 2 + MR0 * r;
+                            }
+                        } else {
+                            // blocks qb and MR0 - qb: row qb + MR0 r mirrors row (MR0 - qb) + MR0 (MR1 - 1 - r)
+#pragma unroll
+                            for (int r = 0; r < MR1; ++r) {
+                                sp[r] = cadd(v[0][r], v[1][MR1 - 1 - r]);
+                                sm[r] = csub(v[0][r], v[1][MR1 - 1 - r]);
+                                jr[r] = qb + MR0 * r;
+                            }
+                            sp[MR1] = sm[MR1] = make_float2(0.f, 0.f);
+                            jr[MR1] = 0;
+                        }
+                        const int nu = qb == 0 ? MR1 + 1 : MR1;
+#pragma unroll
+                        for (int n4 = 0; n4 < kFGMax; n4 += 4) {
+                            if (n4 < G) {
+                                float2 a[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f),
+                                               make_float2(0.f, 0.f)};
+#pragma unroll
+                                for (int u = 0; u < MR1 + 1; ++u) {
+                                    if (u < nu) {
+                                        const float4 w = *reinterpret_cast<const float4*>(hgy + jr[u] * kFGMax + n4);
+                                        a[0].x = fmaf(w.x, sp[u].x, a[0].x);
+                                        a[0].y = fmaf(w.x, sp[u].y, a[0].y);
+                                        a[1].x = fmaf(w.y, sm[u].x, a[1].x);
+                                        a[1].y = fmaf(w.y, sm[u].y, a[1].y);
+                                        a[2].x = fmaf(w.z, sp[u].x, a[2].x);
+                                        a[2].y = fmaf(w.z, sp[u].y, a[2].y);
+                                        a[3].x = fmaf(w.w, sm[u].x, a[3].x);
+                                        a[3].y = fmaf(w.w, sm[u].y, a[3].y);
+                                    }
+                                }
+#pragma unroll
+                                for (int c = 0; c < 4; ++c)
+                                    if (n4 + c < G) part[(qb * G + n4 + c) * M + i] = a[c];
+                            }
+                        }
+                    } else {
+#pragma unroll
+                        for (int n4 = 0; n4 < kFGMax; n4 += 4) {
+                            if (n4 < G) {
+                                float2 a[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f),
+                                               make_float2(0.f, 0.f)};
+#pragma unroll
+                                for (int bb = 0; bb < BPQ; ++bb) {
+#pragma unroll
+                                    for (int r = 0; r < MR1; ++r) {
+                                        const int j = qb * BPQ + bb + MR0 * r;
+                                        const float4 u = *reinterpret_cast<const float4*>(hgy + j * kFGMax + n4);
+                                        const float2 e = v[bb][r];
+                                        a[0].x = fmaf(u.x, e.x, a[0].x);
+                                        a[0].y = fmaf(u.x, e.y, a[0].y);
+                                        a[1].x = fmaf(u.y, e.x, a[1].x);
+                                        a[1].y = fmaf(u.y, e.y, a[1].y);
+                                        a[2].x = fmaf(u.z, e.x, a[2].x);
+                                        a[2].y = fmaf(u.z, e.y, a[2].y);
+                                        a[3].x = fmaf(u.w, e.x, a[3].x);
+                                        a[3].y = fmaf(u.w, e.y, a[3].y);
+                                    }
+                                }
+#pragma unroll
+                                for (int c = 0; c < 4; ++c)
+                                    if (n4 + c < G) part[(qb * G + n4 + c) * M + i] = a[c];
+                            }
                         }
                     }
                 }
@@ -398,56 +466,42 @@ __global__ void __launch_bounds__(FusedShape<M, T>::NT, FusedShape<M, T>::MINB)
 
         // ---------------------------------------------------------------- HG overlap, x contraction
         if (ov) {
-            // T[n][i]: the partial sums of the QB row groups added in a fixed order
-            for (int t = tid; t < G * M; t += NT) {
-                float2 v = part[t];
-#pragma unroll
-                for (int q = 1; q < QB; ++q) {
-                    const float2 w = part[q * G * M + t];
-                    v.x += w.x;
-                    v.y += w.y;
-                }
-                tsum[t] = v;
-            }
-            __syncthreads();
-            // c_mn = sum_i u_m(x'_i) T[n][i]: modes spread over the warps in groups of KW; independent
-            // products first, then interleaved shuffle trees (fixed order)
-            const int warp = tid >> 5, lane = tid & 31;
-            constexpr int NW = NT / 32, KW = 4;
+            // c_mn = sum_i u_m(x'_i) T[n][i] with T[n][i] = sum_qb part[qb][n][i] (groups added in a fixed order):
+            // eight threads per mode, thread s taking the column pairs i = 2s + 16h, h < M/16, then a fixed
+            // three-level shuffle tree over the eight
             float2* cf = A.coefs + (size_t)(f * P.pols + pol) * modes;
-            for (int k0 = 0; warp + k0 * NW < modes; k0 += KW) {
-                float2 sacc[KW];
+            const int s8 = tid & 7;
+            for (int t0 = tid & ~31; t0 < modes * 8; t0 += NT) {
+                const int k = (t0 + (tid & 31)) >> 3;
+                float2 acc = make_float2(0.f, 0.f);
+                if (k < modes) {
+                    const float* um = hgx + mdm[k] * M;
+                    const float2* tn = part + mdn[k] * M;
 #pragma unroll
-                for (int kk = 0; kk < KW; ++kk) {
-                    sacc[kk] = make_float2(0.f, 0.f);
-                    const int k = warp + (k0 + kk) * NW;
-                    if (k < modes) {
-                        const float* um = hgx + mdm[k] * M;
-                        const float2* tn = tsum + mdn[k] * M;
+                    for (int h = 0; h < M / 16; ++h) {
+                        const int i = 2 * s8 + 16 * h;
+                        const float2 u = *reinterpret_cast<const float2*>(um + i);
+                        float4 v = *reinterpret_cast<const float4*>(tn + i);
 #pragma unroll
-                        for (int i = lane; i < M; i += 32) {
-                            const float u = um[i];
-                            const float2 t = tn[i];
-                            sacc[kk].x = fmaf(u, t.x, sacc[kk].x);
-                            sacc[kk].y = fmaf(u, t.y, sacc[kk].y);
+                        for (int q = 1; q < QB; ++q) {
+                            const float4 w = *reinterpret_cast<const float4*>(tn + q * G * M + i);
+                            v.x += w.x;
+                            v.y += w.y;
+                            v.z += w.z;
+                            v.w += w.w;
                         }
+                        acc.x = fmaf(u.x, v.x, acc.x);
+                        acc.y = fmaf(u.x, v.y, acc.y);
+                        acc.x = fmaf(u.y, v.z, acc.x);
+                        acc.y = fmaf(u.y, v.w, acc.y);
                     }
                 }
 #pragma unroll
-                for (int o = 16; o > 0; o >>= 1) {
-#pragma unroll
-                    for (int kk = 0; kk < KW; ++kk) {
-                        sacc[kk].x += __shfl_xor_sync(0xffffffffu, sacc[kk].x, o);
-                        sacc[kk].y += __shfl_xor_sync(0xffffffffu, sacc[kk].y, o);
-                    }
+                for (int o = 1; o < 8; o <<= 1) {
+                    acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
+                    acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
                 }
-                if (lane == 0) {
-#pragma unroll
-                    for (int kk = 0; kk < KW; ++kk) {
-                        const int k = warp + (k0 + kk) * NW;
-                        if (k < modes) cf[k] = sacc[kk];
-                    }
-                }
+                if (s8 == 0 && k < modes) cf[k] = acc;
             }
         }
         __syncthreads();

@@ -132,13 +132,18 @@ def test_budget_errors_and_timeouts():
         finally:
             dh.dh_server_destroy(srv0)
         big = torch.from_numpy(np.repeat(fr.numpy(), 48, axis=0)).pin_memory()
+        m, modes, _ = dh.dh_get_output_dims(h)
+        flds = [torch.empty((48, 1, m, m), dtype=torch.complex64).pin_memory() for _ in range(3)]
         srv = dh.dh_server_create(1 << 30, 1)
         try:
-            t = dh.dh_server_submit(srv, h, big, dh.DH_DTYPE_U16, 48)
+            # the last of three queued requests (48 frames of 1024 x 1024 with fields each, milliseconds of GPU
+            # work apiece) cannot have finished when a zero timeout is asked right after its submission
+            ts = [dh.dh_server_submit(srv, h, big, dh.DH_DTYPE_U16, 48, flds[k]) for k in range(3)]
             with pytest.raises(dh.DigHoloError) as ei:
-                dh.dh_server_wait(srv, t, 0)
+                dh.dh_server_wait(srv, ts[-1], 0)
             assert ei.value.code == dh.DH_ERROR_TIMEOUT
-            dh.dh_server_wait(srv, t, -1)
+            for t in ts:
+                dh.dh_server_wait(srv, t, -1)
         finally:
             dh.dh_server_destroy(srv)
     finally:
