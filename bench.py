@@ -424,7 +424,9 @@ def run_ours(args, ws, rank, local):
         workers = os.cpu_count() or 1
         pool = OraclePool(workers)
         pool.warm(setup, data["frames"])
-        rate, dt, n = pool.run(setup, data["frames"], repeat=max(1, 6000 // frames_n))
+        # one pass to size the sample, then about ten seconds of oracle work
+        _, dt0, _ = pool.run(setup, data["frames"])
+        rate, dt, n = pool.run(setup, data["frames"], repeat=max(1, min(200, int(round(10.0 / max(dt0, 1e-3))))))
         pool.close()
         cpu = {"value": rate, "unit": "frames/s", "cores": workers, "kind": "oracle",
                "sample": f"{n} frames (repeated passes over the step's batch) in {dt:.1f} s on {workers} processes"}

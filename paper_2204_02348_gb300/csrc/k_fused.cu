@@ -12,8 +12,9 @@
 //   inverse  M-point inverse transform along x (DIT, digit-reversed in / natural out) and along y (DIF,
 //            natural in / digit-reversed out), in place;
 //   epilogue residual tilt and defocus removal in registers inside the last y pass, field write (coalesced
-//            along x), and the separable HG contraction: partial sums over y per group of row blocks, then the
-//            modes spread over the warps with fixed shuffle trees (deterministic, no atomics).
+//            along x), and the separable HG contraction: partial sums over y per group of row blocks (mirrored
+//            rows j and M - j paired, using the parity of u_n), then eight threads per mode summing the groups
+//            and contracting along x with a fixed shuffle tree (deterministic, no atomics).
 // Shared memory: the staging buffer of the next window (filled by the tensor copy while the current one is
 // processed), one complex work buffer used in place by every step (y tile, box rows, window, field partial
 // sums), twiddles, phases, the HG tables and the digit-reversal table: ~112 KB for uint16 frames, so two blocks

@@ -70,9 +70,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_ypass(const __grid_constant__ P
 
 // k_ypass for the power-of-two windows, with the host plan's radix sequence fixed at compile time (128: 16 x 8,
 // 256: 16 x 16, 512: 8 x 8 x 8, 1024: 16 x 8 x 8): no runtime radix dispatch, twiddles staged in shared
-// memory, 2^LOGC column pairs per block.  Same inputs, outputs and arithmetic order as k_ypass.
+// memory, 2^LOGC column pairs per block, three blocks per SM.  Same inputs, outputs and arithmetic order as
+// k_ypass.
 template <typename T, int N, int R0, int R1, int R2, int LOGC>
-__global__ void __launch_bounds__(kThreads, 2) k_ypass_s(const __grid_constant__ Plan P, const __grid_constant__ Batch B) {
+__global__ void __launch_bounds__(kThreads, 3) k_ypass_s(const __grid_constant__ Plan P, const __grid_constant__ Batch B) {
     extern __shared__ float2 smem[];   // [N][C] tile, then the twiddles W_N^k
     constexpr int C = 1 << LOGC, half = N / 2;
     static_assert(R0 * R1 * R2 == N, "the radices multiply to N");
@@ -83,19 +84,33 @@ __global__ void __launch_bounds__(kThreads, 2) k_ypass_s(const __grid_constant__
     const PolDev& pd = P.pol[pol];
     const int x0 = blockIdx.x * C;
     for (int i = tid; i < N; i += kThreads) tw[i] = P.tw_fwd_n[i];
+    static_assert((N * C) % (8 * kThreads) == 0, "whole load batches");
     for (int fb = blockIdx.z; fb < B.count; fb += gridDim.z) {
         const int f = B.frame0 + fb;
         const T* fr = (const T*)B.src + (size_t)f * P.width * P.height;
-        for (int idx = tid; idx < N * C; idx += kThreads) {
-            const int y = idx >> LOGC, c = idx & (C - 1);
-            const T* row = fr + (size_t)(pd.oy + y) * P.width + pd.ox + x0 + c;
-            float2 v = make_float2(to_f(row[0]), to_f(row[half]));
-            if (pd.cal) {
-                const float* k = pd.cal + (size_t)y * N + x0 + c;
-                v.x *= __ldg(k);
-                v.y *= __ldg(k + half);
+        // eight pixel pairs in flight per thread before their shared-memory stores
+        for (int i0 = tid; i0 < N * C; i0 += 8 * kThreads) {
+            T a[8], b[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int idx = i0 + u * kThreads;
+                const int y = idx >> LOGC, c = idx & (C - 1);
+                const T* row = fr + (size_t)(pd.oy + y) * P.width + pd.ox + x0 + c;
+                a[u] = row[0];
+                b[u] = row[half];
             }
-            smem[idx] = v;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int idx = i0 + u * kThreads;
+                float2 v = make_float2(to_f(a[u]), to_f(b[u]));
+                if (pd.cal) {
+                    const int y = idx >> LOGC, c = idx & (C - 1);
+                    const float* k = pd.cal + (size_t)y * N + x0 + c;
+                    v.x *= __ldg(k);
+                    v.y *= __ldg(k + half);
+                }
+                smem[idx] = v;
+            }
         }
         __syncthreads();
         spass<R0, false, false, N, N, C, C, 1, kThreads>(smem, tw, tid);
@@ -206,7 +221,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_xpass(const __grid_constant__ P
 // k_xpass with the x transform's radix sequence fixed at compile time (the same plans as k_ypass_s) and its
 // twiddles in shared memory; the M-point inverse keeps the runtime plan.  Same results as k_xpass.
 template <int N, int R0, int R1, int R2, int LOGR, int MR0, int MR1, int MR2>
-__global__ void __launch_bounds__(kThreads, 2) k_xpass_s(const __grid_constant__ Plan P, const __grid_constant__ Batch B) {
+__global__ void __launch_bounds__(kThreads, (N == 256 && LOGR == 4 && MR0 != 0) ? 3 : 2) k_xpass_s(const __grid_constant__ Plan P, const __grid_constant__ Batch B) {
     extern __shared__ float2 smem[];
     const int tid = threadIdx.x, nthr = blockDim.x;
     constexpr int R = 1 << LOGR, es = R + 1, logr = LOGR, logn = (N == 128 ? 7 : N == 256 ? 8 : N == 512 ? 9 : 10);
@@ -310,23 +325,33 @@ static bool launch_xpass_static(const Plan& P, const Batch& B, int zf, cudaStrea
     };
     switch (P.n) {
         case 128: if (!is(16, 8, 1)) return false; launch_xs<128, 16, 8, 1, 5>(P, B, zf, st); return true;
-        case 256: if (!is(16, 16, 1)) return false; launch_xs<256, 16, 16, 1, 5>(P, B, zf, st); return true;
+        case 256: if (!is(16, 16, 1)) return false; launch_xs<256, 16, 16, 1, 4>(P, B, zf, st); return true;
         case 512: if (!is(8, 8, 8)) return false; launch_xs<512, 8, 8, 8, 4>(P, B, zf, st); return true;
         case 1024: if (!is(16, 8, 8)) return false; launch_xs<1024, 16, 8, 8, 4>(P, B, zf, st); return true;
         default: return false;
     }
 }
 
-// MR0 MR1 MR2: the radix plan of M fixed at compile time, or MR0 = 0 for the runtime plan.
+// MR0 MR1 MR2: the radix plan of M fixed at compile time, or MR0 = 0 for the runtime plan.  The compile-time
+// plans fit 85 registers, so three blocks share an SM; the runtime plan needs more and runs two.
 template <int MR0, int MR1, int MR2>
-__global__ void __launch_bounds__(kThreads, 2) k_yinv(const __grid_constant__ Plan P, const __grid_constant__ Batch B) {
+__global__ void __launch_bounds__(kThreads, MR0 == 0 ? 2 : 3) k_yinv(const __grid_constant__ Plan P, const __grid_constant__ Batch B) {
     extern __shared__ float2 smem[];
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int M = P.m, G = P.groups, modes = P.modes;
     float2* buf = smem;                          // [M][kChunkI]
     float2* tp = smem + (size_t)M * kChunkI;     // [G][kChunkI]
+    // u_n(y'_j) for the rows j <= M/2, two modes of one parity per entry: block k holds n = 4 (k/2) + k%2 and
+    // n + 2 (zero beyond G); [M/2 + 1][nbk]
+    const int nbk = 2 * ((G + 3) / 4), hm = M / 2;
+    float2* u2 = tp + (size_t)std::max(G, 1) * kChunkI;
     const int pol = blockIdx.x;
     const PolDev& pd = P.pol[pol];
+    for (int t = tid; t < (hm + 1) * nbk; t += nthr) {
+        const int j = t / nbk, k = t - j * nbk;
+        const int na = 4 * (k >> 1) + (k & 1), nb = na + 2;
+        u2[t] = make_float2(na < G ? pd.hg_y[(size_t)na * M + j] : 0.f, nb < G ? pd.hg_y[(size_t)nb * M + j] : 0.f);
+    }
     for (int fb = blockIdx.y; fb < B.count; fb += gridDim.y) {
         const int f = B.frame0 + fb;
         const float2* g = B.g + (size_t)(fb * P.pols + pol) * M * M;
@@ -364,18 +389,39 @@ __global__ void __launch_bounds__(kThreads, 2) k_yinv(const __grid_constant__ Pl
             }
             __syncthreads();
             if (G > 0) {
-                // T[n][i] = sum_j u_n(y'_j) E[j][i]
-                for (int idx = tid; idx < G * kChunkI; idx += nthr) {
-                    const int n = idx >> 5, i = idx & (kChunkI - 1);
-                    const float* u = pd.hg_y + (size_t)n * M;
-                    float2 s = make_float2(0.f, 0.f);
-                    for (int j = 0; j < M; ++j) {
-                        const float w = __ldg(&u[j]);
-                        const float2 e = buf[j * kChunkI + i];
-                        s.x = fmaf(w, e.x, s.x);
-                        s.y = fmaf(w, e.y, s.y);
+                // T[n][i] = sum_j u_n(y'_j) E[j][i].  Rows j and M - j carry u_n(y'_{M-j}) = (-1)^n u_n(y'_j), so
+                // rows j = 1 .. M/2 - 1 become E_j + E_{M-j} (kept at j, for the even modes) and E_j - E_{M-j}
+                // (at M - j, for the odd ones); rows 0 and M/2 have no partner and serve both parities.
+                for (int idx = tid; idx < (hm - 1) * kChunkI; idx += nthr) {
+                    const int j = 1 + (idx >> 5), i = idx & (kChunkI - 1);
+                    const float2 a = buf[j * kChunkI + i], b = buf[(M - j) * kChunkI + i];
+                    buf[j * kChunkI + i] = cadd(a, b);
+                    buf[(M - j) * kChunkI + i] = csub(a, b);
+                }
+                __syncthreads();
+                for (int idx = tid; idx < nbk * kChunkI; idx += nthr) {
+                    const int k = idx >> 5, i = idx & (kChunkI - 1);   // k is the same across a warp
+                    const bool odd = k & 1;
+                    float2 sa = make_float2(0.f, 0.f), sb = make_float2(0.f, 0.f);
+                    {
+                        const float2 w = u2[k], e = buf[i];
+                        sa.x = fmaf(w.x, e.x, sa.x); sa.y = fmaf(w.x, e.y, sa.y);
+                        sb.x = fmaf(w.y, e.x, sb.x); sb.y = fmaf(w.y, e.y, sb.y);
                     }
-                    tp[n * kChunkI + i] = s;
+                    for (int j = 1; j < hm; ++j) {
+                        const float2 w = u2[j * nbk + k];
+                        const float2 e = buf[(odd ? M - j : j) * kChunkI + i];
+                        sa.x = fmaf(w.x, e.x, sa.x); sa.y = fmaf(w.x, e.y, sa.y);
+                        sb.x = fmaf(w.y, e.x, sb.x); sb.y = fmaf(w.y, e.y, sb.y);
+                    }
+                    {
+                        const float2 w = u2[hm * nbk + k], e = buf[hm * kChunkI + i];
+                        sa.x = fmaf(w.x, e.x, sa.x); sa.y = fmaf(w.x, e.y, sa.y);
+                        sb.x = fmaf(w.y, e.x, sb.x); sb.y = fmaf(w.y, e.y, sb.y);
+                    }
+                    const int na = 4 * (k >> 1) + (k & 1);
+                    if (na < G) tp[na * kChunkI + i] = sa;
+                    if (na + 2 < G) tp[(na + 2) * kChunkI + i] = sb;
                 }
                 __syncthreads();
                 // c_mn += sum_i u_m(x'_i) T[n][i]
@@ -428,9 +474,9 @@ cudaError_t split_init() {
 #define DH_XS_ATTR(...)                                                                                         \
     if ((e = cudaFuncSetAttribute(k_xpass_s<__VA_ARGS__>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem))) \
         return e;
-    DH_XS_ATTR(128, 16, 8, 1, 5, 0, 0, 0) DH_XS_ATTR(256, 16, 16, 1, 5, 0, 0, 0)
+    DH_XS_ATTR(128, 16, 8, 1, 5, 0, 0, 0) DH_XS_ATTR(256, 16, 16, 1, 4, 0, 0, 0)
     DH_XS_ATTR(512, 8, 8, 8, 4, 0, 0, 0) DH_XS_ATTR(1024, 16, 8, 8, 4, 0, 0, 0)
-    DH_XS_ATTR(256, 16, 16, 1, 5, 8, 4, 3) DH_XS_ATTR(512, 8, 8, 8, 4, 16, 11, 1)
+    DH_XS_ATTR(256, 16, 16, 1, 4, 8, 4, 3) DH_XS_ATTR(512, 8, 8, 8, 4, 16, 11, 1)
 #undef DH_XS_ATTR
     if ((e = cudaFuncSetAttribute(k_yinv<8, 4, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem))) return e;
     if ((e = cudaFuncSetAttribute(k_yinv<16, 11, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem))) return e;
@@ -478,7 +524,8 @@ cudaError_t launch_last(const Plan& P, const Batch& B, cudaStream_t st, StageTim
     // k_yinv (or its tensor-core variant): one block per window
     const int zf = std::min(B.count, 65535);
     dim3 g3(P.pols, zf);
-    const size_t sm3 = (size_t)(P.m + std::max(P.groups, 1)) * kChunkI * sizeof(float2);
+    const size_t sm3 = ((size_t)(P.m + std::max(P.groups, 1)) * kChunkI +
+                        (size_t)(P.m / 2 + 1) * 2 * ((P.groups + 3) / 4)) * sizeof(float2);
     if (tc_supported(P)) {
         if (tm) tm->start(st);
         cudaError_t e = launch_yinv_tc(P, B, st);
