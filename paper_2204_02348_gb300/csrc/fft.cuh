@@ -110,17 +110,38 @@ __device__ __forceinline__ void dft3(float2* a) {
     a[2] = csub(t, d);
 }
 
-// Direct R-point DFT with roots of unity from the transform's own twiddle table (tw[e * step] is the
-// R-th root raised to e, for e in [0, R)).  Used for the odd primes 5..19 of reduced field sizes.
+// R-point DFT for an odd prime R with roots of unity from the transform's own twiddle table (tw[e * step] is
+// the R-th root W raised to e, for e in [0, R)).  Used for the odd primes 5..19 of reduced field sizes.
+// Inputs r and R - r meet conjugate roots, W^{(R-r)k} = conj(W^{rk}), so with s_r = a_r + a_{R-r} and
+// d_r = a_r - a_{R-r}:  y_k = a_0 + sum_r s_r Re(W^{rk}) + i d_r Im(W^{rk}) and y_{R-k} the same with the
+// second sum negated (r, k = 1 .. (R-1)/2): a quarter of the multiplications of the plain sum.
 template <int R>
 __device__ __forceinline__ void dft_direct(float2* a, const float2* __restrict__ tw, int step) {
+    static_assert(R % 2 == 1, "odd radix");
+    constexpr int H = (R - 1) / 2;
+    float2 sp[H], dm[H];
+    float2 y0 = a[0];
+#pragma unroll
+    for (int r = 1; r <= H; ++r) {
+        sp[r - 1] = cadd(a[r], a[R - r]);
+        dm[r - 1] = csub(a[r], a[R - r]);
+        y0 = cadd(y0, sp[r - 1]);
+    }
     float2 y[R];
+    y[0] = y0;
 #pragma unroll
-    for (int k = 0; k < R; ++k) {
-        float2 acc = a[0];
+    for (int k = 1; k <= H; ++k) {
+        float2 ac = a[0], bc = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int r = 1; r < R; ++r) acc = cadd(acc, cmul(a[r], tw[((r * k) % R) * step]));
-        y[k] = acc;
+        for (int r = 1; r <= H; ++r) {
+            const float2 w = tw[((r * k) % R) * step];
+            ac.x = fmaf(sp[r - 1].x, w.x, ac.x);
+            ac.y = fmaf(sp[r - 1].y, w.x, ac.y);
+            bc.x = fmaf(-dm[r - 1].y, w.y, bc.x);
+            bc.y = fmaf(dm[r - 1].x, w.y, bc.y);
+        }
+        y[k] = cadd(ac, bc);
+        y[R - k] = csub(ac, bc);
     }
 #pragma unroll
     for (int k = 0; k < R; ++k) a[k] = y[k];
