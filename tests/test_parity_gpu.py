@@ -410,3 +410,18 @@ def test_full_size_large_scoring_sampled():
         ref = orc.score_settings(distinct[b % 8][None], s, cand["tilt_deg"][k:k + 1], cand["defocus"][k:k + 1],
                                  cand["waist"][k:k + 1])[0, 0]
         assert abs(got[b, k] - ref) / ref <= 2 * SPLIT_COEF_TOL, (b, k, got[b, k], ref)
+
+
+# ----------------------------------------------------------------------------- odd-prime inverse radices
+@pytest.mark.parametrize("kind,m", [("256x256_1pol", 80), ("256x256_1pol", 112), ("256x256_1pol", 176),
+                                    ("256x256_1pol", 208), ("1024x1024_1pol", 272), ("1024x1024_1pol", 304)])
+def test_odd_prime_field_sizes(kind, m):
+    # M = 16 x {5, 7, 11, 13, 17, 19}: every odd-prime butterfly of the inverse transforms (runtime radix plans,
+    # and the compile-time plan at 176), FP32; the split-BF16 overlap where its kernel takes the size (M <= 192)
+    s = syn.with_(syn.serving_geometry(kind, np.random.default_rng(400 + m)), ifft_size=m)
+    d = syn.make_frames(s, 2, seed=401 + m)
+    out = run_library(s, d["frames"])
+    assert out["m"] == m
+    _check(s, d["frames"], out)
+    if m <= 192:
+        _check(s, d["frames"], run_library(s, d["frames"], precision=1, fields=False), coef_tol=SPLIT_COEF_TOL)
