@@ -274,6 +274,23 @@ __device__ __forceinline__ void spass(float2* buf, const float2* tw, int tid) {
 }
 
 
+// Position of index k after DIF passes of radices R0 R1 R2 (in that order; R2 = 1 for two passes): the digits
+// of k, least significant first, weighted by the block lengths R1 R2, R2, 1.  The same map as the host's
+// position tables, for plans fixed at compile time.
+template <int R0, int R1, int R2>
+__device__ __forceinline__ int dif_pos(int k) {
+    return (k % R0) * (R1 * R2) + ((k / R0) % R1) * R2 + k / (R0 * R1);
+}
+
+// Position of index k: from the host's table for a runtime plan (R0 = 0), else computed.
+template <int R0, int R1, int R2>
+__device__ __forceinline__ int plan_pos(const int* __restrict__ table, int k) {
+    if constexpr (R0 == 0)
+        return table[k];
+    else
+        return dif_pos<R0, R1, R2>(k);
+}
+
 // Inverse (DIT) transform with the radix plan fixed at compile time: R0 R1 R2 in the host plan's DIF order
 // (R2 = 1 for a two-radix plan), passes run last radix first, as fft_run<true> does at run time.  NB
 // transforms, element e of transform b at buf[e * ES + b].  Ends with a barrier.

@@ -127,8 +127,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_ypass_s(const __grid_constant__
             int k = (pd.kly + q) % N;
             if (k < 0) k += N;
             const int km = (N - k) & (N - 1);
-            const float2 za = smem[P.pos_n[k] * C + c];
-            const float2 zb = smem[P.pos_n[km] * C + c];
+            const float2 za = smem[dif_pos<R0, R1, R2>(k) * C + c];
+            const float2 zb = smem[dif_pos<R0, R1, R2>(km) * C + c];
             r1[(size_t)q * N + x0 + c] = make_float2(0.5f * (za.x + zb.x), 0.5f * (za.y - zb.y));
             r1[(size_t)q * N + x0 + c + half] = make_float2(0.5f * (za.y + zb.y), 0.5f * (zb.x - za.x));
         }
@@ -270,11 +270,11 @@ __global__ void __launch_bounds__(kThreads, (N == 256 && LOGR == 4 && MR0 != 0) 
                 if (pp >= pd.mask_lo[q] && pp <= pd.mask_hi[q]) {
                     int kx = (pd.klx + pp) % N;
                     if (kx < 0) kx += N;
-                    v = cmul(cmul(bufN[P.pos_n[kx] * es + row], pd.phase_x[pp]), pd.phase_y[q]);
+                    v = cmul(cmul(bufN[dif_pos<R0, R1, R2>(kx) * es + row], pd.phase_x[pp]), pd.phase_y[q]);
                 }
                 if (B.window) B.window[((size_t)(f * P.pols + pol) * M + q) * M + pp] = v;
             }
-            bufM[P.pos_m[pp] * es + row] = v;
+            bufM[plan_pos<MR0, MR1, MR2>(P.pos_m, pp) * es + row] = v;
         }
         __syncthreads();
         if constexpr (MR0 == 0)
@@ -369,7 +369,7 @@ __global__ void __launch_bounds__(kThreads, MR0 == 0 ? 2 : 3) k_yinv(const __gri
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
                     const int idx = j0 + u * nthr;
-                    if (idx < M * kChunkI) buf[P.pos_m[idx >> 5] * kChunkI + (idx & (kChunkI - 1))] = v[u];
+                    if (idx < M * kChunkI) buf[plan_pos<MR0, MR1, MR2>(P.pos_m, idx >> 5) * kChunkI + (idx & (kChunkI - 1))] = v[u];
                 }
             }
             __syncthreads();

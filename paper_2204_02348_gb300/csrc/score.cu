@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(kSThreads, 2) k_xinv_sel(const __grid_constant
                     const int q = q0 + row;
                     float2 w = make_float2(0.f, 0.f);
                     if (q < M && p >= pd.mask_lo[q] && p <= pd.mask_hi[q]) w = cmul(cmul(v[u], pd.phase_x[p]), pd.phase_y[q]);
-                    smem[P.pos_m[p] * es + row] = w;
+                    smem[plan_pos<MR0, MR1, MR2>(P.pos_m, p) * es + row] = w;
                 }
             }
         }
