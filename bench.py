@@ -141,7 +141,7 @@ def measured_peak():
 # source file of each timed kernel; its hash also covers the device headers every kernel includes
 KERNEL_SOURCES = {"k_fused128": "k_fused.cu", "k_yinv_tc": "k_overlap_tc.cu", "k_ypass": "k_split.cu",
                   "k_xpass": "k_split.cu", "k_yinv": "k_split.cu"}
-DEVICE_HEADERS = ("fft.cuh", "kernels.cuh", "sync.cuh")
+DEVICE_HEADERS = ("fft.cuh", "kernels.cuh", "sync.cuh", "umma.cuh")
 
 
 def kernel_source_hash(kernel):

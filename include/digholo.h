@@ -181,7 +181,10 @@ int dh_set_ref_calibration(dh_handle h, const uint16_t* cal, int wavelength_coun
  * enabling without one gives DH_ERROR_INVALIDARGUMENT. */
 int dh_set_ref_calibration_enabled(dh_handle h, int enabled);
 
-/* Overlap arithmetic: DH_PRECISION_FP32 or DH_PRECISION_SPLIT_BF16. */
+/* Overlap arithmetic (the transforms are FP32 either way): DH_PRECISION_FP32, or DH_PRECISION_SPLIT_BF16, the
+ * y contraction of the HG overlap on the tensor cores with bfloat16 hi + lo parts of the field and of the basis
+ * (hi hi + hi lo + lo hi, FP32 accumulation); coefficients then agree with the FP32 ones to about 1e-5
+ * relative.  Any other value gives DH_ERROR_INVALIDARGUMENT. */
 int dh_set_precision(dh_handle h, int precision);
 
 /* Validate the settings and report the output geometry: field size M (square), number of coefficients per

@@ -15,6 +15,10 @@
 //            along x), and the separable HG contraction: partial sums over y per group of row blocks (mirrored
 //            rows j and M - j paired, using the parity of u_n), then eight threads per mode summing the groups
 //            and contracting along x with a fixed shuffle tree (deterministic, no atomics).
+//            Split-BF16 variant (field size 64): the corrected field is written as the bf16 hi / lo A operand
+//            of one 128 x 16 x 64 tcgen05 contraction over y (three products per K step, FP32 accumulation in
+//            tensor memory, issued by one thread and awaited on an mbarrier with a bounded wait), read back by
+//            four warps and contracted along x as above.
 // Shared memory: the staging buffer of the next window (filled by the tensor copy while the current one is
 // processed), one complex work buffer used in place by every step (y tile, box rows, window, field partial
 // sums), twiddles, phases, the HG tables and the digit-reversal table: ~112 KB for uint16 frames, so two blocks
@@ -29,9 +33,12 @@
 #include <cstring>
 #include <string>
 
+#include <cuda_bf16.h>
+
 #include "fft.cuh"
 #include "runtime.hpp"
 #include "sync.cuh"
+#include "umma.cuh"
 
 namespace dhk {
 
@@ -111,7 +118,8 @@ __device__ __forceinline__ void emit_pair(float2* r1, int pitch, int M, int kly,
     }
 }
 
-template <int M, int MR0, int MR1, typename T, int MODE>
+// TC: the y contraction in split-BF16 on the tensor cores (the split-BF16 precision; field size 64 only).
+template <int M, int MR0, int MR1, typename T, int MODE, bool TC = false>
 __global__ void __launch_bounds__(FusedShape<M, T>::NT, FusedShape<M, T>::MINB)
     k_fused128(const __grid_constant__ Plan P, const __grid_constant__ FusedArgs A, const __grid_constant__ CUtensorMap tmap) {
     using L = FusedLayout<M, T>;
@@ -124,11 +132,20 @@ __global__ void __launch_bounds__(FusedShape<M, T>::NT, FusedShape<M, T>::MINB)
     static_assert(NBLK % QB == 0, "row blocks split evenly into the partial-sum groups");
     static_assert(L::WB + QB * kFGMax * M <= L::BUF, "the partial sums fit behind the window");
     // y contraction over mirrored rows: group 0 holds blocks 0 and MR0/2, group qb > 0 blocks qb and MR0 - qb
-    constexpr bool PAIRS = MR0 == 8 && QB == 4 && BPQ == 2 && MR1 % 2 == 0;
+    constexpr bool PAIRS = !TC && MR0 == 8 && QB == 4 && BPQ == 2 && MR1 % 2 == 0;
+    // tensor-core y contraction: A = the corrected field as bf16 hi + lo, 2M rows (real parts of columns i, then
+    // imaginary parts) by K = M field rows in the order kappa = MR1 blk + r of the last pass's outputs (row
+    // j = blk + MR0 r), 2 x 2M x M bf16 behind the window; B = u_n(y'_j) dy' as bf16 hi + lo with its K rows
+    // permuted the same way, in place of the FP32 y table; D = 2M x 16 FP32 in tensor memory
+    static_assert(!TC || (M == 64 && MR1 == 8 && MODE != kModeForward), "tensor-core variant: M = 64");
+    static_assert(!TC || L::WB * 8 + 8 * M * M <= L::BUF * 8, "A operand fits behind the window");
+    constexpr uint32_t kTcTmemCols = 32;
     static_assert(M % 8 == 0, "box rows below M come in whole radix-8 tasks");
     // 128-byte alignment: tensor-copy destination; no larger, so that two blocks fit an SM
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t mbar;
+    __shared__ __align__(8) uint64_t mbar_mma;   // TC: completion of the window's MMAs
+    __shared__ uint32_t tmem_slot;               // TC: tensor-memory address
     __shared__ int abort_flag;
     T* stg = reinterpret_cast<T*>(smem_raw);
     float2* buf = reinterpret_cast<float2*>(smem_raw + L::STG);
@@ -162,10 +179,24 @@ __global__ void __launch_bounds__(FusedShape<M, T>::NT, FusedShape<M, T>::MINB)
         mhi[i] = pd.mask_hi[i];
     }
     for (int i = tid; i < G * M; i += NT) hgx[i] = pd.hg_x[i];
-    // u_n(y'_j) stored [j][n] (n fastest, kFGMax wide) so the y contraction reads four groups per load
-    for (int i = tid; i < kFGMax * M; i += NT) {
-        const int j = i / kFGMax, n = i - j * kFGMax;
-        hgy[i] = n < G ? pd.hg_y[n * M + j] : 0.f;
+    if constexpr (TC) {
+        // B operand: the host's bf16 hi / lo planes of u_n(y'_j) dy' (rows n < 16, K = j), K permuted to kappa
+        __nv_bfloat16* bop = reinterpret_cast<__nv_bfloat16*>(hgy);
+        const __nv_bfloat16* src = reinterpret_cast<const __nv_bfloat16*>(pd.hgy_tc);
+        for (int t = tid; t < 2 * kFGMax * M; t += NT) {
+            const int hl = t / (kFGMax * M), rem = t - hl * kFGMax * M, n = rem / M, kap = rem - n * M;
+            const int j = kap / MR1 + MR0 * (kap % MR1);
+            bop[hl * kFGMax * M + umma_off(n, kap, M)] =
+                G > 0 ? src[(size_t)hl * P.tc_np * M + umma_off(n, j, M)] : __float2bfloat16_rn(0.f);
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        if (tid < 32) tmem_alloc(smem_u32(&tmem_slot), kTcTmemCols);
+    } else {
+        // u_n(y'_j) stored [j][n] (n fastest, kFGMax wide) so the y contraction reads four groups per load
+        for (int i = tid; i < kFGMax * M; i += NT) {
+            const int j = i / kFGMax, n = i - j * kFGMax;
+            hgy[i] = n < G ? pd.hg_y[n * M + j] : 0.f;
+        }
     }
     for (int i = tid; i < modes; i += NT) {
         mdm[i] = P.mode_m[i];
@@ -176,6 +207,10 @@ __global__ void __launch_bounds__(FusedShape<M, T>::NT, FusedShape<M, T>::MINB)
     int b = blockIdx.x / P.pols;
     if (tid == 0) {
         abort_flag = 0;
+        if constexpr (TC) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar_mma)));
+            asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        }
         if (MODE != kModeInverse) {
             asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb));
             asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
@@ -185,6 +220,12 @@ __global__ void __launch_bounds__(FusedShape<M, T>::NT, FusedShape<M, T>::MINB)
     __syncthreads();
     const int xo = A.xo[pol];
     uint32_t parity = 0;
+    uint32_t tmem = 0, mma_parity = 0;
+    bool tc_ok = true;                           // TC: every MMA wait so far completed
+    if constexpr (TC) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        tmem = tmem_slot;
+    }
     for (; b < A.count; b += fstride) {
         const int f = A.frame0 + b;
         if constexpr (MODE == kModeInverse) {
@@ -370,7 +411,29 @@ __global__ void __launch_bounds__(FusedShape<M, T>::NT, FusedShape<M, T>::MINB)
                     }
                 }
                 if (ov) {
-                    if constexpr (PAIRS) {
+                    if constexpr (TC) {
+                        // this thread's rows j = blk + MR0 r are the 8 consecutive K positions kappa = MR1 blk + r:
+                        // one 16-byte row of a core matrix per plane (hi / lo) and part (real / imaginary)
+                        __nv_bfloat16* aop = reinterpret_cast<__nv_bfloat16*>(buf + L::WB);
+#pragma unroll
+                        for (int bb = 0; bb < BPQ; ++bb) {
+                            const int blk = qb * BPQ + bb;
+                            __align__(16) __nv_bfloat16 hr[8], hm[8], lr[8], lm[8];
+#pragma unroll
+                            for (int r = 0; r < MR1; ++r) {
+                                const float2 e = v[bb][r];
+                                hr[r] = __float2bfloat16_rn(e.x);
+                                hm[r] = __float2bfloat16_rn(e.y);
+                                lr[r] = __float2bfloat16_rn(e.x - __bfloat162float(hr[r]));
+                                lm[r] = __float2bfloat16_rn(e.y - __bfloat162float(hm[r]));
+                            }
+                            const int o_r = umma_off(i, MR1 * blk, M), o_m = umma_off(M + i, MR1 * blk, M);
+                            *reinterpret_cast<uint4*>(aop + o_r) = *reinterpret_cast<const uint4*>(hr);
+                            *reinterpret_cast<uint4*>(aop + o_m) = *reinterpret_cast<const uint4*>(hm);
+                            *reinterpret_cast<uint4*>(aop + 2 * M * M + o_r) = *reinterpret_cast<const uint4*>(lr);
+                            *reinterpret_cast<uint4*>(aop + 2 * M * M + o_m) = *reinterpret_cast<const uint4*>(lm);
+                        }
+                    } else if constexpr (PAIRS) {
                         // rows j and M - j carry u_n(y'_{M-j}) = (-1)^n u_n(y'_j): the even modes contract the
                         // sums E_j + E_{M-j}, the odd ones the differences, each with u_n(y'_j) (half the products)
                         float2 sp[MR1 + 1], sm[MR1 + 1];
@@ -463,7 +526,52 @@ __global__ void __launch_bounds__(FusedShape<M, T>::NT, FusedShape<M, T>::MINB)
                 }
             }
         }
+        if constexpr (TC) asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         __syncthreads();
+        // TC: T[n][r] (r < M: real part of column r, r >= M: imaginary part of column r - M) over the consumed
+        // window, [16][kTsPitch]
+        constexpr int kTsPitch = 2 * M + 1;
+        float* Ts = reinterpret_cast<float*>(buf);
+        if constexpr (TC) {
+            if (ov) {
+                // y contraction: hi hi + hi lo + lo hi per 16-wide K step, FP32 accumulation in tensor memory
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const uint32_t mbm = smem_u32(&mbar_mma);
+                if (tid == 0 && tc_ok) {
+                    const uint32_t a_hi = smem_u32(buf + L::WB), a_lo = a_hi + 4 * M * M;
+                    const uint32_t b_hi = smem_u32(hgy), b_lo = b_hi + 2 * kFGMax * M;
+                    constexpr uint32_t idesc = umma_idesc_bf16(2 * M, kFGMax);
+                    const uint32_t lbo = 128, sbo = 16 * M;
+#pragma unroll
+                    for (int ks = 0; ks < M / 16; ++ks) {
+                        const uint32_t ko = ks * 256;
+                        umma_bf16(tmem, umma_desc(a_hi + ko, lbo, sbo), umma_desc(b_hi + ko, lbo, sbo), idesc, ks > 0);
+                        umma_bf16(tmem, umma_desc(a_hi + ko, lbo, sbo), umma_desc(b_lo + ko, lbo, sbo), idesc, 1);
+                        umma_bf16(tmem, umma_desc(a_lo + ko, lbo, sbo), umma_desc(b_hi + ko, lbo, sbo), idesc, 1);
+                    }
+                    umma_commit(mbm);
+                }
+                bool done = false;
+                if (tc_ok) {   // the same for every thread
+                    done = bounded_mbar_wait(mbm, mma_parity, kFWaitLimit);
+                    mma_parity ^= 1u;
+                }
+                // one decision for the whole block (the tensor-memory loads below are warp-collective)
+                const bool all = __syncthreads_and(done ? 1 : 0) != 0;
+                if (tc_ok && !all && tid == 0 && P.status) atomicOr(P.status, 2);
+                tc_ok = tc_ok && all;
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const int warp = tid >> 5, lane = tid & 31;
+                if (warp < 4) {
+                    float tv[16];
+                    if (tc_ok) tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16), tv);
+#pragma unroll
+                    for (int n = 0; n < kFGMax; ++n) Ts[n * kTsPitch + 32 * warp + lane] = tc_ok ? tv[n] : __int_as_float(0x7fc00000);
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+                __syncthreads();
+            }
+        }
 
         // ---------------------------------------------------------------- HG overlap, x contraction
         if (ov) {
@@ -475,7 +583,19 @@ __global__ void __launch_bounds__(FusedShape<M, T>::NT, FusedShape<M, T>::MINB)
             for (int t0 = tid & ~31; t0 < modes * 8; t0 += NT) {
                 const int k = (t0 + (tid & 31)) >> 3;
                 float2 acc = make_float2(0.f, 0.f);
-                if (k < modes) {
+                if (TC && k < modes) {
+                    const float* um = hgx + mdm[k] * M;
+                    const float* tr = Ts + mdn[k] * kTsPitch;
+#pragma unroll
+                    for (int h = 0; h < M / 16; ++h) {
+                        const int i = 2 * s8 + 16 * h;
+                        const float2 u = *reinterpret_cast<const float2*>(um + i);
+                        acc.x = fmaf(u.x, tr[i], acc.x);
+                        acc.y = fmaf(u.x, tr[M + i], acc.y);
+                        acc.x = fmaf(u.y, tr[i + 1], acc.x);
+                        acc.y = fmaf(u.y, tr[M + i + 1], acc.y);
+                    }
+                } else if (k < modes) {
                     const float* um = hgx + mdm[k] * M;
                     const float2* tn = part + mdn[k] * M;
 #pragma unroll
@@ -509,6 +629,14 @@ __global__ void __launch_bounds__(FusedShape<M, T>::NT, FusedShape<M, T>::MINB)
     }
     // a tensor copy still in flight (only after an expired wait) must land before the block exits
     if (MODE != kModeInverse && abort_flag && tid == 0) mbar_wait(mb, parity);
+    if constexpr (TC) {
+        // MMAs still in flight (only after an expired wait: the last ones issued) must complete before their tensor
+        // memory is freed
+        if (!tc_ok && tid == 0) bounded_mbar_wait(smem_u32(&mbar_mma), mma_parity ^ 1u, kFWaitLimit);
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        __syncthreads();
+        if (tid < 32) tmem_free(tmem, kTcTmemCols);
+    }
 }
 
 template <int M, int MR0, int MR1, int MODE>
@@ -526,8 +654,22 @@ static cudaError_t set_attr() {
     cudaError_t e;
     if ((e = set_attr_mode<M, MR0, MR1, kModeFull>())) return e;
     if ((e = set_attr_mode<M, MR0, MR1, kModeForward>())) return e;
-    return cudaFuncSetAttribute(k_fused128<M, MR0, MR1, uint16_t, kModeInverse>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FusedLayout<M, uint16_t>::bytes);
+    if ((e = cudaFuncSetAttribute(k_fused128<M, MR0, MR1, uint16_t, kModeInverse>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)FusedLayout<M, uint16_t>::bytes)))
+        return e;
+    if constexpr (M == 64) {
+        // the split-BF16 (tensor-core) variants of the modes that contract
+        if ((e = cudaFuncSetAttribute(k_fused128<M, MR0, MR1, uint16_t, kModeFull, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FusedLayout<M, uint16_t>::bytes)))
+            return e;
+        if ((e = cudaFuncSetAttribute(k_fused128<M, MR0, MR1, float, kModeFull, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FusedLayout<M, float>::bytes)))
+            return e;
+        if ((e = cudaFuncSetAttribute(k_fused128<M, MR0, MR1, uint16_t, kModeInverse, true>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)FusedLayout<M, uint16_t>::bytes)))
+            return e;
+    }
+    return cudaSuccess;
 }
 
 // Resident blocks per SM of one instantiation (the persistent grid is SMs x this).  The inverse-only mode
@@ -548,22 +690,23 @@ static int blocks_per_sm(int dtype, int mode) {
     return (e == cudaSuccess && n > 0) ? n : 1;
 }
 
-template <int M, int MR0, int MR1, typename T, int MODE>
+template <int M, int MR0, int MR1, typename T, int MODE, bool TC = false>
 static void launch_one(const Plan& P, const FusedArgs& A, const CUtensorMap& tm, int grid, cudaStream_t st) {
-    k_fused128<M, MR0, MR1, T, MODE><<<grid, FusedShape<M, T>::NT, FusedLayout<M, T>::bytes, st>>>(P, A, tm);
+    k_fused128<M, MR0, MR1, T, MODE, TC><<<grid, FusedShape<M, T>::NT, FusedLayout<M, T>::bytes, st>>>(P, A, tm);
 }
 
-template <int M, int MR0, int MR1>
+// TC: the split-BF16 variant (field size 64; the forward-only mode does not contract and has none)
+template <int M, int MR0, int MR1, bool TC>
 static void launch(const Plan& P, const FusedArgs& A, const CUtensorMap& tm, int dtype, int mode, int grid,
                    cudaStream_t st) {
     if (mode == kModeInverse)
-        launch_one<M, MR0, MR1, uint16_t, kModeInverse>(P, A, tm, grid, st);
+        launch_one<M, MR0, MR1, uint16_t, kModeInverse, TC>(P, A, tm, grid, st);
     else if (dtype == DH_DTYPE_U16)
         mode == kModeForward ? launch_one<M, MR0, MR1, uint16_t, kModeForward>(P, A, tm, grid, st)
-                             : launch_one<M, MR0, MR1, uint16_t, kModeFull>(P, A, tm, grid, st);
+                             : launch_one<M, MR0, MR1, uint16_t, kModeFull, TC>(P, A, tm, grid, st);
     else
         mode == kModeForward ? launch_one<M, MR0, MR1, float, kModeForward>(P, A, tm, grid, st)
-                             : launch_one<M, MR0, MR1, float, kModeFull>(P, A, tm, grid, st);
+                             : launch_one<M, MR0, MR1, float, kModeFull, TC>(P, A, tm, grid, st);
 }
 
 }  // namespace dhk
@@ -575,8 +718,10 @@ static int g_bps[64][9] = {};   // resident blocks per SM per (field size, pixel
 static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
 bool use_fused(const dhk::Plan& P) {
-    if (P.n != dhk::kFN || P.groups > dhk::kFGMax || P.precision != DH_PRECISION_FP32) return false;
-    return P.m == 32 || P.m == 48 || P.m == 64;
+    if (P.n != dhk::kFN || P.groups > dhk::kFGMax) return false;
+    if (P.precision == DH_PRECISION_SPLIT_BF16)   // the tensor-core variant: field size 64, B operand of 16 rows
+        return P.m == 64 && (P.groups == 0 || P.tc_np == dhk::kFGMax);
+    return P.precision == DH_PRECISION_FP32 && (P.m == 32 || P.m == 48 || P.m == 64);
 }
 
 bool fused_frames_ok(const dhk::Plan& P, const void* frames, int dtype) {
@@ -654,11 +799,20 @@ int launch_fused(Handle* H, const dhk::Plan& P, const void* frames, int dtype, i
     const int grid = (int)per_pol * P.pols;
     if (tm) tm->start(st);
     switch (P.m) {
-        case 32: dhk::launch<32, 8, 4>(P, A, tmap, dtype, mode, grid, st); break;
-        case 48: dhk::launch<48, 3, 16>(P, A, tmap, dtype, mode, grid, st); break;
-        default: dhk::launch<64, 8, 8>(P, A, tmap, dtype, mode, grid, st); break;
+        case 32: dhk::launch<32, 8, 4, false>(P, A, tmap, dtype, mode, grid, st); break;
+        case 48: dhk::launch<48, 3, 16, false>(P, A, tmap, dtype, mode, grid, st); break;
+        default:
+            if (P.precision == DH_PRECISION_SPLIT_BF16)
+                dhk::launch<64, 8, 8, true>(P, A, tmap, dtype, mode, grid, st);
+            else
+                dhk::launch<64, 8, 8, false>(P, A, tmap, dtype, mode, grid, st);
+            break;
     }
-    if (tm) tm->stop(st, mode == dhk::kModeForward ? "k_fused128_fwd" : mode == dhk::kModeInverse ? "k_fused128_inv" : "k_fused128");
+    const bool tc = P.precision == DH_PRECISION_SPLIT_BF16 && mode != dhk::kModeForward;
+    if (tm)
+        tm->stop(st, mode == dhk::kModeForward ? "k_fused128_fwd"
+                     : mode == dhk::kModeInverse ? (tc ? "k_fused128_inv_tc" : "k_fused128_inv")
+                                                 : (tc ? "k_fused128_tc" : "k_fused128"));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "fused launch");
     return DH_SUCCESS;

@@ -22,6 +22,7 @@
 #include "fft.cuh"
 #include "kernels.cuh"
 #include "sync.cuh"
+#include "umma.cuh"
 
 namespace dhk {
 
@@ -35,34 +36,7 @@ constexpr long kWaitLimit = 1L << 24;
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return smem_u32(p); }
 
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-    uint64_t d = (uint64_t)((addr & 0x3FFFFu) >> 4);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-    d |= (uint64_t)1 << 46;   // descriptor version
-    return d;                 // base offset 0, no swizzle
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
-    asm volatile(
-        "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
-}
-
 __device__ __forceinline__ bool wait_parity(uint32_t mbar, uint32_t parity) { return bounded_mbar_wait(mbar, parity, kWaitLimit); }
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* out) {
-    uint32_t v[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]), "=r"(v[8]),
-          "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) out[i] = __uint_as_float(v[i]);
-}
 
 constexpr int kTsPitch = 129;        // accumulator rows per mode row in shared memory (padded)
 
@@ -112,9 +86,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_yinv_tc(const __grid_constant
     }
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     if (warp == 0) {
-        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(&tmem_slot)),
-                     "r"(kTmemCols));
-        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+        tmem_alloc(smem_addr(&tmem_slot), kTmemCols);
     }
     if (tid == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_addr(&mbar)));
@@ -127,7 +99,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_yinv_tc(const __grid_constant
     const uint32_t a_hi = smem_addr(A), a_lo = a_hi + 128 * M * 2;
     const uint32_t b_hi = smem_addr(Bm), b_lo = b_hi + NP * M * 2;
     const uint32_t lbo = 128, sbo = 16 * M;
-    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(NP >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+    const uint32_t idesc = umma_idesc_bf16(128, NP);
     uint32_t phase = 0;
     bool ok = true;
 
@@ -139,7 +111,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_yinv_tc(const __grid_constant
             if constexpr (R0 == 0 || R0 * R1 * R2 > 128) {
                 for (int idx = tid; idx < M * kTcCols; idx += kTcThreads) {
                     const int q = idx >> 6, i = idx & (kTcCols - 1);
-                    buf[P.pos_m[q] * kTcCols + i] = (i0 + i < M) ? g[(size_t)q * M + i0 + i] : make_float2(0.f, 0.f);
+                    buf[plan_pos<R0, R1, R2>(P.pos_m, q) * kTcCols + i] = (i0 + i < M) ? g[(size_t)q * M + i0 + i] : make_float2(0.f, 0.f);
                 }
             } else {
                 // a small fixed plan leaves the registers for eight loads in flight per thread (at M = 176 the
@@ -156,7 +128,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_yinv_tc(const __grid_constant
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
                         const int idx = j0 + u * kTcThreads;
-                        if (idx < MM * kTcCols) buf[P.pos_m[idx >> 6] * kTcCols + (idx & (kTcCols - 1))] = v[u];
+                        if (idx < MM * kTcCols) buf[dif_pos<R0, R1, R2>(idx >> 6) * kTcCols + (idx & (kTcCols - 1))] = v[u];
                     }
                 }
             }
@@ -204,12 +176,11 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_yinv_tc(const __grid_constant
             if (tid == 0 && ok) {
                 for (int ks = 0; ks < M / 16; ++ks) {
                     const uint32_t ko = ks * 256;
-                    mma_bf16(tmem, smem_desc(a_hi + ko, lbo, sbo), smem_desc(b_hi + ko, lbo, sbo), idesc, ks > 0);
-                    mma_bf16(tmem, smem_desc(a_hi + ko, lbo, sbo), smem_desc(b_lo + ko, lbo, sbo), idesc, 1);
-                    mma_bf16(tmem, smem_desc(a_lo + ko, lbo, sbo), smem_desc(b_hi + ko, lbo, sbo), idesc, 1);
+                    umma_bf16(tmem, umma_desc(a_hi + ko, lbo, sbo), umma_desc(b_hi + ko, lbo, sbo), idesc, ks > 0);
+                    umma_bf16(tmem, umma_desc(a_hi + ko, lbo, sbo), umma_desc(b_lo + ko, lbo, sbo), idesc, 1);
+                    umma_bf16(tmem, umma_desc(a_lo + ko, lbo, sbo), umma_desc(b_hi + ko, lbo, sbo), idesc, 1);
                 }
-                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(mbar_a)
-                             : "memory");
+                umma_commit(mbar_a);
             }
             const bool done = ok && wait_parity(mbar_a, phase);
             phase ^= 1u;
@@ -251,7 +222,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_yinv_tc(const __grid_constant
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(kTmemCols));
+    if (warp == 0) tmem_free(tmem, kTmemCols);
 }
 
 bool tc_supported(const Plan& P) {

@@ -124,3 +124,13 @@ def test_avg_with_reference_calibration():
     f, c = _run_avg(s, d["frames"], 2, 3, 0)
     f_ref, c_ref = orc.process_batch_avg(d["frames"], s, 3, 0)
     _check(f, c, f_ref, c_ref)
+
+
+def test_avg_batching_split_bf16_fused():
+    # the fused kernel's forward-only mode, the averaging kernels and its tensor-core inverse-only mode
+    s = syn.setup_batching()
+    d = syn.make_avg_frames(s, 3, 3, 0, seed=135)
+    f_ref, c_ref = orc.process_batch_avg(d["frames"], s, 3, 0)
+    f, c = _run_avg(s, d["frames"], 3, 3, 0, precision=1)
+    _check(f, c, f_ref, c_ref, coef_tol=SPLIT_COEF_TOL)
+

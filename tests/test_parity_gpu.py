@@ -230,6 +230,26 @@ def test_split_bf16_overlap(name, frames):
     assert rel_l2(out["fields"], plain["fields"]).max() <= FIELD_TOL
 
 
+@pytest.mark.parametrize("base,kw", [("batching", {}), ("plain", {"ifft_size": 64, "group_count": 16, "signal_groups": 9}),
+                                     ("batching", {"group_count": 16, "signal_groups": 9})])
+def test_split_bf16_fused_path(base, kw):
+    # 128 x 128 windows with 64 x 64 fields run the fused kernel's tensor-core variant (uint16 frames of the
+    # batching geometry, float32 frames of the plain one, G up to 16); the window output forces the generic
+    # path, whose split-BF16 overlap is the other kernel
+    s = syn.with_(syn.WORKLOADS[base](), **kw)
+    d = syn.make_frames(s, 5, seed=63)
+    out = run_library(s, d["frames"], precision=SPLIT)
+    _check(s, d["frames"], out, coef_tol=SPLIT_COEF_TOL)
+    gen = run_library(s, d["frames"], precision=SPLIT, window=True)
+    fp32 = run_library(s, d["frames"])
+    assert rel_l2(out["coefs"], gen["coefs"]).max() <= SPLIT_COEF_TOL
+    assert rel_l2(out["coefs"], fp32["coefs"]).max() <= SPLIT_COEF_TOL
+    # the fields do not depend on the overlap's precision
+    assert rel_l2(out["fields"], fp32["fields"]).max() <= FIELD_TOL
+    again = run_library(s, d["frames"], precision=SPLIT)
+    assert np.array_equal(out["coefs"].view(np.uint32), again["coefs"].view(np.uint32))
+
+
 def test_split_bf16_serving_geometry_and_determinism():
     s = syn.serving_geometry("512x512_2pol", np.random.default_rng(61))
     d = syn.make_frames(s, 3, seed=62)
