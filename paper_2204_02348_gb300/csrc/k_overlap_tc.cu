@@ -45,10 +45,10 @@ struct TcLayout {
 };
 
 // buf holds the field chunk, then (after the A operand is built from it) the accumulator T[n][r]
-__host__ __device__ inline TcLayout tc_layout(int M, int NP) {
+__host__ __device__ inline TcLayout tc_layout(int M, int NP, int cols) {
     TcLayout L;
-    L.buf = 0;                                             // float2 [M][64]  /  float [NP][129]
-    size_t bufb = (size_t)M * kTcCols * 8;
+    L.buf = 0;                                             // float2 [M][cols]  /  float [NP][129]
+    size_t bufb = (size_t)M * cols * 8;
     const size_t tsb = (size_t)NP * kTsPitch * 4;
     if (tsb > bufb) bufb = tsb;
     L.a = L.buf + ((bufb + 1023) & ~(size_t)1023);         // bf16 [2][128][M]
@@ -61,15 +61,17 @@ __host__ __device__ inline TcLayout tc_layout(int M, int NP) {
 }  // namespace
 
 // R0 R1 R2: the host plan's radices of M fixed at compile time (inverse passes run last radix first), or
-// R0 = 0 for the runtime plan.
-template <int R0, int R1, int R2>
+// R0 = 0 for the runtime plan.  COLS: field columns per chunk (A rows: real parts at i, imaginary parts at
+// 64 + i; with fewer than 64 columns the other rows stay zero), 48 at M = 96 so that no chunk is padded.
+template <int R0, int R1, int R2, int COLS = kTcCols>
 __global__ void __launch_bounds__(kTcThreads, 2) k_yinv_tc(const __grid_constant__ Plan P, const __grid_constant__ Batch B) {
+    static_assert(COLS % 16 == 0 && COLS <= kTcCols && (R0 != 0 || COLS == kTcCols), "chunk width");
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_slot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int M = P.m, G = P.groups, modes = P.modes, NP = P.tc_np;
-    const TcLayout L = tc_layout(M, NP);
+    const int M = P.m, modes = P.modes, NP = P.tc_np;
+    const TcLayout L = tc_layout(M, NP, COLS);
     float2* buf = reinterpret_cast<float2*>(sm + L.buf);
     float* Ts = reinterpret_cast<float*>(sm + L.buf);
     __nv_bfloat16* A = reinterpret_cast<__nv_bfloat16*>(sm + L.a);
@@ -83,6 +85,16 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_yinv_tc(const __grid_constant
         uint4* dst = reinterpret_cast<uint4*>(Bm);
         const int n16 = (2 * NP * M * 2) / 16;
         for (int i = tid; i < n16; i += kTcThreads) dst[i] = __ldg(&src[i]);
+    }
+    if constexpr (COLS < kTcCols) {
+        // the A rows no column maps to (COLS .. 63 and 64 + COLS .. 127) stay zero in both planes
+        constexpr int ZR = kTcCols - COLS;
+        for (int t = tid; t < 2 * 2 * ZR * M; t += kTcThreads) {
+            const int plane = t / (2 * ZR * M), rem = t - plane * 2 * ZR * M;
+            const int rr = rem / M, k = rem - rr * M;
+            const int row = rr < ZR ? COLS + rr : kTcCols + COLS + (rr - ZR);
+            A[(size_t)plane * 128 * M + umma_off(row, k, M)] = __float2bfloat16_rn(0.f);
+        }
     }
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     if (warp == 0) {
@@ -107,28 +119,28 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_yinv_tc(const __grid_constant
         const int f = B.frame0 + fb;
         const float2* g = B.g + (size_t)(fb * P.pols + pol) * M * M;
         float2 acc = make_float2(0.f, 0.f);   // mode tid (modes <= 256)
-        for (int i0 = 0; i0 < M; i0 += kTcCols) {
+        for (int i0 = 0; i0 < M; i0 += COLS) {
             if constexpr (R0 == 0 || R0 * R1 * R2 > 128) {
-                for (int idx = tid; idx < M * kTcCols; idx += kTcThreads) {
-                    const int q = idx >> 6, i = idx & (kTcCols - 1);
-                    buf[plan_pos<R0, R1, R2>(P.pos_m, q) * kTcCols + i] = (i0 + i < M) ? g[(size_t)q * M + i0 + i] : make_float2(0.f, 0.f);
+                for (int idx = tid; idx < M * COLS; idx += kTcThreads) {
+                    const int q = idx / COLS, i = idx % COLS;
+                    buf[plan_pos<R0, R1, R2>(P.pos_m, q) * COLS + i] = (i0 + i < M) ? g[(size_t)q * M + i0 + i] : make_float2(0.f, 0.f);
                 }
             } else {
                 // a small fixed plan leaves the registers for eight loads in flight per thread (at M = 176 the
                 // extra registers cost more than the loads gain)
                 constexpr int MM = R0 * R1 * R2;
-                for (int j0 = tid; j0 < MM * kTcCols; j0 += 8 * kTcThreads) {
+                for (int j0 = tid; j0 < MM * COLS; j0 += 8 * kTcThreads) {
                     float2 v[8];
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
                         const int idx = j0 + u * kTcThreads;
-                        const int q = idx >> 6, i = idx & (kTcCols - 1);
-                        v[u] = (idx < MM * kTcCols && i0 + i < MM) ? g[(size_t)q * MM + i0 + i] : make_float2(0.f, 0.f);
+                        const int q = idx / COLS, i = idx % COLS;
+                        v[u] = (idx < MM * COLS && i0 + i < MM) ? g[(size_t)q * MM + i0 + i] : make_float2(0.f, 0.f);
                     }
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
                         const int idx = j0 + u * kTcThreads;
-                        if (idx < MM * kTcCols) buf[dif_pos<R0, R1, R2>(idx >> 6) * kTcCols + (idx & (kTcCols - 1))] = v[u];
+                        if (idx < MM * COLS) buf[dif_pos<R0, R1, R2>(idx / COLS) * COLS + idx % COLS] = v[u];
                     }
                 }
             }
@@ -136,10 +148,10 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_yinv_tc(const __grid_constant
             if constexpr (R0 == 0) {
                 fft_run<true>(buf, M, P.rad_m, P.nrad_m, 6, kTcCols, P.tw_inv_m, tid, kTcThreads);
             } else {
-                ifft_static<R0, R1, R2, kTcCols, kTcCols, kTcThreads>(buf, P.tw_inv_m, tid);
+                ifft_static<R0, R1, R2, COLS, COLS, kTcThreads>(buf, P.tw_inv_m, tid);
             }
-            for (int idx = tid; idx < M * kTcCols; idx += kTcThreads) {
-                const int j = idx >> 6, i = idx & (kTcCols - 1);
+            for (int idx = tid; idx < M * COLS; idx += kTcThreads) {
+                const int j = idx / COLS, i = idx % COLS;
                 if (i0 + i < M) {
                     const float2 e = cmul(cmul(buf[idx], pd.corr_y[j]), pd.corr_x[i0 + i]);
                     buf[idx] = e;
@@ -150,12 +162,12 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_yinv_tc(const __grid_constant
             }
             __syncthreads();
             // A operand: rows r = i (real part) and 64 + i (imaginary part), K = j; 8 consecutive j per task
-            for (int t = tid; t < kTcCols * (M / 8); t += kTcThreads) {
-                const int i = t & (kTcCols - 1), jb = t >> 6;
+            for (int t = tid; t < COLS * (M / 8); t += kTcThreads) {
+                const int i = t % COLS, jb = t / COLS;
                 __align__(16) __nv_bfloat16 hr[8], hi_[8], lr[8], li[8];
 #pragma unroll
                 for (int c = 0; c < 8; ++c) {
-                    const float2 e = buf[(8 * jb + c) * kTcCols + i];
+                    const float2 e = buf[(8 * jb + c) * COLS + i];
                     const __nv_bfloat16 xr = __float2bfloat16_rn(e.x), xi = __float2bfloat16_rn(e.y);
                     hr[c] = xr;
                     hi_[c] = xi;
@@ -205,7 +217,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_yinv_tc(const __grid_constant
                 const int m = P.mode_m[tid], n = P.mode_n[tid];
                 const float* u = pd.hg_x + (size_t)m * M + i0;
                 const float* tr = Ts + n * kTsPitch;
-                const int lim = min(kTcCols, M - i0);
+                const int lim = min(COLS, M - i0);
                 float sr = 0.f, si = 0.f;
                 for (int i = 0; i < lim; ++i) {
                     const float w = __ldg(&u[i]);
@@ -234,13 +246,13 @@ cudaError_t tc_init() {
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(k_yinv_tc<0, 0, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024 - 1024)))
         return e;
-    if ((e = cudaFuncSetAttribute(k_yinv_tc<8, 4, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024 - 1024)))
+    if ((e = cudaFuncSetAttribute(k_yinv_tc<8, 4, 3, 48>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024 - 1024)))
         return e;
     return cudaFuncSetAttribute(k_yinv_tc<16, 11, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024 - 1024);
 }
 
 cudaError_t launch_yinv_tc(const Plan& P, const Batch& B, cudaStream_t st) {
-    const TcLayout L = tc_layout(P.m, P.tc_np);
+    const TcLayout L = tc_layout(P.m, P.tc_np, kTcCols);
     dim3 grid(P.pols, B.count < 65535 ? B.count : 65535);
     // the field sizes of the precision (96 = 8 4 3) and large (176 = 16 11) configurations run with their
     // radix plan fixed at compile time
@@ -248,8 +260,8 @@ cudaError_t launch_yinv_tc(const Plan& P, const Batch& B, cudaStream_t st) {
         const int n = c > 1 ? 3 : 2;
         return P.nrad_m == n && P.rad_m[0] == a && P.rad_m[1] == b && (n == 2 || P.rad_m[2] == c);
     };
-    if (P.m == 96 && plan_is(8, 4, 3))
-        k_yinv_tc<8, 4, 3><<<grid, kTcThreads, L.bytes, st>>>(P, B);
+    if (P.m == 96 && plan_is(8, 4, 3))   // two chunks of 48 columns
+        k_yinv_tc<8, 4, 3, 48><<<grid, kTcThreads, tc_layout(P.m, P.tc_np, 48).bytes, st>>>(P, B);
     else if (P.m == 176 && plan_is(16, 11, 1))
         k_yinv_tc<16, 11, 1><<<grid, kTcThreads, L.bytes, st>>>(P, B);
     else
