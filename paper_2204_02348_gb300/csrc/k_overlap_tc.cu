@@ -1,18 +1,17 @@
 // Split-BF16 tensor-core variant of the generic path's last kernel (pipeline step 2 along y, tilt and defocus
 // removal, and the HG modal decomposition of step 3).
 //
-// One block per (frame, polarisation) window, 64 field columns per chunk.  After the y inverse transform and
-// the correction, the chunk's field E[j][i] (FP32) is split into bfloat16 hi + lo parts and written as the A
-// operand of a 128 x NP x M contraction (rows: real and imaginary parts of the 64 columns; K: the field row
-// j), whose B operand holds u_n(y'_j) dy' as bfloat16 hi + lo (host-built, FP64 -> bf16).  One elected thread
+// One block per (frame, polarisation) window, 64 field columns per chunk (48 at M = 96).  After the y inverse
+// transform and the correction, the chunk's field E[j][i] (FP32) is split into bfloat16 hi + lo parts and
+// written as the A operand of a 128 x NP x M contraction (rows: real parts of the chunk's columns at i,
+// imaginary parts at 64 + i; K: the field row j), whose B operand holds u_n(y'_j) dy' as bfloat16 hi + lo
+// (host-built, FP64 -> bf16).  One elected thread
 // issues the three products hi*hi + hi*lo + lo*hi per 16-wide K step with tcgen05.mma (kind::f16, FP32
 // accumulation in tensor memory) and commits them to an mbarrier; the four warps of the first warpgroup read
 // the 128 x NP accumulator back with tcgen05.ld into shared memory, and one thread per mode finishes the
 // second (x) contraction on CUDA cores in a fixed order.  The lo*lo product is below FP32 rounding of the result and is dropped.
 //
-// Operands use the no-swizzle K-major canonical layout: 8-row x 16-byte core matrices stored contiguously,
-// core (rb, kb) at (rb * K/8 + kb) * 128 bytes, so the descriptor's leading-dimension offset (between cores
-// along K) is 128 bytes and its stride-dimension offset (between 8-row groups) is 16 K bytes.
+// Operands use the no-swizzle K-major canonical layout of umma.cuh.
 // Every wait on the mbarrier is bounded; on expiry the window's coefficients are written as NaN, the plan's
 // status word records it, and the block releases its tensor memory before it returns.
 #include <cuda_bf16.h>
