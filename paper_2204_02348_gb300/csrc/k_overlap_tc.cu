@@ -40,7 +40,7 @@ __device__ __forceinline__ bool wait_parity(uint32_t mbar, uint32_t parity) { re
 constexpr int kTsPitch = 129;        // accumulator rows per mode row in shared memory (padded)
 
 struct TcLayout {
-    size_t buf, a, b, bytes;
+    size_t buf, a, b, c, bytes;
 };
 
 // buf holds the field chunk, then (after the A operand is built from it) the accumulator T[n][r]
@@ -52,7 +52,8 @@ __host__ __device__ inline TcLayout tc_layout(int M, int NP, int cols) {
     if (tsb > bufb) bufb = tsb;
     L.a = L.buf + ((bufb + 1023) & ~(size_t)1023);         // bf16 [2][128][M]
     L.b = L.a + (size_t)2 * 128 * M * 2;                    // bf16 [2][NP][M]
-    L.bytes = L.b + (size_t)2 * NP * M * 2;
+    L.c = L.b + (size_t)2 * NP * M * 2;                     // float2 [2][M]: correction along x, then y
+    L.bytes = L.c + (size_t)2 * M * 8;
     L.bytes = (L.bytes + 1023) & ~(size_t)1023;
     return L;
 }
@@ -75,8 +76,13 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_yinv_tc(const __grid_constant
     float* Ts = reinterpret_cast<float*>(sm + L.buf);
     __nv_bfloat16* A = reinterpret_cast<__nv_bfloat16*>(sm + L.a);
     __nv_bfloat16* Bm = reinterpret_cast<__nv_bfloat16*>(sm + L.b);
+    float2* cxy = reinterpret_cast<float2*>(sm + L.c);
     const int pol = blockIdx.x;
     const PolDev& pd = P.pol[pol];
+    for (int i = tid; i < M; i += kTcThreads) {
+        cxy[i] = pd.corr_x[i];
+        cxy[M + i] = pd.corr_y[i];
+    }
 
     // B operand (static per polarisation): 16-byte copies
     {
@@ -152,7 +158,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_yinv_tc(const __grid_constant
             for (int idx = tid; idx < M * COLS; idx += kTcThreads) {
                 const int j = idx / COLS, i = idx % COLS;
                 if (i0 + i < M) {
-                    const float2 e = cmul(cmul(buf[idx], pd.corr_y[j]), pd.corr_x[i0 + i]);
+                    const float2 e = cmul(cmul(buf[idx], cxy[M + j]), cxy[i0 + i]);
                     buf[idx] = e;
                     if (B.fields) B.fields[((size_t)(f * P.pols + pol) * M + j) * M + i0 + i] = e;
                 } else {

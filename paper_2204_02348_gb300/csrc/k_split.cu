@@ -230,10 +230,21 @@ __global__ void __launch_bounds__(kThreads, (N == 256 && LOGR == 4 && MR0 != 0) 
     float2* bufN = smem;
     float2* bufM = smem + (size_t)N * es;
     float2* twN = bufM + (size_t)M * es;
+    float2* phx = twN + N;                       // [M] beam-centre phase along x
+    float2* phy = phx + M;                       // [R] along y, this block's box rows
+    int* mlo = reinterpret_cast<int*>(phy + R);  // [R] kept column range of this block's box rows
+    int* mhi = mlo + R;
     for (int i = tid; i < N; i += kThreads) twN[i] = P.tw_fwd_n[i];
     const int pol = blockIdx.y;
     const PolDev& pd = P.pol[pol];
     const int q0 = blockIdx.x * R;
+    for (int i = tid; i < M; i += kThreads) phx[i] = pd.phase_x[i];
+    for (int i = tid; i < R; i += kThreads) {
+        const bool in = q0 + i < M;
+        phy[i] = in ? pd.phase_y[q0 + i] : make_float2(0.f, 0.f);
+        mlo[i] = in ? pd.mask_lo[q0 + i] : 1;
+        mhi[i] = in ? pd.mask_hi[q0 + i] : 0;
+    }
     for (int fb = blockIdx.z; fb < B.count; fb += gridDim.z) {
         const int f = B.frame0 + fb;
         const float2* r1 = B.r1 + (size_t)(fb * P.pols + pol) * M * N;
@@ -267,10 +278,10 @@ __global__ void __launch_bounds__(kThreads, (N == 256 && LOGR == 4 && MR0 != 0) 
             const int q = q0 + row;
             float2 v = make_float2(0.f, 0.f);
             if (q < M) {
-                if (pp >= pd.mask_lo[q] && pp <= pd.mask_hi[q]) {
+                if (pp >= mlo[row] && pp <= mhi[row]) {
                     int kx = (pd.klx + pp) % N;
                     if (kx < 0) kx += N;
-                    v = cmul(cmul(bufN[dif_pos<R0, R1, R2>(kx) * es + row], pd.phase_x[pp]), pd.phase_y[q]);
+                    v = cmul(cmul(bufN[dif_pos<R0, R1, R2>(kx) * es + row], phx[pp]), phy[row]);
                 }
                 if (B.window) B.window[((size_t)(f * P.pols + pol) * M + q) * M + pp] = v;
             }
@@ -301,7 +312,7 @@ template <int N, int R0, int R1, int R2, int LOGR>
 static void launch_xs(const Plan& P, const Batch& B, int zf, cudaStream_t st) {
     constexpr int R = 1 << LOGR;
     dim3 g((P.m + R - 1) / R, P.pols, zf);
-    const size_t sm = ((size_t)(N + P.m) * (R + 1) + N) * sizeof(float2);
+    const size_t sm = ((size_t)(N + P.m) * (R + 1) + N + P.m + 2 * R) * sizeof(float2);
     // the precision (256: M = 96) and large (512: M = 176) configurations also fix the inverse plan
     if constexpr (N == 256) {
         if (P.m == 96 && m_plan_is(P, 8, 4, 3)) {
@@ -345,8 +356,13 @@ __global__ void __launch_bounds__(kThreads, MR0 == 0 ? 2 : 3) k_yinv(const __gri
     // n + 2 (zero beyond G); [M/2 + 1][nbk]
     const int nbk = 2 * ((G + 3) / 4), hm = M / 2;
     float2* u2 = tp + (size_t)std::max(G, 1) * kChunkI;
+    float2* cxy = u2 + (size_t)(hm + 1) * nbk;   // [2][M] correction phases along x, then y
     const int pol = blockIdx.x;
     const PolDev& pd = P.pol[pol];
+    for (int i = tid; i < M; i += nthr) {
+        cxy[i] = pd.corr_x[i];
+        cxy[M + i] = pd.corr_y[i];
+    }
     for (int t = tid; t < (hm + 1) * nbk; t += nthr) {
         const int j = t / nbk, k = t - j * nbk;
         const int na = 4 * (k >> 1) + (k & 1), nb = na + 2;
@@ -380,7 +396,7 @@ __global__ void __launch_bounds__(kThreads, MR0 == 0 ? 2 : 3) k_yinv(const __gri
             for (int idx = tid; idx < M * kChunkI; idx += nthr) {
                 const int j = idx >> 5, i = idx & (kChunkI - 1);
                 if (i0 + i < M) {
-                    const float2 e = cmul(cmul(buf[idx], pd.corr_y[j]), pd.corr_x[i0 + i]);
+                    const float2 e = cmul(cmul(buf[idx], cxy[M + j]), cxy[i0 + i]);
                     buf[idx] = e;
                     if (B.fields) B.fields[((size_t)(f * P.pols + pol) * M + j) * M + i0 + i] = e;
                 } else {
@@ -525,7 +541,7 @@ cudaError_t launch_last(const Plan& P, const Batch& B, cudaStream_t st, StageTim
     const int zf = std::min(B.count, 65535);
     dim3 g3(P.pols, zf);
     const size_t sm3 = ((size_t)(P.m + std::max(P.groups, 1)) * kChunkI +
-                        (size_t)(P.m / 2 + 1) * 2 * ((P.groups + 3) / 4)) * sizeof(float2);
+                        (size_t)(P.m / 2 + 1) * 2 * ((P.groups + 3) / 4) + 2 * (size_t)P.m) * sizeof(float2);
     if (tc_supported(P)) {
         if (tm) tm->start(st);
         cudaError_t e = launch_yinv_tc(P, B, st);
