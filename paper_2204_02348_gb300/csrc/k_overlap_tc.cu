@@ -40,11 +40,12 @@ __device__ __forceinline__ bool wait_parity(uint32_t mbar, uint32_t parity) { re
 constexpr int kTsPitch = 129;        // accumulator rows per mode row in shared memory (padded)
 
 struct TcLayout {
-    size_t buf, a, b, c, bytes;
+    size_t buf, a, b, c, h, bytes;
 };
 
 // buf holds the field chunk, then (after the A operand is built from it) the accumulator T[n][r]
-__host__ __device__ inline TcLayout tc_layout(int M, int NP, int cols) {
+// hg_rows: modes of the staged x table u_m(x'_i) dx' ([hg_rows][M + 1] floats; 0 = read from global memory)
+__host__ __device__ inline TcLayout tc_layout(int M, int NP, int cols, int hg_rows) {
     TcLayout L;
     L.buf = 0;                                             // float2 [M][cols]  /  float [NP][129]
     size_t bufb = (size_t)M * cols * 8;
@@ -53,7 +54,8 @@ __host__ __device__ inline TcLayout tc_layout(int M, int NP, int cols) {
     L.a = L.buf + ((bufb + 1023) & ~(size_t)1023);         // bf16 [2][128][M]
     L.b = L.a + (size_t)2 * 128 * M * 2;                    // bf16 [2][NP][M]
     L.c = L.b + (size_t)2 * NP * M * 2;                     // float2 [2][M]: correction along x, then y
-    L.bytes = L.c + (size_t)2 * M * 8;
+    L.h = L.c + (size_t)2 * M * 8;
+    L.bytes = L.h + (size_t)hg_rows * (M + 1) * 4;
     L.bytes = (L.bytes + 1023) & ~(size_t)1023;
     return L;
 }
@@ -71,17 +73,25 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_yinv_tc(const __grid_constant
     __shared__ uint32_t tmem_slot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int M = P.m, modes = P.modes, NP = P.tc_np;
-    const TcLayout L = tc_layout(M, NP, COLS);
+    // compile-time plans stage u_m(x'_i) dx' as [G][M + 1] (odd pitch: the modes of a warp on distinct banks)
+    const TcLayout L = tc_layout(M, NP, COLS, R0 != 0 ? P.groups : 0);
     float2* buf = reinterpret_cast<float2*>(sm + L.buf);
     float* Ts = reinterpret_cast<float*>(sm + L.buf);
     __nv_bfloat16* A = reinterpret_cast<__nv_bfloat16*>(sm + L.a);
     __nv_bfloat16* Bm = reinterpret_cast<__nv_bfloat16*>(sm + L.b);
     float2* cxy = reinterpret_cast<float2*>(sm + L.c);
+    float* hgxs = reinterpret_cast<float*>(sm + L.h);
     const int pol = blockIdx.x;
     const PolDev& pd = P.pol[pol];
     for (int i = tid; i < M; i += kTcThreads) {
         cxy[i] = pd.corr_x[i];
         cxy[M + i] = pd.corr_y[i];
+    }
+    if constexpr (R0 != 0) {
+        for (int t = tid; t < P.groups * M; t += kTcThreads) {
+            const int n = t / M, i = t - n * M;
+            hgxs[n * (M + 1) + i] = pd.hg_x[t];
+        }
     }
 
     // B operand (static per polarisation): 16-byte copies
@@ -220,14 +230,22 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_yinv_tc(const __grid_constant
             // c_mn += sum_i u_m(x'_i) T[n][i] over this chunk's columns, one mode per thread, fixed order
             if (tid < modes) {
                 const int m = P.mode_m[tid], n = P.mode_n[tid];
-                const float* u = pd.hg_x + (size_t)m * M + i0;
                 const float* tr = Ts + n * kTsPitch;
                 const int lim = min(COLS, M - i0);
                 float sr = 0.f, si = 0.f;
-                for (int i = 0; i < lim; ++i) {
-                    const float w = __ldg(&u[i]);
-                    sr = fmaf(w, tr[i], sr);
-                    si = fmaf(w, tr[64 + i], si);
+                if constexpr (R0 != 0) {
+                    const float* u = hgxs + (size_t)m * (M + 1) + i0;
+                    for (int i = 0; i < lim; ++i) {
+                        sr = fmaf(u[i], tr[i], sr);
+                        si = fmaf(u[i], tr[64 + i], si);
+                    }
+                } else {
+                    const float* u = pd.hg_x + (size_t)m * M + i0;
+                    for (int i = 0; i < lim; ++i) {
+                        const float w = __ldg(&u[i]);
+                        sr = fmaf(w, tr[i], sr);
+                        si = fmaf(w, tr[64 + i], si);
+                    }
                 }
                 acc.x += sr;
                 acc.y += si;
@@ -257,7 +275,7 @@ cudaError_t tc_init() {
 }
 
 cudaError_t launch_yinv_tc(const Plan& P, const Batch& B, cudaStream_t st) {
-    const TcLayout L = tc_layout(P.m, P.tc_np, kTcCols);
+    const TcLayout L = tc_layout(P.m, P.tc_np, kTcCols, 0);
     dim3 grid(P.pols, B.count < 65535 ? B.count : 65535);
     // the field sizes of the precision (96 = 8 4 3) and large (176 = 16 11) configurations run with their
     // radix plan fixed at compile time
@@ -266,9 +284,9 @@ cudaError_t launch_yinv_tc(const Plan& P, const Batch& B, cudaStream_t st) {
         return P.nrad_m == n && P.rad_m[0] == a && P.rad_m[1] == b && (n == 2 || P.rad_m[2] == c);
     };
     if (P.m == 96 && plan_is(8, 4, 3))   // two chunks of 48 columns
-        k_yinv_tc<8, 4, 3, 48><<<grid, kTcThreads, tc_layout(P.m, P.tc_np, 48).bytes, st>>>(P, B);
+        k_yinv_tc<8, 4, 3, 48><<<grid, kTcThreads, tc_layout(P.m, P.tc_np, 48, P.groups).bytes, st>>>(P, B);
     else if (P.m == 176 && plan_is(16, 11, 1))
-        k_yinv_tc<16, 11, 1><<<grid, kTcThreads, L.bytes, st>>>(P, B);
+        k_yinv_tc<16, 11, 1><<<grid, kTcThreads, tc_layout(P.m, P.tc_np, kTcCols, P.groups).bytes, st>>>(P, B);
     else
         k_yinv_tc<0, 0, 0><<<grid, kTcThreads, L.bytes, st>>>(P, B);
     return cudaGetLastError();

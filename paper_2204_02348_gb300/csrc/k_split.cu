@@ -357,11 +357,19 @@ __global__ void __launch_bounds__(kThreads, MR0 == 0 ? 2 : 3) k_yinv(const __gri
     const int nbk = 2 * ((G + 3) / 4), hm = M / 2;
     float2* u2 = tp + (size_t)std::max(G, 1) * kChunkI;
     float2* cxy = u2 + (size_t)(hm + 1) * nbk;   // [2][M] correction phases along x, then y
+    // compile-time plans: u_m(x'_i) dx' as [G][M + 1] (the odd pitch puts the modes of a warp on distinct banks)
+    float* hgxs = reinterpret_cast<float*>(cxy + 2 * M);
     const int pol = blockIdx.x;
     const PolDev& pd = P.pol[pol];
     for (int i = tid; i < M; i += nthr) {
         cxy[i] = pd.corr_x[i];
         cxy[M + i] = pd.corr_y[i];
+    }
+    if constexpr (MR0 != 0) {
+        for (int t = tid; t < G * M; t += nthr) {
+            const int n = t / M, i = t - n * M;
+            hgxs[n * (M + 1) + i] = pd.hg_x[t];
+        }
     }
     for (int t = tid; t < (hm + 1) * nbk; t += nthr) {
         const int j = t / nbk, k = t - j * nbk;
@@ -445,13 +453,21 @@ __global__ void __launch_bounds__(kThreads, MR0 == 0 ? 2 : 3) k_yinv(const __gri
                 for (int kk = 0; kk < 3; ++kk) {
                     const int k = tid + kk * nthr;
                     if (k < modes) {
-                        const float* u = pd.hg_x + (size_t)P.mode_m[k] * M + i0;
                         const float2* t = tp + P.mode_n[k] * kChunkI;
                         const int lim = min(kChunkI, M - i0);
-                        for (int i = 0; i < lim; ++i) {
-                            const float w = __ldg(&u[i]);
-                            acc[kk].x = fmaf(w, t[i].x, acc[kk].x);
-                            acc[kk].y = fmaf(w, t[i].y, acc[kk].y);
+                        if constexpr (MR0 != 0) {
+                            const float* u = hgxs + (size_t)P.mode_m[k] * (M + 1) + i0;
+                            for (int i = 0; i < lim; ++i) {
+                                acc[kk].x = fmaf(u[i], t[i].x, acc[kk].x);
+                                acc[kk].y = fmaf(u[i], t[i].y, acc[kk].y);
+                            }
+                        } else {
+                            const float* u = pd.hg_x + (size_t)P.mode_m[k] * M + i0;
+                            for (int i = 0; i < lim; ++i) {
+                                const float w = __ldg(&u[i]);
+                                acc[kk].x = fmaf(w, t[i].x, acc[kk].x);
+                                acc[kk].y = fmaf(w, t[i].y, acc[kk].y);
+                            }
                         }
                     }
                 }
@@ -549,11 +565,12 @@ cudaError_t launch_last(const Plan& P, const Batch& B, cudaStream_t st, StageTim
         if (e != cudaSuccess) return e;
         return cudaGetLastError();
     }
+    const size_t sm3s = sm3 + (size_t)P.groups * (P.m + 1) * sizeof(float);   // with the staged x table
     if (tm) tm->start(st);
     if (P.m == 96 && m_plan_is(P, 8, 4, 3))
-        k_yinv<8, 4, 3><<<g3, kThreads, sm3, st>>>(P, B);
+        k_yinv<8, 4, 3><<<g3, kThreads, sm3s, st>>>(P, B);
     else if (P.m == 176 && m_plan_is(P, 16, 11, 1))
-        k_yinv<16, 11, 1><<<g3, kThreads, sm3, st>>>(P, B);
+        k_yinv<16, 11, 1><<<g3, kThreads, sm3s, st>>>(P, B);
     else
         k_yinv<0, 0, 0><<<g3, kThreads, sm3, st>>>(P, B);
     if (tm) tm->stop(st, "k_yinv");
