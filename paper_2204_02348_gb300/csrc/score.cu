@@ -89,15 +89,27 @@ __global__ void __launch_bounds__(kSThreads, 2) k_xfwd(const __grid_constant__ P
 // MR0 MR1 MR2: the radix plan of M fixed at compile time (then 16 rows per block, logr = 4), or MR0 = 0 for
 // the runtime plan.
 template <int MR0, int MR1, int MR2>
-__global__ void __launch_bounds__(kSThreads, 2) k_xinv_sel(const __grid_constant__ Plan P, const __grid_constant__ Superset S,
+__global__ void __launch_bounds__(kSThreads, MR0 == 0 ? 2 : 3) k_xinv_sel(const __grid_constant__ Plan P, const __grid_constant__ Superset S,
                                                            const float2* __restrict__ xs, float2* __restrict__ g,
                                                            int count, int qoff0, int qoff1, int poff0, int poff1, int logr) {
-    extern __shared__ float2 smem[];
+    extern __shared__ float2 smem[];   // [M][R + 1] tile, then the phase and mask tables
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int R = 1 << logr, es = R + 1, M = P.m;
     const int pol = blockIdx.y, q0 = blockIdx.x * R;
     const int qoff = pol ? qoff1 : qoff0, poff = pol ? poff1 : poff0;
     const PolDev& pd = P.pol[pol];
+    float2* phx = smem + (size_t)M * es;         // [M] beam-centre phase along x
+    float2* phy = phx + M;                       // [R] along y, this block's box rows
+    int* mlo = reinterpret_cast<int*>(phy + R);  // [R] kept column range of this block's box rows
+    int* mhi = mlo + R;
+    for (int i = tid; i < M; i += nthr) phx[i] = pd.phase_x[i];
+    for (int i = tid; i < R; i += nthr) {
+        const bool in = q0 + i < M;
+        phy[i] = in ? pd.phase_y[q0 + i] : make_float2(0.f, 0.f);
+        mlo[i] = in ? pd.mask_lo[q0 + i] : 1;
+        mhi[i] = in ? pd.mask_hi[q0 + i] : 0;
+    }
+    __syncthreads();
     for (int fb = blockIdx.z; fb < count; fb += gridDim.z) {
         const float2* src = xs + (size_t)(fb * P.pols + pol) * S.ms * S.msx;
         // eight independent loads in flight per thread before their shared-memory stores
@@ -109,7 +121,7 @@ __global__ void __launch_bounds__(kSThreads, 2) k_xinv_sel(const __grid_constant
                 const int row = idx / M, p = idx - row * M;
                 const int q = q0 + row;
                 v[u] = make_float2(0.f, 0.f);
-                if (idx < R * M && q < M && p >= pd.mask_lo[q] && p <= pd.mask_hi[q])
+                if (idx < R * M && q < M && p >= mlo[row] && p <= mhi[row])
                     v[u] = src[(size_t)(qoff + q) * S.msx + poff + p];
             }
 #pragma unroll
@@ -119,7 +131,7 @@ __global__ void __launch_bounds__(kSThreads, 2) k_xinv_sel(const __grid_constant
                     const int row = idx / M, p = idx - row * M;
                     const int q = q0 + row;
                     float2 w = make_float2(0.f, 0.f);
-                    if (q < M && p >= pd.mask_lo[q] && p <= pd.mask_hi[q]) w = cmul(cmul(v[u], pd.phase_x[p]), pd.phase_y[q]);
+                    if (q < M && p >= mlo[row] && p <= mhi[row]) w = cmul(cmul(v[u], phx[p]), phy[row]);
                     smem[plan_pos<MR0, MR1, MR2>(P.pos_m, p) * es + row] = w;
                 }
             }
@@ -316,10 +328,10 @@ extern "C" int dh_score_settings(dh_handle h, const void* d_frames, int dtype, i
             if (tm) tm->start(st);
             // the large configuration's field size (176 = 16 11) runs with its inverse plan fixed at compile time
             if (M == 176 && R == 16 && Pc.nrad_m == 2 && Pc.rad_m[0] == 16 && Pc.rad_m[1] == 11)
-                dhk::k_xinv_sel<16, 11, 1><<<gi, dhk::kSThreads, (size_t)M * (R + 1) * sizeof(float2), st>>>(Pc, S, xs, gbuf, n, qo[0], qo[1],
+                dhk::k_xinv_sel<16, 11, 1><<<gi, dhk::kSThreads, ((size_t)M * (R + 1) + M + 2 * R) * sizeof(float2), st>>>(Pc, S, xs, gbuf, n, qo[0], qo[1],
                                                                                               po[0], po[1], logr);
             else
-                dhk::k_xinv_sel<0, 0, 0><<<gi, dhk::kSThreads, (size_t)M * (R + 1) * sizeof(float2), st>>>(Pc, S, xs, gbuf, n, qo[0], qo[1],
+                dhk::k_xinv_sel<0, 0, 0><<<gi, dhk::kSThreads, ((size_t)M * (R + 1) + M + 2 * R) * sizeof(float2), st>>>(Pc, S, xs, gbuf, n, qo[0], qo[1],
                                                                                               po[0], po[1], logr);
             if (tm) tm->stop(st, "k_xinv_sel");
             e = cudaGetLastError();
