@@ -68,6 +68,30 @@ __global__ void __launch_bounds__(kThreads, 2) k_ypass(const __grid_constant__ P
     }
 }
 
+// Four consecutive pixels as one load (8 bytes of uint16, 16 bytes of float32) and their values as float.
+template <typename T>
+struct Pix4;
+template <>
+struct Pix4<uint16_t> {
+    using type = uint2;
+    __device__ __forceinline__ static void unpack(uint2 w, float* p) {
+        p[0] = (float)(w.x & 0xFFFFu);
+        p[1] = (float)(w.x >> 16);
+        p[2] = (float)(w.y & 0xFFFFu);
+        p[3] = (float)(w.y >> 16);
+    }
+};
+template <>
+struct Pix4<float> {
+    using type = float4;
+    __device__ __forceinline__ static void unpack(float4 w, float* p) {
+        p[0] = w.x;
+        p[1] = w.y;
+        p[2] = w.z;
+        p[3] = w.w;
+    }
+};
+
 // k_ypass for the power-of-two windows, with the host plan's radix sequence fixed at compile time (128: 16 x 8,
 // 256: 16 x 16, 512: 8 x 8 x 8, 1024: 16 x 8 x 8): no runtime radix dispatch, twiddles staged in shared
 // memory, 2^LOGC column pairs per block, three blocks per SM.  Same inputs, outputs and arithmetic order as
@@ -88,28 +112,72 @@ __global__ void __launch_bounds__(kThreads, 3) k_ypass_s(const __grid_constant__
     for (int fb = blockIdx.z; fb < B.count; fb += gridDim.z) {
         const int f = B.frame0 + fb;
         const T* fr = (const T*)B.src + (size_t)f * P.width * P.height;
-        // eight pixel pairs in flight per thread before their shared-memory stores
-        for (int i0 = tid; i0 < N * C; i0 += 8 * kThreads) {
-            T a[8], b[8];
+        if (((pd.ox + x0) & 3) == 0 && (P.width & 3) == 0) {
+            // the block's columns start on a 4-pixel boundary: four pixels of each column group per load, eight
+            // (uint16) or four (float32) such load pairs in flight per thread
+            using V4 = typename Pix4<T>::type;
+            constexpr int LB = sizeof(T) == 2 ? 8 : 4, Q = C / 4;
+            for (int i0 = tid; i0 < N * Q; i0 += LB * kThreads) {
+                V4 a[LB], b[LB];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int idx = i0 + u * kThreads;
-                const int y = idx >> LOGC, c = idx & (C - 1);
-                const T* row = fr + (size_t)(pd.oy + y) * P.width + pd.ox + x0 + c;
-                a[u] = row[0];
-                b[u] = row[half];
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int idx = i0 + u * kThreads;
-                float2 v = make_float2(to_f(a[u]), to_f(b[u]));
-                if (pd.cal) {
-                    const int y = idx >> LOGC, c = idx & (C - 1);
-                    const float* k = pd.cal + (size_t)y * N + x0 + c;
-                    v.x *= __ldg(k);
-                    v.y *= __ldg(k + half);
+                for (int u = 0; u < LB; ++u) {
+                    const int idx = i0 + u * kThreads;
+                    if (idx < N * Q) {
+                        const int y = idx / Q, c = (idx % Q) * 4;
+                        const T* row = fr + (size_t)(pd.oy + y) * P.width + pd.ox + x0 + c;
+                        a[u] = *reinterpret_cast<const V4*>(row);
+                        b[u] = *reinterpret_cast<const V4*>(row + half);
+                    }
                 }
-                smem[idx] = v;
+#pragma unroll
+                for (int u = 0; u < LB; ++u) {
+                    const int idx = i0 + u * kThreads;
+                    if (idx < N * Q) {
+                        const int y = idx / Q, c = (idx % Q) * 4;
+                        float pa[4], pb[4];
+                        Pix4<T>::unpack(a[u], pa);
+                        Pix4<T>::unpack(b[u], pb);
+                        float2 v[4];
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) v[e] = make_float2(pa[e], pb[e]);
+                        if (pd.cal) {
+                            const float* k = pd.cal + (size_t)y * N + x0 + c;
+#pragma unroll
+                            for (int e = 0; e < 4; ++e) {
+                                v[e].x *= __ldg(k + e);
+                                v[e].y *= __ldg(k + half + e);
+                            }
+                        }
+                        float4* d = reinterpret_cast<float4*>(smem + y * C + c);
+                        d[0] = make_float4(v[0].x, v[0].y, v[1].x, v[1].y);
+                        d[1] = make_float4(v[2].x, v[2].y, v[3].x, v[3].y);
+                    }
+                }
+            }
+        } else {
+            // eight pixel pairs in flight per thread before their shared-memory stores
+            for (int i0 = tid; i0 < N * C; i0 += 8 * kThreads) {
+                T a[8], b[8];
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int idx = i0 + u * kThreads;
+                    const int y = idx >> LOGC, c = idx & (C - 1);
+                    const T* row = fr + (size_t)(pd.oy + y) * P.width + pd.ox + x0 + c;
+                    a[u] = row[0];
+                    b[u] = row[half];
+                }
+#pragma unroll
+                for (int u = 0; u < 8; ++u) {
+                    const int idx = i0 + u * kThreads;
+                    float2 v = make_float2(to_f(a[u]), to_f(b[u]));
+                    if (pd.cal) {
+                        const int y = idx >> LOGC, c = idx & (C - 1);
+                        const float* k = pd.cal + (size_t)y * N + x0 + c;
+                        v.x *= __ldg(k);
+                        v.y *= __ldg(k + half);
+                    }
+                    smem[idx] = v;
+                }
             }
         }
         __syncthreads();
