@@ -130,32 +130,46 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_yinv_tc(const __grid_constant
     uint32_t phase = 0;
     bool ok = true;
 
+    const bool g16 = ((uintptr_t)B.g & 15) == 0;   // 16-byte loads of the rows (M is even)
     for (int fb = blockIdx.y; fb < B.count; fb += gridDim.y) {
         const int f = B.frame0 + fb;
         const float2* g = B.g + (size_t)(fb * P.pols + pol) * M * M;
         float2 acc = make_float2(0.f, 0.f);   // mode tid (modes <= 256)
         for (int i0 = 0; i0 < M; i0 += COLS) {
-            if constexpr (R0 == 0 || R0 * R1 * R2 > 128) {
-                for (int idx = tid; idx < M * COLS; idx += kTcThreads) {
-                    const int q = idx / COLS, i = idx % COLS;
-                    buf[plan_pos<R0, R1, R2>(P.pos_m, q) * COLS + i] = (i0 + i < M) ? g[(size_t)q * M + i0 + i] : make_float2(0.f, 0.f);
-                }
-            } else {
-                // a small fixed plan leaves the registers for eight loads in flight per thread (at M = 176 the
-                // extra registers cost more than the loads gain)
-                constexpr int MM = R0 * R1 * R2;
-                for (int j0 = tid; j0 < MM * COLS; j0 += 8 * kTcThreads) {
-                    float2 v[8];
+            // a small fixed plan leaves the registers for eight loads in flight per thread, otherwise one at a time
+            constexpr int LB = (R0 != 0 && R0 * R1 * R2 <= 128) ? 8 : 1;
+            if (g16) {
+                // two columns per 16-byte load and store (M, COLS and the chunk start are even)
+                for (int j0 = tid; j0 < M * COLS / 2; j0 += LB * kTcThreads) {
+                    float4 v[LB];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {
+                    for (int u = 0; u < LB; ++u) {
                         const int idx = j0 + u * kTcThreads;
-                        const int q = idx / COLS, i = idx % COLS;
-                        v[u] = (idx < MM * COLS && i0 + i < MM) ? g[(size_t)q * MM + i0 + i] : make_float2(0.f, 0.f);
+                        const int q = idx / (COLS / 2), i = 2 * (idx % (COLS / 2));
+                        v[u] = (idx < M * COLS / 2 && i0 + i < M) ? *reinterpret_cast<const float4*>(g + (size_t)q * M + i0 + i)
+                                                                 : make_float4(0.f, 0.f, 0.f, 0.f);
                     }
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {
+                    for (int u = 0; u < LB; ++u) {
                         const int idx = j0 + u * kTcThreads;
-                        if (idx < MM * COLS) buf[dif_pos<R0, R1, R2>(idx / COLS) * COLS + idx % COLS] = v[u];
+                        if (idx < M * COLS / 2)
+                            *reinterpret_cast<float4*>(buf + plan_pos<R0, R1, R2>(P.pos_m, idx / (COLS / 2)) * COLS +
+                                                       2 * (idx % (COLS / 2))) = v[u];
+                    }
+                }
+            } else {
+                for (int j0 = tid; j0 < M * COLS; j0 += LB * kTcThreads) {
+                    float2 v[LB];
+#pragma unroll
+                    for (int u = 0; u < LB; ++u) {
+                        const int idx = j0 + u * kTcThreads;
+                        const int q = idx / COLS, i = idx % COLS;
+                        v[u] = (idx < M * COLS && i0 + i < M) ? g[(size_t)q * M + i0 + i] : make_float2(0.f, 0.f);
+                    }
+#pragma unroll
+                    for (int u = 0; u < LB; ++u) {
+                        const int idx = j0 + u * kTcThreads;
+                        if (idx < M * COLS) buf[plan_pos<R0, R1, R2>(P.pos_m, idx / COLS) * COLS + idx % COLS] = v[u];
                     }
                 }
             }

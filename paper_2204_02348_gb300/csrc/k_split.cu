@@ -444,24 +444,47 @@ __global__ void __launch_bounds__(kThreads, MR0 == 0 ? 2 : 3) k_yinv(const __gri
         const int na = 4 * (k >> 1) + (k & 1), nb = na + 2;
         u2[t] = make_float2(na < G ? pd.hg_y[(size_t)na * M + j] : 0.f, nb < G ? pd.hg_y[(size_t)nb * M + j] : 0.f);
     }
+    const bool g16 = ((uintptr_t)B.g & 15) == 0;   // 16-byte loads of the rows (M is even)
     for (int fb = blockIdx.y; fb < B.count; fb += gridDim.y) {
         const int f = B.frame0 + fb;
         const float2* g = B.g + (size_t)(fb * P.pols + pol) * M * M;
         float2 acc[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
         for (int i0 = 0; i0 < M; i0 += kChunkI) {
-            // eight independent loads in flight per thread before their shared-memory stores
-            for (int j0 = tid; j0 < M * kChunkI; j0 += 8 * nthr) {
-                float2 v[8];
+            if (g16) {
+                // two columns per 16-byte load and store (M and the chunk start are even), eight loads in flight
+                // per thread before their shared-memory stores
+                for (int j0 = tid; j0 < M * kChunkI / 2; j0 += 8 * nthr) {
+                    float4 v[8];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int idx = j0 + u * nthr;
-                    const int q = idx >> 5, i = idx & (kChunkI - 1);
-                    v[u] = (idx < M * kChunkI && i0 + i < M) ? g[(size_t)q * M + i0 + i] : make_float2(0.f, 0.f);
+                    for (int u = 0; u < 8; ++u) {
+                        const int idx = j0 + u * nthr;
+                        const int q = idx / (kChunkI / 2), i = 2 * (idx % (kChunkI / 2));
+                        v[u] = (idx < M * kChunkI / 2 && i0 + i < M) ? *reinterpret_cast<const float4*>(g + (size_t)q * M + i0 + i)
+                                                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int idx = j0 + u * nthr;
+                        if (idx < M * kChunkI / 2)
+                            *reinterpret_cast<float4*>(buf + plan_pos<MR0, MR1, MR2>(P.pos_m, idx / (kChunkI / 2)) * kChunkI +
+                                                       2 * (idx % (kChunkI / 2))) = v[u];
+                    }
                 }
+            } else {
+                // eight independent loads in flight per thread before their shared-memory stores
+                for (int j0 = tid; j0 < M * kChunkI; j0 += 8 * nthr) {
+                    float2 v[8];
 #pragma unroll
-                for (int u = 0; u < 8; ++u) {
-                    const int idx = j0 + u * nthr;
-                    if (idx < M * kChunkI) buf[plan_pos<MR0, MR1, MR2>(P.pos_m, idx >> 5) * kChunkI + (idx & (kChunkI - 1))] = v[u];
+                    for (int u = 0; u < 8; ++u) {
+                        const int idx = j0 + u * nthr;
+                        const int q = idx >> 5, i = idx & (kChunkI - 1);
+                        v[u] = (idx < M * kChunkI && i0 + i < M) ? g[(size_t)q * M + i0 + i] : make_float2(0.f, 0.f);
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int idx = j0 + u * nthr;
+                        if (idx < M * kChunkI) buf[plan_pos<MR0, MR1, MR2>(P.pos_m, idx >> 5) * kChunkI + (idx & (kChunkI - 1))] = v[u];
+                    }
                 }
             }
             __syncthreads();

@@ -272,7 +272,10 @@ extern "C" int dh_score_settings(dh_handle h, const void* d_frames, int dtype, i
     const size_t per_frame_scratch = ((size_t)ms * N + (size_t)ms * msx + (size_t)M * M) * sizeof(float2) * pols;
     const size_t per_frame_coefs = (size_t)count * per_frame * sizeof(float2);
     const int chunk = chunk_frames(per_frame_scratch + per_frame_coefs, pols, batch, H->device);
-    const size_t spectra_bytes = (per_frame_scratch * chunk + 255) & ~(size_t)255;
+    // superset rows, superset spectra and candidate x-inverse rows, each region starting on a 256-byte boundary
+    const size_t r1s_bytes = ((size_t)chunk * pols * ms * N * sizeof(float2) + 255) & ~(size_t)255;
+    const size_t xs_bytes = ((size_t)chunk * pols * ms * msx * sizeof(float2) + 255) & ~(size_t)255;
+    const size_t spectra_bytes = (r1s_bytes + xs_bytes + (size_t)chunk * pols * M * M * sizeof(float2) + 255) & ~(size_t)255;
     rc = ensure_scratch(H, spectra_bytes + per_frame_coefs * chunk);
     if (rc) {
         cleanup();
@@ -289,8 +292,8 @@ extern "C" int dh_score_settings(dh_handle h, const void* d_frames, int dtype, i
         return e == cudaSuccess ? DH_SUCCESS : cuda_fail(e, "power");
     };
     float2* r1s = (float2*)H->d_scratch;
-    float2* xs = r1s + (size_t)chunk * pols * ms * N;
-    float2* gbuf = xs + (size_t)chunk * pols * ms * msx;
+    float2* xs = (float2*)((char*)H->d_scratch + r1s_bytes);
+    float2* gbuf = (float2*)((char*)H->d_scratch + r1s_bytes + xs_bytes);
     dhk::Plan Psup = P0;                 // the y pass extracts the superset rows
     Psup.m = ms;
     for (int p = 0; p < pols; ++p) Psup.pol[p].kly = kly_min[p];
