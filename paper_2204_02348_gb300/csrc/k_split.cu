@@ -109,6 +109,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_ypass_s(const __grid_constant__
     const int x0 = blockIdx.x * C;
     for (int i = tid; i < N; i += kThreads) tw[i] = P.tw_fwd_n[i];
     static_assert((N * C) % (8 * kThreads) == 0, "whole load batches");
+    const bool r1_16 = ((uintptr_t)B.r1 & 15) == 0;   // M N is even: every window's rows stay 16-byte aligned
     for (int fb = blockIdx.z; fb < B.count; fb += gridDim.z) {
         const int f = B.frame0 + fb;
         const T* fr = (const T*)B.src + (size_t)f * P.width * P.height;
@@ -190,15 +191,31 @@ __global__ void __launch_bounds__(kThreads, 3) k_ypass_s(const __grid_constant__
             __syncthreads();
         }
         float2* r1 = B.r1 + (size_t)(fb * P.pols + pol) * M * N;
-        for (int idx = tid; idx < M * C; idx += kThreads) {
-            const int q = idx >> LOGC, c = idx & (C - 1);
-            int k = (pd.kly + q) % N;
-            if (k < 0) k += N;
-            const int km = (N - k) & (N - 1);
-            const float2 za = smem[dif_pos<R0, R1, R2>(k) * C + c];
-            const float2 zb = smem[dif_pos<R0, R1, R2>(km) * C + c];
-            r1[(size_t)q * N + x0 + c] = make_float2(0.5f * (za.x + zb.x), 0.5f * (za.y - zb.y));
-            r1[(size_t)q * N + x0 + c + half] = make_float2(0.5f * (za.y + zb.y), 0.5f * (zb.x - za.x));
+        if (r1_16) {
+            // two adjacent column pairs per thread: 16-byte shared-memory reads and global writes
+            for (int idx = tid; idx < M * C / 2; idx += kThreads) {
+                const int q = idx / (C / 2), c = 2 * (idx % (C / 2));
+                int k = (pd.kly + q) % N;
+                if (k < 0) k += N;
+                const int km = (N - k) & (N - 1);
+                const float4 za = *reinterpret_cast<const float4*>(smem + dif_pos<R0, R1, R2>(k) * C + c);
+                const float4 zb = *reinterpret_cast<const float4*>(smem + dif_pos<R0, R1, R2>(km) * C + c);
+                *reinterpret_cast<float4*>(r1 + (size_t)q * N + x0 + c) =
+                    make_float4(0.5f * (za.x + zb.x), 0.5f * (za.y - zb.y), 0.5f * (za.z + zb.z), 0.5f * (za.w - zb.w));
+                *reinterpret_cast<float4*>(r1 + (size_t)q * N + x0 + c + half) =
+                    make_float4(0.5f * (za.y + zb.y), 0.5f * (zb.x - za.x), 0.5f * (za.w + zb.w), 0.5f * (zb.z - za.z));
+            }
+        } else {
+            for (int idx = tid; idx < M * C; idx += kThreads) {
+                const int q = idx >> LOGC, c = idx & (C - 1);
+                int k = (pd.kly + q) % N;
+                if (k < 0) k += N;
+                const int km = (N - k) & (N - 1);
+                const float2 za = smem[dif_pos<R0, R1, R2>(k) * C + c];
+                const float2 zb = smem[dif_pos<R0, R1, R2>(km) * C + c];
+                r1[(size_t)q * N + x0 + c] = make_float2(0.5f * (za.x + zb.x), 0.5f * (za.y - zb.y));
+                r1[(size_t)q * N + x0 + c + half] = make_float2(0.5f * (za.y + zb.y), 0.5f * (zb.x - za.x));
+            }
         }
         __syncthreads();
     }
