@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_xpass(const __grid_constant__ P
 // k_xpass with the x transform's radix sequence fixed at compile time (the same plans as k_ypass_s) and its
 // twiddles in shared memory; the M-point inverse keeps the runtime plan.  Same results as k_xpass.
 template <int N, int R0, int R1, int R2, int LOGR, int MR0, int MR1, int MR2>
-__global__ void __launch_bounds__(kThreads, (N == 256 && LOGR == 4 && MR0 != 0) ? 3 : 2) k_xpass_s(const __grid_constant__ Plan P, const __grid_constant__ Batch B) {
+__global__ void __launch_bounds__(kThreads, (N == 256 && LOGR == 4 && MR0 != 0) ? 4 : 2) k_xpass_s(const __grid_constant__ Plan P, const __grid_constant__ Batch B) {
     extern __shared__ float2 smem[];
     const int tid = threadIdx.x, nthr = blockDim.x;
     constexpr int R = 1 << LOGR, es = R + 1, logr = LOGR, logn = (N == 128 ? 7 : N == 256 ? 8 : N == 512 ? 9 : 10);
@@ -429,9 +429,10 @@ static bool launch_xpass_static(const Plan& P, const Batch& B, int zf, cudaStrea
 }
 
 // MR0 MR1 MR2: the radix plan of M fixed at compile time, or MR0 = 0 for the runtime plan.  The compile-time
-// plans fit 85 registers, so three blocks share an SM; the runtime plan needs more and runs two.
+// plans fit 64 registers at M <= 128 (four blocks per SM) and 85 above (three); the runtime plan needs more
+// and runs two.
 template <int MR0, int MR1, int MR2>
-__global__ void __launch_bounds__(kThreads, MR0 == 0 ? 2 : 3) k_yinv(const __grid_constant__ Plan P, const __grid_constant__ Batch B) {
+__global__ void __launch_bounds__(kThreads, MR0 == 0 ? 2 : (MR0 * MR1 * MR2 <= 128 ? 4 : 3)) k_yinv(const __grid_constant__ Plan P, const __grid_constant__ Batch B) {
     extern __shared__ float2 smem[];
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int M = P.m, G = P.groups, modes = P.modes;
