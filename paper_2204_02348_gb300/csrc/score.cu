@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(kSThreads, 2) k_xfwd(const __grid_constant__ P
 // MR0 MR1 MR2: the radix plan of M fixed at compile time (then 16 rows per block, logr = 4), or MR0 = 0 for
 // the runtime plan.
 template <int MR0, int MR1, int MR2>
-__global__ void __launch_bounds__(kSThreads, MR0 == 0 ? 2 : 3) k_xinv_sel(const __grid_constant__ Plan P, const __grid_constant__ Superset S,
+__global__ void __launch_bounds__(kSThreads, MR0 == 0 ? 2 : 4) k_xinv_sel(const __grid_constant__ Plan P, const __grid_constant__ Superset S,
                                                            const float2* __restrict__ xs, float2* __restrict__ g,
                                                            int count, int qoff0, int qoff1, int poff0, int poff1, int logr) {
     extern __shared__ float2 smem[];   // [M][R + 1] tile, then the phase and mask tables
