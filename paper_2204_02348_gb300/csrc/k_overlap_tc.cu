@@ -64,9 +64,10 @@ __host__ __device__ inline TcLayout tc_layout(int M, int NP, int cols, int hg_ro
 
 // R0 R1 R2: the host plan's radices of M fixed at compile time (inverse passes run last radix first), or
 // R0 = 0 for the runtime plan.  COLS: field columns per chunk (A rows: real parts at i, imaginary parts at
-// 64 + i; with fewer than 64 columns the other rows stay zero), 48 at M = 96 so that no chunk is padded.
-template <int R0, int R1, int R2, int COLS = kTcCols>
-__global__ void __launch_bounds__(kTcThreads, 2) k_yinv_tc(const __grid_constant__ Plan P, const __grid_constant__ Batch B) {
+// 64 + i; with fewer than 64 columns the other rows stay zero), 48 at M = 96 so that no chunk is padded.  NT:
+// threads per block; 512 at M = 176, whose shared memory allows one block per SM.
+template <int R0, int R1, int R2, int COLS = kTcCols, int NT = kTcThreads>
+__global__ void __launch_bounds__(NT, NT == kTcThreads ? 2 : 1) k_yinv_tc(const __grid_constant__ Plan P, const __grid_constant__ Batch B) {
     static_assert(COLS % 16 == 0 && COLS <= kTcCols && (R0 != 0 || COLS == kTcCols), "chunk width");
     extern __shared__ __align__(1024) unsigned char sm[];
     __shared__ __align__(8) uint64_t mbar;
@@ -83,12 +84,12 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_yinv_tc(const __grid_constant
     float* hgxs = reinterpret_cast<float*>(sm + L.h);
     const int pol = blockIdx.x;
     const PolDev& pd = P.pol[pol];
-    for (int i = tid; i < M; i += kTcThreads) {
+    for (int i = tid; i < M; i += NT) {
         cxy[i] = pd.corr_x[i];
         cxy[M + i] = pd.corr_y[i];
     }
     if constexpr (R0 != 0) {
-        for (int t = tid; t < P.groups * M; t += kTcThreads) {
+        for (int t = tid; t < P.groups * M; t += NT) {
             const int n = t / M, i = t - n * M;
             hgxs[n * (M + 1) + i] = pd.hg_x[t];
         }
@@ -99,12 +100,12 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_yinv_tc(const __grid_constant
         const uint4* src = reinterpret_cast<const uint4*>(pd.hgy_tc);
         uint4* dst = reinterpret_cast<uint4*>(Bm);
         const int n16 = (2 * NP * M * 2) / 16;
-        for (int i = tid; i < n16; i += kTcThreads) dst[i] = __ldg(&src[i]);
+        for (int i = tid; i < n16; i += NT) dst[i] = __ldg(&src[i]);
     }
     if constexpr (COLS < kTcCols) {
         // the A rows no column maps to (COLS .. 63 and 64 + COLS .. 127) stay zero in both planes
         constexpr int ZR = kTcCols - COLS;
-        for (int t = tid; t < 2 * 2 * ZR * M; t += kTcThreads) {
+        for (int t = tid; t < 2 * 2 * ZR * M; t += NT) {
             const int plane = t / (2 * ZR * M), rem = t - plane * 2 * ZR * M;
             const int rr = rem / M, k = rem - rr * M;
             const int row = rr < ZR ? COLS + rr : kTcCols + COLS + (rr - ZR);
@@ -136,50 +137,51 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_yinv_tc(const __grid_constant
         const float2* g = B.g + (size_t)(fb * P.pols + pol) * M * M;
         float2 acc = make_float2(0.f, 0.f);   // mode tid (modes <= 256)
         for (int i0 = 0; i0 < M; i0 += COLS) {
-            // a small fixed plan leaves the registers for eight loads in flight per thread, otherwise one at a time
-            constexpr int LB = (R0 != 0 && R0 * R1 * R2 <= 128) ? 8 : 1;
+            // loads in flight per thread: eight for a small fixed plan, four for a larger one (one block per SM),
+            // one for the runtime plan
+            constexpr int LB = R0 == 0 ? 1 : (R0 * R1 * R2 <= 128 ? 8 : 4);
             if (g16) {
                 // two columns per 16-byte load and store (M, COLS and the chunk start are even)
-                for (int j0 = tid; j0 < M * COLS / 2; j0 += LB * kTcThreads) {
+                for (int j0 = tid; j0 < M * COLS / 2; j0 += LB * NT) {
                     float4 v[LB];
 #pragma unroll
                     for (int u = 0; u < LB; ++u) {
-                        const int idx = j0 + u * kTcThreads;
+                        const int idx = j0 + u * NT;
                         const int q = idx / (COLS / 2), i = 2 * (idx % (COLS / 2));
                         v[u] = (idx < M * COLS / 2 && i0 + i < M) ? *reinterpret_cast<const float4*>(g + (size_t)q * M + i0 + i)
                                                                  : make_float4(0.f, 0.f, 0.f, 0.f);
                     }
 #pragma unroll
                     for (int u = 0; u < LB; ++u) {
-                        const int idx = j0 + u * kTcThreads;
+                        const int idx = j0 + u * NT;
                         if (idx < M * COLS / 2)
                             *reinterpret_cast<float4*>(buf + plan_pos<R0, R1, R2>(P.pos_m, idx / (COLS / 2)) * COLS +
                                                        2 * (idx % (COLS / 2))) = v[u];
                     }
                 }
             } else {
-                for (int j0 = tid; j0 < M * COLS; j0 += LB * kTcThreads) {
+                for (int j0 = tid; j0 < M * COLS; j0 += LB * NT) {
                     float2 v[LB];
 #pragma unroll
                     for (int u = 0; u < LB; ++u) {
-                        const int idx = j0 + u * kTcThreads;
+                        const int idx = j0 + u * NT;
                         const int q = idx / COLS, i = idx % COLS;
                         v[u] = (idx < M * COLS && i0 + i < M) ? g[(size_t)q * M + i0 + i] : make_float2(0.f, 0.f);
                     }
 #pragma unroll
                     for (int u = 0; u < LB; ++u) {
-                        const int idx = j0 + u * kTcThreads;
+                        const int idx = j0 + u * NT;
                         if (idx < M * COLS) buf[plan_pos<R0, R1, R2>(P.pos_m, idx / COLS) * COLS + idx % COLS] = v[u];
                     }
                 }
             }
             __syncthreads();
             if constexpr (R0 == 0) {
-                fft_run<true>(buf, M, P.rad_m, P.nrad_m, 6, kTcCols, P.tw_inv_m, tid, kTcThreads);
+                fft_run<true>(buf, M, P.rad_m, P.nrad_m, 6, kTcCols, P.tw_inv_m, tid, NT);
             } else {
-                ifft_static<R0, R1, R2, COLS, COLS, kTcThreads>(buf, P.tw_inv_m, tid);
+                ifft_static<R0, R1, R2, COLS, COLS, NT>(buf, P.tw_inv_m, tid);
             }
-            for (int idx = tid; idx < M * COLS; idx += kTcThreads) {
+            for (int idx = tid; idx < M * COLS; idx += NT) {
                 const int j = idx / COLS, i = idx % COLS;
                 if (i0 + i < M) {
                     const float2 e = cmul(cmul(buf[idx], cxy[M + j]), cxy[i0 + i]);
@@ -191,7 +193,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_yinv_tc(const __grid_constant
             }
             __syncthreads();
             // A operand: rows r = i (real part) and 64 + i (imaginary part), K = j; 8 consecutive j per task
-            for (int t = tid; t < COLS * (M / 8); t += kTcThreads) {
+            for (int t = tid; t < COLS * (M / 8); t += NT) {
                 const int i = t % COLS, jb = t / COLS;
                 __align__(16) __nv_bfloat16 hr[8], hi_[8], lr[8], li[8];
 #pragma unroll
@@ -285,7 +287,8 @@ cudaError_t tc_init() {
         return e;
     if ((e = cudaFuncSetAttribute(k_yinv_tc<8, 4, 3, 48>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024 - 1024)))
         return e;
-    return cudaFuncSetAttribute(k_yinv_tc<16, 11, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024 - 1024);
+    return cudaFuncSetAttribute(k_yinv_tc<16, 11, 1, kTcCols, 2 * kTcThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                227 * 1024 - 1024);
 }
 
 cudaError_t launch_yinv_tc(const Plan& P, const Batch& B, cudaStream_t st) {
@@ -300,7 +303,7 @@ cudaError_t launch_yinv_tc(const Plan& P, const Batch& B, cudaStream_t st) {
     if (P.m == 96 && plan_is(8, 4, 3))   // two chunks of 48 columns
         k_yinv_tc<8, 4, 3, 48><<<grid, kTcThreads, tc_layout(P.m, P.tc_np, 48, P.groups).bytes, st>>>(P, B);
     else if (P.m == 176 && plan_is(16, 11, 1))
-        k_yinv_tc<16, 11, 1><<<grid, kTcThreads, tc_layout(P.m, P.tc_np, kTcCols, P.groups).bytes, st>>>(P, B);
+        k_yinv_tc<16, 11, 1, kTcCols, 2 * kTcThreads><<<grid, 2 * kTcThreads, tc_layout(P.m, P.tc_np, kTcCols, P.groups).bytes, st>>>(P, B);
     else
         k_yinv_tc<0, 0, 0><<<grid, kTcThreads, L.bytes, st>>>(P, B);
     return cudaGetLastError();
