@@ -42,13 +42,14 @@ Handle* get_handle(dh_handle h) {
 
 static void release_device(Handle* H) {
     release_pipe(H);
-    if (H->d_blob || H->d_scratch || H->d_hg) {
+    if (H->d_blob || H->d_scratch || H->d_hg || H->d_cand) {
         int cur = -1;
         cudaGetDevice(&cur);
         if (H->device >= 0 && H->device != cur) cudaSetDevice(H->device);
         if (H->d_blob) cudaFree(H->d_blob);
         if (H->d_scratch) cudaFree(H->d_scratch);
         if (H->d_hg) cudaFree(H->d_hg);
+        if (H->d_cand) cudaFree(H->d_cand);
         if (H->device >= 0 && H->device != cur && cur >= 0) cudaSetDevice(cur);
     }
     H->d_blob = nullptr;
@@ -56,6 +57,8 @@ static void release_device(Handle* H) {
     H->scratch_bytes = 0;
     H->d_hg = nullptr;
     H->hg_bytes = 0;
+    H->d_cand = nullptr;
+    H->cand_bytes = 0;
     H->device = -1;
 }
 
@@ -86,43 +89,46 @@ static std::vector<int> pos_table(int len, const std::vector<int>& rad) {
     return pos;
 }
 
-int upload_plan(const Settings& s, const Geometry& g, const Tables& t, void** out_blob, dhk::Plan* out) {
+// The host image of a plan's device tables, with each table's offset in it.
+struct PlanImage {
+    Blob b;
+    size_t o_twn = 0, o_twm = 0, o_pn = 0, o_pm = 0, o_mm = 0, o_mn = 0, o_st = 0, o_bt = 0;
+    size_t o_pol[DH_MAX_POLS][10] = {};
+};
+
+static int build_plan_image(const Geometry& g, const Tables& t, PlanImage* im) {
     if ((int)t.radix_n.size() > dhk::kMaxRadices || (int)t.radix_m.size() > dhk::kMaxRadices)
         return fail(DH_ERROR_INVALIDDIMENSION, "too many radix passes");
-    Blob b;
-    const size_t o_twn = b.put(t.tw_fwd_n.data(), t.tw_fwd_n.size() * 4);
-    const size_t o_twm = b.put(t.tw_inv_m.data(), t.tw_inv_m.size() * 4);
+    Blob& b = im->b;
+    im->o_twn = b.put(t.tw_fwd_n.data(), t.tw_fwd_n.size() * 4);
+    im->o_twm = b.put(t.tw_inv_m.data(), t.tw_inv_m.size() * 4);
     std::vector<int> pn = pos_table(g.n, t.radix_n), pm = pos_table(g.m, t.radix_m);
-    const size_t o_pn = b.put(pn.data(), pn.size() * 4);
-    const size_t o_pm = b.put(pm.data(), pm.size() * 4);
-    const size_t o_mm = b.put(t.mode_m.data(), t.mode_m.size() * 4);
-    const size_t o_mn = b.put(t.mode_n.data(), t.mode_n.size() * 4);
+    im->o_pn = b.put(pn.data(), pn.size() * 4);
+    im->o_pm = b.put(pm.data(), pm.size() * 4);
+    im->o_mm = b.put(t.mode_m.data(), t.mode_m.size() * 4);
+    im->o_mn = b.put(t.mode_n.data(), t.mode_n.size() * 4);
     const int zero_status[4] = {0, 0, 0, 0};
-    const size_t o_st = b.put(zero_status, sizeof zero_status);
-    const size_t o_bt = b.put(t.basis_tt.data(), t.basis_tt.size() * 4);
-    size_t o_pol[DH_MAX_POLS][10] = {};
+    im->o_st = b.put(zero_status, sizeof zero_status);
+    im->o_bt = b.put(t.basis_tt.data(), t.basis_tt.size() * 4);
     for (int p = 0; p < g.pols; ++p) {
         const PolTables& pt = t.pol[p];
-        o_pol[p][0] = b.put(pt.mask_lo.data(), pt.mask_lo.size() * 4);
-        o_pol[p][1] = b.put(pt.mask_hi.data(), pt.mask_hi.size() * 4);
-        o_pol[p][2] = b.put(pt.phase_x.data(), pt.phase_x.size() * 4);
-        o_pol[p][3] = b.put(pt.phase_y.data(), pt.phase_y.size() * 4);
-        o_pol[p][4] = b.put(pt.corr_x.data(), pt.corr_x.size() * 4);
-        o_pol[p][5] = b.put(pt.corr_y.data(), pt.corr_y.size() * 4);
-        o_pol[p][6] = b.put(pt.hg_x.data(), pt.hg_x.size() * 4);
-        o_pol[p][7] = b.put(pt.hg_y.data(), pt.hg_y.size() * 4);
-        o_pol[p][8] = b.put(pt.hgy_tc.data(), pt.hgy_tc.size() * 2);
-        o_pol[p][9] = b.put(pt.cal.data(), pt.cal.size() * 4);
+        im->o_pol[p][0] = b.put(pt.mask_lo.data(), pt.mask_lo.size() * 4);
+        im->o_pol[p][1] = b.put(pt.mask_hi.data(), pt.mask_hi.size() * 4);
+        im->o_pol[p][2] = b.put(pt.phase_x.data(), pt.phase_x.size() * 4);
+        im->o_pol[p][3] = b.put(pt.phase_y.data(), pt.phase_y.size() * 4);
+        im->o_pol[p][4] = b.put(pt.corr_x.data(), pt.corr_x.size() * 4);
+        im->o_pol[p][5] = b.put(pt.corr_y.data(), pt.corr_y.size() * 4);
+        im->o_pol[p][6] = b.put(pt.hg_x.data(), pt.hg_x.size() * 4);
+        im->o_pol[p][7] = b.put(pt.hg_y.data(), pt.hg_y.size() * 4);
+        im->o_pol[p][8] = b.put(pt.hgy_tc.data(), pt.hgy_tc.size() * 2);
+        im->o_pol[p][9] = b.put(pt.cal.data(), pt.cal.size() * 4);
     }
-    void* d = nullptr;
-    cudaError_t e = cudaMalloc(&d, b.bytes.size());
-    if (e != cudaSuccess) return fail(DH_ERROR_MEMORYALLOCATION, std::string("plan tables: ") + cudaGetErrorString(e));
-    e = cudaMemcpy(d, b.bytes.data(), b.bytes.size(), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) {
-        cudaFree(d);
-        return cuda_fail(e, "plan upload");
-    }
-    unsigned char* base = (unsigned char*)d;
+    return DH_SUCCESS;
+}
+
+// The kernel plan of an image uploaded at device address `base`.
+static void plan_from_image(const Settings& s, const Geometry& g, const Tables& t, const PlanImage& im,
+                            unsigned char* base, dhk::Plan* out) {
     dhk::Plan& P = *out;
     std::memset(&P, 0, sizeof P);
     P.n = g.n;
@@ -138,33 +144,81 @@ int upload_plan(const Settings& s, const Geometry& g, const Tables& t, void** ou
     P.nrad_m = (int)t.radix_m.size();
     for (int i = 0; i < P.nrad_n; ++i) P.rad_n[i] = t.radix_n[i];
     for (int i = 0; i < P.nrad_m; ++i) P.rad_m[i] = t.radix_m[i];
-    P.tw_fwd_n = (const float2*)(base + o_twn);
-    P.tw_inv_m = (const float2*)(base + o_twm);
-    P.pos_n = (const int*)(base + o_pn);
-    P.pos_m = (const int*)(base + o_pm);
-    P.mode_m = (const int*)(base + o_mm);
-    P.mode_n = (const int*)(base + o_mn);
-    P.status = (int*)(base + o_st);
+    P.tw_fwd_n = (const float2*)(base + im.o_twn);
+    P.tw_inv_m = (const float2*)(base + im.o_twm);
+    P.pos_n = (const int*)(base + im.o_pn);
+    P.pos_m = (const int*)(base + im.o_pm);
+    P.mode_m = (const int*)(base + im.o_mm);
+    P.mode_n = (const int*)(base + im.o_mn);
+    P.status = (int*)(base + im.o_st);
     P.modes_out = g.modes_out;
-    P.basis_tt = t.basis_tt.empty() ? nullptr : (const float2*)(base + o_bt);
+    P.basis_tt = t.basis_tt.empty() ? nullptr : (const float2*)(base + im.o_bt);
     for (int p = 0; p < g.pols; ++p) {
         dhk::PolDev& pd = P.pol[p];
         pd.ox = g.pol[p].ax[0].origin;
         pd.oy = g.pol[p].ax[1].origin;
         pd.klx = g.pol[p].ax[0].klo;
         pd.kly = g.pol[p].ax[1].klo;
-        pd.mask_lo = (const int*)(base + o_pol[p][0]);
-        pd.mask_hi = (const int*)(base + o_pol[p][1]);
-        pd.phase_x = (const float2*)(base + o_pol[p][2]);
-        pd.phase_y = (const float2*)(base + o_pol[p][3]);
-        pd.corr_x = (const float2*)(base + o_pol[p][4]);
-        pd.corr_y = (const float2*)(base + o_pol[p][5]);
-        pd.hg_x = (const float*)(base + o_pol[p][6]);
-        pd.hg_y = (const float*)(base + o_pol[p][7]);
-        pd.hgy_tc = (const uint16_t*)(base + o_pol[p][8]);
-        pd.cal = t.pol[p].cal.empty() ? nullptr : (const float*)(base + o_pol[p][9]);
+        pd.mask_lo = (const int*)(base + im.o_pol[p][0]);
+        pd.mask_hi = (const int*)(base + im.o_pol[p][1]);
+        pd.phase_x = (const float2*)(base + im.o_pol[p][2]);
+        pd.phase_y = (const float2*)(base + im.o_pol[p][3]);
+        pd.corr_x = (const float2*)(base + im.o_pol[p][4]);
+        pd.corr_y = (const float2*)(base + im.o_pol[p][5]);
+        pd.hg_x = (const float*)(base + im.o_pol[p][6]);
+        pd.hg_y = (const float*)(base + im.o_pol[p][7]);
+        pd.hgy_tc = (const uint16_t*)(base + im.o_pol[p][8]);
+        pd.cal = t.pol[p].cal.empty() ? nullptr : (const float*)(base + im.o_pol[p][9]);
     }
+}
+
+int upload_plan(const Settings& s, const Geometry& g, const Tables& t, void** out_blob, dhk::Plan* out) {
+    PlanImage im;
+    int rc = build_plan_image(g, t, &im);
+    if (rc) return rc;
+    void* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, im.b.bytes.size());
+    if (e != cudaSuccess) return fail(DH_ERROR_MEMORYALLOCATION, std::string("plan tables: ") + cudaGetErrorString(e));
+    e = cudaMemcpy(d, im.b.bytes.data(), im.b.bytes.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(d);
+        return cuda_fail(e, "plan upload");
+    }
+    plan_from_image(s, g, t, im, (unsigned char*)d, out);
     *out_blob = d;
+    return DH_SUCCESS;
+}
+
+int upload_plans(Handle* H, const std::vector<Geometry>& geos, const std::vector<Tables>& tabs,
+                 std::vector<dhk::Plan>* plans) {
+    const size_t n = geos.size();
+    std::vector<PlanImage> ims(n);
+    std::vector<size_t> at(n);
+    size_t total = 0;
+    for (size_t i = 0; i < n; ++i) {
+        int rc = build_plan_image(geos[i], tabs[i], &ims[i]);
+        if (rc) return rc;
+        at[i] = total;
+        total = (total + ims[i].b.bytes.size() + 255) & ~(size_t)255;
+    }
+    if (total > H->cand_bytes) {
+        if (H->d_cand) cudaFree(H->d_cand);
+        H->d_cand = nullptr;
+        H->cand_bytes = 0;
+        cudaError_t e = cudaMalloc(&H->d_cand, total);
+        if (e != cudaSuccess) {
+            H->d_cand = nullptr;
+            return fail(DH_ERROR_MEMORYALLOCATION, std::string("candidate plan tables: ") + cudaGetErrorString(e));
+        }
+        H->cand_bytes = total;
+    }
+    std::vector<unsigned char> all(total, 0);
+    for (size_t i = 0; i < n; ++i) std::memcpy(all.data() + at[i], ims[i].b.bytes.data(), ims[i].b.bytes.size());
+    cudaError_t e = cudaMemcpy(H->d_cand, all.data(), total, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return cuda_fail(e, "candidate plan upload");
+    plans->resize(n);
+    for (size_t i = 0; i < n; ++i)
+        plan_from_image(H->s, geos[i], tabs[i], ims[i], (unsigned char*)H->d_cand + at[i], &(*plans)[i]);
     return DH_SUCCESS;
 }
 

@@ -56,6 +56,8 @@ struct Handle {
     size_t scratch_bytes = 0;
     void* d_hg = nullptr;         // HG coefficients ahead of an output-basis transform (device)
     size_t hg_bytes = 0;
+    void* d_cand = nullptr;       // plan tables of the candidates of a scoring call (device, reused by later calls)
+    size_t cand_bytes = 0;
     HostPipe* pipe = nullptr;     // host-buffer pipeline, created on first use
     Profiler prof;
     dhk::StageTimer* timer() { return prof.on ? &prof : nullptr; }
@@ -72,6 +74,11 @@ int ensure_scratch(Handle* H, size_t bytes);
 size_t split_window_bytes(const dhk::Plan& P);
 // Upload the tables of a geometry to a fresh device blob and fill the kernel plan that points into it.
 int upload_plan(const Settings& s, const Geometry& g, const Tables& t, void** out_blob, dhk::Plan* out);
+// Upload the tables of several geometries (with the handle's settings) into the handle's candidate area, one
+// copy for all, growing the area as needed, and fill their kernel plans.  The area is reused by the next call:
+// the caller's work that reads it must be complete by then.
+int upload_plans(Handle* H, const std::vector<Geometry>& geos, const std::vector<Tables>& tabs,
+                 std::vector<dhk::Plan>* plans);
 // Queue the generic three-kernel path for frames [0, batch) with the given plan and scratch.
 int run_split(const dhk::Plan& P, void* scratch, size_t scratch_bytes, const void* frames, int dtype, int batch,
               void* window, void* fields, void* coefs, cudaStream_t st, dhk::StageTimer* timer);

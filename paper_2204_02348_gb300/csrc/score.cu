@@ -191,35 +191,21 @@ extern "C" int dh_score_settings(dh_handle h, const void* d_frames, int dtype, i
         score_ready[H->device] = true;
     }
     cudaStream_t st = (cudaStream_t)stream;
-    // candidate plans: geometry and tables of every candidate, validated before any work is queued
-    std::vector<void*> blobs;
+    // candidate plans: geometry and tables of every candidate, validated before any work is queued, uploaded into
+    // the handle's candidate area with one copy; the call returns once its work is done, so the next call may
+    // overwrite the area
     std::vector<dhk::Plan> plans;
-    std::vector<Geometry> geos;
-    auto cleanup = [&]() {
-        if (!blobs.empty()) cudaStreamSynchronize(st);
-        for (void* b : blobs) cudaFree(b);
-    };
+    std::vector<Geometry> geos(count);
+    std::vector<Tables> tabs(count);
+    auto cleanup = [&]() { cudaStreamSynchronize(st); };
     for (int s = 0; s < count; ++s) {
-        Geometry g;
         std::string why;
-        rc = build_geometry_candidate(H->s, settings[s], &g, &why);
-        if (rc) {
-            cleanup();
-            return fail(rc, "candidate " + std::to_string(s) + ": " + why);
-        }
-        Tables t;
-        build_tables(H->s, g, &t);
-        void* blob = nullptr;
-        dhk::Plan P;
-        rc = upload_plan(H->s, g, t, &blob, &P);
-        if (rc) {
-            cleanup();
-            return rc;
-        }
-        blobs.push_back(blob);
-        plans.push_back(P);
-        geos.push_back(g);
+        rc = build_geometry_candidate(H->s, settings[s], &geos[s], &why);
+        if (rc) return fail(rc, "candidate " + std::to_string(s) + ": " + why);
+        build_tables(H->s, geos[s], &tabs[s]);
     }
+    rc = upload_plans(H, geos, tabs, &plans);
+    if (rc) return rc;
     const dhk::Plan& P0 = H->plan;
     const int N = P0.n, M = P0.m, pols = P0.pols;
     const int per_frame = pols * P0.modes;
