@@ -94,10 +94,10 @@ struct Pix4<float> {
 
 // k_ypass for the power-of-two windows, with the host plan's radix sequence fixed at compile time (128: 16 x 8,
 // 256: 16 x 16, 512: 8 x 8 x 8, 1024: 16 x 8 x 8): no runtime radix dispatch, twiddles staged in shared
-// memory, 2^LOGC column pairs per block, three blocks per SM.  Same inputs, outputs and arithmetic order as
-// k_ypass.
+// memory, 2^LOGC column pairs per block, three blocks per SM (four at N = 256, whose 16-pair tiles fit 64
+// registers).  Same inputs, outputs and arithmetic order as k_ypass.
 template <typename T, int N, int R0, int R1, int R2, int LOGC>
-__global__ void __launch_bounds__(kThreads, 3) k_ypass_s(const __grid_constant__ Plan P, const __grid_constant__ Batch B) {
+__global__ void __launch_bounds__(kThreads, (N == 256 && LOGC == 4) ? 4 : 3) k_ypass_s(const __grid_constant__ Plan P, const __grid_constant__ Batch B) {
     extern __shared__ float2 smem[];   // [N][C] tile, then the twiddles W_N^k
     constexpr int C = 1 << LOGC, half = N / 2;
     static_assert(R0 * R1 * R2 == N, "the radices multiply to N");
@@ -238,7 +238,7 @@ static bool launch_ypass_static(const Plan& P, const Batch& B, int zf, cudaStrea
     };
     switch (P.n) {
         case 128: if (!is(16, 8, 1)) return false; launch_ys<T, 128, 16, 8, 1, 5>(P, B, zf, st); return true;
-        case 256: if (!is(16, 16, 1)) return false; launch_ys<T, 256, 16, 16, 1, 5>(P, B, zf, st); return true;
+        case 256: if (!is(16, 16, 1)) return false; launch_ys<T, 256, 16, 16, 1, 4>(P, B, zf, st); return true;
         case 512: if (!is(8, 8, 8)) return false; launch_ys<T, 512, 8, 8, 8, 4>(P, B, zf, st); return true;
         case 1024: if (!is(16, 8, 8)) return false; launch_ys<T, 1024, 16, 8, 8, 3>(P, B, zf, st); return true;
         default: return false;
@@ -608,7 +608,7 @@ cudaError_t split_init() {
     if ((e = cudaFuncSetAttribute(k_ypass_s<T, N, A, B2, C2, L>, cudaFuncAttributeMaxDynamicSharedMemorySize, kMaxSmem))) \
         return e;
     DH_YS_ATTR(uint16_t, 128, 16, 8, 1, 5) DH_YS_ATTR(float, 128, 16, 8, 1, 5)
-    DH_YS_ATTR(uint16_t, 256, 16, 16, 1, 5) DH_YS_ATTR(float, 256, 16, 16, 1, 5)
+    DH_YS_ATTR(uint16_t, 256, 16, 16, 1, 4) DH_YS_ATTR(float, 256, 16, 16, 1, 4)
     DH_YS_ATTR(uint16_t, 512, 8, 8, 8, 4) DH_YS_ATTR(float, 512, 8, 8, 8, 4)
     DH_YS_ATTR(uint16_t, 1024, 16, 8, 8, 3) DH_YS_ATTR(float, 1024, 16, 8, 8, 3)
 #undef DH_YS_ATTR
