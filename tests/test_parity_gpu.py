@@ -445,3 +445,41 @@ def test_odd_prime_field_sizes(kind, m):
     _check(s, d["frames"], out)
     if m <= 192:
         _check(s, d["frames"], run_library(s, d["frames"], precision=1, fields=False), coef_tol=SPLIT_COEF_TOL)
+
+
+# ----------------------------------------------------------------------------- fused split-BF16 with the optional stages
+@pytest.mark.parametrize("stage", ["lg", "fill_factor", "calibration"])
+def test_split_bf16_fused_optional_stages(stage):
+    # the tensor-core variant of the fused kernel under the LG output basis (k_basis after it), the fill-factor
+    # correction (in its phase tables) and the reference calibration (applied as the window is read)
+    base = syn.setup_batching()
+    if stage == "lg":
+        s = syn.with_(base, basis="lg")
+    elif stage == "fill_factor":
+        s = syn.with_(base, fill_factor=True)
+    else:
+        s = _calibrated(base)
+    d = syn.make_frames(s, 3, seed=160)
+    out = run_library(s, d["frames"], precision=SPLIT)
+    _check(s, d["frames"], out, coef_tol=SPLIT_COEF_TOL)
+
+
+def test_split_bf16_fused_host_pipeline():
+    # the host-buffer entry point runs the same fused tensor-core kernel per chunk: bit-identical results
+    import torch
+    import paper_2204_02348_gb300 as dh
+    s = syn.setup_batching()
+    fr = syn.make_frames(s, 40, seed=161)["frames"]
+    dev = run_library(s, fr, precision=SPLIT)
+    h = dh.dh_create()
+    try:
+        dh.configure(h, s)
+        dh.dh_set_precision(h, SPLIT)
+        hin = torch.from_numpy(fr).pin_memory()
+        f = torch.empty(dev["fields"].shape, dtype=torch.complex64).pin_memory()
+        c = torch.empty(dev["coefs"].shape, dtype=torch.complex64).pin_memory()
+        dh.dh_process_batch_host(h, hin, dh.DH_DTYPE_U16, fr.shape[0], f, c)
+    finally:
+        dh.dh_destroy(h)
+    assert np.array_equal(f.numpy().view(np.uint32), dev["fields"].view(np.uint32))
+    assert np.array_equal(c.numpy().view(np.uint32), dev["coefs"].view(np.uint32))
