@@ -176,3 +176,44 @@ def test_lg_basis_request_equals_alone(kind):
         assert np.array_equal(c.numpy().view(np.uint32), ca.view(np.uint32))
     finally:
         dh.dh_destroy(h)
+
+
+def test_mixed_precisions_equal_alone():
+    # requests on the batching geometry with the FP32 and the split-BF16 overlap (the fused kernel's two
+    # variants) interleaved with a split-BF16 256 x 256 geometry (generic path): each equals its lone run
+    import torch
+    import paper_2204_02348_gb300 as dh
+    geos = [syn.setup_batching(), syn.setup_batching(), syn.serving_geometry("256x256_1pol", np.random.default_rng(97))]
+    precs = [dh.DH_PRECISION_FP32, dh.DH_PRECISION_SPLIT_BF16, dh.DH_PRECISION_SPLIT_BF16]
+    handles = []
+    for s, p in zip(geos, precs):
+        h = dh.dh_create()
+        dh.configure(h, s)
+        dh.dh_set_precision(h, p)
+        handles.append(h)
+    try:
+        reqs = []
+        for k in range(9):
+            gi = k % 3
+            n = 2 + k % 4
+            fr = syn.make_frames(geos[gi], n, seed=1100 + k)["frames"]
+            m, modes, _ = dh.dh_get_output_dims(handles[gi])
+            hin = torch.from_numpy(fr).pin_memory()
+            f = torch.empty((n, geos[gi].pol_count, m, m), dtype=torch.complex64).pin_memory()
+            c = torch.empty((n, geos[gi].pol_count, modes), dtype=torch.complex64).pin_memory()
+            reqs.append((gi, fr, hin, f, c))
+        alone = [_alone(dh, torch, handles[gi], geos[gi], fr) for gi, fr, _, _, _ in reqs]
+        srv = dh.dh_server_create(1 << 30, 3)
+        try:
+            tickets = [dh.dh_server_submit(srv, handles[gi], hin, dh.DH_DTYPE_U16, fr.shape[0], f, c)
+                       for gi, fr, hin, f, c in reqs]
+            for t in tickets:
+                dh.dh_server_wait(srv, t, -1)
+        finally:
+            dh.dh_server_destroy(srv)
+        for (gi, fr, hin, f, c), (fa, ca) in zip(reqs, alone):
+            assert np.array_equal(f.numpy().view(np.uint32), fa.view(np.uint32))
+            assert np.array_equal(c.numpy().view(np.uint32), ca.view(np.uint32))
+    finally:
+        for h in handles:
+            dh.dh_destroy(h)
