@@ -10,8 +10,8 @@
 //             the beam-centre phase and 1/N, then inverse transformed along x (M-point DIT).  Writes g[q][i].
 //   k_yinv  : step 2 along y, tilt/defocus removal and step 3.  Column chunks of g are inverse transformed
 //             along y, multiplied by the separable correction, written as the field, and contracted with the
-//             Hermite-Gaussian tables (first over y, then over x) into per-mode accumulators held in
-//             registers, in a fixed order (deterministic, no atomics).
+//             Hermite-Gaussian tables (first over y, on sums and differences of mirrored rows, then over x)
+//             into per-mode accumulators held in registers, in a fixed order (deterministic, no atomics).
 #include <algorithm>
 
 #include "fft.cuh"
