@@ -201,7 +201,10 @@ int dh_get_axes(dh_handle h, int pol, double* x, double* y);
  * float32 (dtype); d_fields (nullable): device complex64 [batch][pol][M][M]; d_coefs (nullable, ignored when
  * G = 0): device complex64 [batch][pol][modes].  batch < 1 is treated as 1 (digHoloConfigSetBatchCount).
  * Asynchronous on stream (a cudaStream_t, NULL = legacy default stream); the plan tables are uploaded on
- * the first call after a settings change, which synchronises the device once. */
+ * the first call after a settings change, which synchronises the device once.  Geometries that take the
+ * generic multi-kernel path keep the spectra between their kernels in scratch owned by the handle, one
+ * buffer per handle: calls on one handle queued on different streams race on it, so queue them on one stream
+ * (or use one handle per stream). */
 int dh_process_batch(dh_handle h, const void* d_frames, int dtype, int batch, void* d_fields, void* d_coefs,
                      void* stream);
 
@@ -243,8 +246,9 @@ int dh_process_batch_avg(dh_handle h, const void* d_frames, int dtype, int batch
  * buffers).  It exists for callers that cannot let a library allocate device memory while they process: code
  * whose device memory belongs to another allocator (a framework's caching pool, a serving process that has
  * already divided a fixed HBM budget) and acquisition loops that must not stall, since cudaMalloc / cudaFree
- * synchronise the device and can fail in the middle of a run.  It runs the same kernels as dh_process_batch
- * (FP32 overlap) with the same arguments, outputs and error codes, but takes its plan tables and scratch from
+ * synchronise the device and can fail in the middle of a run.  It runs the generic kernels of dh_process_batch
+ * with the same arguments, outputs and error codes, always with the FP32 overlap (a handle set to
+ * DH_PRECISION_SPLIT_BF16 still gets FP32 coefficients here), but takes its plan tables and scratch from
  * one 16 MiB array of static device memory (1 MiB of tables, 15 MiB of scratch) that every GPU loading the
  * library holds until the process exits; it calls no cudaMalloc, cudaFree or other allocating routine.
  *   - The first call on each device looks up the array's device address (cudaGetSymbolAddress) with that
@@ -257,7 +261,9 @@ int dh_process_batch_avg(dh_handle h, const void* d_frames, int dtype, int batch
  *     output-basis matrix counts against the tables: the LG matrix fits up to G = 16 at every supported size).
  *   - All calls share the array, which keeps the last call's contents; nothing in it needs to start at zero
  *     (every element is written before it is read within a call).  Calls that overlap on the GPU (different
- *     streams, or threads without ordering) race on the array: serialise them on one stream. */
+ *     streams, or threads without ordering) race on the array: serialise them on one stream.
+ *   - Its kernels contain no bounded waits, so it never sets the handle's device status word
+ *     (dh_get_device_status does not report on it). */
 int dh_process_batch_noalloc(dh_handle h, const void* d_frames, int dtype, int batch, void* d_fields, void* d_coefs,
                              void* stream);
 

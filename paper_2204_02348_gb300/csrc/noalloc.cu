@@ -8,11 +8,12 @@
 //
 // The array is 16 MiB: 1 MiB for the plan tables (uploaded by each call with a stream-ordered copy) and
 // 15 MiB of scratch (the per-frame spectra between the kernels; the batch is processed in chunks that fit).
-// Every GPU that loads the library holds the array until the process exits.  All calls share it and it keeps
-// the last call's contents; nothing in it has to start at zero, because every table entry and every scratch
-// element is written before it is read within the same call.  Calls that overlap on the GPU (queued on
-// different streams, or from different threads without ordering) race on the array: serialise them on one
-// stream.
+// The overlap is always the FP32 one (the split-BF16 tables are not packed), so the handle's precision
+// setting does not apply here.  Every GPU that loads the library holds the array until the process exits.
+// All calls share it and it keeps the last call's contents; nothing in it has to start at zero, because every
+// table entry and every scratch element is written before it is read within the same call.  Calls that
+// overlap on the GPU (queued on different streams, or from different threads without ordering) race on the
+// array: serialise them on one stream.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -103,7 +104,9 @@ int pack_plan(const Settings& s, const Geometry& g, const Tables& t, unsigned ch
     P.pols = g.pols;
     P.width = s.width;
     P.height = s.height;
-    P.precision = s.precision;
+    // The static table area holds no tensor-core B operand, so this path always runs the FP32 overlap,
+    // whatever precision the handle asks for; a split-BF16 plan here would have no B tiles to read.
+    P.precision = DH_PRECISION_FP32;
     P.nrad_n = (int)t.radix_n.size();
     P.nrad_m = (int)t.radix_m.size();
     for (int i = 0; i < P.nrad_n; ++i) P.rad_n[i] = t.radix_n[i];

@@ -22,7 +22,7 @@ def _cuda():
         pytest.skip("no CUDA device")
 
 
-def _run(setup, frames_np, noalloc):
+def _run(setup, frames_np, noalloc, precision=None):
     import torch
     import paper_2204_02348_gb300 as dh
     fr = torch.from_numpy(frames_np).cuda()
@@ -30,6 +30,8 @@ def _run(setup, frames_np, noalloc):
     h = dh.dh_create()
     try:
         dh.configure(h, setup)
+        if precision is not None:
+            dh.dh_set_precision(h, precision)
         m, modes, _ = dh.dh_get_output_dims(h)
         B, P = frames_np.shape[0], setup.pol_count
         nan = complex(float("nan"), float("nan"))
@@ -97,3 +99,21 @@ def test_noalloc_reference_calibration_matches_oracle():
     f_ref, c_ref = orc.process_batch(fr, s)
     assert rel_l2(got[0], f_ref).max() <= FIELD_TOL
     assert rel_l2(got[1], c_ref).max() <= COEF_TOL
+
+
+def test_noalloc_split_precision_handle_gets_fp32_overlap():
+    """A handle set to the split-BF16 overlap still gets the FP32 overlap from the allocation-free call (its
+    static table area carries no tensor-core operand tables): the result equals the allocating call on an
+    FP32 handle, and the coefficients match the oracle at the FP32 bar."""
+    import paper_2204_02348_gb300 as dh
+    from oracle import digholo_oracle as orc
+    s_fp32 = syn.setup_precision()
+    fr = syn.make_frames(s_fp32, 6, seed=141)["frames"]
+    ref = _run(s_fp32, fr, noalloc=False, precision=dh.DH_PRECISION_FP32)
+    got = _run(s_fp32, fr, noalloc=True, precision=dh.DH_PRECISION_SPLIT_BF16)
+    assert np.all(np.isfinite(got[0])) and np.all(np.isfinite(got[1]))
+    assert rel_l2(got[0], ref[0]).max() <= FIELD_TOL
+    assert rel_l2(got[1], ref[1]).max() <= COEF_TOL
+    f_ref, c_ref = orc.process_batch(fr[:2], s_fp32)
+    assert rel_l2(got[0][:2], f_ref).max() <= FIELD_TOL
+    assert rel_l2(got[1][:2], c_ref).max() <= COEF_TOL
