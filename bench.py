@@ -38,6 +38,7 @@ WORKLOAD = "batching: 1000 frames 320x256 u16, 2 pol windows 128x128, 64x64 fiel
 FRAMES = 1000
 ROTATE = 4                      # distinct input batches cycled between steps (4 x 164 MB > 129 MB L2)
 FALLBACK_HBM_GBS = 6800.0
+VARIANTS = {"auto": 0, "fused": 1, "fused_pruned": 2, "generic": 3}
 
 
 def parse_args():
@@ -47,7 +48,13 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--precision", choices=["fp32", "split_bf16"], default="fp32")
+    ap.add_argument("--variant", choices=list(VARIANTS), default="auto",
+                    help="kernel variant the handle is held to (dh_set_variant); auto: the library's choice")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-precision-case", action="store_true",
+                    help="skip the precision configuration's sub-record in the default line")
+    ap.add_argument("--sustain-s", type=float, default=2.5,
+                    help="seconds of back-to-back steps after the timed region (latency percentiles, clocks)")
     ap.add_argument("--frames", type=int, default=FRAMES, help="frames per step and GPU (default: the workload's 1000)")
     ap.add_argument("--workload", choices=["batching", "serving", "plain", "precision", "large_batch", "extensions"],
                     default="batching")
@@ -139,7 +146,7 @@ def measured_peak():
 
 
 # source file of each timed kernel; its hash also covers the device headers every kernel includes
-KERNEL_SOURCES = {"k_fused128": "k_fused.cu", "k_yinv_tc": "k_overlap_tc.cu", "k_ypass": "k_split.cu",
+KERNEL_SOURCES = {"k_fused128": "k_fused.cu", "k_fused128p": ("k_fused_pr.cu", "fused_pr.hpp"), "k_yinv_tc": "k_overlap_tc.cu", "k_ypass": "k_split.cu",
                   "k_xpass": "k_split.cu", "k_yinv": "k_split.cu"}
 DEVICE_HEADERS = ("fft.cuh", "kernels.cuh", "sync.cuh", "umma.cuh")
 
@@ -151,7 +158,8 @@ def kernel_source_hash(kernel):
         return None
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2204_02348_gb300", "csrc")
-    for name in (KERNEL_SOURCES[kernel],) + DEVICE_HEADERS:
+    src = KERNEL_SOURCES[kernel]
+    for name in (src if isinstance(src, tuple) else (src,)) + DEVICE_HEADERS:
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode())
             h.update(f.read())
@@ -183,6 +191,7 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.lines = []
+        self.stamps = []
         self.thread = None
 
     def start(self):
@@ -199,6 +208,18 @@ class ClockSampler:
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
+            self.stamps.append(time.perf_counter())
+
+    def samples(self):
+        """(host time, SM MHz, power W) of every sample read so far."""
+        out = []
+        for t, ln in zip(list(self.stamps), list(self.lines)):
+            parts = [p.strip() for p in ln.split(",")]
+            try:
+                out.append((t, float(parts[1]), float(parts[3])))
+            except (ValueError, IndexError):
+                continue
+        return out
 
     def stop(self):
         if self.proc is None:
@@ -323,8 +344,10 @@ def run_ours(args, ws, rank, local):
     h = dh.dh_create()
     dh.configure(h, setup)
     dh.dh_set_precision(h, prec)
+    dh.dh_set_variant(h, VARIANTS[args.variant])
     m, modes, _ = dh.dh_get_output_dims(h)
     P = setup.pol_count
+    variant = {v: k for k, v in VARIANTS.items()}[dh.dh_get_variant(h)]
     fields = torch.empty((frames_n, P, m, m), dtype=torch.complex64, device=dev)
     coefs = torch.empty((frames_n, P, modes), dtype=torch.complex64, device=dev)
     stream = torch.cuda.current_stream(dev)
@@ -365,6 +388,58 @@ def run_ours(args, ws, rank, local):
     per_step = [evs[k].elapsed_time(evs[k + 1]) for k in range(args.steps)]
     total_ms = max_over_ranks(evs[0].elapsed_time(evs[-1]), ws, dev)
     value = whole_job_rate(ws, frames_n, args.steps, total_ms)
+
+    # ---- sustained: the same step back to back for at least 2.5 s, in segments of 1000 steps (each drained
+    # with a synchronize, so its host interval brackets its device work); per-step events give the latency
+    # percentiles over every step, clock samples are binned by the segment they fall in
+    sustained = None
+    if rank == 0 and args.sustain_s > 0:
+        sampler2 = ClockSampler(local)
+        sampler2.start()
+        time.sleep(0.5)
+        seg_steps, segs, lat2 = 1000, [], []
+        t_start = time.perf_counter()
+        k = 0
+        while time.perf_counter() - t_start < args.sustain_s:
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(seg_steps + 1)]
+            torch.cuda.synchronize()
+            h0 = time.perf_counter()
+            ev[0].record(stream)
+            for i in range(seg_steps):
+                step(k)
+                k += 1
+                ev[i + 1].record(stream)
+            torch.cuda.synchronize()
+            h1 = time.perf_counter()
+            ms = ev[0].elapsed_time(ev[-1])
+            lat2.extend(ev[i].elapsed_time(ev[i + 1]) for i in range(seg_steps))
+            segs.append((h0, h1, ms))
+        smp = sampler2.samples()
+        sampler2.stop()
+        bins = {}
+        seg_mhz = []
+        for (h0, h1, ms) in segs:
+            inside = [mhz for (t, mhz, _) in smp if h0 <= t <= h1]
+            mhz = statistics.median(inside) if inside else None
+            seg_mhz.append(mhz)
+            if mhz is not None:
+                b = int(round(mhz / 30.0) * 30)
+                n, tot = bins.get(b, (0, 0.0))
+                bins[b] = (n + 1, tot + ms)
+        lat2.sort()
+        tot_ms = sum(ms for (_, _, ms) in segs)
+        loaded = [mhz for (t, mhz, _) in smp if segs and segs[0][0] <= t <= segs[-1][1]]
+        power = [w for (t, _, w) in smp if segs and segs[0][0] <= t <= segs[-1][1]]
+        sustained = {
+            "seconds": tot_ms / 1e3, "steps": len(lat2),
+            "frames_per_s": frames_n * len(lat2) / (tot_ms / 1e3),
+            "sm_mhz_median": statistics.median(loaded) if loaded else None,
+            "power_w_max": max(power) if power else None, "clock_samples": len(loaded),
+            "latency_ms": {"p50": lat2[len(lat2) // 2], "p99": lat2[min(len(lat2) - 1, int(0.99 * len(lat2)))],
+                           "max": lat2[-1], "unit": f"ms per {frames_n}-frame batch"},
+            "by_clock": [{"sm_mhz": b, "segments": n, "frames_per_s": frames_n * seg_steps * n / (t / 1e3)}
+                         for b, (n, t) in sorted(bins.items())],
+        }
 
     # ---- dominant kernel roofline
     peak, peak_src = measured_peak()
@@ -432,6 +507,12 @@ def run_ours(args, ws, rank, local):
                "sample": f"{n} frames (repeated passes over the step's batch) in {dt:.1f} s on {workers} processes"}
 
     dh.dh_destroy(h)
+    # ---- the precision configuration beside the headline one (rank 0, N = 1 only)
+    prec_case = None
+    if rank == 0 and ws == 1 and not args.no_precision_case:
+        del inputs, fields, coefs
+        torch.cuda.empty_cache()
+        prec_case = precision_case(20, dev)
     if rank == 0:
         lat = sorted(per_step)
         line = {
@@ -441,7 +522,7 @@ def run_ours(args, ws, rank, local):
             "config": {"workload": WORKLOAD if frames_n == FRAMES else WORKLOAD.replace("1000", str(frames_n)),
                        "frames_per_step_per_gpu": frames_n, "frame": [320, 256],
                        "pols": P, "window": setup.window, "field": m, "modes": modes,
-                       "overlap": args.precision, "l2": f"{ROTATE} rotating input batches "
+                       "overlap": args.precision, "variant": variant, "l2": f"{ROTATE} rotating input batches "
                        f"({ROTATE * host.numel() * 2 / 1e6:.0f} MB) > 129 MB L2",
                        "parallelism": f"replicas x{ws}"},
             "latency_ms": {"p50": lat[len(lat) // 2], "p99": lat[min(len(lat) - 1, int(0.99 * len(lat)))],
@@ -452,6 +533,8 @@ def run_ours(args, ws, rank, local):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "clocks": clocks,
+            "sustained": sustained,
+            "precision_case": prec_case,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -564,6 +647,53 @@ def _tiled_frames(setup, count, distinct, seed):
     return base, np.ascontiguousarray(base["frames"][idx])
 
 
+def precision_case(steps, dev):
+    """The precision configuration (1024 frames 640x512 u16, two 256x256 windows, 96x96 fields, 120 modes) with
+    the FP32 and the split-BF16 overlap: frames/s from CUDA events over `steps` batches (the 671 MB input is
+    larger than L2), the step's fraction of the HBM and FP32 ceilings, per-kernel event times, and the
+    split-BF16 coefficients' deviation from the FP32 ones."""
+    import numpy as np
+    import torch
+
+    import paper_2204_02348_gb300 as dh
+    from synth import holograms as syn
+    s = syn.setup_precision()
+    B = 1024
+    _, frames = _tiled_frames(s, B, 16, syn.BASE_SEED + 2)
+    fr = torch.from_numpy(frames).to(dev)
+    peak, _ = measured_peak()
+    fpk, _ = fp32_peak_tflops(dev)
+    res, c_fp32 = {}, None
+    for name, prec in (("fp32", dh.DH_PRECISION_FP32), ("split_bf16", dh.DH_PRECISION_SPLIT_BF16)):
+        h = dh.dh_create()
+        dh.configure(h, s)
+        dh.dh_set_precision(h, prec)
+        m, modes, _ = dh.dh_get_output_dims(h)
+        f = torch.empty((B, 2, m, m), dtype=torch.complex64, device=dev)
+        c = torch.empty((B, 2, modes), dtype=torch.complex64, device=dev)
+        ms = _event_time(lambda: dh.dh_process_batch(h, fr, dh.DH_DTYPE_U16, B, f, c), steps, 3)
+        dh.dh_set_profiling(h, True)
+        dh.dh_process_batch(h, fr, dh.DH_DTYPE_U16, B, f, c)
+        torch.cuda.synchronize()
+        prof = dh.dh_get_profile(h)
+        dh.dh_set_profiling(h, False)
+        cc = c.cpu().numpy().astype(np.complex128)
+        fps = B / (ms / 1e3)
+        bpf, fpf = bytes_per_frame(s, m, modes), flops_per_frame(s, m, modes)
+        res[name] = {"frames_per_s": fps, "ms_per_batch": ms,
+                     "hbm_frac": fps * bpf / 1e9 / peak, "alu_frac": fps * fpf / 1e12 / fpk,
+                     "bytes_per_frame": bpf, "flops_per_frame": fpf,
+                     "kernels_ms": {k: v[1] / max(v[0], 1) for k, v in prof.items()}}
+        if c_fp32 is None:
+            c_fp32 = cc
+        else:
+            dev_rel = np.linalg.norm(cc - c_fp32, axis=-1) / np.linalg.norm(c_fp32, axis=-1)
+            res[name]["coef_rel_l2_vs_fp32_max"] = float(dev_rel.max())
+        dh.dh_destroy(h)
+    del fr
+    return res
+
+
 def _event_time(fn, steps, warmup):
     import torch
     for _ in range(warmup):
@@ -636,35 +766,13 @@ def run_workload(args, ws, rank, local):
                     "e2e_latency_ms": {"p50": pct(lat_e2e, 0.5), "p99": pct(lat_e2e, 0.99),
                                        "note": "host frame in, host field and coefficients out"}})
     elif args.workload == "precision":
-        s = syn.setup_precision()
-        B = 1024
-        base, frames = _tiled_frames(s, B, 16, syn.BASE_SEED + 2)
-        fr = torch.from_numpy(frames).to(dev)
-        res, c_fp32 = {}, None
-        for name, prec in (("fp32", dh.DH_PRECISION_FP32), ("split_bf16", dh.DH_PRECISION_SPLIT_BF16)):
-            h = dh.dh_create()
-            dh.configure(h, s)
-            dh.dh_set_precision(h, prec)
-            m, modes, _ = dh.dh_get_output_dims(h)
-            f = torch.empty((B, 2, m, m), dtype=torch.complex64, device=dev)
-            c = torch.empty((B, 2, modes), dtype=torch.complex64, device=dev)
-            ms = _event_time(lambda: dh.dh_process_batch(h, fr, dh.DH_DTYPE_U16, B, f, c), max(3, args.steps // 20), 3)
-            cc = c.cpu().numpy().astype(np.complex128)
-            res[name] = {"frames_per_s": B / (ms / 1e3), "ms_per_batch": ms}
-            if c_fp32 is None:
-                c_fp32 = cc
-            else:
-                dev_rel = np.linalg.norm(cc - c_fp32, axis=-1) / np.linalg.norm(c_fp32, axis=-1)
-                res[name]["coef_rel_l2_vs_fp32_max"] = float(dev_rel.max())
-            dh.dh_destroy(h)
-        bpf = 2 * (256 * 256 * 2 + 96 * 96 * 8 + 120 * 8)
-        peak, _ = measured_peak()
+        res = precision_case(max(3, args.steps // 20), dev)
         out.update({"metric": "frames/s, precision case (split-BF16 vs FP32 overlap)", "value": res["split_bf16"]["frames_per_s"],
                     "unit": "frames/s", "steps": max(3, args.steps // 20), "warmup": 3, "dtype": "f32 FFT, split-bf16 overlap",
                     "config": {"workload": "precision: 1024 frames 640x512 u16, 2 windows 256x256, 96x96 fields, 120 modes",
                                "frame_content": "16 seeded frames tiled"},
                     "precision": res,
-                    "hbm_frac": {k: v["frames_per_s"] * bpf / 1e9 / peak for k, v in res.items()}})
+                    "hbm_frac": {k: v["hbm_frac"] for k, v in res.items()}})
     elif args.workload == "large_batch":
         s = syn.setup_large_batch()
         B, S = 2000, 64

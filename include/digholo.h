@@ -63,6 +63,13 @@ extern "C" {
 #define DH_PRECISION_FP32 0
 #define DH_PRECISION_SPLIT_BF16 1
 
+/* Kernel variants of the reconstruction (dh_set_variant).  The guide's counterpart is the FFTW planning mode
+ * (digHoloConfigSetFFTWPlanMode), which chooses how a transform is computed without changing its result. */
+#define DH_VARIANT_AUTO 0           /* the library's choice, or the tuner's (dh_autotune) */
+#define DH_VARIANT_FUSED 1          /* single-kernel path, window stays on chip, every pass over 128 x 128 */
+#define DH_VARIANT_FUSED_PRUNED 2   /* single-kernel path transforming only the columns the window keeps */
+#define DH_VARIANT_GENERIC 3        /* three-kernel path through library scratch (any window size) */
+
 /* Coefficient bases (digHoloConfigSetBasisType): the field is always projected onto the HG modes; LG and
  * custom coefficients are a matrix applied to the HG coefficients. */
 #define DH_BASIS_HG 0
@@ -186,6 +193,20 @@ int dh_set_ref_calibration_enabled(dh_handle h, int enabled);
  * (hi hi + hi lo + lo hi, FP32 accumulation); coefficients then agree with the FP32 ones to about 1e-5
  * relative.  Any other value gives DH_ERROR_INVALIDARGUMENT. */
 int dh_set_precision(dh_handle h, int precision);
+
+/* Hold the handle to one kernel variant (DH_VARIANT_*), as the guide's FFTW planning mode
+ * (digHoloConfigSetFFTWPlanMode) selects how transforms are computed; every variant computes the same
+ * reconstruction to rounding.  A variant that does not apply to the current settings (a fused variant for a
+ * window other than 128 x 128, the pruned one outside 64 x 64 fields with the FP32 overlap and at most 48
+ * kept columns, or frames whose base or row pitch is not 16-byte aligned) falls back to the next one that
+ * does (pruned -> fused -> generic).  DH_VARIANT_AUTO (the default) takes the tuner's choice when one exists
+ * for these settings, else the fused variant where it applies and the generic one elsewhere.  Unknown values
+ * give DH_ERROR_INVALIDARGUMENT. */
+int dh_set_variant(dh_handle h, int variant);
+
+/* The variant that dh_process_batch runs for the current settings and aligned frames (the fallbacks and the
+ * tuner's choice resolved); validates the settings like dh_get_output_dims. */
+int dh_get_variant(dh_handle h, int* variant);
 
 /* Validate the settings and report the output geometry: field size M (square), number of coefficients per
  * polarisation in the selected basis, and the field sample pitch dx' = N px / M in metres.  Any pointer may be

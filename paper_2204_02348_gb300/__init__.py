@@ -35,6 +35,10 @@ DH_DTYPE_U16 = 0
 DH_DTYPE_F32 = 1
 DH_PRECISION_FP32 = 0
 DH_PRECISION_SPLIT_BF16 = 1
+DH_VARIANT_AUTO = 0
+DH_VARIANT_FUSED = 1
+DH_VARIANT_FUSED_PRUNED = 2
+DH_VARIANT_GENERIC = 3
 DH_BASIS_HG = 0
 DH_BASIS_LG = 1
 DH_BASIS_CUSTOM = 2
@@ -83,6 +87,8 @@ _PROTOS = {
     "dh_set_defocus": [_i, _i, _d],
     "dh_set_basis": [_i, _i, _d, _i],
     "dh_set_precision": [_i, _i],
+    "dh_set_variant": [_i, _i],
+    "dh_get_variant": [_i, ctypes.POINTER(_i)],
     "dh_set_fill_factor_correction": [_i, _i],
     "dh_set_basis_type": [_i, _i],
     "dh_set_ref_calibration": [_i, _p, _i, _i, _i],
@@ -236,6 +242,16 @@ def dh_set_basis_transform(h: int, transform) -> None:
 
 def dh_set_precision(h: int, precision: int) -> None:
     _check(_lib.dh_set_precision(h, precision))
+
+
+def dh_set_variant(h: int, variant: int) -> None:
+    _check(_lib.dh_set_variant(h, variant))
+
+
+def dh_get_variant(h: int) -> int:
+    v = _i()
+    _check(_lib.dh_get_variant(h, ctypes.byref(v)))
+    return v.value
 
 
 def dh_get_output_dims(h: int):

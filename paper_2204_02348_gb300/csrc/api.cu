@@ -93,7 +93,7 @@ static std::vector<int> pos_table(int len, const std::vector<int>& rad) {
 struct PlanImage {
     Blob b;
     size_t o_twn = 0, o_twm = 0, o_pn = 0, o_pm = 0, o_mm = 0, o_mn = 0, o_st = 0, o_bt = 0;
-    size_t o_pol[DH_MAX_POLS][10] = {};
+    size_t o_pol[DH_MAX_POLS][11] = {};
 };
 
 static int build_plan_image(const Geometry& g, const Tables& t, PlanImage* im) {
@@ -122,6 +122,7 @@ static int build_plan_image(const Geometry& g, const Tables& t, PlanImage* im) {
         im->o_pol[p][7] = b.put(pt.hg_y.data(), pt.hg_y.size() * 4);
         im->o_pol[p][8] = b.put(pt.hgy_tc.data(), pt.hgy_tc.size() * 2);
         im->o_pol[p][9] = b.put(pt.cal.data(), pt.cal.size() * 4);
+        im->o_pol[p][10] = b.put(pt.pr.data(), pt.pr.size());
     }
     return DH_SUCCESS;
 }
@@ -169,6 +170,7 @@ static void plan_from_image(const Settings& s, const Geometry& g, const Tables& 
         pd.hg_y = (const float*)(base + im.o_pol[p][7]);
         pd.hgy_tc = (const uint16_t*)(base + im.o_pol[p][8]);
         pd.cal = t.pol[p].cal.empty() ? nullptr : (const float*)(base + im.o_pol[p][9]);
+        pd.pr = t.pol[p].pr.empty() ? nullptr : base + im.o_pol[p][10];
     }
 }
 
@@ -232,6 +234,8 @@ int init_device_once(int dev) {
     e = dhk::tc_init();
     if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
     e = fused_init();
+    if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
+    e = fused_pr_init();
     if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
     e = dhk::basis_init();
     if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
@@ -405,7 +409,7 @@ int process(Handle* H, const void* frames, int dtype, int batch, void* window, v
     void* out = nullptr;
     rc = basis_target(H, batch, &coefs, &out);
     if (rc) return rc;
-    if (use_fused(P) && !window && fused_frames_ok(P, frames, dtype)) {
+    if (fused_allowed(H, P) && !window && fused_frames_ok(P, frames, dtype)) {
         rc = launch_fused_path(H, P, frames, dtype, batch, fields, coefs, st, H->timer());
     } else {
         const size_t per_frame = split_window_bytes(P) * P.pols;
@@ -441,7 +445,7 @@ int process_avg(Handle* H, const void* frames, int dtype, int batch, int avg, in
     const int slices = dhk::avg_slices(elems);
     // 128 x 128 windows: the fused kernel's forward-only mode writes each member's window and its inverse-only
     // mode reconstructs the group means (no r1 scratch); otherwise the generic forward kernels
-    const bool fused = use_fused(P) && fused_frames_ok(P, frames, dtype);
+    const bool fused = fused_allowed(H, P) && fused_frames_ok(P, frames, dtype);
     // per member frame: its window (fused) or the generic path's r1 and window
     const size_t member = fused ? (size_t)elems * sizeof(float2) : split_window_bytes(P) * P.pols;
     const size_t per_group = (size_t)avg * member + (size_t)elems * sizeof(float2) + (size_t)avg * slices * sizeof(float2);
@@ -543,7 +547,7 @@ int process_plan(Handle* H, const dhk::Plan& P, const void* frames, int dtype, i
         coefs = (unsigned char*)scratch + scratch_bytes;
     }
     int rc;
-    if (use_fused(P) && fused_frames_ok(P, frames, dtype))
+    if (fused_allowed(H, P) && fused_frames_ok(P, frames, dtype))
         rc = launch_fused_path(H, P, frames, dtype, batch, fields, coefs, st, nullptr);
     else
         rc = run_split(P, scratch, scratch_bytes, frames, dtype, batch, nullptr, fields, coefs, st, nullptr);
@@ -777,6 +781,23 @@ int dh_set_basis_transform(dh_handle h, int modes_in, int modes_out, const void*
     H->s.custom_out = modes_out;
     H->s.basis = DH_BASIS_CUSTOM;
     H->dirty = true;
+    return DH_SUCCESS;
+}
+
+int dh_set_variant(dh_handle h, int variant) {
+    GET_HANDLE(h);
+    if (variant < DH_VARIANT_AUTO || variant > DH_VARIANT_GENERIC)
+        return fail(DH_ERROR_INVALIDARGUMENT, "variant must be one of DH_VARIANT_AUTO, _FUSED, _FUSED_PRUNED, _GENERIC");
+    H->variant = variant;
+    return DH_SUCCESS;
+}
+
+int dh_get_variant(dh_handle h, int* variant) {
+    GET_HANDLE(h);
+    if (!variant) return fail(DH_ERROR_NULLPOINTER, "variant is null");
+    int rc = ensure_plan(H);
+    if (rc) return rc;
+    *variant = resolve_variant(H, H->plan, true);
     return DH_SUCCESS;
 }
 

@@ -29,6 +29,7 @@ struct PolDev {
     const float* hg_y;       // [G][M]
     const uint16_t* hgy_tc;  // [2][NP][M] bf16 hi / lo of hg_y, tensor-core core-matrix layout
     const float* cal;        // nullable [N][N] reference-calibration factor over the window
+    const unsigned char* pr; // nullable table block of the column-pruned fused kernel (fused_pr.hpp)
 };
 
 struct Plan {

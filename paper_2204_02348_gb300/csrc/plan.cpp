@@ -3,6 +3,8 @@
 // taken here, in FP64, once per plan.
 #include "plan.hpp"
 
+#include "fused_pr.hpp"
+
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -302,7 +304,93 @@ void build_tables(const Settings& s, const Geometry& g, Tables* t) {
                 }
             }
         }
+        build_pr_block(g, p, &pt);
     }
+}
+
+// Table block of the column-pruned fused kernel (layout in fused_pr.hpp), or empty when the geometry is not
+// one it serves (N = 128, M = 64, G <= 16, at most kPrMaxK kept columns, each with a contiguous row range).
+// Every value derives from the tables above, in FP64: the kept bins are exactly those of the row-wise mask.
+void build_pr_block(const Geometry& g, int p, PolTables* ptp) {
+    using L = dhk::PrLayout;
+    PolTables& pt = *ptp;
+    pt.pr.clear();
+    const int n = g.n, m = g.m, G = g.groups;
+    if (n != dhk::kPrN || m != dhk::kPrM || G > dhk::kPrG) return;
+    const PolGeom& pg = g.pol[p];
+    const int klx = pg.ax[0].klo, kly = pg.ax[1].klo;
+    // columns p of the box with at least one kept bin, and each column's kept rows
+    int plo = m, phi = -1;
+    for (int q = 0; q < m; ++q)
+        if (pt.mask_lo[q] <= pt.mask_hi[q]) { plo = std::min(plo, pt.mask_lo[q]); phi = std::max(phi, pt.mask_hi[q]); }
+    if (phi < plo) return;
+    const int nk = phi - plo + 1;
+    if (nk > dhk::kPrMaxK) return;
+    std::vector<int> qlo(nk, m), qhi(nk, -1);
+    for (int c = 0; c < nk; ++c) {
+        const int pp = plo + c;
+        for (int q = 0; q < m; ++q)
+            if (pt.mask_lo[q] <= pp && pp <= pt.mask_hi[q]) { qlo[c] = std::min(qlo[c], q); qhi[c] = std::max(qhi[c], q); }
+        for (int q = qlo[c]; q <= qhi[c]; ++q)   // the kernel keeps a contiguous row range per column
+            if (!(pt.mask_lo[q] <= pp && pp <= pt.mask_hi[q])) return;
+        if (qhi[c] < qlo[c]) { qlo[c] = 1; qhi[c] = 0; }
+    }
+    const int kxlo = klx + plo;
+    std::vector<unsigned char> blk(L::BYTES, 0);
+    auto i32 = [&](int off) { return reinterpret_cast<int*>(blk.data() + off); };
+    auto f32 = [&](int off) { return reinterpret_cast<float*>(blk.data() + off); };
+    i32(L::HDR)[0] = nk;
+    i32(L::HDR)[1] = kxlo;
+    i32(L::HDR)[2] = klx;
+    i32(L::HDR)[3] = kly;
+    for (int c = 0; c < nk; ++c) {
+        i32(L::QLIM)[2 * c] = qlo[c];
+        i32(L::QLIM)[2 * c + 1] = qhi[c];
+        // the 1/2 of separating the two real rows packed in one complex row (a power of two: exact)
+        f32(L::PHX)[2 * c] = 0.5f * pt.phase_x[2 * (plo + c)];
+        f32(L::PHX)[2 * c + 1] = 0.5f * pt.phase_x[2 * (plo + c) + 1];
+    }
+    for (int q = 0; q < 2 * m; ++q) {
+        f32(L::PHY)[q] = pt.phase_y[q];
+        f32(L::CY)[q] = pt.corr_y[q];
+        f32(L::CX)[q] = pt.corr_x[q];
+    }
+    auto put_w = [&](float* dst, double ang) { dst[0] = (float)std::cos(ang); dst[1] = (float)std::sin(ang); };
+    for (int k1 = 0; k1 < 8; ++k1)
+        for (int n2 = 0; n2 < 16; ++n2) put_w(f32(L::TW1) + 2 * (k1 * 16 + n2), -2.0 * kPi * n2 * k1 / n);
+    for (int t = 0; t < 8; ++t)
+        for (int k1 = 0; k1 < 16; ++k1) put_w(f32(L::TW2) + 2 * (t * 18 + k1), -2.0 * kPi * t * k1 / n);
+    for (int s = 0; s < 8; ++s)
+        for (int j1 = 0; j1 < 8; ++j1) put_w(f32(L::TW3) + 2 * (s * 10 + j1), 2.0 * kPi * s * j1 / m);
+    // F1 slots: kept column c at slot c, its mirror N - k (the conjugate partner of the real-row separation) at
+    // slot nk + c; a column that is its own mirror (k = 0 or N/2) keeps slot nk + c as exchange space
+    for (int k = 0; k < n; ++k) {
+        int slot = -1;
+        const int mk = (n - k) % n;
+        if (k >= kxlo && k < kxlo + nk) slot = k - kxlo;
+        else if (mk >= kxlo && mk < kxlo + nk) slot = nk + mk - kxlo;
+        i32(L::SLOT)[(k % 8) * 16 + k / 8] = slot;
+    }
+    for (int j = 0; j < m; ++j)
+        for (int nn = 0; nn < G; ++nn) f32(L::HGY)[j * 20 + nn] = pt.hg_y[(size_t)nn * m + j];
+    // V[mm][c] = phx[c] sum_i u_mm(x'_i) dx' corr_x[i] exp(+2 pi i p_c i / M), p_c = plo + c the box column:
+    // the x inverse transform, the x correction and the x contraction of column c in one complex weight
+    for (int mm = 0; mm < G; ++mm)
+        for (int c = 0; c < nk; ++c) {
+            double re = 0.0, im = 0.0;
+            for (int i = 0; i < m; ++i) {
+                const double ang = 2.0 * kPi * (double)((plo + c) * i % m) / m;
+                const double u = pt.hg_x[(size_t)mm * m + i];
+                const double cr = pt.corr_x[2 * i], ci = pt.corr_x[2 * i + 1];
+                const double wr = std::cos(ang), wi = std::sin(ang);
+                re += u * (cr * wr - ci * wi);
+                im += u * (cr * wi + ci * wr);
+            }
+            const double pr = 0.5 * pt.phase_x[2 * (plo + c)], pi = 0.5 * pt.phase_x[2 * (plo + c) + 1];
+            f32(L::V)[2 * (mm * dhk::kPrMaxK + c)] = (float)(re * pr - im * pi);
+            f32(L::V)[2 * (mm * dhk::kPrMaxK + c) + 1] = (float)(re * pi + im * pr);
+        }
+    pt.pr.swap(blk);
 }
 
 }  // namespace dh

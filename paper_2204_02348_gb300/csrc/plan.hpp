@@ -71,6 +71,8 @@ struct PolTables {
     std::vector<uint16_t> hgy_tc;
     // reference calibration over the window, [N][N] (y, x): sqrt(max cal / cal), 0 where cal = 0; empty if off
     std::vector<float> cal;
+    // table block of the column-pruned fused kernel (fused_pr.hpp); empty when the geometry is not one it serves
+    std::vector<unsigned char> pr;
 };
 
 // Rows of the tensor-core B operand (the group count rounded up to 16).
@@ -102,6 +104,8 @@ int build_geometry(const Settings& s, Geometry* g, std::string* why);
 int build_geometry_candidate(const Settings& s, const dh_setting& c, Geometry* g, std::string* why);
 // Fill the host tables of a geometry.
 void build_tables(const Settings& s, const Geometry& g, Tables* t);
+// Fill PolTables::pr of polarisation p from its other tables (after they are built).
+void build_pr_block(const Geometry& g, int p, PolTables* pt);
 // HG -> LG coefficient matrix (FP64, complex interleaved [modes][modes], LG rows by group then l ascending,
 // HG columns by group then m ascending): c_LG = T c_HG.
 void lg_transform(int groups, std::vector<double>* t);

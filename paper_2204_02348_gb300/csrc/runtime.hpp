@@ -41,6 +41,9 @@ struct Profiler : dhk::StageTimer {
     ~Profiler() override;
 };
 
+// Kernel variants a handle can be held to (the values of DH_VARIANT_* in digholo.h).
+constexpr int kVariantAuto = 0, kVariantFusedLegacy = 1, kVariantFusedPruned = 2, kVariantGeneric = 3;
+
 struct HostPipe;   // streams and staging buffers of dh_process_batch_host (host.cu)
 
 struct Handle {
@@ -59,6 +62,8 @@ struct Handle {
     void* d_cand = nullptr;       // plan tables of the candidates of a scoring call (device, reused by later calls)
     size_t cand_bytes = 0;
     HostPipe* pipe = nullptr;     // host-buffer pipeline, created on first use
+    int variant = 0;              // kernel variant (DH_VARIANT_*): 0 lets the library (or its tuner) choose
+    int tuned = 0;                // the tuner's variant for the current settings (0: none)
     Profiler prof;
     dhk::StageTimer* timer() { return prof.on ? &prof : nullptr; }
 };
@@ -85,6 +90,10 @@ int run_split(const dhk::Plan& P, void* scratch, size_t scratch_bytes, const voi
 
 // Fused single-kernel path for small windows (k_fused.cu).
 bool use_fused(const dhk::Plan& P);
+// The variant a call runs (dh_set_variant's rules; `aligned`: the frames suit tensor copies).
+int resolve_variant(const Handle* H, const dhk::Plan& P, bool aligned);
+// use_fused, unless the handle's variant resolves to the generic path.
+bool fused_allowed(const Handle* H, const dhk::Plan& P);
 // The fused kernel stages windows with tensor copies: the frames need a 16-byte aligned base and row pitch.
 bool fused_frames_ok(const dhk::Plan& P, const void* frames, int dtype);
 cudaError_t fused_init();
@@ -96,6 +105,13 @@ int launch_fused_path(Handle* H, const dhk::Plan& P, const void* frames, int dty
 int launch_fused(Handle* H, const dhk::Plan& P, const void* frames, int dtype, int total, int frame0, int count,
                  int mode, const float2* win_in, float2* win_out, void* fields, void* coefs, cudaStream_t st,
                  dhk::StageTimer* timer);
+
+// Column-pruned fused path (k_fused_pr.cu): 128 x 128 windows, 64 x 64 fields, FP32 overlap, whole path only;
+// used by launch_fused_path when the plan carries its table block.
+bool use_fused_pr(const dhk::Plan& P);
+cudaError_t fused_pr_init();
+int launch_fused_pr(Handle* H, const dhk::Plan& P, const void* frames, int dtype, int batch, void* fields, void* coefs,
+                    cudaStream_t st, dhk::StageTimer* timer);
 
 // HG coefficient bytes per frame that an output-basis transform needs as scratch (0 for the HG basis).
 size_t basis_scratch_bytes(const dhk::Plan& P);

@@ -19,9 +19,10 @@ def rel_l2(a, b):
     return num / np.maximum(den, 1e-300)
 
 
-def run_library(setup, frames, precision=0, fields=True, coefs=True, window=False, batch=None):
+def run_library(setup, frames, precision=0, fields=True, coefs=True, window=False, batch=None, variant=0):
     """Process frames (numpy [B][H][W]) on cuda:0 through dh_process_batch[_window]; returns numpy outputs.
-    Outputs are pre-filled with NaN so unwritten elements fail the comparison."""
+    Outputs are pre-filled with NaN so unwritten elements fail the comparison.  variant: DH_VARIANT_* the handle
+    is held to; the result's "variant" is the one dh_get_variant reports for the call's settings."""
     import torch
     import paper_2204_02348_gb300 as dh
     dev = torch.device("cuda", 0)
@@ -31,6 +32,7 @@ def run_library(setup, frames, precision=0, fields=True, coefs=True, window=Fals
     try:
         dh.configure(h, setup)
         dh.dh_set_precision(h, precision)
+        dh.dh_set_variant(h, variant)
         m, modes, _ = dh.dh_get_output_dims(h)
         B = frames.shape[0] if batch is None else max(batch, 1)
         P = setup.pol_count
@@ -46,7 +48,8 @@ def run_library(setup, frames, precision=0, fields=True, coefs=True, window=Fals
         torch.cuda.synchronize()
         out = {"fields": None if f is None else f.cpu().numpy(),
                "coefs": None if c is None else c.cpu().numpy(),
-               "window": None if w is None else w.cpu().numpy(), "m": m, "modes": modes}
+               "window": None if w is None else w.cpu().numpy(), "m": m, "modes": modes,
+               "variant": dh.dh_get_variant(h)}
     finally:
         dh.dh_destroy(h)
     return out
