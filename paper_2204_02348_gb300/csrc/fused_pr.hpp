@@ -22,11 +22,8 @@ struct PrLayout {
     static constexpr int PHY = PHX + 8 * kPrMaxK;         // float2[M]: y beam-centre phase of box row q
     static constexpr int CY = PHY + 8 * kPrM;             // float2[M]: y residual tilt and defocus removal
     static constexpr int CX = CY + 8 * kPrM;              // float2[M]: x residual tilt and defocus removal
-    static constexpr int TW1 = CX + 8 * kPrM;             // float2[8][16]: exp(-2 pi i n2 k1 / N) at [k1][n2]
-    static constexpr int TW2 = TW1 + 8 * 8 * 16;          // float2[8][18]: exp(-2 pi i t k1 / N) at [t][k1]
-    static constexpr int TW3 = TW2 + 8 * 8 * 18;          // float2[8][10]: exp(+2 pi i s j1 / M) at [s][j1]
-    static constexpr int SLOT = TW3 + 8 * 8 * 10;         // int[8][16]: F1 slot of x frequency j + 8 k2 at [j][k2]
-    static constexpr int HGY = SLOT + 4 * kPrN;           // float[M][20]: u_n(y'_j) dy' at [j][n] (n < 16)
+    static constexpr int TWN = CX + 8 * kPrM;             // float2[N]: exp(-2 pi i k / N), the twiddle bases
+    static constexpr int HGY = TWN + 8 * kPrN;            // float[M][20]: u_n(y'_j) dy' at [j][n] (n < 16)
     static constexpr int V = HGY + 4 * kPrM * 20;         // float2[16][kPrMaxK]: x contraction of column c
     static constexpr int BYTES = V + 8 * kPrG * kPrMaxK;
 };

@@ -47,10 +47,19 @@ constexpr long kPrWaitLimit = 1L << 24;
 template <typename T>
 struct PrStage {
     static constexpr int ALIGN = 16 / (int)sizeof(T);            // elements per 16 bytes
-    static constexpr int W = kPrN + ALIGN;                        // staged row: window plus alignment slack
+    // staged row: the window plus 32 bytes of slack (the 16-byte alignment of the copy, and a row pitch of
+    // 8 banks modulo 32, so that the four row pairs of a warp read pixel pairs from distinct banks)
+    static constexpr int W = kPrN + 2 * ALIGN;
     static constexpr int BYTES = kPrN * W * (int)sizeof(T);
     static_assert(BYTES >= 64 * 512, "P1's exchange (512 bytes per row pair) fits in the staging buffer");
+    static_assert(BYTES % 128 == 0, "F1 starts on a 128-byte boundary");
 };
+
+// F1 slot of x frequency k: kept column k - kxlo, the mirror of kept column c at nk + c, else -1.
+__device__ __forceinline__ int pr_slot(int k, int kxlo, int nk) {
+    const int c = k - kxlo, mc = ((kPrN - k) & (kPrN - 1)) - kxlo;
+    return (unsigned)c < (unsigned)nk ? c : (unsigned)mc < (unsigned)nk ? nk + mc : -1;
+}
 
 template <typename T>
 struct PrSmem {
@@ -96,6 +105,18 @@ __device__ __forceinline__ void pr_pixels(const T* row, int x, float& a, float& 
     }
 }
 
+// a[k] *= w^k for k = 1 .. R-1, the powers by binary powering (w^k = w^(k/2) w^((k+1)/2), at most four
+// products deep for R = 16): here shared-memory table reads would cost more than these multiplications.
+template <int R>
+__device__ __forceinline__ void pr_twiddle(float2* a, float2 w) {
+    float2 p[R];
+    p[1] = w;
+#pragma unroll
+    for (int k = 2; k < R; ++k) p[k] = cmul(p[k >> 1], p[(k + 1) >> 1]);
+#pragma unroll
+    for (int k = 1; k < R; ++k) a[k] = cmul(a[k], p[k]);
+}
+
 __device__ __forceinline__ float2 f4lo(float4 v) { return make_float2(v.x, v.y); }
 __device__ __forceinline__ float2 f4hi(float4 v) { return make_float2(v.z, v.w); }
 
@@ -137,10 +158,9 @@ __device__ __noinline__ void pr_columns(unsigned char* smem_base, size_t f1_off,
             const int cc = act ? c : 0;   // groups without a column compute on column 0 and store nothing
             const int kx = kxlo + cc;
             const int mk = (N - kx) & (N - 1);
-            const int* slotT = reinterpret_cast<const int*>(TB + L::SLOT);
             float2* s1 = F1 + cc * kPrPitch;          // the column (Z_k), then its window, then its field values
             float2* s2 = F1 + (nk + cc) * kPrPitch;   // its mirror Z_{N-k} (or spare), then exchange space
-            const float2* sm = F1 + slotT[(mk & 7) * 16 + (mk >> 3)] * kPrPitch;
+            const float2* sm = F1 + pr_slot(mk, kxlo, nk) * kPrPitch;
             // separation: the spectra of rows y (y < 64) and y + 64 at k from Z_k and conj Z_{N-k}
             float2 a16[16];   // y = t + 8 r
 #pragma unroll
@@ -150,32 +170,27 @@ __device__ __noinline__ void pr_columns(unsigned char* smem_base, size_t f1_off,
                 a16[r + 8] = make_float2(a.y + bm.y, bm.x - a.x);
             }
             dft16<false>(a16);   // over r: frequency k1 = ky mod 16
-            {
-                const float4* tw = reinterpret_cast<const float4*>(TB + L::TW2) + t * 9;   // [t][18]
-#pragma unroll
-                for (int h = 0; h < 8; ++h) {
-                    const float4 v = tw[h];
-                    if (h > 0) a16[2 * h] = cmul(a16[2 * h], f4lo(v));
-                    a16[2 * h + 1] = cmul(a16[2 * h + 1], f4hi(v));
-                }
-            }
+            pr_twiddle<16>(a16, reinterpret_cast<const float2*>(TB + L::TWN)[t]);   // W_N^(t k1)
             __syncwarp();   // the group's slot reads are done
             // exchange: rows k1 in 128-byte blocks of two, block bb read by thread bb (blocks 0..3 in s1, 4..7 in
-            // s2), 16-byte chunks XOR-swizzled by the block index
+            // s2); a 16-byte chunk's bank position is XOR-swizzled by the block index, net of the block's own
+            // position (slot s starts s * 528 bytes in, i.e. s chunks past a 128-byte boundary)
+            const int o1 = cc & 7, o2 = (nk + cc) & 7;
 #pragma unroll
             for (int k1 = 0; k1 < 16; ++k1) {
                 const int bb = k1 >> 1;
                 float2* base = (bb < 4 ? s1 : s2) + (bb & 3) * 16;
-                const int ch = ((((k1 & 1) << 2) | (t >> 1)) ^ bb) & 7;
+                const int ch = (((((k1 & 1) << 2) | (t >> 1)) ^ bb) - (bb < 4 ? o1 : o2)) & 7;
                 if (act) base[ch * 2 + (t & 1)] = a16[k1];
             }
             __syncwarp();
             float2 b0[8], b1[8];   // k1 = 2t and 2t + 1, over the eight column threads
             {
                 const float4* base = reinterpret_cast<const float4*>((t < 4 ? s1 : s2) + (t & 3) * 16);
+                const int ob = t < 4 ? o1 : o2;
 #pragma unroll
                 for (int k = 0; k < 8; ++k) {
-                    const float4 v = base[k ^ t];
+                    const float4 v = base[((k ^ t) - ob) & 7];
                     if (k < 4) {
                         b0[2 * k] = f4lo(v);
                         b0[2 * k + 1] = f4hi(v);
@@ -188,37 +203,35 @@ __device__ __noinline__ void pr_columns(unsigned char* smem_base, size_t f1_off,
             dft8<false>(b0);   // ky = 2t + 16 k2
             dft8<false>(b1);   // ky = 2t + 1 + 16 k2
             __syncwarp();      // the exchange blocks are read
-            // window: the kept box rows q of this column times the y beam-centre phase, in box-row order in s1
+            // the box rows q < M of this column in box-row order in s1 (rotated by one place for every other
+            // column pair, so that the two columns of a half-warp write different banks)
+            const int rot = (cc >> 2) & 1;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+#pragma unroll
+                for (int k2 = 0; k2 < 8; ++k2) {
+                    const int q = (2 * t + h + 16 * k2 - kly) & (N - 1);
+                    if (act && q < M) s1[(q + rot) & (M - 1)] = h ? b1[k2] : b0[k2];
+                }
+            }
+            __syncwarp();
+            // 64-point y inverse: radix 8 over r (q = t + 8 r) of the window (kept rows [qlo, qhi] times the y
+            // beam-centre phase, zero elsewhere), twiddles, exchange, radix 8 over t
+            float2 v8[8];
             {
                 const int2 ql = reinterpret_cast<const int2*>(TB + L::QLIM)[cc];
                 const float2* phy = reinterpret_cast<const float2*>(TB + L::PHY);
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-#pragma unroll
-                    for (int k2 = 0; k2 < 8; ++k2) {
-                        const int ky = 2 * t + h + 16 * k2;
-                        const int q = (ky - kly) & (N - 1);
-                        const float2 v = h ? b1[k2] : b0[k2];
-                        const bool keep = q >= ql.x && q <= ql.y;
-                        const float2 o = keep ? cmul(v, phy[q & (M - 1)]) : make_float2(0.f, 0.f);
-                        if (act && q < M) s1[q] = o;
-                    }
+                for (int r = 0; r < 8; ++r) {
+                    const int q = t + 8 * r;
+                    const float2 v = s1[(q + rot) & (M - 1)];
+                    v8[r] = (q >= ql.x && q <= ql.y) ? cmul(v, phy[q]) : make_float2(0.f, 0.f);
                 }
             }
-            __syncwarp();
-            // 64-point y inverse: radix 8 over r (q = t + 8 r), twiddles, exchange, radix 8 over t
-            float2 v8[8];
-#pragma unroll
-            for (int r = 0; r < 8; ++r) v8[r] = s1[t + 8 * r];
             dft8<true>(v8);
             {
-                const float4* tw = reinterpret_cast<const float4*>(TB + L::TW3) + t * 5;   // [s][10]
-#pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    const float4 v = tw[h];
-                    if (h > 0) v8[2 * h] = cmul(v8[2 * h], f4lo(v));
-                    v8[2 * h + 1] = cmul(v8[2 * h + 1], f4hi(v));
-                }
+                const float2 b = reinterpret_cast<const float2*>(TB + L::TWN)[2 * t];
+                pr_twiddle<8>(v8, make_float2(b.x, -b.y));   // exp(+2 pi i t j1 / M)
             }
 #pragma unroll
             for (int j1 = 0; j1 < 8; ++j1)
@@ -309,13 +322,8 @@ __device__ __noinline__ void pr_rows(unsigned char* smem_base, size_t f1_off, in
         }
         dft8<true>(v8);
         {
-            const float4* tw = reinterpret_cast<const float4*>(TB + L::TW3) + t * 5;
-#pragma unroll
-            for (int h = 0; h < 4; ++h) {
-                const float4 v = tw[h];
-                if (h > 0) v8[2 * h] = cmul(v8[2 * h], f4lo(v));
-                v8[2 * h + 1] = cmul(v8[2 * h + 1], f4hi(v));
-            }
+            const float2 b = reinterpret_cast<const float2*>(TB + L::TWN)[2 * t];
+            pr_twiddle<8>(v8, make_float2(b.x, -b.y));   // exp(+2 pi i t j1 / M)
         }
         // exchange in two rounds of a 4 x 8 tile per row, behind the kept columns' slots
         float2* X = F1 + nk * kPrPitch + jr * 32;
@@ -370,7 +378,7 @@ __global__ void __launch_bounds__(kPrNT, sizeof(T) == 2 ? 2 : 1)
     float2* Hs = reinterpret_cast<float2*>(smem + SM::H);
     int* mdm = reinterpret_cast<int*>(smem + SM::MD);
     int* mdn = mdm + kPrMaxModes;
-    const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5, t = tid & 7;
+    const int tid = threadIdx.x, t = tid & 7;
     // every block serves one polarisation: its table block is staged once
     const int pol = blockIdx.x % P.pols;
     const PolDev& pd = P.pol[pol];
@@ -446,12 +454,12 @@ __global__ void __launch_bounds__(kPrNT, sizeof(T) == 2 ? 2 : 1)
         dft8<false>(za);
         dft8<false>(zb);
         {
-            const float4* tw = reinterpret_cast<const float4*>(TB + L::TW1);   // [k1][n2 pair]
+            // W_N^(n2 k1) for n2 = 2t, 2t + 1 from the base table (index n2 k1 < N)
+            const float2* twn = reinterpret_cast<const float2*>(TB + L::TWN);
 #pragma unroll
             for (int k1 = 1; k1 < 8; ++k1) {
-                const float4 v = tw[k1 * 8 + t];
-                za[k1] = cmul(za[k1], f4lo(v));
-                zb[k1] = cmul(zb[k1], f4hi(v));
+                za[k1] = cmul(za[k1], twn[2 * t * k1]);
+                zb[k1] = cmul(zb[k1], twn[(2 * t + 1) * k1]);
             }
         }
         float2 y[16];   // after the exchange: n2 = 0..15 at the frequency k1 = t
@@ -481,16 +489,10 @@ __global__ void __launch_bounds__(kPrNT, sizeof(T) == 2 ? 2 : 1)
             }
         }
         dft16<false>(y);   // y[k2] = Z(t + 8 k2)
-        {
-            const int4* sl4 = reinterpret_cast<const int4*>(TB + L::SLOT) + t * 4;
 #pragma unroll
-            for (int q4 = 0; q4 < 4; ++q4) {
-                const int4 sl = sl4[q4];
-                if (sl.x >= 0) F1[sl.x * kPrPitch + g] = y[4 * q4];
-                if (sl.y >= 0) F1[sl.y * kPrPitch + g] = y[4 * q4 + 1];
-                if (sl.z >= 0) F1[sl.z * kPrPitch + g] = y[4 * q4 + 2];
-                if (sl.w >= 0) F1[sl.w * kPrPitch + g] = y[4 * q4 + 3];
-            }
+        for (int k2 = 0; k2 < 16; ++k2) {
+            const int sl = pr_slot(t + 8 * k2, kxlo, nk);
+            if (sl >= 0) F1[sl * kPrPitch + g] = y[k2];
         }
         // the staging buffer's generic reads and writes are ordered before the next tensor copy into it
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
@@ -601,7 +603,7 @@ int launch_fused_pr(Handle* H, const dhk::Plan& P, const void* frames, int dtype
     std::memset(&tmap, 0, sizeof tmap);
     const cuuint64_t gdim[3] = {(cuuint64_t)P.width, (cuuint64_t)P.height, (cuuint64_t)batch};
     const cuuint64_t gstride[2] = {(cuuint64_t)P.width * esz, (cuuint64_t)P.width * P.height * esz};
-    const cuuint32_t box[3] = {(cuuint32_t)(dhk::kPrN + align), (cuuint32_t)dhk::kPrN, 1};
+    const cuuint32_t box[3] = {(cuuint32_t)(dhk::kPrN + 2 * align), (cuuint32_t)dhk::kPrN, 1};   // PrStage<T>::W
     const cuuint32_t estride[3] = {1, 1, 1};
     CUresult cr = g_pr_encode(&tmap, u16 ? CU_TENSOR_MAP_DATA_TYPE_UINT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3,
                               const_cast<void*>(frames), gdim, gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE,

@@ -355,21 +355,9 @@ void build_pr_block(const Geometry& g, int p, PolTables* ptp) {
         f32(L::CY)[q] = pt.corr_y[q];
         f32(L::CX)[q] = pt.corr_x[q];
     }
-    auto put_w = [&](float* dst, double ang) { dst[0] = (float)std::cos(ang); dst[1] = (float)std::sin(ang); };
-    for (int k1 = 0; k1 < 8; ++k1)
-        for (int n2 = 0; n2 < 16; ++n2) put_w(f32(L::TW1) + 2 * (k1 * 16 + n2), -2.0 * kPi * n2 * k1 / n);
-    for (int t = 0; t < 8; ++t)
-        for (int k1 = 0; k1 < 16; ++k1) put_w(f32(L::TW2) + 2 * (t * 18 + k1), -2.0 * kPi * t * k1 / n);
-    for (int s = 0; s < 8; ++s)
-        for (int j1 = 0; j1 < 8; ++j1) put_w(f32(L::TW3) + 2 * (s * 10 + j1), 2.0 * kPi * s * j1 / m);
-    // F1 slots: kept column c at slot c, its mirror N - k (the conjugate partner of the real-row separation) at
-    // slot nk + c; a column that is its own mirror (k = 0 or N/2) keeps slot nk + c as exchange space
     for (int k = 0; k < n; ++k) {
-        int slot = -1;
-        const int mk = (n - k) % n;
-        if (k >= kxlo && k < kxlo + nk) slot = k - kxlo;
-        else if (mk >= kxlo && mk < kxlo + nk) slot = nk + mk - kxlo;
-        i32(L::SLOT)[(k % 8) * 16 + k / 8] = slot;
+        f32(L::TWN)[2 * k] = (float)std::cos(-2.0 * kPi * k / n);
+        f32(L::TWN)[2 * k + 1] = (float)std::sin(-2.0 * kPi * k / n);
     }
     for (int j = 0; j < m; ++j)
         for (int nn = 0; nn < G; ++nn) f32(L::HGY)[j * 20 + nn] = pt.hg_y[(size_t)nn * m + j];
