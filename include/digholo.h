@@ -208,6 +208,56 @@ int dh_set_variant(dh_handle h, int variant);
  * tuner's choice resolved); validates the settings like dh_get_output_dims. */
 int dh_get_variant(dh_handle h, int* variant);
 
+/* ---------------------------------------------------------------------------------------------- autotuner
+ * The guide lets FFTW plan its transforms (digHoloConfigSetFFTWPlanMode: estimate ... exhaustive) and keeps
+ * the plans in a wisdom file (digHoloFFTWWisdomFilename) so later runs skip the search.  Here the choices are
+ * the kernel variant, the generic path's chunk size (frames per launch, which decides whether the spectra stay
+ * in L2 between its kernels) and the radix plan of the M-point inverse transforms.  dh_autotune times every
+ * candidate on the caller's frames and keeps the fastest; the choices are stored per geometry key in a JSON
+ * cache file, the analogue of the wisdom file.  Every candidate computes the same reconstruction to rounding. */
+
+#define DH_MAX_RADICES 6
+
+typedef struct dh_tuning {
+    int variant;                     /* DH_VARIANT_* (DH_VARIANT_AUTO: the library's default) */
+    int chunk_mb;                    /* generic path: scratch target per launch chunk in MiB (0: default 48) */
+    int nradix;                      /* radix plan of the field size M, first pass first (0: the default plan) */
+    int radix[DH_MAX_RADICES];       /* each radix in {2, 3, 4, 5, 7, 8, 11, 13, 16, 17, 19}, product M */
+} dh_tuning;
+
+/* Geometry key the tuner files choices under (field size, window, groups, polarisations, frame size,
+ * precision, basis), as a NUL-terminated string in buf (at most len bytes, 128 suffice).  Host only. */
+int dh_tuning_key(dh_handle h, char* buf, int len);
+
+/* The candidates dh_autotune times for the current settings, in its order (host only): at most max entries
+ * written to out, their number to *count (may exceed max).  For 128 x 128 windows: the fused variant, the
+ * pruned one where it applies, and the generic path; otherwise the generic path at chunk targets 24, 48 and
+ * 96 MiB with the default radix plan of M and up to three alternatives (the reversed plan, other power-of-two
+ * factorisations). */
+int dh_tuning_candidates(dh_handle h, dh_tuning* out, int max, int* count);
+
+/* Hold the handle to one tuning (NULL: back to the defaults and the cache).  The radix plan is validated
+ * (DH_ERROR_INVALIDARGUMENT unless its radices are supported and multiply to M); a changed plan re-uploads the
+ * tables on the next call.  The tuning stays while the geometry key is unchanged. */
+int dh_set_tuning(dh_handle h, const dh_tuning* t);
+
+/* The tuning in effect for the current settings: the one set or chosen for this key, else the cache's entry,
+ * else zeros (defaults).  Host only. */
+int dh_get_tuning(dh_handle h, dh_tuning* out);
+
+/* Load tuning choices from a JSON cache file and remember the path (dh_autotune writes its choices back to
+ * it).  A missing file is an empty cache; a malformed one gives DH_ERROR_INVALIDARGUMENT and leaves the
+ * handle's cache unchanged.  NULL forgets the path and the loaded choices. */
+int dh_set_tuning_cache(dh_handle h, const char* path);
+
+/* Time every candidate of dh_tuning_candidates on these frames (one untimed run, then `reps` runs between
+ * CUDA events on `stream`, reps < 1 taken as 3), keep the fastest (the first on ties), record it under the
+ * geometry key (and in the cache file when one is set) and run it once more, so that d_fields / d_coefs
+ * (as for dh_process_batch) hold its results on return.  Synchronises the device; uses the handle's own
+ * scratch.  Changes no GPU setting. */
+int dh_autotune(dh_handle h, const void* d_frames, int dtype, int batch, void* d_fields, void* d_coefs, void* stream,
+                int reps);
+
 /* Validate the settings and report the output geometry: field size M (square), number of coefficients per
  * polarisation in the selected basis, and the field sample pitch dx' = N px / M in metres.  Any pointer may be
  * NULL.  Returns DH_ERROR_INVALIDARGUMENT when a polarisation's window leaves the frame, its tilt centre leaves

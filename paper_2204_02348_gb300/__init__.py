@@ -55,6 +55,25 @@ class DigHoloError(RuntimeError):
         self.code = code
 
 
+DH_MAX_RADICES = 6
+
+
+class dh_tuning(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int), ("chunk_mb", ctypes.c_int), ("nradix", ctypes.c_int),
+                ("radix", ctypes.c_int * DH_MAX_RADICES)]
+
+    def as_dict(self):
+        return {"variant": self.variant, "chunk_mb": self.chunk_mb, "radix": list(self.radix[:self.nradix])}
+
+
+def make_tuning(variant=0, chunk_mb=0, radix=()):
+    t = dh_tuning()
+    t.variant, t.chunk_mb, t.nradix = int(variant), int(chunk_mb), len(radix)
+    for i, r in enumerate(radix):
+        t.radix[i] = int(r)
+    return t
+
+
 class dh_setting(ctypes.Structure):
     _fields_ = [("tilt_deg", (ctypes.c_double * 2) * DH_MAX_POLS),
                 ("defocus", ctypes.c_double * DH_MAX_POLS),
@@ -89,6 +108,12 @@ _PROTOS = {
     "dh_set_precision": [_i, _i],
     "dh_set_variant": [_i, _i],
     "dh_get_variant": [_i, ctypes.POINTER(_i)],
+    "dh_tuning_key": [_i, ctypes.c_char_p, _i],
+    "dh_tuning_candidates": [_i, ctypes.POINTER(dh_tuning), _i, ctypes.POINTER(_i)],
+    "dh_set_tuning": [_i, ctypes.POINTER(dh_tuning)],
+    "dh_get_tuning": [_i, ctypes.POINTER(dh_tuning)],
+    "dh_set_tuning_cache": [_i, ctypes.c_char_p],
+    "dh_autotune": [_i, _p, _i, _i, _p, _p, _p, _i],
     "dh_set_fill_factor_correction": [_i, _i],
     "dh_set_basis_type": [_i, _i],
     "dh_set_ref_calibration": [_i, _p, _i, _i, _i],
@@ -252,6 +277,44 @@ def dh_get_variant(h: int) -> int:
     v = _i()
     _check(_lib.dh_get_variant(h, ctypes.byref(v)))
     return v.value
+
+
+def dh_tuning_key(h: int) -> str:
+    buf = ctypes.create_string_buffer(256)
+    _check(_lib.dh_tuning_key(h, buf, 256))
+    return buf.value.decode()
+
+
+def dh_tuning_candidates(h: int):
+    n = _i()
+    _check(_lib.dh_tuning_candidates(h, None, 0, ctypes.byref(n)))
+    arr = (dh_tuning * max(n.value, 1))()
+    _check(_lib.dh_tuning_candidates(h, arr, n.value, ctypes.byref(n)))
+    return [arr[i].as_dict() for i in range(n.value)]
+
+
+def dh_set_tuning(h: int, tuning=None) -> None:
+    """tuning: None (defaults and the cache), a dh_tuning, or a dict with variant / chunk_mb / radix."""
+    if tuning is None:
+        _check(_lib.dh_set_tuning(h, None))
+        return
+    t = tuning if isinstance(tuning, dh_tuning) else make_tuning(**tuning)
+    _check(_lib.dh_set_tuning(h, ctypes.byref(t)))
+
+
+def dh_get_tuning(h: int) -> dict:
+    t = dh_tuning()
+    _check(_lib.dh_get_tuning(h, ctypes.byref(t)))
+    return t.as_dict()
+
+
+def dh_set_tuning_cache(h: int, path) -> None:
+    _check(_lib.dh_set_tuning_cache(h, None if path is None else os.fsencode(path)))
+
+
+def dh_autotune(h: int, frames, dtype: int, batch: int, fields=None, coefs=None, stream=None, reps: int = 3) -> None:
+    """Time every tuning candidate on these device frames, keep the fastest; fields / coefs receive its results."""
+    _check(_lib.dh_autotune(h, _ptr(frames), dtype, batch, _ptr(fields), _ptr(coefs), _stream(stream), reps))
 
 
 def dh_get_output_dims(h: int):

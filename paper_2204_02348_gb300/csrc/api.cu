@@ -252,6 +252,7 @@ int ensure_plan(Handle* H) {
     std::string why;
     int rc = build_geometry(H->s, &g, &why);
     if (rc) return fail(rc, why);
+    tune_refresh(H, g);
     Tables t;
     build_tables(H->s, g, &t);
     rc = init_device_once(dev);
@@ -285,7 +286,7 @@ int ensure_scratch(Handle* H, size_t bytes) {
     return DH_SUCCESS;
 }
 
-int chunk_frames(size_t per_frame_bytes, int pols, int batch, int device) {
+int chunk_frames(size_t per_frame_bytes, int pols, int batch, int device, size_t target) {
     static int sms[64] = {0};
     int n = 148;
     if (device >= 0 && device < 64) {
@@ -294,7 +295,7 @@ int chunk_frames(size_t per_frame_bytes, int pols, int batch, int device) {
     }
     const size_t per = std::max<size_t>(per_frame_bytes, 1);
     size_t frames = ((size_t)8 * n + pols - 1) / pols;
-    frames = std::max(frames, kScratchTarget / per);
+    frames = std::max(frames, target / per);
     frames = std::min(frames, std::max<size_t>(1, kScratchCap / per));
     return (int)std::max<size_t>(1, std::min<size_t>(frames, (size_t)batch));
 }
@@ -413,7 +414,8 @@ int process(Handle* H, const void* frames, int dtype, int batch, void* window, v
         rc = launch_fused_path(H, P, frames, dtype, batch, fields, coefs, st, H->timer());
     } else {
         const size_t per_frame = split_window_bytes(P) * P.pols;
-        const int chunk = chunk_frames(per_frame, P.pols, batch, H->device);
+        const int chunk = chunk_frames(per_frame, P.pols, batch, H->device,
+                                       H->chunk_mb > 0 ? (size_t)H->chunk_mb << 20 : kScratchTarget);
         rc = ensure_scratch(H, per_frame * chunk);
         if (rc) return rc;
         rc = run_split(P, H->d_scratch, H->scratch_bytes, frames, dtype, batch, window, fields, coefs, st, H->timer());

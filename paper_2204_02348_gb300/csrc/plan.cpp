@@ -199,7 +199,7 @@ void build_tables(const Settings& s, const Geometry& g, Tables* t) {
     for (int k = 0; k < n; ++k) push_c(t->tw_fwd_n, std::cos(-2.0 * kPi * k / n), std::sin(-2.0 * kPi * k / n));
     for (int k = 0; k < m; ++k) push_c(t->tw_inv_m, std::cos(2.0 * kPi * k / m), std::sin(2.0 * kPi * k / m));
     t->radix_n = radix_plan(n);
-    t->radix_m = radix_plan(m);
+    t->radix_m = s.radix_m.empty() ? radix_plan(m) : s.radix_m;
     t->mode_m.clear();
     t->mode_n.clear();
     for (int gg = 0; gg < g.groups; ++gg)

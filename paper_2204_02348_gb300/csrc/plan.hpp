@@ -35,6 +35,7 @@ struct Settings {
     int cal_w = 0, cal_h = 0;            // calibration frame size
     double cal_max = 0.0;                // maximum over every calibration frame
     std::vector<uint16_t> cal;           // first calibration frame [cal_h][cal_w] (the single wavelength)
+    std::vector<int> radix_m;            // radix plan of M chosen by the tuner (empty: radix_plan(M))
 };
 
 // Geometry of one axis of one polarisation (all FP64, computed as the conventions in digholo.h state).

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <cstddef>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -18,7 +19,7 @@ namespace dh {
 // kernels), and at most 1 GiB of scratch.
 constexpr size_t kScratchTarget = 48ull << 20;
 constexpr size_t kScratchCap = 1ull << 30;
-int chunk_frames(size_t per_frame_bytes, int pols, int batch, int device);
+int chunk_frames(size_t per_frame_bytes, int pols, int batch, int device, size_t target = kScratchTarget);
 
 // Records a CUDA event pair around every kernel launch of a handle while enabled; totals per kernel name.
 struct Profiler : dhk::StageTimer {
@@ -64,12 +65,22 @@ struct Handle {
     HostPipe* pipe = nullptr;     // host-buffer pipeline, created on first use
     int variant = 0;              // kernel variant (DH_VARIANT_*): 0 lets the library (or its tuner) choose
     int tuned = 0;                // the tuner's variant for the current settings (0: none)
+    int chunk_mb = 0;             // the tuner's generic-path scratch target per chunk, MiB (0: kScratchTarget)
+    std::string tune_key;         // geometry key the tuning above belongs to
+    bool tune_set = false;        // the tuning was set for tune_key (dh_set_tuning / dh_autotune), not looked up
+    std::string tune_path;        // JSON cache file (dh_set_tuning_cache), empty when none
+    std::map<std::string, dh_tuning> tune_cache;   // choices per geometry key
     Profiler prof;
     dhk::StageTimer* timer() { return prof.on ? &prof : nullptr; }
 };
 
 // Free the host-buffer pipeline of a handle (streams, events, device buffers).
 void release_pipe(Handle* H);
+
+// Tuner (tune.cpp): the geometry key of settings, and the tuning in effect for it: applied to the handle
+// (variant, chunk target, radix plan in the settings) whenever the plan is rebuilt.
+std::string tuning_key(const Settings& s, const Geometry& g);
+void tune_refresh(Handle* H, const Geometry& g);
 
 int fail(int code, const std::string& why);
 int cuda_fail(cudaError_t e, const char* where);
