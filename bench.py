@@ -88,9 +88,10 @@ def whole_job_rate(ws, frames_per_rank, steps, max_ms):
     return ws * frames_per_rank * steps / (max_ms / 1e3)
 
 
-def rank_seed(base, rank):
-    """Each rank draws its own frames (weak scaling over disjoint synthetic shards)."""
-    return base + 1000 * rank
+def rank_shard(frames_per_rank, rank):
+    """The contiguous range of the job's global frame stream that one rank processes (weak scaling: rank r
+    takes frames [r F, (r + 1) F) of the one seeded stream, F frames per rank); returns (first, count)."""
+    return rank * frames_per_rank, frames_per_rank
 
 
 def bytes_per_frame(setup, m, modes):
@@ -338,7 +339,8 @@ def run_ours(args, ws, rank, local):
     setup = syn.setup_batching()
     prec = dh.DH_PRECISION_SPLIT_BF16 if args.precision == "split_bf16" else dh.DH_PRECISION_FP32
     frames_n = args.frames
-    data = syn.make_frames(setup, frames_n, seed=rank_seed(syn.BASE_SEED, rank))
+    first, _ = rank_shard(frames_n, rank)
+    data = syn.make_frames(setup, frames_n, seed=syn.BASE_SEED, first=first)
     host = torch.from_numpy(data["frames"]).pin_memory()
     inputs = [host.to(dev) for _ in range(ROTATE)]
     h = dh.dh_create()
@@ -585,8 +587,10 @@ def run_serving(args, ws, rank, local):
             m, modes, _ = dh.dh_get_output_dims(handles[(kind, gi)])
             outs.append(torch.empty((n, geos[kind][gi].pol_count, modes), dtype=torch.complex64).pin_memory())
 
-        def run(load, arr_rng, budget=8 << 30):
+        def run(load, arr_rng, budget=8 << 30, fifo=False):
             srv = dh.dh_server_create(budget, 8)
+            if fifo:
+                dh.dh_server_set_admission(srv, 0, 0)   # strictly in arrival order
             try:
                 # upload every plan and warm the kernels outside the clock
                 for (kind, gi), h in handles.items():
@@ -611,12 +615,19 @@ def run_serving(args, ws, rank, local):
             finally:
                 dh.dh_server_destroy(srv)
             return {"frames_per_s": total_frames / wall, "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"],
-                    "max_ms": st["max_ms"], "peak_inflight": st["peak_inflight"], "peak_bytes": st["peak_bytes"]}
+                    "max_ms": st["max_ms"], "peak_inflight": st["peak_inflight"], "peak_bytes": st["peak_bytes"],
+                    "wait_p50_ms": st["wait_p50_ms"], "wait_p99_ms": st["wait_p99_ms"],
+                    "kernel_p50_ms": st["kernel_p50_ms"], "kernel_p99_ms": st["kernel_p99_ms"],
+                    "span_p50_ms": st["span_p50_ms"], "span_p99_ms": st["span_p99_ms"],
+                    "kernel_ms_total": st["kernel_ms_total"], "bypassed": st["bypassed"],
+                    "kernel_frames_per_s": total_frames / (st["kernel_ms_total"] / 1e3) if st["kernel_ms_total"] else None}
 
         sat = run(None, None)
         out[prec_name] = {"saturated": sat["frames_per_s"], "saturation_run": sat}
         for load in (0.5, 0.9):
             out[prec_name][f"load_{load}"] = run(load, np.random.default_rng(7))
+        # the same 0.9 load with strictly arrival-ordered admission (no request passes one that does not fit)
+        out[prec_name]["load_0.9_fifo"] = run(0.9, np.random.default_rng(7), fifo=True)
         # stress: the same saturated stream through a 256 MiB budget (requests chunked to fit)
         out[prec_name]["saturated_256MiB"] = run(None, None, budget=256 << 20)
         for h in handles.values():

@@ -420,12 +420,25 @@ typedef struct dh_stats {
     double frames_per_s;             /* frames completed / (last completion - first submission) */
     size_t budget_bytes, peak_bytes; /* HBM budget and the largest reservation total seen */
     int max_inflight, peak_inflight;
+    double wait_p50_ms, wait_p99_ms;     /* submission to admission */
+    double kernel_p50_ms, kernel_p99_ms; /* device time of a request's own kernels (CUDA events around them) */
+    double span_p50_ms, span_p99_ms;     /* device time from a request's first copy to its last on its stream */
+    double kernel_ms_total;              /* sum of every completed request's kernel time */
+    long long bypassed;                  /* admissions of a request past an earlier one that did not fit */
 } dh_stats;
 
 /* Create a server on the current device with an HBM budget in bytes (reserved with one allocation; 0 is
  * allowed and then admits nothing) and at most max_inflight concurrently processed requests (1..64, one
- * stream each). */
+ * stream each).  Admission takes queued requests in arrival order; a request that does not fit the free
+ * budget lets later ones that do fit go first, until it has waited DH_SERVER_MAX_WAIT_MS or been passed
+ * DH_SERVER_MAX_BYPASS times, after which nothing is admitted before it. */
+#define DH_SERVER_MAX_WAIT_MS 25
+#define DH_SERVER_MAX_BYPASS 8
 int dh_server_create(size_t hbm_budget, int max_inflight, dh_server* out);
+/* Admission policy of a server: a request that does not fit may be passed by later ones until it has been
+ * passed max_bypass times or has waited max_wait_ms (defaults DH_SERVER_MAX_BYPASS and DH_SERVER_MAX_WAIT_MS);
+ * max_bypass = 0 admits strictly in arrival order.  Negative values give DH_ERROR_INVALIDARGUMENT. */
+int dh_server_set_admission(dh_server s, int max_bypass, int max_wait_ms);
 /* Queue a request; *ticket identifies it.  Validation errors are returned here. */
 int dh_server_submit(dh_server s, const dh_request* r, uint64_t* ticket);
 /* Wait for a request to finish (timeout_ms < 0: no limit).  Returns the request's own status, or

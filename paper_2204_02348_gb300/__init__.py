@@ -89,7 +89,11 @@ class dh_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_longlong), ("completed", ctypes.c_longlong), ("failed", ctypes.c_longlong),
                 ("frames", ctypes.c_longlong), ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double),
                 ("max_ms", ctypes.c_double), ("frames_per_s", ctypes.c_double), ("budget_bytes", ctypes.c_size_t),
-                ("peak_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int), ("peak_inflight", ctypes.c_int)]
+                ("peak_bytes", ctypes.c_size_t), ("max_inflight", ctypes.c_int), ("peak_inflight", ctypes.c_int),
+                ("wait_p50_ms", ctypes.c_double), ("wait_p99_ms", ctypes.c_double),
+                ("kernel_p50_ms", ctypes.c_double), ("kernel_p99_ms", ctypes.c_double),
+                ("span_p50_ms", ctypes.c_double), ("span_p99_ms", ctypes.c_double),
+                ("kernel_ms_total", ctypes.c_double), ("bypassed", ctypes.c_longlong)]
 
 
 _i, _d, _p = ctypes.c_int, ctypes.c_double, ctypes.c_void_p
@@ -136,6 +140,7 @@ _PROTOS = {
     "dh_check_bounded_wait": [ctypes.c_longlong, ctypes.POINTER(_i)],
     "dh_server_create": [ctypes.c_size_t, _i, ctypes.POINTER(_p)],
     "dh_server_submit": [_p, ctypes.POINTER(dh_request), ctypes.POINTER(ctypes.c_uint64)],
+    "dh_server_set_admission": [_p, _i, _i],
     "dh_server_wait": [_p, ctypes.c_uint64, _i],
     "dh_server_stats": [_p, ctypes.POINTER(dh_stats)],
     "dh_server_destroy": [_p],
@@ -432,6 +437,10 @@ def dh_server_create(hbm_budget: int, max_inflight: int = 8) -> int:
     out = _p()
     _check(_lib.dh_server_create(hbm_budget, max_inflight, ctypes.byref(out)))
     return out.value
+
+
+def dh_server_set_admission(server: int, max_bypass: int, max_wait_ms: int) -> None:
+    _check(_lib.dh_server_set_admission(server, max_bypass, max_wait_ms))
 
 
 def dh_server_submit(server: int, geometry: int, frames, dtype: int, batch: int, fields=None, coefs=None) -> int:

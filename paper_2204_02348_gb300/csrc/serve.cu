@@ -1,9 +1,11 @@
 // Serving loop: continuous batching of reconstruction requests under a fixed HBM budget.
 //
-// One scheduler thread per server owns the device work.  Submitted requests wait in a FIFO queue; the head is
-// admitted as soon as a stream slot is free and the budget arena (one device allocation, first-fit with
-// coalescing) can hold its reservation: input frames (the rows holding the windows), the requested outputs and
-// the generic path's scratch for one chunk of frames.  An admitted request is queued on its slot's stream as host-to-device copy,
+// One scheduler thread per server owns the device work.  Submitted requests wait in an arrival-ordered queue;
+// a request is admitted as soon as a stream slot is free and the budget arena (one device allocation,
+// first-fit with coalescing) can hold its reservation: input frames (the rows holding the windows), the
+// requested outputs and the generic path's scratch for one chunk of frames.  A request that does not fit lets
+// later ones that do fit go first (no head-of-line blocking), until it has waited DH_SERVER_MAX_WAIT_MS or
+// been passed DH_SERVER_MAX_BYPASS times; from then on nothing is admitted before it, so it cannot starve.  An admitted request is queued on its slot's stream as host-to-device copy,
 // reconstruction (the same kernels as dh_process_batch, with the handle's device-resident plan and the
 // request's own scratch), and device-to-host copies of its outputs, chunk after chunk, followed by an event.
 // The scheduler polls the events, releases the reservation and the slot of every finished request, records
@@ -91,13 +93,17 @@ struct Req {
     size_t off = 0;
     int status = DH_SUCCESS;
     bool done = false;
-    double t_submit = 0, t_done = 0;
+    double t_submit = 0, t_admit = 0, t_done = 0;
+    int bypassed = 0;              // later requests admitted while this one did not fit
     std::string why;
 };
 
 struct Slot {
     cudaStream_t st = nullptr;
-    cudaEvent_t ev = nullptr;
+    cudaEvent_t ev = nullptr;      // after the request's last copy (timing)
+    cudaEvent_t ev0 = nullptr;     // before its first copy (timing)
+    std::vector<cudaEvent_t> kev;  // pairs around each chunk's kernels (timing), grown as needed
+    int kpairs = 0;                // pairs used by the current request
     Req* req = nullptr;
 };
 
@@ -118,11 +124,12 @@ struct dh_server_s {
     std::thread th;
     bool stop = false;
     // statistics
-    long long submitted = 0, completed = 0, failed = 0, frames = 0;
-    std::vector<double> lat_ms;
+    long long submitted = 0, completed = 0, failed = 0, frames = 0, bypassed = 0;
+    std::vector<double> lat_ms, wait_ms, kernel_ms, span_ms;
     double t_first = -1, t_last = 0;
     size_t peak_bytes = 0;
     int inflight = 0, peak_inflight = 0;
+    int max_bypass = DH_SERVER_MAX_BYPASS, max_wait_ms = DH_SERVER_MAX_WAIT_MS;
 };
 
 namespace dh {
@@ -136,17 +143,42 @@ bool valid(dh_server_s* s) {
     return g_servers.count(s) != 0;
 }
 
-void finish(dh_server_s* S, Req* r, double t) {
+void finish(dh_server_s* S, Req* r, double t, const Slot* sl = nullptr) {
     r->done = true;
     r->t_done = t;
     if (r->status == DH_SUCCESS) {
         S->completed += 1;
         S->frames += r->r.batch;
         S->lat_ms.push_back(1e3 * (r->t_done - r->t_submit));
+        S->wait_ms.push_back(1e3 * (r->t_admit - r->t_submit));
         S->t_last = std::max(S->t_last, t);
+        if (sl) {
+            // device times from the slot's timing events (all complete: the last one has been reached)
+            float span = 0.f, k = 0.f, ktot = 0.f;
+            if (cudaEventElapsedTime(&span, sl->ev0, sl->ev) == cudaSuccess) S->span_ms.push_back(span);
+            bool ok = true;
+            for (int i = 0; i < sl->kpairs && ok; ++i) {
+                ok = cudaEventElapsedTime(&k, sl->kev[2 * i], sl->kev[2 * i + 1]) == cudaSuccess;
+                ktot += k;
+            }
+            if (ok) S->kernel_ms.push_back(ktot);
+        }
     } else {
         S->failed += 1;
     }
+}
+
+// A timing event pair of a slot for one more chunk (created on first use).
+bool chunk_events(Slot& sl, cudaEvent_t* a, cudaEvent_t* b) {
+    while ((int)sl.kev.size() < 2 * (sl.kpairs + 1)) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) return false;
+        sl.kev.push_back(e);
+    }
+    *a = sl.kev[2 * sl.kpairs];
+    *b = sl.kev[2 * sl.kpairs + 1];
+    sl.kpairs += 1;
+    return true;
 }
 
 // Queue one admitted request on its slot's stream (called with the server lock held).
@@ -157,6 +189,8 @@ void launch(dh_server_s* S, Req* r, Slot& sl) {
         std::lock_guard<std::mutex> hl(H->mu);
         rc = ensure_plan(H);
     }
+    sl.kpairs = 0;
+    cudaEventRecord(sl.ev0, sl.st);
     if (rc) {
         r->status = rc;
         r->why = "plan: " + std::string(dh_last_error());
@@ -189,7 +223,11 @@ void launch(dh_server_s* S, Req* r, Slot& sl) {
             rc = cuda_fail(e, "request frames upload");
             break;
         }
+        cudaEvent_t ka = nullptr, kb = nullptr;
+        const bool timed = chunk_events(sl, &ka, &kb);
+        if (timed) cudaEventRecord(ka, sl.st);
         rc = process_plan(H, Pc, d_frames, r->r.dtype, n, d_fields, d_coefs, d_scratch, r->b_scratch, sl.st);
+        if (timed) cudaEventRecord(kb, sl.st);
         if (rc) break;
         if (d_fields) {
             e = cudaMemcpyAsync((unsigned char*)r->r.h_fields + f0 * field_bytes, d_fields, n * field_bytes,
@@ -226,28 +264,41 @@ void scheduler(dh_server_s* S) {
             S->arena->release(r->off, r->bytes);
             sl.req = nullptr;
             S->inflight -= 1;
-            finish(S, r, now_s());
+            finish(S, r, now_s(), &sl);
             S->cv_done.notify_all();
         }
-        // admissions, first come first served
-        while (!S->queue.empty() && !S->stop) {
-            Slot* free_slot = nullptr;
-            for (Slot& sl : S->slots)
-                if (!sl.req) {
-                    free_slot = &sl;
-                    break;
+        // admissions in arrival order; a request that does not fit lets later ones that fit go first, until it
+        // has waited or been passed enough (then nothing is admitted before it)
+        if (!S->stop) {
+            const double tnow = now_s();
+            auto it = S->queue.begin();
+            while (it != S->queue.end()) {
+                Slot* free_slot = nullptr;
+                for (Slot& sl : S->slots)
+                    if (!sl.req) {
+                        free_slot = &sl;
+                        break;
+                    }
+                if (!free_slot) break;
+                Req* r = *it;
+                size_t off = 0;
+                if (!S->arena->alloc(r->bytes, &off)) {
+                    if (r->bypassed >= S->max_bypass || 1e3 * (tnow - r->t_submit) >= S->max_wait_ms) break;
+                    ++it;
+                    continue;
                 }
-            if (!free_slot) break;
-            Req* r = S->queue.front();
-            size_t off = 0;
-            if (!S->arena->alloc(r->bytes, &off)) break;
-            S->queue.pop_front();
-            r->off = off;
-            free_slot->req = r;
-            S->inflight += 1;
-            S->peak_inflight = std::max(S->peak_inflight, S->inflight);
-            S->peak_bytes = std::max(S->peak_bytes, S->arena->used());
-            launch(S, r, *free_slot);
+                // every earlier request still queued is passed by this one
+                for (auto jt = S->queue.begin(); jt != it; ++jt) (*jt)->bypassed += 1;
+                if (it != S->queue.begin()) S->bypassed += 1;
+                it = S->queue.erase(it);
+                r->off = off;
+                r->t_admit = tnow;
+                free_slot->req = r;
+                S->inflight += 1;
+                S->peak_inflight = std::max(S->peak_inflight, S->inflight);
+                S->peak_bytes = std::max(S->peak_bytes, S->arena->used());
+                launch(S, r, *free_slot);
+            }
         }
         if (S->stop) {
             while (!S->queue.empty()) {
@@ -297,11 +348,13 @@ int dh_server_create(size_t hbm_budget, int max_inflight, dh_server* out) {
     S->slots.resize(max_inflight);
     for (Slot& sl : S->slots) {
         e = cudaStreamCreateWithFlags(&sl.st, cudaStreamNonBlocking);
-        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaEventCreate(&sl.ev);
+        if (e == cudaSuccess) e = cudaEventCreate(&sl.ev0);
         if (e != cudaSuccess) {
             for (Slot& s2 : S->slots) {
                 if (s2.st) cudaStreamDestroy(s2.st);
                 if (s2.ev) cudaEventDestroy(s2.ev);
+                if (s2.ev0) cudaEventDestroy(s2.ev0);
             }
             if (S->base) cudaFree(S->base);
             delete S->arena;
@@ -315,6 +368,15 @@ int dh_server_create(size_t hbm_budget, int max_inflight, dh_server* out) {
     }
     S->th = std::thread(scheduler, S);
     *out = S;
+    return DH_SUCCESS;
+}
+
+int dh_server_set_admission(dh_server s, int max_bypass, int max_wait_ms) {
+    if (!valid(s)) return fail(DH_ERROR_INVALIDHANDLE, "invalid server");
+    if (max_bypass < 0 || max_wait_ms < 0) return fail(DH_ERROR_INVALIDARGUMENT, "admission limits must be >= 0");
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->max_bypass = max_bypass;
+    s->max_wait_ms = max_wait_ms;
     return DH_SUCCESS;
 }
 
@@ -410,17 +472,25 @@ int dh_server_stats(dh_server s, dh_stats* out) {
     st.completed = s->completed;
     st.failed = s->failed;
     st.frames = s->frames;
-    std::vector<double> l = s->lat_ms;
-    std::sort(l.begin(), l.end());
-    if (!l.empty()) {
-        auto pct = [&](double p) {
-            size_t i = (size_t)std::ceil(p * l.size()) - 1;
-            return l[std::min(i, l.size() - 1)];
-        };
-        st.p50_ms = pct(0.50);
-        st.p99_ms = pct(0.99);
-        st.max_ms = l.back();
+    auto pct = [](std::vector<double> l, double p) {
+        if (l.empty()) return 0.0;
+        std::sort(l.begin(), l.end());
+        const size_t i = (size_t)std::ceil(p * l.size()) - 1;
+        return l[std::min(i, l.size() - 1)];
+    };
+    if (!s->lat_ms.empty()) {
+        st.p50_ms = pct(s->lat_ms, 0.50);
+        st.p99_ms = pct(s->lat_ms, 0.99);
+        st.max_ms = pct(s->lat_ms, 1.0);
     }
+    st.wait_p50_ms = pct(s->wait_ms, 0.50);
+    st.wait_p99_ms = pct(s->wait_ms, 0.99);
+    st.kernel_p50_ms = pct(s->kernel_ms, 0.50);
+    st.kernel_p99_ms = pct(s->kernel_ms, 0.99);
+    st.span_p50_ms = pct(s->span_ms, 0.50);
+    st.span_p99_ms = pct(s->span_ms, 0.99);
+    for (double k : s->kernel_ms) st.kernel_ms_total += k;
+    st.bypassed = s->bypassed;
     st.frames_per_s = (s->frames > 0 && s->t_last > s->t_first) ? s->frames / (s->t_last - s->t_first) : 0.0;
     st.budget_bytes = s->budget;
     st.peak_bytes = s->peak_bytes;
@@ -446,6 +516,8 @@ int dh_server_destroy(dh_server s) {
         if (sl.st) cudaStreamSynchronize(sl.st);
         if (sl.st) cudaStreamDestroy(sl.st);
         if (sl.ev) cudaEventDestroy(sl.ev);
+        if (sl.ev0) cudaEventDestroy(sl.ev0);
+        for (cudaEvent_t e : sl.kev) cudaEventDestroy(e);
     }
     for (auto& kv : s->reqs) delete kv.second;
     if (s->base) cudaFree(s->base);

@@ -217,3 +217,55 @@ def test_mixed_precisions_equal_alone():
     finally:
         for h in handles:
             dh.dh_destroy(h)
+
+
+def test_small_requests_pass_one_that_does_not_fit_and_report_device_time():
+    """Three large requests and a budget that holds two of them (a request reserves at most half the budget):
+    the third large one waits, and small requests submitted behind it are admitted first (no head-of-line
+    blocking); it still completes (its wait is bounded).  Every result equals the lone run; stats report device
+    times."""
+    import torch
+    import paper_2204_02348_gb300 as dh
+    rng = np.random.default_rng(95)
+    big_s = syn.serving_geometry("1024x1024_1pol", rng)
+    small_s = syn.serving_geometry("256x256_1pol", rng)
+    hb, hs = dh.dh_create(), dh.dh_create()
+    dh.configure(hb, big_s)
+    dh.configure(hs, small_s)
+    big = [syn.make_frames(big_s, 48, seed=1100 + k)["frames"] for k in range(3)]
+    small = [syn.make_frames(small_s, 1, seed=1200 + k)["frames"] for k in range(10)]
+    alone_b = [_alone(dh, torch, hb, big_s, fr) for fr in big]
+    alone_s = [_alone(dh, torch, hs, small_s, fr) for fr in small]
+
+    def bufs(h, s, fr):
+        m, modes, _ = dh.dh_get_output_dims(h)
+        n = fr.shape[0]
+        return (torch.from_numpy(fr).pin_memory(),
+                torch.full((n, s.pol_count, m, m), complex(float("nan"), 0), dtype=torch.complex64).pin_memory(),
+                torch.full((n, s.pol_count, modes), complex(float("nan"), 0), dtype=torch.complex64).pin_memory())
+
+    bb = [bufs(hb, big_s, fr) for fr in big]
+    sb = [bufs(hs, small_s, fr) for fr in small]
+    # per large frame: its rows, field, coefficients and the generic path's scratch (r1 and the window); a budget
+    # of 62.4 such frames gives each large request one chunk of 31 frames, so two run and the third waits, and
+    # 0.4 of a large frame stays free, room for the small requests
+    m, modes, _ = dh.dh_get_output_dims(hb)
+    n = big_s.window
+    per_frame = big_s.frame_w * big_s.frame_h * 2 + m * m * 8 + modes * 8 + (m * n + m * m) * 8
+    srv = dh.dh_server_create(int(62.4 * per_frame), 8)
+    try:
+        tb = [dh.dh_server_submit(srv, hb, b[0], dh.DH_DTYPE_U16, 48, b[1], b[2]) for b in bb]
+        ts = [dh.dh_server_submit(srv, hs, b[0], dh.DH_DTYPE_U16, 1, b[1], b[2]) for b in sb]
+        for t in tb + ts:
+            dh.dh_server_wait(srv, t, -1)
+        st = dh.dh_server_stats(srv)
+    finally:
+        dh.dh_server_destroy(srv)
+        dh.dh_destroy(hb)
+        dh.dh_destroy(hs)
+    assert st["completed"] == 13 and st["failed"] == 0
+    assert 1 <= st["bypassed"] <= 10
+    for (f, c), b in zip(alone_b + alone_s, bb + sb):
+        assert np.array_equal(b[1].numpy(), f) and np.array_equal(b[2].numpy(), c)
+    assert 0 < st["kernel_p50_ms"] <= st["kernel_p99_ms"] <= st["span_p99_ms"] + 1e-3
+    assert st["kernel_ms_total"] > 0 and st["wait_p99_ms"] >= st["wait_p50_ms"] >= 0
