@@ -93,7 +93,7 @@ static std::vector<int> pos_table(int len, const std::vector<int>& rad) {
 struct PlanImage {
     Blob b;
     size_t o_twn = 0, o_twm = 0, o_pn = 0, o_pm = 0, o_mm = 0, o_mn = 0, o_st = 0, o_bt = 0;
-    size_t o_pol[DH_MAX_POLS][11] = {};
+    size_t o_pol[DH_MAX_POLS][13] = {};
 };
 
 static int build_plan_image(const Geometry& g, const Tables& t, PlanImage* im) {
@@ -123,6 +123,8 @@ static int build_plan_image(const Geometry& g, const Tables& t, PlanImage* im) {
         im->o_pol[p][8] = b.put(pt.hgy_tc.data(), pt.hgy_tc.size() * 2);
         im->o_pol[p][9] = b.put(pt.cal.data(), pt.cal.size() * 4);
         im->o_pol[p][10] = b.put(pt.pr.data(), pt.pr.size());
+        im->o_pol[p][11] = b.put(pt.coef_tc.data(), pt.coef_tc.size());
+        im->o_pol[p][12] = b.put(pt.score_tc.data(), pt.score_tc.size());
     }
     return DH_SUCCESS;
 }
@@ -171,7 +173,13 @@ static void plan_from_image(const Settings& s, const Geometry& g, const Tables& 
         pd.hgy_tc = (const uint16_t*)(base + im.o_pol[p][8]);
         pd.cal = t.pol[p].cal.empty() ? nullptr : (const float*)(base + im.o_pol[p][9]);
         pd.pr = t.pol[p].pr.empty() ? nullptr : base + im.o_pol[p][10];
+        pd.coef_tc = t.pol[p].coef_tc.empty() ? nullptr : base + im.o_pol[p][11];
+        pd.score_tc = t.pol[p].score_tc.empty() ? nullptr : base + im.o_pol[p][12];
     }
+    P.coef_np = 0;
+    bool coef_all = g.pols > 0;
+    for (int p = 0; p < g.pols; ++p) coef_all = coef_all && !t.pol[p].coef_tc.empty();
+    if (coef_all) P.coef_np = t.pol[0].coef_np;
 }
 
 int upload_plan(const Settings& s, const Geometry& g, const Tables& t, void** out_blob, dhk::Plan* out) {
@@ -232,6 +240,8 @@ int init_device_once(int dev) {
     cudaError_t e = dhk::split_init();
     if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
     e = dhk::tc_init();
+    if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
+    e = dhk::coef_tc_init();
     if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
     e = fused_init();
     if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");

@@ -667,6 +667,14 @@ cudaError_t launch_last(const Plan& P, const Batch& B, cudaStream_t st, StageTim
     dim3 g3(P.pols, zf);
     const size_t sm3 = ((size_t)(P.m + std::max(P.groups, 1)) * kChunkI +
                         (size_t)(P.m / 2 + 1) * 2 * ((P.groups + 3) / 4) + 2 * (size_t)P.m) * sizeof(float2);
+    if (coef_tc_supported(P, B)) {
+        // no field requested: the y transform and the y overlap as one tensor-core contraction
+        if (tm) tm->start(st);
+        cudaError_t e = launch_coef_tc(P, B, st);
+        if (tm) tm->stop(st, "k_coef_tc");
+        if (e != cudaSuccess) return e;
+        return cudaGetLastError();
+    }
     if (tc_supported(P)) {
         if (tm) tm->start(st);
         cudaError_t e = launch_yinv_tc(P, B, st);

@@ -30,6 +30,10 @@ struct PolDev {
     const uint16_t* hgy_tc;  // [2][NP][M] bf16 hi / lo of hg_y, tensor-core core-matrix layout
     const float* cal;        // nullable [N][N] reference-calibration factor over the window
     const unsigned char* pr; // nullable table block of the column-pruned fused kernel (fused_pr.hpp)
+    const unsigned char* coef_tc;   // nullable coefficient-only tensor-core tables: bf16 hi / lo planes of the
+                                    // y map [coef_np][2M] (canonical K-major), then float2 X[G][M]
+    const unsigned char* score_tc;  // nullable scoring tables, the same layout: phased y map over the raw box
+                                    // rows, then float2 Xh[G][M] over the raw box columns
 };
 
 struct Plan {
@@ -37,6 +41,7 @@ struct Plan {
     int width, height;
     int precision;           // DH_PRECISION_*
     int tc_np;               // rows of the tensor-core B operand (16 or 32)
+    int coef_np;             // rows of the coefficient-only contraction's B operand (2G rounded up to 16), 0: none
     int nrad_n, nrad_m;
     int rad_n[kMaxRadices];
     int rad_m[kMaxRadices];
@@ -94,6 +99,26 @@ cudaError_t basis_init();
 int avg_slices(long long elems);
 cudaError_t launch_avg(const float2* g, float2* part, float2* out, int groups, int members, long long elems,
                        long long mstride, long long gstride, cudaStream_t stream, StageTimer* timer);
+
+// Coefficient-only split-BF16 last kernel (k_coef_tc.cu): the y transform, correction and y overlap as one
+// tensor-core contraction of the x-inverse-transformed rows; for batches without fields.
+bool coef_tc_supported(const Plan& plan, const Batch& batch);
+cudaError_t coef_tc_init();
+cudaError_t launch_coef_tc(const Plan& plan, const Batch& batch, cudaStream_t stream);
+
+// Where an alignment candidate's box sits in the superset spectra of candidate scoring: window w (frame slot
+// times pols plus polarisation) at xs + w ms msx, box row q and column p of polarisation pol at
+// (qoff[pol] + q) msx + poff[pol] + p (raw DFT bins, before mask and phases).
+struct BoxSrc {
+    const float2* xs;
+    int ms, msx;
+    int qoff[DH_MAX_POLS], poff[DH_MAX_POLS];
+};
+// The same contraction reading a candidate's box bins straight from the superset spectra, with the candidate's
+// scoring tables (PolDev::score_tc): the x inverse transform is folded into the x weights, so no x-inverse
+// kernel runs.  Coefficients of frame slot b at batch.coefs[(b pols + pol) modes] (batch.frame0 0).
+bool score_tc_supported(const Plan& plan, const Batch& batch);
+cudaError_t launch_score_tc(const Plan& plan, const Batch& batch, const BoxSrc& src, cudaStream_t stream);
 
 // Split-BF16 tensor-core variant of the last generic kernel (k_overlap_tc.cu).
 bool tc_supported(const Plan& plan);

@@ -6,9 +6,11 @@
 #include "fused_pr.hpp"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <thread>
 
 namespace dh {
 
@@ -137,6 +139,12 @@ uint16_t bf16_bits(float v) {
     return (uint16_t)(u >> 16);
 }
 
+// Offset in elements of (row, k) in a [rows][K] bf16 tensor-core operand stored K-major in 8 x 8 core
+// matrices (8 rows x 16 bytes, contiguous; core (row / 8, k / 8) at ((row / 8) (K / 8) + k / 8) * 64).
+static size_t umma_offset(int row, int k, int K) {
+    return ((size_t)(row >> 3) * (size_t)(K >> 3) + (size_t)(k >> 3)) * 64 + (size_t)(row & 7) * 8 + (size_t)(k & 7);
+}
+
 static float bf16_value(uint16_t b) {
     const uint32_t u = (uint32_t)b << 16;
     float f;
@@ -147,6 +155,32 @@ static float bf16_value(uint16_t b) {
 static void push_c(std::vector<float>& v, double re, double im) {
     v.push_back((float)re);
     v.push_back((float)im);
+}
+
+// Beam-centre phase of box bin klo + q along one axis, FP64: (-1)^klo exp(-2 pi i (klo + q) eps / N) / N, divided
+// by the pixel response sinc((klo + q) / N) when the fill-factor correction is on.
+static void phase_fp64(const Settings& s, const AxisGeom& a, int n, int q, double* re, double* im) {
+    const double sgn = (a.klo % 2 == 0) ? 1.0 : -1.0;
+    const double ang = -2.0 * kPi * (double)(a.klo + q) * a.eps / n;
+    double w = sgn / n;
+    if (s.fill_factor) {
+        const double u = kPi * (double)(a.klo + q) / n;
+        w /= (u == 0.0) ? 1.0 : std::sin(u) / u;
+    }
+    *re = w * std::cos(ang);
+    *im = w * std::sin(ang);
+}
+
+// Tilt and defocus correction of field sample i along one axis, FP64:
+// (-1)^i exp(-2 pi i (kappa - k0)(i - M/2) / M) exp(-i pi D x'_i^2 / lambda).
+static void corr_fp64(const Settings& s, const Geometry& g, const PolGeom& pg, const AxisGeom& a, int i, double* re,
+                      double* im) {
+    const int m = g.m;
+    const double xp = (double)(i - m / 2) * g.dx;
+    const double ang = -2.0 * kPi * (a.kappa - a.k0) * (double)(i - m / 2) / m - kPi * pg.defocus * xp * xp / s.wavelength;
+    const double sg = (i % 2 == 0) ? 1.0 : -1.0;
+    *re = sg * std::cos(ang);
+    *im = sg * std::sin(ang);
 }
 
 // LG_p^l as a sum over the HG modes of its group N = 2p + |l| (Hermite-Laguerre-Gauss relation, as in
@@ -192,7 +226,7 @@ void lg_transform(int groups, std::vector<double>* t) {
     }
 }
 
-void build_tables(const Settings& s, const Geometry& g, Tables* t) {
+void build_tables(const Settings& s, const Geometry& g, Tables* t, bool score) {
     const int n = g.n, m = g.m;
     t->tw_fwd_n.clear();
     t->tw_inv_m.clear();
@@ -247,22 +281,15 @@ void build_tables(const Settings& s, const Geometry& g, Tables* t) {
             const AxisGeom& a = pg.ax[ax];
             ph[ax]->clear();
             co[ax]->clear();
-            const double sgn = (a.klo % 2 == 0) ? 1.0 : -1.0;
             for (int q = 0; q < m; ++q) {
-                const double ang = -2.0 * kPi * (double)(a.klo + q) * a.eps / n;
-                double w = sgn / n;
-                if (s.fill_factor) {
-                    // 100 % fill factor: divide by the pixel response sinc(k / N) of this axis
-                    const double u = kPi * (double)(a.klo + q) / n;
-                    w /= (u == 0.0) ? 1.0 : std::sin(u) / u;
-                }
-                push_c(*ph[ax], w * std::cos(ang), w * std::sin(ang));
+                double re, im;
+                phase_fp64(s, a, n, q, &re, &im);
+                push_c(*ph[ax], re, im);
             }
             for (int i = 0; i < m; ++i) {
-                const double ang = -2.0 * kPi * (a.kappa - a.k0) * (double)(i - m / 2) / m
-                                   - kPi * pg.defocus * xp[i] * xp[i] / s.wavelength;
-                const double sg = (i % 2 == 0) ? 1.0 : -1.0;
-                push_c(*co[ax], sg * std::cos(ang), sg * std::sin(ang));
+                double re, im;
+                corr_fp64(s, g, pg, a, i, &re, &im);
+                push_c(*co[ax], re, im);
             }
         }
         // mask rows: the same FP64 expression as the definition, ((ky-kappa_y)/r)^2 + ((kx-kappa_x)/r)^2 <= 1
@@ -305,7 +332,199 @@ void build_tables(const Settings& s, const Geometry& g, Tables* t) {
             }
         }
         build_pr_block(g, p, &pt);
+        build_coef_tc(s, g, p, u, &pt);
+        pt.score_tc.clear();
+        if (score) build_score_tc(s, g, p, u, &pt);
     }
+}
+
+void build_tables_many(const Settings& s, const std::vector<Geometry>& g, std::vector<Tables>* t, bool score,
+                       int threads) {
+    const int count = (int)g.size();
+    t->resize(count);
+    if (threads <= 0) threads = std::min(16, (int)std::max(1u, std::thread::hardware_concurrency()));
+    threads = std::max(1, std::min(threads, count));
+    std::atomic<int> next{0};
+    auto work = [&]() {
+        for (int k = next++; k < count; k = next++) build_tables(s, g[k], &(*t)[k], score);
+    };
+    std::vector<std::thread> pool;
+    for (int i = 1; i < threads; ++i) pool.emplace_back(work);
+    work();
+    for (std::thread& th : pool) th.join();
+}
+
+// out[k] = sum_j in[j * stride] exp(+2 pi i k j / n) for k < n, in FP64: Cooley-Tukey on the smallest prime
+// factor p of n (n = p m: p interleaved length-m transforms combined with twiddles), a direct sum for a prime.
+// wr / wi: exp(+2 pi i e / L) for e < L, L a multiple of n (the root of unity of order n is entry L / n).
+// Exponents k j mod n are stepped incrementally (one conditional subtraction each), so no division runs in the
+// inner loops.
+static void dft_plus(const double* re, const double* im, int stride, int n, const double* wr, const double* wi, int L,
+                     double* ore, double* oim) {
+    int p = 2;
+    while (p * p <= n && n % p) ++p;
+    if (n % p) p = n;
+    const int sc = L / n;
+    if (p == n) {
+        for (int k = 0; k < n; ++k) {
+            double sr = 0.0, si = 0.0;
+            int e = 0;                                   // k j mod n
+            for (int j = 0; j < n; ++j) {
+                const double xr = re[(size_t)j * stride], xi = im[(size_t)j * stride];
+                sr += xr * wr[e * sc] - xi * wi[e * sc];
+                si += xr * wi[e * sc] + xi * wr[e * sc];
+                e += k;
+                if (e >= n) e -= n;
+            }
+            ore[k] = sr;
+            oim[k] = si;
+        }
+        return;
+    }
+    const int m = n / p;
+    std::vector<double> sr((size_t)p * m), si((size_t)p * m);
+    for (int r = 0; r < p; ++r)
+        dft_plus(re + (size_t)r * stride, im + (size_t)r * stride, stride * p, m, wr, wi, L, &sr[(size_t)r * m], &si[(size_t)r * m]);
+    int km = 0;                                          // k mod m
+    for (int k = 0; k < n; ++k) {
+        double tr = 0.0, ti = 0.0;
+        int e = 0;                                       // r k mod n
+        for (int r = 0; r < p; ++r) {
+            const double xr = sr[(size_t)r * m + km], xi = si[(size_t)r * m + km];
+            tr += xr * wr[e * sc] - xi * wi[e * sc];
+            ti += xr * wi[e * sc] + xi * wr[e * sc];
+            e += k;
+            if (e >= n) e -= n;
+        }
+        ore[k] = tr;
+        oim[k] = ti;
+        if (++km == m) km = 0;
+    }
+}
+
+// Bytes of one tensor-core contraction table: the B operand [np][2M] as bfloat16 hi, then lo, in the canonical
+// K-major layout, built from the complex K-side map A_n[k] (rows n < G: [Re A_n | -Im A_n], rows G + n:
+// [Im A_n | Re A_n], rows past 2G zero), then float2 C[G][M], the second contraction's weights.  A and C are
+// FP64 [G][M] (real and imaginary parts apart).
+static void pack_tc_table(int m, int G, int np, const std::vector<double>& ar, const std::vector<double>& ai,
+                          const std::vector<double>& cr, const std::vector<double>& ci, std::vector<unsigned char>* out) {
+    const int K = 2 * m;
+    std::vector<uint16_t> hi((size_t)np * K, 0), lo((size_t)np * K, 0);
+    auto put = [&](int row, int k, double v) {
+        const uint16_t h = bf16_bits((float)v);
+        const size_t off = (size_t)umma_offset(row, k, K);
+        hi[off] = h;
+        lo[off] = bf16_bits((float)(v - (double)bf16_value(h)));
+    };
+    for (int n = 0; n < G; ++n)
+        for (int q = 0; q < m; ++q) {
+            const double re = ar[(size_t)n * m + q], im = ai[(size_t)n * m + q];
+            put(n, q, re);
+            put(n, m + q, -im);
+            put(G + n, q, im);
+            put(G + n, m + q, re);
+        }
+    const size_t plane = (size_t)np * K * 2;
+    out->resize(2 * plane + (size_t)G * m * 8);
+    std::memcpy(out->data(), hi.data(), plane);
+    std::memcpy(out->data() + plane, lo.data(), plane);
+    float* x = reinterpret_cast<float*>(out->data() + 2 * plane);
+    for (size_t k = 0; k < (size_t)G * m; ++k) {
+        x[2 * k] = (float)cr[k];
+        x[2 * k + 1] = (float)ci[k];
+    }
+}
+
+// Limits of the contraction tables: 2G <= 48 output columns, M a multiple of 16 and at most 384.
+static bool tc_table_fits(int m, int G) { return G > 0 && 2 * G <= 48 && m <= 384 && m % 16 == 0; }
+
+// The y map and the x weights of the regrouped sums, FP64 [G][M]:
+//   Y_n[q] = sum_j u_n(y'_j) dy' corr_y[j] exp(+2 pi i q j / M),   X_m[i] = u_m(x'_i) dx' corr_x[i].
+static void coef_maps(const Settings& s, const Geometry& g, int p, const std::vector<double>& u, std::vector<double>* yr,
+                      std::vector<double>* yi, std::vector<double>* xr, std::vector<double>* xi) {
+    const int m = g.m, G = g.groups;
+    const PolGeom& pg = g.pol[p];
+    const double w = g.dx;
+    yr->assign((size_t)G * m, 0.0);
+    yi->assign((size_t)G * m, 0.0);
+    xr->assign((size_t)G * m, 0.0);
+    xi->assign((size_t)G * m, 0.0);
+    std::vector<double> cxr(m), cxi(m), cyr(m), cyi(m);
+    for (int i = 0; i < m; ++i) {
+        corr_fp64(s, g, pg, pg.ax[0], i, &cxr[i], &cxi[i]);
+        corr_fp64(s, g, pg, pg.ax[1], i, &cyr[i], &cyi[i]);
+    }
+    std::vector<double> ar(m), ai(m), wr(m), wi(m);
+    for (int e = 0; e < m; ++e) {
+        wr[e] = std::cos(2.0 * kPi * e / m);
+        wi[e] = std::sin(2.0 * kPi * e / m);
+    }
+    for (int n = 0; n < G; ++n) {
+        for (int j = 0; j < m; ++j) {
+            const double uc = u[(size_t)n * m + j] * w;
+            ar[j] = uc * cyr[j];
+            ai[j] = uc * cyi[j];
+            (*xr)[(size_t)n * m + j] = uc * cxr[j];
+            (*xi)[(size_t)n * m + j] = uc * cxi[j];
+        }
+        dft_plus(ar.data(), ai.data(), 1, m, wr.data(), wi.data(), m, &(*yr)[(size_t)n * m], &(*yi)[(size_t)n * m]);
+    }
+}
+
+// Tables of the coefficient-only tensor-core contraction.  With g[q][i] the x-inverse-transformed window
+// rows, the y inverse transform, the y correction and the y overlap weights form one complex map Y_n[q], so
+// that c_mn = sum_i X_m[i] sum_q Y_n[q] g[q][i] (the same sums as transform-then-overlap, regrouped; FP64 here).
+void build_coef_tc(const Settings& s, const Geometry& g, int p, const std::vector<double>& u, PolTables* ptp) {
+    PolTables& pt = *ptp;
+    pt.coef_tc.clear();
+    pt.coef_np = 0;
+    if (!tc_table_fits(g.m, g.groups)) return;
+    std::vector<double> yr, yi, xr, xi;
+    coef_maps(s, g, p, u, &yr, &yi, &xr, &xi);
+    const int np = (2 * g.groups + 15) / 16 * 16;
+    pack_tc_table(g.m, g.groups, np, yr, yi, xr, xi, &pt.coef_tc);
+    pt.coef_np = np;
+}
+
+// Tables of the scoring contraction, which reads the raw box bins B[q][p] (before the mask's zeros, the beam-centre
+// phases and the x inverse transform).  With g[q][i] = sum_p B[q][p] phx[p] phy[q] exp(+2 pi i p i / M) over the
+// kept bins,
+//     c_mn = sum_p Xh_m[p] sum_q Yh_n[q] B[q][p],   Yh_n[q] = phy[q] Y_n[q],
+//     Xh_m[p] = phx[p] sum_i X_m[i] exp(+2 pi i p i / M),
+// the same sums once more regrouped: the x inverse transform moves into the x weights (FP64 here).
+void build_score_tc(const Settings& s, const Geometry& g, int p, const std::vector<double>& u, PolTables* ptp) {
+    PolTables& pt = *ptp;
+    pt.score_tc.clear();
+    const int m = g.m, G = g.groups;
+    if (!tc_table_fits(m, G)) return;
+    std::vector<double> yr, yi, xr, xi;
+    coef_maps(s, g, p, u, &yr, &yi, &xr, &xi);
+    const PolGeom& pg = g.pol[p];
+    std::vector<double> pxr(m), pxi(m), pyr(m), pyi(m);
+    for (int q = 0; q < m; ++q) {
+        phase_fp64(s, pg.ax[0], g.n, q, &pxr[q], &pxi[q]);
+        phase_fp64(s, pg.ax[1], g.n, q, &pyr[q], &pyi[q]);
+    }
+    std::vector<double> wr(m), wi(m), hr(m), hi(m);
+    for (int e = 0; e < m; ++e) {
+        wr[e] = std::cos(2.0 * kPi * e / m);
+        wi[e] = std::sin(2.0 * kPi * e / m);
+    }
+    for (int n = 0; n < G; ++n) {
+        double* ry = &yr[(size_t)n * m];
+        double* iy = &yi[(size_t)n * m];
+        for (int q = 0; q < m; ++q) {
+            const double a = ry[q], b = iy[q];
+            ry[q] = a * pyr[q] - b * pyi[q];
+            iy[q] = a * pyi[q] + b * pyr[q];
+        }
+        dft_plus(&xr[(size_t)n * m], &xi[(size_t)n * m], 1, m, wr.data(), wi.data(), m, hr.data(), hi.data());
+        for (int q = 0; q < m; ++q) {
+            xr[(size_t)n * m + q] = hr[q] * pxr[q] - hi[q] * pxi[q];
+            xi[(size_t)n * m + q] = hr[q] * pxi[q] + hi[q] * pxr[q];
+        }
+    }
+    pack_tc_table(m, G, (2 * G + 15) / 16 * 16, yr, yi, xr, xi, &pt.score_tc);
 }
 
 // Table block of the column-pruned fused kernel (layout in fused_pr.hpp), or empty when the geometry is not

@@ -74,6 +74,16 @@ struct PolTables {
     std::vector<float> cal;
     // table block of the column-pruned fused kernel (fused_pr.hpp); empty when the geometry is not one it serves
     std::vector<unsigned char> pr;
+    // coefficient-only tensor-core contraction (k_coef_tc.cu), empty when G = 0 or beyond its limits:
+    // bf16 hi then lo planes of B = the y map [coef_np][2M] (rows n < G: real part of Y_n, G + n: imaginary
+    // part; K = the window rows q of the real, then of the imaginary part of g), canonical K-major layout;
+    // then float2 X[G][M] = u_m(x'_i) dx' corr_x[i]
+    std::vector<unsigned char> coef_tc;
+    int coef_np = 0;
+    // scoring contraction (k_coef_tc.cu, box source), the same layout with B = the y map times the y phase over
+    // the raw box rows q, and C = Xh[G][M], the x weights carried back through the x inverse transform and the x
+    // phase to the box columns p; built for alignment candidates only, empty otherwise or beyond the limits
+    std::vector<unsigned char> score_tc;
 };
 
 // Rows of the tensor-core B operand (the group count rounded up to 16).
@@ -103,8 +113,16 @@ std::vector<int> radix_plan(int len);
 int build_geometry(const Settings& s, Geometry* g, std::string* why);
 // Geometry for one alignment candidate (tilt, defocus, waist replaced).
 int build_geometry_candidate(const Settings& s, const dh_setting& c, Geometry* g, std::string* why);
-// Fill the host tables of a geometry.
-void build_tables(const Settings& s, const Geometry& g, Tables* t);
+// Fill the host tables of a geometry (score: also the scoring contraction's tables, PolTables::score_tc).
+void build_tables(const Settings& s, const Geometry& g, Tables* t, bool score = false);
+// build_tables of every geometry, the geometries taken in turn by up to `threads` host threads (0: the
+// hardware's count, at most 16); tables do not depend on one another, so the result equals the serial loop's.
+void build_tables_many(const Settings& s, const std::vector<Geometry>& g, std::vector<Tables>* t, bool score = false,
+                       int threads = 0);
+// Fill PolTables::coef_tc of polarisation p (u: the FP64 HG functions u_n at the field grid, [G][M]).
+void build_coef_tc(const Settings& s, const Geometry& g, int p, const std::vector<double>& u, PolTables* pt);
+// Fill PolTables::score_tc of polarisation p (same u).
+void build_score_tc(const Settings& s, const Geometry& g, int p, const std::vector<double>& u, PolTables* pt);
 // Fill PolTables::pr of polarisation p from its other tables (after they are built).
 void build_pr_block(const Geometry& g, int p, PolTables* pt);
 // HG -> LG coefficient matrix (FP64, complex interleaved [modes][modes], LG rows by group then l ascending,

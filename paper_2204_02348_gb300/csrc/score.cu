@@ -202,8 +202,8 @@ extern "C" int dh_score_settings(dh_handle h, const void* d_frames, int dtype, i
         std::string why;
         rc = build_geometry_candidate(H->s, settings[s], &geos[s], &why);
         if (rc) return fail(rc, "candidate " + std::to_string(s) + ": " + why);
-        build_tables(H->s, geos[s], &tabs[s]);
     }
+    build_tables_many(H->s, geos, &tabs, H->s.precision == DH_PRECISION_SPLIT_BF16);
     rc = upload_plans(H, geos, tabs, &plans);
     if (rc) return rc;
     const dhk::Plan& P0 = H->plan;
@@ -313,27 +313,34 @@ extern "C" int dh_score_settings(dh_handle h, const void* d_frames, int dtype, i
                 qo[p] = Pc.pol[p].kly - kly_min[p];
                 po[p] = Pc.pol[p].klx - S.klx[p];
             }
-            dim3 gi((M + R - 1) / R, pols, zf);
-            if (tm) tm->start(st);
-            // the large configuration's field size (176 = 16 11) runs with its inverse plan fixed at compile time
-            if (M == 176 && R == 16 && Pc.nrad_m == 2 && Pc.rad_m[0] == 16 && Pc.rad_m[1] == 11)
-                dhk::k_xinv_sel<16, 11, 1><<<gi, dhk::kSThreads, ((size_t)M * (R + 1) + M + 2 * R) * sizeof(float2), st>>>(Pc, S, xs, gbuf, n, qo[0], qo[1],
-                                                                                              po[0], po[1], logr);
-            else
-                dhk::k_xinv_sel<0, 0, 0><<<gi, dhk::kSThreads, ((size_t)M * (R + 1) + M + 2 * R) * sizeof(float2), st>>>(Pc, S, xs, gbuf, n, qo[0], qo[1],
-                                                                                              po[0], po[1], logr);
-            if (tm) tm->stop(st, "k_xinv_sel");
-            e = cudaGetLastError();
-            if (e == cudaSuccess) {
-                dhk::Batch Bc{};
-                Bc.src = d_frames;
-                Bc.dtype = dtype;
-                Bc.frame0 = f0;
-                Bc.count = n;
-                Bc.g = gbuf;
-                // the last kernel writes frame f at (f * pols + pol) * modes: shift so frame f0 lands at slot 0
-                Bc.coefs = coefs + (size_t)s * chunk * per_frame - (size_t)f0 * per_frame;
-                e = dhk::launch_last(Pc, Bc, st, tm);
+            dhk::Batch Bc{};
+            Bc.src = d_frames;
+            Bc.dtype = dtype;
+            Bc.frame0 = f0;
+            Bc.count = n;
+            Bc.g = gbuf;
+            // the last kernel writes frame f at (f * pols + pol) * modes: shift so frame f0 lands at slot 0
+            Bc.coefs = coefs + (size_t)s * chunk * per_frame - (size_t)f0 * per_frame;
+            cudaError_t e = cudaSuccess;
+            if (dhk::score_tc_supported(Pc, Bc)) {
+                // split-BF16: one contraction straight from the candidate's box in the superset spectra
+                const dhk::BoxSrc box{xs, ms, msx, {qo[0], qo[1]}, {po[0], po[1]}};
+                if (tm) tm->start(st);
+                e = dhk::launch_score_tc(Pc, Bc, box, st);
+                if (tm) tm->stop(st, "k_score_tc");
+            } else {
+                dim3 gi((M + R - 1) / R, pols, zf);
+                if (tm) tm->start(st);
+                // the large configuration's field size (176 = 16 11) runs with its inverse plan fixed at compile time
+                if (M == 176 && R == 16 && Pc.nrad_m == 2 && Pc.rad_m[0] == 16 && Pc.rad_m[1] == 11)
+                    dhk::k_xinv_sel<16, 11, 1><<<gi, dhk::kSThreads, ((size_t)M * (R + 1) + M + 2 * R) * sizeof(float2), st>>>(
+                        Pc, S, xs, gbuf, n, qo[0], qo[1], po[0], po[1], logr);
+                else
+                    dhk::k_xinv_sel<0, 0, 0><<<gi, dhk::kSThreads, ((size_t)M * (R + 1) + M + 2 * R) * sizeof(float2), st>>>(
+                        Pc, S, xs, gbuf, n, qo[0], qo[1], po[0], po[1], logr);
+                if (tm) tm->stop(st, "k_xinv_sel");
+                e = cudaGetLastError();
+                if (e == cudaSuccess) e = dhk::launch_last(Pc, Bc, st, tm);
             }
             if (e != cudaSuccess) {
                 rc = cuda_fail(e, "candidate");
