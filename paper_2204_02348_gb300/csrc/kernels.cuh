@@ -30,8 +30,9 @@ struct PolDev {
     const uint16_t* hgy_tc;  // [2][NP][M] bf16 hi / lo of hg_y, tensor-core core-matrix layout
     const float* cal;        // nullable [N][N] reference-calibration factor over the window
     const unsigned char* pr; // nullable table block of the column-pruned fused kernel (fused_pr.hpp)
-    const unsigned char* coef_tc;   // nullable coefficient-only tensor-core tables: bf16 hi / lo planes of the
-                                    // y map [coef_np][2M] (canonical K-major), then float2 X[G][M]
+    const unsigned char* coef_tc;   // nullable coefficient-only tensor-core tables: the y map as bf16 hi / lo
+                                    // chunks of 16 window rows ([hi][lo] x [coef_np][32], canonical K-major),
+                                    // then float2 X[G][M]
     const unsigned char* score_tc;  // nullable scoring tables, the same layout: phased y map over the raw box
                                     // rows, then float2 Xh[G][M] over the raw box columns
 };

@@ -402,19 +402,22 @@ static void dft_plus(const double* re, const double* im, int stride, int n, cons
     }
 }
 
-// Bytes of one tensor-core contraction table: the B operand [np][2M] as bfloat16 hi, then lo, in the canonical
-// K-major layout, built from the complex K-side map A_n[k] (rows n < G: [Re A_n | -Im A_n], rows G + n:
-// [Im A_n | Re A_n], rows past 2G zero), then float2 C[G][M], the second contraction's weights.  A and C are
-// FP64 [G][M] (real and imaginary parts apart).
+// Bytes of one tensor-core contraction table: the B operand [np][2M] as bfloat16 hi and lo, built from the
+// complex K-side map A_n[k] (rows n < G: [Re A_n | -Im A_n], rows G + n: [Im A_n | Re A_n], rows past 2G zero),
+// then float2 C[G][M], the second contraction's weights.  A and C are FP64 [G][M] (real and imaginary parts
+// apart).  B is stored chunk by chunk, as the kernel streams it: chunk c (K rows 16 c .. 16 c + 15) holds
+// [hi plane][lo plane], each [np][32] in the canonical K-major layout with K = 32 (the 16 rows' real-part
+// columns, then their imaginary-part columns), so one chunk is 128 np contiguous bytes.
 static void pack_tc_table(int m, int G, int np, const std::vector<double>& ar, const std::vector<double>& ai,
                           const std::vector<double>& cr, const std::vector<double>& ci, std::vector<unsigned char>* out) {
-    const int K = 2 * m;
-    std::vector<uint16_t> hi((size_t)np * K, 0), lo((size_t)np * K, 0);
+    const size_t plane_el = (size_t)np * 32;            // one plane of one chunk, in bf16 elements
+    std::vector<uint16_t> b((size_t)(m / 16) * 2 * plane_el, 0);
     auto put = [&](int row, int k, double v) {
+        const int kr = k % m, c = kr / 16, kk = (k >= m ? 16 : 0) + kr % 16;
         const uint16_t h = bf16_bits((float)v);
-        const size_t off = (size_t)umma_offset(row, k, K);
-        hi[off] = h;
-        lo[off] = bf16_bits((float)(v - (double)bf16_value(h)));
+        const size_t off = (size_t)c * 2 * plane_el + (size_t)umma_offset(row, kk, 32);
+        b[off] = h;
+        b[off + plane_el] = bf16_bits((float)(v - (double)bf16_value(h)));
     };
     for (int n = 0; n < G; ++n)
         for (int q = 0; q < m; ++q) {
@@ -424,11 +427,10 @@ static void pack_tc_table(int m, int G, int np, const std::vector<double>& ar, c
             put(G + n, q, im);
             put(G + n, m + q, re);
         }
-    const size_t plane = (size_t)np * K * 2;
-    out->resize(2 * plane + (size_t)G * m * 8);
-    std::memcpy(out->data(), hi.data(), plane);
-    std::memcpy(out->data() + plane, lo.data(), plane);
-    float* x = reinterpret_cast<float*>(out->data() + 2 * plane);
+    const size_t bbytes = b.size() * 2;
+    out->resize(bbytes + (size_t)G * m * 8);
+    std::memcpy(out->data(), b.data(), bbytes);
+    float* x = reinterpret_cast<float*>(out->data() + bbytes);
     for (size_t k = 0; k < (size_t)G * m; ++k) {
         x[2 * k] = (float)cr[k];
         x[2 * k + 1] = (float)ci[k];

@@ -75,9 +75,9 @@ struct PolTables {
     // table block of the column-pruned fused kernel (fused_pr.hpp); empty when the geometry is not one it serves
     std::vector<unsigned char> pr;
     // coefficient-only tensor-core contraction (k_coef_tc.cu), empty when G = 0 or beyond its limits:
-    // bf16 hi then lo planes of B = the y map [coef_np][2M] (rows n < G: real part of Y_n, G + n: imaginary
-    // part; K = the window rows q of the real, then of the imaginary part of g), canonical K-major layout;
-    // then float2 X[G][M] = u_m(x'_i) dx' corr_x[i]
+    // B = the y map [coef_np][2M] as bf16 hi and lo (rows n < G: real part of Y_n, G + n: imaginary part;
+    // K = the window rows q of the real, then of the imaginary part of g), stored per chunk of 16 rows q as
+    // [hi][lo] planes [coef_np][32] in the canonical K-major layout; then float2 X[G][M] = u_m(x'_i) dx' corr_x[i]
     std::vector<unsigned char> coef_tc;
     int coef_np = 0;
     // scoring contraction (k_coef_tc.cu, box source), the same layout with B = the y map times the y phase over
