@@ -791,7 +791,8 @@ def run_workload(args, ws, rank, local):
                     "hbm_frac": {k: v["hbm_frac"] for k, v in res.items()}})
     elif args.workload == "large_batch":
         s = syn.setup_large_batch()
-        B, S = 2000, 64
+        # 2000 frames unless --frames names another count (smaller counts serve profiler captures)
+        B, S = (2000 if args.frames == FRAMES else args.frames), 64
         _, frames = _tiled_frames(s, B, 8, syn.BASE_SEED + 4)
         fr = torch.from_numpy(frames).to(dev)
         cand = syn.candidate_settings(s, S)
@@ -806,7 +807,7 @@ def run_workload(args, ws, rank, local):
         dh.dh_destroy(h)
         out.update({"metric": "frames/s scored under 64 alignment candidates (large case, split-BF16)", "value": B / (ms / 1e3),
                     "unit": "frames/s", "steps": 2, "warmup": 1, "dtype": "f32 FFT, split-bf16 overlap",
-                    "config": {"workload": "large_batch: 2000 frames 1280x1024 u16, 2 windows 512x512, 176x176 fields, 210 "
+                    "config": {"workload": f"large_batch: {B} frames 1280x1024 u16, 2 windows 512x512, 176x176 fields, 210 "
                                            "modes, 64 candidates (tilt +-0.02 deg, defocus U(0,0.05) waves, waist x U(0.9,1.1))",
                                "frame_content": "8 seeded frames tiled"},
                     "ms_per_batch": ms, "candidate_windows_per_s": B * 2 * S / (ms / 1e3),

@@ -118,7 +118,7 @@ struct BoxSrc {
 // The same contraction reading a candidate's box bins straight from the superset spectra, with the candidate's
 // scoring tables (PolDev::score_tc): the x inverse transform is folded into the x weights, so no x-inverse
 // kernel runs.  Coefficients of frame slot b at batch.coefs[(b pols + pol) modes] (batch.frame0 0).
-bool score_tc_supported(const Plan& plan, const Batch& batch);
+bool score_tc_supported(const Plan& plan, const Batch& batch, const BoxSrc& src);
 cudaError_t launch_score_tc(const Plan& plan, const Batch& batch, const BoxSrc& src, cudaStream_t stream);
 
 // Split-BF16 tensor-core variant of the last generic kernel (k_overlap_tc.cu).

@@ -226,6 +226,9 @@ extern "C" int dh_score_settings(dh_handle h, const void* d_frames, int dtype, i
         ms = std::max(ms, M + (yhi - ylo));
         msx = std::max(msx, M + (xhi - xlo));
     }
+    // an even column count: every superset row then starts on the same 16-byte phase, as the scoring
+    // contraction's bulk copies need (the extra column is one more DFT bin, never read)
+    msx += msx & 1;
     S.ms = ms;
     S.msx = msx;
     const bool superset = ms <= N && msx <= N;
@@ -260,7 +263,8 @@ extern "C" int dh_score_settings(dh_handle h, const void* d_frames, int dtype, i
     const int chunk = chunk_frames(per_frame_scratch + per_frame_coefs, pols, batch, H->device);
     // superset rows, superset spectra and candidate x-inverse rows, each region starting on a 256-byte boundary
     const size_t r1s_bytes = ((size_t)chunk * pols * ms * N * sizeof(float2) + 255) & ~(size_t)255;
-    const size_t xs_bytes = ((size_t)chunk * pols * ms * msx * sizeof(float2) + 255) & ~(size_t)255;
+    // 256 bytes of slack: a box row copied with 16 bytes of alignment slack may end 8 bytes past the spectra
+    const size_t xs_bytes = ((size_t)chunk * pols * ms * msx * sizeof(float2) + 256 + 255) & ~(size_t)255;
     const size_t spectra_bytes = (r1s_bytes + xs_bytes + (size_t)chunk * pols * M * M * sizeof(float2) + 255) & ~(size_t)255;
     rc = ensure_scratch(H, spectra_bytes + per_frame_coefs * chunk);
     if (rc) {
@@ -322,9 +326,9 @@ extern "C" int dh_score_settings(dh_handle h, const void* d_frames, int dtype, i
             // the last kernel writes frame f at (f * pols + pol) * modes: shift so frame f0 lands at slot 0
             Bc.coefs = coefs + (size_t)s * chunk * per_frame - (size_t)f0 * per_frame;
             cudaError_t e = cudaSuccess;
-            if (dhk::score_tc_supported(Pc, Bc)) {
+            const dhk::BoxSrc box{xs, ms, msx, {qo[0], qo[1]}, {po[0], po[1]}};
+            if (dhk::score_tc_supported(Pc, Bc, box)) {
                 // split-BF16: one contraction straight from the candidate's box in the superset spectra
-                const dhk::BoxSrc box{xs, ms, msx, {qo[0], qo[1]}, {po[0], po[1]}};
                 if (tm) tm->start(st);
                 e = dhk::launch_score_tc(Pc, Bc, box, st);
                 if (tm) tm->stop(st, "k_score_tc");
