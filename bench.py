@@ -38,7 +38,7 @@ WORKLOAD = "batching: 1000 frames 320x256 u16, 2 pol windows 128x128, 64x64 fiel
 FRAMES = 1000
 ROTATE = 4                      # distinct input batches cycled between steps (4 x 164 MB > 129 MB L2)
 FALLBACK_HBM_GBS = 6800.0
-VARIANTS = {"auto": 0, "fused": 1, "fused_pruned": 2, "generic": 3}
+VARIANTS = {"auto": 0, "fused": 1, "fused_pruned": 2, "generic": 3, "fused_groups": 4}
 
 
 def parse_args():

@@ -69,6 +69,8 @@ extern "C" {
 #define DH_VARIANT_FUSED 1          /* single-kernel path, window stays on chip, every pass over 128 x 128 */
 #define DH_VARIANT_FUSED_PRUNED 2   /* single-kernel path transforming only the columns the window keeps */
 #define DH_VARIANT_GENERIC 3        /* three-kernel path through library scratch (any window size) */
+#define DH_VARIANT_FUSED_GROUPS 4   /* single-kernel path, every 1-D transform inside one 8-thread group, the x
+                                     * transforms only on the box rows the window touches */
 
 /* Coefficient bases (digHoloConfigSetBasisType): the field is always projected onto the HG modes; LG and
  * custom coefficients are a matrix applied to the HG coefficients. */
@@ -197,11 +199,11 @@ int dh_set_precision(dh_handle h, int precision);
 /* Hold the handle to one kernel variant (DH_VARIANT_*), as the guide's FFTW planning mode
  * (digHoloConfigSetFFTWPlanMode) selects how transforms are computed; every variant computes the same
  * reconstruction to rounding.  A variant that does not apply to the current settings (a fused variant for a
- * window other than 128 x 128, the pruned one outside 64 x 64 fields with the FP32 overlap and at most 48
- * kept columns, or frames whose base or row pitch is not 16-byte aligned) falls back to the next one that
- * does (pruned -> fused -> generic).  DH_VARIANT_AUTO (the default) takes the tuner's choice when one exists
- * for these settings, else the fused variant where it applies and the generic one elsewhere.  Unknown values
- * give DH_ERROR_INVALIDARGUMENT. */
+ * window other than 128 x 128, the pruned and the group variants outside 64 x 64 fields with the FP32 overlap
+ * (the pruned one also needs at most 48 kept columns), or frames whose base or row pitch is not 16-byte
+ * aligned) falls back to the next one that does (pruned or groups -> fused -> generic).  DH_VARIANT_AUTO (the
+ * default) takes the tuner's choice when one exists for these settings, else the fused variant where it
+ * applies and the generic one elsewhere.  Unknown values give DH_ERROR_INVALIDARGUMENT. */
 int dh_set_variant(dh_handle h, int variant);
 
 /* The variant that dh_process_batch runs for the current settings and aligned frames (the fallbacks and the
@@ -230,8 +232,8 @@ typedef struct dh_tuning {
 int dh_tuning_key(dh_handle h, char* buf, int len);
 
 /* The candidates dh_autotune times for the current settings, in its order (host only): at most max entries
- * written to out, their number to *count (may exceed max).  For 128 x 128 windows: the fused variant, the
- * pruned one where it applies, and the generic path; otherwise the generic path at chunk targets 24, 48 and
+ * written to out, their number to *count (may exceed max).  For 128 x 128 windows: the group variant where it
+ * applies, the fused variant, the pruned one where it applies, and the generic path; otherwise the generic path at chunk targets 24, 48 and
  * 96 MiB with the default radix plan of M and up to three alternatives (the reversed plan, other power-of-two
  * factorisations). */
 int dh_tuning_candidates(dh_handle h, dh_tuning* out, int max, int* count);

@@ -39,6 +39,7 @@ DH_VARIANT_AUTO = 0
 DH_VARIANT_FUSED = 1
 DH_VARIANT_FUSED_PRUNED = 2
 DH_VARIANT_GENERIC = 3
+DH_VARIANT_FUSED_GROUPS = 4
 DH_BASIS_HG = 0
 DH_BASIS_LG = 1
 DH_BASIS_CUSTOM = 2

@@ -247,6 +247,8 @@ int init_device_once(int dev) {
     if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
     e = fused_pr_init();
     if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
+    e = fused_g_init();
+    if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
     e = dhk::basis_init();
     if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
     if (dev >= 0 && dev < 64) inited[dev] = true;
@@ -798,8 +800,9 @@ int dh_set_basis_transform(dh_handle h, int modes_in, int modes_out, const void*
 
 int dh_set_variant(dh_handle h, int variant) {
     GET_HANDLE(h);
-    if (variant < DH_VARIANT_AUTO || variant > DH_VARIANT_GENERIC)
-        return fail(DH_ERROR_INVALIDARGUMENT, "variant must be one of DH_VARIANT_AUTO, _FUSED, _FUSED_PRUNED, _GENERIC");
+    if (variant < DH_VARIANT_AUTO || variant > DH_VARIANT_FUSED_GROUPS)
+        return fail(DH_ERROR_INVALIDARGUMENT,
+                    "variant must be one of DH_VARIANT_AUTO, _FUSED, _FUSED_PRUNED, _GENERIC, _FUSED_GROUPS");
     H->variant = variant;
     return DH_SUCCESS;
 }

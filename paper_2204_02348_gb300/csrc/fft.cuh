@@ -93,7 +93,8 @@ __device__ __forceinline__ void dft16(float2* a) {
     const float sg = INV ? 1.0f : -1.0f;
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        const float2 t = (k == 0) ? o[k] : cmul(o[k], make_float2(c[k], sg * s[k]));
+        // k = 4 is a quarter turn: an exact swap and negation, no multiplication
+        const float2 t = (k == 0) ? o[k] : (k == 4) ? mul_mi<INV>(o[k]) : cmul(o[k], make_float2(c[k], sg * s[k]));
         a[k] = cadd(e[k], t);
         a[k + 8] = csub(e[k], t);
     }

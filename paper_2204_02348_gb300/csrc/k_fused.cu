@@ -727,10 +727,13 @@ bool use_fused(const dhk::Plan& P) {
 int resolve_variant(const Handle* H, const dhk::Plan& P, bool aligned) {
     const bool fused = aligned && use_fused(P);
     const bool pruned = fused && use_fused_pr(P);
-    // without a tuner's choice, the fused kernel that transforms every column is the measured faster default
+    const bool groups = fused && use_fused_g(P);
+    // without a tuner's choice, the fused kernel that transforms every column (measured fastest on the batching
+    // workload; the pruned and group-transform kernels are tuner candidates)
     const int v = H->variant != kVariantAuto ? H->variant : (H->tuned ? H->tuned : kVariantFusedLegacy);
     if (v == kVariantGeneric) return kVariantGeneric;
     if (v == kVariantFusedLegacy) return fused ? kVariantFusedLegacy : kVariantGeneric;
+    if (v == kVariantFusedGroups) return groups ? kVariantFusedGroups : fused ? kVariantFusedLegacy : kVariantGeneric;
     return pruned ? kVariantFusedPruned : fused ? kVariantFusedLegacy : kVariantGeneric;
 }
 
@@ -832,7 +835,9 @@ int launch_fused(Handle* H, const dhk::Plan& P, const void* frames, int dtype, i
 
 int launch_fused_path(Handle* H, const dhk::Plan& P, const void* frames, int dtype, int batch, void* fields,
                       void* coefs, cudaStream_t st, dhk::StageTimer* tm) {
-    if (resolve_variant(H, P, true) == kVariantFusedPruned) return launch_fused_pr(H, P, frames, dtype, batch, fields, coefs, st, tm);
+    const int v = resolve_variant(H, P, true);
+    if (v == kVariantFusedPruned) return launch_fused_pr(H, P, frames, dtype, batch, fields, coefs, st, tm);
+    if (v == kVariantFusedGroups) return launch_fused_g(H, P, frames, dtype, batch, fields, coefs, st, tm);
     return launch_fused(H, P, frames, dtype, batch, 0, batch, dhk::kModeFull, nullptr, nullptr, fields, coefs, st, tm);
 }
 

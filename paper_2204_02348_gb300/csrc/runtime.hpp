@@ -43,7 +43,8 @@ struct Profiler : dhk::StageTimer {
 };
 
 // Kernel variants a handle can be held to (the values of DH_VARIANT_* in digholo.h).
-constexpr int kVariantAuto = 0, kVariantFusedLegacy = 1, kVariantFusedPruned = 2, kVariantGeneric = 3;
+constexpr int kVariantAuto = 0, kVariantFusedLegacy = 1, kVariantFusedPruned = 2, kVariantGeneric = 3,
+              kVariantFusedGroups = 4;
 
 struct HostPipe;   // streams and staging buffers of dh_process_batch_host (host.cu)
 
@@ -123,6 +124,12 @@ bool use_fused_pr(const dhk::Plan& P);
 cudaError_t fused_pr_init();
 int launch_fused_pr(Handle* H, const dhk::Plan& P, const void* frames, int dtype, int batch, void* fields, void* coefs,
                     cudaStream_t st, dhk::StageTimer* timer);
+
+// Group-transform fused path (k_fused_g.cu): 128 x 128 windows, 64 x 64 fields, FP32 overlap, whole path only.
+bool use_fused_g(const dhk::Plan& P);
+cudaError_t fused_g_init();
+int launch_fused_g(Handle* H, const dhk::Plan& P, const void* frames, int dtype, int batch, void* fields, void* coefs,
+                   cudaStream_t st, dhk::StageTimer* timer);
 
 // HG coefficient bytes per frame that an output-basis transform needs as scratch (0 for the HG basis).
 size_t basis_scratch_bytes(const dhk::Plan& P);

@@ -226,7 +226,7 @@ bool parse_cache(const std::string& text, std::map<std::string, dh_tuning>* out,
             *why = "tuning cache entry needs \"key\", \"variant\" and \"chunk_mb\"";
             return false;
         }
-        if (variant < DH_VARIANT_AUTO || variant > DH_VARIANT_GENERIC || chunk < 0 || chunk > 4096) {
+        if (variant < DH_VARIANT_AUTO || variant > DH_VARIANT_FUSED_GROUPS || chunk < 0 || chunk > 4096) {
             *why = "tuning cache entry out of range";
             return false;
         }
@@ -330,6 +330,7 @@ std::vector<dh_tuning> candidates(const Settings& s, const Geometry& g) {
     const bool fused = g.n == 128 && g.groups <= 16 &&
                        (s.precision == DH_PRECISION_FP32 ? (g.m == 32 || g.m == 48 || g.m == 64) : g.m == 64);
     if (fused) {
+        if (g.m == 64 && s.precision == DH_PRECISION_FP32) out.push_back(make_tuning(DH_VARIANT_FUSED_GROUPS, 0, {}));
         out.push_back(make_tuning(DH_VARIANT_FUSED, 0, {}));
         if (pruned_applies(s, g)) out.push_back(make_tuning(DH_VARIANT_FUSED_PRUNED, 0, {}));
         out.push_back(make_tuning(DH_VARIANT_GENERIC, 0, {}));
@@ -348,7 +349,7 @@ int set_tuning(Handle* H, const dh_tuning* t, const Geometry& g, const std::stri
         H->tune_key = key;
         return DH_SUCCESS;
     }
-    if (t->variant < DH_VARIANT_AUTO || t->variant > DH_VARIANT_GENERIC)
+    if (t->variant < DH_VARIANT_AUTO || t->variant > DH_VARIANT_FUSED_GROUPS)
         return fail(DH_ERROR_INVALIDARGUMENT, "tuning variant must be one of DH_VARIANT_*");
     if (t->chunk_mb < 0 || t->chunk_mb > 4096) return fail(DH_ERROR_INVALIDARGUMENT, "tuning chunk_mb must be in [0, 4096]");
     if (t->nradix < 0 || t->nradix > DH_MAX_RADICES)

@@ -7,7 +7,8 @@ import pytest
 import paper_2204_02348_gb300 as dh
 from synth import holograms as syn
 
-FUSED, PRUNED, GENERIC = dh.DH_VARIANT_FUSED, dh.DH_VARIANT_FUSED_PRUNED, dh.DH_VARIANT_GENERIC
+FUSED, PRUNED, GENERIC, GROUPS = (dh.DH_VARIANT_FUSED, dh.DH_VARIANT_FUSED_PRUNED, dh.DH_VARIANT_GENERIC,
+                                  dh.DH_VARIANT_FUSED_GROUPS)
 
 
 @pytest.fixture()
@@ -20,9 +21,9 @@ def handle():
 def test_candidates_for_the_batching_geometry(handle):
     dh.configure(handle, syn.setup_batching())
     c = dh.dh_tuning_candidates(handle)
-    assert [x["variant"] for x in c] == [FUSED, PRUNED, GENERIC]
+    assert [x["variant"] for x in c] == [GROUPS, FUSED, PRUNED, GENERIC]
     assert all(x["chunk_mb"] == 0 and x["radix"] == [] for x in c)
-    # the split-BF16 overlap has no pruned variant
+    # the split-BF16 overlap has neither the pruned nor the group variant
     dh.dh_set_precision(handle, dh.DH_PRECISION_SPLIT_BF16)
     assert [x["variant"] for x in dh.dh_tuning_candidates(handle)] == [FUSED, GENERIC]
 
