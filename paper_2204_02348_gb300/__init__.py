@@ -168,6 +168,17 @@ def _check(rc: int) -> None:
         raise DigHoloError(rc, dh_last_error())
 
 
+def _frames_ptr(frames, dtype: int) -> int:
+    """Address of a frame buffer, after checking that its elements are as wide as dtype says (2 bytes for
+    DH_DTYPE_U16, 4 for DH_DTYPE_F32): a mismatch would make the kernels read twice (or half) the buffer."""
+    if frames is not None and not isinstance(frames, int):
+        width = frames.element_size() if hasattr(frames, "element_size") else getattr(frames, "itemsize", None)
+        want = {DH_DTYPE_U16: 2, DH_DTYPE_F32: 4}.get(dtype)
+        if width is not None and want is not None and width != want:
+            raise ValueError(f"frames have {width}-byte elements but dtype {dtype} needs {want}-byte elements")
+    return _ptr(frames)
+
+
 def _ptr(t) -> int:
     """Device (or host) address of a tensor / integer / None."""
     if t is None:
@@ -320,7 +331,7 @@ def dh_set_tuning_cache(h: int, path) -> None:
 
 def dh_autotune(h: int, frames, dtype: int, batch: int, fields=None, coefs=None, stream=None, reps: int = 3) -> None:
     """Time every tuning candidate on these device frames, keep the fastest; fields / coefs receive its results."""
-    _check(_lib.dh_autotune(h, _ptr(frames), dtype, batch, _ptr(fields), _ptr(coefs), _stream(stream), reps))
+    _check(_lib.dh_autotune(h, _frames_ptr(frames, dtype), dtype, batch, _ptr(fields), _ptr(coefs), _stream(stream), reps))
 
 
 def dh_get_output_dims(h: int):
@@ -337,23 +348,23 @@ def dh_get_axes(h: int, pol: int):
 
 
 def dh_process_batch(h: int, frames, dtype: int, batch: int, fields=None, coefs=None, stream=None) -> None:
-    _check(_lib.dh_process_batch(h, _ptr(frames), dtype, batch, _ptr(fields), _ptr(coefs), _stream(stream)))
+    _check(_lib.dh_process_batch(h, _frames_ptr(frames, dtype), dtype, batch, _ptr(fields), _ptr(coefs), _stream(stream)))
 
 
 def dh_process_batch_window(h: int, frames, dtype: int, batch: int, window, fields=None, coefs=None,
                             stream=None) -> None:
-    _check(_lib.dh_process_batch_window(h, _ptr(frames), dtype, batch, _ptr(window), _ptr(fields), _ptr(coefs),
+    _check(_lib.dh_process_batch_window(h, _frames_ptr(frames, dtype), dtype, batch, _ptr(window), _ptr(fields), _ptr(coefs),
                                         _stream(stream)))
 
 
 def dh_process_batch_host(h: int, frames, dtype: int, batch: int, fields=None, coefs=None, stream=None) -> None:
     """frames, fields, coefs: host tensors or numpy arrays (page-locked for overlapped copies)."""
-    _check(_lib.dh_process_batch_host(h, _ptr(frames), dtype, batch, _ptr(fields), _ptr(coefs), _stream(stream)))
+    _check(_lib.dh_process_batch_host(h, _frames_ptr(frames, dtype), dtype, batch, _ptr(fields), _ptr(coefs), _stream(stream)))
 
 
 def dh_process_batch_avg(h: int, frames, dtype: int, batch: int, avg_count: int, avg_mode: int, fields=None,
                          coefs=None, stream=None) -> None:
-    _check(_lib.dh_process_batch_avg(h, _ptr(frames), dtype, batch, avg_count, avg_mode, _ptr(fields), _ptr(coefs),
+    _check(_lib.dh_process_batch_avg(h, _frames_ptr(frames, dtype), dtype, batch, avg_count, avg_mode, _ptr(fields), _ptr(coefs),
                                      _stream(stream)))
 
 
@@ -386,7 +397,7 @@ def dh_auto_align(h: int, frames, dtype: int, batch: int, steps=None, min_steps=
     st = None if steps is None else (ctypes.c_double * 3)(*steps)
     lo = None if min_steps is None else (ctypes.c_double * 3)(*min_steps)
     power, its = _d(), _i()
-    _check(_lib.dh_auto_align(h, _ptr(frames), dtype, batch, st, lo, max_iter, ctypes.byref(power), ctypes.byref(its),
+    _check(_lib.dh_auto_align(h, _frames_ptr(frames, dtype), dtype, batch, st, lo, max_iter, ctypes.byref(power), ctypes.byref(its),
                               _stream(stream)))
     return power.value, its.value
 
@@ -394,12 +405,12 @@ def dh_auto_align(h: int, frames, dtype: int, batch: int, steps=None, min_steps=
 def dh_process_batch_noalloc(h: int, frames, dtype: int, batch: int, fields=None, coefs=None, stream=None) -> None:
     """dh_process_batch without device allocation: tables and scratch come from the library's static
     16 MiB device array (see include/digholo.h for the limits and the sharing rules)."""
-    _check(_lib.dh_process_batch_noalloc(h, _ptr(frames), dtype, batch, _ptr(fields), _ptr(coefs), _stream(stream)))
+    _check(_lib.dh_process_batch_noalloc(h, _frames_ptr(frames, dtype), dtype, batch, _ptr(fields), _ptr(coefs), _stream(stream)))
 
 
 def dh_score_settings(h: int, frames, dtype: int, batch: int, settings, power, stream=None) -> None:
     arr = (dh_setting * len(settings))(*settings)
-    _check(_lib.dh_score_settings(h, _ptr(frames), dtype, batch, arr, len(settings), _ptr(power), _stream(stream)))
+    _check(_lib.dh_score_settings(h, _frames_ptr(frames, dtype), dtype, batch, arr, len(settings), _ptr(power), _stream(stream)))
 
 
 def dh_get_device_status(h: int) -> int:
@@ -446,7 +457,7 @@ def dh_server_set_admission(server: int, max_bypass: int, max_wait_ms: int) -> N
 
 def dh_server_submit(server: int, geometry: int, frames, dtype: int, batch: int, fields=None, coefs=None) -> int:
     """Queue a request on host buffers (tensors or addresses); returns its ticket."""
-    req = dh_request(geometry, _ptr(frames), dtype, batch, _ptr(fields), _ptr(coefs))
+    req = dh_request(geometry, _frames_ptr(frames, dtype), dtype, batch, _ptr(fields), _ptr(coefs))
     t = ctypes.c_uint64()
     _check(_lib.dh_server_submit(server, ctypes.byref(req), ctypes.byref(t)))
     return t.value

@@ -267,3 +267,21 @@ def test_alignment_getter_and_search_argument_errors():
         assert dh._lib.dh_auto_align(h, 16, 0, 1, None, None, 10, None, None, None) == dh.DH_ERROR_INVALIDARGUMENT
     finally:
         dh.dh_destroy(h)
+
+
+def test_frames_element_width_must_match_dtype():
+    # the binding refuses frames whose element width contradicts dtype before anything reaches the library, so
+    # a uint16 buffer is never read as float32 (twice its bytes)
+    import numpy as np
+    h = dh.dh_create()
+    try:
+        dh.configure(h, syn.setup_batching())
+        u16 = np.zeros((1, 256, 320), np.uint16)
+        f32 = np.zeros((1, 256, 320), np.float32)
+        for fn in (dh.dh_process_batch, dh.dh_process_batch_host, dh.dh_process_batch_noalloc):
+            with pytest.raises(ValueError):
+                fn(h, u16, dh.DH_DTYPE_F32, 1)
+            with pytest.raises(ValueError):
+                fn(h, f32, dh.DH_DTYPE_U16, 1)
+    finally:
+        dh.dh_destroy(h)
