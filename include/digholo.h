@@ -335,8 +335,9 @@ int dh_process_batch_avg(dh_handle h, const void* d_frames, int dtype, int batch
  *   - All calls share the array, which keeps the last call's contents; nothing in it needs to start at zero
  *     (every element is written before it is read within a call).  Calls that overlap on the GPU (different
  *     streams, or threads without ordering) race on the array: serialise them on one stream.
- *   - Its kernels contain no bounded waits, so it never sets the handle's device status word
- *     (dh_get_device_status does not report on it). */
+ *   - Its status block is the first 16 bytes of the array's table area, zeroed by each call's table upload
+ *     (so it reflects the last call); dh_get_device_status and dh_get_check_record fold it into their reports
+ *     on any handle.  Its kernels contain no bounded waits: only the bounds-checked build's guards set it. */
 int dh_process_batch_noalloc(dh_handle h, const void* d_frames, int dtype, int batch, void* d_fields, void* d_coefs,
                              void* stream);
 
@@ -459,6 +460,24 @@ int dh_server_destroy(dh_server s);
  * completes, with `limit` tries, and reports in *expired whether the limit ran out (1) as it must. */
 int dh_get_device_status(dh_handle h, int* status);
 int dh_check_bounded_wait(long long limit, int* expired);
+
+/* Bounds-checked build (the paper has no counterpart; it stands in for a device memory checker).
+ * libdigholo_gb300_checked.so is the same library compiled with DH_CHECKED:
+ * before every guarded global-memory access of the reconstruction kernels (scratch regions against the extent
+ * the host carved for them, outputs against the batch layout, 16-byte vector accesses against their alignment)
+ * it tests the offset, skips the access when the test fails and records the failure instead of touching memory
+ * outside the buffer: bit 2 of the device status word (dh_get_device_status), and the first failing guard site
+ * with its offset and extent (low 32 bits each), which dh_get_check_record returns and clears (site 0: none;
+ * sites are numbered in csrc/check.cuh).  In the normal build the guards compile away and the record stays 0.
+ * dh_checked_build reports which build is loaded (1: checked).  dh_check_bounds_probe runs one guard at an
+ * offset one past its extent, with no memory access behind it in either build: in the checked build it
+ * records site 99 (offset 4, extent 4); in the normal build nothing. */
+#define DH_STATUS_WAIT_COPY 1
+#define DH_STATUS_WAIT_MMA 2
+#define DH_STATUS_BOUNDS 4
+int dh_get_check_record(dh_handle h, int* site, int* offset, int* extent);
+int dh_checked_build(int* checked);
+int dh_check_bounds_probe(dh_handle h);
 
 /* Per-kernel device timing (the analogue of digHoloBenchmark's per-stage rates).  While enabled, every kernel
  * the handle launches is bracketed by a CUDA event pair recorded on the launch stream.  dh_set_profiling

@@ -12,7 +12,9 @@ import ctypes
 import os
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_native", "libdigholo_gb300.so")
+# DH_CHECKED=1 in the environment selects the bounds-checked build of the same library (csrc/check.cuh)
+CHECKED = os.environ.get("DH_CHECKED", "") not in ("", "0")
+LIB_PATH = os.path.join(_HERE, "_native", "libdigholo_gb300_checked.so" if CHECKED else "libdigholo_gb300.so")
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(f"native library missing at {LIB_PATH}; build it with `python paper_2204_02348_gb300/_build.py`")
@@ -139,6 +141,9 @@ _PROTOS = {
     "dh_set_profiling": [_i, _i],
     "dh_get_device_status": [_i, ctypes.POINTER(_i)],
     "dh_check_bounded_wait": [ctypes.c_longlong, ctypes.POINTER(_i)],
+    "dh_get_check_record": [_i, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_i)],
+    "dh_checked_build": [ctypes.POINTER(_i)],
+    "dh_check_bounds_probe": [_i],
     "dh_server_create": [ctypes.c_size_t, _i, ctypes.POINTER(_p)],
     "dh_server_submit": [_p, ctypes.POINTER(dh_request), ctypes.POINTER(ctypes.c_uint64)],
     "dh_server_set_admission": [_p, _i, _i],
@@ -418,6 +423,29 @@ def dh_get_device_status(h: int) -> int:
     st = _i()
     _check(_lib.dh_get_device_status(h, ctypes.byref(st)))
     return st.value
+
+
+DH_STATUS_WAIT_COPY = 1
+DH_STATUS_WAIT_MMA = 2
+DH_STATUS_BOUNDS = 4
+
+
+def dh_get_check_record(h: int):
+    """The first failed bounds guard since the last call, as (site, offset, extent); (0, 0, 0) when none."""
+    a, b, c = _i(), _i(), _i()
+    _check(_lib.dh_get_check_record(h, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return a.value, b.value, c.value
+
+
+def dh_checked_build() -> bool:
+    """Whether the loaded library is the bounds-checked build."""
+    v = _i()
+    _check(_lib.dh_checked_build(ctypes.byref(v)))
+    return bool(v.value)
+
+
+def dh_check_bounds_probe(h: int) -> None:
+    _check(_lib.dh_check_bounds_probe(h))
 
 
 def dh_check_bounded_wait(limit: int) -> bool:

@@ -1,5 +1,7 @@
 """Build the native library in-tree: every ``csrc/*.cu`` with nvcc for sm_103a, ``csrc/*.cpp`` with g++,
-compiled in parallel and linked into ``_native/libdigholo_gb300.so``.
+compiled in parallel and linked into ``_native/libdigholo_gb300.so``; the same CUDA sources compiled again with
+``-DDH_CHECKED`` give the bounds-checked library ``_native/libdigholo_gb300_checked.so`` (loaded by the package
+when the environment sets DH_CHECKED=1).
 
 Run ``python paper_2204_02348_gb300/_build.py`` (or ``__graft_entry__.build()``).  Set DH_PTXAS_VERBOSE=1 to
 print register and shared-memory usage of every kernel.
@@ -18,6 +20,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 OUT = os.path.join(PKG, "_native")
 LIB = os.path.join(OUT, "libdigholo_gb300.so")
+LIB_CHECKED = os.path.join(OUT, "libdigholo_gb300_checked.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -37,10 +40,13 @@ def _sources():
 
 
 def _up_to_date(deps) -> bool:
-    if not os.path.exists(LIB):
-        return False
-    t = os.path.getmtime(LIB)
-    return all(os.path.getmtime(d) <= t for d in deps) and os.path.getmtime(__file__) <= t
+    for lib in (LIB, LIB_CHECKED):
+        if not os.path.exists(lib):
+            return False
+        t = os.path.getmtime(lib)
+        if not (all(os.path.getmtime(d) <= t for d in deps) and os.path.getmtime(__file__) <= t):
+            return False
+    return True
 
 
 def _run(cmd):
@@ -57,15 +63,18 @@ def build(force: bool = False, verbose: bool = False) -> str:
     inc = ["-I", os.path.join(ROOT, "include")]
     ptxas_v = ["-Xptxas", "-v"] if os.environ.get("DH_PTXAS_VERBOSE") else []
     jobs = []
-    objs = []
+    objs, objs_checked = [], []
+    os.makedirs(os.path.join(OUT, "checked"), exist_ok=True)
     for src in cu:
-        obj = os.path.join(OUT, os.path.basename(src) + ".o")
-        objs.append(obj)
-        jobs.append([nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
-                     *ptxas_v, *inc, "-c", src, "-o", obj])
+        for checked in (False, True):
+            obj = os.path.join(OUT, "checked" if checked else "", os.path.basename(src) + ".o")
+            (objs_checked if checked else objs).append(obj)
+            jobs.append([nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
+                         *(["-DDH_CHECKED"] if checked else []), *ptxas_v, *inc, "-c", src, "-o", obj])
     for src in cpp:
         obj = os.path.join(OUT, os.path.basename(src) + ".o")
         objs.append(obj)
+        objs_checked.append(obj)
         jobs.append(["g++", "-O2", "-std=c++17", "-fPIC", "-ffp-contract=off", *inc,
                      "-I", "/usr/local/cuda/include", "-c", src, "-o", obj])
     with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
@@ -76,13 +85,13 @@ def build(force: bool = False, verbose: bool = False) -> str:
             sys.stderr.write(" ".join(c) + "\n" + o)
     if failed:
         raise RuntimeError("native build failed:\n" + "\n".join(o for _, o in failed))
-    tmp = LIB + ".tmp"
-    cmd, rc, o = _run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lpthread"])
-    if rc != 0:
-        raise RuntimeError("link failed:\n" + o)
-    os.replace(tmp, LIB)
+    for lib, o_list in ((LIB, objs), (LIB_CHECKED, objs_checked)):
+        tmp = lib + ".tmp"
+        cmd, rc, o = _run([nvcc, *ARCH, "-shared", "-o", tmp, *o_list, "-lpthread"])
+        if rc != 0:
+            raise RuntimeError("link failed:\n" + o)
+        os.replace(tmp, lib)
     return LIB
-
 
 if __name__ == "__main__":
     print(build(force="--force" in sys.argv, verbose="-v" in sys.argv))

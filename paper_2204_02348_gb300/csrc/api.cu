@@ -227,8 +227,11 @@ int upload_plans(Handle* H, const std::vector<Geometry>& geos, const std::vector
     cudaError_t e = cudaMemcpy(H->d_cand, all.data(), total, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return cuda_fail(e, "candidate plan upload");
     plans->resize(n);
-    for (size_t i = 0; i < n; ++i)
+    for (size_t i = 0; i < n; ++i) {
         plan_from_image(H->s, geos[i], tabs[i], ims[i], (unsigned char*)H->d_cand + at[i], &(*plans)[i]);
+        // candidates report waits and guards through the handle's own status block
+        if (H->plan.status) (*plans)[i].status = H->plan.status;
+    }
     return DH_SUCCESS;
 }
 
@@ -488,6 +491,7 @@ int process_avg(Handle* H, const void* frames, int dtype, int batch, int avg, in
         B.src = frames;
         B.dtype = dtype;
         B.r1 = r1;
+        B.r1_len = fused ? 0 : (long long)chunk * avg * P.pols * P.m * P.n;
         long long mstride, gstride;
         cudaError_t e = cudaSuccess;
         const int total = batch * avg;
@@ -502,6 +506,7 @@ int process_avg(Handle* H, const void* frames, int dtype, int batch, int avg, in
                     B.frame0 = j * batch + g0;
                     B.count = n;
                     B.g = gbuf + (size_t)j * n * elems;
+                    B.g_len = (long long)chunk * avg * elems - (long long)j * n * elems;
                     e = dhk::launch_forward(P, B, st, tm);
                 }
             }
@@ -516,12 +521,15 @@ int process_avg(Handle* H, const void* frames, int dtype, int batch, int avg, in
                 B.frame0 = g0 * avg;
                 B.count = n * avg;
                 B.g = gbuf;
+                B.g_len = (long long)chunk * avg * elems;
                 e = dhk::launch_forward(P, B, st, tm);
             }
             mstride = elems;
             gstride = (long long)avg * elems;
         }
-        if (e == cudaSuccess) e = dhk::launch_avg(gbuf, part, mean, n, avg, elems, mstride, gstride, st, tm);
+        const dhk::AvgExtents X{P.status, (long long)chunk * avg * elems, (long long)chunk * avg * slices,
+                                (long long)chunk * elems};
+        if (e == cudaSuccess) e = dhk::launch_avg(gbuf, part, mean, n, avg, elems, mstride, gstride, X, st, tm);
         if (e == cudaSuccess && fused) {
             rc = launch_fused(H, P, nullptr, dtype, 0, g0, n, dhk::kModeInverse, mean, nullptr, fields, coefs, st, tm);
             if (rc) return rc;
@@ -534,6 +542,7 @@ int process_avg(Handle* H, const void* frames, int dtype, int batch, int avg, in
             L.frame0 = g0;
             L.count = n;
             L.g = mean;
+            L.g_len = (long long)chunk * elems;
             L.fields = (float2*)fields;
             L.coefs = (float2*)coefs;
             e = dhk::launch_last(P, L, st, tm);
@@ -594,6 +603,8 @@ int run_split(const dhk::Plan& P, void* scratch, size_t scratch_bytes, const voi
         B.count = std::min(chunk, batch - f0);
         B.r1 = r1;
         B.g = g;
+        B.r1_len = (long long)chunk * P.pols * P.m * P.n;
+        B.g_len = (long long)chunk * P.pols * P.m * P.m;
         B.window = (float2*)window;
         B.fields = (float2*)fields;
         B.coefs = (float2*)coefs;

@@ -26,7 +26,7 @@ constexpr int kAvgSlice = 8192;   // window elements per k_avg_dot block
 
 __global__ void __launch_bounds__(kAvgThreads) k_avg_dot(const float2* __restrict__ g, float2* __restrict__ part,
                                                          long long elems, int slices, int members,
-                                                         long long mstride, long long gstride) {
+                                                         long long mstride, long long gstride, AvgExtents X) {
     __shared__ float2 red[kAvgThreads / 32];
     const int s = blockIdx.x, j = blockIdx.y + 1, gi = blockIdx.z;
     const float2* w0 = g + (size_t)gi * gstride;
@@ -35,6 +35,8 @@ __global__ void __launch_bounds__(kAvgThreads) k_avg_dot(const float2* __restric
     const long long e1 = e0 + kAvgSlice < elems ? e0 + kAvgSlice : elems;
     float2 acc = make_float2(0.f, 0.f);
     for (long long e = e0 + threadIdx.x; e < e1; e += kAvgThreads) {
+        const long long o0 = (long long)gi * gstride + e, oj = o0 + (long long)j * mstride;
+        if (!(DH_IN(X.status, o0, X.g_len, kSiteAvg) && DH_IN(X.status, oj, X.g_len, kSiteAvg))) continue;
         const float2 a = w0[e], b = wj[e];
         acc.x = fmaf(a.x, b.x, fmaf(a.y, b.y, acc.x));
         acc.y = fmaf(a.x, b.y, fmaf(-a.y, b.x, acc.y));
@@ -52,13 +54,14 @@ __global__ void __launch_bounds__(kAvgThreads) k_avg_dot(const float2* __restric
             t.x += red[w].x;
             t.y += red[w].y;
         }
-        part[((size_t)gi * members + j) * slices + s] = t;
+        if (DH_IN(X.status, ((long long)gi * members + j) * slices + s, X.part_len, kSiteAvg))
+            part[((size_t)gi * members + j) * slices + s] = t;
     }
 }
 
 __global__ void __launch_bounds__(kAvgThreads) k_avg_sum(const float2* __restrict__ g, const float2* __restrict__ part,
                                                          float2* __restrict__ out, long long elems, int slices,
-                                                         int members, long long mstride, long long gstride) {
+                                                         int members, long long mstride, long long gstride, AvgExtents X) {
     extern __shared__ float2 phasor[];   // [members]
     const int gi = blockIdx.y;
     for (int j = threadIdx.x; j < members; j += kAvgThreads) {
@@ -67,6 +70,7 @@ __global__ void __launch_bounds__(kAvgThreads) k_avg_sum(const float2* __restric
             float2 d = make_float2(0.f, 0.f);
             const float2* pj = part + ((size_t)gi * members + j) * slices;
             for (int s = 0; s < slices; ++s) {
+                if (!DH_IN(X.status, ((long long)gi * members + j) * slices + s, X.part_len, kSiteAvg)) continue;
                 d.x += pj[s].x;
                 d.y += pj[s].y;
             }
@@ -86,11 +90,12 @@ __global__ void __launch_bounds__(kAvgThreads) k_avg_sum(const float2* __restric
          e += (long long)gridDim.x * kAvgThreads) {
         float2 acc = make_float2(0.f, 0.f);
         for (int j = 0; j < members; ++j) {
+            if (!DH_IN(X.status, (long long)gi * gstride + (long long)j * mstride + e, X.g_len, kSiteAvg)) continue;
             const float2 a = phasor[j], w = base[(size_t)j * mstride + e];
             acc.x = fmaf(a.x, w.x, fmaf(-a.y, w.y, acc.x));
             acc.y = fmaf(a.x, w.y, fmaf(a.y, w.x, acc.y));
         }
-        o[e] = make_float2(acc.x * scale, acc.y * scale);
+        if (DH_IN(X.status, (long long)gi * elems + e, X.out_len, kSiteAvg)) o[e] = make_float2(acc.x * scale, acc.y * scale);
     }
 }
 
@@ -99,14 +104,14 @@ __global__ void __launch_bounds__(kAvgThreads) k_avg_sum(const float2* __restric
 int avg_slices(long long elems) { return (int)((elems + kAvgSlice - 1) / kAvgSlice); }
 
 cudaError_t launch_avg(const float2* g, float2* part, float2* out, int groups, int members, long long elems,
-                       long long mstride, long long gstride, cudaStream_t st, StageTimer* tm) {
+                       long long mstride, long long gstride, const AvgExtents& X, cudaStream_t st, StageTimer* tm) {
     if (groups < 1 || members < 1 || elems < 1) return cudaSuccess;
     if (groups > 65535 || members > DH_MAX_AVG_COUNT) return cudaErrorInvalidValue;
     const int slices = avg_slices(elems);
     if (members > 1) {
         if (tm) tm->start(st);
         k_avg_dot<<<dim3(slices, members - 1, groups), kAvgThreads, 0, st>>>(g, part, elems, slices, members,
-                                                                             mstride, gstride);
+                                                                             mstride, gstride, X);
         if (tm) tm->stop(st, "k_avg_dot");
         cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return e;
@@ -115,7 +120,7 @@ cudaError_t launch_avg(const float2* g, float2* part, float2* out, int groups, i
     const int gx = (int)std::min<long long>((elems + per_block - 1) / per_block, 65535);
     if (tm) tm->start(st);
     k_avg_sum<<<dim3(gx, groups), kAvgThreads, (size_t)members * sizeof(float2), st>>>(g, part, out, elems, slices,
-                                                                                      members, mstride, gstride);
+                                                                                      members, mstride, gstride, X);
     if (tm) tm->stop(st, "k_avg_sum");
     return cudaGetLastError();
 }

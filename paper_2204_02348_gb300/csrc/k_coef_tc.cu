@@ -235,13 +235,21 @@ __global__ void __launch_bounds__(kCtThreads, 1) k_coef_tc(const __grid_constant
                                        (size_t)(S.qoff[pol] + kCtQ * c) * S.msx + S.poff[pol];
                     const int off = (int)((reinterpret_cast<uintptr_t>(r0) >> 3) & 1);
                     const uint32_t rb = (uint32_t)(M * 8 + 16 * off);
-                    mbar_expect_tx(mb, (uint32_t)kCtQ * rb + (uint32_t)L.slot_b);
-                    for (int r = 0; r < kCtQ; ++r)
-                        bulk_g2s(dst + (uint32_t)(r * L.apitch * 8), r0 + (size_t)r * S.msx - off, rb, mb);
+                    // the chunk's first and last copied elements inside the superset spectra (else no copy: the
+                    // slot keeps stale values, the guard is recorded)
+                    const long long e0 = (long long)(r0 - S.xs) - off;
+                    const bool in = DH_IN(P.status, e0, S.xs_len, kSiteCoefTcCopy) &&
+                                    DH_IN(P.status, e0 + (long long)(kCtQ - 1) * S.msx + rb / 8 - 1, S.xs_len, kSiteCoefTcCopy);
+                    mbar_expect_tx(mb, (in ? (uint32_t)kCtQ * rb : 0u) + (uint32_t)L.slot_b);
+                    if (in)
+                        for (int r = 0; r < kCtQ; ++r)
+                            bulk_g2s(dst + (uint32_t)(r * L.apitch * 8), r0 + (size_t)r * S.msx - off, rb, mb);
                 } else {
                     // 16 contiguous rows of M complex values
-                    mbar_expect_tx(mb, (uint32_t)(L.slot_a + L.slot_b));
-                    bulk_g2s(dst, B.g + (size_t)(fb * P.pols + pol) * wstride + (size_t)(kCtQ * c) * M, (uint32_t)L.slot_a, mb);
+                    const long long e0 = (long long)(fb * P.pols + pol) * wstride + (long long)(kCtQ * c) * M;
+                    const bool in = DH_IN(P.status, e0 + L.slot_a / 8 - 1, B.g_len, kSiteCoefTcCopy);
+                    mbar_expect_tx(mb, (uint32_t)((in ? L.slot_a : 0) + L.slot_b));
+                    if (in) bulk_g2s(dst, B.g + e0, (uint32_t)L.slot_a, mb);
                 }
                 bulk_g2s(dst + (uint32_t)L.slot_a, tab + (size_t)c * L.slot_b, (uint32_t)L.slot_b, mb);
                 if (++s == slots) s = 0;
@@ -418,7 +426,8 @@ __global__ void __launch_bounds__(kCtThreads, 1) k_coef_tc(const __grid_constant
 #pragma unroll
                             for (int dn = 0; dn < 2; ++dn) {
                                 const int m = m0 + dm, n = n0 + dn, g = m + n;
-                                if (m < G && n < G && g < G)
+                                if (m < G && n < G && g < G &&
+                                    DH_IN(P.status, (long long)pol * modes + g * (g + 1) / 2 + m, (long long)P.pols * modes, kSiteCoefTcCoef))
                                     cf[g * (g + 1) / 2 + m] = make_float2(v[4 * dm + 2 * dn], v[4 * dm + 2 * dn + 1]);
                             }
                     }

@@ -231,7 +231,9 @@ __global__ void __launch_bounds__(FusedShape<M, T>::NT, FusedShape<M, T>::MINB)
         if constexpr (MODE == kModeInverse) {
             // the window comes from memory, rows already in the inverse transform's input order
             const float2* w = A.win_in + (size_t)(b * P.pols + pol) * M * M;
-            for (int t = tid; t < M * M; t += NT) buf[(t / M) * PITCH + t % M] = w[t];
+            for (int t = tid; t < M * M; t += NT)
+                if (DH_IN(P.status, ((long long)b * P.pols + pol) * M * M + t, (long long)A.count * P.pols * M * M, kSiteFusedWindow))
+                    buf[(t / M) * PITCH + t % M] = w[t];
             __syncthreads();
         } else {
         const bool ok = mbar_wait(mb, parity);
@@ -371,7 +373,9 @@ __global__ void __launch_bounds__(FusedShape<M, T>::NT, FusedShape<M, T>::MINB)
         }   // forward part
         if constexpr (MODE == kModeForward) {
             float2* w = A.win_out + (size_t)(b * P.pols + pol) * M * M;
-            for (int t = tid; t < M * M; t += NT) w[t] = buf[(t / M) * PITCH + t % M];
+            for (int t = tid; t < M * M; t += NT)
+                if (DH_IN(P.status, ((long long)b * P.pols + pol) * M * M + t, (long long)A.count * P.pols * M * M, kSiteFusedWindow))
+                    w[t] = buf[(t / M) * PITCH + t % M];
             __syncthreads();
             continue;
         }
@@ -407,7 +411,7 @@ __global__ void __launch_bounds__(FusedShape<M, T>::NT, FusedShape<M, T>::MINB)
                     for (int r = 0; r < MR1; ++r) {
                         const int j = blk + MR0 * r;
                         v[bb][r] = cmul(cmul(v[bb][r], ci), cy[j]);
-                        if (fld) fld[j * M + i] = v[bb][r];
+                        if (fld && DH_IN(P.status, (long long)j * M + i, (long long)M * M, kSiteFusedField)) fld[j * M + i] = v[bb][r];
                     }
                 }
                 if (ov) {
@@ -622,7 +626,7 @@ __global__ void __launch_bounds__(FusedShape<M, T>::NT, FusedShape<M, T>::MINB)
                     acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
                     acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
                 }
-                if (s8 == 0 && k < modes) cf[k] = acc;
+                if (s8 == 0 && k < modes && DH_IN(P.status, k, modes, kSiteFusedCoef)) cf[k] = acc;
             }
         }
         __syncthreads();

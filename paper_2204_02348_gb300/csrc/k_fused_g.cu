@@ -429,7 +429,7 @@ __global__ void __launch_bounds__(kGNT, sizeof(T) == 2 ? 2 : 1)
             for (int y1 = 0; y1 < 8; ++y1) {
                 const int y = t + 8 * y1;
                 e[y1] = cmul(e[y1], CY[y]);
-                if (fld) fld[y * kGM + x] = e[y1];
+                if (fld && DH_IN(P.status, (long long)y * kGM + x, (long long)kGM * kGM, kSiteFusedField)) fld[y * kGM + x] = e[y1];
             }
             if (ov) {
                 __syncwarp();
@@ -521,7 +521,7 @@ __global__ void __launch_bounds__(kGNT, sizeof(T) == 2 ? 2 : 1)
                     acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
                     acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
                 }
-                if (s8 == 0 && k < modes) cf[k] = acc;
+                if (s8 == 0 && k < modes && DH_IN(P.status, k, modes, kSiteFusedCoef)) cf[k] = acc;
             }
         }
         __syncthreads();

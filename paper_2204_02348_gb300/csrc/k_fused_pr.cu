@@ -530,7 +530,7 @@ __global__ void __launch_bounds__(kPrNT, sizeof(T) == 2 ? 2 : 1)
                     acc.x += __shfl_xor_sync(0xffffffffu, acc.x, o);
                     acc.y += __shfl_xor_sync(0xffffffffu, acc.y, o);
                 }
-                if (t == 0 && k < modes) cf[k] = acc;
+                if (t == 0 && k < modes && DH_IN(P.status, k, modes, kSiteFusedCoef)) cf[k] = acc;
             }
         }
     }

@@ -148,8 +148,12 @@ __global__ void __launch_bounds__(NT, NT == kTcThreads ? 2 : 1) k_yinv_tc(const 
                     for (int u = 0; u < LB; ++u) {
                         const int idx = j0 + u * NT;
                         const int q = idx / (COLS / 2), i = 2 * (idx % (COLS / 2));
-                        v[u] = (idx < M * COLS / 2 && i0 + i < M) ? *reinterpret_cast<const float4*>(g + (size_t)q * M + i0 + i)
-                                                                 : make_float4(0.f, 0.f, 0.f, 0.f);
+                        v[u] = (idx < M * COLS / 2 && i0 + i < M &&
+                                DH_IN(P.status, (long long)(fb * P.pols + pol) * M * M + (long long)q * M + i0 + i + 1, B.g_len,
+                                      kSiteYinvG) &&
+                                DH_ALIGNED16(P.status, g + (size_t)q * M + i0 + i))
+                                   ? *reinterpret_cast<const float4*>(g + (size_t)q * M + i0 + i)
+                                   : make_float4(0.f, 0.f, 0.f, 0.f);
                     }
 #pragma unroll
                     for (int u = 0; u < LB; ++u) {
@@ -166,7 +170,9 @@ __global__ void __launch_bounds__(NT, NT == kTcThreads ? 2 : 1) k_yinv_tc(const 
                     for (int u = 0; u < LB; ++u) {
                         const int idx = j0 + u * NT;
                         const int q = idx / COLS, i = idx % COLS;
-                        v[u] = (idx < M * COLS && i0 + i < M) ? g[(size_t)q * M + i0 + i] : make_float2(0.f, 0.f);
+                        v[u] = (idx < M * COLS && i0 + i < M &&
+                                DH_IN(P.status, (long long)(fb * P.pols + pol) * M * M + (long long)q * M + i0 + i, B.g_len, kSiteYinvG))
+                                   ? g[(size_t)q * M + i0 + i] : make_float2(0.f, 0.f);
                     }
 #pragma unroll
                     for (int u = 0; u < LB; ++u) {
@@ -186,7 +192,8 @@ __global__ void __launch_bounds__(NT, NT == kTcThreads ? 2 : 1) k_yinv_tc(const 
                 if (i0 + i < M) {
                     const float2 e = cmul(cmul(buf[idx], cxy[M + j]), cxy[i0 + i]);
                     buf[idx] = e;
-                    if (B.fields) B.fields[((size_t)(f * P.pols + pol) * M + j) * M + i0 + i] = e;
+                    if (B.fields && DH_IN(P.status, ((long long)pol * M + j) * M + i0 + i, (long long)P.pols * M * M, kSiteYinvField))
+                        B.fields[((size_t)(f * P.pols + pol) * M + j) * M + i0 + i] = e;
                 } else {
                     buf[idx] = make_float2(0.f, 0.f);
                 }
@@ -268,7 +275,7 @@ __global__ void __launch_bounds__(NT, NT == kTcThreads ? 2 : 1) k_yinv_tc(const 
             }
             __syncthreads();
         }
-        if (B.coefs && tid < modes)
+        if (B.coefs && tid < modes && DH_IN(P.status, (long long)pol * modes + tid, (long long)P.pols * modes, kSiteYinvCoef))
             B.coefs[(size_t)(f * P.pols + pol) * modes + tid] = ok ? acc : make_float2(__int_as_float(0x7fc00000), __int_as_float(0x7fc00000));
     }
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");

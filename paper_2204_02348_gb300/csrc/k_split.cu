@@ -41,8 +41,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_ypass(const __grid_constant__ P
         const T* fr = (const T*)B.src + (size_t)f * P.width * P.height;
         for (int idx = tid; idx < N * C; idx += nthr) {
             const int y = idx >> logc, c = idx & (C - 1);
-            const T* row = fr + (size_t)(pd.oy + y) * P.width + pd.ox + x0 + c;
-            float2 v = make_float2(to_f(row[0]), to_f(row[half]));
+            const long long po = (long long)(pd.oy + y) * P.width + pd.ox + x0 + c;
+            const T* row = fr + po;
+            float2 v = DH_IN(P.status, po + half, (long long)P.width * P.height, kSiteYpassFrame)
+                           ? make_float2(to_f(row[0]), to_f(row[half])) : make_float2(0.f, 0.f);
             if (pd.cal) {
                 const float* k = pd.cal + (size_t)y * N + x0 + c;
                 v.x *= __ldg(k);
@@ -61,8 +63,12 @@ __global__ void __launch_bounds__(kThreads, 2) k_ypass(const __grid_constant__ P
             const float2 za = smem[P.pos_n[k] * C + c];
             const float2 zb = smem[P.pos_n[km] * C + c];
             // column x: (Z(k) + conj Z(-k)) / 2 ; column x + N/2: (Z(k) - conj Z(-k)) / (2i)
-            r1[(size_t)q * N + x0 + c] = make_float2(0.5f * (za.x + zb.x), 0.5f * (za.y - zb.y));
-            r1[(size_t)q * N + x0 + c + half] = make_float2(0.5f * (za.y + zb.y), 0.5f * (zb.x - za.x));
+            if (DH_IN(P.status, (long long)(fb * P.pols + pol) * M * N + (long long)q * N + x0 + c + half, B.r1_len, kSiteYpassR1)) {
+                if (DH_IN(P.status, (long long)(fb * P.pols + pol) * M * N + (long long)q * N + x0 + c + half, B.r1_len, kSiteYpassR1)) {
+                    r1[(size_t)q * N + x0 + c] = make_float2(0.5f * (za.x + zb.x), 0.5f * (za.y - zb.y));
+                    r1[(size_t)q * N + x0 + c + half] = make_float2(0.5f * (za.y + zb.y), 0.5f * (zb.x - za.x));
+                }
+            }
         }
         __syncthreads();
     }
@@ -125,9 +131,12 @@ __global__ void __launch_bounds__(kThreads, (N == 256 && LOGC == 4) ? 4 : 3) k_y
                     const int idx = i0 + u * kThreads;
                     if (idx < N * Q) {
                         const int y = idx / Q, c = (idx % Q) * 4;
-                        const T* row = fr + (size_t)(pd.oy + y) * P.width + pd.ox + x0 + c;
-                        a[u] = *reinterpret_cast<const V4*>(row);
-                        b[u] = *reinterpret_cast<const V4*>(row + half);
+                        const long long po = (long long)(pd.oy + y) * P.width + pd.ox + x0 + c;
+                        const T* row = fr + po;
+                        if (DH_IN(P.status, po + half + 3, (long long)P.width * P.height, kSiteYpassFrame)) {
+                            a[u] = *reinterpret_cast<const V4*>(row);
+                            b[u] = *reinterpret_cast<const V4*>(row + half);
+                        }
                     }
                 }
 #pragma unroll
@@ -163,9 +172,12 @@ __global__ void __launch_bounds__(kThreads, (N == 256 && LOGC == 4) ? 4 : 3) k_y
                 for (int u = 0; u < 8; ++u) {
                     const int idx = i0 + u * kThreads;
                     const int y = idx >> LOGC, c = idx & (C - 1);
-                    const T* row = fr + (size_t)(pd.oy + y) * P.width + pd.ox + x0 + c;
-                    a[u] = row[0];
-                    b[u] = row[half];
+                    const long long po = (long long)(pd.oy + y) * P.width + pd.ox + x0 + c;
+                    const T* row = fr + po;
+                    if (DH_IN(P.status, po + half, (long long)P.width * P.height, kSiteYpassFrame)) {
+                        a[u] = row[0];
+                        b[u] = row[half];
+                    }
                 }
 #pragma unroll
                 for (int u = 0; u < 8; ++u) {
@@ -200,10 +212,14 @@ __global__ void __launch_bounds__(kThreads, (N == 256 && LOGC == 4) ? 4 : 3) k_y
                 const int km = (N - k) & (N - 1);
                 const float4 za = *reinterpret_cast<const float4*>(smem + dif_pos<R0, R1, R2>(k) * C + c);
                 const float4 zb = *reinterpret_cast<const float4*>(smem + dif_pos<R0, R1, R2>(km) * C + c);
-                *reinterpret_cast<float4*>(r1 + (size_t)q * N + x0 + c) =
-                    make_float4(0.5f * (za.x + zb.x), 0.5f * (za.y - zb.y), 0.5f * (za.z + zb.z), 0.5f * (za.w - zb.w));
-                *reinterpret_cast<float4*>(r1 + (size_t)q * N + x0 + c + half) =
-                    make_float4(0.5f * (za.y + zb.y), 0.5f * (zb.x - za.x), 0.5f * (za.w + zb.w), 0.5f * (zb.z - za.z));
+                if (DH_IN(P.status, (long long)(fb * P.pols + pol) * M * N + (long long)q * N + x0 + c + half + 1, B.r1_len,
+                          kSiteYpassR1) &&
+                    DH_ALIGNED16(P.status, r1 + (size_t)q * N + x0 + c) && DH_ALIGNED16(P.status, r1 + (size_t)q * N + x0 + c + half)) {
+                    *reinterpret_cast<float4*>(r1 + (size_t)q * N + x0 + c) =
+                        make_float4(0.5f * (za.x + zb.x), 0.5f * (za.y - zb.y), 0.5f * (za.z + zb.z), 0.5f * (za.w - zb.w));
+                    *reinterpret_cast<float4*>(r1 + (size_t)q * N + x0 + c + half) =
+                        make_float4(0.5f * (za.y + zb.y), 0.5f * (zb.x - za.x), 0.5f * (za.w + zb.w), 0.5f * (zb.z - za.z));
+                }
             }
         } else {
             for (int idx = tid; idx < M * C; idx += kThreads) {
@@ -213,8 +229,10 @@ __global__ void __launch_bounds__(kThreads, (N == 256 && LOGC == 4) ? 4 : 3) k_y
                 const int km = (N - k) & (N - 1);
                 const float2 za = smem[dif_pos<R0, R1, R2>(k) * C + c];
                 const float2 zb = smem[dif_pos<R0, R1, R2>(km) * C + c];
-                r1[(size_t)q * N + x0 + c] = make_float2(0.5f * (za.x + zb.x), 0.5f * (za.y - zb.y));
-                r1[(size_t)q * N + x0 + c + half] = make_float2(0.5f * (za.y + zb.y), 0.5f * (zb.x - za.x));
+                if (DH_IN(P.status, (long long)(fb * P.pols + pol) * M * N + (long long)q * N + x0 + c + half, B.r1_len, kSiteYpassR1)) {
+                    r1[(size_t)q * N + x0 + c] = make_float2(0.5f * (za.x + zb.x), 0.5f * (za.y - zb.y));
+                    r1[(size_t)q * N + x0 + c + half] = make_float2(0.5f * (za.y + zb.y), 0.5f * (zb.x - za.x));
+                }
             }
         }
         __syncthreads();
@@ -267,7 +285,9 @@ __global__ void __launch_bounds__(kThreads, 2) k_xpass(const __grid_constant__ P
                 const int idx = i0 + u * nthr;
                 const int row = idx >> logn, x = idx & (N - 1);
                 const int q = q0 + row;
-                v[u] = (idx < R * N && q < M) ? r1[(size_t)q * N + x] : make_float2(0.f, 0.f);
+                v[u] = (idx < R * N && q < M &&
+                        DH_IN(P.status, (long long)(fb * P.pols + pol) * M * N + (long long)q * N + x, B.r1_len, kSiteXpassR1))
+                           ? r1[(size_t)q * N + x] : make_float2(0.f, 0.f);
             }
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
@@ -287,7 +307,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_xpass(const __grid_constant__ P
                     if (kx < 0) kx += N;
                     v = cmul(cmul(bufN[P.pos_n[kx] * es + row], pd.phase_x[pp]), pd.phase_y[q]);
                 }
-                if (B.window) B.window[((size_t)(f * P.pols + pol) * M + q) * M + pp] = v;
+                if (B.window && DH_IN(P.status, ((long long)pol * M + q) * M + pp, (long long)P.pols * M * M, kSiteXpassWindow))
+                    B.window[((size_t)(f * P.pols + pol) * M + q) * M + pp] = v;
             }
             bufM[P.pos_m[pp] * es + row] = v;
         }
@@ -297,7 +318,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_xpass(const __grid_constant__ P
         for (int idx = tid; idx < R * M; idx += nthr) {
             const int row = idx / M, i = idx - row * M;
             const int q = q0 + row;
-            if (q < M) g[(size_t)q * M + i] = bufM[i * es + row];
+            if (q < M && DH_IN(P.status, (long long)(fb * P.pols + pol) * M * M + (long long)q * M + i, B.g_len, kSiteXpassG))
+                g[(size_t)q * M + i] = bufM[i * es + row];
         }
         __syncthreads();
     }
@@ -341,7 +363,9 @@ __global__ void __launch_bounds__(kThreads, (N == 256 && LOGR == 4 && MR0 != 0) 
                 const int idx = i0 + u * nthr;
                 const int row = idx >> logn, x = idx & (N - 1);
                 const int q = q0 + row;
-                v[u] = (idx < R * N && q < M) ? r1[(size_t)q * N + x] : make_float2(0.f, 0.f);
+                v[u] = (idx < R * N && q < M &&
+                        DH_IN(P.status, (long long)(fb * P.pols + pol) * M * N + (long long)q * N + x, B.r1_len, kSiteXpassR1))
+                           ? r1[(size_t)q * N + x] : make_float2(0.f, 0.f);
             }
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
@@ -368,7 +392,8 @@ __global__ void __launch_bounds__(kThreads, (N == 256 && LOGR == 4 && MR0 != 0) 
                     if (kx < 0) kx += N;
                     v = cmul(cmul(bufN[dif_pos<R0, R1, R2>(kx) * es + row], phx[pp]), phy[row]);
                 }
-                if (B.window) B.window[((size_t)(f * P.pols + pol) * M + q) * M + pp] = v;
+                if (B.window && DH_IN(P.status, ((long long)pol * M + q) * M + pp, (long long)P.pols * M * M, kSiteXpassWindow))
+                    B.window[((size_t)(f * P.pols + pol) * M + q) * M + pp] = v;
             }
             bufM[plan_pos<MR0, MR1, MR2>(P.pos_m, pp) * es + row] = v;
         }
@@ -381,7 +406,8 @@ __global__ void __launch_bounds__(kThreads, (N == 256 && LOGR == 4 && MR0 != 0) 
         for (int idx = tid; idx < R * M; idx += nthr) {
             const int row = idx / M, i = idx - row * M;
             const int q = q0 + row;
-            if (q < M) g[(size_t)q * M + i] = bufM[i * es + row];
+            if (q < M && DH_IN(P.status, (long long)(fb * P.pols + pol) * M * M + (long long)q * M + i, B.g_len, kSiteXpassG))
+                g[(size_t)q * M + i] = bufM[i * es + row];
         }
         __syncthreads();
     }
@@ -477,8 +503,12 @@ __global__ void __launch_bounds__(kThreads, MR0 == 0 ? 2 : (MR0 * MR1 * MR2 <= 1
                     for (int u = 0; u < 8; ++u) {
                         const int idx = j0 + u * nthr;
                         const int q = idx / (kChunkI / 2), i = 2 * (idx % (kChunkI / 2));
-                        v[u] = (idx < M * kChunkI / 2 && i0 + i < M) ? *reinterpret_cast<const float4*>(g + (size_t)q * M + i0 + i)
-                                                                     : make_float4(0.f, 0.f, 0.f, 0.f);
+                        v[u] = (idx < M * kChunkI / 2 && i0 + i < M &&
+                                DH_IN(P.status, (long long)(fb * P.pols + pol) * M * M + (long long)q * M + i0 + i + 1, B.g_len,
+                                      kSiteYinvG) &&
+                                DH_ALIGNED16(P.status, g + (size_t)q * M + i0 + i))
+                                   ? *reinterpret_cast<const float4*>(g + (size_t)q * M + i0 + i)
+                                   : make_float4(0.f, 0.f, 0.f, 0.f);
                     }
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
@@ -496,7 +526,9 @@ __global__ void __launch_bounds__(kThreads, MR0 == 0 ? 2 : (MR0 * MR1 * MR2 <= 1
                     for (int u = 0; u < 8; ++u) {
                         const int idx = j0 + u * nthr;
                         const int q = idx >> 5, i = idx & (kChunkI - 1);
-                        v[u] = (idx < M * kChunkI && i0 + i < M) ? g[(size_t)q * M + i0 + i] : make_float2(0.f, 0.f);
+                        v[u] = (idx < M * kChunkI && i0 + i < M &&
+                                DH_IN(P.status, (long long)(fb * P.pols + pol) * M * M + (long long)q * M + i0 + i, B.g_len, kSiteYinvG))
+                                   ? g[(size_t)q * M + i0 + i] : make_float2(0.f, 0.f);
                     }
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
@@ -515,7 +547,8 @@ __global__ void __launch_bounds__(kThreads, MR0 == 0 ? 2 : (MR0 * MR1 * MR2 <= 1
                 if (i0 + i < M) {
                     const float2 e = cmul(cmul(buf[idx], cxy[M + j]), cxy[i0 + i]);
                     buf[idx] = e;
-                    if (B.fields) B.fields[((size_t)(f * P.pols + pol) * M + j) * M + i0 + i] = e;
+                    if (B.fields && DH_IN(P.status, ((long long)pol * M + j) * M + i0 + i, (long long)P.pols * M * M, kSiteYinvField))
+                        B.fields[((size_t)(f * P.pols + pol) * M + j) * M + i0 + i] = e;
                 } else {
                     buf[idx] = make_float2(0.f, 0.f);
                 }
@@ -587,7 +620,8 @@ __global__ void __launch_bounds__(kThreads, MR0 == 0 ? 2 : (MR0 * MR1 * MR2 <= 1
 #pragma unroll
             for (int kk = 0; kk < 3; ++kk) {
                 const int k = tid + kk * nthr;
-                if (k < modes) B.coefs[(size_t)(f * P.pols + pol) * modes + k] = acc[kk];
+                if (k < modes && DH_IN(P.status, (long long)pol * modes + k, (long long)P.pols * modes, kSiteYinvCoef))
+                    B.coefs[(size_t)(f * P.pols + pol) * modes + k] = acc[kk];
             }
         }
     }

@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include "../../include/digholo.h"
+#include "check.cuh"
 
 namespace dhk {
 
@@ -68,6 +69,8 @@ struct Batch {
     float2* window;          // nullable [B][pol][M][M] masked window (natural order)
     float2* fields;          // nullable [B][pol][M][M]
     float2* coefs;           // nullable [B][pol][modes]
+    long long r1_len;        // elements of the r1 scratch region (the bounds-checked build tests against them)
+    long long g_len;         // elements of the g scratch region
 };
 
 // Optional per-kernel device timing: start() before and stop() after every launch, on the launch stream.
@@ -97,9 +100,15 @@ cudaError_t basis_init();
 // Batch averaging (k_avg.cu): phase-aligned mean of the x-inverse-transformed windows of each averaging
 // group.  g holds groups x members windows of E = pols * M * M elements, member j of group gi at element
 // offset gi * gstride + j * mstride; out receives [groups][E]; part is scratch of groups * members * slices.
+// X: the status block and the element extents of g, part and out (tested by the bounds-checked build).
+struct AvgExtents {
+    int* status;
+    long long g_len, part_len, out_len;
+};
 int avg_slices(long long elems);
 cudaError_t launch_avg(const float2* g, float2* part, float2* out, int groups, int members, long long elems,
-                       long long mstride, long long gstride, cudaStream_t stream, StageTimer* timer);
+                       long long mstride, long long gstride, const AvgExtents& X, cudaStream_t stream,
+                       StageTimer* timer);
 
 // Coefficient-only split-BF16 last kernel (k_coef_tc.cu): the y transform, correction and y overlap as one
 // tensor-core contraction of the x-inverse-transformed rows; for batches without fields.
@@ -114,6 +123,7 @@ struct BoxSrc {
     const float2* xs;
     int ms, msx;
     int qoff[DH_MAX_POLS], poff[DH_MAX_POLS];
+    long long xs_len;        // elements of the superset spectra (tested by the bounds-checked build)
 };
 // The same contraction reading a candidate's box bins straight from the superset spectra, with the candidate's
 // scoring tables (PolDev::score_tc): the x inverse transform is folded into the x weights, so no x-inverse

@@ -11,7 +11,8 @@
 // The overlap is always the FP32 one (the split-BF16 tables are not packed), so the handle's precision
 // setting does not apply here.  Every GPU that loads the library holds the array until the process exits.
 // All calls share it and it keeps the last call's contents; nothing in it has to start at zero, because every
-// table entry and every scratch element is written before it is read within the same call.  Calls that
+// table entry and every scratch element is written before it is read within the same call (the status block at
+// the start of the table area is part of each call's table upload, so it starts every call at zero).  Calls that
 // overlap on the GPU (queued on different streams, or from different threads without ordering) race on the
 // array: serialise them on one stream.
 #include <cuda_runtime.h>
@@ -86,6 +87,9 @@ int pack_plan(const Settings& s, const Geometry& g, const Tables& t, unsigned ch
               dhk::Plan* out) {
     if ((int)t.radix_n.size() > dhk::kMaxRadices || (int)t.radix_m.size() > dhk::kMaxRadices)
         return fail(DH_ERROR_INVALIDDIMENSION, "too many radix passes");
+    // the status block first (offset 0 of the table area): zero in every call's upload, so it reports the last call
+    const int zero_status[4] = {0, 0, 0, 0};
+    const size_t o_st = pk->put(zero_status, sizeof zero_status);
     const size_t o_twn = pk->put(t.tw_fwd_n.data(), t.tw_fwd_n.size() * 4);
     const size_t o_twm = pk->put(t.tw_inv_m.data(), t.tw_inv_m.size() * 4);
     const std::vector<int> pn = digit_reversed_positions(g.n, t.radix_n);
@@ -119,6 +123,7 @@ int pack_plan(const Settings& s, const Geometry& g, const Tables& t, unsigned ch
     P.mode_n = (const int*)(dev_tables + o_mn);
     P.modes_out = g.modes_out;
     P.basis_tt = t.basis_tt.empty() ? nullptr : (const float2*)(dev_tables + o_bt);
+    P.status = (int*)(dev_tables + o_st);
     for (int p = 0; p < g.pols; ++p) {
         const PolTables& pt = t.pol[p];
         dhk::PolDev& pd = P.pol[p];
@@ -143,6 +148,13 @@ int pack_plan(const Settings& s, const Geometry& g, const Tables& t, unsigned ch
 }
 
 }  // namespace
+
+int* noalloc_status_block(int dev) {
+    if (dev < 0 || dev >= kMaxDevices) return nullptr;
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    return reinterpret_cast<int*>(g_noalloc_addr[dev]);   // offset 0 of the table area, once the array is set up
+}
+
 }  // namespace dh
 
 using namespace dh;

@@ -125,6 +125,10 @@ cudaError_t fused_pr_init();
 int launch_fused_pr(Handle* H, const dhk::Plan& P, const void* frames, int dtype, int batch, void* fields, void* coefs,
                     cudaStream_t st, dhk::StageTimer* timer);
 
+// Status block of the allocation-free path on device dev (the start of its static array; nullptr until the first
+// call on that device set the array up).
+int* noalloc_status_block(int dev);
+
 // Group-transform fused path (k_fused_g.cu): 128 x 128 windows, 64 x 64 fields, FP32 overlap, whole path only.
 bool use_fused_g(const dhk::Plan& P);
 cudaError_t fused_g_init();

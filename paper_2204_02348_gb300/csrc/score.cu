@@ -48,7 +48,7 @@ struct Superset {
 // x transform of R superset rows per block; keeps the superset columns in natural order.
 __global__ void __launch_bounds__(kSThreads, 2) k_xfwd(const __grid_constant__ Plan P, const __grid_constant__ Superset S,
                                                        const float2* __restrict__ r1s, float2* __restrict__ xs, int count,
-                                                       int logr, int logn) {
+                                                       int logr, int logn, long long r1s_len, long long xs_len) {
     extern __shared__ float2 smem[];
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int R = 1 << logr, es = R + 1, N = P.n;
@@ -62,7 +62,9 @@ __global__ void __launch_bounds__(kSThreads, 2) k_xfwd(const __grid_constant__ P
             for (int u = 0; u < 8; ++u) {
                 const int idx = i0 + u * nthr;
                 const int q = q0 + (idx >> logn);
-                v[u] = (idx < R * N && q < S.ms) ? src[(size_t)q * N + (idx & (N - 1))] : make_float2(0.f, 0.f);
+                v[u] = (idx < R * N && q < S.ms &&
+                        DH_IN(P.status, (long long)(fb * P.pols + pol) * S.ms * N + (long long)q * N + (idx & (N - 1)), r1s_len, kSiteScore))
+                           ? src[(size_t)q * N + (idx & (N - 1))] : make_float2(0.f, 0.f);
             }
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
@@ -78,7 +80,8 @@ __global__ void __launch_bounds__(kSThreads, 2) k_xfwd(const __grid_constant__ P
             const int q = q0 + row;
             if (q < S.ms) {
                 const int kx = (S.klx[pol] + c) & (N - 1);
-                dst[(size_t)q * S.msx + c] = smem[P.pos_n[kx] * es + row];
+                if (DH_IN(P.status, (long long)(fb * P.pols + pol) * S.ms * S.msx + (long long)q * S.msx + c, xs_len, kSiteScore))
+                    dst[(size_t)q * S.msx + c] = smem[P.pos_n[kx] * es + row];
             }
         }
         __syncthreads();
@@ -91,7 +94,8 @@ __global__ void __launch_bounds__(kSThreads, 2) k_xfwd(const __grid_constant__ P
 template <int MR0, int MR1, int MR2>
 __global__ void __launch_bounds__(kSThreads, MR0 == 0 ? 2 : 4) k_xinv_sel(const __grid_constant__ Plan P, const __grid_constant__ Superset S,
                                                            const float2* __restrict__ xs, float2* __restrict__ g,
-                                                           int count, int qoff0, int qoff1, int poff0, int poff1, int logr) {
+                                                           int count, int qoff0, int qoff1, int poff0, int poff1, int logr,
+                                                           long long xs_len, long long g_len) {
     extern __shared__ float2 smem[];   // [M][R + 1] tile, then the phase and mask tables
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int R = 1 << logr, es = R + 1, M = P.m;
@@ -121,7 +125,9 @@ __global__ void __launch_bounds__(kSThreads, MR0 == 0 ? 2 : 4) k_xinv_sel(const 
                 const int row = idx / M, p = idx - row * M;
                 const int q = q0 + row;
                 v[u] = make_float2(0.f, 0.f);
-                if (idx < R * M && q < M && p >= mlo[row] && p <= mhi[row])
+                if (idx < R * M && q < M && p >= mlo[row] && p <= mhi[row] &&
+                    DH_IN(P.status, (long long)(fb * P.pols + pol) * S.ms * S.msx + (long long)(qoff + q) * S.msx + poff + p, xs_len,
+                          kSiteScore))
                     v[u] = src[(size_t)(qoff + q) * S.msx + poff + p];
             }
 #pragma unroll
@@ -145,7 +151,8 @@ __global__ void __launch_bounds__(kSThreads, MR0 == 0 ? 2 : 4) k_xinv_sel(const 
         for (int idx = tid; idx < R * M; idx += nthr) {
             const int row = idx / M, i = idx - row * M;
             const int q = q0 + row;
-            if (q < M) dst[(size_t)q * M + i] = smem[i * es + row];
+            if (q < M && DH_IN(P.status, (long long)(fb * P.pols + pol) * M * M + (long long)q * M + i, g_len, kSiteScore))
+                dst[(size_t)q * M + i] = smem[i * es + row];
         }
         __syncthreads();
     }
@@ -298,11 +305,13 @@ extern "C" int dh_score_settings(dh_handle h, const void* d_frames, int dtype, i
         B.frame0 = f0;
         B.count = n;
         B.r1 = r1s;
+        B.r1_len = (long long)(r1s_bytes / sizeof(float2));
         cudaError_t e = dhk::launch_ypass(Psup, B, st, tm);
         if (e == cudaSuccess) {
             dim3 gx((ms + R - 1) / R, pols, zf);
             if (tm) tm->start(st);
-            dhk::k_xfwd<<<gx, dhk::kSThreads, (size_t)N * (R + 1) * sizeof(float2), st>>>(P0, S, r1s, xs, n, logr, ilog2i(N));
+            dhk::k_xfwd<<<gx, dhk::kSThreads, (size_t)N * (R + 1) * sizeof(float2), st>>>(P0, S, r1s, xs, n, logr, ilog2i(N),
+                (long long)(r1s_bytes / sizeof(float2)), (long long)(xs_bytes / sizeof(float2)));
             if (tm) tm->stop(st, "k_xfwd");
             e = cudaGetLastError();
         }
@@ -323,10 +332,11 @@ extern "C" int dh_score_settings(dh_handle h, const void* d_frames, int dtype, i
             Bc.frame0 = f0;
             Bc.count = n;
             Bc.g = gbuf;
+            Bc.g_len = (long long)chunk * pols * M * M;
             // the last kernel writes frame f at (f * pols + pol) * modes: shift so frame f0 lands at slot 0
             Bc.coefs = coefs + (size_t)s * chunk * per_frame - (size_t)f0 * per_frame;
             cudaError_t e = cudaSuccess;
-            const dhk::BoxSrc box{xs, ms, msx, {qo[0], qo[1]}, {po[0], po[1]}};
+            const dhk::BoxSrc box{xs, ms, msx, {qo[0], qo[1]}, {po[0], po[1]}, (long long)(xs_bytes / sizeof(float2))};
             if (dhk::score_tc_supported(Pc, Bc, box)) {
                 // split-BF16: one contraction straight from the candidate's box in the superset spectra
                 if (tm) tm->start(st);
@@ -338,10 +348,12 @@ extern "C" int dh_score_settings(dh_handle h, const void* d_frames, int dtype, i
                 // the large configuration's field size (176 = 16 11) runs with its inverse plan fixed at compile time
                 if (M == 176 && R == 16 && Pc.nrad_m == 2 && Pc.rad_m[0] == 16 && Pc.rad_m[1] == 11)
                     dhk::k_xinv_sel<16, 11, 1><<<gi, dhk::kSThreads, ((size_t)M * (R + 1) + M + 2 * R) * sizeof(float2), st>>>(
-                        Pc, S, xs, gbuf, n, qo[0], qo[1], po[0], po[1], logr);
+                        Pc, S, xs, gbuf, n, qo[0], qo[1], po[0], po[1], logr, (long long)(xs_bytes / sizeof(float2)),
+                        (long long)chunk * pols * M * M);
                 else
                     dhk::k_xinv_sel<0, 0, 0><<<gi, dhk::kSThreads, ((size_t)M * (R + 1) + M + 2 * R) * sizeof(float2), st>>>(
-                        Pc, S, xs, gbuf, n, qo[0], qo[1], po[0], po[1], logr);
+                        Pc, S, xs, gbuf, n, qo[0], qo[1], po[0], po[1], logr, (long long)(xs_bytes / sizeof(float2)),
+                        (long long)chunk * pols * M * M);
                 if (tm) tm->stop(st, "k_xinv_sel");
                 e = cudaGetLastError();
                 if (e == cudaSuccess) e = dhk::launch_last(Pc, Bc, st, tm);

@@ -23,3 +23,26 @@ def _ensure_native_library():
 
 
 _ensure_native_library()
+
+
+@pytest.fixture(autouse=True)
+def _bounds_guards_stay_quiet(monkeypatch):
+    """Under the bounds-checked build (DH_CHECKED=1 in the environment), every handle a test destroys must have
+    passed all of its kernels' guards: its status word and guard record are read before it is destroyed."""
+    if os.environ.get("DH_CHECKED", "") in ("", "0"):
+        yield
+        return
+    import paper_2204_02348_gb300 as dh
+    orig = dh.dh_destroy
+
+    def destroy(h):
+        try:
+            st = dh.dh_get_device_status(h)
+            rec = dh.dh_get_check_record(h)
+        finally:
+            orig(h)
+        if (st & dh.DH_STATUS_BOUNDS) or rec[0]:
+            raise AssertionError(f"bounds guard fired: site {rec[0]}, offset {rec[1]}, extent {rec[2]}")
+
+    monkeypatch.setattr(dh, "dh_destroy", destroy)
+    yield

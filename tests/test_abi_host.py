@@ -285,3 +285,15 @@ def test_frames_element_width_must_match_dtype():
                 fn(h, f32, dh.DH_DTYPE_U16, 1)
     finally:
         dh.dh_destroy(h)
+
+
+def test_checked_build_exports_the_same_symbols():
+    # the bounds-checked library is the same ABI; it reports itself as checked (no GPU work)
+    import ctypes
+    path = os.path.join(os.path.dirname(dh.LIB_PATH), "libdigholo_gb300_checked.so")
+    lib = ctypes.CDLL(path)
+    for n in _declared():
+        assert hasattr(lib, n), n
+    v = ctypes.c_int(-1)
+    assert lib.dh_checked_build(ctypes.byref(v)) == 0 and v.value == 1
+    assert not dh.dh_checked_build()
