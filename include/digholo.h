@@ -122,9 +122,11 @@ int dh_set_frame(dh_handle h, int width, int height, int pol_count, double pixel
 /* Operating wavelength in metres, > 0 (digHoloConfigSetWavelengthCentre). */
 int dh_set_wavelength(dh_handle h, double wavelength);
 
-/* FFT window size (digHoloConfigSetfftWindowSize).  Values are floored to a multiple of 16 as the guide's
- * DIGHOLO_PIXEL_QUANTA rule says; the library accepts square power-of-two windows 16..1024 only
- * (DH_ERROR_INVALIDDIMENSION otherwise).  *set_nx / *set_ny (nullable) receive the sizes actually set. */
+/* FFT window size (digHoloConfigSetfftWindowSize), per axis.  Values are floored to a multiple of 16 as the
+ * guide's DIGHOLO_PIXEL_QUANTA rule says; each must then be a power of two 16..1024 (DH_ERROR_INVALIDDIMENSION
+ * otherwise).  Non-square windows (nx != ny) run the generic three-kernel path with the FP32 overlap (the fused,
+ * split-BF16 and candidate-scoring paths serve square windows and fields).  *set_nx / *set_ny (nullable) receive
+ * the sizes actually set. */
 int dh_set_fft_window(dh_handle h, int nx, int ny, int* set_nx, int* set_ny);
 
 /* Beam centre of one axis (0 = x, 1 = y) and polarisation, metres (digHoloConfigSetBeamCentre). */
@@ -133,9 +135,10 @@ int dh_set_beam_centre(dh_handle h, int axis, int pol, double centre);
 /* Radius w_c of the circular Fourier window, degrees, > 0 (digHoloConfigSetFourierWindowRadius). */
 int dh_set_fourier_window_radius(dh_handle h, double radius_deg);
 
-/* Reduced field size M (IFFT resolution mode 1).  0 selects the guide's rule M = 16 ceil(2 r / 16) (the
- * FFT [IFFT] table of the Benchmarks section); otherwise a positive multiple of 16 up to min(N, 512) whose
- * odd part has prime factors <= 19.  Square only: mx must equal my. */
+/* Reduced field size per axis (IFFT resolution mode 1).  0 selects the guide's rule M = 16 ceil(2 r / 16) with r
+ * the window radius in that axis' bins (the FFT [IFFT] table of the Benchmarks section); otherwise a positive
+ * multiple of 16 up to min(N, 512) of that axis whose odd part has prime factors <= 19.  Fields are
+ * [M_y][M_x]. */
 int dh_set_ifft_size(dh_handle h, int mx, int my);
 
 /* Reference tilt of one axis and polarisation, degrees (digHoloConfigSetTilt): the position of the
@@ -260,14 +263,18 @@ int dh_set_tuning_cache(dh_handle h, const char* path);
 int dh_autotune(dh_handle h, const void* d_frames, int dtype, int batch, void* d_fields, void* d_coefs, void* stream,
                 int reps);
 
-/* Validate the settings and report the output geometry: field size M (square), number of coefficients per
- * polarisation in the selected basis, and the field sample pitch dx' = N px / M in metres.  Any pointer may be
- * NULL.  Returns DH_ERROR_INVALIDARGUMENT when a polarisation's window leaves the frame, its tilt centre leaves
- * the half plane 0 < kappa_x <= N/2, or M exceeds N. */
+/* Validate the settings and report the output geometry: field size M_x (equal to M_y for square fields),
+ * number of coefficients per polarisation in the selected basis, and the field sample pitch dx' = N_x px / M_x
+ * in metres.  Any pointer may be NULL.  Returns DH_ERROR_INVALIDARGUMENT when a polarisation's window leaves
+ * the frame, its tilt centre leaves the half plane 0 < kappa_x <= N_x/2, or a field size exceeds its window. */
 int dh_get_output_dims(dh_handle h, int* m, int* modes, double* dx);
 
+/* The field's size and sample pitch along both axes (dh_get_output_dims' validation): fields are [M_y][M_x]
+ * complex64 per polarisation, dx' = N_x px / M_x, dy' = N_y px / M_y.  Any pointer may be NULL. */
+int dh_get_field_dims(dh_handle h, int* mx, int* my, double* dx, double* dy);
+
 /* Field axes of one polarisation in metres from its beam centre (digHoloGetFields' x and y): host arrays of
- * at least M doubles each. */
+ * at least M_x (x) and M_y (y) doubles. */
 int dh_get_axes(dh_handle h, int pol, double* x, double* y);
 
 /* Reconstruct a batch (digHoloProcessBatch).  d_frames: device array [batch][height][width] of uint16 or

@@ -130,26 +130,34 @@ class PolGeometry:
     fill_factor: bool = False   # divide the window by the 100 %-fill-factor pixel response
 
 
+def _per_axis(v) -> Tuple[int, int]:
+    """A size given once for both axes, or as (x, y)."""
+    return (int(v), int(v)) if np.isscalar(v) else (int(v[0]), int(v[1]))
+
+
 def pol_geometry(setup, p: int, tilt_deg=None, defocus=None, waist=None) -> PolGeometry:
     """Per-polarisation geometry from the acquisition settings (Alignment: beam centre, tilt, defocus;
-    Window sizes: FFT window, Fourier window radius, IFFT resolution mode 1)."""
+    Window sizes: FFT window and IFFT resolution mode 1 per axis, Fourier window radius).  Angles become bins
+    with that axis' window length: kappa = theta N px / lambda, r = w_c N px / lambda."""
     px, lam = float(setup.pixel), float(setup.wavelength)
-    n = int(setup.window)
+    ns = _per_axis(setup.window)
+    ms_req = _per_axis(setup.ifft_size)
     tdeg = setup.tilt_deg[p] if tilt_deg is None else tilt_deg
     dfc = float(setup.defocus[p] if defocus is None else defocus)
     wst = float(setup.waist[p] if waist is None else waist)
     r_rad = math.radians(float(setup.radius_deg))
-    axes = []
+    ag, rs = [], []
     for ax in range(2):
+        n = ns[ax]
         c = float(setup.beam_centre[p][ax])
         origin = round_half_away(c / px) - n // 2
         kappa = math.radians(float(tdeg[ax])) * n * px / lam
-        axes.append((c, origin, kappa))
-    r_bins = r_rad * n * px / lam
-    m = int(setup.ifft_size) if int(setup.ifft_size) > 0 else ifft_size_rule(r_bins)
-    ag = [AxisGeometry(n=n, origin=o, centre=c, kappa=k, k0=round_half_away(k), m=m, dx=n * px / m)
-          for (c, o, k) in axes]
-    return PolGeometry(x=ag[0], y=ag[1], r_x=r_bins, r_y=r_bins, defocus=dfc, waist=wst,
+        r_bins = r_rad * n * px / lam
+        m = ms_req[ax] if ms_req[ax] > 0 else ifft_size_rule(r_bins)
+        ag.append(AxisGeometry(n=n, origin=origin, centre=c, kappa=kappa, k0=round_half_away(kappa), m=m,
+                               dx=n * px / m))
+        rs.append(r_bins)
+    return PolGeometry(x=ag[0], y=ag[1], r_x=rs[0], r_y=rs[1], defocus=dfc, waist=wst,
                        groups=int(setup.group_count), pixel=px, wavelength=lam,
                        fill_factor=bool(getattr(setup, "fill_factor", False)))
 
@@ -183,11 +191,11 @@ def calibrated(frame: np.ndarray, setup) -> np.ndarray:
 
 
 def cut_window(frame: np.ndarray, g: PolGeometry) -> np.ndarray:
-    """The N x N window of polarisation p, as float64 (pipeline step 1; uint16 converts exactly)."""
-    oy, ox, n = g.y.origin, g.x.origin, g.x.n
-    if oy < 0 or ox < 0 or oy + n > frame.shape[0] or ox + n > frame.shape[1]:
+    """The N_y x N_x window of polarisation p, as float64 (pipeline step 1; uint16 converts exactly)."""
+    oy, ox, ny, nx = g.y.origin, g.x.origin, g.y.n, g.x.n
+    if oy < 0 or ox < 0 or oy + ny > frame.shape[0] or ox + nx > frame.shape[1]:
         raise ValueError("window outside the frame")
-    return np.asarray(frame[oy:oy + n, ox:ox + n], dtype=np.float64)
+    return np.asarray(frame[oy:oy + ny, ox:ox + nx], dtype=np.float64)
 
 
 def dft_rows(ax: AxisGeometry, pixel: float, bins: np.ndarray) -> np.ndarray:
@@ -347,16 +355,16 @@ def process_window(frame: np.ndarray, g: PolGeometry):
 
 
 def process_batch(frames: np.ndarray, setup) -> Tuple[np.ndarray, np.ndarray]:
-    """digHoloProcessBatch: fields [B][P][M][M] and coefficients [B][P][modes] (pol-blocked, as
+    """digHoloProcessBatch: fields [B][P][M_y][M_x] and coefficients [B][P][modes] (pol-blocked, as
     digHoloBasisGetCoefs lays them out), in the setup's basis (attribute basis: "hg" default, "lg", or
     "custom" with attribute basis_transform)."""
     geos = [pol_geometry(setup, p) for p in range(setup.pol_count)]
-    m = geos[0].x.m
+    mx, my = geos[0].x.m, geos[0].y.m
     basis = getattr(setup, "basis", "hg")
     transform = getattr(setup, "basis_transform", None)
     modes = np.asarray(transform).shape[0] if basis == "custom" else len(mode_list(geos[0].groups))
     B = frames.shape[0]
-    fields = np.empty((B, setup.pol_count, m, m), dtype=np.complex128)
+    fields = np.empty((B, setup.pol_count, my, mx), dtype=np.complex128)
     coefs = np.empty((B, setup.pol_count, modes), dtype=np.complex128)
     for b in range(B):
         frame = calibrated(frames[b], setup)
@@ -397,16 +405,16 @@ def process_batch_avg(frames: np.ndarray, setup, avg_count: int, avg_mode: int =
     """Averaged reconstruction of batch = len(frames) / avg_count fields: per group, every member's kept
     window (after the fill-factor correction when enabled, i.e. the spectrum that is inverse transformed)
     is phase-aligned with the first member's by align_phases, the aligned windows are averaged, and the
-    average is inverse transformed and decomposed once.  Returns fields [batch][P][M][M] and coefficients
+    average is inverse transformed and decomposed once.  Returns fields [batch][P][M_y][M_x] and coefficients
     [batch][P][modes] in the setup's basis."""
     geos = [pol_geometry(setup, p) for p in range(setup.pol_count)]
     A = max(int(avg_count), 1)
     B = frames.shape[0] // A
-    m = geos[0].x.m
+    mx, my = geos[0].x.m, geos[0].y.m
     basis = getattr(setup, "basis", "hg")
     transform = getattr(setup, "basis_transform", None)
     modes = np.asarray(transform).shape[0] if basis == "custom" else len(mode_list(geos[0].groups))
-    fields = np.empty((B, setup.pol_count, m, m), dtype=np.complex128)
+    fields = np.empty((B, setup.pol_count, my, mx), dtype=np.complex128)
     coefs = np.empty((B, setup.pol_count, modes), dtype=np.complex128)
     masks = [window_mask(g) for g in geos]
     corr = []
@@ -414,7 +422,7 @@ def process_batch_avg(frames: np.ndarray, setup, avg_count: int, avg_mode: int =
         if g.fill_factor:
             corr.append(1.0 / np.outer(pixel_response(g.y, box_bins(g.y)), pixel_response(g.x, box_bins(g.x))))
         else:
-            corr.append(np.ones((m, m)))
+            corr.append(np.ones((my, mx)))
     for b in range(B):
         boxes = []
         for j in range(A):

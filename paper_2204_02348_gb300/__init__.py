@@ -128,6 +128,7 @@ _PROTOS = {
     "dh_set_basis_transform": [_i, _i, _i, _p],
     "dh_get_output_dims": [_i, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_d)],
     "dh_get_axes": [_i, _i, ctypes.POINTER(_d), ctypes.POINTER(_d)],
+    "dh_get_field_dims": [_i, ctypes.POINTER(_i), ctypes.POINTER(_i), ctypes.POINTER(_d), ctypes.POINTER(_d)],
     "dh_process_batch": [_i, _p, _i, _i, _p, _p, _p],
     "dh_process_batch_window": [_i, _p, _i, _i, _p, _p, _p, _p],
     "dh_process_batch_noalloc": [_i, _p, _i, _i, _p, _p, _p],
@@ -345,9 +346,16 @@ def dh_get_output_dims(h: int):
     return m.value, modes.value, dx.value
 
 
+def dh_get_field_dims(h: int):
+    """(M_x, M_y, dx', dy'): fields are [M_y][M_x] per polarisation."""
+    mx, my, dx, dy = _i(), _i(), _d(), _d()
+    _check(_lib.dh_get_field_dims(h, ctypes.byref(mx), ctypes.byref(my), ctypes.byref(dx), ctypes.byref(dy)))
+    return mx.value, my.value, dx.value, dy.value
+
+
 def dh_get_axes(h: int, pol: int):
-    m, _, _ = dh_get_output_dims(h)
-    x, y = (_d * m)(), (_d * m)()
+    mx, my, _, _ = dh_get_field_dims(h)
+    x, y = (_d * mx)(), (_d * my)()
     _check(_lib.dh_get_axes(h, pol, x, y))
     return list(x), list(y)
 
@@ -525,9 +533,12 @@ def configure(h: int, setup) -> None:
     fill_factor, basis, basis_transform and ref_cal) to a handle through the setters."""
     dh_set_frame(h, setup.frame_w, setup.frame_h, setup.pol_count, setup.pixel)
     dh_set_wavelength(h, setup.wavelength)
-    dh_set_fft_window(h, setup.window, setup.window)
+    # window and ifft_size: one size for both axes, or (x, y)
+    nx, ny = (setup.window, setup.window) if isinstance(setup.window, int) else tuple(setup.window)
+    mx, my = (setup.ifft_size, setup.ifft_size) if isinstance(setup.ifft_size, int) else tuple(setup.ifft_size)
+    dh_set_fft_window(h, nx, ny)
     dh_set_fourier_window_radius(h, setup.radius_deg)
-    dh_set_ifft_size(h, setup.ifft_size, setup.ifft_size)
+    dh_set_ifft_size(h, mx, my)
     for p in range(setup.pol_count):
         for ax in range(2):
             dh_set_beam_centre(h, ax, p, setup.beam_centre[p][ax])
@@ -554,13 +565,14 @@ class Reconstructor:
         configure(self.h, setup)
         dh_set_precision(self.h, precision)
         self.m, self.modes, self.dx = dh_get_output_dims(self.h)
+        self.my = dh_get_field_dims(self.h)[1]
         self.pols = setup.pol_count
 
     def __call__(self, frames, fields: bool = True, coefs: bool = True, stream=None):
         import torch
         b = frames.shape[0]
         dt = DH_DTYPE_U16 if frames.dtype == torch.uint16 else DH_DTYPE_F32
-        f = torch.empty((b, self.pols, self.m, self.m), dtype=torch.complex64, device=frames.device) if fields else None
+        f = torch.empty((b, self.pols, self.my, self.m), dtype=torch.complex64, device=frames.device) if fields else None
         c = torch.empty((b, self.pols, self.modes), dtype=torch.complex64, device=frames.device) \
             if (coefs and self.modes) else None
         dh_process_batch(self.h, frames, dt, b, f, c, stream)

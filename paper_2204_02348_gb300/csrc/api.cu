@@ -93,11 +93,13 @@ static std::vector<int> pos_table(int len, const std::vector<int>& rad) {
 struct PlanImage {
     Blob b;
     size_t o_twn = 0, o_twm = 0, o_pn = 0, o_pm = 0, o_mm = 0, o_mn = 0, o_st = 0, o_bt = 0;
+    size_t o_twny = 0, o_twmy = 0, o_pny = 0, o_pmy = 0;
     size_t o_pol[DH_MAX_POLS][13] = {};
 };
 
 static int build_plan_image(const Geometry& g, const Tables& t, PlanImage* im) {
-    if ((int)t.radix_n.size() > dhk::kMaxRadices || (int)t.radix_m.size() > dhk::kMaxRadices)
+    if ((int)t.radix_n.size() > dhk::kMaxRadices || (int)t.radix_m.size() > dhk::kMaxRadices ||
+        (int)t.radix_ny.size() > dhk::kMaxRadices || (int)t.radix_my.size() > dhk::kMaxRadices)
         return fail(DH_ERROR_INVALIDDIMENSION, "too many radix passes");
     Blob& b = im->b;
     im->o_twn = b.put(t.tw_fwd_n.data(), t.tw_fwd_n.size() * 4);
@@ -105,6 +107,18 @@ static int build_plan_image(const Geometry& g, const Tables& t, PlanImage* im) {
     std::vector<int> pn = pos_table(g.n, t.radix_n), pm = pos_table(g.m, t.radix_m);
     im->o_pn = b.put(pn.data(), pn.size() * 4);
     im->o_pm = b.put(pm.data(), pm.size() * 4);
+    if (g.square()) {
+        im->o_twny = im->o_twn;
+        im->o_twmy = im->o_twm;
+        im->o_pny = im->o_pn;
+        im->o_pmy = im->o_pm;
+    } else {
+        im->o_twny = b.put(t.tw_fwd_ny.data(), t.tw_fwd_ny.size() * 4);
+        im->o_twmy = b.put(t.tw_inv_my.data(), t.tw_inv_my.size() * 4);
+        std::vector<int> pny = pos_table(g.ny, t.radix_ny), pmy = pos_table(g.my, t.radix_my);
+        im->o_pny = b.put(pny.data(), pny.size() * 4);
+        im->o_pmy = b.put(pmy.data(), pmy.size() * 4);
+    }
     im->o_mm = b.put(t.mode_m.data(), t.mode_m.size() * 4);
     im->o_mn = b.put(t.mode_n.data(), t.mode_n.size() * 4);
     const int zero_status[4] = {0, 0, 0, 0};
@@ -151,6 +165,16 @@ static void plan_from_image(const Settings& s, const Geometry& g, const Tables& 
     P.tw_inv_m = (const float2*)(base + im.o_twm);
     P.pos_n = (const int*)(base + im.o_pn);
     P.pos_m = (const int*)(base + im.o_pm);
+    P.ny = g.ny;
+    P.my = g.my;
+    P.nrad_ny = (int)t.radix_ny.size();
+    P.nrad_my = (int)t.radix_my.size();
+    for (int i = 0; i < P.nrad_ny; ++i) P.rad_ny[i] = t.radix_ny[i];
+    for (int i = 0; i < P.nrad_my; ++i) P.rad_my[i] = t.radix_my[i];
+    P.tw_fwd_ny = (const float2*)(base + im.o_twny);
+    P.tw_inv_my = (const float2*)(base + im.o_twmy);
+    P.pos_ny = (const int*)(base + im.o_pny);
+    P.pos_my = (const int*)(base + im.o_pmy);
     P.mode_m = (const int*)(base + im.o_mm);
     P.mode_n = (const int*)(base + im.o_mn);
     P.status = (int*)(base + im.o_st);
@@ -170,7 +194,7 @@ static void plan_from_image(const Settings& s, const Geometry& g, const Tables& 
         pd.corr_y = (const float2*)(base + im.o_pol[p][5]);
         pd.hg_x = (const float*)(base + im.o_pol[p][6]);
         pd.hg_y = (const float*)(base + im.o_pol[p][7]);
-        pd.hgy_tc = (const uint16_t*)(base + im.o_pol[p][8]);
+        pd.hgy_tc = t.pol[p].hgy_tc.empty() ? nullptr : (const uint16_t*)(base + im.o_pol[p][8]);
         pd.cal = t.pol[p].cal.empty() ? nullptr : (const float*)(base + im.o_pol[p][9]);
         pd.pr = t.pol[p].pr.empty() ? nullptr : base + im.o_pol[p][10];
         pd.coef_tc = t.pol[p].coef_tc.empty() ? nullptr : base + im.o_pol[p][11];
@@ -315,7 +339,7 @@ int chunk_frames(size_t per_frame_bytes, int pols, int batch, int device, size_t
     return (int)std::max<size_t>(1, std::min<size_t>(frames, (size_t)batch));
 }
 
-size_t split_window_bytes(const dhk::Plan& P) { return ((size_t)P.m * P.n + (size_t)P.m * P.m) * sizeof(float2); }
+size_t split_window_bytes(const dhk::Plan& P) { return ((size_t)P.my * P.n + (size_t)P.my * P.m) * sizeof(float2); }
 
 // ------------------------------------------------------------------------------------------- profiler
 
@@ -458,7 +482,7 @@ int process_avg(Handle* H, const void* frames, int dtype, int batch, int avg, in
     void* out = nullptr;
     rc = basis_target(H, batch, &coefs, &out);
     if (rc) return rc;
-    const long long elems = (long long)P.pols * P.m * P.m;
+    const long long elems = (long long)P.pols * P.my * P.m;
     const int slices = dhk::avg_slices(elems);
     // 128 x 128 windows: the fused kernel's forward-only mode writes each member's window and its inverse-only
     // mode reconstructs the group means (no r1 scratch); otherwise the generic forward kernels
@@ -479,7 +503,7 @@ int process_avg(Handle* H, const void* frames, int dtype, int batch, int avg, in
     if (rc) return rc;
     // scratch: [r1 of every member (generic path only)] [member windows] [group means] [inner-product partials]
     float2* r1 = (float2*)H->d_scratch;
-    float2* gbuf = fused ? r1 : r1 + (size_t)chunk * avg * P.pols * P.m * P.n;
+    float2* gbuf = fused ? r1 : r1 + (size_t)chunk * avg * P.pols * P.my * P.n;
     float2* mean = gbuf + (size_t)chunk * avg * elems;
     float2* part = mean + (size_t)chunk * elems;
     if ((size_t)((part + (size_t)chunk * avg * slices) - r1) * sizeof(float2) > H->scratch_bytes)
@@ -491,7 +515,7 @@ int process_avg(Handle* H, const void* frames, int dtype, int batch, int avg, in
         B.src = frames;
         B.dtype = dtype;
         B.r1 = r1;
-        B.r1_len = fused ? 0 : (long long)chunk * avg * P.pols * P.m * P.n;
+        B.r1_len = fused ? 0 : (long long)chunk * avg * P.pols * P.my * P.n;
         long long mstride, gstride;
         cudaError_t e = cudaSuccess;
         const int total = batch * avg;
@@ -582,7 +606,7 @@ void window_rows(const dhk::Plan& P, int* row0, int* rows) {
     int lo = P.height, hi = 0;
     for (int p = 0; p < P.pols; ++p) {
         lo = std::min(lo, P.pol[p].oy);
-        hi = std::max(hi, P.pol[p].oy + P.n);
+        hi = std::max(hi, P.pol[p].oy + P.ny);   // the window is N_y rows high
     }
     *row0 = lo;
     *rows = hi - lo;
@@ -594,7 +618,7 @@ int run_split(const dhk::Plan& P, void* scratch, size_t scratch_bytes, const voi
     const int chunk = (int)std::min<size_t>((size_t)batch, scratch_bytes / per_frame);
     if (chunk < 1) return fail(DH_ERROR_MEMORYALLOCATION, "scratch smaller than one frame");
     float2* r1 = (float2*)scratch;
-    float2* g = r1 + (size_t)chunk * P.pols * P.m * P.n;
+    float2* g = r1 + (size_t)chunk * P.pols * P.my * P.n;
     for (int f0 = 0; f0 < batch; f0 += chunk) {
         dhk::Batch B;
         B.src = frames;
@@ -603,8 +627,8 @@ int run_split(const dhk::Plan& P, void* scratch, size_t scratch_bytes, const voi
         B.count = std::min(chunk, batch - f0);
         B.r1 = r1;
         B.g = g;
-        B.r1_len = (long long)chunk * P.pols * P.m * P.n;
-        B.g_len = (long long)chunk * P.pols * P.m * P.m;
+        B.r1_len = (long long)chunk * P.pols * P.my * P.n;
+        B.g_len = (long long)chunk * P.pols * P.my * P.m;
         B.window = (float2*)window;
         B.fields = (float2*)fields;
         B.coefs = (float2*)coefs;
@@ -673,9 +697,10 @@ int dh_set_fft_window(dh_handle h, int nx, int ny, int* set_nx, int* set_ny) {
     GET_HANDLE(h);
     const int fx = (nx / 16) * 16, fy = (ny / 16) * 16;
     if (fx <= 0 || fy <= 0) return fail(DH_ERROR_INVALIDDIMENSION, "window size must be at least 16");
-    if (fx != fy) return fail(DH_ERROR_INVALIDDIMENSION, "only square FFT windows are supported");
-    if (fx > DH_MAX_WINDOW || (fx & (fx - 1))) return fail(DH_ERROR_INVALIDDIMENSION, "window size must be a power of two up to 1024");
+    if (fx > DH_MAX_WINDOW || (fx & (fx - 1)) || fy > DH_MAX_WINDOW || (fy & (fy - 1)))
+        return fail(DH_ERROR_INVALIDDIMENSION, "window sizes must be powers of two up to 1024");
     H->s.n = fx;
+    H->s.ny = fy;
     H->dirty = true;
     if (set_nx) *set_nx = fx;
     if (set_ny) *set_ny = fy;
@@ -702,10 +727,12 @@ int dh_set_fourier_window_radius(dh_handle h, double radius_deg) {
 
 int dh_set_ifft_size(dh_handle h, int mx, int my) {
     GET_HANDLE(h);
-    if (mx != my) return fail(DH_ERROR_INVALIDDIMENSION, "only square fields are supported");
-    if (mx < 0 || (mx > 0 && (mx % 16 || mx > DH_MAX_FIELD || radix_plan(mx).empty())))
-        return fail(DH_ERROR_INVALIDDIMENSION, "field size must be 0 or a multiple of 16 up to 512 with a 19-smooth odd part");
+    for (int v : {mx, my})
+        if (v < 0 || (v > 0 && (v % 16 || v > DH_MAX_FIELD || radix_plan(v).empty())))
+            return fail(DH_ERROR_INVALIDDIMENSION,
+                        "field sizes must be 0 or multiples of 16 up to 512 with a 19-smooth odd part");
     H->s.m_req = mx;
+    H->s.my_req = my;
     H->dirty = true;
     return DH_SUCCESS;
 }
@@ -839,6 +866,19 @@ int dh_get_output_dims(dh_handle h, int* m, int* modes, double* dx) {
     return DH_SUCCESS;
 }
 
+int dh_get_field_dims(dh_handle h, int* mx, int* my, double* dx, double* dy) {
+    GET_HANDLE(h);
+    Geometry g;
+    std::string why;
+    int rc = build_geometry(H->s, &g, &why);
+    if (rc) return fail(rc, why);
+    if (mx) *mx = g.m;
+    if (my) *my = g.my;
+    if (dx) *dx = g.dx;
+    if (dy) *dy = g.dy;
+    return DH_SUCCESS;
+}
+
 int dh_get_axes(dh_handle h, int pol, double* x, double* y) {
     GET_HANDLE(h);
     if (!x || !y) return fail(DH_ERROR_NULLPOINTER, "axis arrays are null");
@@ -847,10 +887,8 @@ int dh_get_axes(dh_handle h, int pol, double* x, double* y) {
     std::string why;
     int rc = build_geometry(H->s, &g, &why);
     if (rc) return fail(rc, why);
-    for (int i = 0; i < g.m; ++i) {
-        x[i] = (double)(i - g.m / 2) * g.dx;
-        y[i] = (double)(i - g.m / 2) * g.dx;
-    }
+    for (int i = 0; i < g.m; ++i) x[i] = (double)(i - g.m / 2) * g.dx;
+    for (int j = 0; j < g.my; ++j) y[j] = (double)(j - g.my / 2) * g.dy;
     return DH_SUCCESS;
 }
 

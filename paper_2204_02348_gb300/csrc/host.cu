@@ -105,7 +105,7 @@ static int process_host(Handle* H, const void* h_frames, int dtype, int batch, v
     for (int p = 0; p < P.pols; ++p) Pc.pol[p].oy -= row0;
     const size_t full = (size_t)P.width * P.height * esz;
     const size_t frame = (size_t)P.width * rows * esz;
-    const size_t field = h_fields ? (size_t)P.pols * P.m * P.m * sizeof(float2) : 0;
+    const size_t field = h_fields ? (size_t)P.pols * P.my * P.m * sizeof(float2) : 0;
     const size_t coef = h_coefs ? (size_t)P.pols * P.modes_out * sizeof(float2) : 0;
     // staged frames start 256-byte aligned, so the row pitch alone decides whether the fused path applies
     const bool fused = fused_allowed(H, P) && ((size_t)P.width * esz) % 16 == 0;

@@ -501,8 +501,8 @@ cudaError_t ct_launch(const Plan& P, const Batch& B, const BoxSrc& S, cudaStream
 }  // namespace
 
 bool coef_tc_supported(const Plan& P, const Batch& B) {
-    // the rows are copied in bulk: 16-byte aligned
-    if (!ct_fits(P, B, false) || !B.g || (reinterpret_cast<uintptr_t>(B.g) & 15) != 0) return false;
+    // the rows are copied in bulk: 16-byte aligned; square fields only
+    if (P.ny != P.n || P.my != P.m || !ct_fits(P, B, false) || !B.g || (reinterpret_cast<uintptr_t>(B.g) & 15) != 0) return false;
     for (int p = 0; p < P.pols; ++p)
         if (!P.pol[p].coef_tc) return false;
     return true;
@@ -511,7 +511,7 @@ bool coef_tc_supported(const Plan& P, const Batch& B) {
 bool score_tc_supported(const Plan& P, const Batch& B, const BoxSrc& S) {
     // bulk copies of the box rows: every row of a window starts at the same offset from a 16-byte boundary (an
     // even superset pitch on a 16-byte aligned base)
-    if (!ct_fits(P, B, true) || !S.xs || (reinterpret_cast<uintptr_t>(S.xs) & 15) != 0 || (S.msx & 1) != 0) return false;
+    if (P.ny != P.n || P.my != P.m || !ct_fits(P, B, true) || !S.xs || (reinterpret_cast<uintptr_t>(S.xs) & 15) != 0 || (S.msx & 1) != 0) return false;
     for (int p = 0; p < P.pols; ++p)
         if (!P.pol[p].score_tc) return false;
     return true;

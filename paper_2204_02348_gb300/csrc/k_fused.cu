@@ -722,7 +722,7 @@ static int g_bps[64][9] = {};   // resident blocks per SM per (field size, pixel
 static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
 
 bool use_fused(const dhk::Plan& P) {
-    if (P.n != dhk::kFN || P.groups > dhk::kFGMax) return false;
+    if (P.n != dhk::kFN || P.ny != P.n || P.my != P.m || P.groups > dhk::kFGMax) return false;
     if (P.precision == DH_PRECISION_SPLIT_BF16)   // the tensor-core variant: field size 64, B operand of 16 rows
         return P.m == 64 && (P.groups == 0 || P.tc_np == dhk::kFGMax);
     return P.precision == DH_PRECISION_FP32 && (P.m == 32 || P.m == 48 || P.m == 64);

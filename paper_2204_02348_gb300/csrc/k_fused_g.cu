@@ -539,7 +539,8 @@ static int g_g_bps[64][2] = {};
 static PFN_cuTensorMapEncodeTiled_v12000 g_g_encode = nullptr;
 
 bool use_fused_g(const dhk::Plan& P) {
-    return P.n == dhk::kGN && P.m == dhk::kGM && P.groups <= dhk::kGG && P.precision == DH_PRECISION_FP32;
+    return P.n == dhk::kGN && P.m == dhk::kGM && P.ny == P.n && P.my == P.m && P.groups <= dhk::kGG &&
+           P.precision == DH_PRECISION_FP32;
 }
 
 cudaError_t fused_g_init() {

@@ -547,7 +547,9 @@ static int g_pr_sms[64] = {0};
 static int g_pr_bps[64][2] = {};   // resident blocks per SM, per pixel type
 
 bool use_fused_pr(const dhk::Plan& P) {
-    if (P.n != dhk::kPrN || P.m != dhk::kPrM || P.groups > dhk::kPrG || P.precision != DH_PRECISION_FP32) return false;
+    if (P.n != dhk::kPrN || P.m != dhk::kPrM || P.ny != P.n || P.my != P.m || P.groups > dhk::kPrG ||
+        P.precision != DH_PRECISION_FP32)
+        return false;
     for (int p = 0; p < P.pols; ++p)
         if (!P.pol[p].pr) return false;
     return true;

@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(NT, NT == kTcThreads ? 2 : 1) k_yinv_tc(const 
 // A plan reaches the tensor-core kernel only with a B operand built for it: tc_np > 0 rows and a bf16
 // hi/lo table for every polarisation (an N = 0 instruction descriptor or a missing table is never launched).
 bool tc_supported(const Plan& P) {
-    if (!(P.precision == DH_PRECISION_SPLIT_BF16 && P.groups > 0 && P.modes <= kTcThreads && P.m <= kTcMaxM &&
+    if (!(P.precision == DH_PRECISION_SPLIT_BF16 && P.ny == P.n && P.my == P.m && P.groups > 0 && P.modes <= kTcThreads && P.m <= kTcMaxM &&
           P.m % 16 == 0 && P.tc_np > 0 && P.tc_np % 16 == 0 && P.tc_np <= kTmemCols))
         return false;
     for (int p = 0; p < P.pols; ++p)

@@ -32,14 +32,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_ypass(const __grid_constant__ P
     extern __shared__ float2 smem[];
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int C = 1 << logc;
-    const int N = P.n, M = P.m, half = N / 2;
+    // columns: N_x (packed pairs x, x + N_x/2); transform length N_y along y; M_y box rows
+    const int N = P.n, M = P.my, NY = P.ny, half = N / 2;
     const int pol = blockIdx.y;
     const PolDev& pd = P.pol[pol];
     const int x0 = blockIdx.x * C;
     for (int fb = blockIdx.z; fb < B.count; fb += gridDim.z) {
         const int f = B.frame0 + fb;
         const T* fr = (const T*)B.src + (size_t)f * P.width * P.height;
-        for (int idx = tid; idx < N * C; idx += nthr) {
+        for (int idx = tid; idx < NY * C; idx += nthr) {
             const int y = idx >> logc, c = idx & (C - 1);
             const long long po = (long long)(pd.oy + y) * P.width + pd.ox + x0 + c;
             const T* row = fr + po;
@@ -53,15 +54,15 @@ __global__ void __launch_bounds__(kThreads, 2) k_ypass(const __grid_constant__ P
             smem[idx] = v;
         }
         __syncthreads();
-        fft_run<false>(smem, N, P.rad_n, P.nrad_n, logc, C, P.tw_fwd_n, tid, nthr);
+        fft_run<false>(smem, NY, P.rad_ny, P.nrad_ny, logc, C, P.tw_fwd_ny, tid, nthr);
         float2* r1 = B.r1 + (size_t)(fb * P.pols + pol) * M * N;
         for (int idx = tid; idx < M * C; idx += nthr) {
             const int q = idx >> logc, c = idx & (C - 1);
-            int k = (pd.kly + q) % N;
-            if (k < 0) k += N;
-            const int km = (N - k) & (N - 1);
-            const float2 za = smem[P.pos_n[k] * C + c];
-            const float2 zb = smem[P.pos_n[km] * C + c];
+            int k = (pd.kly + q) % NY;
+            if (k < 0) k += NY;
+            const int km = (NY - k) & (NY - 1);
+            const float2 za = smem[P.pos_ny[k] * C + c];
+            const float2 zb = smem[P.pos_ny[km] * C + c];
             // column x: (Z(k) + conj Z(-k)) / 2 ; column x + N/2: (Z(k) - conj Z(-k)) / (2i)
             if (DH_IN(P.status, (long long)(fb * P.pols + pol) * M * N + (long long)q * N + x0 + c + half, B.r1_len, kSiteYpassR1)) {
                 if (DH_IN(P.status, (long long)(fb * P.pols + pol) * M * N + (long long)q * N + x0 + c + half, B.r1_len, kSiteYpassR1)) {
@@ -268,7 +269,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_xpass(const __grid_constant__ P
     extern __shared__ float2 smem[];
     const int tid = threadIdx.x, nthr = blockDim.x;
     const int R = 1 << logr, es = R + 1;
-    const int N = P.n, M = P.m;
+    // M_y box rows of N_x values each; M_x box columns kept and inverse transformed along x
+    const int N = P.n, M = P.m, MY = P.my;
     float2* bufN = smem;
     float2* bufM = smem + (size_t)N * es;
     const int pol = blockIdx.y;
@@ -276,7 +278,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_xpass(const __grid_constant__ P
     const int q0 = blockIdx.x * R;
     for (int fb = blockIdx.z; fb < B.count; fb += gridDim.z) {
         const int f = B.frame0 + fb;
-        const float2* r1 = B.r1 + (size_t)(fb * P.pols + pol) * M * N;
+        const float2* r1 = B.r1 + (size_t)(fb * P.pols + pol) * MY * N;
         // eight independent loads in flight per thread before their shared-memory stores
         for (int i0 = tid; i0 < R * N; i0 += 8 * nthr) {
             float2 v[8];
@@ -285,8 +287,8 @@ __global__ void __launch_bounds__(kThreads, 2) k_xpass(const __grid_constant__ P
                 const int idx = i0 + u * nthr;
                 const int row = idx >> logn, x = idx & (N - 1);
                 const int q = q0 + row;
-                v[u] = (idx < R * N && q < M &&
-                        DH_IN(P.status, (long long)(fb * P.pols + pol) * M * N + (long long)q * N + x, B.r1_len, kSiteXpassR1))
+                v[u] = (idx < R * N && q < MY &&
+                        DH_IN(P.status, (long long)(fb * P.pols + pol) * MY * N + (long long)q * N + x, B.r1_len, kSiteXpassR1))
                            ? r1[(size_t)q * N + x] : make_float2(0.f, 0.f);
             }
 #pragma unroll
@@ -301,24 +303,24 @@ __global__ void __launch_bounds__(kThreads, 2) k_xpass(const __grid_constant__ P
             const int row = idx & (R - 1), pp = idx >> logr;
             const int q = q0 + row;
             float2 v = make_float2(0.f, 0.f);
-            if (q < M) {
+            if (q < MY) {
                 if (pp >= pd.mask_lo[q] && pp <= pd.mask_hi[q]) {
                     int kx = (pd.klx + pp) % N;
                     if (kx < 0) kx += N;
                     v = cmul(cmul(bufN[P.pos_n[kx] * es + row], pd.phase_x[pp]), pd.phase_y[q]);
                 }
-                if (B.window && DH_IN(P.status, ((long long)pol * M + q) * M + pp, (long long)P.pols * M * M, kSiteXpassWindow))
-                    B.window[((size_t)(f * P.pols + pol) * M + q) * M + pp] = v;
+                if (B.window && DH_IN(P.status, ((long long)pol * MY + q) * M + pp, (long long)P.pols * MY * M, kSiteXpassWindow))
+                    B.window[((size_t)(f * P.pols + pol) * MY + q) * M + pp] = v;
             }
             bufM[P.pos_m[pp] * es + row] = v;
         }
         __syncthreads();
         fft_run<true>(bufM, M, P.rad_m, P.nrad_m, logr, es, P.tw_inv_m, tid, nthr);
-        float2* g = B.g + (size_t)(fb * P.pols + pol) * M * M;
+        float2* g = B.g + (size_t)(fb * P.pols + pol) * MY * M;
         for (int idx = tid; idx < R * M; idx += nthr) {
             const int row = idx / M, i = idx - row * M;
             const int q = q0 + row;
-            if (q < M && DH_IN(P.status, (long long)(fb * P.pols + pol) * M * M + (long long)q * M + i, B.g_len, kSiteXpassG))
+            if (q < MY && DH_IN(P.status, (long long)(fb * P.pols + pol) * MY * M + (long long)q * M + i, B.g_len, kSiteXpassG))
                 g[(size_t)q * M + i] = bufM[i * es + row];
         }
         __syncthreads();
@@ -461,22 +463,21 @@ template <int MR0, int MR1, int MR2>
 __global__ void __launch_bounds__(kThreads, MR0 == 0 ? 2 : (MR0 * MR1 * MR2 <= 128 ? 4 : 3)) k_yinv(const __grid_constant__ Plan P, const __grid_constant__ Batch B) {
     extern __shared__ float2 smem[];
     const int tid = threadIdx.x, nthr = blockDim.x;
-    const int M = P.m, G = P.groups, modes = P.modes;
-    float2* buf = smem;                          // [M][kChunkI]
-    float2* tp = smem + (size_t)M * kChunkI;     // [G][kChunkI]
+    // M: field columns (x), MY: field rows (y; equal to M for square fields)
+    const int M = P.m, MY = P.my, G = P.groups, modes = P.modes;
+    float2* buf = smem;                          // [MY][kChunkI]
+    float2* tp = smem + (size_t)MY * kChunkI;    // [G][kChunkI]
     // u_n(y'_j) for the rows j <= M/2, two modes of one parity per entry: block k holds n = 4 (k/2) + k%2 and
     // n + 2 (zero beyond G); [M/2 + 1][nbk]
-    const int nbk = 2 * ((G + 3) / 4), hm = M / 2;
+    const int nbk = 2 * ((G + 3) / 4), hm = MY / 2;
     float2* u2 = tp + (size_t)std::max(G, 1) * kChunkI;
-    float2* cxy = u2 + (size_t)(hm + 1) * nbk;   // [2][M] correction phases along x, then y
+    float2* cxy = u2 + (size_t)(hm + 1) * nbk;   // [M + MY] correction phases along x, then y
     // compile-time plans: u_m(x'_i) dx' as [G][M + 1] (the odd pitch puts the modes of a warp on distinct banks)
-    float* hgxs = reinterpret_cast<float*>(cxy + 2 * M);
+    float* hgxs = reinterpret_cast<float*>(cxy + M + MY);
     const int pol = blockIdx.x;
     const PolDev& pd = P.pol[pol];
-    for (int i = tid; i < M; i += nthr) {
-        cxy[i] = pd.corr_x[i];
-        cxy[M + i] = pd.corr_y[i];
-    }
+    for (int i = tid; i < M; i += nthr) cxy[i] = pd.corr_x[i];
+    for (int i = tid; i < MY; i += nthr) cxy[M + i] = pd.corr_y[i];
     if constexpr (MR0 != 0) {
         for (int t = tid; t < G * M; t += nthr) {
             const int n = t / M, i = t - n * M;
@@ -486,25 +487,25 @@ __global__ void __launch_bounds__(kThreads, MR0 == 0 ? 2 : (MR0 * MR1 * MR2 <= 1
     for (int t = tid; t < (hm + 1) * nbk; t += nthr) {
         const int j = t / nbk, k = t - j * nbk;
         const int na = 4 * (k >> 1) + (k & 1), nb = na + 2;
-        u2[t] = make_float2(na < G ? pd.hg_y[(size_t)na * M + j] : 0.f, nb < G ? pd.hg_y[(size_t)nb * M + j] : 0.f);
+        u2[t] = make_float2(na < G ? pd.hg_y[(size_t)na * MY + j] : 0.f, nb < G ? pd.hg_y[(size_t)nb * MY + j] : 0.f);
     }
     const bool g16 = ((uintptr_t)B.g & 15) == 0;   // 16-byte loads of the rows (M is even)
     for (int fb = blockIdx.y; fb < B.count; fb += gridDim.y) {
         const int f = B.frame0 + fb;
-        const float2* g = B.g + (size_t)(fb * P.pols + pol) * M * M;
+        const float2* g = B.g + (size_t)(fb * P.pols + pol) * MY * M;
         float2 acc[3] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f)};
         for (int i0 = 0; i0 < M; i0 += kChunkI) {
             if (g16) {
                 // two columns per 16-byte load and store (M and the chunk start are even), eight loads in flight
                 // per thread before their shared-memory stores
-                for (int j0 = tid; j0 < M * kChunkI / 2; j0 += 8 * nthr) {
+                for (int j0 = tid; j0 < MY * kChunkI / 2; j0 += 8 * nthr) {
                     float4 v[8];
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
                         const int idx = j0 + u * nthr;
                         const int q = idx / (kChunkI / 2), i = 2 * (idx % (kChunkI / 2));
-                        v[u] = (idx < M * kChunkI / 2 && i0 + i < M &&
-                                DH_IN(P.status, (long long)(fb * P.pols + pol) * M * M + (long long)q * M + i0 + i + 1, B.g_len,
+                        v[u] = (idx < MY * kChunkI / 2 && i0 + i < M &&
+                                DH_IN(P.status, (long long)(fb * P.pols + pol) * MY * M + (long long)q * M + i0 + i + 1, B.g_len,
                                       kSiteYinvG) &&
                                 DH_ALIGNED16(P.status, g + (size_t)q * M + i0 + i))
                                    ? *reinterpret_cast<const float4*>(g + (size_t)q * M + i0 + i)
@@ -513,42 +514,42 @@ __global__ void __launch_bounds__(kThreads, MR0 == 0 ? 2 : (MR0 * MR1 * MR2 <= 1
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
                         const int idx = j0 + u * nthr;
-                        if (idx < M * kChunkI / 2)
-                            *reinterpret_cast<float4*>(buf + plan_pos<MR0, MR1, MR2>(P.pos_m, idx / (kChunkI / 2)) * kChunkI +
+                        if (idx < MY * kChunkI / 2)
+                            *reinterpret_cast<float4*>(buf + plan_pos<MR0, MR1, MR2>(P.pos_my, idx / (kChunkI / 2)) * kChunkI +
                                                        2 * (idx % (kChunkI / 2))) = v[u];
                     }
                 }
             } else {
                 // eight independent loads in flight per thread before their shared-memory stores
-                for (int j0 = tid; j0 < M * kChunkI; j0 += 8 * nthr) {
+                for (int j0 = tid; j0 < MY * kChunkI; j0 += 8 * nthr) {
                     float2 v[8];
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
                         const int idx = j0 + u * nthr;
                         const int q = idx >> 5, i = idx & (kChunkI - 1);
-                        v[u] = (idx < M * kChunkI && i0 + i < M &&
-                                DH_IN(P.status, (long long)(fb * P.pols + pol) * M * M + (long long)q * M + i0 + i, B.g_len, kSiteYinvG))
+                        v[u] = (idx < MY * kChunkI && i0 + i < M &&
+                                DH_IN(P.status, (long long)(fb * P.pols + pol) * MY * M + (long long)q * M + i0 + i, B.g_len, kSiteYinvG))
                                    ? g[(size_t)q * M + i0 + i] : make_float2(0.f, 0.f);
                     }
 #pragma unroll
                     for (int u = 0; u < 8; ++u) {
                         const int idx = j0 + u * nthr;
-                        if (idx < M * kChunkI) buf[plan_pos<MR0, MR1, MR2>(P.pos_m, idx >> 5) * kChunkI + (idx & (kChunkI - 1))] = v[u];
+                        if (idx < MY * kChunkI) buf[plan_pos<MR0, MR1, MR2>(P.pos_my, idx >> 5) * kChunkI + (idx & (kChunkI - 1))] = v[u];
                     }
                 }
             }
             __syncthreads();
             if constexpr (MR0 == 0)
-                fft_run<true>(buf, M, P.rad_m, P.nrad_m, 5, kChunkI, P.tw_inv_m, tid, nthr);
+                fft_run<true>(buf, MY, P.rad_my, P.nrad_my, 5, kChunkI, P.tw_inv_my, tid, nthr);
             else
-                ifft_static<MR0, MR1, MR2, kChunkI, kChunkI, kThreads>(buf, P.tw_inv_m, tid);
-            for (int idx = tid; idx < M * kChunkI; idx += nthr) {
+                ifft_static<MR0, MR1, MR2, kChunkI, kChunkI, kThreads>(buf, P.tw_inv_my, tid);
+            for (int idx = tid; idx < MY * kChunkI; idx += nthr) {
                 const int j = idx >> 5, i = idx & (kChunkI - 1);
                 if (i0 + i < M) {
                     const float2 e = cmul(cmul(buf[idx], cxy[M + j]), cxy[i0 + i]);
                     buf[idx] = e;
-                    if (B.fields && DH_IN(P.status, ((long long)pol * M + j) * M + i0 + i, (long long)P.pols * M * M, kSiteYinvField))
-                        B.fields[((size_t)(f * P.pols + pol) * M + j) * M + i0 + i] = e;
+                    if (B.fields && DH_IN(P.status, ((long long)pol * MY + j) * M + i0 + i, (long long)P.pols * MY * M, kSiteYinvField))
+                        B.fields[((size_t)(f * P.pols + pol) * MY + j) * M + i0 + i] = e;
                 } else {
                     buf[idx] = make_float2(0.f, 0.f);
                 }
@@ -560,9 +561,9 @@ __global__ void __launch_bounds__(kThreads, MR0 == 0 ? 2 : (MR0 * MR1 * MR2 <= 1
                 // (at M - j, for the odd ones); rows 0 and M/2 have no partner and serve both parities.
                 for (int idx = tid; idx < (hm - 1) * kChunkI; idx += nthr) {
                     const int j = 1 + (idx >> 5), i = idx & (kChunkI - 1);
-                    const float2 a = buf[j * kChunkI + i], b = buf[(M - j) * kChunkI + i];
+                    const float2 a = buf[j * kChunkI + i], b = buf[(MY - j) * kChunkI + i];
                     buf[j * kChunkI + i] = cadd(a, b);
-                    buf[(M - j) * kChunkI + i] = csub(a, b);
+                    buf[(MY - j) * kChunkI + i] = csub(a, b);
                 }
                 __syncthreads();
                 for (int idx = tid; idx < nbk * kChunkI; idx += nthr) {
@@ -576,7 +577,7 @@ __global__ void __launch_bounds__(kThreads, MR0 == 0 ? 2 : (MR0 * MR1 * MR2 <= 1
                     }
                     for (int j = 1; j < hm; ++j) {
                         const float2 w = u2[j * nbk + k];
-                        const float2 e = buf[(odd ? M - j : j) * kChunkI + i];
+                        const float2 e = buf[(odd ? MY - j : j) * kChunkI + i];
                         sa.x = fmaf(w.x, e.x, sa.x); sa.y = fmaf(w.x, e.y, sa.y);
                         sb.x = fmaf(w.y, e.x, sb.x); sb.y = fmaf(w.y, e.y, sb.y);
                     }
@@ -665,18 +666,21 @@ cudaError_t launch_split(const Plan& P, const Batch& B, cudaStream_t st, StageTi
     return launch_last(P, B, st, tm);
 }
 
+// The compile-time specialisations serve square windows and fields only.
+static bool square(const Plan& P) { return P.ny == P.n && P.my == P.m; }
+
 cudaError_t launch_forward(const Plan& P, const Batch& B, cudaStream_t st, StageTimer* tm) {
     const int N = P.n, M = P.m;
     const int zf = std::min(B.count, 65535);
-    // k_ypass: C packed column pairs per block, N x C complex in shared memory
-    int logc = (N >= 1024) ? 4 : 5;
+    // k_ypass: C packed column pairs per block, N_y x C complex in shared memory
+    int logc = (std::max(N, P.ny) >= 1024) ? 4 : 5;
     logc = std::min(logc, ilog2(N / 2));
     const int C = 1 << logc;
     dim3 g1((N / 2) / C, P.pols, zf);
-    const size_t sm1 = (size_t)N * C * sizeof(float2);
+    const size_t sm1 = (size_t)P.ny * C * sizeof(float2);
     if (tm) tm->start(st);
-    const bool done = B.dtype == DH_DTYPE_U16 ? launch_ypass_static<uint16_t>(P, B, zf, st)
-                                              : launch_ypass_static<float>(P, B, zf, st);
+    const bool done = square(P) && (B.dtype == DH_DTYPE_U16 ? launch_ypass_static<uint16_t>(P, B, zf, st)
+                                                            : launch_ypass_static<float>(P, B, zf, st));
     if (!done) {
         if (B.dtype == DH_DTYPE_U16)
             k_ypass<uint16_t><<<g1, kThreads, sm1, st>>>(P, B, logc);
@@ -687,10 +691,10 @@ cudaError_t launch_forward(const Plan& P, const Batch& B, cudaStream_t st, Stage
     // k_xpass: R box rows per block
     const int logr = (N >= 512) ? 4 : 5;
     const int R = 1 << logr;
-    dim3 g2((M + R - 1) / R, P.pols, zf);
+    dim3 g2((P.my + R - 1) / R, P.pols, zf);
     const size_t sm2 = (size_t)(N + M) * (R + 1) * sizeof(float2);
     if (tm) tm->start(st);
-    if (!launch_xpass_static(P, B, zf, st)) k_xpass<<<g2, kThreads, sm2, st>>>(P, B, logr, ilog2(N));
+    if (!(square(P) && launch_xpass_static(P, B, zf, st))) k_xpass<<<g2, kThreads, sm2, st>>>(P, B, logr, ilog2(N));
     if (tm) tm->stop(st, "k_xpass");
     return cudaGetLastError();
 }
@@ -699,8 +703,8 @@ cudaError_t launch_last(const Plan& P, const Batch& B, cudaStream_t st, StageTim
     // k_yinv (or its tensor-core variant): one block per window
     const int zf = std::min(B.count, 65535);
     dim3 g3(P.pols, zf);
-    const size_t sm3 = ((size_t)(P.m + std::max(P.groups, 1)) * kChunkI +
-                        (size_t)(P.m / 2 + 1) * 2 * ((P.groups + 3) / 4) + 2 * (size_t)P.m) * sizeof(float2);
+    const size_t sm3 = ((size_t)(P.my + std::max(P.groups, 1)) * kChunkI +
+                        (size_t)(P.my / 2 + 1) * 2 * ((P.groups + 3) / 4) + (size_t)P.m + (size_t)P.my) * sizeof(float2);
     if (coef_tc_supported(P, B)) {
         // no field requested: the y transform and the y overlap as one tensor-core contraction
         if (tm) tm->start(st);
@@ -718,9 +722,9 @@ cudaError_t launch_last(const Plan& P, const Batch& B, cudaStream_t st, StageTim
     }
     const size_t sm3s = sm3 + (size_t)P.groups * (P.m + 1) * sizeof(float);   // with the staged x table
     if (tm) tm->start(st);
-    if (P.m == 96 && m_plan_is(P, 8, 4, 3))
+    if (square(P) && P.m == 96 && m_plan_is(P, 8, 4, 3))
         k_yinv<8, 4, 3><<<g3, kThreads, sm3s, st>>>(P, B);
-    else if (P.m == 176 && m_plan_is(P, 16, 11, 1))
+    else if (square(P) && P.m == 176 && m_plan_is(P, 16, 11, 1))
         k_yinv<16, 11, 1><<<g3, kThreads, sm3s, st>>>(P, B);
     else
         k_yinv<0, 0, 0><<<g3, kThreads, sm3, st>>>(P, B);
@@ -731,14 +735,14 @@ cudaError_t launch_last(const Plan& P, const Batch& B, cudaStream_t st, StageTim
 cudaError_t launch_ypass(const Plan& P, const Batch& B, cudaStream_t st, StageTimer* tm) {
     const int N = P.n;
     const int zf = std::min(B.count, 65535);
-    int logc = (N >= 1024) ? 4 : 5;
+    int logc = (std::max(N, P.ny) >= 1024) ? 4 : 5;
     logc = std::min(logc, ilog2(N / 2));
     const int C = 1 << logc;
     dim3 g1((N / 2) / C, P.pols, zf);
-    const size_t sm1 = (size_t)N * C * sizeof(float2);
+    const size_t sm1 = (size_t)P.ny * C * sizeof(float2);
     if (tm) tm->start(st);
-    const bool done = B.dtype == DH_DTYPE_U16 ? launch_ypass_static<uint16_t>(P, B, zf, st)
-                                              : launch_ypass_static<float>(P, B, zf, st);
+    const bool done = square(P) && (B.dtype == DH_DTYPE_U16 ? launch_ypass_static<uint16_t>(P, B, zf, st)
+                                                            : launch_ypass_static<float>(P, B, zf, st));
     if (!done) {
         if (B.dtype == DH_DTYPE_U16)
             k_ypass<uint16_t><<<g1, kThreads, sm1, st>>>(P, B, logc);

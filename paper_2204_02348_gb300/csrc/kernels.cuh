@@ -39,7 +39,8 @@ struct PolDev {
 };
 
 struct Plan {
-    int n, m, groups, modes, pols;
+    int n, m, groups, modes, pols;   // n, m: window and field size along x
+    int ny, my;              // window and field size along y (n, m for square geometries)
     int width, height;
     int precision;           // DH_PRECISION_*
     int tc_np;               // rows of the tensor-core B operand (16 or 32)
@@ -51,6 +52,14 @@ struct Plan {
     const float2* tw_inv_m;  // [M]
     const int* pos_n;        // [N] position of frequency k after the forward DIF passes
     const int* pos_m;        // [M] position of index k for the inverse DIT input
+    // the y axis' transforms (the generic kernels' y passes read these; equal to the x ones when square)
+    int nrad_ny, nrad_my;
+    int rad_ny[kMaxRadices];
+    int rad_my[kMaxRadices];
+    const float2* tw_fwd_ny; // [N_y]
+    const float2* tw_inv_my; // [M_y]
+    const int* pos_ny;       // [N_y]
+    const int* pos_my;       // [M_y]
     const int* mode_m;       // [modes]
     const int* mode_n;       // [modes]
     int modes_out;           // coefficients per polarisation in the output basis

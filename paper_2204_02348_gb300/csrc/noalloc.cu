@@ -85,7 +85,8 @@ std::vector<int> digit_reversed_positions(int len, const std::vector<int>& rad) 
 // Host image of the plan tables plus the kernel plan pointing into the device copy at `dev_tables`.
 int pack_plan(const Settings& s, const Geometry& g, const Tables& t, unsigned char* dev_tables, Packer* pk,
               dhk::Plan* out) {
-    if ((int)t.radix_n.size() > dhk::kMaxRadices || (int)t.radix_m.size() > dhk::kMaxRadices)
+    if ((int)t.radix_n.size() > dhk::kMaxRadices || (int)t.radix_m.size() > dhk::kMaxRadices ||
+        (int)t.radix_ny.size() > dhk::kMaxRadices || (int)t.radix_my.size() > dhk::kMaxRadices)
         return fail(DH_ERROR_INVALIDDIMENSION, "too many radix passes");
     // the status block first (offset 0 of the table area): zero in every call's upload, so it reports the last call
     const int zero_status[4] = {0, 0, 0, 0};
@@ -96,6 +97,16 @@ int pack_plan(const Settings& s, const Geometry& g, const Tables& t, unsigned ch
     const std::vector<int> pm = digit_reversed_positions(g.m, t.radix_m);
     const size_t o_pn = pk->put(pn.data(), pn.size() * 4);
     const size_t o_pm = pk->put(pm.data(), pm.size() * 4);
+    // the y axis' transforms: the x ones for square geometries, their own tables otherwise
+    size_t o_twny = o_twn, o_twmy = o_twm, o_pny = o_pn, o_pmy = o_pm;
+    if (!g.square()) {
+        o_twny = pk->put(t.tw_fwd_ny.data(), t.tw_fwd_ny.size() * 4);
+        o_twmy = pk->put(t.tw_inv_my.data(), t.tw_inv_my.size() * 4);
+        const std::vector<int> pny = digit_reversed_positions(g.ny, t.radix_ny);
+        const std::vector<int> pmy = digit_reversed_positions(g.my, t.radix_my);
+        o_pny = pk->put(pny.data(), pny.size() * 4);
+        o_pmy = pk->put(pmy.data(), pmy.size() * 4);
+    }
     const size_t o_mm = pk->put(t.mode_m.data(), t.mode_m.size() * 4);
     const size_t o_mn = pk->put(t.mode_n.data(), t.mode_n.size() * 4);
     const size_t o_bt = pk->put(t.basis_tt.data(), t.basis_tt.size() * 4);
@@ -119,6 +130,16 @@ int pack_plan(const Settings& s, const Geometry& g, const Tables& t, unsigned ch
     P.tw_inv_m = (const float2*)(dev_tables + o_twm);
     P.pos_n = (const int*)(dev_tables + o_pn);
     P.pos_m = (const int*)(dev_tables + o_pm);
+    P.ny = g.ny;
+    P.my = g.my;
+    P.nrad_ny = (int)t.radix_ny.size();
+    P.nrad_my = (int)t.radix_my.size();
+    for (int i = 0; i < P.nrad_ny; ++i) P.rad_ny[i] = t.radix_ny[i];
+    for (int i = 0; i < P.nrad_my; ++i) P.rad_my[i] = t.radix_my[i];
+    P.tw_fwd_ny = (const float2*)(dev_tables + o_twny);
+    P.tw_inv_my = (const float2*)(dev_tables + o_twmy);
+    P.pos_ny = (const int*)(dev_tables + o_pny);
+    P.pos_my = (const int*)(dev_tables + o_pmy);
     P.mode_m = (const int*)(dev_tables + o_mm);
     P.mode_n = (const int*)(dev_tables + o_mn);
     P.modes_out = g.modes_out;
@@ -202,7 +223,7 @@ extern "C" int dh_process_batch_noalloc(dh_handle h, const void* d_frames, int d
     // output-basis transform: chunks whose HG coefficients sit at the end of the static scratch
     const int chunk = (int)std::min<size_t>((size_t)batch, kNoallocScratchBytes / per_frame);
     const size_t frame_bytes = (size_t)P.width * P.height * (dtype == DH_DTYPE_U16 ? 2 : 4);
-    const size_t field_bytes = (size_t)P.pols * P.m * P.m * sizeof(float2);
+    const size_t field_bytes = (size_t)P.pols * P.my * P.m * sizeof(float2);
     const size_t coef_bytes = (size_t)P.pols * P.modes_out * sizeof(float2);
     float2* hg = (float2*)(scratch + kNoallocScratchBytes - (size_t)chunk * hg_frame);
     for (int f0 = 0; f0 < batch; f0 += chunk) {

@@ -42,9 +42,10 @@ std::vector<int> radix_plan(int len) {
 static int axis_geometry(const Settings& s, int p, int ax, const double tilt_deg, AxisGeom* a) {
     const double c = s.centre[p][ax];
     const int rc = round_half_away(c / s.pixel);
-    a->origin = rc - s.n / 2;
+    const int n = ax == 0 ? s.n : s.ny;
+    a->origin = rc - n / 2;
     a->eps = (double)rc - c / s.pixel;
-    a->kappa = tilt_deg * kDegToRad * (double)s.n * s.pixel / s.wavelength;
+    a->kappa = tilt_deg * kDegToRad * (double)n * s.pixel / s.wavelength;
     a->k0 = round_half_away(a->kappa);
     return DH_SUCCESS;
 }
@@ -56,19 +57,27 @@ static int fill(const Settings& s, const double tilt[DH_MAX_POLS][2], const doub
     if (!(s.pixel > 0.0) || !(s.wavelength > 0.0)) { *why = "pixel size and wavelength must be positive"; return DH_ERROR_INVALIDARGUMENT; }
     if (!(s.radius_deg > 0.0)) { *why = "Fourier window radius must be positive"; return DH_ERROR_INVALIDARGUMENT; }
     g->n = s.n;
+    g->ny = s.ny;
     g->pols = s.pols;
     g->groups = s.groups;
     g->modes = s.groups * (s.groups + 1) / 2;
     g->basis = s.basis == DH_BASIS_CUSTOM && s.custom.empty() ? DH_BASIS_HG : s.basis;
     g->modes_out = g->modes == 0 ? 0 : g->basis == DH_BASIS_CUSTOM ? s.custom_out : g->modes;
+    // the radius in bins along each axis: the angle times that axis' N px / lambda
     const double r = s.radius_deg * kDegToRad * (double)s.n * s.pixel / s.wavelength;
+    const double ry = s.radius_deg * kDegToRad * (double)s.ny * s.pixel / s.wavelength;
     g->m = s.m_req > 0 ? s.m_req : ifft_size_rule(r);
-    if (g->m < 16 || g->m % 16 || g->m > s.n || g->m > DH_MAX_FIELD || radix_plan(g->m).empty()) {
-        char b[160];
-        std::snprintf(b, sizeof b, "field size M=%d invalid for window N=%d (multiple of 16, <= N, <= %d, odd part 19-smooth)",
-                      g->m, s.n, DH_MAX_FIELD);
-        *why = b;
-        return DH_ERROR_INVALIDARGUMENT;
+    g->my = s.my_req > 0 ? s.my_req : ifft_size_rule(ry);
+    for (int ax = 0; ax < 2; ++ax) {
+        const int m = ax == 0 ? g->m : g->my, n = ax == 0 ? s.n : s.ny;
+        if (m < 16 || m % 16 || m > n || m > DH_MAX_FIELD || radix_plan(m).empty()) {
+            char b[192];
+            std::snprintf(b, sizeof b,
+                          "field size M=%d invalid for window N=%d along axis %d (multiple of 16, <= N, <= %d, odd part 19-smooth)",
+                          m, n, ax, DH_MAX_FIELD);
+            *why = b;
+            return DH_ERROR_INVALIDARGUMENT;
+        }
     }
     if (s.cal_on && (s.cal_w != s.width || s.cal_h != s.height)) {
         char b[160];
@@ -78,19 +87,23 @@ static int fill(const Settings& s, const double tilt[DH_MAX_POLS][2], const doub
         return DH_ERROR_INVALIDDIMENSION;
     }
     g->dx = (double)s.n * s.pixel / (double)g->m;
+    g->dy = (double)s.ny * s.pixel / (double)g->my;
     for (int p = 0; p < s.pols; ++p) {
         PolGeom& pg = g->pol[p];
         for (int ax = 0; ax < 2; ++ax) axis_geometry(s, p, ax, tilt[p][ax], &pg.ax[ax]);
         pg.r = r;
+        pg.ry = ry;
         pg.defocus = defocus[p];
         pg.waist = waist[p];
-        for (int ax = 0; ax < 2; ++ax) pg.ax[ax].klo = pg.ax[ax].k0 - g->m / 2;
+        pg.ax[0].klo = pg.ax[0].k0 - g->m / 2;
+        pg.ax[1].klo = pg.ax[1].k0 - g->my / 2;
         const int lim[2] = {s.width, s.height};
         for (int ax = 0; ax < 2; ++ax) {
-            if (pg.ax[ax].origin < 0 || pg.ax[ax].origin + s.n > lim[ax]) {
+            const int n = ax == 0 ? s.n : s.ny;
+            if (pg.ax[ax].origin < 0 || pg.ax[ax].origin + n > lim[ax]) {
                 char b[160];
                 std::snprintf(b, sizeof b, "window of polarisation %d leaves the frame along axis %d (origin %d, N %d, frame %d)",
-                              p, ax, pg.ax[ax].origin, s.n, lim[ax]);
+                              p, ax, pg.ax[ax].origin, n, lim[ax]);
                 *why = b;
                 return DH_ERROR_INVALIDARGUMENT;
             }
@@ -173,10 +186,10 @@ static void phase_fp64(const Settings& s, const AxisGeom& a, int n, int q, doubl
 
 // Tilt and defocus correction of field sample i along one axis, FP64:
 // (-1)^i exp(-2 pi i (kappa - k0)(i - M/2) / M) exp(-i pi D x'_i^2 / lambda).
-static void corr_fp64(const Settings& s, const Geometry& g, const PolGeom& pg, const AxisGeom& a, int i, double* re,
-                      double* im) {
-    const int m = g.m;
-    const double xp = (double)(i - m / 2) * g.dx;
+static void corr_fp64(const Settings& s, const Geometry& g, const PolGeom& pg, const AxisGeom& a, int ax, int i,
+                      double* re, double* im) {
+    const int m = ax == 0 ? g.m : g.my;
+    const double xp = (double)(i - m / 2) * (ax == 0 ? g.dx : g.dy);
     const double ang = -2.0 * kPi * (a.kappa - a.k0) * (double)(i - m / 2) / m - kPi * pg.defocus * xp * xp / s.wavelength;
     const double sg = (i % 2 == 0) ? 1.0 : -1.0;
     *re = sg * std::cos(ang);
@@ -227,13 +240,20 @@ void lg_transform(int groups, std::vector<double>* t) {
 }
 
 void build_tables(const Settings& s, const Geometry& g, Tables* t, bool score) {
-    const int n = g.n, m = g.m;
+    const int n = g.n, m = g.m, ny = g.ny, my = g.my;
     t->tw_fwd_n.clear();
     t->tw_inv_m.clear();
+    t->tw_fwd_ny.clear();
+    t->tw_inv_my.clear();
     for (int k = 0; k < n; ++k) push_c(t->tw_fwd_n, std::cos(-2.0 * kPi * k / n), std::sin(-2.0 * kPi * k / n));
     for (int k = 0; k < m; ++k) push_c(t->tw_inv_m, std::cos(2.0 * kPi * k / m), std::sin(2.0 * kPi * k / m));
+    for (int k = 0; k < ny; ++k) push_c(t->tw_fwd_ny, std::cos(-2.0 * kPi * k / ny), std::sin(-2.0 * kPi * k / ny));
+    for (int k = 0; k < my; ++k) push_c(t->tw_inv_my, std::cos(2.0 * kPi * k / my), std::sin(2.0 * kPi * k / my));
     t->radix_n = radix_plan(n);
-    t->radix_m = s.radix_m.empty() ? radix_plan(m) : s.radix_m;
+    // the tuner's radix plan is one of M (square geometries only)
+    t->radix_m = s.radix_m.empty() || !g.square() ? radix_plan(m) : s.radix_m;
+    t->radix_ny = radix_plan(ny);
+    t->radix_my = g.square() ? t->radix_m : radix_plan(my);
     t->mode_m.clear();
     t->mode_n.clear();
     for (int gg = 0; gg < g.groups; ++gg)
@@ -260,16 +280,17 @@ void build_tables(const Settings& s, const Geometry& g, Tables* t, bool score) {
                 }
         }
     }
-    std::vector<double> xp(m);
+    std::vector<double> xp(m), yp(my);
     for (int i = 0; i < m; ++i) xp[i] = (double)(i - m / 2) * g.dx;
+    for (int j = 0; j < my; ++j) yp[j] = (double)(j - my / 2) * g.dy;
     for (int p = 0; p < g.pols; ++p) {
         const PolGeom& pg = g.pol[p];
         PolTables& pt = t->pol[p];
         pt.cal.clear();
         if (s.cal_on) {
             // divide the frame by the reference's relative amplitude sqrt(cal / max cal)
-            pt.cal.resize((size_t)n * n);
-            for (int y = 0; y < n; ++y)
+            pt.cal.resize((size_t)ny * n);
+            for (int y = 0; y < ny; ++y)
                 for (int x = 0; x < n; ++x) {
                     const double c = s.cal[(size_t)(pg.ax[1].origin + y) * s.cal_w + pg.ax[0].origin + x];
                     pt.cal[(size_t)y * n + x] = c > 0.0 ? (float)std::sqrt(s.cal_max / c) : 0.f;
@@ -281,23 +302,25 @@ void build_tables(const Settings& s, const Geometry& g, Tables* t, bool score) {
             const AxisGeom& a = pg.ax[ax];
             ph[ax]->clear();
             co[ax]->clear();
-            for (int q = 0; q < m; ++q) {
+            const int ma = ax == 0 ? m : my, na = ax == 0 ? n : ny;
+            for (int q = 0; q < ma; ++q) {
                 double re, im;
-                phase_fp64(s, a, n, q, &re, &im);
+                phase_fp64(s, a, na, q, &re, &im);
                 push_c(*ph[ax], re, im);
             }
-            for (int i = 0; i < m; ++i) {
+            for (int i = 0; i < ma; ++i) {
                 double re, im;
-                corr_fp64(s, g, pg, a, i, &re, &im);
+                corr_fp64(s, g, pg, a, ax, i, &re, &im);
                 push_c(*co[ax], re, im);
             }
         }
-        // mask rows: the same FP64 expression as the definition, ((ky-kappa_y)/r)^2 + ((kx-kappa_x)/r)^2 <= 1
-        pt.mask_lo.assign(m, 1);
-        pt.mask_hi.assign(m, 0);
-        for (int q = 0; q < m; ++q) {
+        // mask rows: the same FP64 expression as the definition, ((ky-kappa_y)/r_y)^2 + ((kx-kappa_x)/r_x)^2 <= 1
+        // (per box row q < M_y, the kept box columns p < M_x)
+        pt.mask_lo.assign(my, 1);
+        pt.mask_hi.assign(my, 0);
+        for (int q = 0; q < my; ++q) {
             const double ky = (double)(pg.ax[1].klo + q);
-            const double ddy = (ky - pg.ax[1].kappa) / pg.r;
+            const double ddy = (ky - pg.ax[1].kappa) / pg.ry;
             int lo = -1, hi = -2;
             for (int pp = 0; pp < m; ++pp) {
                 const int kxi = pg.ax[0].klo + pp;
@@ -314,6 +337,22 @@ void build_tables(const Settings& s, const Geometry& g, Tables* t, bool score) {
         std::vector<double> u((size_t)std::max(g.groups, 1) * m);
         pt.hg_x.clear();
         pt.hg_y.clear();
+        pt.hgy_tc.clear();
+        pt.pr.clear();
+        pt.coef_tc.clear();
+        pt.coef_np = 0;
+        pt.score_tc.clear();
+        if (g.groups > 0 && !g.square()) {
+            // a field of M_x x M_y: u_m on the x grid (pitch dx'), u_n on the y grid (pitch dy'); the tensor-core
+            // and fused-kernel tables are built for square geometries only
+            hg_table(g.groups, xp.data(), m, pg.waist, u.data());
+            for (size_t k = 0; k < (size_t)g.groups * m; ++k) pt.hg_x.push_back((float)(u[k] * w));
+            std::vector<double> uy((size_t)g.groups * my);
+            hg_table(g.groups, yp.data(), my, pg.waist, uy.data());
+            for (size_t k = 0; k < (size_t)g.groups * my; ++k) pt.hg_y.push_back((float)(uy[k] * g.dy));
+            continue;
+        }
+        if (!g.square()) continue;
         if (g.groups > 0) {
             hg_table(g.groups, xp.data(), m, pg.waist, u.data());
             for (size_t k = 0; k < (size_t)g.groups * m; ++k) pt.hg_x.push_back((float)(u[k] * w));
@@ -453,8 +492,8 @@ static void coef_maps(const Settings& s, const Geometry& g, int p, const std::ve
     xi->assign((size_t)G * m, 0.0);
     std::vector<double> cxr(m), cxi(m), cyr(m), cyi(m);
     for (int i = 0; i < m; ++i) {
-        corr_fp64(s, g, pg, pg.ax[0], i, &cxr[i], &cxi[i]);
-        corr_fp64(s, g, pg, pg.ax[1], i, &cyr[i], &cyi[i]);
+        corr_fp64(s, g, pg, pg.ax[0], 0, i, &cxr[i], &cxi[i]);   // square fields only here
+        corr_fp64(s, g, pg, pg.ax[1], 1, i, &cyr[i], &cyi[i]);
     }
     std::vector<double> ar(m), ai(m), wr(m), wi(m);
     for (int e = 0; e < m; ++e) {

@@ -18,10 +18,12 @@ struct Settings {
     int width = 0, height = 0, pols = 1;
     double pixel = 20e-6;
     double wavelength = 1565e-9;
-    int n = 128;                         // FFT window (square)
+    int n = 128;                         // FFT window along x
+    int ny = 128;                        // FFT window along y
     double centre[DH_MAX_POLS][2] = {{0, 0}, {0, 0}};
     double radius_deg = 0.0;
-    int m_req = 0;                       // 0: the guide's size rule
+    int m_req = 0;                       // field size along x; 0: the guide's size rule
+    int my_req = 0;                      // field size along y; 0: the guide's size rule
     double tilt_deg[DH_MAX_POLS][2] = {{0, 0}, {0, 0}};
     double defocus[DH_MAX_POLS] = {0, 0};
     double waist[DH_MAX_POLS] = {100e-6, 100e-6};
@@ -49,15 +51,19 @@ struct AxisGeom {
 
 struct PolGeom {
     AxisGeom ax[2];
-    double r;        // window radius in bins
+    double r;        // window radius in bins along x (the radius in angle times N_x px / lambda)
+    double ry;       // the same along y (N_y px / lambda)
     double defocus, waist;
 };
 
 struct Geometry {
-    int n, m, groups, modes, pols;
+    int n, m, groups, modes, pols;   // n, m: window and field size along x
+    int ny, my;      // window and field size along y (equal to n, m for square geometries)
+    double dy;       // field pitch along y, N_y px / M_y
     int basis;       // effective basis: DH_BASIS_HG, DH_BASIS_LG or DH_BASIS_CUSTOM
     int modes_out;   // coefficients per polarisation in that basis (0 when G = 0)
-    double dx;       // field pitch N px / M
+    double dx;       // field pitch along x, N_x px / M_x
+    bool square() const { return n == ny && m == my; }
     PolGeom pol[DH_MAX_POLS];
 };
 
@@ -92,10 +98,14 @@ int tc_rows(int groups);
 uint16_t bf16_bits(float v);
 
 struct Tables {
-    std::vector<float> tw_fwd_n;   // complex [N]: exp(-2 pi i k / N)
-    std::vector<float> tw_inv_m;   // complex [M]: exp(+2 pi i k / M)
-    std::vector<int> radix_n;      // radices of N (first pass first)
-    std::vector<int> radix_m;      // radices of M
+    std::vector<float> tw_fwd_n;   // complex [N_x]: exp(-2 pi i k / N_x)
+    std::vector<float> tw_inv_m;   // complex [M_x]: exp(+2 pi i k / M_x)
+    std::vector<int> radix_n;      // radices of N_x (first pass first)
+    std::vector<int> radix_m;      // radices of M_x
+    std::vector<float> tw_fwd_ny;  // the y axis' tables (copies of the x ones for square geometries)
+    std::vector<float> tw_inv_my;
+    std::vector<int> radix_ny;
+    std::vector<int> radix_my;
     std::vector<int> mode_m, mode_n;
     // basis transform, transposed: complex [modes][modes_out] holding T[k][l] at [l][k]; empty for HG
     std::vector<float> basis_tt;

@@ -191,6 +191,8 @@ extern "C" int dh_score_settings(dh_handle h, const void* d_frames, int dtype, i
     int rc = ensure_plan(H);
     if (rc) return rc;
     if (H->plan.modes == 0) return fail(DH_ERROR_INVALIDARGUMENT, "scoring needs a basis (group count > 0)");
+    if (H->plan.ny != H->plan.n || H->plan.my != H->plan.m)
+        return fail(DH_ERROR_INVALIDDIMENSION, "candidate scoring needs a square window and field");
     static bool score_ready[64] = {false};
     if (H->device >= 0 && H->device < 64 && !score_ready[H->device]) {
         cudaError_t e = dhk::score_init();
@@ -293,6 +295,7 @@ extern "C" int dh_score_settings(dh_handle h, const void* d_frames, int dtype, i
     float2* gbuf = (float2*)((char*)H->d_scratch + r1s_bytes + xs_bytes);
     dhk::Plan Psup = P0;                 // the y pass extracts the superset rows
     Psup.m = ms;
+    Psup.my = ms;
     for (int p = 0; p < pols; ++p) Psup.pol[p].kly = kly_min[p];
     const int logr = (N >= 512) ? 4 : 5;
     const int R = 1 << logr;

@@ -212,7 +212,7 @@ void launch(dh_server_s* S, Req* r, Slot& sl) {
     for (int p = 0; p < P.pols; ++p) Pc.pol[p].oy -= row0;
     const size_t full_bytes = (size_t)P.width * P.height * esz;
     const size_t frame_bytes = (size_t)P.width * rows * esz;
-    const size_t field_bytes = (size_t)P.pols * P.m * P.m * 8;
+    const size_t field_bytes = (size_t)P.pols * P.my * P.m * 8;
     const size_t coef_bytes = (size_t)P.pols * P.modes_out * 8;
     for (int f0 = 0; f0 < r->r.batch && rc == DH_SUCCESS; f0 += r->chunk) {
         const int n = std::min(r->chunk, r->r.batch - f0);
@@ -404,7 +404,7 @@ int dh_server_submit(dh_server s, const dh_request* r, uint64_t* ticket) {
     int row0 = 0, rows = 0;
     window_rows(P, &row0, &rows);
     const size_t frame = (size_t)P.width * rows * esz;   // the uploaded rows of one frame
-    const size_t field = r->h_fields ? (size_t)P.pols * P.m * P.m * 8 : 0;
+    const size_t field = r->h_fields ? (size_t)P.pols * P.my * P.m * 8 : 0;
     const size_t coef = (r->h_coefs && P.modes) ? (size_t)P.pols * P.modes_out * 8 : 0;
     // the fused path needs no scratch; frames staged in the arena are 256-byte aligned, so only the row pitch
     // decides whether tensor copies apply

@@ -289,9 +289,13 @@ bool write_cache(const std::string& path, const std::map<std::string, dh_tuning>
 namespace dh {
 
 std::string tuning_key(const Settings& s, const Geometry& g) {
-    char b[160];
-    std::snprintf(b, sizeof b, "N%d_M%d_G%d_P%d_W%d_H%d_prec%d_basis%d", g.n, g.m, g.groups, g.pols, s.width, s.height,
-                  s.precision, g.basis);
+    char b[192];
+    if (g.square())
+        std::snprintf(b, sizeof b, "N%d_M%d_G%d_P%d_W%d_H%d_prec%d_basis%d", g.n, g.m, g.groups, g.pols, s.width, s.height,
+                      s.precision, g.basis);
+    else   // non-square windows or fields name both axes
+        std::snprintf(b, sizeof b, "N%dx%d_M%dx%d_G%d_P%d_W%d_H%d_prec%d_basis%d", g.n, g.ny, g.m, g.my, g.groups, g.pols,
+                      s.width, s.height, s.precision, g.basis);
     return b;
 }
 
@@ -327,7 +331,7 @@ bool pruned_applies(const Settings& s, const Geometry& g) {
 
 std::vector<dh_tuning> candidates(const Settings& s, const Geometry& g) {
     std::vector<dh_tuning> out;
-    const bool fused = g.n == 128 && g.groups <= 16 &&
+    const bool fused = g.n == 128 && g.square() && g.groups <= 16 &&
                        (s.precision == DH_PRECISION_FP32 ? (g.m == 32 || g.m == 48 || g.m == 64) : g.m == 64);
     if (fused) {
         if (g.m == 64 && s.precision == DH_PRECISION_FP32) out.push_back(make_tuning(DH_VARIANT_FUSED_GROUPS, 0, {}));
@@ -336,8 +340,10 @@ std::vector<dh_tuning> candidates(const Settings& s, const Geometry& g) {
         out.push_back(make_tuning(DH_VARIANT_GENERIC, 0, {}));
         return out;
     }
+    // non-square geometries: the chunk size only (their radix plans stay the defaults)
     for (int mb : kChunkMb)
-        for (const auto& plan : m_plans(g.m)) out.push_back(make_tuning(DH_VARIANT_GENERIC, mb, plan));
+        for (const auto& plan : g.square() ? m_plans(g.m) : std::vector<std::vector<int>>{radix_plan(g.m)})
+            out.push_back(make_tuning(DH_VARIANT_GENERIC, mb, plan));
     return out;
 }
 

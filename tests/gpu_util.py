@@ -34,12 +34,13 @@ def run_library(setup, frames, precision=0, fields=True, coefs=True, window=Fals
         dh.dh_set_precision(h, precision)
         dh.dh_set_variant(h, variant)
         m, modes, _ = dh.dh_get_output_dims(h)
+        my = dh.dh_get_field_dims(h)[1]   # fields are [M_y][M_x]
         B = frames.shape[0] if batch is None else max(batch, 1)
         P = setup.pol_count
         nan = complex(math.nan, math.nan)
-        f = torch.full((B, P, m, m), nan, dtype=torch.complex64, device=dev) if fields else None
+        f = torch.full((B, P, my, m), nan, dtype=torch.complex64, device=dev) if fields else None
         c = torch.full((B, P, modes), nan, dtype=torch.complex64, device=dev) if (coefs and modes) else None
-        w = torch.full((B, P, m, m), nan, dtype=torch.complex64, device=dev) if window else None
+        w = torch.full((B, P, my, m), nan, dtype=torch.complex64, device=dev) if window else None
         nb = frames.shape[0] if batch is None else batch
         if window:
             dh.dh_process_batch_window(h, fr, dt, nb, w, f, c)

@@ -4,6 +4,7 @@ import math
 import os
 import re
 
+import numpy as np
 import pytest
 
 import paper_2204_02348_gb300 as dh
@@ -57,9 +58,10 @@ def test_invalid_handle_and_arguments():
         assert _code(dh.dh_set_ifft_size, h, 16 * 23, 16 * 23) == dh.DH_ERROR_INVALIDDIMENSION  # prime 23
         assert _code(dh.dh_set_basis, h, 0, 100e-6, 40) == dh.DH_ERROR_INVALIDDIMENSION
         assert _code(dh.dh_set_precision, h, 7) == dh.DH_ERROR_INVALIDARGUMENT
-        assert _code(dh.dh_set_fft_window, h, 64, 128) == dh.DH_ERROR_INVALIDDIMENSION
+        assert _code(dh.dh_set_fft_window, h, 64, 96) == dh.DH_ERROR_INVALIDDIMENSION   # 96: not a power of two
         assert _code(dh.dh_set_fft_window, h, 15, 15) == dh.DH_ERROR_INVALIDDIMENSION
-        assert "square" in dh.dh_last_error() or "16" in dh.dh_last_error()
+        assert "16" in dh.dh_last_error()
+        assert _code(dh.dh_set_ifft_size, h, 32, 40) == dh.DH_ERROR_INVALIDDIMENSION
         # frame geometry never set
         assert _code(dh.dh_get_output_dims, h) == dh.DH_ERROR_INVALIDDIMENSION
     finally:
@@ -70,7 +72,8 @@ def test_invalid_handle_and_arguments():
 def test_fft_window_floors_to_pixel_quanta():
     h = dh.dh_create()
     try:
-        assert dh.dh_set_fft_window(h, 130, 140) == (128, 128)   # floor to multiples of 16, then equal
+        assert dh.dh_set_fft_window(h, 130, 140) == (128, 128)   # floor to multiples of 16
+        assert dh.dh_set_fft_window(h, 260, 140) == (256, 128)   # each axis on its own
         assert _code(dh.dh_set_fft_window, h, 100, 100) == dh.DH_ERROR_INVALIDDIMENSION  # 96: not a power of two
     finally:
         dh.dh_destroy(h)
@@ -297,3 +300,25 @@ def test_checked_build_exports_the_same_symbols():
     v = ctypes.c_int(-1)
     assert lib.dh_checked_build(ctypes.byref(v)) == 0 and v.value == 1
     assert not dh.dh_checked_build()
+
+
+@pytest.mark.parametrize("window,ifft", [((128, 64), 0), ((64, 128), (32, 48)), ((256, 128), (96, 48))])
+def test_non_square_dims_and_axes_match_oracle(window, ifft):
+    # per-axis windows and fields: the library's field size, pitch and axes against the oracle's geometry
+    s = syn.with_(syn.setup_batching(), frame_w=640, frame_h=512, window=window, ifft_size=ifft,
+                  beam_centre=[(160 * syn.PIXEL, 256 * syn.PIXEL), (480 * syn.PIXEL, 256 * syn.PIXEL)])
+    h = dh.dh_create()
+    try:
+        dh.configure(h, s)
+        g = orc.pol_geometry(s, 1)
+        mx, my, dx, dy = dh.dh_get_field_dims(h)
+        assert (mx, my) == (g.x.m, g.y.m)
+        assert dx == pytest.approx(g.x.dx, rel=1e-15) and dy == pytest.approx(g.y.dx, rel=1e-15)
+        m, modes, dx1 = dh.dh_get_output_dims(h)
+        assert (m, dx1) == (mx, dx) and modes == s.modes
+        x, y = dh.dh_get_axes(h, 1)
+        xe, ye = orc.output_axes(g)
+        assert np.allclose(x, xe, rtol=0, atol=1e-15) and np.allclose(y, ye, rtol=0, atol=1e-15)
+        assert len(x) == mx and len(y) == my
+    finally:
+        dh.dh_destroy(h)

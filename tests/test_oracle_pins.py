@@ -573,3 +573,82 @@ def test_search_recovers_the_true_alignment():
     p_start = orc.score_settings(d["frames"], off, np.array([off.tilt_deg]), np.array([off.defocus]),
                                  np.array([off.waist])).sum()
     assert power >= p_true * (1 - 1e-3) and power > p_start
+
+
+# ----------------------------------------------------------------------------- non-square windows and fields
+
+
+def _rect_geom(n=(32, 16), m=(16, 32), centre=(20.0, 9.0), kappa=(9.3, 4.6), r=(6.0, 3.0), defocus=0.0):
+    ax = []
+    for a in range(2):
+        c = centre[a] * PX
+        o = orc.round_half_away(c / PX) - n[a] // 2
+        ax.append(orc.AxisGeometry(n=n[a], origin=o, centre=c, kappa=kappa[a], k0=orc.round_half_away(kappa[a]),
+                                   m=m[a], dx=n[a] * PX / m[a]))
+    return orc.PolGeometry(x=ax[0], y=ax[1], r_x=r[0], r_y=r[1], defocus=defocus, waist=100e-6, groups=3,
+                           pixel=PX, wavelength=LAM)
+
+
+def test_rectangular_window_spectrum_equals_numpy_fft():
+    # an N_y x N_x window (rows along y): the separable DFT on unwrapped bins equals numpy's fft2 with each
+    # axis' own period
+    rng = np.random.default_rng(11)
+    g = _rect_geom(n=(32, 16), centre=(20.0, 9.0))
+    frame = rng.standard_normal((24, 48))
+    win = orc.cut_window(frame, g)
+    assert win.shape == (16, 32)
+    bx, by = np.arange(-16, 21), np.arange(-8, 11)
+    f = orc.window_spectrum(win, g, bins_x=bx, bins_y=by)
+    d = np.fft.fft2(win)                             # d[ky][kx]
+    ref = ((-1.0) ** (by[:, None] + bx[None, :])) * d[np.ix_(by % 16, bx % 32)]
+    assert np.max(np.abs(f - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("n,m,kappa,r", [((64, 32), (32, 16), (14.3, 6.7), (9.0, 4.5)),
+                                         ((32, 64), (16, 48), (7.2, 14.6), (4.0, 8.0))])
+def test_rectangular_exact_recovery(n, m, kappa, r):
+    """Linear hologram of a signal whose S R* has integer frequencies inside the elliptic window (the circle in
+    angle is an ellipse in bins when N_x != N_y): the reconstruction is A_R S on the M_y x M_x grid."""
+    rng = np.random.default_rng(12)
+    dioptre, a_r = 1.3, 2.0
+    g = _rect_geom(n=n, m=m, centre=(40.4, 38.7), kappa=kappa, r=r, defocus=dioptre)
+    k0 = np.array([g.x.k0, g.y.k0])
+    kap = np.array(kappa)
+    qs = [(qx, qy) for qx in range(-4, 5) for qy in range(-4, 5)
+          if ((k0[0] + qx - kap[0]) / r[0]) ** 2 + ((k0[1] + qy - kap[1]) / r[1]) ** 2 <= 0.8 and rng.uniform() < 0.7]
+    assert len(qs) >= 4
+    amps = rng.standard_normal(len(qs)) + 1j * rng.standard_normal(len(qs))
+
+    def signal(X, Y):
+        p = np.zeros(np.broadcast(X, Y).shape, dtype=np.complex128)
+        for (qx, qy), a in zip(qs, amps):
+            p += a * np.exp(2j * np.pi * (qx * X / (n[0] * PX) + qy * Y / (n[1] * PX)))
+        res = np.exp(-2j * np.pi * ((kap[0] - k0[0]) * X / (n[0] * PX) + (kap[1] - k0[1]) * Y / (n[1] * PX)))
+        return p * res * np.exp(-1j * np.pi * dioptre * (X ** 2 + Y ** 2) / LAM)
+
+    X = np.arange(80)[None, :] * PX - g.x.centre
+    Y = np.arange(80)[:, None] * PX - g.y.centre
+    R = np.exp(-2j * np.pi * (kap[0] * X / (n[0] * PX) + kap[1] * Y / (n[1] * PX))) * \
+        np.exp(-1j * np.pi * dioptre * (X ** 2 + Y ** 2) / LAM)
+    frame = a_r ** 2 + 2.0 * np.real(a_r * signal(X, Y) * np.conj(R))
+    _, _, e, _ = orc.process_window(frame, g)
+    assert e.shape == (m[1], m[0])
+    xp, yp = orc.output_axes(g)
+    expected = a_r * signal(xp[None, :], yp[:, None])
+    err = np.linalg.norm(e - expected) / np.linalg.norm(expected)
+    assert err < 1e-10, err
+
+
+def test_rectangular_geometry_per_axis_bins():
+    # per axis, angles become bins with that axis' window: kappa = theta N px / lambda, r = w_c N px / lambda,
+    # and the field-size rule 16 ceil(2 r / 16) uses that axis' radius
+    s = syn.with_(syn.setup_batching(), window=(128, 64), ifft_size=0)
+    g = orc.pol_geometry(s, 0)
+    th = [math.radians(t) for t in s.tilt_deg[0]]
+    assert g.x.kappa == pytest.approx(th[0] * 128 * PX / LAM, rel=1e-15)
+    assert g.y.kappa == pytest.approx(th[1] * 64 * PX / LAM, rel=1e-15)
+    rx = math.radians(s.radius_deg) * 128 * PX / LAM
+    assert g.r_x == pytest.approx(rx, rel=1e-15) and g.r_y == pytest.approx(rx / 2, rel=1e-15)
+    assert (g.x.m, g.y.m) == (16 * math.ceil(2 * rx / 16), 16 * math.ceil(rx / 16))
+    assert (g.x.n, g.y.n) == (128, 64)
+    assert g.x.dx == pytest.approx(128 * PX / g.x.m) and g.y.dx == pytest.approx(64 * PX / g.y.m)
