@@ -147,9 +147,9 @@ def measured_peak():
 
 
 # source file of each timed kernel; its hash also covers the device headers every kernel includes
-KERNEL_SOURCES = {"k_fused128": "k_fused.cu", "k_fused128p": ("k_fused_pr.cu", "fused_pr.hpp"), "k_yinv_tc": "k_overlap_tc.cu", "k_ypass": "k_split.cu",
-                  "k_xpass": "k_split.cu", "k_yinv": "k_split.cu"}
-DEVICE_HEADERS = ("fft.cuh", "kernels.cuh", "sync.cuh", "umma.cuh")
+KERNEL_SOURCES = {"k_fused128": "k_fused.cu", "k_fused128p": ("k_fused_pr.cu", "fused_pr.hpp"), "k_fused128g": "k_fused_g.cu",
+                  "k_yinv_tc": "k_overlap_tc.cu", "k_ypass": "k_split.cu", "k_xpass": "k_split.cu", "k_yinv": "k_split.cu"}
+DEVICE_HEADERS = ("fft.cuh", "kernels.cuh", "sync.cuh", "umma.cuh", "check.cuh")
 
 
 def kernel_source_hash(kernel):
