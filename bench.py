@@ -52,7 +52,7 @@ def parse_args():
                     help="kernel variant the handle is held to (dh_set_variant); auto: the library's choice")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-precision-case", action="store_true",
-                    help="skip the precision configuration's sub-record in the default line")
+                    help="skip the precision configuration's and the kernel variants' sub-records in the default line")
     ap.add_argument("--sustain-s", type=float, default=2.5,
                     help="seconds of back-to-back steps after the timed region (latency percentiles, clocks)")
     ap.add_argument("--frames", type=int, default=FRAMES, help="frames per step and GPU (default: the workload's 1000)")
@@ -508,6 +508,17 @@ def run_ours(args, ws, rank, local):
         cpu = {"value": rate, "unit": "frames/s", "cores": workers, "kind": "oracle",
                "sample": f"{n} frames (repeated passes over the step's batch) in {dt:.1f} s on {workers} processes"}
 
+    # ---- every kernel variant of the 128 x 128 path on the same resident batches (rank 0, N = 1 only): the
+    # measured ground for the library's default and the tuner's candidates
+    var_case = None
+    if rank == 0 and ws == 1 and not args.no_precision_case:
+        var_case = {}
+        for name in ("fused", "fused_groups", "fused_pruned", "generic"):
+            dh.dh_set_variant(h, VARIANTS[name])
+            ms = _event_time(lambda: [step(k) for k in range(ROTATE)], 25, 3) / ROTATE
+            var_case[name] = {"runs": {v: k for k, v in VARIANTS.items()}[dh.dh_get_variant(h)],
+                              "frames_per_s": frames_n / (ms / 1e3), "ms_per_batch": ms}
+        dh.dh_set_variant(h, VARIANTS[args.variant])
     dh.dh_destroy(h)
     # ---- the precision configuration beside the headline one (rank 0, N = 1 only)
     prec_case = None
@@ -537,6 +548,7 @@ def run_ours(args, ws, rank, local):
             "clocks": clocks,
             "sustained": sustained,
             "precision_case": prec_case,
+            "variants_case": var_case,
         }
         print(json.dumps(line), flush=True)
     if ws > 1:
