@@ -276,6 +276,8 @@ int init_device_once(int dev) {
     if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
     e = fused_g_init();
     if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
+    e = fused256_init();
+    if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
     e = dhk::basis_init();
     if (e != cudaSuccess) return cuda_fail(e, "kernel attributes");
     if (dev >= 0 && dev < 64) inited[dev] = true;
@@ -486,7 +488,7 @@ int process_avg(Handle* H, const void* frames, int dtype, int batch, int avg, in
     const int slices = dhk::avg_slices(elems);
     // 128 x 128 windows: the fused kernel's forward-only mode writes each member's window and its inverse-only
     // mode reconstructs the group means (no r1 scratch); otherwise the generic forward kernels
-    const bool fused = fused_allowed(H, P) && fused_frames_ok(P, frames, dtype);
+    const bool fused = fused_allowed(H, P) && use_fused(P) && fused_frames_ok(P, frames, dtype);
     // per member frame: its window (fused) or the generic path's r1 and window
     const size_t member = fused ? (size_t)elems * sizeof(float2) : split_window_bytes(P) * P.pols;
     const size_t per_group = (size_t)avg * member + (size_t)elems * sizeof(float2) + (size_t)avg * slices * sizeof(float2);

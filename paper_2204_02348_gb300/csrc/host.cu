@@ -108,7 +108,7 @@ static int process_host(Handle* H, const void* h_frames, int dtype, int batch, v
     const size_t field = h_fields ? (size_t)P.pols * P.my * P.m * sizeof(float2) : 0;
     const size_t coef = h_coefs ? (size_t)P.pols * P.modes_out * sizeof(float2) : 0;
     // staged frames start 256-byte aligned, so the row pitch alone decides whether the fused path applies
-    const bool fused = fused_allowed(H, P) && ((size_t)P.width * esz) % 16 == 0;
+    const bool fused = fused_allowed(H, P) && fused_layout_ok(P, dtype);
     const size_t scratch = (fused ? 0 : split_window_bytes(P) * P.pols) + (coef ? basis_scratch_bytes(P) : 0);
     const size_t per_frame = frame + field + coef + scratch;
     if (align_up(frame) + align_up(field) + align_up(coef) + align_up(scratch) > kSlotCap)

@@ -728,27 +728,6 @@ bool use_fused(const dhk::Plan& P) {
     return P.precision == DH_PRECISION_FP32 && (P.m == 32 || P.m == 48 || P.m == 64);
 }
 
-int resolve_variant(const Handle* H, const dhk::Plan& P, bool aligned) {
-    const bool fused = aligned && use_fused(P);
-    const bool pruned = fused && use_fused_pr(P);
-    const bool groups = fused && use_fused_g(P);
-    // without a tuner's choice, the fused kernel that transforms every column (measured fastest on the batching
-    // workload; the pruned and group-transform kernels are tuner candidates)
-    const int v = H->variant != kVariantAuto ? H->variant : (H->tuned ? H->tuned : kVariantFusedLegacy);
-    if (v == kVariantGeneric) return kVariantGeneric;
-    if (v == kVariantFusedLegacy) return fused ? kVariantFusedLegacy : kVariantGeneric;
-    if (v == kVariantFusedGroups) return groups ? kVariantFusedGroups : fused ? kVariantFusedLegacy : kVariantGeneric;
-    return pruned ? kVariantFusedPruned : fused ? kVariantFusedLegacy : kVariantGeneric;
-}
-
-bool fused_allowed(const Handle* H, const dhk::Plan& P) { return resolve_variant(H, P, true) != kVariantGeneric; }
-
-bool fused_frames_ok(const dhk::Plan& P, const void* frames, int dtype) {
-    const int esz = dtype == DH_DTYPE_U16 ? 2 : 4;
-    // tensor-copy rules: 16-byte aligned base and row pitch
-    return ((uintptr_t)frames % 16 == 0) && ((size_t)P.width * esz) % 16 == 0;
-}
-
 cudaError_t fused_init() {
     cudaError_t e;
     if (!g_encode) {
@@ -835,14 +814,6 @@ int launch_fused(Handle* H, const dhk::Plan& P, const void* frames, int dtype, i
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "fused launch");
     return DH_SUCCESS;
-}
-
-int launch_fused_path(Handle* H, const dhk::Plan& P, const void* frames, int dtype, int batch, void* fields,
-                      void* coefs, cudaStream_t st, dhk::StageTimer* tm) {
-    const int v = resolve_variant(H, P, true);
-    if (v == kVariantFusedPruned) return launch_fused_pr(H, P, frames, dtype, batch, fields, coefs, st, tm);
-    if (v == kVariantFusedGroups) return launch_fused_g(H, P, frames, dtype, batch, fields, coefs, st, tm);
-    return launch_fused(H, P, frames, dtype, batch, 0, batch, dhk::kModeFull, nullptr, nullptr, fields, coefs, st, tm);
 }
 
 }  // namespace dh

@@ -1,0 +1,554 @@
+// Fused single-kernel path for 256 x 256 windows with 96 x 96 fields (uint16 frames, FP32 overlap, G <= 16): one
+// 512-thread block per SM reconstructs one (frame, polarisation) window at a time entirely in shared memory,
+// persistent over windows.
+//
+// The y-transformed box rows of a 256 x 256 window (96 rows of 256 complex values, 192 KB) do not fit beside a
+// staging buffer, so the window is transformed along x first and along y by decimation in time over four row
+// groups: window row n = 4 n1 + n2 belongs to group n2, and the spectrum at row frequency k is
+//     X[k] = sum_{n2 < 4} W_256^{n2 k} A_{n2}[k mod 64],   A_{n2} = the 64-point DFT over n1 of group n2's rows,
+// so each group's contribution is added to a 96 x 96 accumulator as soon as it is transformed (the guide's
+// pipeline steps 1-2: FFT of the window, selection of the off-axis window; the same sums in another order).
+// Per group (64 rows, staged by two tensor copies of 136-column boxes through a 4-D view of the window rows):
+//   x pass      rows n1 and n1 + 32 packed as one complex row (times the reference-calibration factors when
+//               enabled), radix-16 DIF pass from the staged rows, radix-16 pass in place, then the separation
+//               of the two real spectra (Z(k), conj Z(-k)) on the 96 box columns;
+//   y pass      radix-16 then radix-4 DIF over n1 on the box columns; each output is multiplied by W_256^{n2 k}
+//               and added to the accumulator of its box row (one or two rows per output).  The circular mask
+//               and the beam-centre phase are applied as the last group is added.
+// Then (pipeline step 3 and digHoloProcessRemoveTilt):
+//   inverse     96-point inverse transforms with radices 12 (prime-factor 3 x 4, no twiddles) and 8, along x
+//               (DIT: the first pass reads the accumulator and writes the window in digit-reversed order) and
+//               along y (DIF);
+//   epilogue    the last y pass in registers with the residual tilt and defocus removal, the field write and the
+//               separable HG contraction (mirrored row pairs, then eight threads per mode along x), as the
+//               128 x 128 kernel does.
+// Shared memory: staging of one row group (34.8 KB, refilled by the next group's tensor copies while the current
+// group is transformed), one work buffer (the packed x rows, then the box columns, then the window during the
+// inverse), the accumulator (then the partial sums of the y contraction) and the tables: 199 KB, one block per SM.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <cstring>
+#include <string>
+
+#include "fft.cuh"
+#include "runtime.hpp"
+#include "sync.cuh"
+
+namespace dhk {
+
+constexpr int k2N = 256;             // window size
+constexpr int k2M = 96;              // field size
+constexpr int k2G = 16;              // largest group count
+constexpr int k2NT = 512;            // threads per block
+constexpr int k2Rows = 64;           // window rows per group (n1)
+constexpr int k2BoxW = 136;          // staged columns per tensor copy (128 plus the 16-byte alignment slack)
+constexpr int k2BoxBytes = k2BoxW * k2Rows * 2;
+constexpr int k2PW = k2N + 1;        // pitch of the packed x rows (odd: conflict-free column access)
+constexpr int k2PB = k2Rows + 1;     // pitch of the box columns [c][n1]
+constexpr int k2PA = k2M + 1;        // pitch of the accumulator [c][q] and of the window [x][q]
+constexpr int k2MR0 = 8, k2MR1 = 12; // inverse radix plan (DIF order)
+constexpr long k2WaitLimit = 1L << 24;
+
+struct F256Args {
+    int count;                       // frames [0, count)
+    int xo[DH_MAX_POLS];             // window origin minus the 16-byte-aligned staging origin, per polarisation
+    int x0[DH_MAX_POLS];             // staging origin (16-byte aligned element index), per polarisation
+    float2* fields;                  // nullable [B][pol][M][M]
+    float2* coefs;                   // nullable [B][pol][modes]
+};
+
+struct F256Smem {
+    static constexpr size_t STG = 2 * (size_t)k2BoxBytes;                                    // two boxes
+    static constexpr size_t WORKN = (32 * k2PW > k2M * k2PA) ? 32 * k2PW : k2M * k2PA;       // float2
+    static constexpr size_t ACCN = (size_t)k2M * k2PA;                                       // float2
+    static constexpr size_t TABN = k2N + 5 * k2M;                                            // float2
+    static constexpr size_t HGN = 2 * (size_t)k2G * k2M;                                     // float
+    static constexpr size_t INTN = 2 * k2M + 2 * (k2G * (k2G + 1) / 2);                      // int
+    static constexpr size_t bytes = STG + (WORKN + ACCN + TABN) * 8 + HGN * 4 + INTN * 4;
+};
+static_assert(F256Smem::STG % 16 == 0 && (F256Smem::WORKN * 8) % 16 == 0 && (F256Smem::ACCN * 8) % 16 == 0,
+              "16-byte aligned regions");
+static_assert(4 * k2G * k2M <= (int)F256Smem::ACCN, "the partial sums fit in the accumulator");
+static_assert(k2M * k2PB <= (int)F256Smem::WORKN, "the box columns fit in the work buffer");
+
+// 12-point DFT in registers by the prime-factor map (3 x 4, coprime, so no twiddles): input n = (4 n1 + 3 n2)
+// mod 12 enters the 3-point transform n2 at position n1, and output k = (4 k1 + 9 k2) mod 12 leaves the
+// 4-point transform k1 at position k2.
+template <bool INV>
+__device__ __forceinline__ void dft12(float2* a) {
+    float2 t[4][3];
+#pragma unroll
+    for (int n2 = 0; n2 < 4; ++n2) {
+#pragma unroll
+        for (int n1 = 0; n1 < 3; ++n1) t[n2][n1] = a[(4 * n1 + 3 * n2) % 12];
+        dft3<INV>(t[n2]);
+    }
+#pragma unroll
+    for (int k1 = 0; k1 < 3; ++k1) {
+        float2 h0 = t[0][k1], h1 = t[1][k1], h2 = t[2][k1], h3 = t[3][k1];
+        dft4<INV>(h0, h1, h2, h3);
+        a[(4 * k1) % 12] = h0;
+        a[(4 * k1 + 9) % 12] = h1;
+        a[(4 * k1 + 18) % 12] = h2;
+        a[(4 * k1 + 27) % 12] = h3;
+    }
+}
+
+// One thread: expect one row group's bytes on the mbarrier and start its two tensor copies (columns x0 .. x0 + 135
+// and x0 + 128 .. x0 + 263 of window rows n2, n2 + 4, ..., n2 + 252 of frame f).
+__device__ __forceinline__ void stage_group(const CUtensorMap* tmap, uint32_t dst, uint32_t mbar, int x0, int n2, int f) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar), "r"(2 * k2BoxBytes) : "memory");
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+        asm volatile(
+            "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], [%6];\n" ::"r"(
+                dst + h * k2BoxBytes),
+            "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x0 + 128 * h), "r"(n2), "r"(0), "r"(f), "r"(mbar)
+            : "memory");
+}
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity) {
+    return bounded_mbar_wait(mbar, parity, k2WaitLimit);
+}
+
+// Position of frequency k of a 256-point transform after two radix-16 DIF passes.
+__device__ __forceinline__ int pos256(int k) { return (k & 15) * 16 + (k >> 4); }
+
+__global__ void __launch_bounds__(k2NT, 1)
+    k_fused256(const __grid_constant__ Plan P, const __grid_constant__ F256Args A,
+               const __grid_constant__ CUtensorMap tmap0, const __grid_constant__ CUtensorMap tmap1) {
+    using L = F256Smem;
+    constexpr int N = k2N, M = k2M, NT = k2NT, MR0 = k2MR0, MR1 = k2MR1;
+    constexpr int QB = 4, BPQ = 2;   // partial-sum groups of the y contraction, row blocks per group
+    static_assert(M == MR0 * MR1 && MR0 == 8 && MR1 % 2 == 0, "mirrored-row y contraction: eight row blocks");
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ int abort_flag;
+    const uint16_t* stg = reinterpret_cast<const uint16_t*>(smem_raw);
+    float2* work = reinterpret_cast<float2*>(smem_raw + L::STG);
+    float2* acc = work + L::WORKN;
+    float2* twN = acc + L::ACCN;
+    float2* twM = twN + N;
+    float2* phx = twM + M;
+    float2* phy = phx + M;
+    float2* cx = phy + M;
+    float2* cy = cx + M;
+    float* hgx = reinterpret_cast<float*>(cy + M);   // u_m(x'_i) dx' at [m][i]
+    float* hgy = hgx + k2G * M;                      // u_n(y'_j) dy' at [j][n] (n fastest, k2G wide)
+    int* mlo = reinterpret_cast<int*>(hgy + k2G * M);
+    int* mhi = mlo + M;
+    int* mdm = mhi + M;
+    int* mdn = mdm + k2G * (k2G + 1) / 2;
+    float2* B = work;                                // box columns [c][n1] of the current group
+    float2* win = work;                              // window [x position][q] during the inverse
+    float2* part = acc;                              // y-contraction partial sums [QB][G][M] during the epilogue
+    const int tid = threadIdx.x;
+    const int pol = blockIdx.x % P.pols;
+    const PolDev& pd = P.pol[pol];
+    const CUtensorMap* tmap = pol == 0 ? &tmap0 : &tmap1;
+    const int G = P.groups, modes = P.modes;
+    const int klx = pd.klx, kly = pd.kly;
+    for (int i = tid; i < N; i += NT) twN[i] = P.tw_fwd_n[i];
+    for (int i = tid; i < M; i += NT) {
+        twM[i] = P.tw_inv_m[i];
+        phx[i] = pd.phase_x[i];
+        phy[i] = cscale(pd.phase_y[i], 0.5f);   // with the 1/2 of the real-spectra separation
+        cx[i] = pd.corr_x[i];
+        cy[i] = pd.corr_y[i];
+        mlo[i] = pd.mask_lo[i];
+        mhi[i] = pd.mask_hi[i];
+    }
+    for (int i = tid; i < G * M; i += NT) hgx[i] = pd.hg_x[i];
+    for (int i = tid; i < k2G * M; i += NT) {
+        const int j = i / k2G, n = i - j * k2G;
+        hgy[i] = n < G ? pd.hg_y[n * M + j] : 0.f;
+    }
+    for (int i = tid; i < modes; i += NT) {
+        mdm[i] = P.mode_m[i];
+        mdn[i] = P.mode_n[i];
+    }
+    const uint32_t mb = smem_u32(&mbar), dst = smem_u32(smem_raw);
+    const int fstride = gridDim.x / P.pols;
+    const int x0 = A.x0[pol], xo = A.xo[pol];
+    int b = blockIdx.x / P.pols;
+    if (tid == 0) {
+        abort_flag = 0;
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb));
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        if (b < A.count) stage_group(tmap, dst, mb, x0, 0, b);
+    }
+    __syncthreads();
+    uint32_t parity = 0;
+    bool aborted = false;
+    for (; b < A.count && !aborted; b += fstride) {
+        const int f = b;
+        for (int n2 = 0; n2 < 4; ++n2) {
+            if (!mbar_wait_bounded(mb, parity)) abort_flag = 1;
+            __syncthreads();
+            if (abort_flag) {
+                if (tid == 0 && P.status) atomicOr(P.status, 1);
+                aborted = true;
+                break;
+            }
+            parity ^= 1u;
+
+            // ------------------------------------------------------------ x pass 1: radix 16 from the staged rows
+            {
+                const int u = tid >> 4, j = tid & 15;
+                const uint16_t* ra = stg + u * k2BoxW + xo + j;                        // row n1 = u, box 0
+                const uint16_t* rb = ra + 32 * k2BoxW;                                 // row n1 = u + 32
+                const uint16_t* sa = ra + k2Rows * k2BoxW - 128;                       // box 1 (columns from 128)
+                const uint16_t* sb = rb + k2Rows * k2BoxW - 128;
+                float2 v[16];
+#pragma unroll
+                for (int r = 0; r < 8; ++r) v[r] = make_float2((float)ra[16 * r], (float)rb[16 * r]);
+#pragma unroll
+                for (int r = 8; r < 16; ++r) v[r] = make_float2((float)sa[16 * r], (float)sb[16 * r]);
+                if (pd.cal) {
+                    // reference calibration: window pixel (x, y) times sqrt(max cal / cal), from the L2-resident table
+                    const float* ka = pd.cal + (4 * u + n2) * N + j;
+                    const float* kb = pd.cal + (4 * (u + 32) + n2) * N + j;
+#pragma unroll
+                    for (int r = 0; r < 16; ++r) {
+                        v[r].x *= __ldg(ka + 16 * r);
+                        v[r].y *= __ldg(kb + 16 * r);
+                    }
+                }
+                dft16<false>(v);
+#pragma unroll
+                for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], twN[j * r]);
+#pragma unroll
+                for (int r = 0; r < 16; ++r) work[u * k2PW + j + 16 * r] = v[r];
+            }
+            // the staged rows have been read: order those reads before the next tensor copies into the buffer
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            __syncthreads();
+            if (tid == 0) {
+                if (n2 < 3)
+                    stage_group(tmap, dst, mb, x0, n2 + 1, f);
+                else if (b + fstride < A.count)
+                    stage_group(tmap, dst, mb, x0, 0, f + fstride);
+            }
+
+            // ------------------------------------------------------------ x pass 2: radix 16 in place
+            {
+                const int u = tid & 31, blk = tid >> 5;
+                float2 v[16];
+                float2* row = work + u * k2PW + 16 * blk;
+#pragma unroll
+                for (int r = 0; r < 16; ++r) v[r] = row[r];
+                dft16<false>(v);
+#pragma unroll
+                for (int r = 0; r < 16; ++r) row[r] = v[r];
+            }
+            __syncthreads();
+
+            // ------------------------------------------------------------ real-spectra separation on the box columns
+            {
+                // items (u, c): packed row u gives rows n1 = u (Z(k) + conj Z(-k)) and n1 = u + 32 (-i (Z(k) -
+                // conj Z(-k))) at box column c, frequency k = klx + c; read, barrier, then written over the rows
+                constexpr int IT = 32 * M / NT;
+                static_assert(32 * M % NT == 0, "whole items per thread");
+                float2 xa[IT], xb[IT];
+#pragma unroll
+                for (int k = 0; k < IT; ++k) {
+                    const int t = tid + k * NT, u = t & 31, c = t >> 5;
+                    const int kx = (klx + c) & (N - 1);
+                    const float2 zk = work[u * k2PW + pos256(kx)];
+                    const float2 zm = work[u * k2PW + pos256((N - kx) & (N - 1))];
+                    xa[k] = make_float2(zk.x + zm.x, zk.y - zm.y);
+                    xb[k] = make_float2(zk.y + zm.y, zm.x - zk.x);
+                }
+                __syncthreads();
+#pragma unroll
+                for (int k = 0; k < IT; ++k) {
+                    const int t = tid + k * NT, u = t & 31, c = t >> 5;
+                    B[c * k2PB + u] = xa[k];
+                    B[c * k2PB + u + 32] = xb[k];
+                }
+            }
+            __syncthreads();
+
+            // ------------------------------------------------------------ y pass 1: radix 16 over n1 (span 64)
+            if (tid < 4 * M) {
+                const int c = tid % M, j = tid / M;
+                float2* col = B + c * k2PB + j;
+                float2 v[16];
+#pragma unroll
+                for (int r = 0; r < 16; ++r) v[r] = col[4 * r];
+                dft16<false>(v);
+#pragma unroll
+                for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], twN[4 * j * r]);   // W_64^{j r}
+#pragma unroll
+                for (int r = 0; r < 16; ++r) col[4 * r] = v[r];
+            }
+            __syncthreads();
+
+            // ------------------------------------------------------------ y pass 2: radix 4, accumulate
+            for (int t = tid; t < 16 * M; t += NT) {
+                const int c = t % M, blk = t / M;
+                const float2* col = B + c * k2PB + 4 * blk;
+                float2 v0 = col[0], v1 = col[1], v2 = col[2], v3 = col[3];
+                dft4<false>(v0, v1, v2, v3);
+                const float2 vv[4] = {v0, v1, v2, v3};
+#pragma unroll
+                for (int r2 = 0; r2 < 4; ++r2) {
+                    const int k1 = blk + 16 * r2;           // output frequency mod 64
+                    const int q0 = (k1 - kly) & 63;         // box rows q with kly + q = k1 mod 64: q0, q0 + 64
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int q = q0 + 64 * h;
+                        if (q < M) {
+                            float2 a = cmul(vv[r2], twN[(n2 * (kly + q)) & (N - 1)]);
+                            if (n2 > 0) a = cadd(a, acc[c * k2PA + q]);
+                            if (n2 == 3)
+                                a = (c >= mlo[q] && c <= mhi[q]) ? cmul(cmul(a, phx[c]), phy[q]) : make_float2(0.f, 0.f);
+                            acc[c * k2PA + q] = a;
+                        }
+                    }
+                }
+            }
+            __syncthreads();
+        }
+        if (aborted) break;
+
+        // ---------------------------------------------------------------- inverse transforms
+        // x, first DIT pass (radix 12, span 12): window position blk MR1 + r holds box column blk + MR0 r
+        for (int t = tid; t < MR0 * M; t += NT) {
+            const int q = t % M, blk = t / M;
+            float2 v[MR1];
+#pragma unroll
+            for (int r = 0; r < MR1; ++r) v[r] = acc[(blk + MR0 * r) * k2PA + q];
+            dft12<true>(v);
+#pragma unroll
+            for (int r = 0; r < MR1; ++r) win[(blk * MR1 + r) * k2PA + q] = v[r];
+        }
+        __syncthreads();
+        spass<MR0, true, true, M, M, M, k2PA, 1, NT>(win, twM, tid);
+        __syncthreads();
+        spass<MR0, true, false, M, M, M, 1, k2PA, NT>(win, twM, tid);
+        __syncthreads();
+
+        // ---------------------------------------------------------------- last y pass, correction, field, y overlap
+        // The last DIF pass (span MR1, no twiddles) leaves output j = blk + MR0 r at position blk MR1 + r of column
+        // i; it is corrected in registers, written to the field (coalesced along i) and contracted with u_n(y'_j)
+        // into part[qb][n][i] over row blocks qb and MR0 - qb (block 0 with MR0 / 2), whose rows mirror each other
+        // (M - j): the even modes contract sums of mirrored rows, the odd ones differences.
+        const bool ov = A.coefs && G > 0;
+        {
+            float2* fld = A.fields ? A.fields + (size_t)(f * P.pols + pol) * M * M : nullptr;
+            for (int t = tid; t < M * QB; t += NT) {
+                const int i = t % M, qb = t / M;
+                const float2 ci = cx[i];
+                float2 v[BPQ][MR1];
+#pragma unroll
+                for (int bb = 0; bb < BPQ; ++bb) {
+                    const int blk = qb == 0 ? bb * (MR0 / 2) : (bb == 0 ? qb : MR0 - qb);
+#pragma unroll
+                    for (int r = 0; r < MR1; ++r) v[bb][r] = win[i * k2PA + blk * MR1 + r];
+                    dft12<true>(v[bb]);
+#pragma unroll
+                    for (int r = 0; r < MR1; ++r) {
+                        const int j = blk + MR0 * r;
+                        v[bb][r] = cmul(cmul(v[bb][r], ci), cy[j]);
+                        if (fld && DH_IN(P.status, (long long)j * M + i, (long long)M * M, kSiteFusedField)) fld[j * M + i] = v[bb][r];
+                    }
+                }
+                if (ov) {
+                    float2 sp[MR1 + 1], sm[MR1 + 1];
+                    int jr[MR1 + 1];
+                    if (qb == 0) {
+                        // block 0 (rows MR0 r) pairs r with MR1 - r; row 0 has no mirror and row M/2 is its own (odd
+                        // modes vanish there); block MR0/2 pairs r with MR1 - 1 - r
+                        int w = 0;
+#pragma unroll
+                        for (int r = 1; r < MR1 / 2; ++r, ++w) {
+                            sp[w] = cadd(v[0][r], v[0][MR1 - r]);
+                            sm[w] = csub(v[0][r], v[0][MR1 - r]);
+                            jr[w] = MR0 * r;
+                        }
+                        sp[w] = sm[w] = v[0][0];
+                        jr[w++] = 0;
+                        sp[w] = sm[w] = v[0][MR1 / 2];
+                        jr[w++] = M / 2;
+#pragma unroll
+                        for (int r = 0; r < MR1 / 2; ++r, ++w) {
+                            sp[w] = cadd(v[1][r], v[1][MR1 - 1 - r]);
+                            sm[w] = csub(v[1][r], v[1][MR1 - 1 - r]);
+                            jr[w] = MR0 / 2 + MR0 * r;
+                        }
+                    } else {
+                        // blocks qb and MR0 - qb: row qb + MR0 r mirrors row (MR0 - qb) + MR0 (MR1 - 1 - r)
+#pragma unroll
+                        for (int r = 0; r < MR1; ++r) {
+                            sp[r] = cadd(v[0][r], v[1][MR1 - 1 - r]);
+                            sm[r] = csub(v[0][r], v[1][MR1 - 1 - r]);
+                            jr[r] = qb + MR0 * r;
+                        }
+                        sp[MR1] = sm[MR1] = make_float2(0.f, 0.f);
+                        jr[MR1] = 0;
+                    }
+                    const int nu = qb == 0 ? MR1 + 1 : MR1;
+#pragma unroll
+                    for (int n4 = 0; n4 < k2G; n4 += 4) {
+                        if (n4 < G) {
+                            float2 a[4] = {make_float2(0.f, 0.f), make_float2(0.f, 0.f), make_float2(0.f, 0.f),
+                                           make_float2(0.f, 0.f)};
+#pragma unroll
+                            for (int w = 0; w < MR1 + 1; ++w) {
+                                if (w < nu) {
+                                    const float4 u = *reinterpret_cast<const float4*>(hgy + jr[w] * k2G + n4);
+                                    a[0].x = fmaf(u.x, sp[w].x, a[0].x);
+                                    a[0].y = fmaf(u.x, sp[w].y, a[0].y);
+                                    a[1].x = fmaf(u.y, sm[w].x, a[1].x);
+                                    a[1].y = fmaf(u.y, sm[w].y, a[1].y);
+                                    a[2].x = fmaf(u.z, sp[w].x, a[2].x);
+                                    a[2].y = fmaf(u.z, sp[w].y, a[2].y);
+                                    a[3].x = fmaf(u.w, sm[w].x, a[3].x);
+                                    a[3].y = fmaf(u.w, sm[w].y, a[3].y);
+                                }
+                            }
+#pragma unroll
+                            for (int c = 0; c < 4; ++c)
+                                if (n4 + c < G) part[(qb * G + n4 + c) * M + i] = a[c];
+                        }
+                    }
+                }
+            }
+        }
+        __syncthreads();
+
+        // ---------------------------------------------------------------- HG overlap, x contraction
+        if (ov) {
+            // c_mn = sum_i u_m(x'_i) T[n][i], T[n][i] = sum_qb part[qb][n][i] (groups added in a fixed order): eight
+            // threads per mode, thread s taking the column pairs i = 2s + 16h, then a fixed shuffle tree
+            float2* cf = A.coefs + (size_t)(f * P.pols + pol) * modes;
+            const int s8 = tid & 7;
+            for (int t0 = tid & ~31; t0 < modes * 8; t0 += NT) {
+                const int k = (t0 + (tid & 31)) >> 3;
+                float2 sum = make_float2(0.f, 0.f);
+                if (k < modes) {
+                    const float* um = hgx + mdm[k] * M;
+                    const float2* tn = part + mdn[k] * M;
+#pragma unroll
+                    for (int h = 0; h < M / 16; ++h) {
+                        const int i = 2 * s8 + 16 * h;
+                        const float2 u = *reinterpret_cast<const float2*>(um + i);
+                        float4 v = *reinterpret_cast<const float4*>(tn + i);
+#pragma unroll
+                        for (int q = 1; q < QB; ++q) {
+                            const float4 w = *reinterpret_cast<const float4*>(tn + q * G * M + i);
+                            v.x += w.x;
+                            v.y += w.y;
+                            v.z += w.z;
+                            v.w += w.w;
+                        }
+                        sum.x = fmaf(u.x, v.x, sum.x);
+                        sum.y = fmaf(u.x, v.y, sum.y);
+                        sum.x = fmaf(u.y, v.z, sum.x);
+                        sum.y = fmaf(u.y, v.w, sum.y);
+                    }
+                }
+#pragma unroll
+                for (int o = 1; o < 8; o <<= 1) {
+                    sum.x += __shfl_xor_sync(0xffffffffu, sum.x, o);
+                    sum.y += __shfl_xor_sync(0xffffffffu, sum.y, o);
+                }
+                if (s8 == 0 && k < modes && DH_IN(P.status, k, modes, kSiteFusedCoef)) cf[k] = sum;
+            }
+        }
+        __syncthreads();
+    }
+    // a tensor copy still in flight (only after an expired wait) must land before the block exits
+    if (aborted && tid == 0) mbar_wait_bounded(mb, parity);
+}
+
+}  // namespace dhk
+
+namespace dh {
+
+static int g_256_sms[64] = {0};
+static int g_256_bps[64] = {0};
+static PFN_cuTensorMapEncodeTiled_v12000 g_256_encode = nullptr;
+
+bool use_fused256(const dhk::Plan& P) {
+    return P.n == dhk::k2N && P.ny == dhk::k2N && P.m == dhk::k2M && P.my == dhk::k2M && P.groups <= dhk::k2G &&
+           P.pols <= 2 && P.precision == DH_PRECISION_FP32;
+}
+
+cudaError_t fused256_init() {
+    if (!g_256_encode) {
+        void* fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return e != cudaSuccess ? e : cudaErrorNotSupported;
+        g_256_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    }
+    return cudaFuncSetAttribute(dhk::k_fused256, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dhk::F256Smem::bytes);
+}
+
+int launch_fused256(Handle* H, const dhk::Plan& P, const void* frames, int dtype, int batch, void* fields, void* coefs,
+                    cudaStream_t st, dhk::StageTimer* tm) {
+    const int dev = H->device;
+    if (dev < 0 || dev >= 64) return fail(DH_ERROR_ERROR, "device index out of range");
+    if (batch < 1) return DH_SUCCESS;
+    if (dtype != DH_DTYPE_U16) return fail(DH_ERROR_INVALIDARGUMENT, "the 256 x 256 fused kernel reads uint16 frames");
+    if (!g_256_encode) return fail(DH_ERROR_ERROR, "tensor-map encoder unavailable");
+    if (!g_256_sms[dev]) {
+        int n = 0;
+        cudaError_t e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return cuda_fail(e, "device attribute");
+        g_256_sms[dev] = n;
+    }
+    if (!g_256_bps[dev]) {
+        int n = 0;
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, dhk::k_fused256, dhk::k2NT, dhk::F256Smem::bytes);
+        if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
+        g_256_bps[dev] = n > 0 ? n : 1;
+    }
+    // per polarisation, the window rows as a 4-D tensor [frame][n1 < 64][n2 < 4][x]: window row 4 n1 + n2 of frame
+    // f at (frames + f H W + (oy + 4 n1 + n2) W) (every row inside the frame); one box = 64 rows n1 of one group
+    // n2 by 136 columns
+    const size_t esz = 2;
+    CUtensorMap tmap[DH_MAX_POLS];
+    std::memset(tmap, 0, sizeof tmap);
+    for (int p = 0; p < P.pols; ++p) {
+        const cuuint64_t gdim[4] = {(cuuint64_t)P.width, 4, (cuuint64_t)dhk::k2Rows, (cuuint64_t)batch};
+        const cuuint64_t gstride[3] = {(cuuint64_t)P.width * esz, (cuuint64_t)P.width * esz * 4,
+                                       (cuuint64_t)P.width * P.height * esz};
+        const cuuint32_t box[4] = {(cuuint32_t)dhk::k2BoxW, 1, (cuuint32_t)dhk::k2Rows, 1};
+        const cuuint32_t estride[4] = {1, 1, 1, 1};
+        void* base = (unsigned char*)const_cast<void*>(frames) + (size_t)P.pol[p].oy * P.width * esz;
+        CUresult cr = g_256_encode(&tmap[p], CU_TENSOR_MAP_DATA_TYPE_UINT16, 4, base, gdim, gstride, box, estride,
+                                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                   CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (cr != CUDA_SUCCESS) return fail(DH_ERROR_CUDA, "cuTensorMapEncodeTiled failed (" + std::to_string((int)cr) + ")");
+    }
+    if (P.pols == 1) tmap[1] = tmap[0];
+    dhk::F256Args A;
+    std::memset(&A, 0, sizeof A);
+    A.count = batch;
+    for (int p = 0; p < P.pols; ++p) {
+        const int ox = P.pol[p].ox;               // window origins are >= 0
+        A.x0[p] = (ox / 8) * 8;                   // 16-byte aligned staging origin
+        A.xo[p] = ox - A.x0[p];
+    }
+    A.fields = (float2*)fields;
+    A.coefs = (float2*)coefs;
+    // a persistent grid of every resident block; each block serves one polarisation
+    const int resident = g_256_sms[dev] * g_256_bps[dev];
+    const long long per_pol = std::min<long long>(batch, std::max(1, resident / P.pols));
+    const int grid = (int)per_pol * P.pols;
+    if (tm) tm->start(st);
+    dhk::k_fused256<<<grid, dhk::k2NT, dhk::F256Smem::bytes, st>>>(P, A, tmap[0], tmap[1]);
+    if (tm) tm->stop(st, "k_fused256");
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "fused launch");
+    return DH_SUCCESS;
+}
+
+}  // namespace dh

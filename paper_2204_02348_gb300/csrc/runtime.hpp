@@ -100,14 +100,23 @@ int upload_plans(Handle* H, const std::vector<Geometry>& geos, const std::vector
 int run_split(const dhk::Plan& P, void* scratch, size_t scratch_bytes, const void* frames, int dtype, int batch,
               void* window, void* fields, void* coefs, cudaStream_t st, dhk::StageTimer* timer);
 
-// Fused single-kernel path for small windows (k_fused.cu).
+// Fused single-kernel path for 128 x 128 windows (k_fused.cu).
 bool use_fused(const dhk::Plan& P);
+// Fused single-kernel path for 256 x 256 windows with 96 x 96 fields, uint16 frames, FP32 overlap (k_fused256.cu).
+bool use_fused256(const dhk::Plan& P);
+cudaError_t fused256_init();
+int launch_fused256(Handle* H, const dhk::Plan& P, const void* frames, int dtype, int batch, void* fields, void* coefs,
+                    cudaStream_t st, dhk::StageTimer* timer);
 // The variant a call runs (dh_set_variant's rules; `aligned`: the frames suit tensor copies).
 int resolve_variant(const Handle* H, const dhk::Plan& P, bool aligned);
 // use_fused, unless the handle's variant resolves to the generic path.
 bool fused_allowed(const Handle* H, const dhk::Plan& P);
-// The fused kernel stages windows with tensor copies: the frames need a 16-byte aligned base and row pitch.
+// The fused kernels stage windows with tensor copies: the frames need a 16-byte aligned base and row pitch (and,
+// for the 256 x 256 kernel, uint16 pixels).  fused_layout_ok: the pitch and pixel rule alone (frames staged
+// 256-byte aligned by the library itself).
 bool fused_frames_ok(const dhk::Plan& P, const void* frames, int dtype);
+bool fused_layout_ok(const dhk::Plan& P, int dtype);
+// The variant rules and the fused paths' dispatch live in dispatch.cu.
 cudaError_t fused_init();
 int launch_fused_path(Handle* H, const dhk::Plan& P, const void* frames, int dtype, int batch, void* fields,
                       void* coefs, cudaStream_t st, dhk::StageTimer* timer);

@@ -408,7 +408,7 @@ int dh_server_submit(dh_server s, const dh_request* r, uint64_t* ticket) {
     const size_t coef = (r->h_coefs && P.modes) ? (size_t)P.pols * P.modes_out * 8 : 0;
     // the fused path needs no scratch; frames staged in the arena are 256-byte aligned, so only the row pitch
     // decides whether tensor copies apply
-    const bool fused = fused_allowed(H, P) && ((size_t)P.width * esz) % 16 == 0;
+    const bool fused = fused_allowed(H, P) && fused_layout_ok(P, r->dtype);
     const size_t scratch = (fused ? 0 : split_window_bytes(P) * P.pols) + (coef ? basis_scratch_bytes(P) : 0);
     const size_t per_frame = frame + field + coef + scratch;
     const size_t cap = std::max(s->budget / 2, per_frame);

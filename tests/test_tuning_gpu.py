@@ -93,7 +93,7 @@ def test_autotune_writes_cache_that_a_fresh_handle_reads(tmp_path):
     doc = json.load(open(path))
     assert doc["format"] == "digholo-gb300-tuning"
     ent = [e for e in doc["entries"] if e["key"] == key]
-    assert len(ent) == 1 and ent[0]["candidates"] == 12 and ent[0]["ms"] > 0
+    assert len(ent) == 1 and ent[0]["candidates"] == 13 and ent[0]["ms"] > 0
     assert {"variant": ent[0]["variant"], "chunk_mb": ent[0]["chunk_mb"], "radix": ent[0]["radix"]} == tun
     # a fresh handle loading the cache runs the same choice, with the same results to rounding
     import torch

@@ -32,9 +32,15 @@ def test_candidates_for_the_precision_geometry(handle):
     dh.configure(handle, syn.setup_precision())
     c = dh.dh_tuning_candidates(handle)
     plans = [[8, 4, 3], [3, 4, 8], [4, 8, 3], [16, 2, 3]]
-    expect = [{"variant": GENERIC, "chunk_mb": mb, "radix": p} for mb in (24, 48, 96) for p in plans]
+    # the 256 x 256 fused kernel first, then the generic path's chunk sizes and radix plans
+    expect = [{"variant": FUSED, "chunk_mb": 0, "radix": []}]
+    expect += [{"variant": GENERIC, "chunk_mb": mb, "radix": p} for mb in (24, 48, 96) for p in plans]
     assert c == expect
-    for x in c:
+    # the split-BF16 overlap has no fused kernel at this size
+    dh.dh_set_precision(handle, dh.DH_PRECISION_SPLIT_BF16)
+    assert all(x["variant"] == GENERIC for x in dh.dh_tuning_candidates(handle))
+    dh.dh_set_precision(handle, dh.DH_PRECISION_FP32)
+    for x in c[1:]:
         prod = 1
         for r in x["radix"]:
             prod *= r
