@@ -701,13 +701,19 @@ def precision_case(steps, dev):
         prof = dh.dh_get_profile(h)
         dh.dh_set_profiling(h, False)
         cc = c.cpu().numpy().astype(np.complex128)
+        # the generic three-kernel path held, for comparison with the default
+        variant = dh.dh_get_variant(h)
+        dh.dh_set_variant(h, dh.DH_VARIANT_GENERIC)
+        ms_g = _event_time(lambda: dh.dh_process_batch(h, fr, dh.DH_DTYPE_U16, B, f, c), steps, 3)
+        dh.dh_set_variant(h, dh.DH_VARIANT_AUTO)
         # the tuner's choice for this geometry, timed the same way after the default
         dh.dh_autotune(h, fr, dh.DH_DTYPE_U16, B, f, c, reps=3)
         tuning = dh.dh_get_tuning(h)
         ms_t = _event_time(lambda: dh.dh_process_batch(h, fr, dh.DH_DTYPE_U16, B, f, c), steps, 3)
         fps = B / (ms / 1e3)
         bpf, fpf = bytes_per_frame(s, m, modes), flops_per_frame(s, m, modes)
-        res[name] = {"frames_per_s": fps, "ms_per_batch": ms,
+        res[name] = {"frames_per_s": fps, "ms_per_batch": ms, "variant": variant,
+                     "generic": {"frames_per_s": B / (ms_g / 1e3), "ms_per_batch": ms_g},
                      "tuned": {"tuning": tuning, "frames_per_s": B / (ms_t / 1e3), "ms_per_batch": ms_t},
                      "hbm_frac": fps * bpf / 1e9 / peak, "alu_frac": fps * fpf / 1e12 / fpk,
                      "bytes_per_frame": bpf, "flops_per_frame": fpf,

@@ -65,15 +65,15 @@ struct F256Smem {
     static constexpr size_t STG = 2 * (size_t)k2BoxBytes;                                    // two boxes
     static constexpr size_t WORKN = (32 * k2PW > k2M * k2PA) ? 32 * k2PW : k2M * k2PA;       // float2
     static constexpr size_t ACCN = (size_t)k2M * k2PA;                                       // float2
-    static constexpr size_t TABN = k2N + 5 * k2M;                                            // float2
+    static constexpr size_t TABN = 2 * k2N + 5 * k2M;                                        // float2
     static constexpr size_t HGN = 2 * (size_t)k2G * k2M;                                     // float
     static constexpr size_t INTN = 2 * k2M + 2 * (k2G * (k2G + 1) / 2);                      // int
     static constexpr size_t bytes = STG + (WORKN + ACCN + TABN) * 8 + HGN * 4 + INTN * 4;
 };
 static_assert(F256Smem::STG % 16 == 0 && (F256Smem::WORKN * 8) % 16 == 0 && (F256Smem::ACCN * 8) % 16 == 0,
               "16-byte aligned regions");
-static_assert(4 * k2G * k2M <= (int)F256Smem::ACCN, "the partial sums fit in the accumulator");
-static_assert(k2M * k2PB <= (int)F256Smem::WORKN, "the box columns fit in the work buffer");
+static_assert(4 * k2G * k2M <= (int)F256Smem::WORKN, "the partial sums fit in the work buffer");
+static_assert(k2M * k2PB <= (int)F256Smem::ACCN, "the box columns fit in the second buffer");
 
 // 12-point DFT in registers by the prime-factor map (3 x 4, coprime, so no twiddles): input n = (4 n1 + 3 n2)
 // mod 12 enters the 3-point transform n2 at position n1, and output k = (4 k1 + 9 k2) mod 12 leaves the
@@ -130,9 +130,10 @@ __global__ void __launch_bounds__(k2NT, 1)
     __shared__ int abort_flag;
     const uint16_t* stg = reinterpret_cast<const uint16_t*>(smem_raw);
     float2* work = reinterpret_cast<float2*>(smem_raw + L::STG);
-    float2* acc = work + L::WORKN;
-    float2* twN = acc + L::ACCN;
-    float2* twM = twN + N;
+    float2* buf2 = work + L::WORKN;
+    float2* twN = buf2 + L::ACCN;
+    float2* tw16 = twN + N;                          // W_256^{j r} at [r][j]: the first x pass's twiddles
+    float2* twM = tw16 + N;
     float2* phx = twM + M;
     float2* phy = phx + M;
     float2* cx = phy + M;
@@ -143,16 +144,20 @@ __global__ void __launch_bounds__(k2NT, 1)
     int* mhi = mlo + M;
     int* mdm = mhi + M;
     int* mdn = mdm + k2G * (k2G + 1) / 2;
-    float2* B = work;                                // box columns [c][n1] of the current group
-    float2* win = work;                              // window [x position][q] during the inverse
-    float2* part = acc;                              // y-contraction partial sums [QB][G][M] during the epilogue
+    float2* B = buf2;                                // box columns [c][n1] of the current group
+    float2* acc = work;                              // the window spectrum [c][q] after the last group
+    float2* win = buf2;                              // window [x position][q] during the inverse
+    float2* part = work;                             // y-contraction partial sums [QB][G][M] during the epilogue
     const int tid = threadIdx.x;
     const int pol = blockIdx.x % P.pols;
     const PolDev& pd = P.pol[pol];
     const CUtensorMap* tmap = pol == 0 ? &tmap0 : &tmap1;
     const int G = P.groups, modes = P.modes;
     const int klx = pd.klx, kly = pd.kly;
-    for (int i = tid; i < N; i += NT) twN[i] = P.tw_fwd_n[i];
+    for (int i = tid; i < N; i += NT) {
+        twN[i] = P.tw_fwd_n[i];
+        tw16[i] = P.tw_fwd_n[((i >> 4) * (i & 15)) & (N - 1)];
+    }
     for (int i = tid; i < M; i += NT) {
         twM[i] = P.tw_inv_m[i];
         phx[i] = pd.phase_x[i];
@@ -184,8 +189,15 @@ __global__ void __launch_bounds__(k2NT, 1)
     __syncthreads();
     uint32_t parity = 0;
     bool aborted = false;
+    // the second y pass: task k of this thread is box column c = t mod M, block blk = t / M of t = tid + k NT; its
+    // outputs k1 = blk + 16 r2 (r2 < 4) feed the box rows q with kly + q = k1 mod 64.  With (blk - kly) mod 64 =
+    // s + 16 tr (s < 16), those are the six rows q = s + 16 m (m < 6), row m fed by output r2 = (m - tr) mod 4;
+    // their sums over the four groups stay in registers
+    constexpr int YT = 16 * M / NT;
+    static_assert(16 * M % NT == 0 && M == 96, "whole second-pass tasks per thread; six rows per task");
     for (; b < A.count && !aborted; b += fstride) {
         const int f = b;
+        float2 ya[YT][6];
         for (int n2 = 0; n2 < 4; ++n2) {
             if (!mbar_wait_bounded(mb, parity)) abort_flag = 1;
             __syncthreads();
@@ -198,7 +210,9 @@ __global__ void __launch_bounds__(k2NT, 1)
 
             // ------------------------------------------------------------ x pass 1: radix 16 from the staged rows
             {
-                const int u = tid >> 4, j = tid & 15;
+                // the two half-warps take rows u and u + 2 (their staged rows 8 banks apart)
+                const int w = tid >> 5, j = tid & 15;
+                const int u = 4 * (w >> 1) + (w & 1) + 2 * ((tid >> 4) & 1);
                 const uint16_t* ra = stg + u * k2BoxW + xo + j;                        // row n1 = u, box 0
                 const uint16_t* rb = ra + 32 * k2BoxW;                                 // row n1 = u + 32
                 const uint16_t* sa = ra + k2Rows * k2BoxW - 128;                       // box 1 (columns from 128)
@@ -220,7 +234,7 @@ __global__ void __launch_bounds__(k2NT, 1)
                 }
                 dft16<false>(v);
 #pragma unroll
-                for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], twN[j * r]);
+                for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], tw16[r * 16 + j]);
 #pragma unroll
                 for (int r = 0; r < 16; ++r) work[u * k2PW + j + 16 * r] = v[r];
             }
@@ -248,28 +262,15 @@ __global__ void __launch_bounds__(k2NT, 1)
             __syncthreads();
 
             // ------------------------------------------------------------ real-spectra separation on the box columns
-            {
-                // items (u, c): packed row u gives rows n1 = u (Z(k) + conj Z(-k)) and n1 = u + 32 (-i (Z(k) -
-                // conj Z(-k))) at box column c, frequency k = klx + c; read, barrier, then written over the rows
-                constexpr int IT = 32 * M / NT;
-                static_assert(32 * M % NT == 0, "whole items per thread");
-                float2 xa[IT], xb[IT];
-#pragma unroll
-                for (int k = 0; k < IT; ++k) {
-                    const int t = tid + k * NT, u = t & 31, c = t >> 5;
-                    const int kx = (klx + c) & (N - 1);
-                    const float2 zk = work[u * k2PW + pos256(kx)];
-                    const float2 zm = work[u * k2PW + pos256((N - kx) & (N - 1))];
-                    xa[k] = make_float2(zk.x + zm.x, zk.y - zm.y);
-                    xb[k] = make_float2(zk.y + zm.y, zm.x - zk.x);
-                }
-                __syncthreads();
-#pragma unroll
-                for (int k = 0; k < IT; ++k) {
-                    const int t = tid + k * NT, u = t & 31, c = t >> 5;
-                    B[c * k2PB + u] = xa[k];
-                    B[c * k2PB + u + 32] = xb[k];
-                }
+            // items (u, c): packed row u gives rows n1 = u (Z(k) + conj Z(-k)) and n1 = u + 32 (-i (Z(k) -
+            // conj Z(-k))) at box column c, frequency k = klx + c
+            for (int t = tid; t < 32 * M; t += NT) {
+                const int u = t & 31, c = t >> 5;
+                const int kx = (klx + c) & (N - 1);
+                const float2 zk = work[u * k2PW + pos256(kx)];
+                const float2 zm = work[u * k2PW + pos256((N - kx) & (N - 1))];
+                B[c * k2PB + u] = make_float2(zk.x + zm.x, zk.y - zm.y);
+                B[c * k2PB + u + 32] = make_float2(zk.y + zm.y, zm.x - zk.x);
             }
             __syncthreads();
 
@@ -289,32 +290,43 @@ __global__ void __launch_bounds__(k2NT, 1)
             __syncthreads();
 
             // ------------------------------------------------------------ y pass 2: radix 4, accumulate
-            for (int t = tid; t < 16 * M; t += NT) {
-                const int c = t % M, blk = t / M;
+#pragma unroll
+            for (int k = 0; k < YT; ++k) {
+                const int blk = (tid + k * NT) / M, c = (tid + k * NT) % M;
+                const int tr = ((blk - kly) & 63) >> 4, qs = (blk - kly) & 15;
                 const float2* col = B + c * k2PB + 4 * blk;
                 float2 v0 = col[0], v1 = col[1], v2 = col[2], v3 = col[3];
                 dft4<false>(v0, v1, v2, v3);
-                const float2 vv[4] = {v0, v1, v2, v3};
+                // rotate by tr: o[m mod 4] = output (m - tr) mod 4
+                const float2 o0 = tr == 0 ? v0 : tr == 1 ? v3 : tr == 2 ? v2 : v1;
+                const float2 o1 = tr == 0 ? v1 : tr == 1 ? v0 : tr == 2 ? v3 : v2;
+                const float2 o2 = tr == 0 ? v2 : tr == 1 ? v1 : tr == 2 ? v0 : v3;
+                const float2 o3 = tr == 0 ? v3 : tr == 1 ? v2 : tr == 2 ? v1 : v0;
+                const float2 o[4] = {o0, o1, o2, o3};
 #pragma unroll
-                for (int r2 = 0; r2 < 4; ++r2) {
-                    const int k1 = blk + 16 * r2;           // output frequency mod 64
-                    const int q0 = (k1 - kly) & 63;         // box rows q with kly + q = k1 mod 64: q0, q0 + 64
-#pragma unroll
-                    for (int h = 0; h < 2; ++h) {
-                        const int q = q0 + 64 * h;
-                        if (q < M) {
-                            float2 a = cmul(vv[r2], twN[(n2 * (kly + q)) & (N - 1)]);
-                            if (n2 > 0) a = cadd(a, acc[c * k2PA + q]);
-                            if (n2 == 3)
-                                a = (c >= mlo[q] && c <= mhi[q]) ? cmul(cmul(a, phx[c]), phy[q]) : make_float2(0.f, 0.f);
-                            acc[c * k2PA + q] = a;
-                        }
-                    }
+                for (int m = 0; m < 6; ++m) {
+                    if (n2 == 0)
+                        ya[k][m] = o[m & 3];
+                    else
+                        ya[k][m] = cadd(ya[k][m], cmul(o[m & 3], twN[(n2 * (kly + qs + 16 * m)) & (N - 1)]));
                 }
             }
-            __syncthreads();
+            // (the next group's wait ends in a barrier before anything here is overwritten)
         }
         if (aborted) break;
+        // the window: the circular mask and the beam-centre phase on the summed spectrum, written [c][q]
+#pragma unroll
+        for (int k = 0; k < YT; ++k) {
+            const int blk = (tid + k * NT) / M, c = (tid + k * NT) % M;
+            const int qs = (blk - kly) & 15;
+            const float2 px = phx[c];
+#pragma unroll
+            for (int m = 0; m < 6; ++m) {
+                const int q = qs + 16 * m;
+                acc[c * k2PA + q] = (c >= mlo[q] && c <= mhi[q]) ? cmul(cmul(ya[k][m], px), phy[q]) : make_float2(0.f, 0.f);
+            }
+        }
+        __syncthreads();
 
         // ---------------------------------------------------------------- inverse transforms
         // x, first DIT pass (radix 12, span 12): window position blk MR1 + r holds box column blk + MR0 r
@@ -421,11 +433,21 @@ __global__ void __launch_bounds__(k2NT, 1)
             }
         }
         __syncthreads();
+        if (ov) {
+            // T[n][i] = sum_qb part[qb][n][i] (groups added in a fixed order), in place of group 0
+            for (int t = tid; t < G * M; t += NT) {
+                float2 s = part[t];
+#pragma unroll
+                for (int q = 1; q < QB; ++q) s = cadd(s, part[q * G * M + t]);
+                part[t] = s;
+            }
+        }
+        __syncthreads();
 
         // ---------------------------------------------------------------- HG overlap, x contraction
         if (ov) {
-            // c_mn = sum_i u_m(x'_i) T[n][i], T[n][i] = sum_qb part[qb][n][i] (groups added in a fixed order): eight
-            // threads per mode, thread s taking the column pairs i = 2s + 16h, then a fixed shuffle tree
+            // c_mn = sum_i u_m(x'_i) T[n][i]: eight threads per mode, thread s taking the column pairs i = 2s + 16h,
+            // then a fixed shuffle tree
             float2* cf = A.coefs + (size_t)(f * P.pols + pol) * modes;
             const int s8 = tid & 7;
             for (int t0 = tid & ~31; t0 < modes * 8; t0 += NT) {
@@ -438,15 +460,7 @@ __global__ void __launch_bounds__(k2NT, 1)
                     for (int h = 0; h < M / 16; ++h) {
                         const int i = 2 * s8 + 16 * h;
                         const float2 u = *reinterpret_cast<const float2*>(um + i);
-                        float4 v = *reinterpret_cast<const float4*>(tn + i);
-#pragma unroll
-                        for (int q = 1; q < QB; ++q) {
-                            const float4 w = *reinterpret_cast<const float4*>(tn + q * G * M + i);
-                            v.x += w.x;
-                            v.y += w.y;
-                            v.z += w.z;
-                            v.w += w.w;
-                        }
+                        const float4 v = *reinterpret_cast<const float4*>(tn + i);
                         sum.x = fmaf(u.x, v.x, sum.x);
                         sum.y = fmaf(u.x, v.y, sum.y);
                         sum.x = fmaf(u.y, v.z, sum.x);
