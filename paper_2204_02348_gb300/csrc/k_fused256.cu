@@ -65,9 +65,9 @@ struct F256Smem {
     static constexpr size_t STG = 2 * (size_t)k2BoxBytes;                                    // two boxes
     static constexpr size_t WORKN = (32 * k2PW > k2M * k2PA) ? 32 * k2PW : k2M * k2PA;       // float2
     static constexpr size_t ACCN = (size_t)k2M * k2PA;                                       // float2
-    static constexpr size_t TABN = 2 * k2N + 5 * k2M;                                        // float2
+    static constexpr size_t TABN = 2 * k2N + 5 * k2M + 4 * k2M + 64;                         // float2
     static constexpr size_t HGN = 2 * (size_t)k2G * k2M;                                     // float
-    static constexpr size_t INTN = 2 * k2M + 2 * (k2G * (k2G + 1) / 2);                      // int
+    static constexpr size_t INTN = 4 * k2M + 2 * (k2G * (k2G + 1) / 2);                      // int
     static constexpr size_t bytes = STG + (WORKN + ACCN + TABN) * 8 + HGN * 4 + INTN * 4;
 };
 static_assert(F256Smem::STG % 16 == 0 && (F256Smem::WORKN * 8) % 16 == 0 && (F256Smem::ACCN * 8) % 16 == 0,
@@ -138,12 +138,15 @@ __global__ void __launch_bounds__(k2NT, 1)
     float2* phy = phx + M;
     float2* cx = phy + M;
     float2* cy = cx + M;
-    float* hgx = reinterpret_cast<float*>(cy + M);   // u_m(x'_i) dx' at [m][i]
+    float2* twq = cy + M;                            // W_256^{n2 (kly + q)} at [n2][q]: the group sums' twiddles
+    float2* ty1 = twq + 4 * M;                       // the first y pass's twiddles at [j][r] (see there)
+    float* hgx = reinterpret_cast<float*>(ty1 + 64); // u_m(x'_i) dx' at [m][i]
     float* hgy = hgx + k2G * M;                      // u_n(y'_j) dy' at [j][n] (n fastest, k2G wide)
     int* mlo = reinterpret_cast<int*>(hgy + k2G * M);
     int* mhi = mlo + M;
     int* mdm = mhi + M;
     int* mdn = mdm + k2G * (k2G + 1) / 2;
+    int2* zp = reinterpret_cast<int2*>(mdn + k2G * (k2G + 1) / 2);   // positions of Z(k), Z(-k) per box column
     float2* B = buf2;                                // box columns [c][n1] of the current group
     float2* acc = work;                              // the window spectrum [c][q] after the last group
     float2* win = buf2;                              // window [x position][q] during the inverse
@@ -166,6 +169,16 @@ __global__ void __launch_bounds__(k2NT, 1)
         cy[i] = pd.corr_y[i];
         mlo[i] = pd.mask_lo[i];
         mhi[i] = pd.mask_hi[i];
+        const int kx = (klx + i) & (N - 1);
+        zp[i] = make_int2(pos256(kx), pos256((N - kx) & (N - 1)));
+    }
+    for (int i = tid; i < 4 * M; i += NT) twq[i] = P.tw_fwd_n[((i / M) * (kly + i % M)) & (N - 1)];
+    for (int i = tid; i < 64; i += NT) {
+        // output r of first-pass task j is input j of second-pass block r; its twiddle W_64^{j r} carries the factor
+        // W_4^{-j tr(r)} that rotates that block's four outputs by tr(r) = ((r - kly) mod 64) / 16 (see the second
+        // pass)
+        const int j = i >> 4, r = i & 15, tr = ((r - kly) & 63) >> 4;
+        ty1[i] = P.tw_fwd_n[(4 * j * r - 64 * j * tr) & (N - 1)];
     }
     for (int i = tid; i < G * M; i += NT) hgx[i] = pd.hg_x[i];
     for (int i = tid; i < k2G * M; i += NT) {
@@ -192,7 +205,8 @@ __global__ void __launch_bounds__(k2NT, 1)
     // the second y pass: task k of this thread is box column c = t mod M, block blk = t / M of t = tid + k NT; its
     // outputs k1 = blk + 16 r2 (r2 < 4) feed the box rows q with kly + q = k1 mod 64.  With (blk - kly) mod 64 =
     // s + 16 tr (s < 16), those are the six rows q = s + 16 m (m < 6), row m fed by output r2 = (m - tr) mod 4;
-    // their sums over the four groups stay in registers
+    // the first pass's twiddles rotate each block's outputs by tr, so output m mod 4 feeds row m.  The rows' sums
+    // over the four groups stay in registers
     constexpr int YT = 16 * M / NT;
     static_assert(16 * M % NT == 0 && M == 96, "whole second-pass tasks per thread; six rows per task");
     for (; b < A.count && !aborted; b += fstride) {
@@ -266,9 +280,9 @@ __global__ void __launch_bounds__(k2NT, 1)
             // conj Z(-k))) at box column c, frequency k = klx + c
             for (int t = tid; t < 32 * M; t += NT) {
                 const int u = t & 31, c = t >> 5;
-                const int kx = (klx + c) & (N - 1);
-                const float2 zk = work[u * k2PW + pos256(kx)];
-                const float2 zm = work[u * k2PW + pos256((N - kx) & (N - 1))];
+                const int2 z = zp[c];
+                const float2 zk = work[u * k2PW + z.x];
+                const float2 zm = work[u * k2PW + z.y];
                 B[c * k2PB + u] = make_float2(zk.x + zm.x, zk.y - zm.y);
                 B[c * k2PB + u + 32] = make_float2(zk.y + zm.y, zm.x - zk.x);
             }
@@ -283,7 +297,7 @@ __global__ void __launch_bounds__(k2NT, 1)
                 for (int r = 0; r < 16; ++r) v[r] = col[4 * r];
                 dft16<false>(v);
 #pragma unroll
-                for (int r = 1; r < 16; ++r) v[r] = cmul(v[r], twN[4 * j * r]);   // W_64^{j r}
+                for (int r = 0; r < 16; ++r) v[r] = cmul(v[r], ty1[j * 16 + r]);   // W_64^{j r} W_4^{-j tr(r)}
 #pragma unroll
                 for (int r = 0; r < 16; ++r) col[4 * r] = v[r];
             }
@@ -293,22 +307,18 @@ __global__ void __launch_bounds__(k2NT, 1)
 #pragma unroll
             for (int k = 0; k < YT; ++k) {
                 const int blk = (tid + k * NT) / M, c = (tid + k * NT) % M;
-                const int tr = ((blk - kly) & 63) >> 4, qs = (blk - kly) & 15;
+                const int qs = (blk - kly) & 15;
                 const float2* col = B + c * k2PB + 4 * blk;
-                float2 v0 = col[0], v1 = col[1], v2 = col[2], v3 = col[3];
-                dft4<false>(v0, v1, v2, v3);
-                // rotate by tr: o[m mod 4] = output (m - tr) mod 4
-                const float2 o0 = tr == 0 ? v0 : tr == 1 ? v3 : tr == 2 ? v2 : v1;
-                const float2 o1 = tr == 0 ? v1 : tr == 1 ? v0 : tr == 2 ? v3 : v2;
-                const float2 o2 = tr == 0 ? v2 : tr == 1 ? v1 : tr == 2 ? v0 : v3;
-                const float2 o3 = tr == 0 ? v3 : tr == 1 ? v2 : tr == 2 ? v1 : v0;
-                const float2 o[4] = {o0, o1, o2, o3};
+                // the inputs carry W_4^{-n tr}, so output m is the one of frequency k1 = blk + 16 ((m - tr) mod 4)
+                float2 o[4] = {col[0], col[1], col[2], col[3]};
+                dft4<false>(o[0], o[1], o[2], o[3]);
+                const float2* tq = twq + n2 * M + qs;
 #pragma unroll
                 for (int m = 0; m < 6; ++m) {
                     if (n2 == 0)
                         ya[k][m] = o[m & 3];
                     else
-                        ya[k][m] = cadd(ya[k][m], cmul(o[m & 3], twN[(n2 * (kly + qs + 16 * m)) & (N - 1)]));
+                        ya[k][m] = cadd(ya[k][m], cmul(o[m & 3], tq[16 * m]));
                 }
             }
             // (the next group's wait ends in a barrier before anything here is overwritten)
