@@ -252,8 +252,9 @@ __global__ void __launch_bounds__(k2NT, 1)
 #pragma unroll
                 for (int r = 0; r < 16; ++r) work[u * k2PW + j + 16 * r] = v[r];
             }
-            // the staged rows have been read: order those reads before the next tensor copies into the buffer
-            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            // the staged rows have been read (into registers) by every thread once the barrier completes; the next
+            // tensor copies into the buffer are issued after it (a read-before-write across the proxies, ordered by
+            // the barrier alone, as tensor-copy pipelines release a consumed stage)
             __syncthreads();
             if (tid == 0) {
                 if (n2 < 3)
