@@ -266,8 +266,9 @@ __global__ void __launch_bounds__(FusedShape<M, T>::NT, FusedShape<M, T>::MINB)
 #pragma unroll
             for (int r = 0; r < 16; ++r) buf[(j + 8 * r) * 64 + c] = v[r];
         }
-        // the staged window has been read: order those reads before the next tensor copy into the buffer
-        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        // the staged window has been read (into registers) by every thread once the barrier completes; the next
+        // tensor copy into the buffer is issued after it (a read-before-write across the proxies, ordered by the
+        // barrier alone, as tensor-copy pipelines release a consumed stage)
         __syncthreads();
         if (tid == 0 && b + fstride < A.count) stage_window(&tmap, dst, mb, A.x0[pol], pd.oy, f + fstride, S::BYTES);
         {
