@@ -148,6 +148,7 @@ def measured_peak():
 
 # source file of each timed kernel; its hash also covers the device headers every kernel includes
 KERNEL_SOURCES = {"k_fused128": "k_fused.cu", "k_fused128p": ("k_fused_pr.cu", "fused_pr.hpp"), "k_fused128g": "k_fused_g.cu",
+                  "k_fused256": "k_fused256.cu",
                   "k_yinv_tc": "k_overlap_tc.cu", "k_ypass": "k_split.cu", "k_xpass": "k_split.cu", "k_yinv": "k_split.cu"}
 DEVICE_HEADERS = ("fft.cuh", "kernels.cuh", "sync.cuh", "umma.cuh", "check.cuh")
 
@@ -726,7 +727,11 @@ def precision_case(steps, dev):
         ms_t = _event_time(lambda: dh.dh_process_batch(h, fr, dh.DH_DTYPE_U16, B, f, c), steps, 3)
         fps = B / (ms / 1e3)
         bpf, fpf = bytes_per_frame(s, m, modes), flops_per_frame(s, m, modes)
+        # DRAM traffic of a single-kernel step from the committed capture (null for other kernel sources)
+        tr = recorded_traffic(next(iter(prof)), B) if len(prof) == 1 else None
         res[name] = {"frames_per_s": fps, "ms_per_batch": ms, "variant": variant,
+                     "traffic_per_frame": None if tr is None else tr / B,
+                     "traffic_over_algorithmic": None if tr is None else tr / B / bpf,
                      "generic": {"frames_per_s": B / (ms_g / 1e3), "ms_per_batch": ms_g},
                      "tuned": {"tuning": tuning, "frames_per_s": B / (ms_t / 1e3), "ms_per_batch": ms_t},
                      "hbm_frac": fps * bpf / 1e9 / peak, "alu_frac": fps * fpf / 1e12 / fpk,
