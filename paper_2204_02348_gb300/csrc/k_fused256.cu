@@ -21,7 +21,11 @@
 //               along y (DIF);
 //   epilogue    the last y pass in registers with the residual tilt and defocus removal, the field write and the
 //               separable HG contraction (mirrored row pairs, then eight threads per mode along x), as the
-//               128 x 128 kernel does.
+//               128 x 128 kernel does.  Split-BF16 variant (TC): the corrected field is written as the bf16 hi / lo
+//               A operand (192 rows: real, then imaginary parts of the 96 columns; K = the 96 field rows in the
+//               order the last pass leaves them) of two 128 x 16 x 96 tcgen05 contractions over y (three products
+//               per K step, FP32 accumulation in 32 tensor-memory columns, issued by one thread and awaited on an
+//               mbarrier with a bounded wait), read back by four warps and contracted along x.
 // Shared memory: staging of one row group (34.8 KB, refilled by the next group's tensor copies while the current
 // group is transformed), one work buffer (the packed x rows, then the box columns, then the window during the
 // inverse), the accumulator (then the partial sums of the y contraction) and the tables: 199 KB, one block per SM.
@@ -34,9 +38,12 @@
 #include <cstring>
 #include <string>
 
+#include <cuda_bf16.h>
+
 #include "fft.cuh"
 #include "runtime.hpp"
 #include "sync.cuh"
+#include "umma.cuh"
 
 namespace dhk {
 
@@ -115,9 +122,32 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity
     return bounded_mbar_wait(mbar, parity, k2WaitLimit);
 }
 
+// bf16 bits (round to nearest even) of a and b packed low / high, and of their remainders a - hi(a), b - hi(b).
+__device__ __forceinline__ void split_pair(float a, float b, uint32_t& hi, uint32_t& lo) {
+    const __nv_bfloat16 ha = __float2bfloat16_rn(a), hb = __float2bfloat16_rn(b);
+    const __nv_bfloat16 la = __float2bfloat16_rn(a - __bfloat162float(ha));
+    const __nv_bfloat16 lb = __float2bfloat16_rn(b - __bfloat162float(hb));
+    hi = (uint32_t)__bfloat16_as_ushort(ha) | ((uint32_t)__bfloat16_as_ushort(hb) << 16);
+    lo = (uint32_t)__bfloat16_as_ushort(la) | ((uint32_t)__bfloat16_as_ushort(lb) << 16);
+}
+
+// Twelve bf16 values (six packed pairs) at K positions kb .. kb + 11 of one row of a canonical K-major operand with
+// K = 96 (kb a multiple of 4): one 16-byte and one 8-byte store.
+__device__ __forceinline__ void store_run12(__nv_bfloat16* op, int row, int kb, const uint32_t* w) {
+    if ((kb & 7) == 0) {
+        *reinterpret_cast<uint4*>(op + umma_off(row, kb, k2M)) = make_uint4(w[0], w[1], w[2], w[3]);
+        *reinterpret_cast<uint2*>(op + umma_off(row, kb + 8, k2M)) = make_uint2(w[4], w[5]);
+    } else {
+        *reinterpret_cast<uint2*>(op + umma_off(row, kb, k2M)) = make_uint2(w[0], w[1]);
+        *reinterpret_cast<uint4*>(op + umma_off(row, kb + 4, k2M)) = make_uint4(w[2], w[3], w[4], w[5]);
+    }
+}
+
 // Position of frequency k of a 256-point transform after two radix-16 DIF passes.
 __device__ __forceinline__ int pos256(int k) { return (k & 15) * 16 + (k >> 4); }
 
+// TC: the y contraction in split-BF16 on the tensor cores (the split-BF16 precision).
+template <bool TC>
 __global__ void __launch_bounds__(k2NT, 1)
     k_fused256(const __grid_constant__ Plan P, const __grid_constant__ F256Args A,
                const __grid_constant__ CUtensorMap tmap0, const __grid_constant__ CUtensorMap tmap1) {
@@ -125,8 +155,17 @@ __global__ void __launch_bounds__(k2NT, 1)
     constexpr int N = k2N, M = k2M, NT = k2NT, MR0 = k2MR0, MR1 = k2MR1;
     constexpr int QB = 4, BPQ = 2;   // partial-sum groups of the y contraction, row blocks per group
     static_assert(M == MR0 * MR1 && MR0 == 8 && MR1 % 2 == 0, "mirrored-row y contraction: eight row blocks");
+    // TC: A = [2M rows][K = M] bf16 hi, then lo, over the work buffer; K position kappa = MR1 blk + r holds field row
+    // j = blk + MR0 r.  The second 128-row tile (rows 128 .. 255) reads 64 rows past the 2M written ones: they only
+    // feed accumulator rows 192 .. 255, which nothing reads, and stay inside the block's shared memory.
+    static_assert(4 * M * M * 2 <= (int)L::WORKN * 8, "the A operand's two planes fit in the work buffer");
+    static_assert(L::STG + 4 * M * M + 256 * M * 2 <= L::bytes, "the second tile's reads stay in shared memory");
+    constexpr uint32_t kTcCols = 32;
+    constexpr int kTsPitch = 2 * M + 1;   // TC: T[n][r] read back from tensor memory, r < M real, r >= M imaginary
     extern __shared__ __align__(128) unsigned char smem_raw[];
     __shared__ __align__(8) uint64_t mbar;
+    __shared__ __align__(8) uint64_t mbar_mma;   // TC: completion of the window's MMAs
+    __shared__ uint32_t tmem_slot;               // TC: tensor-memory address
     __shared__ int abort_flag;
     const uint16_t* stg = reinterpret_cast<const uint16_t*>(smem_raw);
     float2* work = reinterpret_cast<float2*>(smem_raw + L::STG);
@@ -141,7 +180,7 @@ __global__ void __launch_bounds__(k2NT, 1)
     float2* twq = cy + M;                            // W_256^{n2 (kly + q)} at [n2][q]: the group sums' twiddles
     float2* ty1 = twq + 4 * M;                       // the first y pass's twiddles at [j][r] (see there)
     float* hgx = reinterpret_cast<float*>(ty1 + 64); // u_m(x'_i) dx' at [m][i]
-    float* hgy = hgx + k2G * M;                      // u_n(y'_j) dy' at [j][n] (n fastest, k2G wide)
+    float* hgy = hgx + k2G * M;                      // u_n(y'_j) dy' at [j][n] (n fastest, k2G wide); TC: B operand
     int* mlo = reinterpret_cast<int*>(hgy + k2G * M);
     int* mhi = mlo + M;
     int* mdm = mhi + M;
@@ -181,9 +220,23 @@ __global__ void __launch_bounds__(k2NT, 1)
         ty1[i] = P.tw_fwd_n[(4 * j * r - 64 * j * tr) & (N - 1)];
     }
     for (int i = tid; i < G * M; i += NT) hgx[i] = pd.hg_x[i];
-    for (int i = tid; i < k2G * M; i += NT) {
-        const int j = i / k2G, n = i - j * k2G;
-        hgy[i] = n < G ? pd.hg_y[n * M + j] : 0.f;
+    if constexpr (TC) {
+        // B operand: the host's bf16 hi / lo planes of u_n(y'_j) dy' (rows n < 16, K = j), K permuted to kappa
+        __nv_bfloat16* bop = reinterpret_cast<__nv_bfloat16*>(hgy);
+        const __nv_bfloat16* src = reinterpret_cast<const __nv_bfloat16*>(pd.hgy_tc);
+        for (int t = tid; t < 2 * k2G * M; t += NT) {
+            const int hl = t / (k2G * M), rem = t - hl * k2G * M, n = rem / M, kap = rem - n * M;
+            const int j = kap / MR1 + MR0 * (kap % MR1);
+            bop[hl * k2G * M + umma_off(n, kap, M)] =
+                G > 0 ? src[(size_t)hl * P.tc_np * M + umma_off(n, j, M)] : __float2bfloat16_rn(0.f);
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        if (tid < 32) tmem_alloc(smem_u32(&tmem_slot), kTcCols);
+    } else {
+        for (int i = tid; i < k2G * M; i += NT) {
+            const int j = i / k2G, n = i - j * k2G;
+            hgy[i] = n < G ? pd.hg_y[n * M + j] : 0.f;
+        }
     }
     for (int i = tid; i < modes; i += NT) {
         mdm[i] = P.mode_m[i];
@@ -195,6 +248,7 @@ __global__ void __launch_bounds__(k2NT, 1)
     int b = blockIdx.x / P.pols;
     if (tid == 0) {
         abort_flag = 0;
+        if constexpr (TC) asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(&mbar_mma)));
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mb));
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         if (b < A.count) stage_group(tmap, dst, mb, x0, 0, b);
@@ -202,6 +256,12 @@ __global__ void __launch_bounds__(k2NT, 1)
     __syncthreads();
     uint32_t parity = 0;
     bool aborted = false;
+    uint32_t tmem = 0, mma_parity = 0;
+    bool tc_ok = true;                           // TC: every MMA wait so far completed
+    if constexpr (TC) {
+        asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+        tmem = tmem_slot;
+    }
     // the second y pass: task k of this thread is box column c = t mod M, block blk = t / M of t = tid + k NT; its
     // outputs k1 = blk + 16 r2 (r2 < 4) feed the box rows q with kly + q = k1 mod 64.  With (blk - kly) mod 64 =
     // s + 16 tr (s < 16), those are the six rows q = s + 16 m (m < 6), row m fed by output r2 = (m - tr) mod 4;
@@ -381,7 +441,25 @@ __global__ void __launch_bounds__(k2NT, 1)
                         if (fld && DH_IN(P.status, (long long)j * M + i, (long long)M * M, kSiteFusedField)) fld[j * M + i] = v[bb][r];
                     }
                 }
-                if (ov) {
+                if (TC && ov) {
+                    // this thread's rows j = blk + MR0 r sit at K positions MR1 blk + r of rows i (real parts) and
+                    // M + i (imaginary parts), hi plane then lo plane
+                    __nv_bfloat16* aop = reinterpret_cast<__nv_bfloat16*>(work);
+#pragma unroll
+                    for (int bb = 0; bb < BPQ; ++bb) {
+                        const int blk = qb == 0 ? bb * (MR0 / 2) : (bb == 0 ? qb : MR0 - qb);
+                        uint32_t hr[MR1 / 2], lr[MR1 / 2], hm[MR1 / 2], lm[MR1 / 2];
+#pragma unroll
+                        for (int t2 = 0; t2 < MR1 / 2; ++t2) {
+                            split_pair(v[bb][2 * t2].x, v[bb][2 * t2 + 1].x, hr[t2], lr[t2]);
+                            split_pair(v[bb][2 * t2].y, v[bb][2 * t2 + 1].y, hm[t2], lm[t2]);
+                        }
+                        store_run12(aop, i, MR1 * blk, hr);
+                        store_run12(aop, M + i, MR1 * blk, hm);
+                        store_run12(aop + 2 * M * M, i, MR1 * blk, lr);
+                        store_run12(aop + 2 * M * M, M + i, MR1 * blk, lm);
+                    }
+                } else if (ov) {
                     float2 sp[MR1 + 1], sm[MR1 + 1];
                     int jr[MR1 + 1];
                     if (qb == 0) {
@@ -443,17 +521,72 @@ __global__ void __launch_bounds__(k2NT, 1)
                 }
             }
         }
+        if constexpr (TC) asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         __syncthreads();
-        if (ov) {
-            // T[n][i] = sum_qb part[qb][n][i] (groups added in a fixed order), in place of group 0
-            for (int t = tid; t < G * M; t += NT) {
-                float2 s = part[t];
+        float* Ts = reinterpret_cast<float*>(buf2);   // TC: T[n][r] over the consumed window, [16][kTsPitch]
+        if constexpr (TC) {
+            if (ov) {
+                // y contraction: hi hi + hi lo + lo hi per 16-wide K step, two 128-row tiles, FP32 accumulation in
+                // tensor memory (tile t in columns 16 t .. 16 t + 15)
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const uint32_t mbm = smem_u32(&mbar_mma);
+                if (tid == 0 && tc_ok) {
+                    const uint32_t a_hi = smem_u32(work), a_lo = a_hi + 4 * M * M;
+                    const uint32_t b_hi = smem_u32(hgy), b_lo = b_hi + 2 * k2G * M;
+                    constexpr uint32_t idesc = umma_idesc_bf16(128, k2G);
+                    const uint32_t lbo = 128, sbo = 16 * M;
 #pragma unroll
-                for (int q = 1; q < QB; ++q) s = cadd(s, part[q * G * M + t]);
-                part[t] = s;
+                    for (int tile = 0; tile < 2; ++tile) {
+                        const uint32_t ao = tile * 16 * sbo;
+#pragma unroll
+                        for (int ks = 0; ks < M / 16; ++ks) {
+                            const uint32_t ko = ks * 256, d = tmem + tile * k2G;
+                            umma_bf16(d, umma_desc(a_hi + ao + ko, lbo, sbo), umma_desc(b_hi + ko, lbo, sbo), idesc, ks > 0);
+                            umma_bf16(d, umma_desc(a_hi + ao + ko, lbo, sbo), umma_desc(b_lo + ko, lbo, sbo), idesc, 1);
+                            umma_bf16(d, umma_desc(a_lo + ao + ko, lbo, sbo), umma_desc(b_hi + ko, lbo, sbo), idesc, 1);
+                        }
+                    }
+                    umma_commit(mbm);
+                }
+                bool done = false;
+                if (tc_ok) {   // the same for every thread
+                    done = bounded_mbar_wait(mbm, mma_parity, k2WaitLimit);
+                    mma_parity ^= 1u;
+                }
+                // one decision for the whole block (the tensor-memory loads below are warp-collective)
+                const bool all = __syncthreads_and(done ? 1 : 0) != 0;
+                if (tc_ok && !all && tid == 0 && P.status) atomicOr(P.status, 2);
+                tc_ok = tc_ok && all;
+                asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+                const int warp = tid >> 5, lane = tid & 31;
+                if (warp < 4) {
+                    float tv[16];
+                    if (tc_ok) tmem_ld16(tmem + ((uint32_t)(32 * warp) << 16), tv);
+#pragma unroll
+                    for (int n = 0; n < k2G; ++n) Ts[n * kTsPitch + 32 * warp + lane] = tc_ok ? tv[n] : __int_as_float(0x7fc00000);
+                    if (warp < 2) {
+                        // the second tile's rows 128 .. 191 (imaginary parts of columns 32 .. 95)
+                        if (tc_ok) tmem_ld16(tmem + k2G + ((uint32_t)(32 * warp) << 16), tv);
+#pragma unroll
+                        for (int n = 0; n < k2G; ++n)
+                            Ts[n * kTsPitch + 128 + 32 * warp + lane] = tc_ok ? tv[n] : __int_as_float(0x7fc00000);
+                    }
+                }
+                asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+                __syncthreads();
             }
+        } else {
+            if (ov) {
+                // T[n][i] = sum_qb part[qb][n][i] (groups added in a fixed order), in place of group 0
+                for (int t = tid; t < G * M; t += NT) {
+                    float2 s = part[t];
+#pragma unroll
+                    for (int q = 1; q < QB; ++q) s = cadd(s, part[q * G * M + t]);
+                    part[t] = s;
+                }
+            }
+            __syncthreads();
         }
-        __syncthreads();
 
         // ---------------------------------------------------------------- HG overlap, x contraction
         if (ov) {
@@ -464,7 +597,19 @@ __global__ void __launch_bounds__(k2NT, 1)
             for (int t0 = tid & ~31; t0 < modes * 8; t0 += NT) {
                 const int k = (t0 + (tid & 31)) >> 3;
                 float2 sum = make_float2(0.f, 0.f);
-                if (k < modes) {
+                if (TC && k < modes) {
+                    const float* um = hgx + mdm[k] * M;
+                    const float* tr = Ts + mdn[k] * kTsPitch;
+#pragma unroll
+                    for (int h = 0; h < M / 16; ++h) {
+                        const int i = 2 * s8 + 16 * h;
+                        const float2 u = *reinterpret_cast<const float2*>(um + i);
+                        sum.x = fmaf(u.x, tr[i], sum.x);
+                        sum.y = fmaf(u.x, tr[M + i], sum.y);
+                        sum.x = fmaf(u.y, tr[i + 1], sum.x);
+                        sum.y = fmaf(u.y, tr[M + i + 1], sum.y);
+                    }
+                } else if (k < modes) {
                     const float* um = hgx + mdm[k] * M;
                     const float2* tn = part + mdn[k] * M;
 #pragma unroll
@@ -490,6 +635,14 @@ __global__ void __launch_bounds__(k2NT, 1)
     }
     // a tensor copy still in flight (only after an expired wait) must land before the block exits
     if (aborted && tid == 0) mbar_wait_bounded(mb, parity);
+    if constexpr (TC) {
+        // MMAs still in flight (only after an expired wait: the last ones issued) must complete before their tensor
+        // memory is freed
+        if (!tc_ok && tid == 0) bounded_mbar_wait(smem_u32(&mbar_mma), mma_parity ^ 1u, k2WaitLimit);
+        asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+        __syncthreads();
+        if (tid < 32) tmem_free(tmem, kTcCols);
+    }
 }
 
 }  // namespace dhk
@@ -501,8 +654,11 @@ static int g_256_bps[64] = {0};
 static PFN_cuTensorMapEncodeTiled_v12000 g_256_encode = nullptr;
 
 bool use_fused256(const dhk::Plan& P) {
-    return P.n == dhk::k2N && P.ny == dhk::k2N && P.m == dhk::k2M && P.my == dhk::k2M && P.groups <= dhk::k2G &&
-           P.pols <= 2 && P.precision == DH_PRECISION_FP32;
+    if (P.n != dhk::k2N || P.ny != dhk::k2N || P.m != dhk::k2M || P.my != dhk::k2M || P.groups > dhk::k2G || P.pols > 2)
+        return false;
+    if (P.precision == DH_PRECISION_SPLIT_BF16)   // the tensor-core variant: B operand of 16 rows
+        return P.groups == 0 || (P.tc_np == dhk::k2G && P.pol[0].hgy_tc && (P.pols < 2 || P.pol[1].hgy_tc));
+    return P.precision == DH_PRECISION_FP32;
 }
 
 cudaError_t fused256_init() {
@@ -513,7 +669,10 @@ cudaError_t fused256_init() {
         if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) return e != cudaSuccess ? e : cudaErrorNotSupported;
         g_256_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
     }
-    return cudaFuncSetAttribute(dhk::k_fused256, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dhk::F256Smem::bytes);
+    cudaError_t e = cudaFuncSetAttribute(dhk::k_fused256<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)dhk::F256Smem::bytes);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(dhk::k_fused256<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dhk::F256Smem::bytes);
 }
 
 int launch_fused256(Handle* H, const dhk::Plan& P, const void* frames, int dtype, int batch, void* fields, void* coefs,
@@ -531,7 +690,7 @@ int launch_fused256(Handle* H, const dhk::Plan& P, const void* frames, int dtype
     }
     if (!g_256_bps[dev]) {
         int n = 0;
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, dhk::k_fused256, dhk::k2NT, dhk::F256Smem::bytes);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, dhk::k_fused256<false>, dhk::k2NT, dhk::F256Smem::bytes);
         if (e != cudaSuccess) return cuda_fail(e, "occupancy query");
         g_256_bps[dev] = n > 0 ? n : 1;
     }
@@ -569,8 +728,12 @@ int launch_fused256(Handle* H, const dhk::Plan& P, const void* frames, int dtype
     const long long per_pol = std::min<long long>(batch, std::max(1, resident / P.pols));
     const int grid = (int)per_pol * P.pols;
     if (tm) tm->start(st);
-    dhk::k_fused256<<<grid, dhk::k2NT, dhk::F256Smem::bytes, st>>>(P, A, tmap[0], tmap[1]);
-    if (tm) tm->stop(st, "k_fused256");
+    const bool tc = P.precision == DH_PRECISION_SPLIT_BF16;
+    if (tc)
+        dhk::k_fused256<true><<<grid, dhk::k2NT, dhk::F256Smem::bytes, st>>>(P, A, tmap[0], tmap[1]);
+    else
+        dhk::k_fused256<false><<<grid, dhk::k2NT, dhk::F256Smem::bytes, st>>>(P, A, tmap[0], tmap[1]);
+    if (tm) tm->stop(st, tc ? "k_fused256_tc" : "k_fused256");
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "fused launch");
     return DH_SUCCESS;

@@ -340,9 +340,9 @@ std::vector<dh_tuning> candidates(const Settings& s, const Geometry& g) {
         out.push_back(make_tuning(DH_VARIANT_GENERIC, 0, {}));
         return out;
     }
-    // 256 x 256 windows with 96 x 96 fields and the FP32 overlap: the fused kernel (uint16 frames; other frames run
-    // the generic path whatever the choice), then the generic path's chunk sizes and radix plans
-    if (g.n == 256 && g.square() && g.m == 96 && g.groups <= 16 && g.pols <= 2 && s.precision == DH_PRECISION_FP32)
+    // 256 x 256 windows with 96 x 96 fields: the fused kernel (uint16 frames; other frames run the generic path
+    // whatever the choice), then the generic path's chunk sizes and radix plans
+    if (g.n == 256 && g.square() && g.m == 96 && g.groups <= 16 && g.pols <= 2)
         out.push_back(make_tuning(DH_VARIANT_FUSED, 0, {}));
     // non-square geometries: the chunk size only (their radix plans stay the defaults)
     for (int mb : kChunkMb)

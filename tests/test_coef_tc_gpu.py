@@ -31,6 +31,9 @@ def _coefs(setup, frames, precision):
     try:
         dh.configure(h, setup)
         dh.dh_set_precision(h, precision)
+        # the generic path, whose last kernel the coefficient-only contraction replaces (the fused kernels would
+        # take the 256 x 256 geometries with 96 x 96 fields)
+        dh.dh_set_variant(h, dh.DH_VARIANT_GENERIC)
         _, modes, _ = dh.dh_get_output_dims(h)
         B = frames.shape[0]
         c = torch.full((B, setup.pol_count, modes), complex(math.nan, math.nan), dtype=torch.complex64, device=dev)

@@ -1,5 +1,5 @@
-"""The 256 x 256 fused kernel (k_fused256: 96 x 96 fields, uint16 frames, FP32 overlap, up to 16 HG groups)
-against the oracle: window positions (odd origins, frame edges, sub-pixel centres), box positions (wrapping
+"""The 256 x 256 fused kernel (k_fused256: 96 x 96 fields, uint16 frames, FP32 overlap or its split-BF16
+tensor-core variant, up to 16 HG groups) against the oracle: window positions (odd origins, frame edges, sub-pixel centres), box positions (wrapping
 below bin 0, crossing Nyquist), the optional stages, partial outputs, batch sizes around the persistent grid,
 and the rules that send other frames to the generic path."""
 import math
@@ -7,7 +7,7 @@ import math
 import numpy as np
 import pytest
 
-from gpu_util import COEF_TOL, FIELD_TOL, rel_l2, run_library
+from gpu_util import COEF_TOL, FIELD_TOL, SPLIT_COEF_TOL, rel_l2, run_library
 from oracle import digholo_oracle as orc
 from synth import holograms as syn
 
@@ -28,7 +28,7 @@ def _dh():
     return dh
 
 
-def _check(setup, frames, out, idx=None):
+def _check(setup, frames, out, idx=None, coef_tol=COEF_TOL):
     sel = frames if idx is None else frames[idx]
     f_ref, c_ref = orc.process_batch(sel, setup)
     if out["fields"] is not None:
@@ -40,7 +40,7 @@ def _check(setup, frames, out, idx=None):
         c = out["coefs"] if idx is None else out["coefs"][idx]
         assert np.all(np.isfinite(c))
         ec = rel_l2(c, c_ref)
-        assert ec.max() <= COEF_TOL, ec
+        assert ec.max() <= coef_tol, ec
 
 
 def test_precision_geometry_selects_the_fused_kernel():
@@ -163,3 +163,57 @@ def test_deterministic_bitwise():
     a = run_library(s, d["frames"])
     b = run_library(s, d["frames"])
     assert np.array_equal(a["fields"], b["fields"]) and np.array_equal(a["coefs"], b["coefs"])
+
+
+# ----------------------------------------------------------------------------- split-BF16 (tensor-core y contraction)
+SPLIT = 1
+
+
+def test_split_bf16_selects_the_fused_kernel():
+    dh = _dh()
+    s = syn.setup_precision()
+    d = syn.make_frames(s, 3, seed=420)
+    out = run_library(s, d["frames"], precision=SPLIT)
+    assert out["variant"] == dh.DH_VARIANT_FUSED
+    _check(s, d["frames"], out, coef_tol=SPLIT_COEF_TOL)
+    # the fields are the FP32 path's (only the overlap differs)
+    fp32 = run_library(s, d["frames"])
+    assert np.array_equal(out["fields"], fp32["fields"])
+    assert rel_l2(out["coefs"], fp32["coefs"]).max() <= SPLIT_COEF_TOL
+
+
+@pytest.mark.parametrize("groups", [0, 1, 16])
+def test_split_bf16_group_counts(groups):
+    s = syn.with_(syn.setup_precision(), group_count=groups, signal_groups=max(groups, 1))
+    d = syn.make_frames(s, 2, seed=421 + groups)
+    out = run_library(s, d["frames"], precision=SPLIT)
+    _check(s, d["frames"], out, coef_tol=SPLIT_COEF_TOL)
+
+
+def test_split_bf16_options_and_one_polarisation():
+    base = syn.setup_precision()
+    cal, amp = syn.reference_profile(base, sigma_fraction=0.2, floor=200)
+    s = syn.with_(base, defocus=[0.7, -1.1], fill_factor=True, ref_amplitude=amp, ref_cal=cal,
+                  beam_centre=[(163.4 * PX, 255.6 * PX), (477.7 * PX, 256.4 * PX)])
+    d = syn.make_frames(s, 2, seed=425)
+    _check(s, d["frames"], run_library(s, d["frames"], precision=SPLIT), coef_tol=SPLIT_COEF_TOL)
+    s1 = syn.with_(base, pol_count=1, beam_centre=[(300.2 * PX, 260.7 * PX)], tilt_deg=base.tilt_deg[:1],
+                   defocus=[0.3], waist=base.waist[:1], basis="lg")
+    d1 = syn.make_frames(s1, 3, seed=426)
+    _check(s1, d1["frames"], run_library(s1, d1["frames"], precision=SPLIT), coef_tol=SPLIT_COEF_TOL)
+
+
+@pytest.mark.parametrize("count", [1, 230])
+def test_split_bf16_batches_and_determinism(count):
+    s = syn.setup_precision()
+    distinct = syn.make_frames(s, 5, seed=427)["frames"]
+    frames = np.ascontiguousarray(distinct[np.arange(count) % 5])
+    a = run_library(s, frames, precision=SPLIT)
+    b = run_library(s, frames, precision=SPLIT, coefs=True, fields=False)
+    assert np.all(np.isfinite(a["coefs"])) and np.array_equal(a["coefs"], b["coefs"])
+    idx = sorted({0, count // 2, count - 1})
+    f_ref, c_ref = orc.process_batch(distinct[[i % 5 for i in idx]], s)
+    assert rel_l2(a["fields"][idx], f_ref).max() <= FIELD_TOL
+    assert rel_l2(a["coefs"][idx], c_ref).max() <= SPLIT_COEF_TOL
+    for i in range(5, count, 37):
+        assert np.array_equal(a["coefs"][i], a["coefs"][i % 5])

@@ -36,9 +36,9 @@ def test_candidates_for_the_precision_geometry(handle):
     expect = [{"variant": FUSED, "chunk_mb": 0, "radix": []}]
     expect += [{"variant": GENERIC, "chunk_mb": mb, "radix": p} for mb in (24, 48, 96) for p in plans]
     assert c == expect
-    # the split-BF16 overlap has no fused kernel at this size
+    # the split-BF16 overlap has the same candidates (the fused kernel's tensor-core variant first)
     dh.dh_set_precision(handle, dh.DH_PRECISION_SPLIT_BF16)
-    assert all(x["variant"] == GENERIC for x in dh.dh_tuning_candidates(handle))
+    assert dh.dh_tuning_candidates(handle) == expect
     dh.dh_set_precision(handle, dh.DH_PRECISION_FP32)
     for x in c[1:]:
         prod = 1
