@@ -10,11 +10,12 @@
 // pipeline steps 1-2: FFT of the window, selection of the off-axis window; the same sums in another order).
 // Per group (64 rows, staged by two tensor copies of 136-column boxes through a 4-D view of the window rows):
 //   x pass      rows n1 and n1 + 32 packed as one complex row (times the reference-calibration factors when
-//               enabled), radix-16 DIF pass from the staged rows, radix-16 pass in place, then the separation
-//               of the two real spectra (Z(k), conj Z(-k)) on the 96 box columns;
-//   y pass      radix-16 then radix-4 DIF over n1 on the box columns; each output is multiplied by W_256^{n2 k}
-//               and added to the accumulator of its box row (one or two rows per output).  The circular mask
-//               and the beam-centre phase are applied as the last group is added.
+//               enabled), radix-16 DIF pass from the staged rows, radix-16 pass written out in natural frequency
+//               order;
+//   y pass      on the 96 box columns: the separation of the two real spectra (Z(k), conj Z(-k)) as the first
+//               pass reads them, radix-16 then radix-4 DIF over n1; each output is multiplied by W_256^{n2 k}
+//               and added to the sum of its box row (one or two rows per output).  The circular mask and the
+//               beam-centre phase are applied after the last group.
 // Then (pipeline step 3 and digHoloProcessRemoveTilt):
 //   inverse     96-point inverse transforms with radices 12 (prime-factor 3 x 4, no twiddles) and 8, along x
 //               (DIT: the first pass reads the accumulator and writes the window in digit-reversed order) and
@@ -27,8 +28,9 @@
 //               per K step, FP32 accumulation in 32 tensor-memory columns, issued by one thread and awaited on an
 //               mbarrier with a bounded wait), read back by four warps and contracted along x.
 // Shared memory: staging of one row group (34.8 KB, refilled by the next group's tensor copies while the current
-// group is transformed), one work buffer (the packed x rows, then the box columns, then the window during the
-// inverse), the accumulator (then the partial sums of the y contraction) and the tables: 199 KB, one block per SM.
+// group is transformed), two work buffers (the packed x rows, then the box columns, then the window during the
+// inverse; and the x spectra, then the summed window spectrum, then the partial sums of the y contraction or the
+// tensor-core A operand) and the tables: 209 KB, one block per SM.
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -74,13 +76,14 @@ struct F256Smem {
     static constexpr size_t ACCN = (size_t)k2M * k2PA;                                       // float2
     static constexpr size_t TABN = 2 * k2N + 5 * k2M + 4 * k2M + 64;                         // float2
     static constexpr size_t HGN = 2 * (size_t)k2G * k2M;                                     // float
-    static constexpr size_t INTN = 4 * k2M + 2 * (k2G * (k2G + 1) / 2);                      // int
+    static constexpr size_t INTN = 2 * k2M + 2 * (k2G * (k2G + 1) / 2);                      // int
     static constexpr size_t bytes = STG + (WORKN + ACCN + TABN) * 8 + HGN * 4 + INTN * 4;
 };
 static_assert(F256Smem::STG % 16 == 0 && (F256Smem::WORKN * 8) % 16 == 0 && (F256Smem::ACCN * 8) % 16 == 0,
               "16-byte aligned regions");
-static_assert(4 * k2G * k2M <= (int)F256Smem::WORKN, "the partial sums fit in the work buffer");
-static_assert(k2M * k2PB <= (int)F256Smem::ACCN, "the box columns fit in the second buffer");
+static_assert(4 * k2G * k2M <= (int)F256Smem::ACCN, "the partial sums fit in the second buffer");
+static_assert(32 * k2PW <= (int)F256Smem::ACCN, "the x spectra fit in the second buffer");
+static_assert(k2M * k2PB <= (int)F256Smem::WORKN, "the box columns fit in the work buffer");
 
 // 12-point DFT in registers by the prime-factor map (3 x 4, coprime, so no twiddles): input n = (4 n1 + 3 n2)
 // mod 12 enters the 3-point transform n2 at position n1, and output k = (4 k1 + 9 k2) mod 12 leaves the
@@ -143,9 +146,6 @@ __device__ __forceinline__ void store_run12(__nv_bfloat16* op, int row, int kb, 
     }
 }
 
-// Position of frequency k of a 256-point transform after two radix-16 DIF passes.
-__device__ __forceinline__ int pos256(int k) { return (k & 15) * 16 + (k >> 4); }
-
 // TC: the y contraction in split-BF16 on the tensor cores (the split-BF16 precision).
 template <bool TC>
 __global__ void __launch_bounds__(k2NT, 1)
@@ -155,11 +155,11 @@ __global__ void __launch_bounds__(k2NT, 1)
     constexpr int N = k2N, M = k2M, NT = k2NT, MR0 = k2MR0, MR1 = k2MR1;
     constexpr int QB = 4, BPQ = 2;   // partial-sum groups of the y contraction, row blocks per group
     static_assert(M == MR0 * MR1 && MR0 == 8 && MR1 % 2 == 0, "mirrored-row y contraction: eight row blocks");
-    // TC: A = [2M rows][K = M] bf16 hi, then lo, over the work buffer; K position kappa = MR1 blk + r holds field row
-    // j = blk + MR0 r.  The second 128-row tile (rows 128 .. 255) reads 64 rows past the 2M written ones: they only
-    // feed accumulator rows 192 .. 255, which nothing reads, and stay inside the block's shared memory.
-    static_assert(4 * M * M * 2 <= (int)L::WORKN * 8, "the A operand's two planes fit in the work buffer");
-    static_assert(L::STG + 4 * M * M + 256 * M * 2 <= L::bytes, "the second tile's reads stay in shared memory");
+    // TC: A = [2M rows][K = M] bf16 hi, then lo, over the second buffer; K position kappa = MR1 blk + r holds field
+    // row j = blk + MR0 r.  The second 128-row tile (rows 128 .. 255) reads 64 rows past the 2M written ones: they
+    // only feed accumulator rows 192 .. 255, which nothing reads, and stay inside the block's shared memory.
+    static_assert(4 * M * M * 2 <= (int)L::ACCN * 8, "the A operand's two planes fit in the second buffer");
+    static_assert(L::STG + L::WORKN * 8 + 4 * M * M + 256 * M * 2 <= L::bytes, "the second tile's reads stay in shared memory");
     constexpr uint32_t kTcCols = 32;
     constexpr int kTsPitch = 2 * M + 1;   // TC: T[n][r] read back from tensor memory, r < M real, r >= M imaginary
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -185,11 +185,11 @@ __global__ void __launch_bounds__(k2NT, 1)
     int* mhi = mlo + M;
     int* mdm = mhi + M;
     int* mdn = mdm + k2G * (k2G + 1) / 2;
-    int2* zp = reinterpret_cast<int2*>(mdn + k2G * (k2G + 1) / 2);   // positions of Z(k), Z(-k) per box column
-    float2* B = buf2;                                // box columns [c][n1] of the current group
-    float2* acc = work;                              // the window spectrum [c][q] after the last group
-    float2* win = buf2;                              // window [x position][q] during the inverse
-    float2* part = work;                             // y-contraction partial sums [QB][G][M] during the epilogue
+    float2* Z = buf2;                                // x spectra [u][k] of the packed rows, natural order
+    float2* B = work;                                // box columns [c][n1] of the current group
+    float2* acc = buf2;                              // the window spectrum [c][q] after the last group
+    float2* win = work;                              // window [x position][q] during the inverse
+    float2* part = buf2;                             // y-contraction partial sums [QB][G][M] during the epilogue
     const int tid = threadIdx.x;
     const int pol = blockIdx.x % P.pols;
     const PolDev& pd = P.pol[pol];
@@ -208,8 +208,6 @@ __global__ void __launch_bounds__(k2NT, 1)
         cy[i] = pd.corr_y[i];
         mlo[i] = pd.mask_lo[i];
         mhi[i] = pd.mask_hi[i];
-        const int kx = (klx + i) & (N - 1);
-        zp[i] = make_int2(pos256(kx), pos256((N - kx) & (N - 1)));
     }
     for (int i = tid; i < 4 * M; i += NT) twq[i] = P.tw_fwd_n[((i / M) * (kly + i % M)) & (N - 1)];
     for (int i = tid; i < 64; i += NT) {
@@ -323,39 +321,35 @@ __global__ void __launch_bounds__(k2NT, 1)
                     stage_group(tmap, dst, mb, x0, 0, f + fstride);
             }
 
-            // ------------------------------------------------------------ x pass 2: radix 16 in place
+            // ------------------------------------------------------------ x pass 2: radix 16, natural order out
             {
+                // block blk's outputs are frequencies blk + 16 r of packed row u
                 const int u = tid & 31, blk = tid >> 5;
                 float2 v[16];
-                float2* row = work + u * k2PW + 16 * blk;
+                const float2* row = work + u * k2PW + 16 * blk;
 #pragma unroll
                 for (int r = 0; r < 16; ++r) v[r] = row[r];
                 dft16<false>(v);
 #pragma unroll
-                for (int r = 0; r < 16; ++r) row[r] = v[r];
-            }
-            __syncthreads();
-
-            // ------------------------------------------------------------ real-spectra separation on the box columns
-            // items (u, c): packed row u gives rows n1 = u (Z(k) + conj Z(-k)) and n1 = u + 32 (-i (Z(k) -
-            // conj Z(-k))) at box column c, frequency k = klx + c
-            for (int t = tid; t < 32 * M; t += NT) {
-                const int u = t & 31, c = t >> 5;
-                const int2 z = zp[c];
-                const float2 zk = work[u * k2PW + z.x];
-                const float2 zm = work[u * k2PW + z.y];
-                B[c * k2PB + u] = make_float2(zk.x + zm.x, zk.y - zm.y);
-                B[c * k2PB + u + 32] = make_float2(zk.y + zm.y, zm.x - zk.x);
+                for (int r = 0; r < 16; ++r) Z[u * k2PW + blk + 16 * r] = v[r];
             }
             __syncthreads();
 
             // ------------------------------------------------------------ y pass 1: radix 16 over n1 (span 64)
             if (tid < 4 * M) {
+                // box column c, frequency k = klx + c: packed row u gives rows n1 = u (Z(k) + conj Z(-k)) and
+                // n1 = u + 32 (-i (Z(k) - conj Z(-k))), inputs r and r + 8 of this task (u = j + 4 r, r < 8)
                 const int c = tid % M, j = tid / M;
-                float2* col = B + c * k2PB + j;
+                const int kx = (klx + c) & (N - 1), km = (N - kx) & (N - 1);
                 float2 v[16];
 #pragma unroll
-                for (int r = 0; r < 16; ++r) v[r] = col[4 * r];
+                for (int r = 0; r < 8; ++r) {
+                    const float2 zk = Z[(j + 4 * r) * k2PW + kx];
+                    const float2 zm = Z[(j + 4 * r) * k2PW + km];
+                    v[r] = make_float2(zk.x + zm.x, zk.y - zm.y);
+                    v[r + 8] = make_float2(zk.y + zm.y, zm.x - zk.x);
+                }
+                float2* col = B + c * k2PB + j;
                 dft16<false>(v);
 #pragma unroll
                 for (int r = 0; r < 16; ++r) v[r] = cmul(v[r], ty1[j * 16 + r]);   // W_64^{j r} W_4^{-j tr(r)}
@@ -444,7 +438,7 @@ __global__ void __launch_bounds__(k2NT, 1)
                 if (TC && ov) {
                     // this thread's rows j = blk + MR0 r sit at K positions MR1 blk + r of rows i (real parts) and
                     // M + i (imaginary parts), hi plane then lo plane
-                    __nv_bfloat16* aop = reinterpret_cast<__nv_bfloat16*>(work);
+                    __nv_bfloat16* aop = reinterpret_cast<__nv_bfloat16*>(buf2);
 #pragma unroll
                     for (int bb = 0; bb < BPQ; ++bb) {
                         const int blk = qb == 0 ? bb * (MR0 / 2) : (bb == 0 ? qb : MR0 - qb);
@@ -523,7 +517,7 @@ __global__ void __launch_bounds__(k2NT, 1)
         }
         if constexpr (TC) asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         __syncthreads();
-        float* Ts = reinterpret_cast<float*>(buf2);   // TC: T[n][r] over the consumed window, [16][kTsPitch]
+        float* Ts = reinterpret_cast<float*>(work);   // TC: T[n][r] over the consumed window, [16][kTsPitch]
         if constexpr (TC) {
             if (ov) {
                 // y contraction: hi hi + hi lo + lo hi per 16-wide K step, two 128-row tiles, FP32 accumulation in
@@ -531,7 +525,7 @@ __global__ void __launch_bounds__(k2NT, 1)
                 asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
                 const uint32_t mbm = smem_u32(&mbar_mma);
                 if (tid == 0 && tc_ok) {
-                    const uint32_t a_hi = smem_u32(work), a_lo = a_hi + 4 * M * M;
+                    const uint32_t a_hi = smem_u32(buf2), a_lo = a_hi + 4 * M * M;
                     const uint32_t b_hi = smem_u32(hgy), b_lo = b_hi + 2 * k2G * M;
                     constexpr uint32_t idesc = umma_idesc_bf16(128, k2G);
                     const uint32_t lbo = 128, sbo = 16 * M;
