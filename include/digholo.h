@@ -291,7 +291,7 @@ int dh_process_batch(dh_handle h, const void* d_frames, int dtype, int batch, vo
 /* Host-buffer variant of dh_process_batch, as the guide's own processing call works on frames in host memory
  * (digHoloSetBatch / digHoloSetBatchUint16, then digHoloProcessBatch).  h_frames: host [batch][height][width]
  * uint16 or float32; h_fields (nullable): host complex64 [batch][pol][M][M]; h_coefs (nullable, ignored when
- * G = 0): host complex64 [batch][pol][modes].  The batch is cut into chunks that cycle over three internal
+ * G = 0): host complex64 [batch][pol][modes].  The batch is cut into chunks that cycle over four internal
  * streams with their own device staging buffers (at most 256 MiB each, owned by the handle and kept for the
  * next call), so that host-to-device copies, reconstruction and device-to-host copies of consecutive chunks
  * overlap; only the frame rows that hold the polarisation windows are copied to the device.  The kernels and
@@ -300,6 +300,20 @@ int dh_process_batch(dh_handle h, const void* d_frames, int dtype, int batch, vo
  * Page-locked host buffers are needed for the copies to overlap; pageable ones work but copy synchronously. */
 int dh_process_batch_host(dh_handle h, const void* h_frames, int dtype, int batch, void* h_fields, void* h_coefs,
                           void* stream);
+
+/* dh_process_batch_host that returns once the copies and kernels are queued, for streams of batches: the next
+ * call's uploads then start while this call's downloads run.  The work starts after the work already queued on
+ * stream; the outputs of every call made so far are in host memory when dh_process_batch_host_wait returns.
+ * Until then h_frames must stay unchanged and valid, h_fields / h_coefs must not be read, and the handle's
+ * settings must not change.  Calls on one handle run chunk by chunk in call order, so consecutive calls may
+ * reuse the same host buffers.  Page-locked host buffers are needed for the call to return before the copies
+ * complete (pageable ones copy synchronously). */
+int dh_process_batch_host_async(dh_handle h, const void* h_frames, int dtype, int batch, void* h_fields,
+                                void* h_coefs, void* stream);
+
+/* Wait for every dh_process_batch_host_async call made on the handle: returns DH_SUCCESS once their outputs are
+ * in host memory, or the CUDA error of the pipeline (DH_ERROR_CUDA). */
+int dh_process_batch_host_wait(dh_handle h);
 
 /* As dh_process_batch, and also writes the Fourier window that is inverse transformed for every (frame, pol)
  * (digHoloGetFourierPlaneWindow): d_window complex64 [batch][pol][M][M] with

@@ -134,6 +134,8 @@ _PROTOS = {
     "dh_process_batch_noalloc": [_i, _p, _i, _i, _p, _p, _p],
     "dh_process_batch_avg": [_i, _p, _i, _i, _i, _i, _p, _p, _p],
     "dh_process_batch_host": [_i, _p, _i, _i, _p, _p, _p],
+    "dh_process_batch_host_async": [_i, _p, _i, _i, _p, _p, _p],
+    "dh_process_batch_host_wait": [_i],
     "dh_get_alignment": [_i, ctypes.POINTER(dh_setting)],
     "dh_calc_metrics": [_i, _p, _i, _i, ctypes.POINTER(_d), ctypes.POINTER(_d), _p],
     "dh_auto_align": [_i, _p, _i, _i, ctypes.POINTER(_d), ctypes.POINTER(_d), _i, ctypes.POINTER(_d),
@@ -373,6 +375,17 @@ def dh_process_batch_window(h: int, frames, dtype: int, batch: int, window, fiel
 def dh_process_batch_host(h: int, frames, dtype: int, batch: int, fields=None, coefs=None, stream=None) -> None:
     """frames, fields, coefs: host tensors or numpy arrays (page-locked for overlapped copies)."""
     _check(_lib.dh_process_batch_host(h, _frames_ptr(frames, dtype), dtype, batch, _ptr(fields), _ptr(coefs), _stream(stream)))
+
+
+def dh_process_batch_host_async(h: int, frames, dtype: int, batch: int, fields=None, coefs=None, stream=None) -> None:
+    """As dh_process_batch_host, returning once queued: the outputs are valid after dh_process_batch_host_wait
+    (page-locked host tensors; keep them alive and unread until then)."""
+    _check(_lib.dh_process_batch_host_async(h, _frames_ptr(frames, dtype), dtype, batch, _ptr(fields), _ptr(coefs),
+                                            _stream(stream)))
+
+
+def dh_process_batch_host_wait(h: int) -> None:
+    _check(_lib.dh_process_batch_host_wait(h))
 
 
 def dh_process_batch_avg(h: int, frames, dtype: int, batch: int, avg_count: int, avg_mode: int, fields=None,

@@ -5,7 +5,10 @@
 // the host-to-device copy of one chunk, the reconstruction of the previous one and the device-to-host copy of
 // the one before that run at the same time (the two copy directions use separate copy engines).  Only the frame
 // rows that hold the polarisation windows are copied (one strided copy per chunk), and the kernels run with a
-// copy of the plan whose frame height and window rows are those of the cropped frames.
+// copy of the plan whose frame height and window rows are those of the cropped frames.  The asynchronous entry
+// returns once everything is queued, so that the next batch's uploads start behind this one's downloads: each
+// internal stream keeps its own staging slot from call to call, and a call whose slot layout differs from the
+// last one first waits for the streams.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -17,7 +20,7 @@ namespace dh {
 
 namespace {
 
-constexpr int kSlots = 3;
+constexpr int kSlots = 4;
 constexpr size_t kAlign = 256;
 constexpr size_t kSlotCap = 256ull << 20;   // device bytes per slot
 constexpr int kMinChunk = 32;                // frames
@@ -34,6 +37,7 @@ struct HostPipe {
     cudaEvent_t done[kSlots] = {};
     unsigned char* buf = nullptr;
     size_t bytes = 0;
+    size_t slot = 0;                  // staging bytes per stream of the last call (its layout)
 };
 
 void release_pipe(Handle* H) {
@@ -88,7 +92,7 @@ static int ensure_pipe(Handle* H, size_t bytes) {
 }
 
 static int process_host(Handle* H, const void* h_frames, int dtype, int batch, void* h_fields, void* h_coefs,
-                        cudaStream_t caller) {
+                        cudaStream_t caller, bool wait) {
     if (!h_frames) return fail(DH_ERROR_NULLPOINTER, "frames pointer is null");
     if (dtype != DH_DTYPE_U16 && dtype != DH_DTYPE_F32)
         return fail(DH_ERROR_INVALIDARGUMENT, "dtype must be DH_DTYPE_U16 or DH_DTYPE_F32");
@@ -129,6 +133,12 @@ static int process_host(Handle* H, const void* h_frames, int dtype, int batch, v
     rc = ensure_pipe(H, slot * slots);
     if (rc) return rc;
     HostPipe* p = H->pipe;
+    if (p->slot != slot) {
+        // stream s stages its chunks at s * slot: with another slot size the regions of different streams would
+        // overlap the work of earlier calls still in flight
+        for (int s = 0; s < kSlots; ++s) cudaStreamSynchronize(p->st[s]);
+        p->slot = slot;
+    }
     // order the pipeline after the work already queued on the caller's stream
     cudaError_t e = cudaEventRecord(p->start, caller);
     for (int s = 0; s < slots && e == cudaSuccess; ++s) e = cudaStreamWaitEvent(p->st[s], p->start, 0);
@@ -162,7 +172,10 @@ static int process_host(Handle* H, const void* h_frames, int dtype, int batch, v
             if (e != cudaSuccess) rc = cuda_fail(e, "coefficients download");
         }
     }
-    // the results are in host memory when the call returns; the caller's stream also waits for the pipeline
+    // the asynchronous entry leaves the completion to dh_process_batch_host_wait (a wait of the caller's stream
+    // would order the next call's first upload after this call's last download)
+    if (!wait) return rc;
+    // the caller's stream waits for the pipeline; the call returns when the results are in host memory
     for (int s = 0; s < slots; ++s) {
         cudaEventRecord(p->done[s], p->st[s]);
         cudaStreamWaitEvent(caller, p->done[s], 0);
@@ -183,5 +196,27 @@ extern "C" int dh_process_batch_host(dh_handle h, const void* h_frames, int dtyp
     Handle* H = get_handle(h);
     if (!H) return fail(DH_ERROR_INVALIDHANDLE, "invalid handle");
     std::lock_guard<std::mutex> lk(H->mu);
-    return process_host(H, h_frames, dtype, batch, h_fields, h_coefs, (cudaStream_t)stream);
+    return process_host(H, h_frames, dtype, batch, h_fields, h_coefs, (cudaStream_t)stream, true);
+}
+
+extern "C" int dh_process_batch_host_async(dh_handle h, const void* h_frames, int dtype, int batch, void* h_fields,
+                                           void* h_coefs, void* stream) {
+    Handle* H = get_handle(h);
+    if (!H) return fail(DH_ERROR_INVALIDHANDLE, "invalid handle");
+    std::lock_guard<std::mutex> lk(H->mu);
+    return process_host(H, h_frames, dtype, batch, h_fields, h_coefs, (cudaStream_t)stream, false);
+}
+
+extern "C" int dh_process_batch_host_wait(dh_handle h) {
+    Handle* H = get_handle(h);
+    if (!H) return fail(DH_ERROR_INVALIDHANDLE, "invalid handle");
+    std::lock_guard<std::mutex> lk(H->mu);
+    HostPipe* p = H->pipe;
+    if (!p) return DH_SUCCESS;
+    int rc = DH_SUCCESS;
+    for (int s = 0; s < kSlots; ++s) {
+        const cudaError_t e = p->st[s] ? cudaStreamSynchronize(p->st[s]) : cudaSuccess;
+        if (e != cudaSuccess && rc == DH_SUCCESS) rc = cuda_fail(e, "host pipeline");
+    }
+    return rc;
 }

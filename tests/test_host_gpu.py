@@ -85,3 +85,37 @@ def test_host_pipeline_generic_geometry_lg_basis_coefficients_only():
         assert np.array_equal(ch.view(np.uint32), cd.view(np.uint32))
     finally:
         dh.dh_destroy(h)
+
+
+def test_async_host_calls_match_the_device_entry():
+    """dh_process_batch_host_async: three calls back to back into the same host buffers, then one with another
+    batch size (another staging layout) into other buffers, one wait: every output bit-identical to
+    dh_process_batch on device buffers."""
+    import torch
+    import paper_2204_02348_gb300 as dh
+    for name, count in (("batching", 300), ("precision", 70)):
+        s = syn.WORKLOADS[name]()
+        fr = syn.make_frames(s, count, seed=142)["frames"]
+        h = dh.dh_create()
+        try:
+            dh.configure(h, s)
+            fd, cd = _device(dh, torch, h, s, fr)
+            m, modes, _ = dh.dh_get_output_dims(h)
+            hin = torch.from_numpy(fr).pin_memory()
+            nan = complex(math.nan, math.nan)
+            f = torch.full((count, s.pol_count, m, m), nan, dtype=torch.complex64).pin_memory()
+            c = torch.full((count, s.pol_count, modes), nan, dtype=torch.complex64).pin_memory()
+            part = max(1, count // 3)
+            f2 = torch.full((part, s.pol_count, m, m), nan, dtype=torch.complex64).pin_memory()
+            c2 = torch.full((part, s.pol_count, modes), nan, dtype=torch.complex64).pin_memory()
+            for _ in range(3):
+                dh.dh_process_batch_host_async(h, hin, dh.DH_DTYPE_U16, count, f, c)
+            dh.dh_process_batch_host_async(h, hin[:part], dh.DH_DTYPE_U16, part, f2, c2)
+            dh.dh_process_batch_host_wait(h)
+            assert np.array_equal(f.numpy().view(np.uint32), fd.view(np.uint32))
+            assert np.array_equal(c.numpy().view(np.uint32), cd.view(np.uint32))
+            assert np.array_equal(f2.numpy().view(np.uint32), fd[:part].view(np.uint32))
+            assert np.array_equal(c2.numpy().view(np.uint32), cd[:part].view(np.uint32))
+            dh.dh_process_batch_host_wait(h)   # nothing in flight: returns at once
+        finally:
+            dh.dh_destroy(h)
