@@ -421,6 +421,39 @@ __global__ void __launch_bounds__(k2NT, 1)
             for (int t = tid; t < M * QB; t += NT) {
                 const int i = t % M, qb = t / M;
                 const float2 ci = cx[i];
+                if constexpr (TC) {
+                    // one row block at a time (no mirrored pairs): field, then the A operand: rows j = blk + MR0 r
+                    // sit at K positions MR1 blk + r of rows i (real parts) and M + i (imaginary parts), hi plane
+                    // then lo plane
+                    __nv_bfloat16* aop = reinterpret_cast<__nv_bfloat16*>(buf2);
+#pragma unroll 1
+                    for (int bb = 0; bb < BPQ; ++bb) {
+                        const int blk = qb == 0 ? bb * (MR0 / 2) : (bb == 0 ? qb : MR0 - qb);
+                        float2 w[MR1];
+#pragma unroll
+                        for (int r = 0; r < MR1; ++r) w[r] = win[i * k2PA + blk * MR1 + r];
+                        dft12<true>(w);
+#pragma unroll
+                        for (int r = 0; r < MR1; ++r) {
+                            const int j = blk + MR0 * r;
+                            w[r] = cmul(cmul(w[r], ci), cy[j]);
+                            if (fld && DH_IN(P.status, (long long)j * M + i, (long long)M * M, kSiteFusedField)) fld[j * M + i] = w[r];
+                        }
+                        if (ov) {
+                            uint32_t hr[MR1 / 2], lr[MR1 / 2], hm[MR1 / 2], lm[MR1 / 2];
+#pragma unroll
+                            for (int t2 = 0; t2 < MR1 / 2; ++t2) {
+                                split_pair(w[2 * t2].x, w[2 * t2 + 1].x, hr[t2], lr[t2]);
+                                split_pair(w[2 * t2].y, w[2 * t2 + 1].y, hm[t2], lm[t2]);
+                            }
+                            store_run12(aop, i, MR1 * blk, hr);
+                            store_run12(aop, M + i, MR1 * blk, hm);
+                            store_run12(aop + 2 * M * M, i, MR1 * blk, lr);
+                            store_run12(aop + 2 * M * M, M + i, MR1 * blk, lm);
+                        }
+                    }
+                    continue;
+                }
                 float2 v[BPQ][MR1];
 #pragma unroll
                 for (int bb = 0; bb < BPQ; ++bb) {
@@ -435,25 +468,7 @@ __global__ void __launch_bounds__(k2NT, 1)
                         if (fld && DH_IN(P.status, (long long)j * M + i, (long long)M * M, kSiteFusedField)) fld[j * M + i] = v[bb][r];
                     }
                 }
-                if (TC && ov) {
-                    // this thread's rows j = blk + MR0 r sit at K positions MR1 blk + r of rows i (real parts) and
-                    // M + i (imaginary parts), hi plane then lo plane
-                    __nv_bfloat16* aop = reinterpret_cast<__nv_bfloat16*>(buf2);
-#pragma unroll
-                    for (int bb = 0; bb < BPQ; ++bb) {
-                        const int blk = qb == 0 ? bb * (MR0 / 2) : (bb == 0 ? qb : MR0 - qb);
-                        uint32_t hr[MR1 / 2], lr[MR1 / 2], hm[MR1 / 2], lm[MR1 / 2];
-#pragma unroll
-                        for (int t2 = 0; t2 < MR1 / 2; ++t2) {
-                            split_pair(v[bb][2 * t2].x, v[bb][2 * t2 + 1].x, hr[t2], lr[t2]);
-                            split_pair(v[bb][2 * t2].y, v[bb][2 * t2 + 1].y, hm[t2], lm[t2]);
-                        }
-                        store_run12(aop, i, MR1 * blk, hr);
-                        store_run12(aop, M + i, MR1 * blk, hm);
-                        store_run12(aop + 2 * M * M, i, MR1 * blk, lr);
-                        store_run12(aop + 2 * M * M, M + i, MR1 * blk, lm);
-                    }
-                } else if (ov) {
+                if (ov) {
                     float2 sp[MR1 + 1], sm[MR1 + 1];
                     int jr[MR1 + 1];
                     if (qb == 0) {
