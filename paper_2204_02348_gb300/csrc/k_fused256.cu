@@ -6,7 +6,7 @@
 // staging buffer, so the window is transformed along x first and along y by decimation in time over four row
 // groups: window row n = 4 n1 + n2 belongs to group n2, and the spectrum at row frequency k is
 //     X[k] = sum_{n2 < 4} W_256^{n2 k} A_{n2}[k mod 64],   A_{n2} = the 64-point DFT over n1 of group n2's rows,
-// so each group's contribution is added to a 96 x 96 accumulator as soon as it is transformed (the guide's
+// so each group's contribution is added to the 96 x 96 box sums (in registers) as soon as it is transformed (the guide's
 // pipeline steps 1-2: FFT of the window, selection of the off-axis window; the same sums in another order).
 // Per group (64 rows, staged by two tensor copies of 136-column boxes through a 4-D view of the window rows):
 //   x pass      rows n1 and n1 + 32 packed as one complex row (times the reference-calibration factors when
@@ -18,7 +18,7 @@
 //               beam-centre phase are applied after the last group.
 // Then (pipeline step 3 and digHoloProcessRemoveTilt):
 //   inverse     96-point inverse transforms with radices 12 (prime-factor 3 x 4, no twiddles) and 8, along x
-//               (DIT: the first pass reads the accumulator and writes the window in digit-reversed order) and
+//               (DIT: the first pass reads the summed spectrum and writes the window in digit-reversed order) and
 //               along y (DIF);
 //   epilogue    the last y pass in registers with the residual tilt and defocus removal, the field write and the
 //               separable HG contraction (mirrored row pairs, then eight threads per mode along x), as the
@@ -58,7 +58,7 @@ constexpr int k2BoxW = 136;          // staged columns per tensor copy (128 plus
 constexpr int k2BoxBytes = k2BoxW * k2Rows * 2;
 constexpr int k2PW = k2N + 1;        // pitch of the packed x rows (odd: conflict-free column access)
 constexpr int k2PB = k2Rows + 1;     // pitch of the box columns [c][n1]
-constexpr int k2PA = k2M + 1;        // pitch of the accumulator [c][q] and of the window [x][q]
+constexpr int k2PA = k2M + 1;        // pitch of the summed spectrum [c][q] and of the window [x][q]
 constexpr int k2MR0 = 8, k2MR1 = 12; // inverse radix plan (DIF order)
 constexpr long k2WaitLimit = 1L << 24;
 
@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(k2NT, 1)
     static_assert(M == MR0 * MR1 && MR0 == 8 && MR1 % 2 == 0, "mirrored-row y contraction: eight row blocks");
     // TC: A = [2M rows][K = M] bf16 hi, then lo, over the second buffer; K position kappa = MR1 blk + r holds field
     // row j = blk + MR0 r.  The second 128-row tile (rows 128 .. 255) reads 64 rows past the 2M written ones: they
-    // only feed accumulator rows 192 .. 255, which nothing reads, and stay inside the block's shared memory.
+    // only feed tensor-memory rows 192 .. 255, which nothing reads, and stay inside the block's shared memory.
     static_assert(4 * M * M * 2 <= (int)L::ACCN * 8, "the A operand's two planes fit in the second buffer");
     static_assert(L::STG + L::WORKN * 8 + 4 * M * M + 256 * M * 2 <= L::bytes, "the second tile's reads stay in shared memory");
     constexpr uint32_t kTcCols = 32;
