@@ -119,3 +119,30 @@ def test_async_host_calls_match_the_device_entry():
             dh.dh_process_batch_host_wait(h)   # nothing in flight: returns at once
         finally:
             dh.dh_destroy(h)
+
+
+def test_async_host_calls_generic_path_with_scratch_and_lg_basis():
+    """The asynchronous entry on a geometry that runs the generic kernels (1024 x 1024 window, spectra in each
+    staging slot's scratch) with the LG output basis (HG coefficients in scratch before the transform): two calls
+    into the same host buffers, one wait, bit-identical to dh_process_batch."""
+    import torch
+    import paper_2204_02348_gb300 as dh
+    s = syn.with_(syn.serving_geometry("1024x1024_1pol", np.random.default_rng(143)), basis="lg")
+    fr = syn.make_frames(s, 6, seed=144)["frames"]
+    h = dh.dh_create()
+    try:
+        dh.configure(h, s)
+        assert dh.dh_get_variant(h) == dh.DH_VARIANT_GENERIC
+        fd, cd = _device(dh, torch, h, s, fr)
+        m, modes, _ = dh.dh_get_output_dims(h)
+        nan = complex(math.nan, math.nan)
+        hin = torch.from_numpy(fr).pin_memory()
+        f = torch.full((6, 1, m, m), nan, dtype=torch.complex64).pin_memory()
+        c = torch.full((6, 1, modes), nan, dtype=torch.complex64).pin_memory()
+        for _ in range(2):
+            dh.dh_process_batch_host_async(h, hin, dh.DH_DTYPE_U16, 6, f, c)
+        dh.dh_process_batch_host_wait(h)
+        assert np.array_equal(f.numpy().view(np.uint32), fd.view(np.uint32))
+        assert np.array_equal(c.numpy().view(np.uint32), cd.view(np.uint32))
+    finally:
+        dh.dh_destroy(h)
