@@ -146,3 +146,35 @@ def test_async_host_calls_generic_path_with_scratch_and_lg_basis():
         assert np.array_equal(c.numpy().view(np.uint32), cd.view(np.uint32))
     finally:
         dh.dh_destroy(h)
+
+
+def test_host_pipeline_windows_at_different_heights():
+    """Two 256 x 256 windows 100 rows apart (the fused 256 x 256 kernel): the host pipeline uploads the 356 rows
+    that hold both, and each polarisation's window starts at its own row of the cropped frames; blocking and
+    asynchronous calls bit-identical to dh_process_batch."""
+    import torch
+    import paper_2204_02348_gb300 as dh
+    px = syn.PIXEL
+    s = syn.with_(syn.setup_precision(), beam_centre=[(160.0 * px, 200.0 * px), (480.0 * px, 300.0 * px)])
+    fr = syn.make_frames(s, 40, seed=145)["frames"]
+    h = dh.dh_create()
+    try:
+        dh.configure(h, s)
+        assert dh.dh_get_variant(h) == dh.DH_VARIANT_FUSED
+        fd, cd = _device(dh, torch, h, s, fr)
+        fh, ch = _host(dh, torch, h, s, fr)
+        assert np.array_equal(fh.view(np.uint32), fd.view(np.uint32))
+        assert np.array_equal(ch.view(np.uint32), cd.view(np.uint32))
+        m, modes, _ = dh.dh_get_output_dims(h)
+        hin = torch.from_numpy(fr).pin_memory()
+        f = torch.empty((40, 2, m, m), dtype=torch.complex64).pin_memory()
+        c = torch.empty((40, 2, modes), dtype=torch.complex64).pin_memory()
+        dh.dh_process_batch_host_async(h, hin, dh.DH_DTYPE_U16, 40, f, c)
+        dh.dh_process_batch_host_wait(h)
+        assert np.array_equal(f.numpy().view(np.uint32), fd.view(np.uint32))
+        assert np.array_equal(c.numpy().view(np.uint32), cd.view(np.uint32))
+    finally:
+        dh.dh_destroy(h)
+    f_ref, c_ref = orc.process_batch(fr[:2], s)
+    assert rel_l2(fd[:2], f_ref).max() <= FIELD_TOL
+    assert rel_l2(cd[:2], c_ref).max() <= COEF_TOL
