@@ -24,7 +24,7 @@ constexpr int kSlots = 4;
 constexpr size_t kAlign = 256;
 constexpr size_t kSlotCap = 256ull << 20;   // device bytes per slot
 constexpr int kMinChunk = 32;                // frames
-constexpr int kChunksTarget = 8;             // chunks per batch when the batch is large enough
+constexpr int kChunksTarget = 4;             // chunks per batch when the batch is large enough
 
 size_t align_up(size_t v) { return (v + kAlign - 1) & ~(kAlign - 1); }
 
