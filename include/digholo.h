@@ -66,7 +66,8 @@ extern "C" {
 /* Kernel variants of the reconstruction (dh_set_variant).  The guide's counterpart is the FFTW planning mode
  * (digHoloConfigSetFFTWPlanMode), which chooses how a transform is computed without changing its result. */
 #define DH_VARIANT_AUTO 0           /* the library's choice, or the tuner's (dh_autotune) */
-#define DH_VARIANT_FUSED 1          /* single-kernel path, window stays on chip, every pass over 128 x 128 */
+#define DH_VARIANT_FUSED 1          /* single-kernel path, window stays on chip: 128 x 128 windows, and 256 x 256
+                                     * windows with 96 x 96 fields and uint16 frames */
 #define DH_VARIANT_FUSED_PRUNED 2   /* single-kernel path transforming only the columns the window keeps */
 #define DH_VARIANT_GENERIC 3        /* three-kernel path through library scratch (any window size) */
 #define DH_VARIANT_FUSED_GROUPS 4   /* single-kernel path, every 1-D transform inside one 8-thread group, the x
@@ -202,7 +203,8 @@ int dh_set_precision(dh_handle h, int precision);
 /* Hold the handle to one kernel variant (DH_VARIANT_*), as the guide's FFTW planning mode
  * (digHoloConfigSetFFTWPlanMode) selects how transforms are computed; every variant computes the same
  * reconstruction to rounding.  A variant that does not apply to the current settings (a fused variant for a
- * window other than 128 x 128, the pruned and the group variants outside 64 x 64 fields with the FP32 overlap
+ * window other than 128 x 128 or 256 x 256 with 96 x 96 fields (the latter: uint16 frames, at most 16 HG
+ * groups), the pruned and the group variants outside 128 x 128 windows with 64 x 64 fields and the FP32 overlap
  * (the pruned one also needs at most 48 kept columns), or frames whose base or row pitch is not 16-byte
  * aligned) falls back to the next one that does (pruned or groups -> fused -> generic).  DH_VARIANT_AUTO (the
  * default) takes the tuner's choice when one exists for these settings, else the fused variant where it
